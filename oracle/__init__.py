@@ -1,0 +1,220 @@
+"""The oracle: a plain, slow FP64 CPU implementation of the JAX-FLUIDS
+finite-volume RK3 stage (arXiv 2203.13760, Sections 2-3), written in C++
+(``jf_oracle.hpp``) and loaded here with ctypes.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s ``cpu_baseline`` / ``--impl reference`` legs may import this
+package.  The product path (``paper_2203_13760_gb300``) never imports it, and the
+two share no code; the seeded input generators in
+``paper_2203_13760_gb300/inputs.py`` are the only module both sides use.
+
+Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
+  rhs / rk3_step / run   pinned (free stream, conservation, Sod vs exact
+                         Riemann solution, 5th-order convergence, mirror
+                         symmetry, manufactured viscous fields)
+  weno5                  pinned (polynomial exactness, linear weights on
+                         smooth data, non-oscillation at a jump)
+  hllc                   pinned (consistency with the physical flux,
+                         Rankine-Hugoniot for an isolated shock and contact)
+  exact_star/sample      pinned (Rankine-Hugoniot, isentropic and Riemann
+                         invariant relations, contact continuity)
+  jvp_run                pinned (against central finite differences of run)
+  compute_dt             pinned (closed form on uniform states)
+  count_flops            descriptive only (an operation count, not a result)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ["oracle_capi.cpp", "jf_oracle.hpp", "dual.hpp", "exact_riemann.hpp"]
+_lock = threading.Lock()
+_lib = None
+
+BC_PERIODIC = 0
+BC_ZERO_GRADIENT = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (FP64, no FMA contraction, OpenMP)."""
+    newest = max(os.path.getmtime(os.path.join(_HERE, s)) for s in _SOURCES)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", os.path.join(_HERE, "oracle_capi.cpp"), "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``orc::Config`` in jf_oracle.hpp."""
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("bc", ctypes.c_int * 6),
+        ("gamma", ctypes.c_double),
+        ("R", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("Pr", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("convective", ctypes.c_int),
+        ("viscous", ctypes.c_int),
+        ("heat", ctypes.c_int),
+        ("safe", ctypes.c_int),
+    ]
+
+
+def config(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gamma=1.4, R=1.0,
+           mu=0.0, Pr=0.72, eps=1e-6, cfl=0.5, convective=True, viscous=False, heat=False,
+           safe=False) -> Config:
+    n = tuple(int(x) for x in n) + (1,) * (3 - len(n))
+    c = Config()
+    c.n[:] = n
+    c.lo[:] = [float(x) for x in lo]
+    c.hi[:] = [float(x) for x in hi]
+    c.bc[:] = [int(x) for x in bc]
+    c.gamma, c.R, c.mu, c.Pr, c.eps, c.cfl = gamma, R, mu, Pr, eps, cfl
+    c.convective, c.viscous, c.heat, c.safe = int(convective), int(viscous), int(heat), int(safe)
+    return c
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.POINTER
+            d = ctypes.c_double
+            dp = P(d)
+            cp = P(Config)
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_set_threads.restype = ctypes.c_int
+            L.orc_rhs.argtypes = [cp, dp, dp]
+            L.orc_rhs.restype = ctypes.c_int
+            L.orc_compute_dt.argtypes = [cp, dp]
+            L.orc_compute_dt.restype = d
+            L.orc_run.argtypes = [cp, dp, ctypes.c_int, d, d, dp]
+            L.orc_run.restype = ctypes.c_int
+            L.orc_jvp_run.argtypes = [cp, dp, dp, ctypes.c_int, d]
+            L.orc_jvp_run.restype = ctypes.c_int
+            L.orc_weno5.argtypes = [dp, d]
+            L.orc_weno5.restype = d
+            L.orc_hllc.argtypes = [dp, dp, ctypes.c_int, d, dp]
+            L.orc_hllc.restype = None
+            L.orc_exact_star.argtypes = [dp, dp, d, dp]
+            L.orc_exact_star.restype = ctypes.c_int
+            L.orc_exact_sample.argtypes = [dp, dp, d, d, d, ctypes.c_int, dp, dp]
+            L.orc_exact_sample.restype = ctypes.c_int
+            L.orc_count_flops.argtypes = [cp, dp]
+            L.orc_count_flops.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _state(c: Config, U) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    want = (5, c.n[2], c.n[1], c.n[0])
+    if U.size != np.prod(want):
+        raise ValueError(f"state has {U.size} values, config wants {want}")
+    return U.reshape(want).copy()
+
+
+def set_threads(n: int) -> int:
+    return lib().orc_set_threads(int(n))
+
+
+def rhs(c: Config, U) -> np.ndarray:
+    """dU/dt of Eq. (FVD) for the interior state U[5][nz][ny][nx]."""
+    U = _state(c, U)
+    out = np.empty_like(U)
+    if lib().orc_rhs(ctypes.byref(c), _ptr(U), _ptr(out)) != 0:
+        raise ValueError("oracle rejected the configuration")
+    return out
+
+
+def compute_dt(c: Config, U) -> float:
+    U = _state(c, U)
+    return float(lib().orc_compute_dt(ctypes.byref(c), _ptr(U)))
+
+
+def run(c: Config, U, nsteps: int, dt: float = 0.0, t_end: float = 0.0):
+    """nsteps TVD-RK3 steps (fixed dt if dt > 0, else CFL steps up to t_end).
+    Returns (U, t, steps_taken)."""
+    U = _state(c, U)
+    t = ctypes.c_double(0.0)
+    s = lib().orc_run(ctypes.byref(c), _ptr(U), int(nsteps), float(dt), float(t_end), ctypes.byref(t))
+    if s < 0:
+        raise ValueError("oracle rejected the configuration")
+    return U, t.value, s
+
+
+def rk3_step(c: Config, U, dt: float) -> np.ndarray:
+    return run(c, U, 1, dt)[0]
+
+
+def jvp_run(c: Config, U, V, nsteps: int, dt: float):
+    """(U_n, J V) for nsteps fixed-dt RK3 steps, by forward-mode dual numbers."""
+    U = _state(c, U)
+    V = _state(c, V)
+    if lib().orc_jvp_run(ctypes.byref(c), _ptr(U), _ptr(V), int(nsteps), float(dt)) != 0:
+        raise ValueError("oracle rejected the configuration")
+    return U, V
+
+
+def weno5(v, eps: float = 1e-6) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return float(lib().orc_weno5(_ptr(v), float(eps)))
+
+
+def hllc(WL, WR, d: int = 0, gamma: float = 1.4) -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.empty(5)
+    lib().orc_hllc(_ptr(WL), _ptr(WR), int(d), float(gamma), _ptr(F))
+    return F
+
+
+def exact_star(WL, WR, gamma: float = 1.4):
+    """(p*, u*, rho*_L, rho*_R) of the exact Riemann solution; W = (rho, u, p)."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    out = np.empty(4)
+    if lib().orc_exact_star(_ptr(WL), _ptr(WR), float(gamma), _ptr(out)) != 0:
+        raise ValueError("no exact solution (vacuum)")
+    return out
+
+
+def exact_sample(WL, WR, x, t: float, x0: float = 0.5, gamma: float = 1.4) -> np.ndarray:
+    """Exact (rho, u, p) at points x and time t: array of shape (len(x), 3)."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    W = np.empty((x.size, 3))
+    if lib().orc_exact_sample(_ptr(WL), _ptr(WR), float(gamma), float(x0), float(t), x.size, _ptr(x), _ptr(W)) != 0:
+        raise ValueError("no exact solution")
+    return W
+
+
+def count_flops(c: Config) -> dict:
+    """Floating-point operations of the scheme as defined (see oracle_capi.cpp)."""
+    out = np.empty(6)
+    if lib().orc_count_flops(ctypes.byref(c), _ptr(out)) != 0:
+        raise ValueError("oracle rejected the configuration")
+    keys = ["primitives", "convective_faces", "dissipative_faces", "divergence", "rhs_per_cell", "rk_combine"]
+    return dict(zip(keys, out.tolist()))
