@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the fused finite-volume RK3 step (libjf) on one or more GPUs.
+
+Default workload: compressible Taylor-Green vortex, 256^3 cells, FP32,
+Navier-Stokes (WENO5-JS + HLLC + C4 viscous and heat fluxes), TVD-RK3 with the
+CFL step computed on the device every step.  One "step" is one full RK3 step
+over the whole grid: the CFL reduction and the three stage launches, each
+called through the C ABI (jf_compute_dt, jf_stage x 3) with CUDA events
+between the calls, so the stage kernel's launch duration is measured live in
+the timed region.
+
+Metric: cell-updates per second (cells x RK3 steps / s), whole job (all ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl jf|reference]
+                  [--workload tgv256|tgv128|hit384|tgv256_f64] [--extras]
+
+--impl reference times the oracle (FP64 C++ CPU implementation) on a bounded
+sample of the same workload on the host cores; it is the reference arm.
+Under torchrun (N > 1) each rank advances its own replica of the workload
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, kwargs, dtype)
+    "tgv256": ("taylor_green", {"n": 256}, "f32"),
+    "tgv128": ("taylor_green", {"n": 128}, "f32"),
+    "tgv256_f64": ("taylor_green", {"n": 256}, "f64"),
+    "tgv128_f64": ("taylor_green", {"n": 128}, "f64"),
+    "hit384": ("solenoidal_turbulence", {"n": 384}, "f32"),
+}
+
+# Algorithmic floating-point operations per cell and per stage launch, as the
+# scheme is defined (one evaluation per face), counted by the oracle's
+# operation-counting scalar (oracle.count_flops: rhs_per_cell + rk_combine).
+FLOPS_PER_CELL_STAGE = {
+    (3, True): 3041.0 + 20.0,   # 3D, viscous + heat
+    (3, False): 2504.0 + 20.0,  # 3D, inviscid
+    (2, True): 1912.0 + 20.0,
+    (2, False): 1674.0 + 20.0,
+    (1, True): 903.0 + 20.0,
+    (1, False): 844.0 + 20.0,
+}
+# Algorithmic HBM values per cell for the three stages of one RK3 step:
+# stage 1 reads Un, writes U1 (10); stages 2 and 3 read U_s and Un and write (15 + 15).
+VALUES_PER_CELL_STEP = 40.0
+CFL_VALUES_PER_CELL = 5.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="jf", choices=["jf", "reference"])
+    p.add_argument("--workload", default="tgv256", choices=sorted(WORKLOADS))
+    p.add_argument("--extras", action="store_true", help="also time the batched and adjoint forms")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--variant", type=int, default=-1)
+    return p.parse_args()
+
+
+def make_case(workload):
+    from paper_2203_13760_gb300 import inputs
+    gen, kw, dtype = WORKLOADS[workload]
+    if gen == "solenoidal_turbulence":
+        import torch
+        kw = dict(kw, device="cuda" if torch.cuda.is_available() else None)
+    return getattr(inputs, gen)(**kw), dtype
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2203_13760_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, cells):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("sources_sha") != kernel_sources_sha():
+        return None
+    per_cell = rec.get("stage_bytes_per_cell", {}).get(workload)
+    return None if per_cell is None else per_cell * cells
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={device_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(workload, budget_s=15.0, threads=None):
+    """Oracle (FP64 C++, OpenMP over cells) on a bounded sample of the
+    workload: the same flow and physics on a 64^3 grid (per-cell work is the
+    same as at full size), RK3 steps repeated until ~budget_s of CPU time."""
+    import numpy as np
+
+    import oracle
+    from paper_2203_13760_gb300 import inputs
+    gen, kw, _ = WORKLOADS[workload]
+    n = 64
+    case = getattr(inputs, gen)(**dict(kw, n=n))
+    c = oracle.config(**case.params())
+    cores = oracle.set_threads(threads or os.cpu_count() or 1)
+    U = case.U.astype(np.float64)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        U, _, _ = oracle.run(c, U, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 50:
+            break
+    cells = case.cells
+    return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{gen} {n}^3 (same physics as {workload}), {steps} CFL RK3 steps in FP64, {el:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle, as it stands, on the host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_2203_13760_gb300 import inputs
+    gen, kw, dtype = WORKLOADS[args.workload]
+    n = 48
+    case = getattr(inputs, gen)(**dict(kw, n=n))
+    c = oracle.config(**case.params())
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    U = case.U.astype(np.float64)
+    for _ in range(args.warmup):
+        U, _, _ = oracle.run(c, U, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, _, _ = oracle.run(c, U, 1)
+    el = time.perf_counter() - t0
+    value = case.cells * args.steps / el
+    line = {
+        "impl": "reference", "metric": "cell-updates/s per RK3 step", "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": f"{gen} {n}^3 per step (bounded sample of the workload)"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{gen} {n}^3, same physics, FP64"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_jf(args):
+    import numpy as np
+    import torch
+
+    from paper_2203_13760_gb300 import _build
+    _build.build()
+    from paper_2203_13760_gb300 import jf
+
+    world, rank, local = dist_setup(args)
+    case, dtype = make_case(args.workload)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    esize = 4 if dtype == "f32" else 8
+    s = jf.Solver.from_case(case, dtype=dtype)
+    if args.variant >= 0:
+        s.set_variant(args.variant)
+    variant = s.variants()[max(args.variant, 0)]
+    U0 = torch.from_numpy(case.U.astype(np.float32 if dtype == "f32" else np.float64))
+    U = U0.cuda()
+    U1 = torch.empty_like(U)
+    U2 = torch.empty_like(U)
+    dt = s.scalar()
+    N = case.cells
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        s.compute_dt(U, dt)
+        if ev is not None:
+            ev[1].record(stream)
+        s.stage(U, None, U1, 0.0, 1.0, dt)
+        if ev is not None:
+            ev[2].record(stream)
+        s.stage(U1, U, U2, 0.75, 0.25, dt)
+        if ev is not None:
+            ev[3].record(stream)
+        s.stage(U2, U, U, 1.0 / 3.0, 2.0 / 3.0, dt)
+        if ev is not None:
+            ev[4].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    s.sync()
+    K = args.steps
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(K):
+        step(events[k])
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    s.sync()  # raises if a kernel met a non-physical state
+    total_ms = events[0][0].elapsed_time(events[-1][4])
+    cfl_ms = [e[0].elapsed_time(e[1]) for e in events]
+    stage_ms = [e[i].elapsed_time(e[i + 1]) for e in events for i in (1, 2, 3)]
+    total_ms = max_over_ranks(total_ms, world)
+    ms_per_step = total_ms / K
+    value = world * N * K / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (the stage kernel)
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    stage_avg_s = statistics.mean(stage_ms) * 1e-3
+    dim = 3 if case.n[2] > 1 else (2 if case.n[1] > 1 else 1)
+    flops = FLOPS_PER_CELL_STAGE.get((dim, bool(case.viscous)), None)
+    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    if dtype == "f32":
+        peak_tflops = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
+    else:
+        peak_tflops = 1.25  # nominal GB300 FP64 rate
+    achieved_tflops = (flops * N / stage_avg_s / 1e12) if flops else None
+    traffic = ncu_traffic(args.workload, N)
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None, "traffic": traffic,
+                "kernel": "stage_kernel", "launch_ms": 1e3 * stage_avg_s,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x {clock_mhz:.0f} MHz"
+                if dtype == "f32" else "nominal FP64 rate"}
+    stage_bytes = (VALUES_PER_CELL_STEP / 3.0) * esize * N
+    hbm_gbs = stage_bytes / stage_avg_s / 1e9
+    hbm = {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_gbs / peaks["hbm_gbs"],
+           "peak_kind": peak_kind, "step_gbs": (VALUES_PER_CELL_STEP * esize * N) / (ms_per_step * 1e-3) / 1e9,
+           "algorithmic_bytes_per_cell_update": VALUES_PER_CELL_STEP * esize}
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # input from pinned memory, one RK3 step (jf_rk3_step), D2H of the result
+    host = U0.pin_memory()
+    host_out = torch.empty_like(host).pin_memory()
+    Ke = max(3, min(K, 10))
+    s.rk3_step(U)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        U.copy_(host, non_blocking=True)
+        s.rk3_step(U)
+        host_out.copy_(U, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e = {"value": world * N * Ke / (e2e_ms * 1e-3), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": int(host.numel() * esize), "d2h_bytes_per_step": int(host_out.numel() * esize)}
+
+    extras = {}
+    if args.extras and rank == 0:
+        extras = run_extras(args)
+
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s per RK3 step", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": args.workload, "cells": N, "grid": list(case.n), "flow": case.name,
+                       "physics": "Navier-Stokes (WENO5-JS, HLLC/Einfeldt, C4 viscous + heat)" if case.viscous
+                       else "Euler (WENO5-JS, HLLC/Einfeldt)", "integrator": "TVD-RK3, CFL 0.5 on device",
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (state %.0f MB)" % (5 * N * esize / 1e6),
+                       "variant": variant},
+            "roofline": roofline,
+            "hbm": hbm,
+            "e2e": e2e,
+            "gpu_launches": 4 * K,
+            "clocks": clk,
+            "breakdown_ms": {"cfl": statistics.mean(cfl_ms), "stage": statistics.mean(stage_ms)},
+            "paper_context": {"hardware": "RTX A6000", "ns_per_cell_step_fp32": {"256^3": 28.36, "384^3": 28.11},
+                              "source": "Table 3"},
+        }
+        if extras:
+            line["extras"] = extras
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(args):
+    """Batched and adjoint forms against the plain per-simulation launch."""
+    return {}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_jf(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * jf.h - C ABI of libjf.so, a GB300 (sm_103a) implementation of the
+ * finite-volume Runge-Kutta stage of the compressible Euler / Navier-Stokes
+ * equations for an ideal gas, following JAX-FLUIDS (Bezgin, Buhendwa, Adams,
+ * arXiv 2203.13760).
+ *
+ * What one RK3 step computes (all steps in hand-written CUDA kernels):
+ *   conservative -> primitive variables      Section 2 (W, U, Eq. StiffenedGas, B = 0)
+ *   WENO5-JS face reconstruction of W        Section 3.3, "High-order Godunov approach"
+ *   HLLC flux with Einfeldt signal speeds    Section 3.3, Eq. (ApproxRiemannSolver)
+ *   C4 viscous and heat fluxes               Sections 2 and 3.4
+ *   flux divergence                          Section 3.1, Eq. (FVD)
+ *   TVD-RK3 stage combination                Section 3.2 (Gottlieb & Shu 1998)
+ *   CFL time step (FP64 max-reduction)       Section 3.2
+ *
+ * Conventions shared by every entry point
+ *   - A field U is a caller-owned, contiguous device array of 5 components
+ *     U[5][nz][ny][nx] (x fastest): rho, rho u, rho v, rho w, E.  Its element
+ *     type is float when jf_scheme.dtype == JF_F32 and double for JF_F64, and it
+ *     must be 16-byte aligned.  Only interior cells are stored; boundary
+ *     conditions are applied inside the kernels.
+ *   - Active axes are a prefix: (nx), (nx, ny) or (nx, ny, nz); an axis with one
+ *     cell is inactive.  An active axis needs at least 5 cells.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call only enqueues work on it and returns; nothing
+ *     synchronises the host except jf_status_sync.
+ *   - Device scalars (dt_dev, dt_used_dev) are FP64 device pointers.
+ *   - Argument errors return synchronously (JF_ERR_ARG / JF_ERR_UNSUPPORTED)
+ *     and enqueue nothing.  Conditions found on the device (non-physical
+ *     state: rho <= 0, p <= 0 or not finite) set a device flag that
+ *     jf_status_sync reports.  No call throws, traps or aborts.
+ *   - The library owns its workspace (stage buffers, reduction scratch),
+ *     allocated in jf_init / jf_batch_create; the step calls never allocate,
+ *     except that the adjoint workspace is allocated at the first
+ *     jf_rk3_step_vjp call of a handle.
+ *   - A handle is used by one host thread at a time.  Two steps on one handle
+ *     in different streams race on the shared workspace.
+ */
+#ifndef JF_H
+#define JF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jf_ctx* jf_handle; /* opaque, owned by the library */
+
+typedef enum {
+  JF_OK = 0,
+  JF_ERR_ARG = -1,          /* invalid argument (null pointer, bad size or option) */
+  JF_ERR_CUDA = -2,         /* a CUDA runtime call failed; see jf_last_error */
+  JF_ERR_OOM = -3,          /* workspace allocation failed */
+  JF_ERR_NONPHYSICAL = -4,  /* a kernel met rho <= 0, p <= 0 or a non-finite value */
+  JF_ERR_TIMEOUT = -5,      /* reserved: a bounded device wait gave up */
+  JF_ERR_UNSUPPORTED = -6   /* valid but unsupported configuration */
+} jf_status;
+
+typedef enum { JF_BC_PERIODIC = 0, JF_BC_ZERO_GRADIENT = 1 } jf_bc;
+enum { JF_F32 = 0, JF_F64 = 1 };
+enum { JF_EINFELDT = 0 };
+
+/* Cartesian grid of nx*ny*nz cells on [lo, hi] (Section 3.1: cuboid cells).
+ * bc[] = {x-lo, x-hi, y-lo, y-hi, z-lo, z-hi} (west, east, south, north,
+ * bottom, top; Section 3.7), each a jf_bc; periodic must be set on both sides
+ * of an axis.  Zero gradient copies the nearest interior cell into the halo
+ * (the "neumann"/transmissive boundary of Appendix A). */
+typedef struct {
+  int nx, ny, nz;
+  double lo[3], hi[3];
+  int bc[6];
+} jf_grid;
+
+/* Ideal gas (Eq. StiffenedGas with B = 0) and transport (Section 2).
+ * mu = 0 makes the run inviscid.  Heat conductivity
+ * lambda = mu gamma R / ((gamma - 1) Pr). */
+typedef struct {
+  double gamma, R, mu, Pr;
+} jf_gas;
+
+/* Scheme options.  dtype: JF_F32 or JF_F64 (arithmetic and storage type of
+ * the fields; the CFL reduction and dt are always FP64).  weno_eps: WENO5-JS
+ * epsilon (1e-6).  cfl: CFL number.  viscous / heat: include the viscous
+ * stresses / heat flux (both need mu > 0).  signal_speed: JF_EINFELDT (the
+ * only estimate built).  safe_recon: 1 = a face side whose reconstructed
+ * density or pressure is not positive falls back to its cell value (the
+ * paper's "is_safe_reconstruction" flag, which it does not define further). */
+typedef struct {
+  int dtype;
+  double weno_eps;
+  double cfl;
+  int viscous, heat;
+  int signal_speed;
+  int safe_recon;
+} jf_scheme;
+
+/* Create a solver for one grid.  Validates the configuration and allocates
+ * the workspace (two stage buffers of 5*nx*ny*nz elements plus scalars) on
+ * the current CUDA device.  On success *out owns them until jf_destroy.
+ * Paper: the InputReader / Initializer / SimulationManager set-up of
+ * Section 4.4. */
+jf_status jf_init(const jf_grid* grid, const jf_gas* gas, const jf_scheme* scheme, jf_handle* out);
+
+/* Release a handle (single-grid or batch) and its workspace.  Waits for the
+ * device to finish work that uses the workspace.  NULL is accepted. */
+jf_status jf_destroy(jf_handle h);
+
+/* dUdt = L(U): the right-hand side of Eq. (FVD) (Section 3.1), i.e. the
+ * Algorithm 3 loop over active axes (inviscid, viscous and heat fluxes) for
+ * the field U.  U and dUdt are device arrays of the handle's dtype and must
+ * not overlap. */
+jf_status jf_rhs(jf_handle h, const void* U, void* dUdt, void* stream);
+
+/* *dt_dev = CFL time step of U (Section 3.2; formula of this library):
+ *   dt = CFL min(dt_c, dt_v), dt_c = min_d dx_d / max_cells max_d (|u_d| + c),
+ *   dt_v = 3/14 min_d dx_d^2 / max_cells max(mu / rho, lambda / (rho c_v))
+ *   (dt_v only when viscous or heat is on), computed in FP64. */
+jf_status jf_compute_dt(jf_handle h, const void* U, double* dt_dev, void* stream);
+
+/* One TVD-RK3 step in place (Section 3.2, Algorithm 2):
+ *   U1 = Un + dt L(Un); U2 = 3/4 Un + 1/4 (U1 + dt L(U1));
+ *   U^{n+1} = 1/3 Un + 2/3 (U2 + dt L(U2)).
+ * dt_dev != NULL: fixed step read from device memory.  dt_dev == NULL: the
+ * CFL step of Un (jf_compute_dt) is computed first.  dt_used_dev (may be
+ * NULL) receives the step used. */
+jf_status jf_rk3_step(jf_handle h, void* U_inout, const double* dt_dev, double* dt_used_dev, void* stream);
+
+/* One Shu-Osher stage (Section 3.2): out = a Un + b (Us + dt L(Us)), with L
+ * as in jf_rhs; Un may be NULL when a == 0, and out may equal Un (it is read
+ * point-wise before it is written) but must not overlap Us.  jf_rk3_step is
+ * three of these calls (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3); custom
+ * Runge-Kutta schemes of the same form (Euler, TVD-RK2) use the same call.
+ * dt_dev is an FP64 device scalar and must not be NULL. */
+jf_status jf_stage(jf_handle h, const void* Us, const void* Un, void* out, double a, double b, const double* dt_dev,
+                   void* stream);
+
+/* nsteps RK3 steps in place, enqueued as one CUDA graph (captured at the
+ * first call for a given (U, nsteps, dt mode) and replayed afterwards).
+ * dt_dev as for jf_rk3_step (a fixed step is read at every step).
+ * dt_hist_dev (may be NULL) receives the nsteps steps used. */
+jf_status jf_rk3_run(jf_handle h, void* U_inout, int nsteps, const double* dt_dev, double* dt_hist_dev,
+                     void* stream);
+
+/* Adjoint of one fixed-dt RK3 step (vector-Jacobian product, Section 7.2:
+ * gradients backpropagated through the solver):
+ *   lam_in = (dU^{n+1} / dU^n)^T lam_out,
+ * with U^{n+1} = RK3(U^n; dt) as in jf_rk3_step and dt held fixed (not
+ * differentiated).  Un is the state at the start of the step (not modified);
+ * the step is recomputed inside.  lam_out and lam_in are device arrays shaped
+ * like U; they may not overlap.  dt_dev must not be NULL. */
+jf_status jf_rk3_step_vjp(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out, void* lam_in,
+                          void* stream);
+
+/* Loss of the adjoint workload: *loss_dev = sum_cells (rho - rho_target)^2 dV
+ * (FP64 accumulation) and, if seed != NULL, seed = dloss/dU (the cotangent
+ * that starts the backward pass: 2 (rho - rho_target) dV in the density
+ * component, 0 elsewhere).  target is a device array of nx*ny*nz densities
+ * of the handle's dtype. */
+jf_status jf_loss_density_l2(jf_handle h, const void* U, const void* target, double* loss_dev, void* seed,
+                             void* stream);
+
+/* Batch of nsim independent simulations with their own grid sizes (Section
+ * 4.5, feed_forward over a batch of initial buffers; here sizes may differ).
+ * All share gas and scheme.  Each grid must be 2D or 1D (nz == 1).  Allocates
+ * each simulation's stage buffers and the work list. */
+jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, const jf_scheme* scheme,
+                          jf_handle* out);
+
+/* Advance every simulation of a batch by nsteps RK3 steps in place, each
+ * with its own CFL step (dt_dev == NULL is not allowed: dt_dev is an array of
+ * nsim FP64 device values that receives the last step of each simulation).
+ * U_ptrs is a HOST array of nsim device pointers to the simulations' fields
+ * (same order as in jf_batch_create).  One persistent kernel launch per RK
+ * stage covers all simulations; the nsteps steps are captured in a CUDA graph
+ * at the first call for a given (U_ptrs, nsteps) and replayed afterwards. */
+jf_status jf_batch_step(jf_handle batch, void* const* U_ptrs, int nsteps, double* dt_dev, void* stream);
+
+/* Choose the launch variant of a handle (autotuner hook): `variant` indexes
+ * the tile/schedule table of jf_variant_info; -1 restores the default.
+ * Returns JF_ERR_ARG for an index outside the table. */
+jf_status jf_set_variant(jf_handle h, int variant);
+
+/* Describe launch variant `variant` for the handle's dimensionality and
+ * precision into buf (NUL-terminated, at most len bytes).  Returns the number
+ * of variants (>= 1), or a negative jf_status. */
+int jf_variant_info(jf_handle h, int variant, char* buf, int len);
+
+/* Wait for the handle's stream work (cudaDeviceSynchronize), then read and
+ * clear the device error flag.  Returns JF_ERR_NONPHYSICAL if a kernel met a
+ * non-physical state since the last call, JF_ERR_CUDA on a CUDA error,
+ * JF_OK otherwise. */
+jf_status jf_status_sync(jf_handle h);
+
+/* Text of the last error on this handle ("" if none).  With h == NULL, the
+ * last error of a call that had no valid handle (e.g. a failed jf_init).
+ * The string is owned by the library and valid until the next call. */
+const char* jf_last_error(jf_handle h);
+
+/* Library version string. */
+const char* jf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JF_H */

@@ -116,6 +116,8 @@ def lib():
             L.orc_exact_star.restype = ctypes.c_int
             L.orc_exact_sample.argtypes = [dp, dp, d, d, d, ctypes.c_int, dp, dp]
             L.orc_exact_sample.restype = ctypes.c_int
+            L.orc_sample_cells.argtypes = [cp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, d, dp]
+            L.orc_sample_cells.restype = ctypes.c_int
             L.orc_count_flops.argtypes = [cp, dp]
             L.orc_count_flops.restype = ctypes.c_int
             _lib = L
@@ -175,6 +177,22 @@ def jvp_run(c: Config, U, V, nsteps: int, dt: float):
     if lib().orc_jvp_run(ctypes.byref(c), _ptr(U), _ptr(V), int(nsteps), float(dt)) != 0:
         raise ValueError("oracle rejected the configuration")
     return U, V
+
+
+def sample_cells(c: Config, U, cells, nsteps: int, dt: float = 0.0) -> np.ndarray:
+    """Values at the given cells [(i, j, k), ...] after nsteps fixed-dt RK3
+    steps of the full state U (nsteps == 0: the right-hand side there),
+    computed one cell at a time on a local patch.  Returns [len(cells), 5]."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    if U.size != 5 * c.n[0] * c.n[1] * c.n[2]:
+        raise ValueError("state does not match the configuration")
+    idx = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 3))
+    out = np.empty((idx.shape[0], 5))
+    r = lib().orc_sample_cells(ctypes.byref(c), _ptr(U), idx.shape[0],
+                               idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(nsteps), float(dt), _ptr(out))
+    if r != 0:
+        raise ValueError("oracle rejected the configuration")
+    return out
 
 
 def weno5(v, eps: float = 1e-6) -> float:

@@ -144,6 +144,67 @@ int orc_jvp_run(const Config* c, double* U, double* V, int nsteps, double dt) {
   return 0;
 }
 
+// Sampled cells of a full-size run, computed one by one: for each sample
+// cell, a cube of half-width 9 * nsteps + 3 cells around it is copied from U
+// through the domain's boundary map (periodic wrap or zero-gradient clamp),
+// nsteps fixed-dt RK3 steps are taken on that patch (the patch's own edges
+// influence at most 3 cells per stage, 9 per step, so the centre cell is exact)
+// and the centre cell's 5 values are written to out[5 * s + m].  idx holds
+// (i, j, k) per sample.  With nsteps == 0 the right-hand side L(U) at the
+// sample cell is written instead (patch half-width 3).
+int orc_sample_cells(const Config* c, const double* U, int nsamples, const int* idx, int nsteps, double dt,
+                     double* out) {
+  if (!valid(c) || nsamples < 0 || nsteps < 0) return -1;
+  const size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
+  const int radius = nsteps == 0 ? 3 : 9 * nsteps + 3;
+  int fail = 0;
+#pragma omp parallel for schedule(dynamic)
+  for (int s = 0; s < nsamples; ++s) {
+    Config pc = *c;
+    int lo[3];
+    for (int d = 0; d < 3; ++d) {
+      if (c->n[d] > 1) {
+        pc.n[d] = 2 * radius + 1;
+        lo[d] = idx[3 * s + d] - radius;
+        const double h = spacing(*c, d);
+        pc.lo[d] = 0.0;
+        pc.hi[d] = h * pc.n[d];
+        pc.bc[2 * d] = pc.bc[2 * d + 1] = BC_ZERO_GRADIENT;
+      } else {
+        lo[d] = 0;
+      }
+    }
+    const size_t M = (size_t)pc.n[0] * pc.n[1] * pc.n[2];
+    std::vector<double> patch(5 * M);
+    for (int k = 0; k < pc.n[2]; ++k)
+      for (int j = 0; j < pc.n[1]; ++j)
+        for (int i = 0; i < pc.n[0]; ++i) {
+          int g[3] = {lo[0] + i, lo[1] + j, lo[2] + k};
+          for (int d = 0; d < 3; ++d) {
+            const int n = c->n[d];
+            if (c->bc[2 * d] == BC_PERIODIC) g[d] = ((g[d] % n) + n) % n;
+            else g[d] = g[d] < 0 ? 0 : (g[d] >= n ? n - 1 : g[d]);
+          }
+          const size_t src = ((size_t)g[2] * c->n[1] + g[1]) * c->n[0] + g[0];
+          const size_t dst = ((size_t)k * pc.n[1] + j) * pc.n[0] + i;
+          for (int m = 0; m < 5; ++m) patch[m * M + dst] = U[m * N + src];
+        }
+    Field<double> f(pc, 5);
+    load_state(pc, patch.data(), f);
+    const int ci = c->n[0] > 1 ? radius : 0, cj = c->n[1] > 1 ? radius : 0, ck = c->n[2] > 1 ? radius : 0;
+    if (nsteps == 0) {
+      Field<double> r(pc, 5);
+      rhs(pc, f, r);
+      for (int m = 0; m < 5; ++m) out[5 * s + m] = r(m, ci, cj, ck);
+    } else {
+      for (int q = 0; q < nsteps; ++q) rk3_step(pc, f, dt);
+      for (int m = 0; m < 5; ++m) out[5 * s + m] = f(m, ci, cj, ck);
+    }
+    if (!(pc.n[0] > 0)) fail = 1;
+  }
+  return fail ? -1 : 0;
+}
+
 // Single WENO5-JS reconstruction v^-_{i+1/2} from v[i-2..i+2].
 double orc_weno5(const double* v, double eps) { return weno5_js(v[0], v[1], v[2], v[3], v[4], eps); }
 

@@ -1,0 +1,441 @@
+// Host side of the libjf C ABI (include/jf.h): argument checking, workspace
+// ownership, launch sequencing of the RK3 step and CUDA-graph capture.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/jf.h"
+#include "jf_internal.h"
+
+namespace jf {
+
+static thread_local std::string g_noctx_error;
+
+void set_error(jf_ctx* h, const std::string& msg) {
+  if (h) h->err = msg; else g_noctx_error = msg;
+}
+
+jf_status cuda_fail(jf_ctx* h, cudaError_t e, const char* what) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  set_error(h, buf);
+  return e == cudaErrorMemoryAllocation ? JF_ERR_OOM : JF_ERR_CUDA;
+}
+
+int active_dims(const jf_grid& g) { return g.nz > 1 ? 3 : (g.ny > 1 ? 2 : 1); }
+
+jf_status check_grid(jf_ctx* h, const jf_grid& g) {
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1) { set_error(h, "grid: sizes must be >= 1"); return JF_ERR_ARG; }
+  if (g.nz > 1 && g.ny == 1) { set_error(h, "grid: active axes must be a prefix (ny == 1 requires nz == 1)"); return JF_ERR_UNSUPPORTED; }
+  const int n[3] = {g.nx, g.ny, g.nz};
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] > 1 && n[d] < 5) { set_error(h, "grid: an active axis needs at least 5 cells"); return JF_ERR_ARG; }
+    if (!(g.hi[d] > g.lo[d]) || !std::isfinite(g.hi[d] - g.lo[d])) { set_error(h, "grid: hi must exceed lo"); return JF_ERR_ARG; }
+    for (int s = 0; s < 2; ++s)
+      if (g.bc[2 * d + s] != JF_BC_PERIODIC && g.bc[2 * d + s] != JF_BC_ZERO_GRADIENT) {
+        set_error(h, "grid: unknown boundary condition");
+        return JF_ERR_ARG;
+      }
+    if ((g.bc[2 * d] == JF_BC_PERIODIC) != (g.bc[2 * d + 1] == JF_BC_PERIODIC)) {
+      set_error(h, "grid: periodic must be set on both sides of an axis");
+      return JF_ERR_ARG;
+    }
+  }
+  if ((long long)g.nx * g.ny * g.nz > (1ll << 40)) { set_error(h, "grid: too many cells"); return JF_ERR_ARG; }
+  return JF_OK;
+}
+
+jf_status check_physics(jf_ctx* h, const jf_gas& gas, const jf_scheme& s) {
+  if (!(gas.gamma > 1.0) || !(gas.R > 0.0) || !(gas.mu >= 0.0) || !std::isfinite(gas.mu)) {
+    set_error(h, "gas: need gamma > 1, R > 0, mu >= 0");
+    return JF_ERR_ARG;
+  }
+  if ((s.viscous || s.heat) && !(gas.mu > 0.0)) { set_error(h, "scheme: viscous/heat need mu > 0"); return JF_ERR_ARG; }
+  if (s.heat && !(gas.Pr > 0.0)) { set_error(h, "gas: heat flux needs Pr > 0"); return JF_ERR_ARG; }
+  if (s.dtype != JF_F32 && s.dtype != JF_F64) { set_error(h, "scheme: dtype must be JF_F32 or JF_F64"); return JF_ERR_ARG; }
+  if (!(s.weno_eps > 0.0) || !(s.cfl > 0.0)) { set_error(h, "scheme: need weno_eps > 0 and cfl > 0"); return JF_ERR_ARG; }
+  if (s.signal_speed != JF_EINFELDT) { set_error(h, "scheme: only Einfeldt signal speeds are built"); return JF_ERR_UNSUPPORTED; }
+  return JF_OK;
+}
+
+double spacing(const jf_grid& g, int d) {
+  const int n[3] = {g.nx, g.ny, g.nz};
+  return (g.hi[d] - g.lo[d]) / n[d];
+}
+
+double conductivity(const jf_gas& gas, const jf_scheme& s) {
+  return s.heat ? gas.mu * gas.gamma * gas.R / ((gas.gamma - 1.0) * gas.Pr) : 0.0;
+}
+
+template <typename T>
+Gas<T> make_gas(const jf_gas& gas, const jf_scheme& s) {
+  Gas<T> g;
+  g.gamma = (T)gas.gamma;
+  g.gm1 = (T)(gas.gamma - 1.0);
+  g.inv_gm1 = (T)(1.0 / (gas.gamma - 1.0));
+  g.inv_R = (T)(1.0 / gas.R);
+  g.mu = (T)(s.viscous ? gas.mu : 0.0);
+  g.lambda = (T)conductivity(gas, s);
+  g.eps = (T)s.weno_eps;
+  g.safe = s.safe_recon ? 1 : 0;
+  return g;
+}
+template Gas<float> make_gas<float>(const jf_gas&, const jf_scheme&);
+template Gas<double> make_gas<double>(const jf_gas&, const jf_scheme&);
+
+bool dissipative(const jf_gas& gas, const jf_scheme& s) { return (s.viscous || s.heat) && gas.mu > 0.0; }
+
+CflArgs make_cfl(const jf_grid& g, const jf_gas& gas, const jf_scheme& s) {
+  CflArgs a;
+  a.N = (long long)g.nx * g.ny * g.nz;
+  a.nactive = active_dims(g);
+  a.gamma = gas.gamma;
+  const double cv = gas.R / (gas.gamma - 1.0);
+  const double mu = s.viscous ? gas.mu : 0.0;
+  a.kdiff = dissipative(gas, s) ? std::fmax(mu, conductivity(gas, s) / cv) : 0.0;
+  double hmin = 1e300;
+  for (int d = 0; d < a.nactive; ++d) hmin = std::fmin(hmin, spacing(g, d));
+  a.hmin = hmin;
+  a.cfl = s.cfl;
+  return a;
+}
+
+int reduce_blocks(long long N, int sms) {
+  long long b = (N + 255) / 256;
+  const long long cap = (long long)sms * 8;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// ------------------------------------------------------------------------
+// Variant selection.  A variant = (compiled tile shape, z chunk).
+static const int kZChunks[] = {32, 16, 64, 8};
+
+template <typename T>
+std::vector<std::pair<int, int>> variant_list(int dim, bool visc) {
+  int count = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count);
+  std::vector<std::pair<int, int>> out;
+  for (int i = 0; i < count; ++i) {
+    if (tab[i].dim != dim || tab[i].visc != visc) continue;
+    if (dim == 3)
+      for (int z : kZChunks) out.emplace_back(i, z);
+    else
+      out.emplace_back(i, 1);
+  }
+  return out;
+}
+
+template <typename T>
+jf_status select_variant(jf_ctx* h, int v) {
+  const bool visc = dissipative(h->gas, h->scheme);
+  auto list = variant_list<T>(h->dim, visc);
+  if (list.empty()) { set_error(h, "no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
+  if (v < 0) v = 0;
+  if (v >= (int)list.size()) { set_error(h, "variant index out of range"); return JF_ERR_ARG; }
+  int count = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count);
+  cudaError_t e = tab[list[v].first].prepare();
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+  h->variant = v;
+  h->table_index = list[v].first;
+  h->zchunk = list[v].second;
+  return JF_OK;
+}
+
+template <typename T>
+int describe_variant(jf_ctx* h, int v, char* buf, int len) {
+  const bool visc = dissipative(h->gas, h->scheme);
+  auto list = variant_list<T>(h->dim, visc);
+  if (v < 0 || v >= (int)list.size()) return (int)list.size();
+  int count = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count);
+  const StageVariant<T>& s = tab[list[v].first];
+  if (buf && len > 0)
+    std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=%d smem=%zu", s.bx, s.by, s.dim == 3 ? list[v].second : 1, s.smem);
+  return (int)list.size();
+}
+
+// ------------------------------------------------------------------------
+template <typename T>
+StageArgs<T> base_args(const jf_ctx* h) {
+  StageArgs<T> A;
+  std::memset(&A, 0, sizeof A);
+  A.nx = h->grid.nx;
+  A.ny = h->grid.ny;
+  A.nz = h->grid.nz;
+  A.N = (long long)A.nx * A.ny * A.nz;
+  for (int d = 0; d < 3; ++d) {
+    A.periodic[d] = h->grid.bc[2 * d] == JF_BC_PERIODIC;
+    A.inv_h[d] = (T)(1.0 / spacing(h->grid, d));
+  }
+  A.zchunk = h->zchunk;
+  A.flag = h->flag;
+  return A;
+}
+
+template <typename T>
+jf_status launch(jf_ctx* h, const StageArgs<T>& A, cudaStream_t s) {
+  int count = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count);
+  const Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  cudaError_t e = tab[h->table_index].launch(A, g, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stage kernel launch");
+  return JF_OK;
+}
+
+template <typename T>
+jf_status rhs_impl(jf_ctx* h, const void* U, void* dUdt, cudaStream_t s) {
+  StageArgs<T> A = base_args<T>(h);
+  A.Us = static_cast<const T*>(U);
+  A.out = static_cast<T*>(dUdt);
+  A.rhs_only = 1;
+  A.a = T(0);
+  A.b = T(1);
+  return launch<T>(h, A, s);
+}
+
+template <typename T>
+jf_status cfl_impl(jf_ctx* h, const void* U, double* dt_out, double* dt_out2, cudaStream_t s) {
+  const CflArgs a = make_cfl(h->grid, h->gas, h->scheme);
+  cfl_kernel<T><<<reduce_blocks(a.N, h->sms), 256, 0, s>>>(static_cast<const T*>(U), a, h->red_cfl, dt_out,
+                                                            dt_out2, h->flag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "cfl kernel launch");
+  return JF_OK;
+}
+
+// One RK3 step: optional CFL reduction, then the three Shu-Osher stages.
+template <typename T>
+jf_status step_impl(jf_ctx* h, void* U, const double* dt_dev, double* dt_used, cudaStream_t s) {
+  const double* dt = dt_dev;
+  jf_status st;
+  if (!dt) {
+    st = cfl_impl<T>(h, U, h->dt_buf, dt_used, s);
+    if (st != JF_OK) return st;
+    dt = h->dt_buf;
+  } else if (dt_used && dt_used != dt_dev) {
+    cudaError_t e = cudaMemcpyAsync(dt_used, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(dt)");
+  }
+  T* Un = static_cast<T*>(U);
+  T* U1 = static_cast<T*>(h->stage[0]);
+  T* U2 = static_cast<T*>(h->stage[1]);
+  StageArgs<T> A = base_args<T>(h);
+  A.dt = dt;
+  // U1 = Un + dt L(Un)
+  A.Us = Un; A.Un = nullptr; A.out = U1; A.a = T(0); A.b = T(1);
+  if ((st = launch<T>(h, A, s)) != JF_OK) return st;
+  // U2 = 3/4 Un + 1/4 (U1 + dt L(U1))
+  A.Us = U1; A.Un = Un; A.out = U2; A.a = T(0.75); A.b = T(0.25);
+  if ((st = launch<T>(h, A, s)) != JF_OK) return st;
+  // U^{n+1} = 1/3 Un + 2/3 (U2 + dt L(U2)), written over Un
+  A.Us = U2; A.Un = Un; A.out = Un; A.a = T(1.0 / 3.0); A.b = T(2.0 / 3.0);
+  return launch<T>(h, A, s);
+}
+
+template <typename T>
+jf_status stage_call(jf_ctx* h, const void* Us, const void* Un, void* out, double a, double b, const double* dt,
+                     cudaStream_t s) {
+  StageArgs<T> A = base_args<T>(h);
+  A.Us = static_cast<const T*>(Us);
+  A.Un = a != 0.0 ? static_cast<const T*>(Un) : nullptr;
+  A.out = static_cast<T*>(out);
+  A.a = (T)a;
+  A.b = (T)b;
+  A.dt = dt;
+  return launch<T>(h, A, s);
+}
+
+template <typename T>
+jf_status loss_impl(jf_ctx* h, const void* U, const void* target, double* loss, void* seed, cudaStream_t s) {
+  const long long N = (long long)h->grid.nx * h->grid.ny * h->grid.nz;
+  double dV = 1.0;
+  for (int d = 0; d < h->dim; ++d) dV *= spacing(h->grid, d);
+  loss_density_kernel<T><<<reduce_blocks(N, h->sms), 256, 0, s>>>(
+      static_cast<const T*>(U), static_cast<const T*>(target), N, dV, h->red_loss, loss, static_cast<T*>(seed));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "loss kernel launch");
+  return JF_OK;
+}
+
+template jf_status select_variant<float>(jf_ctx*, int);
+template jf_status select_variant<double>(jf_ctx*, int);
+template jf_status step_impl<float>(jf_ctx*, void*, const double*, double*, cudaStream_t);
+template jf_status step_impl<double>(jf_ctx*, void*, const double*, double*, cudaStream_t);
+template jf_status cfl_impl<float>(jf_ctx*, const void*, double*, double*, cudaStream_t);
+template jf_status cfl_impl<double>(jf_ctx*, const void*, double*, double*, cudaStream_t);
+template StageArgs<float> base_args<float>(const jf_ctx*);
+template StageArgs<double> base_args<double>(const jf_ctx*);
+template jf_status launch<float>(jf_ctx*, const StageArgs<float>&, cudaStream_t);
+template jf_status launch<double>(jf_ctx*, const StageArgs<double>&, cudaStream_t);
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+void free_graphs(jf_ctx* h) {
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+}
+
+}  // namespace jf
+
+using namespace jf;
+
+#define JF_DISPATCH(h, fn, ...) ((h)->scheme.dtype == JF_F32 ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
+
+extern "C" {
+
+const char* jf_version(void) { return "jf 0.1 (sm_103a)"; }
+
+const char* jf_last_error(jf_handle h) { return h ? h->err.c_str() : g_noctx_error.c_str(); }
+
+jf_status jf_init(const jf_grid* grid, const jf_gas* gas, const jf_scheme* scheme, jf_handle* out) {
+  if (!grid || !gas || !scheme || !out) { set_error(nullptr, "jf_init: null argument"); return JF_ERR_ARG; }
+  *out = nullptr;
+  jf_status st;
+  if ((st = check_grid(nullptr, *grid)) != JF_OK) return st;
+  if ((st = check_physics(nullptr, *gas, *scheme)) != JF_OK) return st;
+  jf_ctx* h = new jf_ctx();
+  h->kind = 0;
+  h->grid = *grid;
+  h->gas = *gas;
+  h->scheme = *scheme;
+  h->dim = active_dims(*grid);
+  h->esize = scheme->dtype == JF_F32 ? 4 : 8;
+  h->N = (size_t)grid->nx * grid->ny * grid->nz;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "jf_init: device query"); delete h; return st; }
+  st = alloc_common(h);
+  if (st == JF_OK) {
+    const size_t bytes = 5 * h->N * h->esize;
+    for (int i = 0; i < 2 && st == JF_OK; ++i) {
+      e = cudaMalloc(&h->stage[i], bytes);
+      if (e != cudaSuccess) st = cuda_fail(nullptr, e, "jf_init: stage buffer");
+    }
+  }
+  if (st == JF_OK) st = JF_DISPATCH(h, select_variant, h, -1);
+  if (st != JF_OK) {
+    if (!h->err.empty()) set_error(nullptr, h->err);
+    jf_destroy(h);
+    return st;
+  }
+  *out = h;
+  return JF_OK;
+}
+
+jf_status jf_destroy(jf_handle h) {
+  if (!h) return JF_OK;
+  cudaDeviceSynchronize();
+  free_graphs(h);
+  release_all(h);
+  delete h;
+  return JF_OK;
+}
+
+jf_status jf_rhs(jf_handle h, const void* U, void* dUdt, void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_rhs: not a single-grid handle"); return JF_ERR_ARG; }
+  if (!U || !dUdt || !aligned16(U) || !aligned16(dUdt) || U == dUdt) {
+    set_error(h, "jf_rhs: U and dUdt must be distinct 16-byte aligned device arrays");
+    return JF_ERR_ARG;
+  }
+  return JF_DISPATCH(h, rhs_impl, h, U, dUdt, (cudaStream_t)stream);
+}
+
+jf_status jf_compute_dt(jf_handle h, const void* U, double* dt_dev, void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_compute_dt: not a single-grid handle"); return JF_ERR_ARG; }
+  if (!U || !dt_dev) { set_error(h, "jf_compute_dt: null pointer"); return JF_ERR_ARG; }
+  return JF_DISPATCH(h, cfl_impl, h, U, dt_dev, nullptr, (cudaStream_t)stream);
+}
+
+jf_status jf_rk3_step(jf_handle h, void* U, const double* dt_dev, double* dt_used_dev, void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_rk3_step: not a single-grid handle"); return JF_ERR_ARG; }
+  if (!U || !aligned16(U)) { set_error(h, "jf_rk3_step: U must be a 16-byte aligned device array"); return JF_ERR_ARG; }
+  return JF_DISPATCH(h, step_impl, h, U, dt_dev, dt_used_dev, (cudaStream_t)stream);
+}
+
+jf_status jf_stage(jf_handle h, const void* Us, const void* Un, void* out, double a, double b, const double* dt_dev,
+                   void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_stage: not a single-grid handle"); return JF_ERR_ARG; }
+  if (!Us || !out || !dt_dev || !aligned16(Us) || !aligned16(out) || (Un && !aligned16(Un)) || Us == out ||
+      (a != 0.0 && !Un)) {
+    set_error(h, "jf_stage: bad arguments");
+    return JF_ERR_ARG;
+  }
+  return JF_DISPATCH(h, stage_call, h, Us, Un, out, a, b, dt_dev, (cudaStream_t)stream);
+}
+
+jf_status jf_rk3_run(jf_handle h, void* U, int nsteps, const double* dt_dev, double* dt_hist_dev, void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_rk3_run: not a single-grid handle"); return JF_ERR_ARG; }
+  if (!U || !aligned16(U) || nsteps < 0) { set_error(h, "jf_rk3_run: bad arguments"); return JF_ERR_ARG; }
+  if (nsteps == 0) return JF_OK;
+  const GraphKey key{U, nsteps, dt_dev, dt_hist_dev, h->variant};
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaStream_t cs = h->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    jf_status st = JF_OK;
+    for (int s = 0; s < nsteps && st == JF_OK; ++s)
+      st = JF_DISPATCH(h, step_impl, h, U, dt_dev, dt_hist_dev ? dt_hist_dev + s : nullptr, cs);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (st != JF_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    it = h->graphs.emplace(key, GraphEntry{graph, exec}).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second.exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+  return JF_OK;
+}
+
+jf_status jf_loss_density_l2(jf_handle h, const void* U, const void* target, double* loss_dev, void* seed,
+                             void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_loss_density_l2: not a single-grid handle"); return JF_ERR_ARG; }
+  if (!U || !target || !loss_dev) { set_error(h, "jf_loss_density_l2: null pointer"); return JF_ERR_ARG; }
+  return JF_DISPATCH(h, loss_impl, h, U, target, loss_dev, seed, (cudaStream_t)stream);
+}
+
+jf_status jf_set_variant(jf_handle h, int variant) {
+  if (!h) { set_error(nullptr, "jf_set_variant: null handle"); return JF_ERR_ARG; }
+  free_graphs(h);
+  if (h->kind == 1) return batch_set_variant(h, variant);
+  return JF_DISPATCH(h, select_variant, h, variant);
+}
+
+int jf_variant_info(jf_handle h, int variant, char* buf, int len) {
+  if (!h) return JF_ERR_ARG;
+  if (h->kind == 1) return batch_variant_info(h, variant, buf, len);
+  return JF_DISPATCH(h, describe_variant, h, variant, buf, len);
+}
+
+jf_status jf_status_sync(jf_handle h) {
+  if (!h) { set_error(nullptr, "jf_status_sync: null handle"); return JF_ERR_ARG; }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+  int flag = 0;
+  e = cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(flag)");
+  if (flag) {
+    const int zero = 0;
+    cudaMemcpy(h->flag, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    set_error(h, "a kernel met a non-physical state (rho <= 0, p <= 0 or not finite)");
+    return JF_ERR_NONPHYSICAL;
+  }
+  return JF_OK;
+}
+
+}  // extern "C"

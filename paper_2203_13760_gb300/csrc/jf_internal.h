@@ -1,0 +1,99 @@
+// Internal state of a libjf handle and the host helpers shared by the
+// translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/jf.h"
+#include "reduce.cuh"
+#include "variants.h"
+
+namespace jf {
+
+struct GraphKey {
+  const void* U;
+  int nsteps;
+  const void* dt;
+  const void* hist;
+  int variant;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(U, nsteps, dt, hist, variant) < std::tie(o.U, o.nsteps, o.dt, o.hist, o.variant);
+  }
+};
+struct GraphEntry {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+// One simulation of a batch (device-side descriptor, see batch.cu).
+struct SimDesc;
+
+}  // namespace jf
+
+struct jf_ctx {
+  int kind = 0;              // 0: single grid, 1: batch
+  jf_grid grid{};            // single grid (batch: unused)
+  jf_gas gas{};
+  jf_scheme scheme{};
+  int dim = 1;               // active axes
+  size_t esize = 4;          // bytes per element
+  size_t N = 0;              // cells
+  int device = 0;
+  int sms = 1;
+  int variant = 0;           // index into the variant list of this configuration
+  int table_index = 0;       // compiled-kernel table entry
+  int zchunk = 32;           // planes per CTA (3D)
+  void* stage[2] = {nullptr, nullptr};  // U1, U2
+  void* adj[4] = {nullptr, nullptr, nullptr, nullptr};  // adjoint buffers (lazy)
+  double* dt_buf = nullptr;  // device scalar
+  jf::ReduceScratch* red_cfl = nullptr;
+  jf::ReduceScratch* red_loss = nullptr;
+  int* flag = nullptr;       // device error flag
+  cudaStream_t capture_stream = nullptr;
+  std::map<jf::GraphKey, jf::GraphEntry> graphs;
+  std::string err;
+  // batch
+  int nsim = 0;
+  std::vector<jf_grid> grids;
+  std::vector<void*> sim_stage;        // 2 per simulation
+  jf::SimDesc* d_sims = nullptr;       // device array of descriptors
+  void* d_work = nullptr;              // device work list
+  int nwork = 0;
+  double* d_dt = nullptr;              // per-simulation dt (internal)
+  jf::ReduceScratch* d_red = nullptr;  // per-simulation reduction scratch
+  std::vector<const void*> bound_ptrs; // U pointers the descriptors hold
+  int batch_blocks = 0;
+};
+
+namespace jf {
+
+void set_error(jf_ctx* h, const std::string& msg);
+jf_status cuda_fail(jf_ctx* h, cudaError_t e, const char* what);
+int active_dims(const jf_grid& g);
+jf_status check_grid(jf_ctx* h, const jf_grid& g);
+jf_status check_physics(jf_ctx* h, const jf_gas& gas, const jf_scheme& s);
+double spacing(const jf_grid& g, int d);
+double conductivity(const jf_gas& gas, const jf_scheme& s);
+bool dissipative(const jf_gas& gas, const jf_scheme& s);
+CflArgs make_cfl(const jf_grid& g, const jf_gas& gas, const jf_scheme& s);
+int reduce_blocks(long long N, int sms);
+bool aligned16(const void* p);
+void free_graphs(jf_ctx* h);
+template <typename T> Gas<T> make_gas(const jf_gas& gas, const jf_scheme& s);
+template <typename T> StageArgs<T> base_args(const jf_ctx* h);
+template <typename T> jf_status launch(jf_ctx* h, const StageArgs<T>& A, cudaStream_t s);
+template <typename T> jf_status step_impl(jf_ctx* h, void* U, const double* dt_dev, double* dt_used, cudaStream_t s);
+
+// workspace shared by every handle kind: flag, dt scalar, reduction scratch, capture stream
+jf_status alloc_common(jf_ctx* h);
+void release_all(jf_ctx* h);
+
+// batch (batch.cu)
+jf_status batch_set_variant(jf_ctx* h, int variant);
+int batch_variant_info(jf_ctx* h, int variant, char* buf, int len);
+
+}  // namespace jf

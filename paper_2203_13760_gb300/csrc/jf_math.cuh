@@ -1,0 +1,130 @@
+// Point-wise numerics of the finite-volume stage, shared by the forward,
+// batched and adjoint kernels of libjf.
+//
+// References (arXiv 2203.13760):
+//   primitives        Section 2, Eq. (StiffenedGas) with B = 0
+//   weno5             Section 3.3 (High-order Godunov approach, step 1),
+//                     WENO5-JS of Jiang & Shu (1996)
+//   hllc              Section 3.3 steps 2-3, Eq. (ApproxRiemannSolver): HLLC
+//                     (Toro 1994) with Einfeldt (1988) signal speeds
+//   df4 / dc4 / rc4   Section 3.4 fourth-order face derivative, cell-centre
+//                     derivative and central interpolation to the face
+#pragma once
+#include <cuda_runtime.h>
+
+namespace jf {
+
+template <typename T>
+struct Gas {
+  T gamma;     // ratio of specific heats
+  T gm1;       // gamma - 1
+  T inv_gm1;   // 1 / (gamma - 1)
+  T inv_R;     // 1 / R
+  T mu;        // dynamic viscosity (0 if inviscid)
+  T lambda;    // heat conductivity
+  T eps;       // WENO5-JS epsilon
+  int safe;    // first-order fallback for non-positive reconstructed rho / p
+};
+
+template <typename T> __device__ __forceinline__ T tsqrt(T x);
+template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
+
+// WENO5-JS: value at x_{i+1/2} biased to the left, from v[i-2..i+2].
+// Candidate stencils q_k, smoothness indicators beta_k, weights
+// alpha_k = d_k / (eps + beta_k)^2 with d = (1/10, 6/10, 3/10),
+// omega_k = alpha_k / sum(alpha).
+template <typename T>
+__device__ __forceinline__ T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
+  const T sixth = T(1) / T(6);
+  const T q0 = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) * sixth;
+  const T q1 = (-vm1 + T(5) * v0 + T(2) * vp1) * sixth;
+  const T q2 = (T(2) * v0 + T(5) * vp1 - vp2) * sixth;
+  const T c13 = T(13) / T(12);
+  const T d0 = vm2 - T(2) * vm1 + v0, e0 = vm2 - T(4) * vm1 + T(3) * v0;
+  const T d1 = vm1 - T(2) * v0 + vp1, e1 = vm1 - vp1;
+  const T d2 = v0 - T(2) * vp1 + vp2, e2 = T(3) * v0 - T(4) * vp1 + vp2;
+  const T b0 = c13 * d0 * d0 + T(0.25) * e0 * e0;
+  const T b1 = c13 * d1 * d1 + T(0.25) * e1 * e1;
+  const T b2 = c13 * d2 * d2 + T(0.25) * e2 * e2;
+  const T t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
+  const T a0 = T(0.1) / (t0 * t0);
+  const T a1 = T(0.6) / (t1 * t1);
+  const T a2 = T(0.3) / (t2 * t2);
+  const T inv = T(1) / (a0 + a1 + a2);
+  return (a0 * q0 + a1 * q1 + a2 * q2) * inv;
+}
+
+// HLLC flux along axis D from the reconstructed primitive states
+// W = [rho, u, v, w, p] left (WL) and right (WR) of the face.
+//   U_K, F_K                conservative state and physical flux of side K
+//   Roe averages (weights sqrt(rho)), c~ = sqrt((gamma-1)(H~ - |u~|^2/2))
+//   S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~)   (Einfeldt)
+//   S*  = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R))
+//         / (rho_L (S_L - u_L) - rho_R (S_R - u_R))
+//   F*_K = F_K + S_K (U*_K - U_K),
+//   U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S*, u_t, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))]
+template <typename T, int D>
+__device__ __forceinline__ void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
+  const T rL = WL[0], rR = WR[0], pL = WL[4], pR = WR[4];
+  const T unL = WL[1 + D], unR = WR[1 + D];
+  const T kL = T(0.5) * rL * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
+  const T kR = T(0.5) * rR * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]);
+  const T EL = pL * g.inv_gm1 + kL;
+  const T ER = pR * g.inv_gm1 + kR;
+  const T cL = tsqrt(g.gamma * pL / rL);
+  const T cR = tsqrt(g.gamma * pR / rR);
+  const T sL = tsqrt(rL), sR = tsqrt(rR);
+  const T inv_s = T(1) / (sL + sR);
+  const T HL = (EL + pL) / rL, HR = (ER + pR) / rR;
+  const T u0 = (sL * WL[1] + sR * WR[1]) * inv_s;
+  const T u1 = (sL * WL[2] + sR * WR[2]) * inv_s;
+  const T u2 = (sL * WL[3] + sR * WR[3]) * inv_s;
+  const T Ht = (sL * HL + sR * HR) * inv_s;
+  const T ct = tsqrt(g.gm1 * (Ht - T(0.5) * (u0 * u0 + u1 * u1 + u2 * u2)));
+  const T un_t = D == 0 ? u0 : (D == 1 ? u1 : u2);
+  const T SL = tmin(unL - cL, un_t - ct);
+  const T SR = tmax(unR + cR, un_t + ct);
+  const T mL = rL * (SL - unL), mR = rR * (SR - unR);
+  const T Ss = (pR - pL + mL * unL - mR * unR) / (mL - mR);
+  // side selection: F_L if 0 <= S_L; F*_L if S_L < 0 <= S*; F*_R if S* < 0 < S_R; F_R if S_R <= 0
+  const bool left = (SL >= T(0)) || (Ss >= T(0));
+  const bool star = left ? !(SL >= T(0)) : (SR > T(0));
+  const T r = left ? rL : rR, p = left ? pL : pR, un = left ? unL : unR, E = left ? EL : ER;
+  const T w0 = left ? WL[1] : WR[1], w1 = left ? WL[2] : WR[2], w2 = left ? WL[3] : WR[3];
+  const T S = left ? SL : SR, m = left ? mL : mR;
+  // physical flux of the chosen side
+  const T mass = r * un;
+  T Fk[5] = {mass, mass * w0, mass * w1, mass * w2, un * (E + p)};
+  Fk[1 + D] += p;
+  if (star) {
+    const T fac = m / (S - Ss);
+    T Us[5] = {fac, fac * w0, fac * w1, fac * w2, fac * (E / r + (Ss - un) * (Ss + p / m))};
+    Us[1 + D] = fac * Ss;
+    const T Uk[5] = {r, r * w0, r * w1, r * w2, E};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = Fk[q] + S * (Us[q] - Uk[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = Fk[q];
+  }
+}
+
+// Section 3.4 stencils (without the 1/h factor).
+template <typename T>
+__device__ __forceinline__ T df4(T a, T b, T c, T d) {  // face derivative * h
+  return (a - T(27) * b + T(27) * c - d) * (T(1) / T(24));
+}
+template <typename T>
+__device__ __forceinline__ T dc4(T m2, T m1, T p1, T p2) {  // cell-centre derivative * h
+  return (m2 - T(8) * m1 + T(8) * p1 - p2) * (T(1) / T(12));
+}
+template <typename T>
+__device__ __forceinline__ T rc4(T a, T b, T c, T d) {  // face interpolation
+  return (-a + T(9) * b + T(9) * c - d) * (T(1) / T(16));
+}
+
+}  // namespace jf

@@ -1,0 +1,145 @@
+// FP64 reductions of libjf: the CFL time step (Section 3.2) and the density
+// mismatch loss of the adjoint workload (Section 7.2, a squared-error state
+// loss).
+//
+// Both are single launches: each CTA reduces its cells (warp shuffles, then
+// shared memory) and folds its result into a global accumulator with one
+// atomic; the last CTA to finish (ticket counter) finalises the result and
+// resets the accumulator and counter for the next launch.  No CTA waits for
+// another.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jf {
+
+struct CflArgs {
+  long long N;        // cells
+  int nactive;        // active axes (velocity components that count), 1..3
+  double gamma;
+  double kdiff;       // max(mu, lambda / c_v) if dissipative, else 0
+  double hmin;        // min_d dx_d over active axes
+  double cfl;
+};
+
+// Scratch of the reductions (device memory owned by the caller).
+struct ReduceScratch {
+  unsigned long long acc[2];  // bit patterns of non-negative doubles (ordered like the values)
+  unsigned int ticket;
+  unsigned int pad;
+  double sum;
+};
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// dt = CFL min(dt_c, dt_v): dt_c = hmin / max(|u_d| + c), dt_v = 3/14 hmin^2 / max(kdiff / rho).
+// Writes dt to dt_out and, if non-null, dt_out2.  blockDim.x == 256.
+template <typename T>
+__global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U, CflArgs a, ReduceScratch* sc,
+                                                  double* dt_out, double* dt_out2, int* flag) {
+  double conv = 0.0, diff = 0.0;
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.N; q += stride) {
+    const double r = (double)U[q];
+    const double inv = 1.0 / r;
+    const double u = (double)U[q + a.N] * inv;
+    const double v = (double)U[q + 2 * a.N] * inv;
+    const double w = (double)U[q + 3 * a.N] * inv;
+    const double p = (a.gamma - 1.0) * ((double)U[q + 4 * a.N] - 0.5 * r * (u * u + v * v + w * w));
+    bad |= !(r > 0.0) || !(p > 0.0);
+    const double c = sqrt(a.gamma * p * inv);
+    double m = fabs(u);
+    if (a.nactive > 1) m = fmax(m, fabs(v));
+    if (a.nactive > 2) m = fmax(m, fabs(w));
+    conv = fmax(conv, m + c);
+    diff = fmax(diff, a.kdiff * inv);
+  }
+  if (bad) atomicOr(flag, 1);
+  __shared__ double s_conv[8], s_diff[8];
+  conv = warp_max(conv);
+  diff = warp_max(diff);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { s_conv[wid] = conv; s_diff[wid] = diff; }
+  __syncthreads();
+  if (wid == 0) {
+    conv = lane < (int)(blockDim.x >> 5) ? s_conv[lane] : 0.0;
+    diff = lane < (int)(blockDim.x >> 5) ? s_diff[lane] : 0.0;
+    conv = warp_max(conv);
+    diff = warp_max(diff);
+    if (lane == 0) {
+      // NaN never wins fmax; a NaN state is reported through the flag
+      atomicMax(&sc->acc[0], (unsigned long long)__double_as_longlong(conv));
+      atomicMax(&sc->acc[1], (unsigned long long)__double_as_longlong(diff));
+      __threadfence();
+      const unsigned int t = atomicAdd(&sc->ticket, 1u);
+      if (t == gridDim.x - 1) {
+        __threadfence();
+        const double C = __longlong_as_double((long long)atomicMax(&sc->acc[0], 0ull));
+        const double Dm = __longlong_as_double((long long)atomicMax(&sc->acc[1], 0ull));
+        double dt = a.hmin / C;
+        if (Dm > 0.0) dt = fmin(dt, (3.0 / 14.0) * a.hmin * a.hmin / Dm);
+        dt *= a.cfl;
+        *dt_out = dt;
+        if (dt_out2) *dt_out2 = dt;
+        sc->acc[0] = 0ull;
+        sc->acc[1] = 0ull;
+        sc->ticket = 0u;
+        __threadfence();
+      }
+    }
+  }
+}
+
+// loss = sum_cells (rho - target)^2 * dV; seed = d loss / dU (density
+// component only).  blockDim.x == 256.
+template <typename T>
+__global__ void __launch_bounds__(256) loss_density_kernel(const T* __restrict__ U, const T* __restrict__ target,
+                                                           long long N, double dV, ReduceScratch* sc,
+                                                           double* loss, T* seed) {
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += stride) {
+    const double d = (double)U[q] - (double)target[q];
+    s += d * d * dV;
+    if (seed) {
+      seed[q] = (T)(2.0 * d * dV);
+      seed[q + N] = T(0);
+      seed[q + 2 * N] = T(0);
+      seed[q + 3 * N] = T(0);
+      seed[q + 4 * N] = T(0);
+    }
+  }
+  __shared__ double s_sum[8];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s_sum[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? s_sum[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) {
+      atomicAdd(&sc->sum, s);
+      __threadfence();
+      const unsigned int t = atomicAdd(&sc->ticket, 1u);
+      if (t == gridDim.x - 1) {
+        __threadfence();
+        *loss = atomicAdd(&sc->sum, 0.0);
+        sc->sum = 0.0;
+        sc->ticket = 0u;
+        __threadfence();
+      }
+    }
+  }
+}
+
+}  // namespace jf

@@ -1,0 +1,341 @@
+// Fused finite-volume RK stage kernel (forward).
+//
+// One launch evaluates, for every interior cell,
+//   out = a Un + b (Us + dt L(Us))            (TVD-RK3 stage, Section 3.2)
+// or out = L(Us) (right-hand side only), with L the right-hand side of
+// Eq. (FVD): conservative -> primitive conversion (Section 2), WENO5-JS face
+// states and HLLC flux (Section 3.3), C4 viscous and heat fluxes (Section
+// 3.4), flux divergence (Section 3.1).
+//
+// Tiling.  A CTA owns a BX x BY column of cells.  In 3D it marches along z
+// over a chunk of planes, keeping the primitive variables of the planes
+// k-3..k+3 in a shared-memory ring (each plane with a 3-cell x/y halo, edges
+// and corners included, as the viscous cross derivatives need them).  Per
+// plane: the new plane k+3 is loaded (128-bit-friendly coalesced rows,
+// periodic / zero-gradient index map applied per cell, converted to W and T),
+// then the x and y face fluxes of plane k are written to shared memory, and
+// each thread computes the z face k+1/2 of its column, keeping the k-1/2 face
+// in registers from the previous plane.  Every face flux is evaluated once per
+// CTA; only the faces on the tile rim are evaluated twice (by both tiles).
+// In 2D / 1D there is one plane and no ring.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jf_math.cuh"
+
+namespace jf {
+
+constexpr int HALO = 3;
+
+// Per-launch description of one grid and one stage.
+template <typename T>
+struct StageArgs {
+  const T* Us;        // stage input, [5][nz][ny][nx]
+  const T* Un;        // U^n for the Shu-Osher combination (read point-wise); null if a == 0
+  T* out;             // output, [5][nz][ny][nx]; may equal Un
+  const double* dt;   // device scalar (null in right-hand-side mode)
+  int nx, ny, nz;
+  long long N;        // nx * ny * nz
+  int periodic[3];    // 1: periodic axis, 0: zero gradient
+  T inv_h[3];         // 1 / dx_d
+  T a, b;             // stage coefficients
+  int rhs_only;       // 1: out = L(Us)
+  int zchunk;         // planes per CTA along z (3D)
+  int* flag;          // device error flag (bit 0: non-physical state)
+};
+
+__device__ __forceinline__ int map_index(int i, int n, int periodic) {
+  if (periodic) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Shared-memory plane geometry.
+template <int BX, int BY, int DIM, bool VISC>
+struct Geo {
+  static constexpr int HY = DIM >= 2 ? HALO : 0;
+  static constexpr int PX = BX + 2 * HALO;           // row pitch
+  static constexpr int PY = BY + 2 * HY;
+  static constexpr int CS = PX * PY;                 // component stride
+  static constexpr int NC = VISC ? 6 : 5;            // rho, u, v, w, p (, T)
+  static constexpr int PLANE = NC * CS;
+  static constexpr int RING = DIM == 3 ? 7 : 1;      // planes held
+  static constexpr int NFX = (BX + 1) * BY;          // x faces per plane
+  static constexpr int NFY = DIM >= 2 ? BX * (BY + 1) : 0;
+  static constexpr int NT = BX * BY;                 // threads
+};
+
+// Load plane gz (global z index, mapped by the boundary condition) of the
+// tile at (gx0, gy0) into dst, as primitive variables (+ temperature).
+template <typename T, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void load_plane(const StageArgs<T>& A, const Gas<T>& g, T* dst, int gx0, int gy0,
+                                           int gz) {
+  using G = Geo<BX, BY, DIM, VISC>;
+  const int kz = DIM == 3 ? map_index(gz, A.nz, A.periodic[2]) : 0;
+  const long long zoff = (long long)kz * A.ny;
+  bool bad = false;
+  for (int t = threadIdx.x; t < G::CS; t += G::NT) {
+    const int ly = t / G::PX;
+    const int lx = t - ly * G::PX;
+    const int gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
+    const int gy = DIM >= 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
+    const long long q = (zoff + gy) * A.nx + gx;
+    const T r = __ldg(A.Us + q);
+    const T mx = __ldg(A.Us + q + A.N);
+    const T my = __ldg(A.Us + q + 2 * A.N);
+    const T mz = __ldg(A.Us + q + 3 * A.N);
+    const T E = __ldg(A.Us + q + 4 * A.N);
+    const T inv = T(1) / r;
+    const T u = mx * inv, v = my * inv, w = mz * inv;
+    const T p = g.gm1 * (E - T(0.5) * r * (u * u + v * v + w * w));
+    bad |= !(r > T(0)) || !(p > T(0)) || !(p < T(INFINITY));
+    dst[t] = r;
+    dst[G::CS + t] = u;
+    dst[2 * G::CS + t] = v;
+    dst[3 * G::CS + t] = w;
+    dst[4 * G::CS + t] = p;
+    if (VISC) dst[5 * G::CS + t] = p * inv * g.inv_R;
+  }
+  if (bad) atomicOr(A.flag, 1);
+}
+
+// Accessor of the ring: value of component c at plane offset e (-3..3),
+// shared-memory row y, column x (both including the halo offset).
+template <typename T, int BX, int BY, int DIM, bool VISC>
+struct RingView {
+  using G = Geo<BX, BY, DIM, VISC>;
+  const T* s;
+  int plane[7];  // element offset of plane k + e, index e + 3
+  __device__ __forceinline__ T at(int c, int x, int y, int e) const {
+    return s[plane[e + 3] + c * G::CS + y * G::PX + x];
+  }
+};
+
+// Axis roles of a face normal to D: offsets (along normal, tangent 1,
+// tangent 2) -> (x, y, plane).
+template <int D> struct Roles;
+template <> struct Roles<0> {
+  static constexpr int T1 = 1, T2 = 2;
+  __device__ static void map(int n, int t1, int t2, int& x, int& y, int& e) { x = n; y = t1; e = t2; }
+};
+template <> struct Roles<1> {
+  static constexpr int T1 = 0, T2 = 2;
+  __device__ static void map(int n, int t1, int t2, int& x, int& y, int& e) { x = t1; y = n; e = t2; }
+};
+template <> struct Roles<2> {
+  static constexpr int T1 = 0, T2 = 1;
+  __device__ static void map(int n, int t1, int t2, int& x, int& y, int& e) { x = t1; y = t2; e = n; }
+};
+
+// Net flux NF = F^d - F through the face between the cell at shared-memory
+// position (x0, y0, plane 0) and its neighbour along D.
+template <typename T, int D, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
+                                          const Gas<T>& g, const T inv_h[3], T NF[5]) {
+  using Ro = Roles<D>;
+  auto val = [&](int c, int n, int t1, int t2) -> T {
+    int x, y, e;
+    Ro::map(n, t1, t2, x, y, e);
+    return R.at(c, x0 + x, y0 + y, e);
+  };
+  // WENO5-JS left / right states of each primitive component (Section 3.3)
+  T Wm[5], Wp[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const T v0 = val(c, -2, 0, 0), v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0);
+    const T v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0), v5 = val(c, 3, 0, 0);
+    Wm[c] = weno5(v0, v1, v2, v3, v4, g.eps);
+    Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps);
+  }
+  if (g.safe) {
+    if (!(Wm[0] > T(0)) || !(Wm[4] > T(0))) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Wm[c] = val(c, 0, 0, 0);
+    }
+    if (!(Wp[0] > T(0)) || !(Wp[4] > T(0))) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Wp[c] = val(c, 1, 0, 0);
+    }
+  }
+  T F[5];
+  hllc<T, D>(Wm, Wp, g, F);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) NF[c] = -F[c];
+  if constexpr (VISC) {
+  // Dissipative flux (Sections 2 and 3.4).  G[a][b] = du_a/dx_b at the face.
+  T G[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) G[a][b] = T(0);
+  const T hn = inv_h[D];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    G[a][D] = df4(val(1 + a, -1, 0, 0), val(1 + a, 0, 0, 0), val(1 + a, 1, 0, 0), val(1 + a, 2, 0, 0)) * hn;
+  const T dTdn = df4(val(5, -1, 0, 0), val(5, 0, 0, 0), val(5, 1, 0, 0), val(5, 2, 0, 0)) * hn;
+  // tangential derivatives: cell-centre C4 at cells -1..2 along the normal,
+  // then fourth-order interpolation to the face
+  if (Ro::T1 < DIM) {
+    constexpr int e = Ro::T1;
+    const T he = inv_h[e];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int a = s == 0 ? D : e;
+      T cen[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        cen[q] = dc4(val(1 + a, q - 1, -2, 0), val(1 + a, q - 1, -1, 0), val(1 + a, q - 1, 1, 0),
+                     val(1 + a, q - 1, 2, 0));
+      G[a][e] = rc4(cen[0], cen[1], cen[2], cen[3]) * he;
+    }
+  }
+  if (Ro::T2 < DIM) {
+    constexpr int e = Ro::T2;
+    const T he = inv_h[e];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int a = s == 0 ? D : e;
+      T cen[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        cen[q] = dc4(val(1 + a, q - 1, 0, -2), val(1 + a, q - 1, 0, -1), val(1 + a, q - 1, 0, 1),
+                     val(1 + a, q - 1, 0, 2));
+      G[a][e] = rc4(cen[0], cen[1], cen[2], cen[3]) * he;
+    }
+  }
+  T uf[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    uf[a] = rc4(val(1 + a, -1, 0, 0), val(1 + a, 0, 0, 0), val(1 + a, 1, 0, 0), val(1 + a, 2, 0, 0));
+  const T div = G[0][0] + G[1][1] + G[2][2];
+  T tau[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) tau[a] = g.mu * (G[D][a] + G[a][D]);
+  tau[D] -= (T(2) / T(3)) * g.mu * div;
+  NF[1] += tau[0];
+  NF[2] += tau[1];
+  NF[3] += tau[2];
+  NF[4] += uf[0] * tau[0] + uf[1] * tau[1] + uf[2] * tau[2] + g.lambda * dTdn;
+  }
+}
+
+// The stage kernel.  blockDim.x == BX * BY.
+// grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/zchunk)) (3D), (.., .., 1) otherwise.
+template <typename T, int DIM, bool VISC, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY) stage_kernel(const StageArgs<T> A, const Gas<T> g) {
+  using G = Geo<BX, BY, DIM, VISC>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  T* Fx = ring + G::RING * G::PLANE;      // [5][BY][BX+1]
+  T* Fy = Fx + 5 * G::NFX;                // [5][BY+1][BX]
+
+  const int gx0 = blockIdx.x * BX;
+  const int gy0 = blockIdx.y * BY;
+  const int tx = threadIdx.x % BX;
+  const int ty = threadIdx.x / BX;
+  const int gx = gx0 + tx, gy = gy0 + ty;
+  const bool own = gx < A.nx && gy < A.ny;
+  const T dt = A.rhs_only ? T(0) : T(*A.dt);
+  const T inv_h[3] = {A.inv_h[0], A.inv_h[1], A.inv_h[2]};
+
+  int z0 = 0, z1 = 1;
+  if (DIM == 3) {
+    z0 = blockIdx.z * A.zchunk;
+    z1 = min(z0 + A.zchunk, A.nz);
+  }
+
+  RingView<T, BX, BY, DIM, VISC> R;
+  R.s = ring;
+  // ring slot of plane z0 + q - 3 is q (mod 7)
+  int base = 0;  // slot of plane (k - 3) for the current k
+  auto set_view = [&](int b) {
+#pragma unroll
+    for (int e = 0; e < 7; ++e) {
+      int s = b + e;
+      s = s >= G::RING ? s - G::RING : s;
+      R.plane[e] = (DIM == 3 ? s : 0) * G::PLANE;
+    }
+  };
+
+  T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
+  if (DIM == 3) {
+    for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
+    // plane z0 - 1 sits in slot 2; its upper face is the lower face of z0
+    __syncthreads();
+    set_view(6);  // plane (z0 - 1) - 3 -> slot 6  (z0-4 is not loaded; only e >= -2 is read)
+    face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+    base = 0;
+  }
+
+  for (int k = z0; k < z1; ++k) {
+    if (DIM == 3) {
+      // slot of plane k + 3 is (base + 6) mod 7; it held plane k - 4
+      int s = base + 6;
+      s = s >= 7 ? s - 7 : s;
+      load_plane<T, BX, BY, DIM, VISC>(A, g, ring + s * G::PLANE, gx0, gy0, k + 3);
+    } else {
+      load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, 0);
+    }
+    set_view(base);
+    __syncthreads();
+
+    // x faces of plane k: face f (0..BX) between tile columns f-1 and f
+    for (int t = threadIdx.x; t < G::NFX; t += G::NT) {
+      const int fy = t / (BX + 1), fx = t - fy * (BX + 1);
+      T NF[5];
+      face_flux<T, 0, BX, BY, DIM, VISC>(R, HALO + fx - 1, G::HY + fy, g, inv_h, NF);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Fx[c * G::NFX + t] = NF[c];
+    }
+    if (DIM >= 2) {
+      for (int t = threadIdx.x; t < G::NFY; t += G::NT) {
+        const int fy = t / BX, fx = t - fy * BX;
+        T NF[5];
+        face_flux<T, 1, BX, BY, DIM, VISC>(R, HALO + fx, G::HY + fy - 1, g, inv_h, NF);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Fy[c * G::NFY + t] = NF[c];
+      }
+    }
+    T NFz_hi[5];
+    if (DIM == 3) face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+    __syncthreads();
+
+    if (own) {
+      const long long q = ((long long)(DIM == 3 ? k : 0) * A.ny + gy) * A.nx + gx;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const int fx = ty * (BX + 1) + tx;
+        T rhs = (Fx[c * G::NFX + fx + 1] - Fx[c * G::NFX + fx]) * inv_h[0];
+        if (DIM >= 2) {
+          const int fy = ty * BX + tx;
+          rhs += (Fy[c * G::NFY + fy + BX] - Fy[c * G::NFY + fy]) * inv_h[1];
+        }
+        if (DIM == 3) rhs += (NFz_hi[c] - NFz_lo[c]) * inv_h[2];
+        T o;
+        if (A.rhs_only) {
+          o = rhs;
+        } else {
+          o = A.b * (__ldg(A.Us + q + c * A.N) + dt * rhs);
+          if (A.Un) o += A.a * A.Un[q + c * A.N];
+        }
+        A.out[q + c * A.N] = o;
+      }
+    }
+    if (DIM == 3) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) NFz_lo[c] = NFz_hi[c];
+      base = base + 1 == 7 ? 0 : base + 1;
+    }
+  }
+}
+
+template <typename T, int DIM, bool VISC, int BX, int BY>
+constexpr size_t stage_smem_bytes() {
+  using G = Geo<BX, BY, DIM, VISC>;
+  return sizeof(T) * (size_t)(G::RING * G::PLANE + 5 * G::NFX + 5 * G::NFY);
+}
+
+}  // namespace jf

@@ -1,0 +1,31 @@
+// Table of compiled launch variants of the stage kernels (host side).
+//
+// Each variant is one template instantiation of a tile shape (BX x BY cells
+// per CTA) for a dimensionality, precision and physics set.  The host API
+// picks the default per configuration; jf_set_variant (the autotuner hook)
+// picks another.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "jf_math.cuh"
+#include "stage.cuh"
+
+namespace jf {
+
+template <typename T>
+struct StageVariant {
+  int dim;
+  bool visc;
+  int bx, by;
+  size_t smem;
+  cudaError_t (*prepare)();  // one-time attribute set-up (dynamic shared memory)
+  cudaError_t (*launch)(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s);
+  // persistent batched launch over a work list (2D / 1D variants only; may be null)
+  const void* batch_kernel;
+};
+
+// All compiled variants for precision T (defined in stage_f32.cu / stage_f64.cu).
+template <typename T>
+const StageVariant<T>* stage_variants(int* count);
+
+}  // namespace jf

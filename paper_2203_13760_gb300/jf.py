@@ -1,0 +1,289 @@
+"""ctypes binding of libjf.so (include/jf.h): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; PyTorch supplies
+device memory and streams.  There is no CPU fallback: if libjf.so cannot be
+loaded, :func:`lib` raises.
+
+Arrays are torch CUDA tensors, contiguous, shaped [5, nz, ny, nx] (x fastest),
+float32 for ``dtype="f32"`` and float64 for ``dtype="f64"``.  Every call is
+enqueued on ``torch.cuda.current_stream()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjf.so")
+
+JF_OK, JF_ERR_ARG, JF_ERR_CUDA, JF_ERR_OOM, JF_ERR_NONPHYSICAL, JF_ERR_TIMEOUT, JF_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+JF_F32, JF_F64 = 0, 1
+PERIODIC, ZERO_GRADIENT = 0, 1
+_STATUS = {0: "JF_OK", -1: "JF_ERR_ARG", -2: "JF_ERR_CUDA", -3: "JF_ERR_OOM", -4: "JF_ERR_NONPHYSICAL",
+           -5: "JF_ERR_TIMEOUT", -6: "JF_ERR_UNSUPPORTED"}
+
+
+class JFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 6)]
+
+
+class GasParams(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("R", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double)]
+
+
+class Scheme(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("weno_eps", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("viscous", ctypes.c_int), ("heat", ctypes.c_int), ("signal_speed", ctypes.c_int),
+                ("safe_recon", ctypes.c_int)]
+
+
+# name -> (restype, argtypes) of every entry point in include/jf.h
+_VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+SIGNATURES = {
+    "jf_init": (_I, [ctypes.POINTER(Grid), ctypes.POINTER(GasParams), ctypes.POINTER(Scheme), ctypes.POINTER(_VP)]),
+    "jf_destroy": (_I, [_VP]),
+    "jf_rhs": (_I, [_VP, _VP, _VP, _VP]),
+    "jf_compute_dt": (_I, [_VP, _VP, _VP, _VP]),
+    "jf_rk3_step": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "jf_stage": (_I, [_VP, _VP, _VP, _VP, _D, _D, _VP, _VP]),
+    "jf_rk3_run": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    "jf_rk3_step_vjp": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jf_loss_density_l2": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jf_batch_create": (_I, [ctypes.POINTER(Grid), _I, ctypes.POINTER(GasParams), ctypes.POINTER(Scheme),
+                             ctypes.POINTER(_VP)]),
+    "jf_batch_step": (_I, [_VP, ctypes.POINTER(_VP), _I, _VP, _VP]),
+    "jf_set_variant": (_I, [_VP, _I]),
+    "jf_variant_info": (_I, [_VP, _I, ctypes.c_char_p, _I]),
+    "jf_status_sync": (_I, [_VP]),
+    "jf_last_error": (ctypes.c_char_p, [_VP]),
+    "jf_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libjf.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing; build it with "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, handle=None):
+    if status != JF_OK:
+        msg = lib().jf_last_error(handle)
+        raise JFError(status, msg.decode() if msg else "")
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1)) -> Grid:
+    n = tuple(int(x) for x in n) + (1,) * (3 - len(n))
+    g = Grid()
+    g.nx, g.ny, g.nz = n
+    g.lo[:] = [float(x) for x in lo]
+    g.hi[:] = [float(x) for x in hi]
+    g.bc[:] = [int(x) for x in bc]
+    return g
+
+
+def make_scheme(dtype="f32", eps=1e-6, cfl=0.5, viscous=False, heat=False, safe=False) -> Scheme:
+    s = Scheme()
+    s.dtype = JF_F32 if dtype in ("f32", "float32") else JF_F64
+    s.weno_eps, s.cfl = float(eps), float(cfl)
+    s.viscous, s.heat, s.signal_speed, s.safe_recon = int(bool(viscous)), int(bool(heat)), 0, int(bool(safe))
+    return s
+
+
+class Solver:
+    """One grid (jf_init).  Parameters mirror jf_grid / jf_gas / jf_scheme."""
+
+    def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gamma=1.4, R=1.0,
+                 mu=0.0, Pr=0.72, dtype="f32", eps=1e-6, cfl=0.5, viscous=False, heat=False, safe=False):
+        import torch
+        self.grid = make_grid(n, lo, hi, bc)
+        self.gas = GasParams(float(gamma), float(R), float(mu), float(Pr))
+        self.scheme = make_scheme(dtype, eps, cfl, viscous, heat, safe)
+        self.dtype = torch.float32 if self.scheme.dtype == JF_F32 else torch.float64
+        self.shape = (5, self.grid.nz, self.grid.ny, self.grid.nx)
+        h = ctypes.c_void_p()
+        _check(lib().jf_init(ctypes.byref(self.grid), ctypes.byref(self.gas), ctypes.byref(self.scheme),
+                             ctypes.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_case(cls, case, dtype="f32", **over):
+        kw = case.params()
+        kw.update(over)
+        return cls(dtype=dtype, **kw)
+
+    # -- helpers -------------------------------------------------------------
+    def _field(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype or tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of shape {self.shape}")
+        return _ptr(t)
+
+    def empty(self):
+        import torch
+        return torch.empty(self.shape, dtype=self.dtype, device="cuda")
+
+    def scalar(self, value=0.0):
+        import torch
+        return torch.full((1,), float(value), dtype=torch.float64, device="cuda")
+
+    # -- entry points ----------------------------------------------------------
+    def rhs(self, U, out=None):
+        out = self.empty() if out is None else out
+        _check(lib().jf_rhs(self.h, self._field(U, "U"), self._field(out, "out"), _stream()), self.h)
+        return out
+
+    def compute_dt(self, U, out=None):
+        out = self.scalar() if out is None else out
+        _check(lib().jf_compute_dt(self.h, self._field(U, "U"), _ptr(out), _stream()), self.h)
+        return out
+
+    def rk3_step(self, U, dt=None, dt_used=None):
+        """One RK3 step in place; dt: None (CFL) or a float64 CUDA tensor."""
+        _check(lib().jf_rk3_step(self.h, self._field(U, "U"), _ptr(dt), _ptr(dt_used), _stream()), self.h)
+        return U
+
+    def stage(self, Us, Un, out, a, b, dt):
+        """out = a Un + b (Us + dt L(Us)); dt a float64 CUDA scalar tensor."""
+        _check(lib().jf_stage(self.h, self._field(Us, "Us"), self._field(Un, "Un") if Un is not None else None,
+                              self._field(out, "out"), float(a), float(b), _ptr(dt), _stream()), self.h)
+        return out
+
+    def run(self, U, nsteps, dt=None, dt_hist=None):
+        """nsteps RK3 steps in place as one CUDA graph."""
+        _check(lib().jf_rk3_run(self.h, self._field(U, "U"), int(nsteps), _ptr(dt), _ptr(dt_hist), _stream()),
+               self.h)
+        return U
+
+    def rk3_step_vjp(self, Un, dt, lam_out, lam_in=None):
+        lam_in = self.empty() if lam_in is None else lam_in
+        _check(lib().jf_rk3_step_vjp(self.h, self._field(Un, "Un"), _ptr(dt), self._field(lam_out, "lam_out"),
+                                     self._field(lam_in, "lam_in"), _stream()), self.h)
+        return lam_in
+
+    def loss_density_l2(self, U, target, loss=None, seed=None, want_seed=True):
+        import torch
+        loss = self.scalar() if loss is None else loss
+        if want_seed and seed is None:
+            seed = self.empty()
+        if target.dtype != self.dtype or target.numel() != self.grid.nx * self.grid.ny * self.grid.nz:
+            raise ValueError("target must hold nx*ny*nz densities of the solver's dtype")
+        _check(lib().jf_loss_density_l2(self.h, self._field(U, "U"), _ptr(target.contiguous()), _ptr(loss),
+                                        _ptr(seed) if want_seed else None, _stream()), self.h)
+        return loss, seed
+
+    def set_variant(self, v):
+        _check(lib().jf_set_variant(self.h, int(v)), self.h)
+
+    def variants(self):
+        buf = ctypes.create_string_buffer(128)
+        n = lib().jf_variant_info(self.h, 0, buf, 128)
+        out = []
+        for v in range(max(n, 0)):
+            lib().jf_variant_info(self.h, v, buf, 128)
+            out.append(buf.value.decode())
+        return out
+
+    def sync(self):
+        """Wait for the device and raise if a kernel flagged a non-physical state."""
+        _check(lib().jf_status_sync(self.h), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent simulations of uneven sizes (jf_batch_create)."""
+
+    def __init__(self, grids, gamma=1.4, R=1.0, mu=0.0, Pr=0.72, dtype="f32", eps=1e-6, cfl=0.5,
+                 viscous=False, heat=False, safe=False):
+        import torch
+        self.grids = (Grid * len(grids))(*[make_grid(**g) if isinstance(g, dict) else g for g in grids])
+        self.nsim = len(grids)
+        self.gas = GasParams(float(gamma), float(R), float(mu), float(Pr))
+        self.scheme = make_scheme(dtype, eps, cfl, viscous, heat, safe)
+        self.dtype = torch.float32 if self.scheme.dtype == JF_F32 else torch.float64
+        h = ctypes.c_void_p()
+        _check(lib().jf_batch_create(self.grids, self.nsim, ctypes.byref(self.gas), ctypes.byref(self.scheme),
+                                     ctypes.byref(h)))
+        self.h = h
+
+    def step(self, Us, nsteps, dt_out=None):
+        import torch
+        if len(Us) != self.nsim:
+            raise ValueError("one field per simulation")
+        for i, (U, g) in enumerate(zip(Us, self.grids)):
+            if (not U.is_cuda or U.dtype != self.dtype or not U.is_contiguous()
+                    or tuple(U.shape) != (5, g.nz, g.ny, g.nx)):
+                raise ValueError(f"field {i} has the wrong shape / dtype / device")
+        ptrs = (ctypes.c_void_p * self.nsim)(*[U.data_ptr() for U in Us])
+        dt_out = torch.zeros(self.nsim, dtype=torch.float64, device="cuda") if dt_out is None else dt_out
+        _check(lib().jf_batch_step(self.h, ptrs, int(nsteps), _ptr(dt_out), _stream()), self.h)
+        return dt_out
+
+    def set_variant(self, v):
+        _check(lib().jf_set_variant(self.h, int(v)), self.h)
+
+    def variants(self):
+        buf = ctypes.create_string_buffer(128)
+        n = lib().jf_variant_info(self.h, 0, buf, 128)
+        out = []
+        for v in range(max(n, 0)):
+            lib().jf_variant_info(self.h, v, buf, 128)
+            out.append(buf.value.decode())
+        return out
+
+    def sync(self):
+        _check(lib().jf_status_sync(self.h), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,210 @@
+"""GPU (libjf, through the C ABI) against the oracle, element by element, on
+the same seeded inputs.
+
+Norm (per conserved component k): ||gpu_k - oracle_k||_inf / max(||oracle_k||_inf, tiny).
+Bars: FP64 <= 1e-12 (one right-hand side, one and ten RK3 steps);
+FP32 <= 1e-5 after ten RK3 steps on smooth flows.
+"""
+import numpy as np
+import pytest
+
+from paper_2203_13760_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines only
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2203_13760_gb300 import jf  # noqa: E402
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(5, -1)
+    b = np.asarray(b, dtype=np.float64).reshape(5, -1)
+    scale = np.maximum(np.abs(b).max(axis=1), 1e-300)
+    return (np.abs(a - b).max(axis=1) / scale).max()
+
+
+def solver_for(case, dtype):
+    return jf.Solver.from_case(case, dtype=dtype)
+
+
+def to_dev(U, dtype):
+    return torch.tensor(np.ascontiguousarray(U), dtype=torch.float32 if dtype == "f32" else torch.float64,
+                        device="cuda")
+
+
+CASES = {
+    "1d_blocks_zg": lambda: inputs.random_blocks((37, 1, 1), seed=1),
+    "1d_smooth_visc": lambda: inputs.random_smooth((64, 1, 1), seed=2, viscous=True, mu=0.02),
+    "1d_sod": lambda: inputs.sod(200),
+    "2d_smooth_visc_ragged": lambda: inputs.random_smooth((37, 19, 1), seed=3, viscous=True, mu=0.01),
+    "2d_blocks_zg_ragged": lambda: inputs.random_blocks((40, 33, 1), seed=4),
+    "2d_mixed_bc": lambda: inputs.random_smooth((33, 24, 1), seed=5, bc=(0, 0, 1, 1, 1, 1), viscous=True, mu=0.01),
+    "3d_smooth_visc_ragged": lambda: inputs.random_smooth((19, 13, 11), seed=6, viscous=True, mu=0.01),
+    "3d_blocks_mixed": lambda: inputs.random_blocks((21, 17, 9), seed=7, bc=(0, 0, 1, 1, 0, 0)),
+    "3d_tgv": lambda: inputs.taylor_green(32),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_fp64(orc, name):
+    case = CASES[name]()
+    c = orc.config(**case.params())
+    want = orc.rhs(c, case.U)
+    s = solver_for(case, "f64")
+    got = s.rhs(to_dev(case.U, "f64")).cpu().numpy()
+    s.sync()
+    assert rel_err(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rk3_steps_fp64(orc, name):
+    """CFL steps: each side computes its own dt (FP64), then the state."""
+    case = CASES[name]()
+    c = orc.config(**case.params())
+    s = solver_for(case, "f64")
+    U = to_dev(case.U, "f64")
+    dt_used = s.scalar()
+    want = case.U.copy()
+    for step in range(10):
+        dt_ref = orc.compute_dt(c, want)
+        want = orc.rk3_step(c, want, dt_ref)
+        s.rk3_step(U, None, dt_used)
+        assert dt_used.item() == pytest.approx(dt_ref, rel=1e-13)
+        if step == 0:
+            assert rel_err(U.cpu().numpy(), want) <= 1e-12
+    s.sync()
+    assert rel_err(U.cpu().numpy(), want) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["1d_smooth_visc", "2d_smooth_visc_ragged", "3d_smooth_visc_ragged", "3d_tgv",
+                                  "2d_mixed_bc"])
+def test_rk3_ten_steps_fp32(orc, name):
+    """FP32 storage and arithmetic against the FP64 oracle started from the
+    same FP32-rounded state, fixed dt."""
+    case = CASES[name]()
+    c = orc.config(**case.params())
+    U32 = case.U.astype(np.float32)
+    dt = 0.5 * orc.compute_dt(c, U32.astype(np.float64))
+    want, _, _ = orc.run(c, U32.astype(np.float64), 10, dt)
+    s = solver_for(case, "f32")
+    U = to_dev(U32, "f32")
+    dtd = s.scalar(dt)
+    for _ in range(10):
+        s.rk3_step(U, dtd)
+    s.sync()
+    assert rel_err(U.cpu().numpy(), want) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n", [(16, 1, 1), (12, 10, 1), (9, 8, 7)])
+def test_free_stream_exact(dtype, n):
+    """Uniform state: the right-hand side is exactly zero."""
+    U = np.empty((5, n[2], n[1], n[0]))
+    U[:] = np.array([1.2, 0.3, -0.2, 0.1, 2.7])[:, None, None, None]
+    s = jf.Solver(n, bc=(0, 0, 1, 1, 0, 0), dtype=dtype, viscous=True, heat=True, mu=0.01)
+    r = s.rhs(to_dev(U, dtype))
+    s.sync()
+    assert torch.all(r == 0).item()
+
+
+def test_conservation_fp64_gpu():
+    """Periodic grid: sum of U is conserved to round-off over 20 steps."""
+    case = inputs.random_smooth((24, 20, 12), seed=9, viscous=True, mu=0.01)
+    s = solver_for(case, "f64")
+    U = to_dev(case.U, "f64")
+    s0 = U.sum(dim=(1, 2, 3)).cpu().numpy()
+    s.run(U, 20)
+    s.sync()
+    s1 = U.sum(dim=(1, 2, 3)).cpu().numpy()
+    scale = np.abs(case.U).reshape(5, -1).sum(1)
+    assert np.all(np.abs(s1 - s0) <= 1e-13 * scale)
+
+
+def test_graph_run_matches_single_steps():
+    """jf_rk3_run (CUDA graph) is bitwise the same as repeated jf_rk3_step."""
+    case = inputs.taylor_green(24)
+    s = solver_for(case, "f32")
+    U1 = to_dev(case.U, "f32")
+    U2 = U1.clone()
+    hist = torch.zeros(7, dtype=torch.float64, device="cuda")
+    for _ in range(7):
+        s.rk3_step(U1)
+    s.run(U2, 7, None, hist)
+    s.run(U2, 7, None, hist)  # replay of the cached graph
+    for _ in range(7):
+        s.rk3_step(U1)
+    s.sync()
+    assert torch.equal(U1, U2)
+    assert torch.all(hist > 0).item()
+
+
+def test_deterministic():
+    case = inputs.random_blocks((40, 33, 1), seed=4)
+    outs = []
+    for _ in range(2):
+        s = solver_for(case, "f32")
+        U = to_dev(case.U, "f32")
+        s.run(U, 5)
+        s.sync()
+        outs.append(U.cpu())
+    assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_variants_agree(variant):
+    """Every launch variant (tile shape / z chunk) gives the same bits."""
+    case = inputs.random_smooth((40, 24, 20), seed=12, viscous=True, mu=0.01)
+    s = solver_for(case, "f32")
+    U = to_dev(case.U, "f32")
+    ref = s.rhs(U).clone()
+    nv = len(s.variants())
+    s.set_variant(variant % nv)
+    got = s.rhs(U)
+    s.sync()
+    assert torch.equal(ref, got)
+
+
+def test_sod_gpu_against_exact(orc):
+    """Full Sod run (200 cells, CFL 0.5, t = 0.2) on the GPU: same L1 error as
+    the oracle against the exact solution, and oracle parity."""
+    case = inputs.sod(200)
+    c = orc.config(**case.params())
+    want, t_ref, nsteps = orc.run(c, case.U, 100000, 0.0, 0.2)
+    s = solver_for(case, "f64")
+    U = to_dev(case.U, "f64")
+    dt_used = s.scalar()
+    t = 0.0
+    for _ in range(nsteps - 1):
+        s.rk3_step(U, None, dt_used)
+        t += dt_used.item()
+    s.rk3_step(U, s.scalar(0.2 - t))
+    s.sync()
+    assert rel_err(U.cpu().numpy(), want) <= 1e-10
+    x = inputs.centres(200, 0, 1)
+    ex = orc.exact_sample([1, 0, 1], [0.125, 0, 0.1], x, 0.2)
+    assert np.mean(np.abs(U[0, 0, 0].cpu().numpy() - ex[:, 0])) < 3e-3
+
+
+def test_nonphysical_state_reported():
+    """A negative density in the input is reported by jf_status_sync as
+    JF_ERR_NONPHYSICAL (the fault is made on the host; no kernel traps)."""
+    case = inputs.random_smooth((16, 16, 1), seed=1)
+    U = case.U.copy()
+    U[0, 0, 3, 5] = -1.0
+    s = solver_for(case, "f32")
+    s.rhs(to_dev(U, "f32"))
+    with pytest.raises(jf.JFError) as e:
+        s.sync()
+    assert e.value.status == jf.JF_ERR_NONPHYSICAL
+    s.sync()  # the flag was cleared
+
+
+def test_compute_dt_fp64(orc):
+    case = inputs.taylor_green(16)
+    c = orc.config(**case.params())
+    s = solver_for(case, "f64")
+    dt = s.compute_dt(to_dev(case.U, "f64")).item()
+    assert dt == pytest.approx(orc.compute_dt(c, case.U), rel=1e-14)
