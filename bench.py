@@ -39,6 +39,7 @@ WORKLOADS = {
     # name: (generator, kwargs, dtype)
     "tgv256": ("taylor_green", {"n": 256}, "f32"),
     "tgv128": ("taylor_green", {"n": 128}, "f32"),
+    "tgv192": ("taylor_green", {"n": 192}, "f32"),
     "tgv256_f64": ("taylor_green", {"n": 256}, "f64"),
     "tgv128_f64": ("taylor_green", {"n": 128}, "f64"),
     "hit384": ("solenoidal_turbulence", {"n": 384}, "f32"),
@@ -214,7 +215,7 @@ def cpu_baseline(workload, budget_s=15.0, threads=None):
         U, _, _ = oracle.run(c, U, 1)
         steps += 1
         el = time.perf_counter() - t0
-        if el >= budget_s or steps >= 50:
+        if el >= budget_s or steps >= 400:
             break
     cells = case.cells
     return {"value": cells * steps / el, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",

@@ -21,6 +21,8 @@ LIB = os.path.join(HERE, "libjf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr"]
+# FP32 kernels use approximate division / square root (see stage_f32.cu)
+PER_FILE_FLAGS = {"stage_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -57,7 +59,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *PER_FILE_FLAGS.get(os.path.basename(src), []), *extra_flags,
+               "-I", INCLUDE, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -51,11 +51,21 @@ __device__ __forceinline__ T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
   const T b1 = c13 * d1 * d1 + T(0.25) * e1 * e1;
   const T b2 = c13 * d2 * d2 + T(0.25) * e2 * e2;
   const T t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
-  const T a0 = T(0.1) / (t0 * t0);
-  const T a1 = T(0.6) / (t1 * t1);
-  const T a2 = T(0.3) / (t2 * t2);
-  const T inv = T(1) / (a0 + a1 + a2);
-  return (a0 * q0 + a1 * q1 + a2 * q2) * inv;
+  if constexpr (sizeof(T) == 8) {
+    // alpha_k scaled by prod_j (eps + beta_j)^2: one division instead of four
+    // (the squares are >= eps^4, far inside the FP64 range)
+    const T s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
+    const T a0 = T(0.1) * s1 * s2;
+    const T a1 = T(0.6) * s0 * s2;
+    const T a2 = T(0.3) * s0 * s1;
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  } else {
+    const T a0 = T(0.1) / (t0 * t0);
+    const T a1 = T(0.6) / (t1 * t1);
+    const T a2 = T(0.3) / (t2 * t2);
+    const T inv = T(1) / (a0 + a1 + a2);
+    return (a0 * q0 + a1 * q1 + a2 * q2) * inv;
+  }
 }
 
 // HLLC flux along axis D from the reconstructed primitive states

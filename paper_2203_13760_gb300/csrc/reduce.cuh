@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "jf_math.cuh"
+
 namespace jf {
 
 struct CflArgs {
@@ -46,40 +48,44 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename T>
 __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U, CflArgs a, ReduceScratch* sc,
                                                   double* dt_out, double* dt_out2, int* flag) {
-  double conv = 0.0, diff = 0.0;
+  // Per-cell rates in the field's precision (FP64 units are scarce on this
+  // part); the maximum and dt are formed in FP64.  A rate converted to FP64 is
+  // exact, so the maximum is the exact maximum of the per-cell values.
+  T conv = T(0), diff = T(0);
+  const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
   bool bad = false;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.N; q += stride) {
-    const double r = (double)U[q];
-    const double inv = 1.0 / r;
-    const double u = (double)U[q + a.N] * inv;
-    const double v = (double)U[q + 2 * a.N] * inv;
-    const double w = (double)U[q + 3 * a.N] * inv;
-    const double p = (a.gamma - 1.0) * ((double)U[q + 4 * a.N] - 0.5 * r * (u * u + v * v + w * w));
-    bad |= !(r > 0.0) || !(p > 0.0);
-    const double c = sqrt(a.gamma * p * inv);
-    double m = fabs(u);
+    const T r = U[q];
+    const T inv = T(1) / r;
+    const T u = U[q + a.N] * inv;
+    const T v = U[q + 2 * a.N] * inv;
+    const T w = U[q + 3 * a.N] * inv;
+    const T p = gm1 * (U[q + 4 * a.N] - T(0.5) * r * (u * u + v * v + w * w));
+    bad |= !(r > T(0)) || !(p > T(0));
+    const T c = tsqrt(gamma * p * inv);
+    T m = fabs(u);
     if (a.nactive > 1) m = fmax(m, fabs(v));
     if (a.nactive > 2) m = fmax(m, fabs(w));
     conv = fmax(conv, m + c);
-    diff = fmax(diff, a.kdiff * inv);
+    diff = fmax(diff, kdiff * inv);
   }
   if (bad) atomicOr(flag, 1);
   __shared__ double s_conv[8], s_diff[8];
-  conv = warp_max(conv);
-  diff = warp_max(diff);
+  double dconv = warp_max((double)conv);
+  double ddiff = warp_max((double)diff);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { s_conv[wid] = conv; s_diff[wid] = diff; }
+  if (lane == 0) { s_conv[wid] = dconv; s_diff[wid] = ddiff; }
   __syncthreads();
   if (wid == 0) {
-    conv = lane < (int)(blockDim.x >> 5) ? s_conv[lane] : 0.0;
-    diff = lane < (int)(blockDim.x >> 5) ? s_diff[lane] : 0.0;
-    conv = warp_max(conv);
-    diff = warp_max(diff);
+    dconv = lane < (int)(blockDim.x >> 5) ? s_conv[lane] : 0.0;
+    ddiff = lane < (int)(blockDim.x >> 5) ? s_diff[lane] : 0.0;
+    dconv = warp_max(dconv);
+    ddiff = warp_max(ddiff);
     if (lane == 0) {
       // NaN never wins fmax; a NaN state is reported through the flag
-      atomicMax(&sc->acc[0], (unsigned long long)__double_as_longlong(conv));
-      atomicMax(&sc->acc[1], (unsigned long long)__double_as_longlong(diff));
+      atomicMax(&sc->acc[0], (unsigned long long)__double_as_longlong(dconv));
+      atomicMax(&sc->acc[1], (unsigned long long)__double_as_longlong(ddiff));
       __threadfence();
       const unsigned int t = atomicAdd(&sc->ticket, 1u);
       if (t == gridDim.x - 1) {

@@ -7,17 +7,24 @@
 // states and HLLC flux (Section 3.3), C4 viscous and heat fluxes (Section
 // 3.4), flux divergence (Section 3.1).
 //
-// Tiling.  A CTA owns a BX x BY column of cells.  In 3D it marches along z
-// over a chunk of planes, keeping the primitive variables of the planes
-// k-3..k+3 in a shared-memory ring (each plane with a 3-cell x/y halo, edges
-// and corners included, as the viscous cross derivatives need them).  Per
-// plane: the new plane k+3 is loaded (128-bit-friendly coalesced rows,
-// periodic / zero-gradient index map applied per cell, converted to W and T),
-// then the x and y face fluxes of plane k are written to shared memory, and
-// each thread computes the z face k+1/2 of its column, keeping the k-1/2 face
-// in registers from the previous plane.  Every face flux is evaluated once per
-// CTA; only the faces on the tile rim are evaluated twice (by both tiles).
-// In 2D / 1D there is one plane and no ring.
+// Tiling.  A CTA owns a BX x BY column of cells (BX = 32: one warp per row
+// of cells).  In 3D it marches along z over a chunk of planes, keeping the
+// primitive variables of the planes k-2..k+3 in a six-slot shared-memory ring
+// (each plane with a 3-cell x/y halo, edges and corners included, as the
+// viscous cross derivatives need them).  Per plane: the new plane k+3 is
+// loaded into the slot of plane k-3 (coalesced rows, periodic / zero-gradient
+// index map applied per cell, converted to W and T), then the x and y face
+// fluxes of plane k are written to shared memory, and each cell thread
+// computes the z face k+1/2 of its column, keeping the k-1/2 face in registers
+// from the previous plane.  Every face flux is evaluated once per CTA; only
+// the faces on the tile rim are evaluated twice (by both tiles).
+//
+// Work balance.  The CTA has BY + 1 warps.  x faces: warp w < BY takes face
+// row w (faces 0..31), warp BY takes the 33rd face of every row; y faces: warp
+// w takes face row w (BY + 1 rows of 32); z faces and cell updates: warps
+// 0..BY-1.  Every warp thus computes about the same number of faces between
+// two barriers, and each warp reads shared memory row-wise (no bank
+// conflicts).  In 2D / 1D there is one plane and no ring.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -62,10 +69,13 @@ struct Geo {
   static constexpr int CS = PX * PY;                 // component stride
   static constexpr int NC = VISC ? 6 : 5;            // rho, u, v, w, p (, T)
   static constexpr int PLANE = NC * CS;
-  static constexpr int RING = DIM == 3 ? 7 : 1;      // planes held
+  static constexpr int RING = DIM == 3 ? 6 : 1;      // planes held
   static constexpr int NFX = (BX + 1) * BY;          // x faces per plane
   static constexpr int NFY = DIM >= 2 ? BX * (BY + 1) : 0;
-  static constexpr int NT = BX * BY;                 // threads
+  static constexpr int NCELL = BX * BY;              // cell threads
+  static constexpr int NT = DIM >= 2 ? BX * (BY + 1) : BX + 32;  // threads
+  static_assert(DIM == 1 || BX == 32, "2D/3D tiles are one warp wide");
+  static_assert(DIM != 1 || BY == 1, "1D tiles are one row");
 };
 
 // Load plane gz (global z index, mapped by the boundary condition) of the
@@ -222,10 +232,11 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
   }
 }
 
-// The stage kernel.  blockDim.x == BX * BY.
+// The stage kernel.  blockDim.x == Geo::NT.
 // grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/zchunk)) (3D), (.., .., 1) otherwise.
-template <typename T, int DIM, bool VISC, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY) stage_kernel(const StageArgs<T> A, const Gas<T> g) {
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
+    stage_kernel(const StageArgs<T> A, const Gas<T> g) {
   using G = Geo<BX, BY, DIM, VISC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);
@@ -234,12 +245,25 @@ __global__ void __launch_bounds__(BX * BY) stage_kernel(const StageArgs<T> A, co
 
   const int gx0 = blockIdx.x * BX;
   const int gy0 = blockIdx.y * BY;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool cell_thread = threadIdx.x < G::NCELL;
   const int tx = threadIdx.x % BX;
   const int ty = threadIdx.x / BX;
   const int gx = gx0 + tx, gy = gy0 + ty;
-  const bool own = gx < A.nx && gy < A.ny;
+  const bool own = cell_thread && gx < A.nx && gy < A.ny;
   const T dt = A.rhs_only ? T(0) : T(*A.dt);
   const T inv_h[3] = {A.inv_h[0], A.inv_h[1], A.inv_h[2]};
+
+  // this thread's x face (-1: none) and y face, as (column, row) in the tile
+  int xf_x = -1, xf_y = 0;
+  if (DIM == 1) {
+    if (threadIdx.x <= BX) { xf_x = threadIdx.x; xf_y = 0; }
+  } else if (warp < BY) {
+    xf_x = lane; xf_y = warp;
+  } else if (lane < BY) {
+    xf_x = BX; xf_y = lane;
+  }
+  const int yf_x = lane, yf_y = warp;  // DIM >= 2: NT == BX * (BY + 1) y faces
 
   int z0 = 0, z1 = 1;
   if (DIM == 3) {
@@ -249,12 +273,14 @@ __global__ void __launch_bounds__(BX * BY) stage_kernel(const StageArgs<T> A, co
 
   RingView<T, BX, BY, DIM, VISC> R;
   R.s = ring;
-  // ring slot of plane z0 + q - 3 is q (mod 7)
-  int base = 0;  // slot of plane (k - 3) for the current k
+  // plane p lives in slot (p - z0 + 3) mod 6; set_view(b) maps plane offset
+  // e (-3..3) of the current plane to slot (b + e + 3) mod 6, b being the
+  // slot of plane (current - 3)
   auto set_view = [&](int b) {
 #pragma unroll
     for (int e = 0; e < 7; ++e) {
       int s = b + e;
+      s = s >= G::RING ? s - G::RING : s;
       s = s >= G::RING ? s - G::RING : s;
       R.plane[e] = (DIM == 3 ? s : 0) * G::PLANE;
     }
@@ -263,44 +289,42 @@ __global__ void __launch_bounds__(BX * BY) stage_kernel(const StageArgs<T> A, co
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
   if (DIM == 3) {
     for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
-    // plane z0 - 1 sits in slot 2; its upper face is the lower face of z0
     __syncthreads();
-    set_view(6);  // plane (z0 - 1) - 3 -> slot 6  (z0-4 is not loaded; only e >= -2 is read)
-    face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
-    base = 0;
+    // lower face of plane z0 = upper face of plane z0 - 1 (slot 2); plane
+    // offset -3 is never read
+    set_view(5);
+    if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+    __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
   }
 
+  int base = 0;  // slot of plane k - 3
   for (int k = z0; k < z1; ++k) {
     if (DIM == 3) {
-      // slot of plane k + 3 is (base + 6) mod 7; it held plane k - 4
-      int s = base + 6;
-      s = s >= 7 ? s - 7 : s;
-      load_plane<T, BX, BY, DIM, VISC>(A, g, ring + s * G::PLANE, gx0, gy0, k + 3);
+      // plane k + 3 goes to the slot of plane k - 3, dead since the previous
+      // plane's faces were finished (barrier)
+      load_plane<T, BX, BY, DIM, VISC>(A, g, ring + base * G::PLANE, gx0, gy0, k + 3);
     } else {
       load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, 0);
     }
     set_view(base);
     __syncthreads();
 
-    // x faces of plane k: face f (0..BX) between tile columns f-1 and f
-    for (int t = threadIdx.x; t < G::NFX; t += G::NT) {
-      const int fy = t / (BX + 1), fx = t - fy * (BX + 1);
+    if (xf_x >= 0) {
       T NF[5];
-      face_flux<T, 0, BX, BY, DIM, VISC>(R, HALO + fx - 1, G::HY + fy, g, inv_h, NF);
+      face_flux<T, 0, BX, BY, DIM, VISC>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
+      const int t = xf_y * (BX + 1) + xf_x;
 #pragma unroll
       for (int c = 0; c < 5; ++c) Fx[c * G::NFX + t] = NF[c];
     }
     if (DIM >= 2) {
-      for (int t = threadIdx.x; t < G::NFY; t += G::NT) {
-        const int fy = t / BX, fx = t - fy * BX;
-        T NF[5];
-        face_flux<T, 1, BX, BY, DIM, VISC>(R, HALO + fx, G::HY + fy - 1, g, inv_h, NF);
+      T NF[5];
+      face_flux<T, 1, BX, BY, DIM, VISC>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
+      const int t = yf_y * BX + yf_x;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) Fy[c * G::NFY + t] = NF[c];
-      }
+      for (int c = 0; c < 5; ++c) Fy[c * G::NFY + t] = NF[c];
     }
     T NFz_hi[5];
-    if (DIM == 3) face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+    if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
     __syncthreads();
 
     if (own) {
@@ -327,7 +351,7 @@ __global__ void __launch_bounds__(BX * BY) stage_kernel(const StageArgs<T> A, co
     if (DIM == 3) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) NFz_lo[c] = NFz_hi[c];
-      base = base + 1 == 7 ? 0 : base + 1;
+      base = base + 1 == 6 ? 0 : base + 1;
     }
   }
 }

@@ -4,26 +4,28 @@
 
 namespace jf {
 
-template <typename T, int DIM, bool VISC, int BX, int BY>
+// MINB: CTAs per SM the register allocation must allow (__launch_bounds__).
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
 cudaError_t prepare_stage() {
   constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
-  return cudaFuncSetAttribute(stage_kernel<T, DIM, VISC, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  return cudaFuncSetAttribute(stage_kernel<T, DIM, VISC, BX, BY, MINB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T, int DIM, bool VISC, int BX, int BY>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
 cudaError_t launch_stage(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s) {
   constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
   const dim3 grid((A.nx + BX - 1) / BX, DIM >= 2 ? (A.ny + BY - 1) / BY : 1,
                   DIM == 3 ? (A.nz + A.zchunk - 1) / A.zchunk : 1);
-  stage_kernel<T, DIM, VISC, BX, BY><<<grid, BX * BY, smem, s>>>(A, g);
+  stage_kernel<T, DIM, VISC, BX, BY, MINB><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, g);
   return cudaGetLastError();
 }
 
-template <typename T, int DIM, bool VISC, int BX, int BY>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
 StageVariant<T> make_variant() {
   return StageVariant<T>{DIM, VISC, BX, BY, stage_smem_bytes<T, DIM, VISC, BX, BY>(),
-                         &prepare_stage<T, DIM, VISC, BX, BY>, &launch_stage<T, DIM, VISC, BX, BY>, nullptr};
+                         &prepare_stage<T, DIM, VISC, BX, BY, MINB>, &launch_stage<T, DIM, VISC, BX, BY, MINB>,
+                         nullptr};
 }
 
 }  // namespace jf
