@@ -134,16 +134,18 @@ std::vector<std::pair<int, int>> variant_list(int dim, bool visc) {
 }
 
 template <typename T>
-jf_status select_variant(jf_ctx* h, int v) {
+jf_status select_variant(jf_ctx* h, int v, bool prepare) {
   const bool visc = dissipative(h->gas, h->scheme);
   auto list = variant_list<T>(h->dim, visc);
   if (list.empty()) { set_error(h, "no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
   if (v < 0) v = 0;
   if (v >= (int)list.size()) { set_error(h, "variant index out of range"); return JF_ERR_ARG; }
-  int count = 0;
-  const StageVariant<T>* tab = stage_variants<T>(&count);
-  cudaError_t e = tab[list[v].first].prepare();
-  if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+  if (prepare) {
+    int count = 0;
+    const StageVariant<T>* tab = stage_variants<T>(&count);
+    cudaError_t e = tab[list[v].first].prepare();
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+  }
   h->variant = v;
   h->table_index = list[v].first;
   h->zchunk = list[v].second;
@@ -266,8 +268,8 @@ jf_status loss_impl(jf_ctx* h, const void* U, const void* target, double* loss, 
   return JF_OK;
 }
 
-template jf_status select_variant<float>(jf_ctx*, int);
-template jf_status select_variant<double>(jf_ctx*, int);
+template jf_status select_variant<float>(jf_ctx*, int, bool);
+template jf_status select_variant<double>(jf_ctx*, int, bool);
 template jf_status step_impl<float>(jf_ctx*, void*, const double*, double*, cudaStream_t);
 template jf_status step_impl<double>(jf_ctx*, void*, const double*, double*, cudaStream_t);
 template jf_status cfl_impl<float>(jf_ctx*, const void*, double*, double*, cudaStream_t);
@@ -324,7 +326,7 @@ jf_status jf_init(const jf_grid* grid, const jf_gas* gas, const jf_scheme* schem
       if (e != cudaSuccess) st = cuda_fail(nullptr, e, "jf_init: stage buffer");
     }
   }
-  if (st == JF_OK) st = JF_DISPATCH(h, select_variant, h, -1);
+  if (st == JF_OK) st = JF_DISPATCH(h, select_variant, h, -1, true);
   if (st != JF_OK) {
     if (!h->err.empty()) set_error(nullptr, h->err);
     jf_destroy(h);
@@ -413,7 +415,7 @@ jf_status jf_set_variant(jf_handle h, int variant) {
   if (!h) { set_error(nullptr, "jf_set_variant: null handle"); return JF_ERR_ARG; }
   free_graphs(h);
   if (h->kind == 1) return batch_set_variant(h, variant);
-  return JF_DISPATCH(h, select_variant, h, variant);
+  return JF_DISPATCH(h, select_variant, h, variant, true);
 }
 
 int jf_variant_info(jf_handle h, int variant, char* buf, int len) {

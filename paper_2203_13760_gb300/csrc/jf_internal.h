@@ -86,6 +86,7 @@ void free_graphs(jf_ctx* h);
 template <typename T> Gas<T> make_gas(const jf_gas& gas, const jf_scheme& s);
 template <typename T> StageArgs<T> base_args(const jf_ctx* h);
 template <typename T> jf_status launch(jf_ctx* h, const StageArgs<T>& A, cudaStream_t s);
+template <typename T> jf_status select_variant(jf_ctx* h, int v, bool prepare);
 template <typename T> jf_status step_impl(jf_ctx* h, void* U, const double* dt_dev, double* dt_used, cudaStream_t s);
 
 // workspace shared by every handle kind: flag, dt scalar, reduction scratch, capture stream
