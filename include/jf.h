@@ -195,6 +195,28 @@ jf_status jf_status_sync(jf_handle h);
  * The string is owned by the library and valid until the next call. */
 const char* jf_last_error(jf_handle h);
 
+/* Largest grid (cells) jf_rk3_step_noalloc accepts. */
+#define JF_NOALLOC_MAX_CELLS 65536
+
+/* One RK3 step exactly like jf_rk3_step, but with no handle and no device
+ * memory allocation (the paper has no counterpart: this serves callers that
+ * may not call cudaMalloc / cudaFree while they run, e.g. under a device
+ * memory budget fixed at start-up or inside another library's hot loop).
+ * The stage buffers, the CFL reduction scratch, dt and the error flag live in
+ * one fixed device array compiled into libjf (about 5.2 MB, held by every GPU
+ * that loads the library until the process exits), sized for
+ * JF_NOALLOC_MAX_CELLS cells in FP64; larger grids are rejected with
+ * JF_ERR_ARG and an explanatory jf_last_error(NULL).
+ * grid / gas / scheme / U_inout / dt_dev / dt_used_dev / stream mean what
+ * they mean for jf_init and jf_rk3_step.  The first call on a device resolves
+ * the array's address and sets kernel attributes for that device (make that
+ * first call before any stream capture).  Every call shares the array: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller.
+ * Device-side non-physical states are not reported (there is no handle for
+ * jf_status_sync). */
+jf_status jf_rk3_step_noalloc(const jf_grid* grid, const jf_gas* gas, const jf_scheme* scheme, void* U_inout,
+                              const double* dt_dev, double* dt_used_dev, void* stream);
+
 /* Library version string. */
 const char* jf_version(void);
 

@@ -65,6 +65,8 @@ SIGNATURES = {
     "jf_status_sync": (_I, [_VP]),
     "jf_last_error": (ctypes.c_char_p, [_VP]),
     "jf_version": (ctypes.c_char_p, []),
+    "jf_rk3_step_noalloc": (_I, [ctypes.POINTER(Grid), ctypes.POINTER(GasParams), ctypes.POINTER(Scheme), _VP, _VP,
+                                 _VP, _VP]),
 }
 
 _lib = None

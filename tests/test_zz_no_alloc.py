@@ -1,0 +1,71 @@
+"""jf_rk3_step_noalloc: the RK3 step for callers that may not allocate device
+memory while they run.  It uses a fixed scratch array compiled into libjf
+instead of the stage buffers jf_init allocates, so its results must equal
+those of the handle path (jf_init + jf_rk3_step) on the same input.
+
+This file is named to be collected last; it passes both alone in a fresh
+process and after the other tests."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2203_13760_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2203_13760_gb300 import jf  # noqa: E402
+
+TOL = {"f32": 1e-5, "f64": 1e-12}  # the parity bars of the other GPU tests
+
+
+def rel_err(a, b):
+    a = a.double().reshape(5, -1).cpu().numpy()
+    b = b.double().reshape(5, -1).cpu().numpy()
+    return max(np.abs(a[g] - b[g]).max() / np.abs(b[g]).max() for g in ([0], [1, 2, 3], [4]))
+
+
+def noalloc_step(s, U, dt, dt_used):
+    """One step through the C ABI entry point jf_rk3_step_noalloc."""
+    L = jf.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return L.jf_rk3_step_noalloc(ctypes.byref(s.grid), ctypes.byref(s.gas), ctypes.byref(s.scheme),
+                                 ctypes.c_void_p(U.data_ptr()), jf._ptr(dt), jf._ptr(dt_used), stream)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("make", [
+    lambda: inputs.kelvin_helmholtz(64),                                   # 2D viscous, periodic
+    lambda: inputs.random_smooth((24, 20, 12), seed=3, viscous=True, mu=0.01),  # 3D, ragged tiles
+    lambda: inputs.random_blocks((200, 1, 1), seed=2),                     # 1D shocks, zero gradient
+])
+def test_noalloc_matches_handle_path(dtype, make):
+    case = make()
+    s = jf.Solver.from_case(case, dtype=dtype)
+    U_ref = torch.tensor(case.U, dtype=s.dtype, device="cuda")
+    U_na = U_ref.clone()
+    used_ref, used_na = s.scalar(), s.scalar()
+    for _ in range(2):  # two calls in a row: the shared scratch is reused
+        s.rk3_step(U_ref, None, used_ref)
+        assert noalloc_step(s, U_na, None, used_na) == jf.JF_OK, jf.lib().jf_last_error(None)
+        torch.cuda.synchronize()
+        assert used_na.item() == pytest.approx(used_ref.item(), rel=TOL[dtype])
+        assert rel_err(U_na, U_ref) <= TOL[dtype]
+    # fixed-dt form as well
+    dt = s.scalar(0.5 * used_ref.item())
+    s.rk3_step(U_ref, dt)
+    assert noalloc_step(s, U_na, dt, None) == jf.JF_OK
+    torch.cuda.synchronize()
+    assert rel_err(U_na, U_ref) <= TOL[dtype]
+    s.sync()
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    s = jf.Solver((300, 300, 1), bc=(0,) * 6, dtype="f32")  # 90,000 cells > 65,536
+    U = s.empty()
+    assert noalloc_step(s, U, None, None) == jf.JF_ERR_ARG
+    assert b"JF_NOALLOC_MAX_CELLS" in jf.lib().jf_last_error(None)
