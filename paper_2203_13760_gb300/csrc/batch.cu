@@ -1,20 +1,309 @@
-// Batched simulations (placeholder until the persistent kernel lands).
+// Batched simulations (jf_batch_create / jf_batch_step): many independent
+// grids of uneven sizes advanced together (Section 4.5, feed_forward over a
+// batch of initial buffers).
+//
+// Per RK3 step: one per-simulation CFL launch (each CTA reduces one chunk of
+// one simulation; the last chunk of a simulation forms its dt) and three
+// persistent stage launches over the flattened (simulation, tile) work list,
+// each item being one tile of the same code as the single-grid kernel.  The
+// nsteps steps are captured into one CUDA graph and replayed; the graph reads
+// the simulations' field pointers from device descriptors, so rebinding new
+// fields only rewrites the descriptors.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
 #include "jf_internal.h"
 
 namespace jf {
-jf_status batch_set_variant(jf_ctx* h, int) { set_error(h, "batch: not built"); return JF_ERR_UNSUPPORTED; }
-int batch_variant_info(jf_ctx*, int, char*, int) { return JF_ERR_UNSUPPORTED; }
+
+constexpr long long kChunk = 16384;  // cells per CFL CTA
+
+struct CflChunk {
+  int sim;
+  int nchunks;   // chunks of this simulation
+  long long begin, end;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) batch_cfl_kernel(const SimDesc<T>* __restrict__ sims,
+                                                        const CflChunk* __restrict__ chunks,
+                                                        const CflArgs* __restrict__ args, ReduceScratch* red,
+                                                        double* dt, int* flag) {
+  const CflChunk ch = chunks[blockIdx.x];
+  const CflArgs a = args[ch.sim];
+  const T* U = sims[ch.sim].U;
+  T conv = T(0), diff = T(0);
+  const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
+  bool bad = false;
+  for (long long q = ch.begin + threadIdx.x; q < ch.end; q += blockDim.x)
+    cell_rates(U, q, a.N, a.nactive, gamma, gm1, kdiff, conv, diff, bad);
+  if (bad) atomicOr(flag, 1);
+  finish_cfl((double)conv, (double)diff, red + ch.sim, (unsigned int)ch.nchunks, a.hmin, a.cfl, dt + ch.sim,
+             nullptr);
+}
+
+namespace {
+
+template <typename T>
+std::vector<int> batch_variant_list(int dim, bool visc) {
+  int count = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count);
+  std::vector<int> out;
+  for (int i = 0; i < count; ++i)
+    if (tab[i].dim == dim && tab[i].visc == visc && tab[i].launch_batch) out.push_back(i);
+  return out;
+}
+
+// (Re)build the work list for the tile shape of the selected variant.
+template <typename T>
+jf_status setup_variant(jf_ctx* h, int v) {
+  const bool visc = dissipative(h->gas, h->scheme);
+  auto list = batch_variant_list<T>(h->dim, visc);
+  if (list.empty()) { set_error(h, "batch: no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
+  if (v < 0) v = 0;
+  if (v >= (int)list.size()) { set_error(h, "batch: variant index out of range"); return JF_ERR_ARG; }
+  int count = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count);
+  const StageVariant<T>& sv = tab[list[v]];
+  int per_sm = 0;
+  cudaError_t e = sv.prepare_batch(&per_sm);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch: kernel set-up");
+  if (per_sm < 1) { set_error(h, "batch: kernel does not fit on an SM"); return JF_ERR_UNSUPPORTED; }
+  std::vector<WorkItem> work;
+  for (int s = 0; s < h->nsim; ++s) {
+    const jf_grid& g = h->grids[s];
+    const int tx = (g.nx + sv.bx - 1) / sv.bx;
+    const int ty = h->dim >= 2 ? (g.ny + sv.by - 1) / sv.by : 1;
+    for (int y = 0; y < ty; ++y)
+      for (int x = 0; x < tx; ++x) work.push_back(WorkItem{s, x, y});
+  }
+  if (h->d_work) cudaFree(h->d_work);
+  h->d_work = nullptr;
+  e = cudaMalloc(&h->d_work, work.size() * sizeof(WorkItem));
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch: work list");
+  e = cudaMemcpy(h->d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch: work list");
+  h->nwork = (int)work.size();
+  const long long cap = (long long)h->sms * per_sm;
+  h->batch_blocks = (int)(h->nwork < cap ? h->nwork : cap);
+  h->variant = v;
+  h->table_index = list[v];
+  return JF_OK;
+}
+
+template <typename T>
+jf_status create_impl(jf_ctx* h) {
+  const int ns = h->nsim;
+  std::vector<SimDesc<T>> desc(ns);
+  std::vector<CflArgs> cfl(ns);
+  std::vector<CflChunk> chunks;
+  h->sim_stage.assign(2 * ns, nullptr);
+  cudaError_t e;
+  // per-simulation dt first: every descriptor points at its slot
+  if ((e = cudaMalloc(&h->d_dt, ns * sizeof(double))) != cudaSuccess) return cuda_fail(h, e, "batch: dt");
+  if ((e = cudaMemset(h->d_dt, 0, ns * sizeof(double))) != cudaSuccess) return cuda_fail(h, e, "batch: dt");
+  for (int s = 0; s < ns; ++s) {
+    const jf_grid& g = h->grids[s];
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    for (int b = 0; b < 2; ++b) {
+      e = cudaMalloc(&h->sim_stage[2 * s + b], 5 * (size_t)N * sizeof(T));
+      if (e != cudaSuccess) return cuda_fail(h, e, "batch: stage buffers");
+    }
+    SimDesc<T>& d = desc[s];
+    std::memset(&d, 0, sizeof d);
+    d.U = nullptr;
+    d.U1 = static_cast<T*>(h->sim_stage[2 * s]);
+    d.U2 = static_cast<T*>(h->sim_stage[2 * s + 1]);
+    d.dt = h->d_dt + s;
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.nz = g.nz;
+    d.N = N;
+    for (int a = 0; a < 3; ++a) {
+      d.periodic[a] = g.bc[2 * a] == JF_BC_PERIODIC;
+      d.inv_h[a] = (T)(1.0 / spacing(g, a));
+    }
+    cfl[s] = make_cfl(g, h->gas, h->scheme);
+    const int nch = (int)((N + kChunk - 1) / kChunk);
+    for (int c = 0; c < nch; ++c) {
+      const long long lo = c * kChunk, hi = lo + kChunk < N ? lo + kChunk : N;
+      chunks.push_back(CflChunk{s, nch, lo, hi});
+    }
+  }
+  void* p = nullptr;
+  if ((e = cudaMalloc(&p, ns * sizeof(SimDesc<T>))) != cudaSuccess) return cuda_fail(h, e, "batch: descriptors");
+  h->d_sims = p;
+  if ((e = cudaMemcpy(p, desc.data(), ns * sizeof(SimDesc<T>), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(h, e, "batch: descriptors");
+  h->host_desc.assign(reinterpret_cast<unsigned char*>(desc.data()),
+                      reinterpret_cast<unsigned char*>(desc.data()) + ns * sizeof(SimDesc<T>));
+  if ((e = cudaMalloc(&p, ns * sizeof(ReduceScratch))) != cudaSuccess) return cuda_fail(h, e, "batch: reduction");
+  h->d_red = static_cast<ReduceScratch*>(p);
+  if ((e = cudaMemset(p, 0, ns * sizeof(ReduceScratch))) != cudaSuccess) return cuda_fail(h, e, "batch: reduction");
+  if ((e = cudaMalloc(&h->d_cfl, ns * sizeof(CflArgs))) != cudaSuccess) return cuda_fail(h, e, "batch: cfl");
+  if ((e = cudaMemcpy(h->d_cfl, cfl.data(), ns * sizeof(CflArgs), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(h, e, "batch: cfl");
+  if ((e = cudaMalloc(&h->d_chunks, chunks.size() * sizeof(CflChunk))) != cudaSuccess)
+    return cuda_fail(h, e, "batch: chunks");
+  if ((e = cudaMemcpy(h->d_chunks, chunks.data(), chunks.size() * sizeof(CflChunk), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return cuda_fail(h, e, "batch: chunks");
+  h->nchunks = (int)chunks.size();
+  h->bound_ptrs.assign(ns, nullptr);
+  return setup_variant<T>(h, -1);
+}
+
+// Point the descriptors at the caller's fields (only when they changed).
+template <typename T>
+jf_status bind_fields(jf_ctx* h, void* const* U_ptrs, cudaStream_t s) {
+  bool same = true;
+  for (int i = 0; i < h->nsim; ++i) same &= h->bound_ptrs[i] == U_ptrs[i];
+  if (same) return JF_OK;
+  SimDesc<T>* desc = reinterpret_cast<SimDesc<T>*>(h->host_desc.data());
+  for (int i = 0; i < h->nsim; ++i) desc[i].U = static_cast<T*>(U_ptrs[i]);
+  // work already queued may still read the old descriptors
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_sims, desc, h->nsim * sizeof(SimDesc<T>), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch: descriptor update");
+  for (int i = 0; i < h->nsim; ++i) h->bound_ptrs[i] = U_ptrs[i];
+  return JF_OK;
+}
+
+template <typename T>
+jf_status enqueue_steps(jf_ctx* h, int nsteps, double* dt_out, cudaStream_t s) {
+  int count = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count);
+  const StageVariant<T>& sv = tab[h->table_index];
+  const Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  const SimDesc<T>* sims = reinterpret_cast<const SimDesc<T>*>(h->d_sims);
+  const WorkItem* work = static_cast<const WorkItem*>(h->d_work);
+  for (int step = 0; step < nsteps; ++step) {
+    batch_cfl_kernel<T><<<h->nchunks, 256, 0, s>>>(sims, static_cast<const CflChunk*>(h->d_chunks),
+                                                   static_cast<const CflArgs*>(h->d_cfl), h->d_red, h->d_dt, h->flag);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch: cfl launch");
+    for (int stage = 1; stage <= 3; ++stage) {
+      e = sv.launch_batch(sims, work, h->nwork, stage, g, h->flag, h->batch_blocks, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "batch: stage launch");
+    }
+  }
+  if (dt_out) {
+    cudaError_t e = cudaMemcpyAsync(dt_out, h->d_dt, h->nsim * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch: dt copy");
+  }
+  return JF_OK;
+}
+
+template <typename T>
+jf_status step_batch(jf_ctx* h, void* const* U_ptrs, int nsteps, double* dt_out, cudaStream_t s) {
+  jf_status st = bind_fields<T>(h, U_ptrs, s);
+  if (st != JF_OK) return st;
+  const GraphKey key{nullptr, nsteps, dt_out, nullptr, h->variant};
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaStream_t cs = h->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    st = enqueue_steps<T>(h, nsteps, dt_out, cs);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (st != JF_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    it = h->graphs.emplace(key, GraphEntry{graph, exec}).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second.exec, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+  return JF_OK;
+}
+
+}  // namespace
+
+jf_status batch_set_variant(jf_ctx* h, int variant) {
+  return h->scheme.dtype == JF_F32 ? setup_variant<float>(h, variant) : setup_variant<double>(h, variant);
+}
+
+int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
+  const bool visc = dissipative(h->gas, h->scheme);
+  std::vector<int> list;
+  int bx = 0, by = 0;
+  if (h->scheme.dtype == JF_F32) {
+    list = batch_variant_list<float>(h->dim, visc);
+    int c = 0;
+    const StageVariant<float>* tab = stage_variants<float>(&c);
+    if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
+  } else {
+    list = batch_variant_list<double>(h->dim, visc);
+    int c = 0;
+    const StageVariant<double>* tab = stage_variants<double>(&c);
+    if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
+  }
+  if (variant >= 0 && variant < (int)list.size() && buf && len > 0)
+    std::snprintf(buf, (size_t)len, "tile=%dx%d persistent", bx, by);
+  return (int)list.size();
+}
+
 }  // namespace jf
 
 using namespace jf;
+
 extern "C" {
-jf_status jf_batch_create(const jf_grid*, int, const jf_gas*, const jf_scheme*, jf_handle* out) {
-  if (out) *out = nullptr;
-  set_error(nullptr, "jf_batch_create: not built yet");
-  return JF_ERR_UNSUPPORTED;
+
+jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, const jf_scheme* scheme,
+                          jf_handle* out) {
+  if (!grids || !gas || !scheme || !out || nsim < 1) {
+    set_error(nullptr, "jf_batch_create: null argument or nsim < 1");
+    return JF_ERR_ARG;
+  }
+  *out = nullptr;
+  jf_status st;
+  if ((st = check_physics(nullptr, *gas, *scheme)) != JF_OK) return st;
+  const int dim = active_dims(grids[0]);
+  for (int s = 0; s < nsim; ++s) {
+    if ((st = check_grid(nullptr, grids[s])) != JF_OK) return st;
+    if (active_dims(grids[s]) != dim) {
+      set_error(nullptr, "jf_batch_create: all simulations must have the same number of active axes");
+      return JF_ERR_UNSUPPORTED;
+    }
+  }
+  if (dim == 3) { set_error(nullptr, "jf_batch_create: batches of 3D grids are not built"); return JF_ERR_UNSUPPORTED; }
+  jf_ctx* h = new jf_ctx();
+  h->kind = 1;
+  h->gas = *gas;
+  h->scheme = *scheme;
+  h->grid = grids[0];
+  h->dim = dim;
+  h->esize = scheme->dtype == JF_F32 ? 4 : 8;
+  h->nsim = nsim;
+  h->grids.assign(grids, grids + nsim);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) { st = cuda_fail(nullptr, e, "jf_batch_create: device query"); delete h; return st; }
+  st = alloc_common(h);
+  if (st == JF_OK) st = scheme->dtype == JF_F32 ? create_impl<float>(h) : create_impl<double>(h);
+  if (st != JF_OK) {
+    if (!h->err.empty()) set_error(nullptr, h->err);
+    jf_destroy(h);
+    return st;
+  }
+  *out = h;
+  return JF_OK;
 }
-jf_status jf_batch_step(jf_handle h, void* const*, int, double*, void*) {
-  set_error(h, "jf_batch_step: not built yet");
-  return JF_ERR_UNSUPPORTED;
+
+jf_status jf_batch_step(jf_handle h, void* const* U_ptrs, int nsteps, double* dt_dev, void* stream) {
+  if (!h || h->kind != 1) { set_error(h, "jf_batch_step: not a batch handle"); return JF_ERR_ARG; }
+  if (!U_ptrs || nsteps < 0) { set_error(h, "jf_batch_step: bad arguments"); return JF_ERR_ARG; }
+  for (int s = 0; s < h->nsim; ++s)
+    if (!U_ptrs[s] || !aligned16(U_ptrs[s])) {
+      set_error(h, "jf_batch_step: every field must be a 16-byte aligned device array");
+      return JF_ERR_ARG;
+    }
+  if (nsteps == 0) return JF_OK;
+  return h->scheme.dtype == JF_F32 ? step_batch<float>(h, U_ptrs, nsteps, dt_dev, (cudaStream_t)stream)
+                                   : step_batch<double>(h, U_ptrs, nsteps, dt_dev, (cudaStream_t)stream);
 }
-}
+
+}  // extern "C"

@@ -30,6 +30,10 @@ void release_all(jf_ctx* h) {
   if (h->d_work) cudaFree(h->d_work);
   if (h->d_dt) cudaFree(h->d_dt);
   if (h->d_red) cudaFree(h->d_red);
+  if (h->d_cfl) cudaFree(h->d_cfl);
+  if (h->d_chunks) cudaFree(h->d_chunks);
+  h->d_cfl = nullptr;
+  h->d_chunks = nullptr;
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   h->flag = nullptr; h->dt_buf = nullptr; h->red_cfl = h->red_loss = nullptr;
   h->d_sims = nullptr; h->d_work = nullptr; h->d_dt = nullptr; h->d_red = nullptr; h->capture_stream = nullptr;

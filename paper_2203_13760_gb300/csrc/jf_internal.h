@@ -29,8 +29,6 @@ struct GraphEntry {
   cudaGraphExec_t exec;
 };
 
-// One simulation of a batch (device-side descriptor, see batch.cu).
-struct SimDesc;
 
 }  // namespace jf
 
@@ -60,7 +58,11 @@ struct jf_ctx {
   int nsim = 0;
   std::vector<jf_grid> grids;
   std::vector<void*> sim_stage;        // 2 per simulation
-  jf::SimDesc* d_sims = nullptr;       // device array of descriptors
+  void* d_sims = nullptr;              // device array of SimDesc<T> (stage.cuh)
+  std::vector<unsigned char> host_desc;  // host copy of the descriptors
+  void* d_cfl = nullptr;               // per-simulation CflArgs
+  void* d_chunks = nullptr;            // CFL chunk list
+  int nchunks = 0;
   void* d_work = nullptr;              // device work list
   int nwork = 0;
   double* d_dt = nullptr;              // per-simulation dt (internal)

@@ -43,58 +43,58 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// dt = CFL min(dt_c, dt_v): dt_c = hmin / max(|u_d| + c), dt_v = 3/14 hmin^2 / max(kdiff / rho).
-// Writes dt to dt_out and, if non-null, dt_out2.  blockDim.x == 256.
+// Per-cell rates of the CFL criterion, folded into running maxima: the wave
+// rate max_d |u_d| + c over the active axes and the diffusion rate kdiff / rho.
+// Computed in the field's precision (FP64 units are scarce on this part); the
+// maxima are later formed in FP64, and a rate converted to FP64 is exact, so
+// the result is the exact maximum of the per-cell values.
 template <typename T>
-__global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U, CflArgs a, ReduceScratch* sc,
-                                                  double* dt_out, double* dt_out2, int* flag) {
-  // Per-cell rates in the field's precision (FP64 units are scarce on this
-  // part); the maximum and dt are formed in FP64.  A rate converted to FP64 is
-  // exact, so the maximum is the exact maximum of the per-cell values.
-  T conv = T(0), diff = T(0);
-  const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
-  bool bad = false;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.N; q += stride) {
-    const T r = U[q];
-    const T inv = T(1) / r;
-    const T u = U[q + a.N] * inv;
-    const T v = U[q + 2 * a.N] * inv;
-    const T w = U[q + 3 * a.N] * inv;
-    const T p = gm1 * (U[q + 4 * a.N] - T(0.5) * r * (u * u + v * v + w * w));
-    bad |= !(r > T(0)) || !(p > T(0));
-    const T c = tsqrt(gamma * p * inv);
-    T m = fabs(u);
-    if (a.nactive > 1) m = fmax(m, fabs(v));
-    if (a.nactive > 2) m = fmax(m, fabs(w));
-    conv = fmax(conv, m + c);
-    diff = fmax(diff, kdiff * inv);
-  }
-  if (bad) atomicOr(flag, 1);
+__device__ __forceinline__ void cell_rates(const T* __restrict__ U, long long q, long long N, int nactive, T gamma,
+                                           T gm1, T kdiff, T& conv, T& diff, bool& bad) {
+  const T r = U[q];
+  const T inv = T(1) / r;
+  const T u = U[q + N] * inv;
+  const T v = U[q + 2 * N] * inv;
+  const T w = U[q + 3 * N] * inv;
+  const T p = gm1 * (U[q + 4 * N] - T(0.5) * r * (u * u + v * v + w * w));
+  bad |= !(r > T(0)) || !(p > T(0));
+  const T c = tsqrt(gamma * p * inv);
+  T m = fabs(u);
+  if (nactive > 1) m = fmax(m, fabs(v));
+  if (nactive > 2) m = fmax(m, fabs(w));
+  conv = fmax(conv, m + c);
+  diff = fmax(diff, kdiff * inv);
+}
+
+// Block-wide FP64 maxima of (conv, diff) folded into sc; the CTA that takes
+// the last of `nblocks` tickets forms dt = CFL min(hmin / C, 3/14 hmin^2 / D)
+// and resets sc.  blockDim.x <= 256, a multiple of 32.
+__device__ __forceinline__ void finish_cfl(double conv, double diff, ReduceScratch* sc, unsigned int nblocks,
+                                           double hmin, double cfl, double* dt_out, double* dt_out2) {
   __shared__ double s_conv[8], s_diff[8];
-  double dconv = warp_max((double)conv);
-  double ddiff = warp_max((double)diff);
+  conv = warp_max(conv);
+  diff = warp_max(diff);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { s_conv[wid] = dconv; s_diff[wid] = ddiff; }
+  if (lane == 0) { s_conv[wid] = conv; s_diff[wid] = diff; }
   __syncthreads();
   if (wid == 0) {
-    dconv = lane < (int)(blockDim.x >> 5) ? s_conv[lane] : 0.0;
-    ddiff = lane < (int)(blockDim.x >> 5) ? s_diff[lane] : 0.0;
-    dconv = warp_max(dconv);
-    ddiff = warp_max(ddiff);
+    conv = lane < (int)(blockDim.x >> 5) ? s_conv[lane] : 0.0;
+    diff = lane < (int)(blockDim.x >> 5) ? s_diff[lane] : 0.0;
+    conv = warp_max(conv);
+    diff = warp_max(diff);
     if (lane == 0) {
       // NaN never wins fmax; a NaN state is reported through the flag
-      atomicMax(&sc->acc[0], (unsigned long long)__double_as_longlong(dconv));
-      atomicMax(&sc->acc[1], (unsigned long long)__double_as_longlong(ddiff));
+      atomicMax(&sc->acc[0], (unsigned long long)__double_as_longlong(conv));
+      atomicMax(&sc->acc[1], (unsigned long long)__double_as_longlong(diff));
       __threadfence();
       const unsigned int t = atomicAdd(&sc->ticket, 1u);
-      if (t == gridDim.x - 1) {
+      if (t == nblocks - 1) {
         __threadfence();
         const double C = __longlong_as_double((long long)atomicMax(&sc->acc[0], 0ull));
         const double Dm = __longlong_as_double((long long)atomicMax(&sc->acc[1], 0ull));
-        double dt = a.hmin / C;
-        if (Dm > 0.0) dt = fmin(dt, (3.0 / 14.0) * a.hmin * a.hmin / Dm);
-        dt *= a.cfl;
+        double dt = hmin / C;
+        if (Dm > 0.0) dt = fmin(dt, (3.0 / 14.0) * hmin * hmin / Dm);
+        dt *= cfl;
         *dt_out = dt;
         if (dt_out2) *dt_out2 = dt;
         sc->acc[0] = 0ull;
@@ -104,6 +104,21 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U, CflAr
       }
     }
   }
+}
+
+// dt = CFL min(dt_c, dt_v): dt_c = hmin / max(|u_d| + c), dt_v = 3/14 hmin^2 / max(kdiff / rho).
+// Writes dt to dt_out and, if non-null, dt_out2.  blockDim.x == 256.
+template <typename T>
+__global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U, CflArgs a, ReduceScratch* sc,
+                                                  double* dt_out, double* dt_out2, int* flag) {
+  T conv = T(0), diff = T(0);
+  const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.N; q += stride)
+    cell_rates(U, q, a.N, a.nactive, gamma, gm1, kdiff, conv, diff, bad);
+  if (bad) atomicOr(flag, 1);
+  finish_cfl((double)conv, (double)diff, sc, gridDim.x, a.hmin, a.cfl, dt_out, dt_out2);
 }
 
 // loss = sum_cells (rho - target)^2 * dV; seed = d loss / dU (density

@@ -234,17 +234,20 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
 
 // The stage kernel.  blockDim.x == Geo::NT.
 // grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/zchunk)) (3D), (.., .., 1) otherwise.
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
-__global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
-    stage_kernel(const StageArgs<T> A, const Gas<T> g) {
+// One tile (tile column (bx, by), z chunk bz) of one grid: the whole stage
+// for its cells.  Shared memory: the ring and the face buffers.  All threads
+// of the CTA call it; it starts and ends without pending shared-memory reads
+// that a following call could disturb (the first barrier inside orders them).
+template <typename T, int DIM, bool VISC, int BX, int BY>
+__device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& g, int bx, int by, int bz,
+                                           T* smem) {
   using G = Geo<BX, BY, DIM, VISC>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = reinterpret_cast<T*>(smem_raw);
+  T* ring = smem;
   T* Fx = ring + G::RING * G::PLANE;      // [5][BY][BX+1]
   T* Fy = Fx + 5 * G::NFX;                // [5][BY+1][BX]
 
-  const int gx0 = blockIdx.x * BX;
-  const int gy0 = blockIdx.y * BY;
+  const int gx0 = bx * BX;
+  const int gy0 = by * BY;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool cell_thread = threadIdx.x < G::NCELL;
   const int tx = threadIdx.x % BX;
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
 
   int z0 = 0, z1 = 1;
   if (DIM == 3) {
-    z0 = blockIdx.z * A.zchunk;
+    z0 = bz * A.zchunk;
     z1 = min(z0 + A.zchunk, A.nz);
   }
 
@@ -353,6 +356,72 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
       for (int c = 0; c < 5; ++c) NFz_lo[c] = NFz_hi[c];
       base = base + 1 == 6 ? 0 : base + 1;
     }
+  }
+}
+
+// The stage kernel: one CTA per tile.  blockDim.x == Geo::NT,
+// grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/zchunk)) (3D), (.., .., 1) otherwise.
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
+    stage_kernel(const StageArgs<T> A, const Gas<T> g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_tile<T, DIM, VISC, BX, BY>(A, g, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<T*>(smem_raw));
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent grids (Section 4.5, feed_forward over a
+// batch; sizes may differ), one persistent launch per RK stage.
+template <typename T>
+struct SimDesc {
+  T* U;               // the simulation's field (caller-owned), [5][nz][ny][nx]
+  T* U1;              // stage buffers (library-owned)
+  T* U2;
+  const double* dt;   // this simulation's step
+  int nx, ny, nz;
+  int periodic[3];
+  T inv_h[3];
+  long long N;
+};
+
+struct WorkItem {
+  int sim;
+  int bx, by;
+};
+
+// stage 1: U1 = U + dt L(U); stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+// stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2)).  CTAs loop over the work list
+// (static round robin: every item is one full tile of equal cost).
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
+    batch_stage_kernel(const SimDesc<T>* __restrict__ sims, const WorkItem* __restrict__ work, int nwork,
+                       int stage, const Gas<T> g, int* flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
+    const WorkItem w = work[item];
+    const SimDesc<T> d = sims[w.sim];
+    StageArgs<T> A;
+    A.nx = d.nx;
+    A.ny = d.ny;
+    A.nz = d.nz;
+    A.N = d.N;
+    A.periodic[0] = d.periodic[0];
+    A.periodic[1] = d.periodic[1];
+    A.periodic[2] = d.periodic[2];
+    A.inv_h[0] = d.inv_h[0];
+    A.inv_h[1] = d.inv_h[1];
+    A.inv_h[2] = d.inv_h[2];
+    A.dt = d.dt;
+    A.rhs_only = 0;
+    A.zchunk = d.nz;
+    A.flag = flag;
+    if (stage == 1) {
+      A.Us = d.U; A.Un = nullptr; A.out = d.U1; A.a = T(0); A.b = T(1);
+    } else if (stage == 2) {
+      A.Us = d.U1; A.Un = d.U; A.out = d.U2; A.a = T(0.75); A.b = T(0.25);
+    } else {
+      A.Us = d.U2; A.Un = d.U; A.out = d.U; A.a = T(1.0 / 3.0); A.b = T(2.0 / 3.0);
+    }
+    stage_tile<T, DIM, VISC, BX, BY>(A, g, w.bx, w.by, 0, reinterpret_cast<T*>(smem_raw));
   }
 }
 

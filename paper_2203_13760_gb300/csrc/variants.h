@@ -20,8 +20,11 @@ struct StageVariant {
   size_t smem;
   cudaError_t (*prepare)();  // one-time attribute set-up (dynamic shared memory)
   cudaError_t (*launch)(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s);
-  // persistent batched launch over a work list (2D / 1D variants only; may be null)
-  const void* batch_kernel;
+  // persistent batched launch over a work list (same tile code; 2D / 1D only, else null)
+  cudaError_t (*prepare_batch)(int* blocks_per_sm);
+  cudaError_t (*launch_batch)(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
+                              int* flag, int grid, cudaStream_t s);
+  int threads;
 };
 
 // All compiled variants for precision T (defined in stage_f32.cu / stage_f64.cu).
