@@ -22,7 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr"]
 # FP32 kernels use approximate division / square root (see stage_f32.cu)
-PER_FILE_FLAGS = {"stage_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+_FAST = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+PER_FILE_FLAGS = {"stage_f32.cu": _FAST, "vjp_f32.cu": _FAST}
 
 
 def nvcc() -> str:

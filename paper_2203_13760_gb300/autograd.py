@@ -1,0 +1,97 @@
+"""Differentiable RK3 steps and trajectories on top of libjf (Section 7.2:
+end-to-end optimisation through the solver; Section 4.5: ``feed_forward`` with
+a fixed step).
+
+``rk3_step(solver, U, dt)``   one fixed-dt step as a torch.autograd.Function;
+                              its backward is jf_rk3_step_vjp.
+``rollout(solver, U0, n, dt, ckpt_every=20)``
+                              n fixed-dt steps whose backward pass recomputes
+                              each segment of ``ckpt_every`` steps from a stored
+                              checkpoint (memory: n / ckpt_every + ckpt_every
+                              states instead of n).
+``density_l2(solver, U, target)``
+                              sum_cells (rho - target)^2 dV (jf_loss_density_l2)
+                              with its gradient.
+
+dt is a float64 CUDA scalar tensor and is not differentiated (the paper's
+feed_forward uses a fixed step).  Every computation runs in libjf's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+
+class _RK3Step(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, solver, dt):
+        ctx.solver = solver
+        ctx.save_for_backward(U, dt)
+        out = U.detach().clone()
+        solver.rk3_step(out, dt)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad):
+        U, dt = ctx.saved_tensors
+        lam = ctx.solver.rk3_step_vjp(U.detach(), dt, grad.contiguous())
+        return lam, None, None
+
+
+def rk3_step(solver, U, dt):
+    return _RK3Step.apply(U, solver, dt)
+
+
+class _Rollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U0, solver, dt, nsteps, ckpt_every):
+        U = U0.detach().clone()
+        ckpts = [U.clone()]
+        for k in range(nsteps):
+            solver.rk3_step(U, dt)
+            if (k + 1) % ckpt_every == 0 and k + 1 < nsteps:
+                ckpts.append(U.clone())
+        ctx.solver, ctx.nsteps, ctx.ckpt_every = solver, nsteps, ckpt_every
+        ctx.ckpts = ckpts
+        ctx.save_for_backward(dt)
+        return U
+
+    @staticmethod
+    def backward(ctx, grad):
+        (dt,) = ctx.saved_tensors
+        s, n, c = ctx.solver, ctx.nsteps, ctx.ckpt_every
+        lam = grad.contiguous().clone()
+        lam_next = torch.empty_like(lam)
+        for seg in reversed(range(len(ctx.ckpts))):
+            start = seg * c
+            length = min(c, n - start)
+            states = [ctx.ckpts[seg]]
+            for _ in range(length - 1):
+                nxt = states[-1].clone()
+                s.rk3_step(nxt, dt)
+                states.append(nxt)
+            for k in reversed(range(length)):
+                s.rk3_step_vjp(states[k], dt, lam, lam_next)
+                lam, lam_next = lam_next, lam
+        ctx.ckpts = None
+        return lam, None, None, None, None
+
+
+def rollout(solver, U0, nsteps, dt, ckpt_every=20):
+    return _Rollout.apply(U0, solver, dt, int(nsteps), int(ckpt_every))
+
+
+class _DensityL2(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, solver, target):
+        loss, seed = solver.loss_density_l2(U.detach(), target)
+        ctx.save_for_backward(seed)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        (seed,) = ctx.saved_tensors
+        return seed * grad, None, None
+
+
+def density_l2(solver, U, target):
+    return _DensityL2.apply(U, solver, target)

@@ -12,6 +12,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+// point-wise numerics compile for the host too (used by host-side checks)
+#define JF_HD __host__ __device__ __forceinline__
+
 namespace jf {
 
 template <typename T>
@@ -26,19 +29,19 @@ struct Gas {
   int safe;    // first-order fallback for non-positive reconstructed rho / p
 };
 
-template <typename T> __device__ __forceinline__ T tsqrt(T x);
-template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+template <typename T> JF_HD T tsqrt(T x);
+template <> JF_HD float tsqrt<float>(float x) { return sqrtf(x); }
+template <> JF_HD double tsqrt<double>(double x) { return sqrt(x); }
 
-template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
-template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
+template <typename T> JF_HD T tmin(T a, T b) { return b < a ? b : a; }
+template <typename T> JF_HD T tmax(T a, T b) { return a < b ? b : a; }
 
 // WENO5-JS: value at x_{i+1/2} biased to the left, from v[i-2..i+2].
 // Candidate stencils q_k, smoothness indicators beta_k, weights
 // alpha_k = d_k / (eps + beta_k)^2 with d = (1/10, 6/10, 3/10),
 // omega_k = alpha_k / sum(alpha).
 template <typename T>
-__device__ __forceinline__ T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
+JF_HD T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
   const T sixth = T(1) / T(6);
   const T q0 = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) * sixth;
   const T q1 = (-vm1 + T(5) * v0 + T(2) * vp1) * sixth;
@@ -78,7 +81,7 @@ __device__ __forceinline__ T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
 //   F*_K = F_K + S_K (U*_K - U_K),
 //   U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S*, u_t, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))]
 template <typename T, int D>
-__device__ __forceinline__ void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
+JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
   const T rL = WL[0], rR = WR[0], pL = WL[4], pR = WR[4];
   const T unL = WL[1 + D], unR = WR[1 + D];
   const T kL = T(0.5) * rL * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
@@ -125,15 +128,15 @@ __device__ __forceinline__ void hllc(const T WL[5], const T WR[5], const Gas<T>&
 
 // Section 3.4 stencils (without the 1/h factor).
 template <typename T>
-__device__ __forceinline__ T df4(T a, T b, T c, T d) {  // face derivative * h
+JF_HD T df4(T a, T b, T c, T d) {  // face derivative * h
   return (a - T(27) * b + T(27) * c - d) * (T(1) / T(24));
 }
 template <typename T>
-__device__ __forceinline__ T dc4(T m2, T m1, T p1, T p2) {  // cell-centre derivative * h
+JF_HD T dc4(T m2, T m1, T p1, T p2) {  // cell-centre derivative * h
   return (m2 - T(8) * m1 + T(8) * p1 - p2) * (T(1) / T(12));
 }
 template <typename T>
-__device__ __forceinline__ T rc4(T a, T b, T c, T d) {  // face interpolation
+JF_HD T rc4(T a, T b, T c, T d) {  // face interpolation
   return (-a + T(9) * b + T(9) * c - d) * (T(1) / T(16));
 }
 
