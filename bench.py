@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="jf", choices=["jf", "reference"])
     p.add_argument("--workload", default="tgv256", choices=sorted(WORKLOADS))
-    p.add_argument("--extras", action="store_true", help="also time the batched and adjoint forms")
+    p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=-1)
     return p.parse_args()
@@ -365,7 +365,7 @@ def run_jf(args):
            "h2d_bytes_per_step": int(host.numel() * esize), "d2h_bytes_per_step": int(host_out.numel() * esize)}
 
     extras = {}
-    if args.extras and rank == 0:
+    if not args.no_extras and rank == 0:
         extras = run_extras(args)
 
     if rank == 0:
@@ -399,9 +399,127 @@ def run_jf(args):
     return 0
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batched(steps=100, nsim=64):
+    """64 four-quadrant Riemann problems (sides from {64, 128, 256, 512},
+    FP32, CFL steps): one persistent launch per stage over all simulations
+    under a captured graph, against the same simulations advanced one by one
+    through jf_rk3_run (one graph per simulation) and through jf_rk3_step."""
+    import numpy as np
+    import torch
+
+    from paper_2203_13760_gb300 import inputs, jf
+    cases = inputs.four_quadrant_batch(nsim=nsim)
+    cells = sum(c.cells for c in cases)
+    grids = [jf.make_grid(c.n, c.lo, c.hi, c.bc) for c in cases]
+    b = jf.Batch(grids, dtype="f32", cfl=0.5)
+    Us = [torch.tensor(c.U, dtype=torch.float32, device="cuda") for c in cases]
+    b.step(Us, steps)  # capture + first run
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    b.step(Us, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    b.sync()
+    solvers = [jf.Solver.from_case(c, dtype="f32") for c in cases]
+    Vs = [torch.tensor(c.U, dtype=torch.float32, device="cuda") for c in cases]
+    for s_, V in zip(solvers, Vs):
+        s_.run(V, steps)  # capture each simulation's graph
+    torch.cuda.synchronize()
+    e0.record()
+    for s_, V in zip(solvers, Vs):
+        s_.run(V, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) * 1e-3
+    Ws = [torch.tensor(c.U, dtype=torch.float32, device="cuda") for c in cases]
+    for s_, W in zip(solvers, Ws):
+        s_.rk3_step(W)
+    torch.cuda.synchronize()
+    e0.record()
+    for s_, W in zip(solvers, Ws):
+        for _ in range(steps):
+            s_.rk3_step(W)
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    # the batch advanced 2 x steps, the graph path 2 x steps: same states
+    same = all(torch.equal(U, V) for U, V in zip(Us, Vs))
+    return {"workload": f"{nsim} four-quadrant Riemann problems, sides {{64,128,256,512}}, FP32, CFL 0.5",
+            "cells": cells, "steps": steps, "unit": "cell-updates/s",
+            "batched": cells * steps / t_batch, "plain_graph_per_sim": cells * steps / t_graph,
+            "plain_per_step_calls": cells * steps / t_plain,
+            "speedup_vs_graph_per_sim": t_graph / t_batch, "speedup_vs_per_step_calls": t_plain / t_batch,
+            "bitwise_equal_to_plain": bool(same), "gpu_launches_batched": 4 * steps}
+
+
+def run_adjoint(n=256, steps=400, ckpt=20):
+    """Kelvin-Helmholtz 256^2 (Re 1e4), FP32, fixed dt: loss = density L2
+    mismatch after 400 steps; gradient w.r.t. the initial state through the
+    checkpointed rollout (checkpoints every 20 steps, recompute)."""
+    import torch
+
+    from paper_2203_13760_gb300 import autograd as jfa
+    from paper_2203_13760_gb300 import inputs, jf
+    case = inputs.kelvin_helmholtz(n)
+    target = torch.tensor(inputs.kelvin_helmholtz(n, seed=7).U[0], dtype=torch.float32, device="cuda")
+    s = jf.Solver.from_case(case, dtype="f32")
+    U0 = torch.tensor(case.U, dtype=torch.float32, device="cuda")
+    dt = s.compute_dt(U0)
+    # plain forward (one graph of 400 steps)
+    V = U0.clone()
+    s.run(V, steps, dt)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    V = U0.clone()
+    e0.record()
+    s.run(V, steps, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    t_fwd_graph = e0.elapsed_time(e1) * 1e-3
+    # differentiable forward + backward
+    X = U0.clone().requires_grad_(True)
+    loss = jfa.density_l2(s, jfa.rollout(s, X, steps, dt, ckpt), target)
+    loss.backward()
+    torch.cuda.synchronize()
+    X.grad = None
+    e0.record()
+    loss = jfa.density_l2(s, jfa.rollout(s, X, steps, dt, ckpt), target)
+    e2, e3 = _events()
+    e2.record()
+    loss.backward()
+    e3.record()
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e2) * 1e-3
+    t_bwd = e2.elapsed_time(e3) * 1e-3
+    s.sync()
+    ok = bool(torch.isfinite(X.grad).all().item())
+    cells = case.cells
+    return {"workload": f"Kelvin-Helmholtz {n}^2, FP32, {steps} fixed-dt steps, checkpoints every {ckpt}",
+            "unit": "cell-updates/s", "forward_graph": cells * steps / t_fwd_graph,
+            "forward_differentiable": cells * steps / t_fwd, "backward": cells * steps / t_bwd,
+            "backward_over_forward_graph": t_bwd / t_fwd_graph, "grad_finite": ok,
+            "backward_ms": 1e3 * t_bwd, "forward_graph_ms": 1e3 * t_fwd_graph}
+
+
 def run_extras(args):
     """Batched and adjoint forms against the plain per-simulation launch."""
-    return {}
+    out = {}
+    try:
+        out["batched"] = run_batched()
+    except Exception as e:  # report, do not hide the main line
+        out["batched"] = {"error": repr(e)}
+    try:
+        out["adjoint"] = run_adjoint()
+    except Exception as e:
+        out["adjoint"] = {"error": repr(e)}
+    return out
 
 
 def main():
