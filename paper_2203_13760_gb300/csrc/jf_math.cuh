@@ -71,6 +71,35 @@ JF_HD T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
   }
 }
 
+// The left and right WENO5-JS states of one face component in packed FP32x2
+// arithmetic (sm_100+ FFMA2 / FADD2 / FMUL2): lane x reconstructs
+// (v[i-2], .., v[i+2]) -> v^-, lane y the mirrored stencil
+// (v[i+3], .., v[i-1]) -> v^+.  Same formula as weno5, two stencils per
+// instruction.
+__device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, float2 vp1, float2 vp2, float eps) {
+  auto c = [](float x) { return make_float2(x, x); };
+  const float2 q0 = __ffma2_rn(c(11.0f / 6.0f), v0, __ffma2_rn(c(-7.0f / 6.0f), vm1, __fmul2_rn(c(2.0f / 6.0f), vm2)));
+  const float2 q1 = __ffma2_rn(c(2.0f / 6.0f), vp1, __ffma2_rn(c(5.0f / 6.0f), v0, __fmul2_rn(c(-1.0f / 6.0f), vm1)));
+  const float2 q2 = __ffma2_rn(c(-1.0f / 6.0f), vp2, __ffma2_rn(c(5.0f / 6.0f), vp1, __fmul2_rn(c(2.0f / 6.0f), v0)));
+  const float2 d0 = __ffma2_rn(c(-2.0f), vm1, __fadd2_rn(vm2, v0));
+  const float2 e0 = __ffma2_rn(c(3.0f), v0, __ffma2_rn(c(-4.0f), vm1, vm2));
+  const float2 d1 = __ffma2_rn(c(-2.0f), v0, __fadd2_rn(vm1, vp1));
+  const float2 e1 = __ffma2_rn(c(-1.0f), vp1, vm1);
+  const float2 d2 = __ffma2_rn(c(-2.0f), vp1, __fadd2_rn(v0, vp2));
+  const float2 e2 = __ffma2_rn(c(3.0f), v0, __ffma2_rn(c(-4.0f), vp1, vp2));
+  const float2 k13 = c(13.0f / 12.0f), k14 = c(0.25f), ke = c(eps);
+  const float2 t0 = __ffma2_rn(__fmul2_rn(k13, d0), d0, __ffma2_rn(__fmul2_rn(k14, e0), e0, ke));
+  const float2 t1 = __ffma2_rn(__fmul2_rn(k13, d1), d1, __ffma2_rn(__fmul2_rn(k14, e1), e1, ke));
+  const float2 t2 = __ffma2_rn(__fmul2_rn(k13, d2), d2, __ffma2_rn(__fmul2_rn(k14, e2), e2, ke));
+  const float2 s0 = __fmul2_rn(t0, t0), s1 = __fmul2_rn(t1, t1), s2 = __fmul2_rn(t2, t2);
+  const float2 a0 = make_float2(0.1f / s0.x, 0.1f / s0.y);
+  const float2 a1 = make_float2(0.6f / s1.x, 0.6f / s1.y);
+  const float2 a2 = make_float2(0.3f / s2.x, 0.3f / s2.y);
+  const float2 sum = __fadd2_rn(__fadd2_rn(a0, a1), a2);
+  const float2 num = __ffma2_rn(a2, q2, __ffma2_rn(a1, q1, __fmul2_rn(a0, q0)));
+  return make_float2(num.x / sum.x, num.y / sum.y);
+}
+
 // HLLC flux along axis D from the reconstructed primitive states
 // W = [rho, u, v, w, p] left (WL) and right (WR) of the face.
 //   U_K, F_K                conservative state and physical flux of side K

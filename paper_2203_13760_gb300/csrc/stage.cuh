@@ -78,38 +78,73 @@ struct Geo {
   static_assert(DIM != 1 || BY == 1, "1D tiles are one row");
 };
 
-// Load plane gz (global z index, mapped by the boundary condition) of the
-// tile at (gx0, gy0) into dst, as primitive variables (+ temperature).
+// Plane loads are split into a fetch (global loads of the conservative state
+// into registers) and a commit (conversion to W (+T) and the shared-memory
+// store), so that the fetch of the next plane can be issued before the face
+// computations of the current one and its latency overlaps with them.
 template <typename T, int BX, int BY, int DIM, bool VISC>
-__device__ __forceinline__ void load_plane(const StageArgs<T>& A, const Gas<T>& g, T* dst, int gx0, int gy0,
-                                           int gz) {
+struct PlaneRegs {
+  using G = Geo<BX, BY, DIM, VISC>;
+  static constexpr int PF = (G::CS + G::NT - 1) / G::NT;  // cells per thread
+  T v[PF][5];
+};
+
+// Fetch plane gz (global z index, mapped by the boundary condition) of the
+// tile at (gx0, gy0).
+template <typename T, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void fetch_plane(const StageArgs<T>& A, PlaneRegs<T, BX, BY, DIM, VISC>& r, int gx0,
+                                            int gy0, int gz) {
   using G = Geo<BX, BY, DIM, VISC>;
   const int kz = DIM == 3 ? map_index(gz, A.nz, A.periodic[2]) : 0;
   const long long zoff = (long long)kz * A.ny;
+#pragma unroll
+  for (int i = 0; i < PlaneRegs<T, BX, BY, DIM, VISC>::PF; ++i) {
+    const int t = threadIdx.x + i * G::NT;
+    if (t < G::CS) {
+      const int ly = t / G::PX;
+      const int lx = t - ly * G::PX;
+      const int gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
+      const int gy = DIM >= 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
+      const long long q = (zoff + gy) * A.nx + gx;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) r.v[i][c] = __ldg(A.Us + q + c * A.N);
+    }
+  }
+}
+
+// Convert fetched conservative values to primitives (+ temperature) and
+// store them into the plane at dst.
+template <typename T, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void commit_plane(const StageArgs<T>& A, const Gas<T>& g,
+                                             const PlaneRegs<T, BX, BY, DIM, VISC>& r, T* dst) {
+  using G = Geo<BX, BY, DIM, VISC>;
   bool bad = false;
-  for (int t = threadIdx.x; t < G::CS; t += G::NT) {
-    const int ly = t / G::PX;
-    const int lx = t - ly * G::PX;
-    const int gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
-    const int gy = DIM >= 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
-    const long long q = (zoff + gy) * A.nx + gx;
-    const T r = __ldg(A.Us + q);
-    const T mx = __ldg(A.Us + q + A.N);
-    const T my = __ldg(A.Us + q + 2 * A.N);
-    const T mz = __ldg(A.Us + q + 3 * A.N);
-    const T E = __ldg(A.Us + q + 4 * A.N);
-    const T inv = T(1) / r;
-    const T u = mx * inv, v = my * inv, w = mz * inv;
-    const T p = g.gm1 * (E - T(0.5) * r * (u * u + v * v + w * w));
-    bad |= !(r > T(0)) || !(p > T(0)) || !(p < T(INFINITY));
-    dst[t] = r;
-    dst[G::CS + t] = u;
-    dst[2 * G::CS + t] = v;
-    dst[3 * G::CS + t] = w;
-    dst[4 * G::CS + t] = p;
-    if (VISC) dst[5 * G::CS + t] = p * inv * g.inv_R;
+#pragma unroll
+  for (int i = 0; i < PlaneRegs<T, BX, BY, DIM, VISC>::PF; ++i) {
+    const int t = threadIdx.x + i * G::NT;
+    if (t < G::CS) {
+      const T rho = r.v[i][0];
+      const T inv = T(1) / rho;
+      const T u = r.v[i][1] * inv, v = r.v[i][2] * inv, w = r.v[i][3] * inv;
+      const T p = g.gm1 * (r.v[i][4] - T(0.5) * rho * (u * u + v * v + w * w));
+      bad |= !(rho > T(0)) || !(p > T(0)) || !(p < T(INFINITY));
+      dst[t] = rho;
+      dst[G::CS + t] = u;
+      dst[2 * G::CS + t] = v;
+      dst[3 * G::CS + t] = w;
+      dst[4 * G::CS + t] = p;
+      if (VISC) dst[5 * G::CS + t] = p * inv * g.inv_R;
+    }
   }
   if (bad) atomicOr(A.flag, 1);
+}
+
+template <typename T, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void load_plane(const StageArgs<T>& A, const Gas<T>& g, T* dst, int gx0, int gy0,
+                                           int gz) {
+  PlaneRegs<T, BX, BY, DIM, VISC> r;
+  fetch_plane<T, BX, BY, DIM, VISC>(A, r, gx0, gy0, gz);
+  commit_plane<T, BX, BY, DIM, VISC>(A, g, r, dst);
 }
 
 // Accessor of the ring: value of component c at plane offset e (-3..3),
@@ -157,8 +192,15 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
   for (int c = 0; c < 5; ++c) {
     const T v0 = val(c, -2, 0, 0), v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0);
     const T v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0), v5 = val(c, 3, 0, 0);
-    Wm[c] = weno5(v0, v1, v2, v3, v4, g.eps);
-    Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps);
+    if constexpr (sizeof(T) == 4) {
+      const float2 r = weno5_pair(make_float2(v0, v5), make_float2(v1, v4), make_float2(v2, v3), make_float2(v3, v2),
+                                  make_float2(v4, v1), g.eps);
+      Wm[c] = r.x;
+      Wp[c] = r.y;
+    } else {
+      Wm[c] = weno5(v0, v1, v2, v3, v4, g.eps);
+      Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps);
+    }
   }
   if (g.safe) {
     if (!(Wm[0] > T(0)) || !(Wm[4] > T(0))) {
@@ -290,6 +332,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   };
 
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
+  PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight during plane k
   if (DIM == 3) {
     for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
     __syncthreads();
@@ -298,19 +341,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     set_view(5);
     if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
     __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
+    load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, z0 + 3);
+    if (z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC>(A, next, gx0, gy0, z0 + 4);
+  } else {
+    load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, 0);
   }
+  __syncthreads();
 
-  int base = 0;  // slot of plane k - 3
+  int base = 0;  // slot of plane k - 3 (and of plane k + 3)
   for (int k = z0; k < z1; ++k) {
-    if (DIM == 3) {
-      // plane k + 3 goes to the slot of plane k - 3, dead since the previous
-      // plane's faces were finished (barrier)
-      load_plane<T, BX, BY, DIM, VISC>(A, g, ring + base * G::PLANE, gx0, gy0, k + 3);
-    } else {
-      load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, 0);
-    }
     set_view(base);
-    __syncthreads();
 
     if (xf_x >= 0) {
       T NF[5];
@@ -354,7 +394,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     if (DIM == 3) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) NFz_lo[c] = NFz_hi[c];
-      base = base + 1 == 6 ? 0 : base + 1;
+      const int nb = base + 1 == 6 ? 0 : base + 1;  // slot of plane k - 2, dead after this plane's faces
+      if (k + 1 < z1) {
+        commit_plane<T, BX, BY, DIM, VISC>(A, g, next, ring + nb * G::PLANE);  // plane k + 4
+        if (k + 2 < z1) fetch_plane<T, BX, BY, DIM, VISC>(A, next, gx0, gy0, k + 5);
+      }
+      __syncthreads();
+      base = nb;
     }
   }
 }
