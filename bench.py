@@ -72,6 +72,10 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=-1)
+    p.add_argument("--only", choices=["batched", "adjoint"], default=None,
+                   help="run only the batched or the adjoint measurement and print it")
+    p.add_argument("--adjoint-n", type=int, default=256)
+    p.add_argument("--adjoint-steps", type=int, default=400)
     return p.parse_args()
 
 
@@ -526,6 +530,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+
+        from paper_2203_13760_gb300 import _build
+        _build.build()
+        torch.cuda.set_device(0)
+        out = run_batched() if args.only == "batched" else run_adjoint(args.adjoint_n, args.adjoint_steps)
+        print(json.dumps({args.only: out}), flush=True)
+        return 0
     return run_jf(args)
 
 

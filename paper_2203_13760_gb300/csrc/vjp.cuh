@@ -113,16 +113,13 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
     vroles<D>(n, 0, x, y);
     return V.w(c, x0 + x, y0 + y);
   };
-  T v[5][6];
-#pragma unroll
-  for (int c = 0; c < 5; ++c)
-#pragma unroll
-    for (int q = 0; q < 6; ++q) v[c][q] = at(c, q - 2);
+  // forward face states (the stencil values are re-read from shared memory
+  // for the reverse WENO passes instead of being kept live across HLLC)
   T Wm[5], Wp[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    Wm[c] = weno5(v[c][0], v[c][1], v[c][2], v[c][3], v[c][4], g.eps);
-    Wp[c] = weno5(v[c][5], v[c][4], v[c][3], v[c][2], v[c][1], g.eps);
+    Wm[c] = weno5(at(c, -2), at(c, -1), at(c, 0), at(c, 1), at(c, 2), g.eps);
+    Wp[c] = weno5(at(c, 3), at(c, 2), at(c, 1), at(c, 0), at(c, -1), g.eps);
   }
   bool fm = false, fp = false;
   if (g.safe) {
@@ -130,8 +127,8 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
     fp = !(Wp[0] > T(0)) || !(Wp[4] > T(0));
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      if (fm) Wm[c] = v[c][2];
-      if (fp) Wp[c] = v[c][3];
+      if (fm) Wm[c] = at(c, 0);
+      if (fp) Wp[c] = at(c, 1);
     }
   }
   T Fb[5], Wmb[5], Wpb[5];
@@ -140,12 +137,15 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
   hllc_vjp<T, D>(Wm, Wp, g, Fb, Wmb, Wpb);
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
+    T v[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) v[q] = at(c, q - 2);
     T vb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     if (fm) {
       vb[2] += Wmb[c];
     } else {
       T t[5] = {T(0), T(0), T(0), T(0), T(0)};
-      weno5_vjp(v[c][0], v[c][1], v[c][2], v[c][3], v[c][4], g.eps, Wmb[c], t);
+      weno5_vjp(v[0], v[1], v[2], v[3], v[4], g.eps, Wmb[c], t);
 #pragma unroll
       for (int q = 0; q < 5; ++q) vb[q] += t[q];
     }
@@ -153,7 +153,7 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
       vb[3] += Wpb[c];
     } else {
       T t[5] = {T(0), T(0), T(0), T(0), T(0)};
-      weno5_vjp(v[c][5], v[c][4], v[c][3], v[c][2], v[c][1], g.eps, Wpb[c], t);
+      weno5_vjp(v[5], v[4], v[3], v[2], v[1], g.eps, Wpb[c], t);
 #pragma unroll
       for (int q = 0; q < 5; ++q) vb[5 - q] += t[q];
     }
@@ -277,7 +277,7 @@ __device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
 // The stage VJP kernel (DIM = 1 or 2).  blockDim.x == BX * BY,
 // grid = (ceil(nx/BX), ceil(ny/BY)).
 template <typename T, int DIM, bool VISC, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY) vjp_stage_kernel(const VjpArgs<T> A, const Gas<T> g) {
+__global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> A, const Gas<T> g) {
   using G = VGeo<BX, BY, DIM, VISC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Wb = reinterpret_cast<T*>(smem_raw);

@@ -126,3 +126,32 @@ def test_batch_rejects_mixed_dimensions():
     grids = [jf.make_grid((32, 32, 1)), jf.make_grid((32, 1, 1))]
     with pytest.raises(jf.JFError):
         jf.Batch(grids)
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    """The autotuner times every variant, selects the fastest, caches it,
+    and a new handle of the same configuration picks it from the cache."""
+    from paper_2203_13760_gb300 import autotune
+    cases = inputs.four_quadrant_batch(nsim=4, sides=(64, 128), seed=3)
+    b = batch_of(cases, "f32")
+    Us = fields(cases, "f32")
+    path = str(tmp_path / "tune.json")
+    rec = autotune.tune(b, Us, steps=2, reps=2, path=path)
+    assert set(rec["ms"]) == set(b.variants())
+    b2 = batch_of(cases, "f32")
+    assert autotune.apply(b2, path=path) == rec["variant"]
+    # the tuned batch still computes the same bits as the single-grid path
+    V = fields(cases, "f32")
+    b2.step(V, 2)
+    b2.sync()
+    for c, U in zip(cases, V):
+        s = jf.Solver.from_case(c, dtype="f32")
+        W = fields([c], "f32")[0]
+        s.run(W, 2)
+        s.sync()
+        assert torch.equal(U, W)
+    case = inputs.taylor_green(48)
+    s = jf.Solver.from_case(case, dtype="f32")
+    U = torch.tensor(case.U, dtype=torch.float32, device="cuda")
+    rec = autotune.tune(s, U, steps=2, reps=2, path=path)
+    assert rec["description"] == s.variants()[rec["variant"]]
