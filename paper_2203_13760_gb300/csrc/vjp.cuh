@@ -96,30 +96,32 @@ struct VTile {
   }
 };
 
-// Roles of the two in-plane axes for a face normal to D: offsets (along the
-// normal, along the tangent) -> tile (x, y).
-template <int D>
-__device__ __forceinline__ void vroles(int n, int t, int& x, int& y) {
-  if (D == 0) { x = n; y = t; } else { x = t; y = n; }
+// In-plane axis roles for a face normal to axis d (runtime): offsets (along
+// the normal, along the tangent) -> tile (x, y).
+__device__ __forceinline__ void vroles(int d, int n, int t, int& x, int& y) {
+  x = d == 0 ? n : t;
+  y = d == 0 ? t : n;
 }
 
 // Reverse pass of the convective flux of the face between tile cells
-// (x0, y0) and its neighbour along D; nu = dLoss/dNF (NF = -F + ...).
-template <typename T, int D, int DIM, bool VISC, int BX, int BY>
-__device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>& V, int x0, int y0, const T nu[5],
-                                              const Gas<T>& g) {
+// (x0, y0) and its neighbour along axis d; nu = dLoss/dNF (NF = -F + ...).
+// HLLC is evaluated in the face frame (normal velocity first), which is the
+// same function of the rotated state, so one instance serves both axes.
+template <typename T, int DIM, bool VISC, int BX, int BY>
+__device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>& V, int d, int x0, int y0,
+                                           const T nu[5], const Gas<T>& g) {
   auto at = [&](int c, int n) -> T {
     int x, y;
-    vroles<D>(n, 0, x, y);
+    vroles(d, n, 0, x, y);
     return V.w(c, x0 + x, y0 + y);
   };
-  // forward face states (the stencil values are re-read from shared memory
-  // for the reverse WENO passes instead of being kept live across HLLC)
+  const int cn = 1 + d, ct = 2 - d;  // normal / tangential velocity components (2D)
   T Wm[5], Wp[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    Wm[c] = weno5(at(c, -2), at(c, -1), at(c, 0), at(c, 1), at(c, 2), g.eps);
-    Wp[c] = weno5(at(c, 3), at(c, 2), at(c, 1), at(c, 0), at(c, -1), g.eps);
+    const int pc = c == 1 ? cn : (c == 2 ? ct : c);  // face-frame order
+    Wm[c] = weno5(at(pc, -2), at(pc, -1), at(pc, 0), at(pc, 1), at(pc, 2), g.eps);
+    Wp[c] = weno5(at(pc, 3), at(pc, 2), at(pc, 1), at(pc, 0), at(pc, -1), g.eps);
   }
   bool fm = false, fp = false;
   if (g.safe) {
@@ -127,149 +129,138 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
     fp = !(Wp[0] > T(0)) || !(Wp[4] > T(0));
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      if (fm) Wm[c] = at(c, 0);
-      if (fp) Wp[c] = at(c, 1);
+      const int pc = c == 1 ? cn : (c == 2 ? ct : c);
+      if (fm) Wm[c] = at(pc, 0);
+      if (fp) Wp[c] = at(pc, 1);
     }
   }
   T Fb[5], Wmb[5], Wpb[5];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) Fb[c] = -nu[c];
-  hllc_vjp<T, D>(Wm, Wp, g, Fb, Wmb, Wpb);
-#pragma unroll
+  Fb[0] = -nu[0];
+  Fb[1] = -(d == 0 ? nu[1] : nu[2]);
+  Fb[2] = -(d == 0 ? nu[2] : nu[1]);
+  Fb[3] = -nu[3];
+  Fb[4] = -nu[4];
+  hllc_vjp<T, 0>(Wm, Wp, g, Fb, Wmb, Wpb);
+#pragma unroll 1
   for (int c = 0; c < 5; ++c) {
+    const int pc = c == 1 ? cn : (c == 2 ? ct : c);
+    const T bm = c == 0 ? Wmb[0] : c == 1 ? Wmb[1] : c == 2 ? Wmb[2] : c == 3 ? Wmb[3] : Wmb[4];
+    const T bp = c == 0 ? Wpb[0] : c == 1 ? Wpb[1] : c == 2 ? Wpb[2] : c == 3 ? Wpb[3] : Wpb[4];
     T v[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) v[q] = at(c, q - 2);
+    for (int q = 0; q < 6; ++q) v[q] = at(pc, q - 2);
     T vb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     if (fm) {
-      vb[2] += Wmb[c];
+      vb[2] += bm;
     } else {
       T t[5] = {T(0), T(0), T(0), T(0), T(0)};
-      weno5_vjp(v[0], v[1], v[2], v[3], v[4], g.eps, Wmb[c], t);
+      weno5_vjp(v[0], v[1], v[2], v[3], v[4], g.eps, bm, t);
 #pragma unroll
       for (int q = 0; q < 5; ++q) vb[q] += t[q];
     }
     if (fp) {
-      vb[3] += Wpb[c];
+      vb[3] += bp;
     } else {
       T t[5] = {T(0), T(0), T(0), T(0), T(0)};
-      weno5_vjp(v[5], v[4], v[3], v[2], v[1], g.eps, Wpb[c], t);
+      weno5_vjp(v[5], v[4], v[3], v[2], v[1], g.eps, bp, t);
 #pragma unroll
       for (int q = 0; q < 5; ++q) vb[5 - q] += t[q];
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       int x, y;
-      vroles<D>(q - 2, 0, x, y);
-      V.add(c, x0 + x, y0 + y, vb[q]);
+      vroles(d, q - 2, 0, x, y);
+      V.add(pc, x0 + x, y0 + y, vb[q]);
     }
   }
 }
 
-// Reverse pass of the dissipative flux of the same face (NF = ... + F^d).
-// Forward (Sections 2, 3.4): G[a][D] = DF4(u_a), dT/dn = DF4(T) along the
-// normal; G[a][e] = RC4 over cells -1..2 of DC4_e(u_a) for a in {D, e};
-// face velocities RC4(u_a); tau_a = mu (G[D][a] + G[a][D]) - 2/3 mu div
-// delta_aD; F^d = [0, tau, u_f . tau + lambda dT/dn].
-template <typename T, int D, int DIM, bool VISC, int BX, int BY>
-__device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY>& V, int x0, int y0, const T nu[5],
-                                              const Gas<T>& g, const T inv_h[2]) {
-  constexpr int E = 1 - D;  // the tangential in-plane axis (2D)
+// Reverse pass of the dissipative flux of the same face (NF = ... + F^d),
+// in the face frame: n = normal axis d, t = the other in-plane axis, z = the
+// out-of-plane axis (no derivatives along it in 2D).  Forward (Sections 2,
+// 3.4): du_k/dn = DF4(u_k), dT/dn = DF4(T); du_n/dt and du_t/dt by DC4 at
+// the cells -1..2 along n, interpolated with RC4; face velocities RC4(u_k);
+// tau_n = mu (2 du_n/dn - 2/3 div), tau_t = mu (du_n/dt + du_t/dn),
+// tau_z = mu du_z/dn, div = du_n/dn + du_t/dt;
+// F^d = [0, tau, u_f . tau + lambda dT/dn] (tau_n in component 1 + d).
+template <typename T, int DIM, bool VISC, int BX, int BY>
+__device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY>& V, int d, int x0, int y0,
+                                           const T nu[5], const Gas<T>& g, const T inv_h[2]) {
   auto at = [&](int c, int n, int t) -> T {
     int x, y;
-    vroles<D>(n, t, x, y);
+    vroles(d, n, t, x, y);
     return V.w(c, x0 + x, y0 + y);
   };
   auto put = [&](int c, int n, int t, T val) {
     int x, y;
-    vroles<D>(n, t, x, y);
+    vroles(d, n, t, x, y);
     V.add(c, x0 + x, y0 + y, val);
   };
-  const T hn = inv_h[D];
+  const int cn = 1 + d, ct = 2 - d, cz = 3;
+  const T hn = d == 0 ? inv_h[0] : inv_h[1];
+  const T ht = d == 0 ? inv_h[1] : inv_h[0];
   const T df[4] = {T(1) / T(24), -T(27) / T(24), T(27) / T(24), -T(1) / T(24)};
   const T rc[4] = {-T(1) / T(16), T(9) / T(16), T(9) / T(16), -T(1) / T(16)};
   const T dcw[4] = {T(1) / T(12), -T(8) / T(12), T(8) / T(12), -T(1) / T(12)};
   const int dco[4] = {-2, -1, 1, 2};
   // ---- forward ----
-  T G[3][3];
+  T gn[3], uf[3];  // d u_k / dn and face velocities, k = n, t, z
+  const int comp[3] = {cn, ct, cz};
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) G[a][b] = T(0);
-  T uf[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
+  for (int k = 0; k < 3; ++k) {
     T s = T(0), f = T(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const T u = at(1 + a, q - 1, 0);
+      const T u = at(comp[k], q - 1, 0);
       s += df[q] * u;
       f += rc[q] * u;
     }
-    G[a][D] = s * hn;
-    uf[a] = f;
+    gn[k] = s * hn;
+    uf[k] = f;
   }
+  T gnt = T(0), gtt = T(0);  // d u_n / dt, d u_t / dt
   if (DIM >= 2) {
-    const T he = inv_h[E];
 #pragma unroll
-    for (int s2 = 0; s2 < 2; ++s2) {
-      const int a = s2 == 0 ? D : E;
+    for (int k = 0; k < 2; ++k) {
       T acc = T(0);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         T cen = T(0);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) cen += dcw[k] * at(1 + a, q - 1, dco[k]);
+        for (int j = 0; j < 4; ++j) cen += dcw[j] * at(comp[k], q - 1, dco[j]);
         acc += rc[q] * cen;
       }
-      G[a][E] = acc * he;
+      if (k == 0) gnt = acc * ht; else gtt = acc * ht;
     }
   }
-  const T div = G[0][0] + G[1][1] + G[2][2];
-  T tau[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) tau[a] = g.mu * (G[D][a] + G[a][D]);
-  tau[D] -= (T(2) / T(3)) * g.mu * div;
+  const T div = gn[0] + gtt;
+  const T tau[3] = {g.mu * (T(2) * gn[0]) - (T(2) / T(3)) * g.mu * div, g.mu * (gnt + gn[1]), g.mu * gn[2]};
   // ---- reverse ----
+  const T nun[3] = {nu[cn], nu[ct], nu[cz]};
   T taub[3], ufb[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    taub[a] = nu[1 + a] + nu[4] * uf[a];
-    ufb[a] = nu[4] * tau[a];
+  for (int k = 0; k < 3; ++k) {
+    taub[k] = nun[k] + nu[4] * uf[k];
+    ufb[k] = nu[4] * tau[k];
   }
   const T dTb = nu[4] * g.lambda;
-  T Gb[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) Gb[a][b] = T(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    Gb[D][a] += g.mu * taub[a];
-    Gb[a][D] += g.mu * taub[a];
-  }
-  const T divb = -(T(2) / T(3)) * g.mu * taub[D];
-  Gb[0][0] += divb;
-  Gb[1][1] += divb;
-  Gb[2][2] += divb;
-  // normal derivatives, face velocities, dT/dn
+  const T divb = -(T(2) / T(3)) * g.mu * taub[0];
+  const T gnb[3] = {T(2) * g.mu * taub[0] + divb, g.mu * taub[1], g.mu * taub[2]};
+  const T gntb = g.mu * taub[1], gttb = divb;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) put(1 + a, q - 1, 0, Gb[a][D] * hn * df[q] + ufb[a] * rc[q]);
+    for (int k = 0; k < 3; ++k) put(comp[k], q - 1, 0, gnb[k] * hn * df[q] + ufb[k] * rc[q]);
     put(5, q - 1, 0, dTb * hn * df[q]);
   }
-  // tangential derivatives
   if (DIM >= 2) {
-    const T he = inv_h[E];
 #pragma unroll
-    for (int s2 = 0; s2 < 2; ++s2) {
-      const int a = s2 == 0 ? D : E;
-      const T gb = Gb[a][E] * he;
+    for (int k = 0; k < 2; ++k) {
+      const T gb = (k == 0 ? gntb : gttb) * ht;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) put(1 + a, q - 1, dco[k], gb * rc[q] * dcw[k]);
+        for (int j = 0; j < 4; ++j) put(comp[k], q - 1, dco[j], gb * rc[q] * dcw[j]);
     }
   }
 }
@@ -334,7 +325,7 @@ __global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> 
       nu[c] = (V.m(c, x, y) - V.m(c, x + 1, y)) * inv_h[0];
       any |= nu[c] != T(0);
     }
-    if (any) conv_face_vjp<T, 0, DIM, VISC, BX, BY>(V, x, y, nu, g);
+    if (any) conv_face_vjp<T, DIM, VISC, BX, BY>(V, 0, x, y, nu, g);
   }
   if (DIM >= 2) {
     // convective faces along y: tile columns, lower cells y = -3 .. BY+1
@@ -347,7 +338,7 @@ __global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> 
         nu[c] = (V.m(c, x, y) - V.m(c, x, y + 1)) * inv_h[1];
         any |= nu[c] != T(0);
       }
-      if (any) conv_face_vjp<T, 1, DIM, VISC, BX, BY>(V, x, y, nu, g);
+      if (any) conv_face_vjp<T, DIM, VISC, BX, BY>(V, 1, x, y, nu, g);
     }
   }
   if (VISC) {
@@ -363,7 +354,7 @@ __global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> 
         nu[c] = (V.m(c, x, y) - V.m(c, x + 1, y)) * inv_h[0];
         any |= nu[c] != T(0);
       }
-      if (any) visc_face_vjp<T, 0, DIM, VISC, BX, BY>(V, x, y, nu, g, inv_h);
+      if (any) visc_face_vjp<T, DIM, VISC, BX, BY>(V, 0, x, y, nu, g, inv_h);
     }
     if (DIM >= 2) {
       // dissipative faces along y: columns -2 .. BX+1, lower cells -2 .. BY
@@ -377,7 +368,7 @@ __global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> 
           nu[c] = (V.m(c, x, y) - V.m(c, x, y + 1)) * inv_h[1];
           any |= nu[c] != T(0);
         }
-        if (any) visc_face_vjp<T, 1, DIM, VISC, BX, BY>(V, x, y, nu, g, inv_h);
+        if (any) visc_face_vjp<T, DIM, VISC, BX, BY>(V, 1, x, y, nu, g, inv_h);
       }
     }
   }
