@@ -13,35 +13,12 @@
 #include <cstring>
 #include <vector>
 
+#include "cfl.cuh"
 #include "jf_internal.h"
 
 namespace jf {
 
 constexpr long long kChunk = 16384;  // cells per CFL CTA
-
-struct CflChunk {
-  int sim;
-  int nchunks;   // chunks of this simulation
-  long long begin, end;
-};
-
-template <typename T>
-__global__ void __launch_bounds__(256) batch_cfl_kernel(const SimDesc<T>* __restrict__ sims,
-                                                        const CflChunk* __restrict__ chunks,
-                                                        const CflArgs* __restrict__ args, ReduceScratch* red,
-                                                        double* dt, int* flag) {
-  const CflChunk ch = chunks[blockIdx.x];
-  const CflArgs a = args[ch.sim];
-  const T* U = sims[ch.sim].U;
-  T conv = T(0), diff = T(0);
-  const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
-  bool bad = false;
-  for (long long q = ch.begin + threadIdx.x; q < ch.end; q += blockDim.x)
-    cell_rates(U, q, a.N, a.nactive, gamma, gm1, kdiff, conv, diff, bad);
-  if (bad) atomicOr(flag, 1);
-  finish_cfl((double)conv, (double)diff, red + ch.sim, (unsigned int)ch.nchunks, a.hmin, a.cfl, dt + ch.sim,
-             nullptr);
-}
 
 namespace {
 
@@ -179,9 +156,8 @@ jf_status enqueue_steps(jf_ctx* h, int nsteps, double* dt_out, cudaStream_t s) {
   const SimDesc<T>* sims = reinterpret_cast<const SimDesc<T>*>(h->d_sims);
   const WorkItem* work = static_cast<const WorkItem*>(h->d_work);
   for (int step = 0; step < nsteps; ++step) {
-    batch_cfl_kernel<T><<<h->nchunks, 256, 0, s>>>(sims, static_cast<const CflChunk*>(h->d_chunks),
-                                                   static_cast<const CflArgs*>(h->d_cfl), h->d_red, h->d_dt, h->flag);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_cfl_batch<T>(sims, h->d_chunks, h->nchunks, static_cast<const CflArgs*>(h->d_cfl),
+                                        h->d_red, h->d_dt, h->flag, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "batch: cfl launch");
     for (int stage = 1; stage <= 3; ++stage) {
       e = sv.launch_batch(sims, work, h->nwork, stage, g, h->flag, h->batch_blocks, s);

@@ -1,0 +1,63 @@
+// The CFL reduction kernel (Section 3.2) for single grids and batches.
+//
+// Single grid (chunks == null): grid-stride over the cells of U, the last CTA
+// (ticket) forms dt.  Batch (chunks != null): each CTA reduces one chunk of
+// one simulation; the last chunk of a simulation forms that simulation's dt.
+// Both forms run the same per-cell and reduction code, so a simulation's dt
+// in a batch is bitwise the dt of the simulation run alone.
+#pragma once
+#include "reduce.cuh"
+#include "stage.cuh"
+
+namespace jf {
+
+struct CflChunk {
+  int sim;
+  int nchunks;   // chunks of this simulation
+  long long begin, end;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U0, CflArgs a0, ReduceScratch* sc0,
+                                                  double* dt0, double* dt0b, int* flag,
+                                                  const SimDesc<T>* __restrict__ sims,
+                                                  const CflChunk* __restrict__ chunks,
+                                                  const CflArgs* __restrict__ args, ReduceScratch* red,
+                                                  double* dts) {
+  const T* U;
+  CflArgs a;
+  ReduceScratch* sc;
+  double *dto, *dto2;
+  long long q0, end, stride;
+  unsigned int nblocks;
+  if (chunks) {
+    const CflChunk ch = chunks[blockIdx.x];
+    a = args[ch.sim];
+    U = sims[ch.sim].U;
+    sc = red + ch.sim;
+    dto = dts + ch.sim;
+    dto2 = nullptr;
+    q0 = ch.begin + threadIdx.x;
+    end = ch.end;
+    stride = blockDim.x;
+    nblocks = (unsigned int)ch.nchunks;
+  } else {
+    a = a0;
+    U = U0;
+    sc = sc0;
+    dto = dt0;
+    dto2 = dt0b;
+    q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    end = a.N;
+    stride = (long long)gridDim.x * blockDim.x;
+    nblocks = gridDim.x;
+  }
+  T conv = T(0), diff = T(0);
+  const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
+  bool bad = false;
+  for (long long q = q0; q < end; q += stride) cell_rates(U, q, a.N, a.nactive, gamma, gm1, kdiff, conv, diff, bad);
+  if (bad) atomicOr(flag, 1);
+  finish_cfl((double)conv, (double)diff, sc, nblocks, a.hmin, a.cfl, dto, dto2);
+}
+
+}  // namespace jf

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/jf.h"
+#include "cfl.cuh"
 #include "jf_internal.h"
 
 namespace jf {
@@ -207,12 +208,27 @@ jf_status rhs_impl(jf_ctx* h, const void* U, void* dUdt, cudaStream_t s) {
 template <typename T>
 jf_status cfl_impl(jf_ctx* h, const void* U, double* dt_out, double* dt_out2, cudaStream_t s) {
   const CflArgs a = make_cfl(h->grid, h->gas, h->scheme);
-  cfl_kernel<T><<<reduce_blocks(a.N, h->sms), 256, 0, s>>>(static_cast<const T*>(U), a, h->red_cfl, dt_out,
-                                                            dt_out2, h->flag);
+  cfl_kernel<T><<<reduce_blocks(a.N, h->sms), 256, 0, s>>>(static_cast<const T*>(U), a, h->red_cfl, dt_out, dt_out2,
+                                                            h->flag, nullptr, nullptr, nullptr, nullptr, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "cfl kernel launch");
   return JF_OK;
 }
+
+// Per-simulation CFL of a batch (same kernel as the single-grid reduction).
+template <typename T>
+cudaError_t launch_cfl_batch(const void* sims, const void* chunks, int nchunks, const CflArgs* args,
+                             ReduceScratch* red, double* dts, int* flag, cudaStream_t s) {
+  CflArgs none{};
+  cfl_kernel<T><<<nchunks, 256, 0, s>>>(nullptr, none, nullptr, nullptr, nullptr, flag,
+                                        static_cast<const SimDesc<T>*>(sims), static_cast<const CflChunk*>(chunks),
+                                        args, red, dts);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cfl_batch<float>(const void*, const void*, int, const CflArgs*, ReduceScratch*, double*,
+                                             int*, cudaStream_t);
+template cudaError_t launch_cfl_batch<double>(const void*, const void*, int, const CflArgs*, ReduceScratch*, double*,
+                                              int*, cudaStream_t);
 
 // One RK3 step: optional CFL reduction, then the three Shu-Osher stages.
 template <typename T>

@@ -91,6 +91,11 @@ template <typename T> jf_status launch(jf_ctx* h, const StageArgs<T>& A, cudaStr
 template <typename T> jf_status select_variant(jf_ctx* h, int v, bool prepare);
 template <typename T> jf_status step_impl(jf_ctx* h, void* U, const double* dt_dev, double* dt_used, cudaStream_t s);
 
+// per-simulation CFL of a batch (jf_api.cu; the single CFL kernel)
+template <typename T>
+cudaError_t launch_cfl_batch(const void* sims, const void* chunks, int nchunks, const CflArgs* args,
+                             ReduceScratch* red, double* dts, int* flag, cudaStream_t s);
+
 // workspace shared by every handle kind: flag, dt scalar, reduction scratch, capture stream
 jf_status alloc_common(jf_ctx* h);
 void release_all(jf_ctx* h);

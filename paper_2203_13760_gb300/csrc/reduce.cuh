@@ -106,21 +106,6 @@ __device__ __forceinline__ void finish_cfl(double conv, double diff, ReduceScrat
   }
 }
 
-// dt = CFL min(dt_c, dt_v): dt_c = hmin / max(|u_d| + c), dt_v = 3/14 hmin^2 / max(kdiff / rho).
-// Writes dt to dt_out and, if non-null, dt_out2.  blockDim.x == 256.
-template <typename T>
-__global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U, CflArgs a, ReduceScratch* sc,
-                                                  double* dt_out, double* dt_out2, int* flag) {
-  T conv = T(0), diff = T(0);
-  const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
-  bool bad = false;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.N; q += stride)
-    cell_rates(U, q, a.N, a.nactive, gamma, gm1, kdiff, conv, diff, bad);
-  if (bad) atomicOr(flag, 1);
-  finish_cfl((double)conv, (double)diff, sc, gridDim.x, a.hmin, a.cfl, dt_out, dt_out2);
-}
-
 // loss = sum_cells (rho - target)^2 * dV; seed = d loss / dU (density
 // component only).  blockDim.x == 256.
 template <typename T>

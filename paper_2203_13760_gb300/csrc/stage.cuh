@@ -351,6 +351,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   int base = 0;  // slot of plane k - 3 (and of plane k + 3)
   for (int k = z0; k < z1; ++k) {
     set_view(base);
+    // this cell's U_s and U^n for the stage combination, loaded now so that
+    // their latency overlaps with the face computations
+    const long long qc = ((long long)(DIM == 3 ? k : 0) * A.ny + gy) * A.nx + gx;
+    T us[5], un[5];
+    if (own && !A.rhs_only) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        us[c] = __ldg(A.Us + qc + c * A.N);
+        un[c] = A.Un ? A.Un[qc + c * A.N] : T(0);
+      }
+    }
 
     if (xf_x >= 0) {
       T NF[5];
@@ -371,7 +382,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     __syncthreads();
 
     if (own) {
-      const long long q = ((long long)(DIM == 3 ? k : 0) * A.ny + gy) * A.nx + gx;
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         const int fx = ty * (BX + 1) + tx;
@@ -385,10 +395,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         if (A.rhs_only) {
           o = rhs;
         } else {
-          o = A.b * (__ldg(A.Us + q + c * A.N) + dt * rhs);
-          if (A.Un) o += A.a * A.Un[q + c * A.N];
+          o = A.b * (us[c] + dt * rhs);
+          if (A.Un) o += A.a * un[c];
         }
-        A.out[q + c * A.N] = o;
+        A.out[qc + c * A.N] = o;
       }
     }
     if (DIM == 3) {
@@ -403,15 +413,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       base = nb;
     }
   }
-}
-
-// The stage kernel: one CTA per tile.  blockDim.x == Geo::NT,
-// grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/zchunk)) (3D), (.., .., 1) otherwise.
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
-__global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
-    stage_kernel(const StageArgs<T> A, const Gas<T> g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_tile<T, DIM, VISC, BX, BY>(A, g, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<T*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -434,40 +435,54 @@ struct WorkItem {
   int bx, by;
 };
 
-// stage 1: U1 = U + dt L(U); stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1));
-// stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2)).  CTAs loop over the work list
-// (static round robin: every item is one full tile of equal cost).
+// The stage kernel.  blockDim.x == Geo::NT.
+//  * Single grid (work == null): one CTA per tile, the tile from blockIdx;
+//    grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/zchunk)) (3D), (.., .., 1) otherwise.
+//  * Batch (work != null): persistent CTAs loop over the (simulation, tile)
+//    work list in a static round robin (every item is one full tile of
+//    equal cost); the grid arguments come from the simulation's descriptor,
+//    stage 1: U1 = U + dt L(U); stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+//    stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2)).
+// Both forms reach the tile computation through the same call below, so a
+// simulation advanced in a batch is bitwise the one advanced alone.
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
-    batch_stage_kernel(const SimDesc<T>* __restrict__ sims, const WorkItem* __restrict__ work, int nwork,
-                       int stage, const Gas<T> g, int* flag) {
+    stage_kernel(const StageArgs<T> A0, const SimDesc<T>* __restrict__ sims, const WorkItem* __restrict__ work,
+                 int nwork, int stage, const Gas<T> g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
-    const WorkItem w = work[item];
-    const SimDesc<T> d = sims[w.sim];
-    StageArgs<T> A;
-    A.nx = d.nx;
-    A.ny = d.ny;
-    A.nz = d.nz;
-    A.N = d.N;
-    A.periodic[0] = d.periodic[0];
-    A.periodic[1] = d.periodic[1];
-    A.periodic[2] = d.periodic[2];
-    A.inv_h[0] = d.inv_h[0];
-    A.inv_h[1] = d.inv_h[1];
-    A.inv_h[2] = d.inv_h[2];
-    A.dt = d.dt;
-    A.rhs_only = 0;
-    A.zchunk = d.nz;
-    A.flag = flag;
-    if (stage == 1) {
-      A.Us = d.U; A.Un = nullptr; A.out = d.U1; A.a = T(0); A.b = T(1);
-    } else if (stage == 2) {
-      A.Us = d.U1; A.Un = d.U; A.out = d.U2; A.a = T(0.75); A.b = T(0.25);
-    } else {
-      A.Us = d.U2; A.Un = d.U; A.out = d.U; A.a = T(1.0 / 3.0); A.b = T(2.0 / 3.0);
+  for (int item = blockIdx.x;; item += gridDim.x) {
+    StageArgs<T> A = A0;
+    int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (work) {
+      if (item >= nwork) break;
+      const WorkItem w = work[item];
+      const SimDesc<T> d = sims[w.sim];
+      A.nx = d.nx;
+      A.ny = d.ny;
+      A.nz = d.nz;
+      A.N = d.N;
+      A.periodic[0] = d.periodic[0];
+      A.periodic[1] = d.periodic[1];
+      A.periodic[2] = d.periodic[2];
+      A.inv_h[0] = d.inv_h[0];
+      A.inv_h[1] = d.inv_h[1];
+      A.inv_h[2] = d.inv_h[2];
+      A.dt = d.dt;
+      A.rhs_only = 0;
+      A.zchunk = d.nz;
+      const T third = T(1.0 / 3.0), two_thirds = T(2.0 / 3.0);
+      A.Us = stage == 1 ? d.U : (stage == 2 ? d.U1 : d.U2);
+      A.Un = stage == 1 ? nullptr : d.U;
+      A.out = stage == 1 ? d.U1 : (stage == 2 ? d.U2 : d.U);
+      A.a = stage == 1 ? T(0) : (stage == 2 ? T(0.75) : third);
+      A.b = stage == 1 ? T(1) : (stage == 2 ? T(0.25) : two_thirds);
+      bx = w.bx;
+      by = w.by;
+      bz = 0;
+    } else if (item != (int)blockIdx.x) {
+      break;
     }
-    stage_tile<T, DIM, VISC, BX, BY>(A, g, w.bx, w.by, 0, reinterpret_cast<T*>(smem_raw));
+    stage_tile<T, DIM, VISC, BX, BY>(A, g, bx, by, bz, reinterpret_cast<T*>(smem_raw));
   }
 }
 
