@@ -191,13 +191,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest value over the ranks (the job's time is its slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world, cells_per_rank, steps, max_ms):
+    """Whole-job cell-updates/s: every rank advances its own replica (weak
+    scaling), the job takes as long as its slowest rank."""
+    return world * cells_per_rank * steps / (max_ms * 1e-3)
 
 
 def cpu_baseline(workload, budget_s=15.0, threads=None):
@@ -321,7 +329,7 @@ def run_jf(args):
     stage_ms = [e[i].elapsed_time(e[i + 1]) for e in events for i in (1, 2, 3)]
     total_ms = max_over_ranks(total_ms, world)
     ms_per_step = total_ms / K
-    value = world * N * K / (total_ms * 1e-3)
+    value = job_value(world, N, K, total_ms)
 
     # roofline of the dominant kernel (the stage kernel)
     peaks, peak_kind = measured_peaks()
