@@ -19,7 +19,7 @@ jf_status vjp_impl(jf_ctx* h, const void* Un, const double* dt, const void* lam_
                    cudaStream_t s) {
   const bool visc = dissipative(h->gas, h->scheme);
   VjpLaunch<T> L = vjp_launcher<T>(h->dim, visc);
-  if (!L) { set_error(h, "jf_rk3_step_vjp: the adjoint is built for 1D and 2D grids"); return JF_ERR_UNSUPPORTED; }
+  if (!L) { set_error(h, "jf_rk3_step_vjp: no adjoint kernel for this configuration"); return JF_ERR_UNSUPPORTED; }
   for (int i = 0; i < 2; ++i)
     if (!h->adj[i]) {
       cudaError_t e = cudaMalloc(&h->adj[i], 5 * h->N * sizeof(T));
@@ -40,13 +40,14 @@ jf_status vjp_impl(jf_ctx* h, const void* Un, const double* dt, const void* lam_
   if ((st = launch<T>(h, A, s)) != JF_OK) return st;
   // backward
   VjpArgs<T> V;
-  V.nx = h->grid.nx;
-  V.ny = h->grid.ny;
+  V.n[0] = h->grid.nx;
+  V.n[1] = h->grid.ny;
+  V.n[2] = h->grid.nz;
   V.N = (long long)h->N;
-  V.periodic[0] = h->grid.bc[0] == JF_BC_PERIODIC;
-  V.periodic[1] = h->grid.bc[2] == JF_BC_PERIODIC;
-  V.inv_h[0] = (T)(1.0 / spacing(h->grid, 0));
-  V.inv_h[1] = (T)(1.0 / spacing(h->grid, 1));
+  for (int a = 0; a < 3; ++a) {
+    V.periodic[a] = h->grid.bc[2 * a] == JF_BC_PERIODIC;
+    V.inv_h[a] = (T)(1.0 / spacing(h->grid, a));
+  }
   V.dt = dt;
   V.flag = h->flag;
   const Gas<T> g = make_gas<T>(h->gas, h->scheme);

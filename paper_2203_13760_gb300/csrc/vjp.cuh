@@ -1,5 +1,5 @@
 // Adjoint (vector-Jacobian product) of one Shu-Osher stage (Sections 3.1-3.4,
-// Section 7.2).
+// Section 7.2), for 1D, 2D and 3D grids.
 //
 // One launch computes, for every interior cell,
 //   out = a1 x1 + a2 x2 + m + dt J(Us)^T m,   m = s_in lam,
@@ -15,16 +15,21 @@
 // its stencil cells; the cell then applies the transposed Jacobian of
 // W(U) (and of T = p / (rho R)).
 //
-// Tiling.  A CTA owns a BX x BY tile of cells.  It stages the primitives of a
-// 5-cell halo around the tile (WENO5 of a face 3 cells outside the tile reads
-// 2 more) and m with a 3-cell halo, evaluates the reverse pass of every face
-// whose stencil touches a tile cell, and accumulates the resulting cotangents
-// of tile cells in shared memory (shared-memory atomics: the summation order,
-// and so the last bits, may vary from run to run).  Ghost cells follow the
-// boundary condition: with zero gradient a ghost has no right-hand side
-// (m = 0) and its cotangent goes to the interior cell it copies; with periodic
-// wrap every ghost face is a real face that the owning tile also evaluates,
-// so only cotangents of the tile's own cells are kept.
+// Tiling.  A CTA owns a BX x BY x BZ box of cells.  It stages the primitives of
+// a 5-cell halo around the box on every active axis (WENO5 of a face 3 cells
+// outside reads 2 more) and m with a 3-cell halo, evaluates the reverse pass
+// of every face whose stencil touches a cell of the box, and accumulates the
+// resulting cotangents of box cells in shared memory (shared-memory atomics:
+// the summation order, and so the last bits, may vary from run to run).
+// Ghost cells follow the boundary condition: with zero gradient a ghost has
+// no right-hand side (m = 0) and its cotangent goes to the interior cell it
+// copies; with periodic wrap every ghost face is a real face that the owning
+// box also evaluates, so only cotangents of the box's own cells are kept.
+//
+// Faces are handled in their own frame (normal axis d, tangential axes t1,
+// t2): HLLC of the rotated state (normal velocity first) and the viscous
+// stress in face coordinates, so one instance of each reverse pass serves
+// every axis.
 #pragma once
 #include "stage.cuh"
 #include "vjp_math.cuh"
@@ -40,86 +45,99 @@ struct VjpArgs {
   T* out;
   const double* dt;
   T s_in, a1, a2;
-  int nx, ny;
+  int n[3];
   long long N;
-  int periodic[2];
-  T inv_h[2];
+  int periodic[3];
+  T inv_h[3];
   int* flag;
 };
 
-template <int BX, int BY, int DIM, bool VISC>
+template <int BX, int BY, int BZ, int DIM, bool VISC>
 struct VGeo {
-  static constexpr int H = 5;                         // W halo
-  static constexpr int HY = DIM >= 2 ? H : 0;
-  static constexpr int PX = BX + 2 * H, PY = BY + 2 * HY, CS = PX * PY;
+  static constexpr int HX = 5, HY = DIM >= 2 ? 5 : 0, HZ = DIM == 3 ? 5 : 0;  // W halo
+  static constexpr int PX = BX + 2 * HX, PY = BY + 2 * HY, PZ = BZ + 2 * HZ, CS = PX * PY * PZ;
   static constexpr int NCW = VISC ? 6 : 5;
-  static constexpr int MH = 3;                        // m halo
-  static constexpr int MHY = DIM >= 2 ? MH : 0;
-  static constexpr int MPX = BX + 2 * MH, MPY = BY + 2 * MHY, MCS = MPX * MPY;
-  static constexpr int NCELL = BX * BY;
-  static constexpr int NT = BX * BY;
-  static constexpr int VR = DIM >= 2 ? 2 : 0;         // viscous faces reach 2 rows beyond the tile
+  static constexpr int MX = 3, MY = DIM >= 2 ? 3 : 0, MZ = DIM == 3 ? 3 : 0;  // m halo
+  static constexpr int MPX = BX + 2 * MX, MPY = BY + 2 * MY, MPZ = BZ + 2 * MZ, MCS = MPX * MPY * MPZ;
+  static constexpr int NCELL = BX * BY * BZ;
+  static constexpr int NT = NCELL;
+  static_assert(DIM >= 2 || BY == 1, "1D boxes are one row");
+  static_assert(DIM == 3 || BZ == 1, "1D/2D boxes are one plane");
 };
 
-template <typename T, int DIM, bool VISC, int BX, int BY>
+template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
 constexpr size_t vjp_smem_bytes() {
-  using G = VGeo<BX, BY, DIM, VISC>;
+  using G = VGeo<BX, BY, BZ, DIM, VISC>;
   return sizeof(T) * (size_t)(G::NCW * G::CS + 5 * G::MCS + 6 * G::NCELL);
 }
 
-// Shared-memory views and the boundary-aware accumulator of one tile.
-template <typename T, int DIM, bool VISC, int BX, int BY>
-struct VTile {
-  using G = VGeo<BX, BY, DIM, VISC>;
-  const T* W;   // [NCW][PY][PX], tile cell (0, 0) at (H, HY)
-  const T* M;   // [5][MPY][MPX], tile cell (0, 0) at (MH, MHY)
-  T* acc;       // [6][BY][BX]
-  int gx0, gy0, nx, ny, px, py;
-
-  __device__ __forceinline__ T w(int c, int x, int y) const { return W[c * G::CS + (y + G::HY) * G::PX + x + G::H]; }
-  __device__ __forceinline__ T m(int c, int x, int y) const {
-    return M[c * G::MCS + (y + G::MHY) * G::MPX + x + G::MH];
-  }
-  // target tile column of tile-relative column x, or -1 if the cotangent is
-  // not this tile's to keep
-  __device__ __forceinline__ int owner(int x, int x0, int n, int periodic, int B) const {
-    const int gxx = x0 + x;
-    if (periodic) return (x >= 0 && x < B && gxx < n) ? x : -1;
-    const int c = gxx < 0 ? 0 : (gxx >= n ? n - 1 : gxx);
-    const int t = c - x0;
-    return (t >= 0 && t < B) ? t : -1;
-  }
-  __device__ __forceinline__ void add(int c, int x, int y, T v) const {
-    const int tx = owner(x, gx0, nx, px, BX);
-    const int ty = DIM >= 2 ? owner(y, gy0, ny, py, BY) : 0;
-    if (tx >= 0 && ty >= 0) atomicAdd(acc + (c * BY + ty) * BX + tx, v);
+// Position along the axes of a face frame: offset n along the normal d, a
+// along t1, b along t2, for axis `axis` of (x, y, z).
+struct Frame {
+  int d, t1, t2;
+  __device__ __forceinline__ int pick(int axis, int n, int a, int b) const {
+    return axis == d ? n : (axis == t1 ? a : b);
   }
 };
 
-// In-plane axis roles for a face normal to axis d (runtime): offsets (along
-// the normal, along the tangent) -> tile (x, y).
-__device__ __forceinline__ void vroles(int d, int n, int t, int& x, int& y) {
-  x = d == 0 ? n : t;
-  y = d == 0 ? t : n;
+// Shared-memory views and the boundary-aware accumulator of one box.
+template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
+struct VTile {
+  using G = VGeo<BX, BY, BZ, DIM, VISC>;
+  const T* W;   // [NCW][PZ][PY][PX], box cell (0, 0, 0) at (HX, HY, HZ)
+  const T* M;   // [5][MPZ][MPY][MPX]
+  T* acc;       // [6][BZ][BY][BX]
+  int g0[3], n[3], per[3];
+
+  // coordinates along inactive axes are always 0: fold them at compile time
+  __device__ __forceinline__ T w(int c, int x, int y, int z) const {
+    const int yy = DIM >= 2 ? y : 0, zz = DIM == 3 ? z : 0;
+    return W[c * G::CS + ((zz + G::HZ) * G::PY + (yy + G::HY)) * G::PX + x + G::HX];
+  }
+  __device__ __forceinline__ T m(int c, int x, int y, int z) const {
+    const int yy = DIM >= 2 ? y : 0, zz = DIM == 3 ? z : 0;
+    return M[c * G::MCS + ((zz + G::MZ) * G::MPY + (yy + G::MY)) * G::MPX + x + G::MX];
+  }
+  // box coordinate that keeps a cotangent landing on box-relative coordinate
+  // x along an axis, or -1 if it is not this box's to keep
+  __device__ __forceinline__ int owner(int x, int x0, int nn, int periodic, int B) const {
+    const int gxx = x0 + x;
+    if (periodic) return (x >= 0 && x < B && gxx < nn) ? x : -1;
+    const int c = gxx < 0 ? 0 : (gxx >= nn ? nn - 1 : gxx);
+    const int t = c - x0;
+    return (t >= 0 && t < B) ? t : -1;
+  }
+  __device__ __forceinline__ void add(int c, int x, int y, int z, T v) const {
+    const int tx = owner(x, g0[0], n[0], per[0], BX);
+    const int ty = DIM >= 2 ? owner(y, g0[1], n[1], per[1], BY) : 0;
+    const int tz = DIM == 3 ? owner(z, g0[2], n[2], per[2], BZ) : 0;
+    if (tx >= 0 && ty >= 0 && tz >= 0) atomicAdd(acc + ((c * BZ + tz) * BY + ty) * BX + tx, v);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T sel3(const T v[5], int i) {  // v[i], i in 1..3, without dynamic indexing
+  return i == 1 ? v[1] : (i == 2 ? v[2] : v[3]);
+}
+template <typename T>
+__device__ __forceinline__ T sel5(const T v[5], int i) {
+  return i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : i == 3 ? v[3] : v[4];
 }
 
-// Reverse pass of the convective flux of the face between tile cells
-// (x0, y0) and its neighbour along axis d; nu = dLoss/dNF (NF = -F + ...).
-// HLLC is evaluated in the face frame (normal velocity first), which is the
-// same function of the rotated state, so one instance serves both axes.
-template <typename T, int DIM, bool VISC, int BX, int BY>
-__device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>& V, int d, int x0, int y0,
-                                           const T nu[5], const Gas<T>& g) {
-  auto at = [&](int c, int n) -> T {
-    int x, y;
-    vroles(d, n, 0, x, y);
-    return V.w(c, x0 + x, y0 + y);
+// Reverse pass of the convective flux of the face between box cell p and its
+// neighbour along F.d; nu = dLoss/dNF (NF = -F + ...).
+template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
+__device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY, BZ>& V, const Frame& F,
+                                              const int p[3], const T nu[5], const Gas<T>& g) {
+  auto at = [&](int c, int s) -> T {
+    return V.w(c, p[0] + F.pick(0, s, 0, 0), p[1] + F.pick(1, s, 0, 0), p[2] + F.pick(2, s, 0, 0));
   };
-  const int cn = 1 + d, ct = 2 - d;  // normal / tangential velocity components (2D)
+  const int cn = 1 + F.d, c1 = 1 + F.t1, c2 = 1 + F.t2;  // physical components of the frame velocities
+  auto phys = [&](int c) { return c == 1 ? cn : (c == 2 ? c1 : (c == 3 ? c2 : c)); };
   T Wm[5], Wp[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    const int pc = c == 1 ? cn : (c == 2 ? ct : c);  // face-frame order
+    const int pc = phys(c);
     Wm[c] = weno5(at(pc, -2), at(pc, -1), at(pc, 0), at(pc, 1), at(pc, 2), g.eps);
     Wp[c] = weno5(at(pc, 3), at(pc, 2), at(pc, 1), at(pc, 0), at(pc, -1), g.eps);
   }
@@ -129,23 +147,21 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
     fp = !(Wp[0] > T(0)) || !(Wp[4] > T(0));
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const int pc = c == 1 ? cn : (c == 2 ? ct : c);
-      if (fm) Wm[c] = at(pc, 0);
-      if (fp) Wp[c] = at(pc, 1);
+      if (fm) Wm[c] = at(phys(c), 0);
+      if (fp) Wp[c] = at(phys(c), 1);
     }
   }
   T Fb[5], Wmb[5], Wpb[5];
   Fb[0] = -nu[0];
-  Fb[1] = -(d == 0 ? nu[1] : nu[2]);
-  Fb[2] = -(d == 0 ? nu[2] : nu[1]);
-  Fb[3] = -nu[3];
+  Fb[1] = -sel3(nu, cn);
+  Fb[2] = -sel3(nu, c1);
+  Fb[3] = -sel3(nu, c2);
   Fb[4] = -nu[4];
   hllc_vjp<T, 0>(Wm, Wp, g, Fb, Wmb, Wpb);
 #pragma unroll 1
   for (int c = 0; c < 5; ++c) {
-    const int pc = c == 1 ? cn : (c == 2 ? ct : c);
-    const T bm = c == 0 ? Wmb[0] : c == 1 ? Wmb[1] : c == 2 ? Wmb[2] : c == 3 ? Wmb[3] : Wmb[4];
-    const T bp = c == 0 ? Wpb[0] : c == 1 ? Wpb[1] : c == 2 ? Wpb[2] : c == 3 ? Wpb[3] : Wpb[4];
+    const int pc = phys(c);
+    const T bm = sel5(Wmb, c), bp = sel5(Wpb, c);
     T v[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) v[q] = at(pc, q - 2);
@@ -167,76 +183,76 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
       for (int q = 0; q < 5; ++q) vb[5 - q] += t[q];
     }
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      int x, y;
-      vroles(d, q - 2, 0, x, y);
-      V.add(pc, x0 + x, y0 + y, vb[q]);
-    }
+    for (int q = 0; q < 6; ++q)
+      V.add(pc, p[0] + F.pick(0, q - 2, 0, 0), p[1] + F.pick(1, q - 2, 0, 0), p[2] + F.pick(2, q - 2, 0, 0), vb[q]);
   }
 }
 
-// Reverse pass of the dissipative flux of the same face (NF = ... + F^d),
-// in the face frame: n = normal axis d, t = the other in-plane axis, z = the
-// out-of-plane axis (no derivatives along it in 2D).  Forward (Sections 2,
-// 3.4): du_k/dn = DF4(u_k), dT/dn = DF4(T); du_n/dt and du_t/dt by DC4 at
-// the cells -1..2 along n, interpolated with RC4; face velocities RC4(u_k);
-// tau_n = mu (2 du_n/dn - 2/3 div), tau_t = mu (du_n/dt + du_t/dn),
-// tau_z = mu du_z/dn, div = du_n/dn + du_t/dt;
-// F^d = [0, tau, u_f . tau + lambda dT/dn] (tau_n in component 1 + d).
-template <typename T, int DIM, bool VISC, int BX, int BY>
-__device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY>& V, int d, int x0, int y0,
-                                           const T nu[5], const Gas<T>& g, const T inv_h[2]) {
-  auto at = [&](int c, int n, int t) -> T {
-    int x, y;
-    vroles(d, n, t, x, y);
-    return V.w(c, x0 + x, y0 + y);
+// Reverse pass of the dissipative flux of the same face (NF = ... + F^d), in
+// face coordinates (n = normal axis, e_j = tangential axes t1, t2, each with
+// derivatives only if active).  Forward (Sections 2, 3.4):
+//   du_k/dn = DF4(u_k), dT/dn = DF4(T) along the normal (k = n, t1, t2);
+//   du_n/de_j and du_ej/de_j by DC4 along e_j at the cells -1..2 along n,
+//   interpolated to the face with RC4; face velocities RC4(u_k);
+//   div = du_n/dn + sum_j du_ej/de_j;
+//   tau_n = mu (2 du_n/dn - 2/3 div), tau_ej = mu (du_n/de_j + du_ej/dn);
+//   F^d = [0, tau, u_f . tau + lambda dT/dn] (tau_n in component 1 + d).
+template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
+__device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY, BZ>& V, const Frame& F,
+                                              const int p[3], const T nu[5], const Gas<T>& g, const T inv_h[3]) {
+  auto at = [&](int c, int s, int a, int b) -> T {
+    return V.w(c, p[0] + F.pick(0, s, a, b), p[1] + F.pick(1, s, a, b), p[2] + F.pick(2, s, a, b));
   };
-  auto put = [&](int c, int n, int t, T val) {
-    int x, y;
-    vroles(d, n, t, x, y);
-    V.add(c, x0 + x, y0 + y, val);
+  auto put = [&](int c, int s, int a, int b, T val) {
+    V.add(c, p[0] + F.pick(0, s, a, b), p[1] + F.pick(1, s, a, b), p[2] + F.pick(2, s, a, b), val);
   };
-  const int cn = 1 + d, ct = 2 - d, cz = 3;
-  const T hn = d == 0 ? inv_h[0] : inv_h[1];
-  const T ht = d == 0 ? inv_h[1] : inv_h[0];
+  const int comp[3] = {1 + F.d, 1 + F.t1, 1 + F.t2};
+  const bool act[2] = {F.t1 < DIM, F.t2 < DIM};
+  const T hn = F.d == 0 ? inv_h[0] : (F.d == 1 ? inv_h[1] : inv_h[2]);
+  const T he[2] = {F.t1 == 0 ? inv_h[0] : (F.t1 == 1 ? inv_h[1] : inv_h[2]),
+                   F.t2 == 0 ? inv_h[0] : (F.t2 == 1 ? inv_h[1] : inv_h[2])};
   const T df[4] = {T(1) / T(24), -T(27) / T(24), T(27) / T(24), -T(1) / T(24)};
   const T rc[4] = {-T(1) / T(16), T(9) / T(16), T(9) / T(16), -T(1) / T(16)};
   const T dcw[4] = {T(1) / T(12), -T(8) / T(12), T(8) / T(12), -T(1) / T(12)};
   const int dco[4] = {-2, -1, 1, 2};
   // ---- forward ----
-  T gn[3], uf[3];  // d u_k / dn and face velocities, k = n, t, z
-  const int comp[3] = {cn, ct, cz};
+  T gn[3], uf[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     T s = T(0), f = T(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const T u = at(comp[k], q - 1, 0);
+      const T u = at(comp[k], q - 1, 0, 0);
       s += df[q] * u;
       f += rc[q] * u;
     }
     gn[k] = s * hn;
     uf[k] = f;
   }
-  T gnt = T(0), gtt = T(0);  // d u_n / dt, d u_t / dt
-  if (DIM >= 2) {
+  T gt[2][2] = {{T(0), T(0)}, {T(0), T(0)}};  // [j][0] = du_n/de_j, [j][1] = du_ej/de_j
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (!act[j]) continue;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
+      const int c = k == 0 ? comp[0] : comp[1 + j];
       T acc = T(0);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         T cen = T(0);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cen += dcw[j] * at(comp[k], q - 1, dco[j]);
+        for (int o = 0; o < 4; ++o)
+          cen += dcw[o] * (j == 0 ? at(c, q - 1, dco[o], 0) : at(c, q - 1, 0, dco[o]));
         acc += rc[q] * cen;
       }
-      if (k == 0) gnt = acc * ht; else gtt = acc * ht;
+      gt[j][k] = acc * he[j];
     }
   }
-  const T div = gn[0] + gtt;
-  const T tau[3] = {g.mu * (T(2) * gn[0]) - (T(2) / T(3)) * g.mu * div, g.mu * (gnt + gn[1]), g.mu * gn[2]};
+  const T div = gn[0] + gt[0][1] + gt[1][1];
+  const T tau[3] = {g.mu * (T(2) * gn[0]) - (T(2) / T(3)) * g.mu * div, g.mu * (gt[0][0] + gn[1]),
+                    g.mu * (gt[1][0] + gn[2])};
   // ---- reverse ----
-  const T nun[3] = {nu[cn], nu[ct], nu[cz]};
+  const T nun[3] = {sel3(nu, comp[0]), sel3(nu, comp[1]), sel3(nu, comp[2])};
   T taub[3], ufb[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -246,44 +262,51 @@ __device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY>&
   const T dTb = nu[4] * g.lambda;
   const T divb = -(T(2) / T(3)) * g.mu * taub[0];
   const T gnb[3] = {T(2) * g.mu * taub[0] + divb, g.mu * taub[1], g.mu * taub[2]};
-  const T gntb = g.mu * taub[1], gttb = divb;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) put(comp[k], q - 1, 0, gnb[k] * hn * df[q] + ufb[k] * rc[q]);
-    put(5, q - 1, 0, dTb * hn * df[q]);
+    for (int k = 0; k < 3; ++k) put(comp[k], q - 1, 0, 0, gnb[k] * hn * df[q] + ufb[k] * rc[q]);
+    put(5, q - 1, 0, 0, dTb * hn * df[q]);
   }
-  if (DIM >= 2) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (!act[j]) continue;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const T gb = (k == 0 ? gntb : gttb) * ht;
+      const int c = k == 0 ? comp[0] : comp[1 + j];
+      const T gb = (k == 0 ? g.mu * taub[1 + j] : divb) * he[j];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) put(comp[k], q - 1, dco[j], gb * rc[q] * dcw[j]);
+        for (int o = 0; o < 4; ++o) {
+          const T val = gb * rc[q] * dcw[o];
+          if (j == 0) put(c, q - 1, dco[o], 0, val); else put(c, q - 1, 0, dco[o], val);
+        }
     }
   }
 }
 
-// The stage VJP kernel (DIM = 1 or 2).  blockDim.x == BX * BY,
-// grid = (ceil(nx/BX), ceil(ny/BY)).
-template <typename T, int DIM, bool VISC, int BX, int BY>
-__global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> A, const Gas<T> g) {
-  using G = VGeo<BX, BY, DIM, VISC>;
+// The stage VJP kernel.  blockDim.x == BX * BY * BZ,
+// grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/BZ)).
+template <typename T, int DIM, bool VISC, int BX, int BY, int BZ, int MINB>
+__global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const VjpArgs<T> A, const Gas<T> g) {
+  using G = VGeo<BX, BY, BZ, DIM, VISC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Wb = reinterpret_cast<T*>(smem_raw);
   T* Mb = Wb + G::NCW * G::CS;
   T* acc = Mb + 5 * G::MCS;
-  const int gx0 = blockIdx.x * BX, gy0 = blockIdx.y * BY;
+  const int B[3] = {BX, BY, BZ};
+  const int g0[3] = {(int)blockIdx.x * BX, (int)blockIdx.y * BY, (int)blockIdx.z * BZ};
   const int tid = threadIdx.x;
 
   // stage W (halo 5) and m = s_in lam (halo 3; zero on zero-gradient ghosts)
   bool bad = false;
   for (int t = tid; t < G::CS; t += G::NT) {
-    const int ly = t / G::PX, lx = t - ly * G::PX;
-    const int gx = map_index(gx0 + lx - G::H, A.nx, A.periodic[0]);
-    const int gy = DIM >= 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
-    const long long q = (long long)gy * A.nx + gx;
+    const int lx = t % G::PX, ly = (t / G::PX) % G::PY, lz = t / (G::PX * G::PY);
+    const int gx = map_index(g0[0] + lx - G::HX, A.n[0], A.periodic[0]);
+    const int gy = DIM >= 2 ? map_index(g0[1] + ly - G::HY, A.n[1], A.periodic[1]) : 0;
+    const int gz = DIM == 3 ? map_index(g0[2] + lz - G::HZ, A.n[2], A.periodic[2]) : 0;
+    const long long q = ((long long)gz * A.n[1] + gy) * A.n[0] + gx;
     const T r = A.Us[q];
     const T inv = T(1) / r;
     const T u = A.Us[q + A.N] * inv, v = A.Us[q + 2 * A.N] * inv, w = A.Us[q + 3 * A.N] * inv;
@@ -298,94 +321,91 @@ __global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> 
   }
   if (bad) atomicOr(A.flag, 1);
   for (int t = tid; t < G::MCS; t += G::NT) {
-    const int ly = t / G::MPX, lx = t - ly * G::MPX;
-    const int rx = gx0 + lx - G::MH, ry = DIM >= 2 ? gy0 + ly - G::MHY : 0;
-    const bool ghost = (!A.periodic[0] && (rx < 0 || rx >= A.nx)) ||
-                       (DIM >= 2 && !A.periodic[1] && (ry < 0 || ry >= A.ny));
-    const int gx = map_index(rx, A.nx, A.periodic[0]);
-    const int gy = DIM >= 2 ? map_index(ry, A.ny, A.periodic[1]) : 0;
-    const long long q = (long long)gy * A.nx + gx;
+    const int lx = t % G::MPX, ly = (t / G::MPX) % G::MPY, lz = t / (G::MPX * G::MPY);
+    const int r[3] = {g0[0] + lx - G::MX, DIM >= 2 ? g0[1] + ly - G::MY : 0, DIM == 3 ? g0[2] + lz - G::MZ : 0};
+    bool ghost = false;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) ghost |= !A.periodic[a] && (r[a] < 0 || r[a] >= A.n[a]);
+    const int gx = map_index(r[0], A.n[0], A.periodic[0]);
+    const int gy = DIM >= 2 ? map_index(r[1], A.n[1], A.periodic[1]) : 0;
+    const int gz = DIM == 3 ? map_index(r[2], A.n[2], A.periodic[2]) : 0;
+    const long long q = ((long long)gz * A.n[1] + gy) * A.n[0] + gx;
 #pragma unroll
     for (int c = 0; c < 5; ++c) Mb[c * G::MCS + t] = ghost ? T(0) : A.s_in * A.lam[q + c * A.N];
   }
   for (int t = tid; t < 6 * G::NCELL; t += G::NT) acc[t] = T(0);
   __syncthreads();
 
-  VTile<T, DIM, VISC, BX, BY> V{Wb, Mb, acc, gx0, gy0, A.nx, A.ny, A.periodic[0], DIM >= 2 ? A.periodic[1] : 1};
-  const T inv_h[2] = {A.inv_h[0], A.inv_h[1]};
+  VTile<T, DIM, VISC, BX, BY, BZ> V;
+  V.W = Wb;
+  V.M = Mb;
+  V.acc = acc;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    V.g0[a] = g0[a];
+    V.n[a] = A.n[a];
+    V.per[a] = a < DIM ? A.periodic[a] : 1;
+  }
+  const T inv_h[3] = {A.inv_h[0], A.inv_h[1], A.inv_h[2]};
 
-  // convective faces along x: tile rows, left cells x = -3 .. BX+1 (a face
-  // reaches cells x-2 .. x+3)
-  for (int f = tid; f < BY * (BX + 5); f += G::NT) {
-    const int y = f / (BX + 5), x = f - y * (BX + 5) - 3;
-    T nu[5];
+  auto face_nu = [&](const Frame& F, const int p[3], T nu[5]) -> bool {
+    const int q0 = p[0] + (F.d == 0), q1 = p[1] + (F.d == 1), q2 = p[2] + (F.d == 2);
+    const T h = F.d == 0 ? inv_h[0] : (F.d == 1 ? inv_h[1] : inv_h[2]);
     bool any = false;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      nu[c] = (V.m(c, x, y) - V.m(c, x + 1, y)) * inv_h[0];
+      nu[c] = (V.m(c, p[0], p[1], p[2]) - V.m(c, q0, q1, q2)) * h;
       any |= nu[c] != T(0);
     }
-    if (any) conv_face_vjp<T, DIM, VISC, BX, BY>(V, 0, x, y, nu, g);
-  }
-  if (DIM >= 2) {
-    // convective faces along y: tile columns, lower cells y = -3 .. BY+1
-    for (int f = tid; f < BX * (BY + 5); f += G::NT) {
-      const int yy = f / BX, x = f - yy * BX, y = yy - 3;
-      T nu[5];
-      bool any = false;
+    return any;
+  };
+
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        nu[c] = (V.m(c, x, y) - V.m(c, x, y + 1)) * inv_h[1];
-        any |= nu[c] != T(0);
-      }
-      if (any) conv_face_vjp<T, DIM, VISC, BX, BY>(V, 1, x, y, nu, g);
-    }
-  }
-  if (VISC) {
-    // dissipative faces along x: rows -VR .. BY-1+VR, left cells -2 .. BX (a
-    // face reaches cells x-1 .. x+2 and rows y-2 .. y+2)
-    constexpr int NXR = BY + 2 * G::VR, NXC = BX + 3;
-    for (int f = tid; f < NXR * NXC; f += G::NT) {
-      const int yy = f / NXC, x = f - yy * NXC - 2, y = yy - G::VR;
-      T nu[5];
-      bool any = false;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        nu[c] = (V.m(c, x, y) - V.m(c, x + 1, y)) * inv_h[0];
-        any |= nu[c] != T(0);
-      }
-      if (any) visc_face_vjp<T, DIM, VISC, BX, BY>(V, 0, x, y, nu, g, inv_h);
-    }
-    if (DIM >= 2) {
-      // dissipative faces along y: columns -2 .. BX+1, lower cells -2 .. BY
-      constexpr int NYC = BX + 4, NYR = BY + 3;
-      for (int f = tid; f < NYC * NYR; f += G::NT) {
-        const int yy = f / NYC, x = f - yy * NYC - 2, y = yy - 2;
+  for (int d = 0; d < DIM; ++d) {
+    const Frame F{d, (d + 1) % 3, (d + 2) % 3};
+    const bool act1 = F.t1 < DIM, act2 = F.t2 < DIM;
+    const int B1 = act1 ? B[F.t1] : 1, B2 = act2 ? B[F.t2] : 1;
+    // convective faces: left cells -3 .. B_d+1 along d (a face reaches cells
+    // -2 .. +3 along d), the box's own cells across
+    {
+      const int en = B[d] + 5, cnt = en * B1 * B2;
+      for (int f = tid; f < cnt; f += G::NT) {
+        const int s = f % en - 3, r = f / en;
+        const int a = r % B1, b = r / B1;
+        const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
         T nu[5];
-        bool any = false;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          nu[c] = (V.m(c, x, y) - V.m(c, x, y + 1)) * inv_h[1];
-          any |= nu[c] != T(0);
-        }
-        if (any) visc_face_vjp<T, DIM, VISC, BX, BY>(V, 1, x, y, nu, g, inv_h);
+        if (face_nu(F, p, nu)) conv_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g);
+      }
+    }
+    if (VISC) {
+      // dissipative faces: left cells -2 .. B_d along d (cells -1 .. +2) and
+      // -2 .. B+1 across on the active tangential axes (reach +-2)
+      const int en = B[d] + 3, e1 = act1 ? B1 + 4 : 1, e2 = act2 ? B2 + 4 : 1, cnt = en * e1 * e2;
+      const int o1 = act1 ? 2 : 0, o2 = act2 ? 2 : 0;
+      for (int f = tid; f < cnt; f += G::NT) {
+        const int s = f % en - 2, r = f / en;
+        const int a = r % e1 - o1, b = r / e1 - o2;
+        const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
+        T nu[5];
+        if (face_nu(F, p, nu)) visc_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g, inv_h);
       }
     }
   }
   __syncthreads();
 
   // cells: cotangent of W (+T) -> cotangent of U, then the stage combination
-  const int tx = tid % BX, ty = tid / BX;
-  const int gx = gx0 + tx, gy = gy0 + ty;
-  if (gx < A.nx && gy < (DIM >= 2 ? A.ny : 1)) {
-    const T r = V.w(0, tx, ty), u = V.w(1, tx, ty), v = V.w(2, tx, ty), w = V.w(3, tx, ty), p = V.w(4, tx, ty);
-    const int cell = ty * BX + tx;
+  const int tx = tid % BX, ty = (tid / BX) % BY, tz = tid / (BX * BY);
+  const int gx = g0[0] + tx, gy = g0[1] + ty, gz = g0[2] + tz;
+  if (gx < A.n[0] && gy < A.n[1] && gz < A.n[2]) {
+    const T r = V.w(0, tx, ty, tz), u = V.w(1, tx, ty, tz), v = V.w(2, tx, ty, tz), w = V.w(3, tx, ty, tz);
+    const T p = V.w(4, tx, ty, tz);
+    const int cell = (tz * BY + ty) * BX + tx;
     T br = acc[cell], bu = acc[G::NCELL + cell], bv = acc[2 * G::NCELL + cell], bw = acc[3 * G::NCELL + cell];
     T bp = acc[4 * G::NCELL + cell];
     if (VISC) {
       const T bT = acc[5 * G::NCELL + cell];
-      const T Tc = V.w(5, tx, ty);
-      br -= bT * Tc / r;       // T = p / (rho R)
+      const T Tc = V.w(5, tx, ty, tz);
+      br -= bT * Tc / r;  // T = p / (rho R)
       bp += bT * Tc / p;
     }
     const T inv = T(1) / r;
@@ -396,10 +416,10 @@ __global__ void __launch_bounds__(BX * BY, 2) vjp_stage_kernel(const VjpArgs<T> 
     bU[3] = bw * inv - bp * g.gm1 * w;
     bU[4] = bp * g.gm1;
     const T dt = T(*A.dt);
-    const long long q = (long long)gy * A.nx + gx;
+    const long long q = ((long long)gz * A.n[1] + gy) * A.n[0] + gx;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      T o = V.m(c, tx, ty) + dt * bU[c];
+      T o = V.m(c, tx, ty, tz) + dt * bU[c];
       if (A.x1) o += A.a1 * A.x1[q + c * A.N];
       if (A.x2) o += A.a2 * A.x2[q + c * A.N];
       A.out[q + c * A.N] = o;

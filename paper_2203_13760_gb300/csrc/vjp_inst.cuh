@@ -1,4 +1,5 @@
-// Launch wrappers of the stage VJP kernel (one tile shape per dimensionality).
+// Launch wrappers of the stage VJP kernel (one box shape per dimensionality
+// and precision).
 #pragma once
 #include "vjp.cuh"
 
@@ -7,14 +8,14 @@ namespace jf {
 template <typename T>
 using VjpLaunch = cudaError_t (*)(const VjpArgs<T>& A, const Gas<T>& g, cudaStream_t s);
 
-template <typename T, int DIM, bool VISC, int BX, int BY>
+template <typename T, int DIM, bool VISC, int BX, int BY, int BZ, int MINB>
 cudaError_t launch_vjp(const VjpArgs<T>& A, const Gas<T>& g, cudaStream_t s) {
-  constexpr size_t smem = vjp_smem_bytes<T, DIM, VISC, BX, BY>();
-  auto k = vjp_stage_kernel<T, DIM, VISC, BX, BY>;
+  constexpr size_t smem = vjp_smem_bytes<T, DIM, VISC, BX, BY, BZ>();
+  auto k = vjp_stage_kernel<T, DIM, VISC, BX, BY, BZ, MINB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((A.nx + BX - 1) / BX, DIM >= 2 ? (A.ny + BY - 1) / BY : 1, 1);
-  k<<<grid, BX * BY, smem, s>>>(A, g);
+  const dim3 grid((A.n[0] + BX - 1) / BX, (A.n[1] + BY - 1) / BY, (A.n[2] + BZ - 1) / BZ);
+  k<<<grid, BX * BY * BZ, smem, s>>>(A, g);
   return cudaGetLastError();
 }
 

@@ -32,6 +32,10 @@ CASES = {
     "2d_blocks_mixed_bc": lambda: inputs.random_blocks((8, 7, 1), seed=6, bc=(0, 0, 1, 1, 1, 1)),
     "2d_kh_visc": lambda: inputs.kelvin_helmholtz(10, seed=1),
     "2d_smooth_zg_visc": lambda: inputs.random_smooth((7, 9, 1), seed=8, bc=(1,) * 6, viscous=True, mu=0.03),
+    "3d_smooth_visc_periodic": lambda: inputs.random_smooth((6, 5, 5), seed=9, viscous=True, mu=0.02),
+    "3d_blocks_mixed_bc": lambda: inputs.random_blocks((5, 6, 5), seed=10, bc=(0, 0, 1, 1, 0, 0)),
+    "3d_smooth_zg_visc_ragged": lambda: inputs.random_smooth((9, 5, 6), seed=12, bc=(1,) * 6, viscous=True,
+                                                             mu=0.03),
 }
 
 
@@ -68,9 +72,25 @@ def test_vjp_fp64_equals_oracle_jacobian(orc, name):
     assert np.array_equal(Un.cpu().numpy(), case.U)
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-4)])
-def test_dot_product_identity(orc, dtype, tol):
-    case = inputs.kelvin_helmholtz(32, seed=3)
+def _tgv_off_symmetry(n):
+    """Taylor-Green field with a 1e-6 seeded perturbation: the exact field is
+    mirror-symmetric, so on its symmetry planes the HLLC contact speed S* is
+    exactly 0, where the flux is continuous but not differentiable (the two
+    one-sided derivatives differ and any rounding picks one of them)."""
+    case = inputs.taylor_green(n)
+    rng = np.random.default_rng(4)
+    case.U = case.U * (1.0 + 1e-6 * rng.standard_normal(case.U.shape))
+    return case
+
+
+@pytest.mark.parametrize("dtype,tol,make", [
+    ("f64", 1e-12, lambda: inputs.kelvin_helmholtz(32, seed=3)),
+    ("f32", 1e-5, lambda: inputs.kelvin_helmholtz(32, seed=3)),
+    ("f64", 1e-12, lambda: _tgv_off_symmetry(12)),
+    ("f32", 1e-5, lambda: _tgv_off_symmetry(16)),
+])
+def test_dot_product_identity(orc, dtype, tol, make):
+    case = make()
     c = orc.config(**case.params())
     dt = orc.compute_dt(c, case.U)
     rng = np.random.default_rng(5)
@@ -83,9 +103,12 @@ def test_dot_product_identity(orc, dtype, tol):
     lam = s.rk3_step_vjp(torch.tensor(U0, dtype=t, device="cuda"), s.scalar(dt),
                          torch.tensor(w, dtype=t, device="cuda"))
     s.sync()
-    lhs = float(np.dot(lam.double().cpu().numpy().reshape(-1), v.reshape(-1)))
+    lam = lam.double().cpu().numpy().reshape(-1)
+    lhs = float(np.dot(lam, v.reshape(-1)))
     rhs = float(np.dot(w.reshape(-1), Jv.reshape(-1)))
-    assert abs(lhs - rhs) <= tol * (abs(rhs) + np.abs(w).sum() * 1e-3)
+    # rounding scale of the two dot products: the sums of their absolute terms
+    scale = float(np.abs(lam * v.reshape(-1)).sum() + np.abs(w.reshape(-1) * Jv.reshape(-1)).sum())
+    assert abs(lhs - rhs) <= tol * scale
 
 
 def _entropy_and_grad(U, gamma):
