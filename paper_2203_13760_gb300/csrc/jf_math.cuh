@@ -33,6 +33,18 @@ template <typename T> JF_HD T tsqrt(T x);
 template <> JF_HD float tsqrt<float>(float x) { return sqrtf(x); }
 template <> JF_HD double tsqrt<double>(double x) { return sqrt(x); }
 
+// Reciprocal of the point-wise numerics.  FP32 device code takes the
+// hardware approximate reciprocal (__fdividef: one MUFU operation, within
+// 2 ulp for |x| < 2^126); FP64 and host code divide exactly.
+template <typename T> JF_HD T trcp(T x) { return T(1) / x; }
+template <> JF_HD float trcp<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(1.0f, x);
+#else
+  return 1.0f / x;
+#endif
+}
+
 template <typename T> JF_HD T tmin(T a, T b) { return b < a ? b : a; }
 template <typename T> JF_HD T tmax(T a, T b) { return a < b ? b : a; }
 
@@ -92,12 +104,14 @@ __device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, 
   const float2 t1 = __ffma2_rn(__fmul2_rn(k13, d1), d1, __ffma2_rn(__fmul2_rn(k14, e1), e1, ke));
   const float2 t2 = __ffma2_rn(__fmul2_rn(k13, d2), d2, __ffma2_rn(__fmul2_rn(k14, e2), e2, ke));
   const float2 s0 = __fmul2_rn(t0, t0), s1 = __fmul2_rn(t1, t1), s2 = __fmul2_rn(t2, t2);
-  const float2 a0 = make_float2(0.1f / s0.x, 0.1f / s0.y);
-  const float2 a1 = make_float2(0.6f / s1.x, 0.6f / s1.y);
-  const float2 a2 = make_float2(0.3f / s2.x, 0.3f / s2.y);
+  // approximate reciprocals (s_k >= eps^2 > 0; alpha_k > 0 so sum > 0)
+  auto rcp2 = [](float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); };
+  const float2 a0 = __fmul2_rn(c(0.1f), rcp2(s0));
+  const float2 a1 = __fmul2_rn(c(0.6f), rcp2(s1));
+  const float2 a2 = __fmul2_rn(c(0.3f), rcp2(s2));
   const float2 sum = __fadd2_rn(__fadd2_rn(a0, a1), a2);
   const float2 num = __ffma2_rn(a2, q2, __ffma2_rn(a1, q1, __fmul2_rn(a0, q0)));
-  return make_float2(num.x / sum.x, num.y / sum.y);
+  return __fmul2_rn(num, rcp2(sum));
 }
 
 // HLLC flux along axis D from the reconstructed primitive states
@@ -117,11 +131,13 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
   const T kR = T(0.5) * rR * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]);
   const T EL = pL * g.inv_gm1 + kL;
   const T ER = pR * g.inv_gm1 + kR;
-  const T cL = tsqrt(g.gamma * pL / rL);
-  const T cR = tsqrt(g.gamma * pR / rR);
+  // every division goes through a reciprocal (1/rho of each side shared)
+  const T irL = trcp(rL), irR = trcp(rR);
+  const T cL = tsqrt(g.gamma * pL * irL);
+  const T cR = tsqrt(g.gamma * pR * irR);
   const T sL = tsqrt(rL), sR = tsqrt(rR);
-  const T inv_s = T(1) / (sL + sR);
-  const T HL = (EL + pL) / rL, HR = (ER + pR) / rR;
+  const T inv_s = trcp(sL + sR);
+  const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   const T u0 = (sL * WL[1] + sR * WR[1]) * inv_s;
   const T u1 = (sL * WL[2] + sR * WR[2]) * inv_s;
   const T u2 = (sL * WL[3] + sR * WR[3]) * inv_s;
@@ -131,11 +147,12 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
   const T SL = tmin(unL - cL, un_t - ct);
   const T SR = tmax(unR + cR, un_t + ct);
   const T mL = rL * (SL - unL), mR = rR * (SR - unR);
-  const T Ss = (pR - pL + mL * unL - mR * unR) / (mL - mR);
+  const T Ss = (pR - pL + mL * unL - mR * unR) * trcp(mL - mR);
   // side selection: F_L if 0 <= S_L; F*_L if S_L < 0 <= S*; F*_R if S* < 0 < S_R; F_R if S_R <= 0
   const bool left = (SL >= T(0)) || (Ss >= T(0));
   const bool star = left ? !(SL >= T(0)) : (SR > T(0));
   const T r = left ? rL : rR, p = left ? pL : pR, un = left ? unL : unR, E = left ? EL : ER;
+  const T ir = left ? irL : irR;
   const T w0 = left ? WL[1] : WR[1], w1 = left ? WL[2] : WR[2], w2 = left ? WL[3] : WR[3];
   const T S = left ? SL : SR, m = left ? mL : mR;
   // physical flux of the chosen side
@@ -143,8 +160,8 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
   T Fk[5] = {mass, mass * w0, mass * w1, mass * w2, un * (E + p)};
   Fk[1 + D] += p;
   if (star) {
-    const T fac = m / (S - Ss);
-    T Us[5] = {fac, fac * w0, fac * w1, fac * w2, fac * (E / r + (Ss - un) * (Ss + p / m))};
+    const T fac = m * trcp(S - Ss);
+    T Us[5] = {fac, fac * w0, fac * w1, fac * w2, fac * (E * ir + (Ss - un) * (Ss + p * trcp(m)))};
     Us[1 + D] = fac * Ss;
     const T Uk[5] = {r, r * w0, r * w1, r * w2, E};
 #pragma unroll

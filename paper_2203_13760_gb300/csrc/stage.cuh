@@ -54,8 +54,11 @@ struct StageArgs {
 
 __device__ __forceinline__ int map_index(int i, int n, int periodic) {
   if (periodic) {
-    i %= n;
-    return i < 0 ? i + n : i;
+    // one wrap covers the 3-cell halo when n >= 3; the remainder handles
+    // shorter periodic axes
+    if (i < 0) i += n; else if (i >= n) i -= n;
+    if ((unsigned)i >= (unsigned)n) { i %= n; if (i < 0) i += n; }
+    return i;
   }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
@@ -124,7 +127,7 @@ __device__ __forceinline__ void commit_plane(const StageArgs<T>& A, const Gas<T>
     const int t = threadIdx.x + i * G::NT;
     if (t < G::CS) {
       const T rho = r.v[i][0];
-      const T inv = T(1) / rho;
+      const T inv = trcp(rho);
       const T u = r.v[i][1] * inv, v = r.v[i][2] * inv, w = r.v[i][3] * inv;
       const T p = g.gm1 * (r.v[i][4] - T(0.5) * rho * (u * u + v * v + w * w));
       bad |= !(rho > T(0)) || !(p > T(0)) || !(p < T(INFINITY));
