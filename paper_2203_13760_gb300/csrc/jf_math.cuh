@@ -86,32 +86,42 @@ JF_HD T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
 // The left and right WENO5-JS states of one face component in packed FP32x2
 // arithmetic (sm_100+ FFMA2 / FADD2 / FMUL2): lane x reconstructs
 // (v[i-2], .., v[i+2]) -> v^-, lane y the mirrored stencil
-// (v[i+3], .., v[i-1]) -> v^+.  Same formula as weno5, two stencils per
-// instruction.
+// (v[i+3], .., v[i-1]) -> v^+.  The formula of weno5, rearranged to fewer
+// operations (equal up to rounding):
+//  * with the differences D1 = vm2 - vm1, D2 = v0 - vm1, D3 = vp1 - v0,
+//    D4 = vp1 - vp2 the candidates are q_k = v0 + delta_k / 6 with
+//    delta = (5 D2 + 2 D1, D2 + 2 D3, 4 D3 + D4), and the smoothness terms
+//    are d0 = D2 + D1, d1 = D3 - D2, |d2| = |D3 + D4|, e0 = 3 D2 + D1,
+//    |e1| = |D2 + D3|, |e2| = |3 D3 + D4| (only their squares enter);
+//  * every eps + beta_k is scaled by 12/13 (a common factor of the three
+//    alpha_k, which cancels in omega_k), so t_k = d_k^2 + 3/13 e_k^2 + 12/13 eps;
+//  * with r_k = 1 / t_k^2 and alpha_k scaled by 10/3 (weights 1/3, 2, 1),
+//    v^ = v0 + (r0 delta0/18 + r1 delta1/3 + r2 delta2/6) / (r0/3 + 2 r1 + r2).
 __device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, float2 vp1, float2 vp2, float eps) {
   auto c = [](float x) { return make_float2(x, x); };
-  const float2 q0 = __ffma2_rn(c(11.0f / 6.0f), v0, __ffma2_rn(c(-7.0f / 6.0f), vm1, __fmul2_rn(c(2.0f / 6.0f), vm2)));
-  const float2 q1 = __ffma2_rn(c(2.0f / 6.0f), vp1, __ffma2_rn(c(5.0f / 6.0f), v0, __fmul2_rn(c(-1.0f / 6.0f), vm1)));
-  const float2 q2 = __ffma2_rn(c(-1.0f / 6.0f), vp2, __ffma2_rn(c(5.0f / 6.0f), vp1, __fmul2_rn(c(2.0f / 6.0f), v0)));
-  const float2 d0 = __ffma2_rn(c(-2.0f), vm1, __fadd2_rn(vm2, v0));
-  const float2 e0 = __ffma2_rn(c(3.0f), v0, __ffma2_rn(c(-4.0f), vm1, vm2));
-  const float2 d1 = __ffma2_rn(c(-2.0f), v0, __fadd2_rn(vm1, vp1));
-  const float2 e1 = __ffma2_rn(c(-1.0f), vp1, vm1);
-  const float2 d2 = __ffma2_rn(c(-2.0f), vp1, __fadd2_rn(v0, vp2));
-  const float2 e2 = __ffma2_rn(c(3.0f), v0, __ffma2_rn(c(-4.0f), vp1, vp2));
-  const float2 k13 = c(13.0f / 12.0f), k14 = c(0.25f), ke = c(eps);
-  const float2 t0 = __ffma2_rn(__fmul2_rn(k13, d0), d0, __ffma2_rn(__fmul2_rn(k14, e0), e0, ke));
-  const float2 t1 = __ffma2_rn(__fmul2_rn(k13, d1), d1, __ffma2_rn(__fmul2_rn(k14, e1), e1, ke));
-  const float2 t2 = __ffma2_rn(__fmul2_rn(k13, d2), d2, __ffma2_rn(__fmul2_rn(k14, e2), e2, ke));
-  const float2 s0 = __fmul2_rn(t0, t0), s1 = __fmul2_rn(t1, t1), s2 = __fmul2_rn(t2, t2);
-  // approximate reciprocals (s_k >= eps^2 > 0; alpha_k > 0 so sum > 0)
+  const float2 m1 = c(-1.0f);
+  const float2 D1 = __ffma2_rn(m1, vm1, vm2);
+  const float2 D2 = __ffma2_rn(m1, vm1, v0);
+  const float2 D3 = __ffma2_rn(m1, v0, vp1);
+  const float2 D4 = __ffma2_rn(m1, vp2, vp1);
+  const float2 d0 = __fadd2_rn(D2, D1), e0 = __ffma2_rn(c(3.0f), D2, D1);
+  const float2 d1 = __ffma2_rn(m1, D2, D3), e1 = __fadd2_rn(D2, D3);
+  const float2 d2 = __fadd2_rn(D3, D4), e2 = __ffma2_rn(c(3.0f), D3, D4);
+  const float2 k3 = c(3.0f / 13.0f), ke = c(12.0f / 13.0f * eps);
+  const float2 t0 = __ffma2_rn(d0, d0, __ffma2_rn(__fmul2_rn(k3, e0), e0, ke));
+  const float2 t1 = __ffma2_rn(d1, d1, __ffma2_rn(__fmul2_rn(k3, e1), e1, ke));
+  const float2 t2 = __ffma2_rn(d2, d2, __ffma2_rn(__fmul2_rn(k3, e2), e2, ke));
+  // approximate reciprocals (t_k^2 >= (12/13 eps)^2 > 0, so the sum is > 0)
   auto rcp2 = [](float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); };
-  const float2 a0 = __fmul2_rn(c(0.1f), rcp2(s0));
-  const float2 a1 = __fmul2_rn(c(0.6f), rcp2(s1));
-  const float2 a2 = __fmul2_rn(c(0.3f), rcp2(s2));
-  const float2 sum = __fadd2_rn(__fadd2_rn(a0, a1), a2);
-  const float2 num = __ffma2_rn(a2, q2, __ffma2_rn(a1, q1, __fmul2_rn(a0, q0)));
-  return __fmul2_rn(num, rcp2(sum));
+  const float2 r0 = rcp2(__fmul2_rn(t0, t0));
+  const float2 r1 = rcp2(__fmul2_rn(t1, t1));
+  const float2 r2 = rcp2(__fmul2_rn(t2, t2));
+  const float2 g0 = __ffma2_rn(c(5.0f / 18.0f), D2, __fmul2_rn(c(1.0f / 9.0f), D1));
+  const float2 g1 = __ffma2_rn(c(2.0f / 3.0f), D3, __fmul2_rn(c(1.0f / 3.0f), D2));
+  const float2 g2 = __ffma2_rn(c(2.0f / 3.0f), D3, __fmul2_rn(c(1.0f / 6.0f), D4));
+  const float2 num = __ffma2_rn(r2, g2, __ffma2_rn(r1, g1, __fmul2_rn(r0, g0)));
+  const float2 den = __ffma2_rn(c(1.0f / 3.0f), r0, __ffma2_rn(c(2.0f), r1, r2));
+  return __ffma2_rn(num, rcp2(den), v0);
 }
 
 // HLLC flux along axis D from the reconstructed primitive states

@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "jf_math.cuh"
 
 namespace jf {
@@ -227,10 +229,64 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
 #pragma unroll
     for (int b = 0; b < 3; ++b) G[a][b] = T(0);
   const T hn = inv_h[D];
+  T dTdn, uf[3];
+  if constexpr (sizeof(T) == 4) {
+    // FP32: the same stencils on component pairs in packed FP32x2 arithmetic
+    // (equal to the scalar form below up to rounding)
+    auto c2 = [](float x) { return make_float2(x, x); };
+    const float2 m1 = c2(-1.0f);
+    auto pair = [&](int c0, int c1, int n, int t1, int t2) {
+      return make_float2(val(c0, n, t1, t2), val(c1, n, t1, t2));
+    };
+    // normal derivative (df4) and face value (rc4) from the cells -1..2
+    // along the normal: (u, v) and (w, T)
+    float2 uv[4], wT[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uv[q] = pair(1, 2, q - 1, 0, 0);
+      wT[q] = pair(3, 5, q - 1, 0, 0);
+    }
+    const float2 kn27 = c2(27.0f / 24.0f * hn), kn1 = c2(hn / 24.0f);
+    auto df4p = [&](const float2 v[4]) {
+      return __ffma2_rn(kn27, __ffma2_rn(m1, v[1], v[2]), __fmul2_rn(kn1, __ffma2_rn(m1, v[3], v[0])));
+    };
+    auto rc4p = [&](const float2 v[4]) {
+      return __ffma2_rn(c2(9.0f / 16.0f), __fadd2_rn(v[1], v[2]), __fmul2_rn(c2(-1.0f / 16.0f), __fadd2_rn(v[0], v[3])));
+    };
+    const float2 g_uv = df4p(uv), g_wT = df4p(wT), f_uv = rc4p(uv), f_wT = rc4p(wT);
+    G[0][D] = g_uv.x;
+    G[1][D] = g_uv.y;
+    G[2][D] = g_wT.x;
+    dTdn = g_wT.y;
+    uf[0] = f_uv.x;
+    uf[1] = f_uv.y;
+    uf[2] = f_wT.x;
+    // tangential derivative along e of (u_D, u_e): cell-centre C4 derivative
+    // at the cells -1..2 along the normal, interpolated to the face:
+    // h_q = (v(q,-2) - v(q,2)) + 8 (v(q,1) - v(q,-1)), G = (9 (h1 + h2) - (h0 + h3)) / 192
+    auto tang = [&](auto role) {
+      constexpr int R = decltype(role)::value;  // 1: tangent T1, 2: tangent T2
+      constexpr int e = R == 1 ? Ro::T1 : Ro::T2;
+      float2 h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        auto at = [&](int j) { return R == 1 ? pair(1 + D, 1 + e, q - 1, j, 0) : pair(1 + D, 1 + e, q - 1, 0, j); };
+        const float2 vm2 = at(-2), vm1 = at(-1), vp1 = at(1), vp2 = at(2);
+        h[q] = __ffma2_rn(c2(8.0f), __ffma2_rn(m1, vm1, vp1), __ffma2_rn(m1, vp2, vm2));
+      }
+      const float he = inv_h[e];
+      const float2 Ge = __ffma2_rn(c2(9.0f / 192.0f * he), __fadd2_rn(h[1], h[2]),
+                                   __fmul2_rn(c2(-1.0f / 192.0f * he), __fadd2_rn(h[0], h[3])));
+      G[D][e] = Ge.x;
+      G[e][e] = Ge.y;
+    };
+    if constexpr (Ro::T1 < DIM) tang(std::integral_constant<int, 1>{});
+    if constexpr (Ro::T2 < DIM) tang(std::integral_constant<int, 2>{});
+  } else {
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     G[a][D] = df4(val(1 + a, -1, 0, 0), val(1 + a, 0, 0, 0), val(1 + a, 1, 0, 0), val(1 + a, 2, 0, 0)) * hn;
-  const T dTdn = df4(val(5, -1, 0, 0), val(5, 0, 0, 0), val(5, 1, 0, 0), val(5, 2, 0, 0)) * hn;
+  dTdn = df4(val(5, -1, 0, 0), val(5, 0, 0, 0), val(5, 1, 0, 0), val(5, 2, 0, 0)) * hn;
   // tangential derivatives: cell-centre C4 at cells -1..2 along the normal,
   // then fourth-order interpolation to the face
   if (Ro::T1 < DIM) {
@@ -261,10 +317,10 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
       G[a][e] = rc4(cen[0], cen[1], cen[2], cen[3]) * he;
     }
   }
-  T uf[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     uf[a] = rc4(val(1 + a, -1, 0, 0), val(1 + a, 0, 0, 0), val(1 + a, 1, 0, 0), val(1 + a, 2, 0, 0));
+  }
   const T div = G[0][0] + G[1][1] + G[2][2];
   T tau[3];
 #pragma unroll
