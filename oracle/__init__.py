@@ -20,6 +20,18 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
                          invariant relations, contact continuity)
   jvp_run                pinned (against central finite differences of run)
   compute_dt             pinned (closed form on uniform states)
+  weno5_z                pinned (fifth order at critical points where WENO5-JS
+                         drops, non-oscillation at a jump, linear exactness)
+  hll / rusanov flux     pinned (consistency, Rankine-Hugoniot across the HLL
+                         fan, Rusanov = HLL with symmetric speeds, upwinding,
+                         contact diffusion ordering)
+  signal_speeds          pinned (equal states give u -+ c; Toro's factor with
+                         the exact p* gives the exact shock speed; PVRS error
+                         of second order in the jump)
+  time_step (rk2/euler)  pinned (temporal orders 1, 2, 3; RK2 = mean of U and
+                         two Euler steps)
+  shock tubes            Sod and Lax against the exact solution for every
+                         solver / speed / reconstruction
   count_flops            descriptive only (an operation count, not a result)
 """
 from __future__ import annotations
@@ -71,12 +83,23 @@ class Config(ctypes.Structure):
         ("viscous", ctypes.c_int),
         ("heat", ctypes.c_int),
         ("safe", ctypes.c_int),
+        ("flux", ctypes.c_int),
+        ("recon", ctypes.c_int),
+        ("speeds", ctypes.c_int),
+        ("integrator", ctypes.c_int),
     ]
+
+
+# scheme options (Table 2); 0 is the Appendix A configuration
+FLUX = {"hllc": 0, "hll": 1, "rusanov": 2}
+RECON = {"weno5-js": 0, "weno5-z": 1}
+SPEEDS = {"einfeldt": 0, "davis": 1, "toro": 2}
+INTEGRATOR = {"rk3": 0, "rk2": 1, "euler": 2}
 
 
 def config(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gamma=1.4, R=1.0,
            mu=0.0, Pr=0.72, eps=1e-6, cfl=0.5, convective=True, viscous=False, heat=False,
-           safe=False) -> Config:
+           safe=False, flux="hllc", recon="weno5-js", speeds="einfeldt", integrator="rk3") -> Config:
     n = tuple(int(x) for x in n) + (1,) * (3 - len(n))
     c = Config()
     c.n[:] = n
@@ -85,6 +108,8 @@ def config(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gam
     c.bc[:] = [int(x) for x in bc]
     c.gamma, c.R, c.mu, c.Pr, c.eps, c.cfl = gamma, R, mu, Pr, eps, cfl
     c.convective, c.viscous, c.heat, c.safe = int(convective), int(viscous), int(heat), int(safe)
+    c.flux, c.recon = FLUX[flux], RECON[recon]
+    c.speeds, c.integrator = SPEEDS[speeds], INTEGRATOR[integrator]
     return c
 
 
@@ -112,6 +137,16 @@ def lib():
             L.orc_weno5.restype = d
             L.orc_hllc.argtypes = [dp, dp, ctypes.c_int, d, dp]
             L.orc_hllc.restype = None
+            L.orc_weno5_z.argtypes = [dp, d]
+            L.orc_weno5_z.restype = d
+            L.orc_signal_speeds.argtypes = [dp, dp, ctypes.c_int, d, ctypes.c_int, dp]
+            L.orc_signal_speeds.restype = None
+            L.orc_toro_q.argtypes = [d, d, d]
+            L.orc_toro_q.restype = d
+            L.orc_flux.argtypes = [dp, dp, ctypes.c_int, d, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_flux.restype = None
+            L.orc_hll_speeds.argtypes = [dp, dp, ctypes.c_int, d, d, d, dp]
+            L.orc_hll_speeds.restype = None
             L.orc_exact_star.argtypes = [dp, dp, d, dp]
             L.orc_exact_star.restype = ctypes.c_int
             L.orc_exact_sample.argtypes = [dp, dp, d, d, d, ctypes.c_int, dp, dp]
@@ -205,6 +240,40 @@ def hllc(WL, WR, d: int = 0, gamma: float = 1.4) -> np.ndarray:
     WR = np.ascontiguousarray(WR, dtype=np.float64)
     F = np.empty(5)
     lib().orc_hllc(_ptr(WL), _ptr(WR), int(d), float(gamma), _ptr(F))
+    return F
+
+
+def weno5_z(v, eps: float = 1e-6) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return float(lib().orc_weno5_z(_ptr(v), float(eps)))
+
+
+def signal_speeds(WL, WR, d: int = 0, gamma: float = 1.4, kind: str = "einfeldt"):
+    """(S_L, S_R) of the named estimate."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    out = np.empty(2)
+    lib().orc_signal_speeds(_ptr(WL), _ptr(WR), int(d), float(gamma), SPEEDS[kind], _ptr(out))
+    return float(out[0]), float(out[1])
+
+
+def toro_q(p_star: float, pK: float, gamma: float = 1.4) -> float:
+    return float(lib().orc_toro_q(float(p_star), float(pK), float(gamma)))
+
+
+def flux(WL, WR, d: int = 0, gamma: float = 1.4, kind: str = "hllc", speeds: str = "einfeldt") -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.empty(5)
+    lib().orc_flux(_ptr(WL), _ptr(WR), int(d), float(gamma), FLUX[kind], SPEEDS[speeds], _ptr(F))
+    return F
+
+
+def hll_with_speeds(WL, WR, SL: float, SR: float, d: int = 0, gamma: float = 1.4) -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    F = np.empty(5)
+    lib().orc_hll_speeds(_ptr(WL), _ptr(WR), int(d), float(gamma), float(SL), float(SR), _ptr(F))
     return F
 
 

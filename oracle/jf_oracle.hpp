@@ -25,15 +25,22 @@
 //                      (StiffenedGas) with B = 0; T = p / (rho R)
 //   weno5_js           Section 3.3 "High-order Godunov approach" step 1 with
 //                      WENO5-JS (Jiang & Shu 1996, cited in Section 3.1/Table 2)
+//   weno5_z            WENO5-Z (Borges et al. 2008), the "Z" of Table 2's
+//                      WENO5-JS/Z
+//   signal_speeds      Table 2 signal speed estimates: Einfeldt (Appendix A
+//                      default), Davis (1988), Toro (1994, PVRS pressure)
 //   hllc_flux          Section 3.3 steps 2-3, Eq. (ApproxRiemannSolver) with
-//                      HLLC (Toro 1994) and Einfeldt signal speeds (Table 2,
-//                      Appendix A "signal_speed": "EINFELDT")
+//                      HLLC (Toro 1994) and the chosen signal speeds
+//   hll_flux           HLL (Harten, Lax, van Leer 1983), Table 2
+//   rusanov_flux       local Lax-Friedrichs / Rusanov, Table 2
 //   dissipative_flux   Section 2 (tau, q = -lambda grad T) discretised by
 //                      Section 3.4 (face C4 derivative, cell-centre C4
 //                      derivative + fourth-order interpolation to the face)
 //   rhs                Eq. (FVD) of Section 3.1, one-point face quadrature,
 //                      dimension by dimension
 //   rk3_step           Section 3.2, TVD-RK3 (Gottlieb & Shu 1998), Shu-Osher form
+//   time_step          Table 2 time integrators: TVD-RK3, TVD-RK2 (Gottlieb &
+//                      Shu 1998, Shu-Osher form), explicit Euler
 //   compute_dt         Section 3.2 CFL criterion (the paper defers the formula
 //                      to another paper; the reading used is written out below)
 #pragma once
@@ -47,6 +54,11 @@
 namespace orc {
 
 enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1 };
+// scheme options of Table 2 (0 = the Appendix A configuration)
+enum { FLUX_HLLC = 0, FLUX_HLL = 1, FLUX_RUSANOV = 2 };
+enum { RECON_WENO5_JS = 0, RECON_WENO5_Z = 1 };
+enum { SPEED_EINFELDT = 0, SPEED_DAVIS = 1, SPEED_TORO = 2 };
+enum { TIME_RK3 = 0, TIME_RK2 = 1, TIME_EULER = 2 };
 constexpr int NG = 3;  // ghost cells per side on an active axis (WENO5 reaches 3)
 
 // Problem description.  An axis with n == 1 is inactive (no fluxes along it).
@@ -63,6 +75,10 @@ struct Config {
   int heat;           // include the heat flux
   int safe;           // "is_safe_reconstruction": first-order fallback at a
                       // face side whose reconstructed rho or p is <= 0
+  int flux;           // FLUX_*: Riemann solver
+  int recon;          // RECON_*: reconstruction
+  int speeds;         // SPEED_*: signal speed estimate (HLLC, HLL)
+  int integrator;     // TIME_*: time integration
 };
 
 inline bool active(const Config& c, int d) { return c.n[d] > 1; }
@@ -191,6 +207,27 @@ T weno5_js(const T& vm2, const T& vm1, const T& v0, const T& vp1, const T& vp2, 
   return w0 * q0 + w1 * q1 + w2 * q2;
 }
 
+// WENO5-Z (Borges, Carmona, Costa, Don 2008): the candidates q_k and
+// smoothness indicators beta_k of WENO5-JS, the global indicator
+// tau5 = |beta_0 - beta_2| and alpha_k = d_k (1 + tau5 / (eps + beta_k)),
+// omega_k = alpha_k / sum(alpha) (power 1 of the ratio).
+template <class T>
+T weno5_z(const T& vm2, const T& vm1, const T& v0, const T& vp1, const T& vp2, double eps) {
+  const T q0 = (2.0 * vm2 - 7.0 * vm1 + 11.0 * v0) / 6.0;
+  const T q1 = (-vm1 + 5.0 * v0 + 2.0 * vp1) / 6.0;
+  const T q2 = (2.0 * v0 + 5.0 * vp1 - vp2) / 6.0;
+  const T b0 = (13.0 / 12.0) * sq(vm2 - 2.0 * vm1 + v0) + 0.25 * sq(vm2 - 4.0 * vm1 + 3.0 * v0);
+  const T b1 = (13.0 / 12.0) * sq(vm1 - 2.0 * v0 + vp1) + 0.25 * sq(vm1 - vp1);
+  const T b2 = (13.0 / 12.0) * sq(v0 - 2.0 * vp1 + vp2) + 0.25 * sq(3.0 * v0 - 4.0 * vp1 + vp2);
+  const T tau5 = fabs(b0 - b2);
+  const T a0 = 0.1 * (1.0 + tau5 / (eps + b0));
+  const T a1 = 0.6 * (1.0 + tau5 / (eps + b1));
+  const T a2 = 0.3 * (1.0 + tau5 / (eps + b2));
+  const T s = a0 + a1 + a2;
+  const T w0 = a0 / s, w1 = a1 / s, w2 = a2 / s;
+  return w0 * q0 + w1 * q1 + w2 * q2;
+}
+
 // Conservative state and physical flux along axis d (Section 2: F, G, H).
 template <class T>
 void conservative_of(const T W[5], double gamma, T U[5]) {
@@ -211,11 +248,54 @@ void physical_flux(const T W[5], const T U[5], int d, T F[5]) {
   F[4] = un * (U[4] + W[4]);
 }
 
-// HLLC flux (Toro 1994) with Einfeldt signal speeds, normal axis d.
+// Signal speed estimates S_L <= S_R of the Riemann fan at a face with normal
+// axis d (Table 2), from the side states W = [rho, u, v, w, p]:
+//   Einfeldt (1988): Roe averages with weights sqrt(rho): u~, H~
+//     (H = (E + p) / rho), c~ = sqrt((gamma - 1)(H~ - |u~|^2 / 2));
+//     S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~);
+//   Davis (1988): S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R);
+//   Toro (1994; Toro 2009, Section 10.5.2): the primitive-variable (PVRS)
+//     pressure p* = max(0, (p_L + p_R) / 2 - (u_R - u_L) rho_ c_ / 2) with
+//     rho_ = (rho_L + rho_R) / 2, c_ = (c_L + c_R) / 2; per side
+//     q_K = 1 if p* <= p_K, else sqrt(1 + (gamma + 1) / (2 gamma) (p* / p_K - 1));
+//     S_L = u_L - c_L q_L, S_R = u_R + c_R q_R.
+template <class T>
+T toro_q(const T& p_star, const T& pK, double gamma) {
+  if (p_star <= pK) return T(1.0);
+  return sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (p_star / pK - 1.0));
+}
+template <class T>
+void signal_speeds(const T WL[5], const T WR[5], int d, double gamma, int kind, T& SL, T& SR) {
+  const T rhoL = WL[0], rhoR = WR[0], pL = WL[4], pR = WR[4];
+  const T unL = WL[1 + d], unR = WR[1 + d];
+  const T cL = sqrt(gamma * pL / rhoL);
+  const T cR = sqrt(gamma * pR / rhoR);
+  if (kind == SPEED_DAVIS) {
+    SL = tmin(unL - cL, unR - cR);
+    SR = tmax(unL + cL, unR + cR);
+  } else if (kind == SPEED_TORO) {
+    const T ppv = 0.5 * (pL + pR) - 0.5 * (unR - unL) * (0.5 * (rhoL + rhoR)) * (0.5 * (cL + cR));
+    const T p_star = tmax(T(0.0), ppv);
+    SL = unL - cL * toro_q(p_star, pL, gamma);
+    SR = unR + cR * toro_q(p_star, pR, gamma);
+  } else {
+    T UL[5], UR[5];
+    conservative_of(WL, gamma, UL);
+    conservative_of(WR, gamma, UR);
+    const T HL = (UL[4] + pL) / rhoL;
+    const T HR = (UR[4] + pR) / rhoR;
+    const T sL = sqrt(rhoL), sR = sqrt(rhoR);
+    T ut[3];
+    for (int m = 0; m < 3; ++m) ut[m] = (sL * WL[1 + m] + sR * WR[1 + m]) / (sL + sR);
+    const T Ht = (sL * HL + sR * HR) / (sL + sR);
+    const T ct = sqrt((gamma - 1.0) * (Ht - 0.5 * (ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2])));
+    SL = tmin(unL - cL, ut[d] - ct);
+    SR = tmax(unR + cR, ut[d] + ct);
+  }
+}
+
+// HLLC flux (Toro 1994), normal axis d, signal speeds of the chosen kind.
 // Section 3.3, Eq. (ApproxRiemannSolver): F(U^-, U^+, W^-, W^+).
-//   Roe averages with weights sqrt(rho): u~, H~ (H = (E + p) / rho),
-//   c~ = sqrt((gamma - 1)(H~ - |u~|^2 / 2));
-//   S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~);
 //   S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R))
 //        / (rho_L (S_L - u_L) - rho_R (S_R - u_R));
 //   U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S* (normal), tangential u,
@@ -224,7 +304,7 @@ void physical_flux(const T W[5], const T U[5], int d, T F[5]) {
 //   F = F_L if 0 <= S_L; F*_L if S_L < 0 <= S*; F*_R if S* < 0 < S_R;
 //       F_R if S_R <= 0.
 template <class T>
-void hllc_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5]) {
+void hllc_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5], int speeds = SPEED_EINFELDT) {
   T UL[5], UR[5], FL[5], FR[5];
   conservative_of(WL, gamma, UL);
   conservative_of(WR, gamma, UR);
@@ -232,17 +312,8 @@ void hllc_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5]) {
   physical_flux(WR, UR, d, FR);
   const T rhoL = WL[0], rhoR = WR[0], pL = WL[4], pR = WR[4];
   const T unL = WL[1 + d], unR = WR[1 + d];
-  const T cL = sqrt(gamma * pL / rhoL);
-  const T cR = sqrt(gamma * pR / rhoR);
-  const T HL = (UL[4] + pL) / rhoL;
-  const T HR = (UR[4] + pR) / rhoR;
-  const T sL = sqrt(rhoL), sR = sqrt(rhoR);
-  T ut[3];
-  for (int m = 0; m < 3; ++m) ut[m] = (sL * WL[1 + m] + sR * WR[1 + m]) / (sL + sR);
-  const T Ht = (sL * HL + sR * HR) / (sL + sR);
-  const T ct = sqrt((gamma - 1.0) * (Ht - 0.5 * (ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2])));
-  const T SL = tmin(unL - cL, ut[d] - ct);
-  const T SR = tmax(unR + cR, ut[d] + ct);
+  T SL, SR;
+  signal_speeds(WL, WR, d, gamma, speeds, SL, SR);
   const T Ss = (pR - pL + rhoL * unL * (SL - unL) - rhoR * unR * (SR - unR)) /
                (rhoL * (SL - unL) - rhoR * (SR - unR));
   if (SL >= 0.0) {
@@ -268,10 +339,58 @@ void hllc_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5]) {
   }
 }
 
+// HLL flux (Harten, Lax, van Leer 1983) for given signal speeds S_L <= S_R:
+//   F = F_L if 0 <= S_L; F_R if S_R <= 0; otherwise
+//   F = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
+template <class T>
+void hll_flux_speeds(const T WL[5], const T WR[5], int d, double gamma, const T& SL, const T& SR, T F[5]) {
+  T UL[5], UR[5], FL[5], FR[5];
+  conservative_of(WL, gamma, UL);
+  conservative_of(WR, gamma, UR);
+  physical_flux(WL, UL, d, FL);
+  physical_flux(WR, UR, d, FR);
+  if (SL >= 0.0) {
+    for (int m = 0; m < 5; ++m) F[m] = FL[m];
+  } else if (SR <= 0.0) {
+    for (int m = 0; m < 5; ++m) F[m] = FR[m];
+  } else {
+    for (int m = 0; m < 5; ++m) F[m] = (SR * FL[m] - SL * FR[m] + SL * SR * (UR[m] - UL[m])) / (SR - SL);
+  }
+}
+template <class T>
+void hll_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5], int speeds = SPEED_EINFELDT) {
+  T SL, SR;
+  signal_speeds(WL, WR, d, gamma, speeds, SL, SR);
+  hll_flux_speeds(WL, WR, d, gamma, SL, SR, F);
+}
+
+// Local Lax-Friedrichs (Rusanov) flux: with a = max(|u_L| + c_L, |u_R| + c_R)
+// (normal velocities),  F = (F_L + F_R) / 2 - a (U_R - U_L) / 2.
+template <class T>
+void rusanov_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5]) {
+  T UL[5], UR[5], FL[5], FR[5];
+  conservative_of(WL, gamma, UL);
+  conservative_of(WR, gamma, UR);
+  physical_flux(WL, UL, d, FL);
+  physical_flux(WR, UR, d, FR);
+  const T cL = sqrt(gamma * WL[4] / WL[0]);
+  const T cR = sqrt(gamma * WR[4] / WR[0]);
+  const T a = tmax(fabs(WL[1 + d]) + cL, fabs(WR[1 + d]) + cR);
+  for (int m = 0; m < 5; ++m) F[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * a * (UR[m] - UL[m]);
+}
+
+// The Riemann solver of the configuration.
+template <class T>
+void riemann_flux(const Config& c, const T WL[5], const T WR[5], int d, T F[5]) {
+  if (c.flux == FLUX_HLL) hll_flux(WL, WR, d, c.gamma, F, c.speeds);
+  else if (c.flux == FLUX_RUSANOV) rusanov_flux(WL, WR, d, c.gamma, F);
+  else hllc_flux(WL, WR, d, c.gamma, F, c.speeds);
+}
+
 // Convective flux at the face between cell c and cell c + e_d (Section 3.3,
-// High-order Godunov approach): WENO5-JS on each primitive component in
-// physical space ("reconstruction_var": "PRIMITIVE"), the right state by the
-// mirrored stencil, then HLLC.
+// High-order Godunov approach): WENO5-JS (or -Z) on each primitive component
+// in physical space ("reconstruction_var": "PRIMITIVE"), the right state by
+// the mirrored stencil, then the Riemann solver (HLLC by default).
 template <class T>
 void convective_face_flux(const Field<T>& W, const Config& c, int d, const Cell& cell, T F[5]) {
   T Wm[5], Wp[5];
@@ -282,8 +401,13 @@ void convective_face_flux(const Field<T>& W, const Config& c, int d, const Cell&
     const T f1 = at(W, m, cell.shift(d, 1));
     const T g2 = at(W, m, cell.shift(d, 2));
     const T h3 = at(W, m, cell.shift(d, 3));
-    Wm[m] = weno5_js(a, b, e0, f1, g2, c.eps);
-    Wp[m] = weno5_js(h3, g2, f1, e0, b, c.eps);
+    if (c.recon == RECON_WENO5_Z) {
+      Wm[m] = weno5_z(a, b, e0, f1, g2, c.eps);
+      Wp[m] = weno5_z(h3, g2, f1, e0, b, c.eps);
+    } else {
+      Wm[m] = weno5_js(a, b, e0, f1, g2, c.eps);
+      Wp[m] = weno5_js(h3, g2, f1, e0, b, c.eps);
+    }
   }
   if (c.safe) {
     // reading of "is_safe_reconstruction": if the reconstructed density or
@@ -293,7 +417,7 @@ void convective_face_flux(const Field<T>& W, const Config& c, int d, const Cell&
     if (!(Wp[0] > 0.0) || !(Wp[4] > 0.0))
       for (int m = 0; m < 5; ++m) Wp[m] = at(W, m, cell.shift(d, 1));
   }
-  hllc_flux(Wm, Wp, d, c.gamma, F);
+  riemann_flux(c, Wm, Wp, d, F);
 }
 
 // Section 3.4 stencils.
@@ -447,6 +571,47 @@ void rk3_step(const Config& c, Field<T>& Un, double dt) {
     Un(m, i, j, k) = (1.0 / 3.0) * Un(m, i, j, k) + (2.0 / 3.0) * (U2(m, i, j, k) + dt * L(m, i, j, k));
   });
   fill_ghosts(Un, c);
+}
+
+// Table 2 time integrators other than TVD-RK3, with fixed dt:
+//   TVD-RK2 (Gottlieb & Shu 1998), Shu-Osher form:
+//     U1 = Un + dt L(Un);  U^{n+1} = 1/2 Un + 1/2 (U1 + dt L(U1))
+//   Euler:  U^{n+1} = Un + dt L(Un)
+template <class T>
+void rk2_step(const Config& c, Field<T>& Un, double dt) {
+  Field<T> L(c, 5), U1(c, 5);
+  fill_ghosts(Un, c);
+  rhs(c, Un, L);
+  for (int m = 0; m < 5; ++m)
+    for (int k = 0; k < c.n[2]; ++k)
+      for (int j = 0; j < c.n[1]; ++j)
+        for (int i = 0; i < c.n[0]; ++i) U1(m, i, j, k) = Un(m, i, j, k) + dt * L(m, i, j, k);
+  fill_ghosts(U1, c);
+  rhs(c, U1, L);
+  for (int m = 0; m < 5; ++m)
+    for (int k = 0; k < c.n[2]; ++k)
+      for (int j = 0; j < c.n[1]; ++j)
+        for (int i = 0; i < c.n[0]; ++i)
+          Un(m, i, j, k) = 0.5 * Un(m, i, j, k) + 0.5 * (U1(m, i, j, k) + dt * L(m, i, j, k));
+  fill_ghosts(Un, c);
+}
+template <class T>
+void euler_step(const Config& c, Field<T>& Un, double dt) {
+  Field<T> L(c, 5);
+  fill_ghosts(Un, c);
+  rhs(c, Un, L);
+  for (int m = 0; m < 5; ++m)
+    for (int k = 0; k < c.n[2]; ++k)
+      for (int j = 0; j < c.n[1]; ++j)
+        for (int i = 0; i < c.n[0]; ++i) Un(m, i, j, k) = Un(m, i, j, k) + dt * L(m, i, j, k);
+  fill_ghosts(Un, c);
+}
+// One step of the configuration's integrator.
+template <class T>
+void time_step(const Config& c, Field<T>& Un, double dt) {
+  if (c.integrator == TIME_RK2) rk2_step(c, Un, dt);
+  else if (c.integrator == TIME_EULER) euler_step(c, Un, dt);
+  else rk3_step(c, Un, dt);
 }
 
 // Time step (Section 3.2 names a CFL criterion and defers its formula).

@@ -41,6 +41,9 @@ inline bool operator<(const Counted& a, const Counted& b) { return a.v < b.v; }
 inline bool operator>(const Counted& a, double b) { return a.v > b; }
 inline bool operator>=(const Counted& a, double b) { return a.v >= b; }
 inline Counted sqrt(const Counted& a) { ++Counted::ops(); return Counted(std::sqrt(a.v)); }
+inline bool operator<=(const Counted& a, const Counted& b) { return a.v <= b.v; }
+inline bool operator<=(const Counted& a, double b) { return a.v <= b; }
+inline Counted fabs(const Counted& a) { return Counted(std::fabs(a.v)); }  // sign only: not counted
 
 template <class T>
 static void store_state(const Config& c, const Field<T>& f, double* U, double* V) {
@@ -69,6 +72,10 @@ static bool valid(const Config* c) {
     const bool p0 = c->bc[2 * d] == BC_PERIODIC, p1 = c->bc[2 * d + 1] == BC_PERIODIC;
     if (p0 != p1) return false;  // periodic must be set on both sides
   }
+  if (c->flux < FLUX_HLLC || c->flux > FLUX_RUSANOV) return false;
+  if (c->recon < RECON_WENO5_JS || c->recon > RECON_WENO5_Z) return false;
+  if (c->speeds < SPEED_EINFELDT || c->speeds > SPEED_TORO) return false;
+  if (c->integrator < TIME_RK3 || c->integrator > TIME_EULER) return false;
   return true;
 }
 
@@ -122,7 +129,7 @@ int orc_run(const Config* c, double* U, int nsteps, double dt, double t_end, dou
     if (t_end > 0.0 && t >= t_end) break;
     double h = dt > 0.0 ? dt : compute_dt(*c, f);
     if (t_end > 0.0 && t + h > t_end) h = t_end - t;
-    rk3_step(*c, f, h);
+    time_step(*c, f, h);
     t += h;
   }
   store_state(*c, f, U, nullptr);
@@ -130,7 +137,7 @@ int orc_run(const Config* c, double* U, int nsteps, double dt, double t_end, dou
   return s;
 }
 
-// Forward-mode derivative of nsteps fixed-dt RK3 steps: on return U holds the
+// Forward-mode derivative of nsteps fixed-dt steps: on return U holds the
 // state after the steps and V holds J V0, J the Jacobian of the steps at U0.
 int orc_jvp_run(const Config* c, double* U, double* V, int nsteps, double dt) {
   if (!valid(c) || !(dt > 0.0)) return -1;
@@ -139,7 +146,7 @@ int orc_jvp_run(const Config* c, double* U, double* V, int nsteps, double dt) {
   for (size_t q = 0; q < 5 * N; ++q) ud[q] = Dual(U[q], V[q]);
   Field<Dual> f(*c, 5);
   load_state(*c, ud.data(), f);
-  for (int s = 0; s < nsteps; ++s) rk3_step(*c, f, dt);
+  for (int s = 0; s < nsteps; ++s) time_step(*c, f, dt);
   store_state(*c, f, U, V);
   return 0;
 }
@@ -197,7 +204,7 @@ int orc_sample_cells(const Config* c, const double* U, int nsamples, const int* 
       rhs(pc, f, r);
       for (int m = 0; m < 5; ++m) out[5 * s + m] = r(m, ci, cj, ck);
     } else {
-      for (int q = 0; q < nsteps; ++q) rk3_step(pc, f, dt);
+      for (int q = 0; q < nsteps; ++q) time_step(pc, f, dt);
       for (int m = 0; m < 5; ++m) out[5 * s + m] = f(m, ci, cj, ck);
     }
     if (!(pc.n[0] > 0)) fail = 1;
@@ -211,6 +218,31 @@ double orc_weno5(const double* v, double eps) { return weno5_js(v[0], v[1], v[2]
 // Single HLLC flux along axis d from primitive states W = [rho, u, v, w, p].
 void orc_hllc(const double* WL, const double* WR, int d, double gamma, double* F) {
   hllc_flux(WL, WR, d, gamma, F);
+}
+
+// Single WENO5-Z reconstruction v^-_{i+1/2} from v[i-2..i+2].
+double orc_weno5_z(const double* v, double eps) { return weno5_z(v[0], v[1], v[2], v[3], v[4], eps); }
+
+// Signal speed estimate `kind` (SPEED_*): out = (S_L, S_R).
+void orc_signal_speeds(const double* WL, const double* WR, int d, double gamma, int kind, double* out) {
+  signal_speeds(WL, WR, d, gamma, kind, out[0], out[1]);
+}
+
+// Toro's shock/rarefaction factor q_K for a given star pressure.
+double orc_toro_q(double p_star, double pK, double gamma) { return toro_q(p_star, pK, gamma); }
+
+// Riemann flux of kind `flux` (FLUX_*) with signal speeds `speeds` (SPEED_*).
+void orc_flux(const double* WL, const double* WR, int d, double gamma, int flux, int speeds, double* F) {
+  Config c{};
+  c.gamma = gamma;
+  c.flux = flux;
+  c.speeds = speeds;
+  riemann_flux(c, WL, WR, d, F);
+}
+
+// HLL flux for given signal speeds (S_L, S_R).
+void orc_hll_speeds(const double* WL, const double* WR, int d, double gamma, double SL, double SR, double* F) {
+  hll_flux_speeds(WL, WR, d, gamma, SL, SR, F);
 }
 
 // Exact Riemann problem: star state (p*, u*, rho*_L, rho*_R).  Returns 0, or -1

@@ -41,6 +41,10 @@ class Case:
     heat: bool = False
     cfl: float = 0.5
     eps: float = 1e-6
+    flux: str = "hllc"          # Riemann solver: hllc | hll | rusanov
+    recon: str = "weno5-js"     # reconstruction: weno5-js | weno5-z
+    speeds: str = "einfeldt"    # signal speeds: einfeldt | davis | toro
+    integrator: str = "rk3"     # time integration: rk3 | rk2 | euler
     dt: float = 0.0     # fixed time step if > 0
 
     @property
@@ -51,7 +55,8 @@ class Case:
         """Grid / gas / scheme parameters as keyword arguments."""
         return dict(n=self.n, lo=self.lo, hi=self.hi, bc=self.bc, gamma=self.gamma, R=self.R,
                     mu=self.mu, Pr=self.Pr, eps=self.eps, cfl=self.cfl, viscous=self.viscous,
-                    heat=self.heat)
+                    heat=self.heat, flux=self.flux, recon=self.recon, speeds=self.speeds,
+                    integrator=self.integrator)
 
 
 def conservative(rho, u, v, w, p, gamma: float) -> np.ndarray:
@@ -97,6 +102,28 @@ def riemann_1d(n: int, WL, WR, x0: float = 0.5, length: float = 1.0, gamma: floa
     p = np.where(left, WL[2], WR[2])
     U = conservative(rho, u, 0.0, 0.0, p, gamma).reshape(5, 1, 1, n)
     return Case("riemann1d", (n, 1, 1), (0.0, 0.0, 0.0), (length, 1.0, 1.0), (1, 1, 1, 1, 1, 1), U, gamma=gamma)
+
+
+# Sod's shock tube (Sod 1978; the Appendix A case): (rho, u, p) left / right.
+SOD_LEFT = (1.0, 0.0, 1.0)
+SOD_RIGHT = (0.125, 0.0, 0.1)
+
+# Lax's shock tube (Lax 1954), with the states tabulated by Shu & Osher (1989,
+# "Efficient implementation of essentially non-oscillatory shock-capturing
+# schemes II", Example 2): (rho, u, p) = (0.445, 0.698, 3.528) left and
+# (0.5, 0, 0.571) right of x = 0.5 on [0, 1]; run to t = 0.14.
+LAX_LEFT = (0.445, 0.698, 3.528)
+LAX_RIGHT = (0.5, 0.0, 0.571)
+LAX_END_TIME = 0.14
+
+
+def lax(n: int = 100, gamma: float = 1.4) -> Case:
+    """Lax shock tube of Section 5.1.2 (domain [0, 1], N = 100, t = 0.14,
+    zero-gradient ends).  The paper only cites Lax (1954) for the states, so
+    the classic ones above are used."""
+    case = riemann_1d(n, LAX_LEFT, LAX_RIGHT, gamma=gamma)
+    case.name = "lax"
+    return case
 
 
 def sine_advection(n: int, gamma: float = 1.4) -> Case:
