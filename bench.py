@@ -72,7 +72,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=-1)
-    p.add_argument("--only", choices=["batched", "adjoint"], default=None,
+    p.add_argument("--only", choices=["batched", "adjoint", "variants"], default=None,
                    help="run only the batched or the adjoint measurement and print it")
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--adjoint-steps", type=int, default=400)
@@ -98,7 +98,8 @@ def measured_peaks():
 
 # the files that define the forward stage kernel and its compile flags
 STAGE_SOURCES = ("csrc/stage.cuh", "csrc/stage_inst.cuh", "csrc/stage_f32.cu", "csrc/stage_f64.cu",
-                 "csrc/jf_math.cuh", "csrc/variants.h", "_build.py")
+                 "csrc/stage_f32_gen.cu", "csrc/stage_f64_gen.cu", "csrc/jf_math.cuh", "csrc/variants.h",
+                 "_build.py")
 
 
 def kernel_sources_sha():
@@ -526,8 +527,50 @@ def run_adjoint(n=256, steps=400, ckpt=20):
             "backward_ms": 1e3 * t_bwd, "forward_graph_ms": 1e3 * t_fwd_graph}
 
 
+VARIANT_SCHEMES = {
+    "hllc_einfeldt_weno5js_rk3 (default)": {},
+    "hll_einfeldt": {"flux": "hll"},
+    "rusanov": {"flux": "rusanov"},
+    "hllc_davis": {"speeds": "davis"},
+    "hllc_toro": {"speeds": "toro"},
+    "hllc_weno5z": {"recon": "weno5-z"},
+    "hllc_rk2": {"integrator": "rk2"},
+}
+
+
+def run_variants(n=256, steps=10):
+    """Table 2 scheme variants on the bench flow (TGV n^3, FP32, viscous +
+    heat, CFL steps through jf_rk3_step): cell-updates/s per variant.  The
+    default row runs the default-scheme kernels, the others the run-time-
+    scheme kernels."""
+    import torch
+
+    from paper_2203_13760_gb300 import inputs, jf
+    case = inputs.taylor_green(n)
+    out = {"workload": f"TGV {n}^3 FP32 Navier-Stokes, {steps} CFL steps per variant", "unit": "cell-updates/s"}
+    U0 = torch.tensor(case.U, dtype=torch.float32, device="cuda")
+    for name, kw in VARIANT_SCHEMES.items():
+        s = jf.Solver.from_case(case, dtype="f32", **kw)
+        U = U0.clone()
+        used = s.scalar()
+        for _ in range(2):
+            s.rk3_step(U, None, used)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(steps):
+            s.rk3_step(U, None, used)
+        e1.record()
+        torch.cuda.synchronize()
+        s.sync()
+        out[name] = case.cells * steps / (e0.elapsed_time(e1) * 1e-3)
+        s.close()
+    return out
+
+
 def run_extras(args):
-    """Batched and adjoint forms against the plain per-simulation launch."""
+    """Batched and adjoint forms against the plain per-simulation launch, and
+    the scheme variants on the bench flow."""
     out = {}
     try:
         out["batched"] = run_batched()
@@ -537,6 +580,10 @@ def run_extras(args):
         out["adjoint"] = run_adjoint()
     except Exception as e:
         out["adjoint"] = {"error": repr(e)}
+    try:
+        out["variants"] = run_variants()
+    except Exception as e:
+        out["variants"] = {"error": repr(e)}
     return out
 
 
@@ -550,7 +597,12 @@ def main():
         from paper_2203_13760_gb300 import _build
         _build.build()
         torch.cuda.set_device(0)
-        out = run_batched() if args.only == "batched" else run_adjoint(args.adjoint_n, args.adjoint_steps)
+        if args.only == "batched":
+            out = run_batched()
+        elif args.only == "variants":
+            out = run_variants()
+        else:
+            out = run_adjoint(args.adjoint_n, args.adjoint_steps)
         print(json.dumps({args.only: out}), flush=True)
         return 0
     return run_jf(args)

@@ -57,7 +57,11 @@ typedef enum {
 
 typedef enum { JF_BC_PERIODIC = 0, JF_BC_ZERO_GRADIENT = 1 } jf_bc;
 enum { JF_F32 = 0, JF_F64 = 1 };
-enum { JF_EINFELDT = 0 };
+/* Scheme options (Table 2 of the paper; 0 is the Appendix A configuration). */
+enum { JF_EINFELDT = 0, JF_DAVIS = 1, JF_TORO = 2 };           /* signal speed estimates */
+enum { JF_FLUX_HLLC = 0, JF_FLUX_HLL = 1, JF_FLUX_RUSANOV = 2 }; /* Riemann solvers */
+enum { JF_WENO5_JS = 0, JF_WENO5_Z = 1 };                        /* reconstructions */
+enum { JF_RK3 = 0, JF_RK2 = 1, JF_EULER = 2 };                   /* time integrators */
 
 /* Cartesian grid of nx*ny*nz cells on [lo, hi] (Section 3.1: cuboid cells).
  * bc[] = {x-lo, x-hi, y-lo, y-hi, z-lo, z-hi} (west, east, south, north,
@@ -78,12 +82,26 @@ typedef struct {
 } jf_gas;
 
 /* Scheme options.  dtype: JF_F32 or JF_F64 (arithmetic and storage type of
- * the fields; the CFL reduction and dt are always FP64).  weno_eps: WENO5-JS
+ * the fields; the CFL reduction and dt are always FP64).  weno_eps: WENO5
  * epsilon (1e-6).  cfl: CFL number.  viscous / heat: include the viscous
- * stresses / heat flux (both need mu > 0).  signal_speed: JF_EINFELDT (the
- * only estimate built).  safe_recon: 1 = a face side whose reconstructed
- * density or pressure is not positive falls back to its cell value (the
- * paper's "is_safe_reconstruction" flag, which it does not define further). */
+ * stresses / heat flux (both need mu > 0).  safe_recon: 1 = a face side whose
+ * reconstructed density or pressure is not positive falls back to its cell
+ * value (the paper's "is_safe_reconstruction" flag, which it does not define
+ * further).  Table 2 variants (a zero-initialised struct gives the Appendix A
+ * configuration):
+ *   signal_speed  JF_EINFELDT (Roe-averaged, Einfeldt 1988), JF_DAVIS (Davis
+ *                 1988), JF_TORO (Toro 1994: PVRS star pressure)
+ *   flux          JF_FLUX_HLLC (Toro 1994), JF_FLUX_HLL (Harten, Lax, van Leer
+ *                 1983), JF_FLUX_RUSANOV (local Lax-Friedrichs); the signal
+ *                 speeds apply to HLLC and HLL
+ *   recon         JF_WENO5_JS (Jiang & Shu 1996), JF_WENO5_Z (Borges et al.
+ *                 2008, power 1)
+ *   integrator    JF_RK3 / JF_RK2 (TVD Runge-Kutta of Gottlieb & Shu 1998,
+ *                 Shu-Osher form) or JF_EULER, used by jf_rk3_step,
+ *                 jf_rk3_run and jf_batch_step (the names keep the default).
+ * The adjoint (jf_rk3_step_vjp) is built for the default configuration only
+ * and returns JF_ERR_UNSUPPORTED otherwise.  An option out of range is
+ * JF_ERR_ARG. */
 typedef struct {
   int dtype;
   double weno_eps;
@@ -91,6 +109,9 @@ typedef struct {
   int viscous, heat;
   int signal_speed;
   int safe_recon;
+  int flux;
+  int recon;
+  int integrator;
 } jf_scheme;
 
 /* Create a solver for one grid.  Validates the configuration and allocates
@@ -160,8 +181,9 @@ jf_status jf_loss_density_l2(jf_handle h, const void* U, const void* target, dou
 
 /* Batch of nsim independent simulations with their own grid sizes (Section
  * 4.5, feed_forward over a batch of initial buffers; here sizes may differ).
- * All share gas and scheme.  Each grid must be 2D or 1D (nz == 1).  Allocates
- * each simulation's stage buffers and the work list. */
+ * All share gas and scheme.  Each grid must be 2D or 1D (nz == 1);
+ * 1 <= nsim <= 65535.  Allocates each simulation's stage buffers and the work
+ * list. */
 jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, const jf_scheme* scheme,
                           jf_handle* out);
 

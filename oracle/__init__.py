@@ -202,6 +202,7 @@ def run(c: Config, U, nsteps: int, dt: float = 0.0, t_end: float = 0.0):
 
 
 def rk3_step(c: Config, U, dt: float) -> np.ndarray:
+    """One fixed-dt step of the configured integrator (TVD-RK3 by default)."""
     return run(c, U, 1, dt)[0]
 
 

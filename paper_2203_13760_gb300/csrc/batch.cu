@@ -2,9 +2,10 @@
 // grids of uneven sizes advanced together (Section 4.5, feed_forward over a
 // batch of initial buffers).
 //
-// Per RK3 step: one per-simulation CFL launch (each CTA reduces one chunk of
-// one simulation; the last chunk of a simulation forms its dt) and three
-// persistent stage launches over the flattened (simulation, tile) work list,
+// Per step: one per-simulation CFL launch (each CTA reduces one chunk of
+// one simulation; the last chunk of a simulation forms its dt) and the
+// integrator's persistent stage launches (TVD-RK3: three, TVD-RK2: two,
+// Euler: one and a copy) over the flattened (simulation, tile) work list,
 // each item being one tile of the same code as the single-grid kernel.  The
 // nsteps steps are captured into one CUDA graph and replayed; the graph reads
 // the simulations' field pointers from device descriptors, so rebinding new
@@ -20,15 +21,26 @@ namespace jf {
 
 constexpr long long kChunk = 16384;  // cells per CFL CTA
 
+// Euler steps of a batch: U = U1 for every simulation (blockIdx.y), the
+// pointers read from the device descriptors so that rebinding stays valid.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_copy_kernel(const SimDesc<T>* __restrict__ sims) {
+  const SimDesc<T> d = sims[blockIdx.y];
+  const long long n = 5 * d.N;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d.U[i] = d.U1[i];
+}
+
 namespace {
 
 template <typename T>
-std::vector<int> batch_variant_list(int dim, bool visc) {
+std::vector<int> batch_variant_list(int dim, bool visc, bool general) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
   std::vector<int> out;
   for (int i = 0; i < count; ++i)
-    if (tab[i].dim == dim && tab[i].visc == visc && tab[i].launch_batch) out.push_back(i);
+    if (tab[i].dim == dim && tab[i].visc == visc && tab[i].general == general && tab[i].launch_batch)
+      out.push_back(i);
   return out;
 }
 
@@ -36,7 +48,7 @@ std::vector<int> batch_variant_list(int dim, bool visc) {
 template <typename T>
 jf_status setup_variant(jf_ctx* h, int v) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = batch_variant_list<T>(h->dim, visc);
+  auto list = batch_variant_list<T>(h->dim, visc, general_scheme(h->scheme));
   if (list.empty()) { set_error(h, "batch: no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
   if (v < 0) v = 0;
   if (v >= (int)list.size()) { set_error(h, "batch: variant index out of range"); return JF_ERR_ARG; }
@@ -159,9 +171,17 @@ jf_status enqueue_steps(jf_ctx* h, int nsteps, double* dt_out, cudaStream_t s) {
     cudaError_t e = launch_cfl_batch<T>(sims, h->d_chunks, h->nchunks, static_cast<const CflArgs*>(h->d_cfl),
                                         h->d_red, h->d_dt, h->flag, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "batch: cfl launch");
-    for (int stage = 1; stage <= 3; ++stage) {
-      e = sv.launch_batch(sims, work, h->nwork, stage, g, h->flag, h->batch_blocks, s);
+    // stage codes of the batch kernel: RK3 1, 2, 3; RK2 1, 4; Euler 1 + copy
+    const int integ = h->scheme.integrator;
+    const int codes[3] = {1, integ == JF_RK2 ? 4 : 2, 3};
+    const int nst = integ == JF_RK3 ? 3 : (integ == JF_RK2 ? 2 : 1);
+    for (int q = 0; q < nst; ++q) {
+      e = sv.launch_batch(sims, work, h->nwork, codes[q], g, h->flag, h->batch_blocks, s);
       if (e != cudaSuccess) return cuda_fail(h, e, "batch: stage launch");
+    }
+    if (integ == JF_EULER) {
+      batch_copy_kernel<T><<<dim3((unsigned)h->sms, (unsigned)h->nsim), 256, 0, s>>>(sims);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "batch: copy launch");
     }
   }
   if (dt_out) {
@@ -207,12 +227,12 @@ int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   std::vector<int> list;
   int bx = 0, by = 0;
   if (h->scheme.dtype == JF_F32) {
-    list = batch_variant_list<float>(h->dim, visc);
+    list = batch_variant_list<float>(h->dim, visc, general_scheme(h->scheme));
     int c = 0;
     const StageVariant<float>* tab = stage_variants<float>(&c);
     if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
   } else {
-    list = batch_variant_list<double>(h->dim, visc);
+    list = batch_variant_list<double>(h->dim, visc, general_scheme(h->scheme));
     int c = 0;
     const StageVariant<double>* tab = stage_variants<double>(&c);
     if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
@@ -230,8 +250,8 @@ extern "C" {
 
 jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, const jf_scheme* scheme,
                           jf_handle* out) {
-  if (!grids || !gas || !scheme || !out || nsim < 1) {
-    set_error(nullptr, "jf_batch_create: null argument or nsim < 1");
+  if (!grids || !gas || !scheme || !out || nsim < 1 || nsim > 65535) {
+    set_error(nullptr, "jf_batch_create: null argument or nsim outside 1..65535");
     return JF_ERR_ARG;
   }
   *out = nullptr;

@@ -63,7 +63,22 @@ jf_status check_physics(jf_ctx* h, const jf_gas& gas, const jf_scheme& s) {
   if (s.heat && !(gas.Pr > 0.0)) { set_error(h, "gas: heat flux needs Pr > 0"); return JF_ERR_ARG; }
   if (s.dtype != JF_F32 && s.dtype != JF_F64) { set_error(h, "scheme: dtype must be JF_F32 or JF_F64"); return JF_ERR_ARG; }
   if (!(s.weno_eps > 0.0) || !(s.cfl > 0.0)) { set_error(h, "scheme: need weno_eps > 0 and cfl > 0"); return JF_ERR_ARG; }
-  if (s.signal_speed != JF_EINFELDT) { set_error(h, "scheme: only Einfeldt signal speeds are built"); return JF_ERR_UNSUPPORTED; }
+  if (s.signal_speed < JF_EINFELDT || s.signal_speed > JF_TORO) {
+    set_error(h, "scheme: signal_speed must be JF_EINFELDT, JF_DAVIS or JF_TORO");
+    return JF_ERR_ARG;
+  }
+  if (s.flux < JF_FLUX_HLLC || s.flux > JF_FLUX_RUSANOV) {
+    set_error(h, "scheme: flux must be JF_FLUX_HLLC, JF_FLUX_HLL or JF_FLUX_RUSANOV");
+    return JF_ERR_ARG;
+  }
+  if (s.recon != JF_WENO5_JS && s.recon != JF_WENO5_Z) {
+    set_error(h, "scheme: recon must be JF_WENO5_JS or JF_WENO5_Z");
+    return JF_ERR_ARG;
+  }
+  if (s.integrator < JF_RK3 || s.integrator > JF_EULER) {
+    set_error(h, "scheme: integrator must be JF_RK3, JF_RK2 or JF_EULER");
+    return JF_ERR_ARG;
+  }
   return JF_OK;
 }
 
@@ -87,6 +102,9 @@ Gas<T> make_gas(const jf_gas& gas, const jf_scheme& s) {
   g.lambda = (T)conductivity(gas, s);
   g.eps = (T)s.weno_eps;
   g.safe = s.safe_recon ? 1 : 0;
+  g.flux = s.flux;
+  g.recon = s.recon;
+  g.speeds = s.signal_speed;
   return g;
 }
 template Gas<float> make_gas<float>(const jf_gas&, const jf_scheme&);
@@ -119,13 +137,17 @@ int reduce_blocks(long long N, int sms) {
 // Variant selection.  A variant = (compiled tile shape, z chunk).
 static const int kZChunks[] = {32, 16, 64, 8};
 
+bool general_scheme(const jf_scheme& s) {
+  return s.flux != JF_FLUX_HLLC || s.signal_speed != JF_EINFELDT || s.recon != JF_WENO5_JS;
+}
+
 template <typename T>
-std::vector<std::pair<int, int>> variant_list(int dim, bool visc) {
+std::vector<std::pair<int, int>> variant_list(int dim, bool visc, bool general) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
   std::vector<std::pair<int, int>> out;
   for (int i = 0; i < count; ++i) {
-    if (tab[i].dim != dim || tab[i].visc != visc) continue;
+    if (tab[i].dim != dim || tab[i].visc != visc || tab[i].general != general) continue;
     if (dim == 3)
       for (int z : kZChunks) out.emplace_back(i, z);
     else
@@ -137,7 +159,7 @@ std::vector<std::pair<int, int>> variant_list(int dim, bool visc) {
 template <typename T>
 jf_status select_variant(jf_ctx* h, int v, bool prepare) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = variant_list<T>(h->dim, visc);
+  auto list = variant_list<T>(h->dim, visc, general_scheme(h->scheme));
   if (list.empty()) { set_error(h, "no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
   if (v < 0) v = 0;
   if (v >= (int)list.size()) { set_error(h, "variant index out of range"); return JF_ERR_ARG; }
@@ -156,7 +178,7 @@ jf_status select_variant(jf_ctx* h, int v, bool prepare) {
 template <typename T>
 int describe_variant(jf_ctx* h, int v, char* buf, int len) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = variant_list<T>(h->dim, visc);
+  auto list = variant_list<T>(h->dim, visc, general_scheme(h->scheme));
   if (v < 0 || v >= (int)list.size()) return (int)list.size();
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
@@ -230,7 +252,9 @@ template cudaError_t launch_cfl_batch<float>(const void*, const void*, int, cons
 template cudaError_t launch_cfl_batch<double>(const void*, const void*, int, const CflArgs*, ReduceScratch*, double*,
                                               int*, cudaStream_t);
 
-// One RK3 step: optional CFL reduction, then the three Shu-Osher stages.
+// One time step of the scheme's integrator: optional CFL reduction, then
+// the Shu-Osher stages (TVD-RK3: three; TVD-RK2: two; Euler: one stage into
+// U1 and a copy back, since a stage cannot write over its own input).
 template <typename T>
 jf_status step_impl(jf_ctx* h, void* U, const double* dt_dev, double* dt_used, cudaStream_t s) {
   const double* dt = dt_dev;
@@ -251,6 +275,15 @@ jf_status step_impl(jf_ctx* h, void* U, const double* dt_dev, double* dt_used, c
   // U1 = Un + dt L(Un)
   A.Us = Un; A.Un = nullptr; A.out = U1; A.a = T(0); A.b = T(1);
   if ((st = launch<T>(h, A, s)) != JF_OK) return st;
+  if (h->scheme.integrator == JF_EULER) {
+    const cudaError_t e = cudaMemcpyAsync(Un, U1, 5 * h->N * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? JF_OK : cuda_fail(h, e, "cudaMemcpyAsync(Euler step)");
+  }
+  if (h->scheme.integrator == JF_RK2) {
+    // U^{n+1} = 1/2 Un + 1/2 (U1 + dt L(U1)), written over Un
+    A.Us = U1; A.Un = Un; A.out = Un; A.a = T(0.5); A.b = T(0.5);
+    return launch<T>(h, A, s);
+  }
   // U2 = 3/4 Un + 1/4 (U1 + dt L(U1))
   A.Us = U1; A.Un = Un; A.out = U2; A.a = T(0.75); A.b = T(0.25);
   if ((st = launch<T>(h, A, s)) != JF_OK) return st;

@@ -81,6 +81,8 @@ jf_status check_physics(jf_ctx* h, const jf_gas& gas, const jf_scheme& s);
 double spacing(const jf_grid& g, int d);
 double conductivity(const jf_gas& gas, const jf_scheme& s);
 bool dissipative(const jf_gas& gas, const jf_scheme& s);
+// a Table 2 variant that needs the run-time-scheme kernels
+bool general_scheme(const jf_scheme& s);
 CflArgs make_cfl(const jf_grid& g, const jf_gas& gas, const jf_scheme& s);
 int reduce_blocks(long long N, int sms);
 bool aligned16(const void* p);

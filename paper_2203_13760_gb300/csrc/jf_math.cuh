@@ -4,9 +4,13 @@
 // References (arXiv 2203.13760):
 //   primitives        Section 2, Eq. (StiffenedGas) with B = 0
 //   weno5             Section 3.3 (High-order Godunov approach, step 1),
-//                     WENO5-JS of Jiang & Shu (1996)
+//                     WENO5-JS of Jiang & Shu (1996) or WENO5-Z of Borges et
+//                     al. (2008) (Table 2)
 //   hllc              Section 3.3 steps 2-3, Eq. (ApproxRiemannSolver): HLLC
-//                     (Toro 1994) with Einfeldt (1988) signal speeds
+//                     (Toro 1994) with Einfeldt (1988), Davis (1988) or Toro
+//                     (1994) signal speeds (Table 2)
+//   hll, rusanov      Table 2: HLL (Harten, Lax, van Leer 1983) and local
+//                     Lax-Friedrichs
 //   df4 / dc4 / rc4   Section 3.4 fourth-order face derivative, cell-centre
 //                     derivative and central interpolation to the face
 #pragma once
@@ -25,8 +29,11 @@ struct Gas {
   T inv_R;     // 1 / R
   T mu;        // dynamic viscosity (0 if inviscid)
   T lambda;    // heat conductivity
-  T eps;       // WENO5-JS epsilon
+  T eps;       // WENO5 epsilon
   int safe;    // first-order fallback for non-positive reconstructed rho / p
+  int flux;    // 0 HLLC, 1 HLL, 2 Rusanov (local Lax-Friedrichs)
+  int recon;   // 0 WENO5-JS, 1 WENO5-Z
+  int speeds;  // 0 Einfeldt, 1 Davis, 2 Toro (PVRS)
 };
 
 template <typename T> JF_HD T tsqrt(T x);
@@ -52,8 +59,10 @@ template <typename T> JF_HD T tmax(T a, T b) { return a < b ? b : a; }
 // Candidate stencils q_k, smoothness indicators beta_k, weights
 // alpha_k = d_k / (eps + beta_k)^2 with d = (1/10, 6/10, 3/10),
 // omega_k = alpha_k / sum(alpha).
+// With z != 0 the WENO5-Z weights of Borges et al. (2008) replace the JS
+// ones: tau5 = |beta_0 - beta_2|, alpha_k = d_k (1 + tau5 / (eps + beta_k)).
 template <typename T>
-JF_HD T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
+JF_HD T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps, int z = 0) {
   const T sixth = T(1) / T(6);
   const T q0 = (T(2) * vm2 - T(7) * vm1 + T(11) * v0) * sixth;
   const T q1 = (-vm1 + T(5) * v0 + T(2) * vp1) * sixth;
@@ -67,19 +76,37 @@ JF_HD T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
   const T b2 = c13 * d2 * d2 + T(0.25) * e2 * e2;
   const T t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
   if constexpr (sizeof(T) == 8) {
-    // alpha_k scaled by prod_j (eps + beta_j)^2: one division instead of four
-    // (the squares are >= eps^4, far inside the FP64 range)
-    const T s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
-    const T a0 = T(0.1) * s1 * s2;
-    const T a1 = T(0.6) * s0 * s2;
-    const T a2 = T(0.3) * s0 * s1;
+    // alpha_k scaled by a common product of the (eps + beta_j) terms: one
+    // division instead of four (the factors are >= eps, far inside the FP64
+    // range).  JS: alpha_k ~ d_k / t_k^2, scaled by (t0 t1 t2)^2; Z:
+    // alpha_k ~ d_k (t_k + tau5) / t_k, scaled by t0 t1 t2.
+    T a0, a1, a2;
+    if (z) {
+      const T tau = fabs(b0 - b2);
+      a0 = T(0.1) * (t0 + tau) * t1 * t2;
+      a1 = T(0.6) * (t1 + tau) * t0 * t2;
+      a2 = T(0.3) * (t2 + tau) * t0 * t1;
+    } else {
+      const T s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
+      a0 = T(0.1) * s1 * s2;
+      a1 = T(0.6) * s0 * s2;
+      a2 = T(0.3) * s0 * s1;
+    }
     return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
   } else {
-    const T a0 = T(0.1) / (t0 * t0);
-    const T a1 = T(0.6) / (t1 * t1);
-    const T a2 = T(0.3) / (t2 * t2);
-    const T inv = T(1) / (a0 + a1 + a2);
-    return (a0 * q0 + a1 * q1 + a2 * q2) * inv;
+    T r0, r1, r2;
+    if (z) {
+      const T tau = fabs(b0 - b2);
+      r0 = (t0 + tau) * trcp(t0);
+      r1 = (t1 + tau) * trcp(t1);
+      r2 = (t2 + tau) * trcp(t2);
+    } else {
+      r0 = trcp(t0 * t0);
+      r1 = trcp(t1 * t1);
+      r2 = trcp(t2 * t2);
+    }
+    const T a0 = T(0.1) * r0, a1 = T(0.6) * r1, a2 = T(0.3) * r2;
+    return (a0 * q0 + a1 * q1 + a2 * q2) * trcp(a0 + a1 + a2);
   }
 }
 
@@ -96,8 +123,11 @@ JF_HD T weno5(T vm2, T vm1, T v0, T vp1, T vp2, T eps) {
 //  * every eps + beta_k is scaled by 12/13 (a common factor of the three
 //    alpha_k, which cancels in omega_k), so t_k = d_k^2 + 3/13 e_k^2 + 12/13 eps;
 //  * with r_k = 1 / t_k^2 and alpha_k scaled by 10/3 (weights 1/3, 2, 1),
-//    v^ = v0 + (r0 delta0/18 + r1 delta1/3 + r2 delta2/6) / (r0/3 + 2 r1 + r2).
-__device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, float2 vp1, float2 vp2, float eps) {
+//    v^ = v0 + (r0 delta0/18 + r1 delta1/3 + r2 delta2/6) / (r0/3 + 2 r1 + r2);
+//  * WENO5-Z (z != 0): r_k = (t_k + tau) / t_k with tau = |t_0 - t_2| (the
+//    same 12/13 scaling of tau5 = |beta_0 - beta_2|).
+__device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, float2 vp1, float2 vp2, float eps,
+                                             int z = 0) {
   auto c = [](float x) { return make_float2(x, x); };
   const float2 m1 = c(-1.0f);
   const float2 D1 = __ffma2_rn(m1, vm1, vm2);
@@ -113,9 +143,18 @@ __device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, 
   const float2 t2 = __ffma2_rn(d2, d2, __ffma2_rn(__fmul2_rn(k3, e2), e2, ke));
   // approximate reciprocals (t_k^2 >= (12/13 eps)^2 > 0, so the sum is > 0)
   auto rcp2 = [](float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); };
-  const float2 r0 = rcp2(__fmul2_rn(t0, t0));
-  const float2 r1 = rcp2(__fmul2_rn(t1, t1));
-  const float2 r2 = rcp2(__fmul2_rn(t2, t2));
+  float2 r0, r1, r2;
+  if (z) {
+    const float2 d02 = __ffma2_rn(m1, t2, t0);
+    const float2 tau = make_float2(fabsf(d02.x), fabsf(d02.y));
+    r0 = __fmul2_rn(__fadd2_rn(t0, tau), rcp2(t0));
+    r1 = __fmul2_rn(__fadd2_rn(t1, tau), rcp2(t1));
+    r2 = __fmul2_rn(__fadd2_rn(t2, tau), rcp2(t2));
+  } else {
+    r0 = rcp2(__fmul2_rn(t0, t0));
+    r1 = rcp2(__fmul2_rn(t1, t1));
+    r2 = rcp2(__fmul2_rn(t2, t2));
+  }
   const float2 g0 = __ffma2_rn(c(5.0f / 18.0f), D2, __fmul2_rn(c(1.0f / 9.0f), D1));
   const float2 g1 = __ffma2_rn(c(2.0f / 3.0f), D3, __fmul2_rn(c(1.0f / 3.0f), D2));
   const float2 g2 = __ffma2_rn(c(2.0f / 3.0f), D3, __fmul2_rn(c(1.0f / 6.0f), D4));
@@ -124,38 +163,90 @@ __device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, 
   return __ffma2_rn(num, rcp2(den), v0);
 }
 
+// Signal speeds S_L <= S_R at a face along axis D (Table 2 estimates), from
+// the side states W = [rho, u, v, w, p] and their total energies E, 1/rho
+// and sound speeds c:
+//   Einfeldt (1988): Roe averages (weights sqrt(rho)) u~, H~ (H = (E + p)/rho),
+//     c~ = sqrt((gamma - 1)(H~ - |u~|^2/2)); S_L = min(u_L - c_L, u~ - c~),
+//     S_R = max(u_R + c_R, u~ + c~);
+//   Davis (1988): S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R);
+//   Toro (1994): PVRS pressure p* = max(0, (p_L + p_R)/2 - (u_R - u_L)(rho_L + rho_R)(c_L + c_R)/8);
+//     q_K = 1 if p* <= p_K else sqrt(1 + (gamma + 1)/(2 gamma)(p*/p_K - 1));
+//     S_L = u_L - c_L q_L, S_R = u_R + c_R q_R.
+template <typename T, int D>
+JF_HD void signal_speeds(const T WL[5], const T WR[5], const Gas<T>& g, int speeds, T EL, T ER, T irL, T irR, T cL,
+                         T cR, T& SL, T& SR) {
+  const T rL = WL[0], rR = WR[0], pL = WL[4], pR = WR[4];
+  const T unL = WL[1 + D], unR = WR[1 + D];
+  if (speeds == 1) {
+    SL = tmin(unL - cL, unR - cR);
+    SR = tmax(unL + cL, unR + cR);
+  } else if (speeds == 2) {
+    const T ps = tmax(T(0), T(0.5) * (pL + pR) - T(0.125) * (unR - unL) * (rL + rR) * (cL + cR));
+    const T k = (g.gamma + T(1)) * trcp(T(2) * g.gamma);
+    const T qL = ps > pL ? tsqrt(T(1) + k * (ps * trcp(pL) - T(1))) : T(1);
+    const T qR = ps > pR ? tsqrt(T(1) + k * (ps * trcp(pR) - T(1))) : T(1);
+    SL = unL - cL * qL;
+    SR = unR + cR * qR;
+  } else {
+    const T sL = tsqrt(rL), sR = tsqrt(rR);
+    const T inv_s = trcp(sL + sR);
+    const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
+    const T u0 = (sL * WL[1] + sR * WR[1]) * inv_s;
+    const T u1 = (sL * WL[2] + sR * WR[2]) * inv_s;
+    const T u2 = (sL * WL[3] + sR * WR[3]) * inv_s;
+    const T Ht = (sL * HL + sR * HR) * inv_s;
+    const T ct = tsqrt(g.gm1 * (Ht - T(0.5) * (u0 * u0 + u1 * u1 + u2 * u2)));
+    const T un_t = D == 0 ? u0 : (D == 1 ? u1 : u2);
+    SL = tmin(unL - cL, un_t - ct);
+    SR = tmax(unR + cR, un_t + ct);
+  }
+}
+
+// Total energy, 1/rho and sound speed of one side.
+template <typename T>
+JF_HD void side_state(const T W[5], const Gas<T>& g, T& E, T& ir, T& c) {
+  E = W[4] * g.inv_gm1 + T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  ir = trcp(W[0]);
+  c = tsqrt(g.gamma * W[4] * ir);
+}
+
+// Physical flux along D and conservative state of one side.
+template <typename T, int D>
+JF_HD void side_flux(const T W[5], T E, T F[5], T U[5]) {
+  const T un = W[1 + D], mass = W[0] * un;
+  F[0] = mass;
+  F[1] = mass * W[1];
+  F[2] = mass * W[2];
+  F[3] = mass * W[3];
+  F[1 + D] += W[4];
+  F[4] = un * (E + W[4]);
+  U[0] = W[0];
+  U[1] = W[0] * W[1];
+  U[2] = W[0] * W[2];
+  U[3] = W[0] * W[3];
+  U[4] = E;
+}
+
 // HLLC flux along axis D from the reconstructed primitive states
-// W = [rho, u, v, w, p] left (WL) and right (WR) of the face.
+// W = [rho, u, v, w, p] left (WL) and right (WR) of the face; `speeds` picks
+// the signal speed estimate (0 Einfeldt, 1 Davis, 2 Toro).
 //   U_K, F_K                conservative state and physical flux of side K
-//   Roe averages (weights sqrt(rho)), c~ = sqrt((gamma-1)(H~ - |u~|^2/2))
-//   S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~)   (Einfeldt)
+//   S_L, S_R                signal speeds of the selected estimate
 //   S*  = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R))
 //         / (rho_L (S_L - u_L) - rho_R (S_R - u_R))
 //   F*_K = F_K + S_K (U*_K - U_K),
 //   U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S*, u_t, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))]
 template <typename T, int D>
-JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
+JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speeds = 0) {
   const T rL = WL[0], rR = WR[0], pL = WL[4], pR = WR[4];
   const T unL = WL[1 + D], unR = WR[1 + D];
-  const T kL = T(0.5) * rL * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
-  const T kR = T(0.5) * rR * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]);
-  const T EL = pL * g.inv_gm1 + kL;
-  const T ER = pR * g.inv_gm1 + kR;
   // every division goes through a reciprocal (1/rho of each side shared)
-  const T irL = trcp(rL), irR = trcp(rR);
-  const T cL = tsqrt(g.gamma * pL * irL);
-  const T cR = tsqrt(g.gamma * pR * irR);
-  const T sL = tsqrt(rL), sR = tsqrt(rR);
-  const T inv_s = trcp(sL + sR);
-  const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
-  const T u0 = (sL * WL[1] + sR * WR[1]) * inv_s;
-  const T u1 = (sL * WL[2] + sR * WR[2]) * inv_s;
-  const T u2 = (sL * WL[3] + sR * WR[3]) * inv_s;
-  const T Ht = (sL * HL + sR * HR) * inv_s;
-  const T ct = tsqrt(g.gm1 * (Ht - T(0.5) * (u0 * u0 + u1 * u1 + u2 * u2)));
-  const T un_t = D == 0 ? u0 : (D == 1 ? u1 : u2);
-  const T SL = tmin(unL - cL, un_t - ct);
-  const T SR = tmax(unR + cR, un_t + ct);
+  T EL, ER, irL, irR, cL, cR;
+  side_state(WL, g, EL, irL, cL);
+  side_state(WR, g, ER, irR, cR);
+  T SL, SR;
+  signal_speeds<T, D>(WL, WR, g, speeds, EL, ER, irL, irR, cL, cR, SL, SR);
   const T mL = rL * (SL - unL), mR = rR * (SR - unR);
   const T Ss = (pR - pL + mL * unL - mR * unR) * trcp(mL - mR);
   // side selection: F_L if 0 <= S_L; F*_L if S_L < 0 <= S*; F*_R if S* < 0 < S_R; F_R if S_R <= 0
@@ -180,6 +271,55 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) F[q] = Fk[q];
   }
+}
+
+// HLL flux (Harten, Lax, van Leer 1983): F_L if 0 <= S_L, F_R if S_R <= 0,
+// else (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
+template <typename T, int D>
+JF_HD void hll(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speeds = 0) {
+  T EL, ER, irL, irR, cL, cR;
+  side_state(WL, g, EL, irL, cL);
+  side_state(WR, g, ER, irR, cR);
+  T SL, SR;
+  signal_speeds<T, D>(WL, WR, g, speeds, EL, ER, irL, irR, cL, cR, SL, SR);
+  T FL[5], FR[5], UL[5], UR[5];
+  side_flux<T, D>(WL, EL, FL, UL);
+  side_flux<T, D>(WR, ER, FR, UR);
+  if (SL >= T(0)) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = FL[q];
+  } else if (SR <= T(0)) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = FR[q];
+  } else {
+    const T inv = trcp(SR - SL);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) * inv;
+  }
+}
+
+// Local Lax-Friedrichs (Rusanov): a = max(|u_L| + c_L, |u_R| + c_R),
+// F = (F_L + F_R)/2 - a (U_R - U_L)/2.
+template <typename T, int D>
+JF_HD void rusanov(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
+  T EL, ER, irL, irR, cL, cR;
+  side_state(WL, g, EL, irL, cL);
+  side_state(WR, g, ER, irR, cR);
+  const T a = tmax(fabs(WL[1 + D]) + cL, fabs(WR[1 + D]) + cR);
+  T FL[5], FR[5], UL[5], UR[5];
+  side_flux<T, D>(WL, EL, FL, UL);
+  side_flux<T, D>(WR, ER, FR, UR);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) F[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * a * (UR[q] - UL[q]);
+}
+
+// The Riemann solver and signal speeds of the configuration (uniform branch;
+// the default kernels call hllc with Einfeldt speeds directly).
+template <typename T, int D>
+JF_HD void riemann_flux(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
+  if (g.flux == 1) hll<T, D>(WL, WR, g, F, g.speeds);
+  else if (g.flux == 2) rusanov<T, D>(WL, WR, g, F);
+  else hllc<T, D>(WL, WR, g, F, g.speeds);
 }
 
 // Section 3.4 stencils (without the 1/h factor).

@@ -182,10 +182,13 @@ template <> struct Roles<2> {
 
 // Net flux NF = F^d - F through the face between the cell at shared-memory
 // position (x0, y0, plane 0) and its neighbour along D.
-template <typename T, int D, int BX, int BY, int DIM, bool VISC>
+// GEN = false: the default scheme (WENO5-JS, HLLC, Einfeldt speeds) compiled
+// alone; GEN = true: the Table 2 variants chosen at run time from g.
+template <typename T, int D, int BX, int BY, int DIM, bool VISC, bool GEN>
 __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
                                           const Gas<T>& g, const T inv_h[3], T NF[5]) {
   using Ro = Roles<D>;
+  const int recon = GEN ? g.recon : 0;
   auto val = [&](int c, int n, int t1, int t2) -> T {
     int x, y, e;
     Ro::map(n, t1, t2, x, y, e);
@@ -199,12 +202,12 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
     const T v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0), v5 = val(c, 3, 0, 0);
     if constexpr (sizeof(T) == 4) {
       const float2 r = weno5_pair(make_float2(v0, v5), make_float2(v1, v4), make_float2(v2, v3), make_float2(v3, v2),
-                                  make_float2(v4, v1), g.eps);
+                                  make_float2(v4, v1), g.eps, recon);
       Wm[c] = r.x;
       Wp[c] = r.y;
     } else {
-      Wm[c] = weno5(v0, v1, v2, v3, v4, g.eps);
-      Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps);
+      Wm[c] = weno5(v0, v1, v2, v3, v4, g.eps, recon);
+      Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps, recon);
     }
   }
   if (g.safe) {
@@ -218,7 +221,8 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
     }
   }
   T F[5];
-  hllc<T, D>(Wm, Wp, g, F);
+  if constexpr (GEN) riemann_flux<T, D>(Wm, Wp, g, F);
+  else hllc<T, D>(Wm, Wp, g, F, 0);
 #pragma unroll
   for (int c = 0; c < 5; ++c) NF[c] = -F[c];
   if constexpr (VISC) {
@@ -339,7 +343,7 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
 // for its cells.  Shared memory: the ring and the face buffers.  All threads
 // of the CTA call it; it starts and ends without pending shared-memory reads
 // that a following call could disturb (the first barrier inside orders them).
-template <typename T, int DIM, bool VISC, int BX, int BY>
+template <typename T, int DIM, bool VISC, int BX, int BY, bool GEN>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& g, int bx, int by, int bz,
                                            T* smem) {
   using G = Geo<BX, BY, DIM, VISC>;
@@ -398,7 +402,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     // lower face of plane z0 = upper face of plane z0 - 1 (slot 2); plane
     // offset -3 is never read
     set_view(5);
-    if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+    if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, GEN>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
     __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
     load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, z0 + 3);
     if (z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC>(A, next, gx0, gy0, z0 + 4);
@@ -424,20 +428,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
 
     if (xf_x >= 0) {
       T NF[5];
-      face_flux<T, 0, BX, BY, DIM, VISC>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
+      face_flux<T, 0, BX, BY, DIM, VISC, GEN>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
       const int t = xf_y * (BX + 1) + xf_x;
 #pragma unroll
       for (int c = 0; c < 5; ++c) Fx[c * G::NFX + t] = NF[c];
     }
     if (DIM >= 2) {
       T NF[5];
-      face_flux<T, 1, BX, BY, DIM, VISC>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
+      face_flux<T, 1, BX, BY, DIM, VISC, GEN>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
       const int t = yf_y * BX + yf_x;
 #pragma unroll
       for (int c = 0; c < 5; ++c) Fy[c * G::NFY + t] = NF[c];
     }
     T NFz_hi[5];
-    if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+    if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, GEN>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
     __syncthreads();
 
     if (own) {
@@ -501,10 +505,11 @@ struct WorkItem {
 //    work list in a static round robin (every item is one full tile of
 //    equal cost); the grid arguments come from the simulation's descriptor,
 //    stage 1: U1 = U + dt L(U); stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1));
-//    stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2)).
+//    stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2)); stage 4 (TVD-RK2):
+//    U = 1/2 U + 1/2 (U1 + dt L(U1)).
 // Both forms reach the tile computation through the same call below, so a
 // simulation advanced in a batch is bitwise the one advanced alone.
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, bool GEN>
 __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
     stage_kernel(const StageArgs<T> A0, const SimDesc<T>* __restrict__ sims, const WorkItem* __restrict__ work,
                  int nwork, int stage, const Gas<T> g) {
@@ -530,18 +535,22 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
       A.rhs_only = 0;
       A.zchunk = d.nz;
       const T third = T(1.0 / 3.0), two_thirds = T(2.0 / 3.0);
-      A.Us = stage == 1 ? d.U : (stage == 2 ? d.U1 : d.U2);
-      A.Un = stage == 1 ? nullptr : d.U;
-      A.out = stage == 1 ? d.U1 : (stage == 2 ? d.U2 : d.U);
-      A.a = stage == 1 ? T(0) : (stage == 2 ? T(0.75) : third);
-      A.b = stage == 1 ? T(1) : (stage == 2 ? T(0.25) : two_thirds);
+      if (stage == 1) {         // U1 = U + dt L(U)  (every integrator)
+        A.Us = d.U; A.Un = nullptr; A.out = d.U1; A.a = T(0); A.b = T(1);
+      } else if (stage == 2) {  // TVD-RK3: U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+        A.Us = d.U1; A.Un = d.U; A.out = d.U2; A.a = T(0.75); A.b = T(0.25);
+      } else if (stage == 3) {  // TVD-RK3: U = 1/3 U + 2/3 (U2 + dt L(U2))
+        A.Us = d.U2; A.Un = d.U; A.out = d.U; A.a = third; A.b = two_thirds;
+      } else {                  // TVD-RK2: U = 1/2 U + 1/2 (U1 + dt L(U1))
+        A.Us = d.U1; A.Un = d.U; A.out = d.U; A.a = T(0.5); A.b = T(0.5);
+      }
       bx = w.bx;
       by = w.by;
       bz = 0;
     } else if (item != (int)blockIdx.x) {
       break;
     }
-    stage_tile<T, DIM, VISC, BX, BY>(A, g, bx, by, bz, reinterpret_cast<T*>(smem_raw));
+    stage_tile<T, DIM, VISC, BX, BY, GEN>(A, g, bx, by, bz, reinterpret_cast<T*>(smem_raw));
   }
 }
 

@@ -2,31 +2,41 @@
 // compiled with approximate division and square root (-prec-div=false
 // -prec-sqrt=false -ftz=true): the FP32 path meets its parity bar with them
 // and they cut the instruction count of WENO5 / HLLC substantially.
+#include <vector>
+
 #include "stage_inst.cuh"
 
 namespace jf {
 
+// The default-scheme kernels (WENO5-JS, HLLC, Einfeldt) of every tile shape,
+// then the run-time-scheme kernels of stage_f32_gen.cu (one tile shape each).
 template <>
 const StageVariant<float>* stage_variants<float>(int* count) {
-  static const StageVariant<float> table[] = {
+  static const std::vector<StageVariant<float>> table = [] {
+    std::vector<StageVariant<float>> v = {
       // 3D (the first entry per configuration is the default)
-      make_variant<float, 3, true, 32, 8, 2>(),
-      make_variant<float, 3, true, 32, 6, 3>(),
-      make_variant<float, 3, true, 32, 4, 3>(),
-      make_variant<float, 3, false, 32, 8, 2>(),
-      make_variant<float, 3, false, 32, 6, 3>(),
-      make_variant<float, 3, false, 32, 4, 3>(),
+      make_variant<float, 3, true, 32, 8, 2, false>(),
+      make_variant<float, 3, true, 32, 6, 3, false>(),
+      make_variant<float, 3, true, 32, 4, 3, false>(),
+      make_variant<float, 3, false, 32, 8, 2, false>(),
+      make_variant<float, 3, false, 32, 6, 3, false>(),
+      make_variant<float, 3, false, 32, 4, 3, false>(),
       // 2D
-      make_variant<float, 2, true, 32, 8, 2>(),
-      make_variant<float, 2, true, 32, 4, 4>(),
-      make_variant<float, 2, false, 32, 8, 2>(),
-      make_variant<float, 2, false, 32, 4, 4>(),
+      make_variant<float, 2, true, 32, 8, 2, false>(),
+      make_variant<float, 2, true, 32, 4, 4, false>(),
+      make_variant<float, 2, false, 32, 8, 2, false>(),
+      make_variant<float, 2, false, 32, 4, 4, false>(),
       // 1D
-      make_variant<float, 1, true, 128, 1, 2>(),
-      make_variant<float, 1, false, 128, 1, 2>(),
-  };
-  *count = (int)(sizeof(table) / sizeof(table[0]));
-  return table;
+      make_variant<float, 1, true, 128, 1, 2, false>(),
+      make_variant<float, 1, false, 128, 1, 2, false>(),
+    };
+    int ng = 0;
+    const StageVariant<float>* gen = general_variants_f32(&ng);
+    v.insert(v.end(), gen, gen + ng);
+    return v;
+  }();
+  *count = (int)table.size();
+  return table.data();
 }
 
 }  // namespace jf

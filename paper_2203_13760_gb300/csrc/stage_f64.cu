@@ -1,27 +1,37 @@
 // Instantiations of the stage kernel in FP64 (IEEE division and square root).
+#include <vector>
+
 #include "stage_inst.cuh"
 
 namespace jf {
 
+// The default-scheme kernels (WENO5-JS, HLLC, Einfeldt) of every tile shape,
+// then the run-time-scheme kernels of stage_f64_gen.cu (one tile shape each).
 template <>
 const StageVariant<double>* stage_variants<double>(int* count) {
-  static const StageVariant<double> table[] = {
+  static const std::vector<StageVariant<double>> table = [] {
+    std::vector<StageVariant<double>> v = {
       // 3D (the first entry per configuration is the default)
-      make_variant<double, 3, true, 32, 4, 1>(),
-      make_variant<double, 3, true, 32, 2, 2>(),
-      make_variant<double, 3, false, 32, 4, 1>(),
-      make_variant<double, 3, false, 32, 2, 2>(),
+      make_variant<double, 3, true, 32, 4, 1, false>(),
+      make_variant<double, 3, true, 32, 2, 2, false>(),
+      make_variant<double, 3, false, 32, 4, 1, false>(),
+      make_variant<double, 3, false, 32, 2, 2, false>(),
       // 2D
-      make_variant<double, 2, true, 32, 8, 1>(),
-      make_variant<double, 2, true, 32, 4, 2>(),
-      make_variant<double, 2, false, 32, 8, 1>(),
-      make_variant<double, 2, false, 32, 4, 2>(),
+      make_variant<double, 2, true, 32, 8, 1, false>(),
+      make_variant<double, 2, true, 32, 4, 2, false>(),
+      make_variant<double, 2, false, 32, 8, 1, false>(),
+      make_variant<double, 2, false, 32, 4, 2, false>(),
       // 1D
-      make_variant<double, 1, true, 128, 1, 1>(),
-      make_variant<double, 1, false, 128, 1, 1>(),
-  };
-  *count = (int)(sizeof(table) / sizeof(table[0]));
-  return table;
+      make_variant<double, 1, true, 128, 1, 1, false>(),
+      make_variant<double, 1, false, 128, 1, 1, false>(),
+    };
+    int ng = 0;
+    const StageVariant<double>* gen = general_variants_f64(&ng);
+    v.insert(v.end(), gen, gen + ng);
+    return v;
+  }();
+  *count = (int)table.size();
+  return table.data();
 }
 
 }  // namespace jf

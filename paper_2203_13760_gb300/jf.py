@@ -42,7 +42,15 @@ class GasParams(ctypes.Structure):
 class Scheme(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("weno_eps", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("viscous", ctypes.c_int), ("heat", ctypes.c_int), ("signal_speed", ctypes.c_int),
-                ("safe_recon", ctypes.c_int)]
+                ("safe_recon", ctypes.c_int), ("flux", ctypes.c_int), ("recon", ctypes.c_int),
+                ("integrator", ctypes.c_int)]
+
+
+# scheme options of include/jf.h (0: the default configuration)
+FLUX = {"hllc": 0, "hll": 1, "rusanov": 2}
+RECON = {"weno5-js": 0, "weno5-z": 1}
+SPEEDS = {"einfeldt": 0, "davis": 1, "toro": 2}
+INTEGRATOR = {"rk3": 0, "rk2": 1, "euler": 2}
 
 
 # name -> (restype, argtypes) of every entry point in include/jf.h
@@ -115,11 +123,14 @@ def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1)) 
     return g
 
 
-def make_scheme(dtype="f32", eps=1e-6, cfl=0.5, viscous=False, heat=False, safe=False) -> Scheme:
+def make_scheme(dtype="f32", eps=1e-6, cfl=0.5, viscous=False, heat=False, safe=False, flux="hllc",
+                recon="weno5-js", speeds="einfeldt", integrator="rk3") -> Scheme:
     s = Scheme()
     s.dtype = JF_F32 if dtype in ("f32", "float32") else JF_F64
     s.weno_eps, s.cfl = float(eps), float(cfl)
-    s.viscous, s.heat, s.signal_speed, s.safe_recon = int(bool(viscous)), int(bool(heat)), 0, int(bool(safe))
+    s.viscous, s.heat, s.safe_recon = int(bool(viscous)), int(bool(heat)), int(bool(safe))
+    s.signal_speed, s.flux, s.recon = SPEEDS[speeds], FLUX[flux], RECON[recon]
+    s.integrator = INTEGRATOR[integrator]
     return s
 
 
@@ -127,11 +138,12 @@ class Solver:
     """One grid (jf_init).  Parameters mirror jf_grid / jf_gas / jf_scheme."""
 
     def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gamma=1.4, R=1.0,
-                 mu=0.0, Pr=0.72, dtype="f32", eps=1e-6, cfl=0.5, viscous=False, heat=False, safe=False):
+                 mu=0.0, Pr=0.72, dtype="f32", eps=1e-6, cfl=0.5, viscous=False, heat=False, safe=False,
+                 flux="hllc", recon="weno5-js", speeds="einfeldt", integrator="rk3"):
         import torch
         self.grid = make_grid(n, lo, hi, bc)
         self.gas = GasParams(float(gamma), float(R), float(mu), float(Pr))
-        self.scheme = make_scheme(dtype, eps, cfl, viscous, heat, safe)
+        self.scheme = make_scheme(dtype, eps, cfl, viscous, heat, safe, flux, recon, speeds, integrator)
         self.dtype = torch.float32 if self.scheme.dtype == JF_F32 else torch.float64
         self.shape = (5, self.grid.nz, self.grid.ny, self.grid.nx)
         h = ctypes.c_void_p()
@@ -239,12 +251,13 @@ class Batch:
     """Many independent simulations of uneven sizes (jf_batch_create)."""
 
     def __init__(self, grids, gamma=1.4, R=1.0, mu=0.0, Pr=0.72, dtype="f32", eps=1e-6, cfl=0.5,
-                 viscous=False, heat=False, safe=False):
+                 viscous=False, heat=False, safe=False, flux="hllc", recon="weno5-js", speeds="einfeldt",
+                 integrator="rk3"):
         import torch
         self.grids = (Grid * len(grids))(*[make_grid(**g) if isinstance(g, dict) else g for g in grids])
         self.nsim = len(grids)
         self.gas = GasParams(float(gamma), float(R), float(mu), float(Pr))
-        self.scheme = make_scheme(dtype, eps, cfl, viscous, heat, safe)
+        self.scheme = make_scheme(dtype, eps, cfl, viscous, heat, safe, flux, recon, speeds, integrator)
         self.dtype = torch.float32 if self.scheme.dtype == JF_F32 else torch.float64
         h = ctypes.c_void_p()
         _check(lib().jf_batch_create(self.grids, self.nsim, ctypes.byref(self.gas), ctypes.byref(self.scheme),

@@ -9,7 +9,7 @@
 using namespace jf;
 template <int D> double check_hllc(std::mt19937_64& rng, double speed) {
   std::uniform_real_distribution<double> U(0, 1);
-  Gas<double> g; g.gamma = 1.4; g.gm1 = 0.4; g.inv_gm1 = 2.5; g.inv_R = 1; g.mu = 0; g.lambda = 0; g.eps = 1e-6; g.safe = 0;
+  Gas<double> g{}; g.gamma = 1.4; g.gm1 = 0.4; g.inv_gm1 = 2.5; g.inv_R = 1; g.mu = 0; g.lambda = 0; g.eps = 1e-6; g.safe = 0;
   double WL[5] = {0.2 + 2*U(rng), speed*(2*U(rng)-1), speed*(2*U(rng)-1), speed*(2*U(rng)-1), 0.2+2*U(rng)};
   double WR[5] = {0.2 + 2*U(rng), speed*(2*U(rng)-1), speed*(2*U(rng)-1), speed*(2*U(rng)-1), 0.2+2*U(rng)};
   double Fb[5]; for (auto& x : Fb) x = 2*U(rng)-1;

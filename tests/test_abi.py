@@ -58,6 +58,14 @@ def test_bad_arguments_rejected_on_host(libjf):
     visc = libjf.make_scheme("f32", viscous=True)  # viscous with mu = 0
     assert L.jf_init(ctypes.byref(grid), ctypes.byref(gas), ctypes.byref(visc), ctypes.byref(h)) == libjf.JF_ERR_ARG
     assert L.jf_init(None, None, None, None) == libjf.JF_ERR_ARG
+    # scheme options out of range (Table 2 variants are 0..2 / 0..1)
+    for field, value in (("flux", 3), ("recon", 2), ("signal_speed", 3), ("integrator", -1)):
+        bad = libjf.make_scheme("f32")
+        setattr(bad, field, value)
+        assert L.jf_init(ctypes.byref(grid), ctypes.byref(gas), ctypes.byref(bad), ctypes.byref(h)) == libjf.JF_ERR_ARG
+        assert field.split("_")[0].encode() in L.jf_last_error(None)
+        assert L.jf_batch_create(ctypes.byref(grid), 1, ctypes.byref(gas), ctypes.byref(bad),
+                                 ctypes.byref(h)) == libjf.JF_ERR_ARG
     assert L.jf_rhs(None, None, None, None) == libjf.JF_ERR_ARG
     assert L.jf_destroy(None) == libjf.JF_OK
     assert L.jf_version().startswith(b"jf")
