@@ -32,6 +32,10 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
                          two Euler steps)
   shock tubes            Sod and Lax against the exact solution for every
                          solver / speed / reconstruction
+  roe_eigensystem /      pinned (L = R^-1; R diag(lambda) L equals the flux
+  fs_flux (ROE setup)    Jacobian by finite differences; Roe's property
+                         A~ (U_R - U_L) = F_R - F_L; consistency; fifth order
+                         on smooth advection; Sod and Lax convergence)
   count_flops            descriptive only (an operation count, not a result)
 """
 from __future__ import annotations
@@ -91,7 +95,7 @@ class Config(ctypes.Structure):
 
 
 # scheme options (Table 2); 0 is the Appendix A configuration
-FLUX = {"hllc": 0, "hll": 1, "rusanov": 2}
+FLUX = {"hllc": 0, "hll": 1, "rusanov": 2, "roe": 3}
 RECON = {"weno5-js": 0, "weno5-z": 1}
 SPEEDS = {"einfeldt": 0, "davis": 1, "toro": 2}
 INTEGRATOR = {"rk3": 0, "rk2": 1, "euler": 2}
@@ -147,6 +151,10 @@ def lib():
             L.orc_flux.restype = None
             L.orc_hll_speeds.argtypes = [dp, dp, ctypes.c_int, d, d, d, dp]
             L.orc_hll_speeds.restype = None
+            L.orc_roe_eigensystem.argtypes = [dp, dp, ctypes.c_int, d, dp, dp, dp]
+            L.orc_roe_eigensystem.restype = None
+            L.orc_fs_flux.argtypes = [dp, ctypes.c_int, d, d, ctypes.c_int, dp]
+            L.orc_fs_flux.restype = None
             L.orc_exact_star.argtypes = [dp, dp, d, dp]
             L.orc_exact_star.restype = ctypes.c_int
             L.orc_exact_sample.argtypes = [dp, dp, d, d, d, ctypes.c_int, dp, dp]
@@ -275,6 +283,24 @@ def hll_with_speeds(WL, WR, SL: float, SR: float, d: int = 0, gamma: float = 1.4
     WR = np.ascontiguousarray(WR, dtype=np.float64)
     F = np.empty(5)
     lib().orc_hll_speeds(_ptr(WL), _ptr(WR), int(d), float(gamma), float(SL), float(SR), _ptr(F))
+    return F
+
+
+def roe_eigensystem(WL, WR, d: int = 0, gamma: float = 1.4):
+    """(lambda[5], R[5x5], L[5x5]) of the Roe-averaged flux Jacobian along d."""
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    lam, R, L = np.empty(5), np.empty((5, 5)), np.empty((5, 5))
+    lib().orc_roe_eigensystem(_ptr(WL), _ptr(WR), int(d), float(gamma), _ptr(lam), _ptr(R), _ptr(L))
+    return lam, R, L
+
+
+def fs_flux(W6, d: int = 0, gamma: float = 1.4, eps: float = 1e-6, recon: str = "weno5-js") -> np.ndarray:
+    """Flux-splitting (ROE setup) face flux from six primitive states
+    (cells i-2 .. i+3 of the face x_{i+1/2}) along d."""
+    W6 = np.ascontiguousarray(W6, dtype=np.float64).reshape(6, 5)
+    F = np.empty(5)
+    lib().orc_fs_flux(_ptr(W6), int(d), float(gamma), float(eps), RECON[recon], _ptr(F))
     return F
 
 

@@ -33,6 +33,9 @@
 //                      HLLC (Toro 1994) and the chosen signal speeds
 //   hll_flux           HLL (Harten, Lax, van Leer 1983), Table 2
 //   rusanov_flux       local Lax-Friedrichs / Rusanov, Table 2
+//   roe_eigensystem,   Section 3.3 "Flux-Splitting approach" with the Roe
+//   flux_splitting_    average and Roe flux splitting: the paper's ROE setup
+//   face_flux          (Section 5: WENO5 in characteristic space)
 //   dissipative_flux   Section 2 (tau, q = -lambda grad T) discretised by
 //                      Section 3.4 (face C4 derivative, cell-centre C4
 //                      derivative + fourth-order interpolation to the face)
@@ -55,7 +58,7 @@ namespace orc {
 
 enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1 };
 // scheme options of Table 2 (0 = the Appendix A configuration)
-enum { FLUX_HLLC = 0, FLUX_HLL = 1, FLUX_RUSANOV = 2 };
+enum { FLUX_HLLC = 0, FLUX_HLL = 1, FLUX_RUSANOV = 2, FLUX_ROE_FS = 3 };
 enum { RECON_WENO5_JS = 0, RECON_WENO5_Z = 1 };
 enum { SPEED_EINFELDT = 0, SPEED_DAVIS = 1, SPEED_TORO = 2 };
 enum { TIME_RK3 = 0, TIME_RK2 = 1, TIME_EULER = 2 };
@@ -264,8 +267,10 @@ T toro_q(const T& p_star, const T& pK, double gamma) {
   if (p_star <= pK) return T(1.0);
   return sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (p_star / pK - 1.0));
 }
+// EL, ER: total energies of the two sides (already formed by the callers).
 template <class T>
-void signal_speeds(const T WL[5], const T WR[5], int d, double gamma, int kind, T& SL, T& SR) {
+void signal_speeds(const T WL[5], const T WR[5], const T& EL, const T& ER, int d, double gamma, int kind, T& SL,
+                   T& SR) {
   const T rhoL = WL[0], rhoR = WR[0], pL = WL[4], pR = WR[4];
   const T unL = WL[1 + d], unR = WR[1 + d];
   const T cL = sqrt(gamma * pL / rhoL);
@@ -279,11 +284,8 @@ void signal_speeds(const T WL[5], const T WR[5], int d, double gamma, int kind, 
     SL = unL - cL * toro_q(p_star, pL, gamma);
     SR = unR + cR * toro_q(p_star, pR, gamma);
   } else {
-    T UL[5], UR[5];
-    conservative_of(WL, gamma, UL);
-    conservative_of(WR, gamma, UR);
-    const T HL = (UL[4] + pL) / rhoL;
-    const T HR = (UR[4] + pR) / rhoR;
+    const T HL = (EL + pL) / rhoL;
+    const T HR = (ER + pR) / rhoR;
     const T sL = sqrt(rhoL), sR = sqrt(rhoR);
     T ut[3];
     for (int m = 0; m < 3; ++m) ut[m] = (sL * WL[1 + m] + sR * WR[1 + m]) / (sL + sR);
@@ -313,7 +315,7 @@ void hllc_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5], int sp
   const T rhoL = WL[0], rhoR = WR[0], pL = WL[4], pR = WR[4];
   const T unL = WL[1 + d], unR = WR[1 + d];
   T SL, SR;
-  signal_speeds(WL, WR, d, gamma, speeds, SL, SR);
+  signal_speeds(WL, WR, UL[4], UR[4], d, gamma, speeds, SL, SR);
   const T Ss = (pR - pL + rhoL * unL * (SL - unL) - rhoR * unR * (SR - unR)) /
                (rhoL * (SL - unL) - rhoR * (SR - unR));
   if (SL >= 0.0) {
@@ -359,8 +361,11 @@ void hll_flux_speeds(const T WL[5], const T WR[5], int d, double gamma, const T&
 }
 template <class T>
 void hll_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5], int speeds = SPEED_EINFELDT) {
+  T UL[5], UR[5];
+  conservative_of(WL, gamma, UL);
+  conservative_of(WR, gamma, UR);
   T SL, SR;
-  signal_speeds(WL, WR, d, gamma, speeds, SL, SR);
+  signal_speeds(WL, WR, UL[4], UR[4], d, gamma, speeds, SL, SR);
   hll_flux_speeds(WL, WR, d, gamma, SL, SR, F);
 }
 
@@ -387,12 +392,148 @@ void riemann_flux(const Config& c, const T WL[5], const T WR[5], int d, T F[5]) 
   else hllc_flux(WL, WR, d, c.gamma, F, c.speeds);
 }
 
+// Roe average and eigen-decomposition of the flux Jacobian along d (Section
+// 3.3, Flux-Splitting approach, steps 1-2), from the primitive states of the
+// two cells beside the face:
+//   sqrt(rho) weights: u~ (3 components), H~ = weighted (E + p) / rho,
+//   c~ = sqrt((gamma - 1)(H~ - |u~|^2 / 2));
+//   eigenvalues (u_n - c, u_n, u_t1, u_t2 ... ) = (u_n - c, u_n, u_n, u_n, u_n + c);
+//   right eigenvectors (columns of R, conservative variables [rho, m, E] with
+//   the normal momentum in slot 1 + d):
+//     r0 = [1, u - c n, H - u_n c],  r1 = [1, u, |u|^2 / 2],
+//     r2 = [0, t1, u_t1],  r3 = [0, t2, u_t2],  r4 = [1, u + c n, H + u_n c]
+//   with n the unit normal and t1, t2 the two other unit axes;
+//   left eigenvectors L = R^{-1} (rows), written out with
+//   b1 = (gamma - 1) / c^2, b2 = b1 |u|^2 / 2:
+//     l0 = 1/2 [b2 + u_n / c, -b1 u - n / c, b1],
+//     l1 = [1 - b2, b1 u, -b1],
+//     l2 = [-u_t1, t1, 0],  l3 = [-u_t2, t2, 0],
+//     l4 = 1/2 [b2 - u_n / c, -b1 u + n / c, b1].
+template <class T>
+struct Eigensystem {
+  T lambda[5];
+  T R[5][5];  // R[row][column]
+  T L[5][5];  // L[row][column] = R^{-1}
+};
+template <class T>
+Eigensystem<T> roe_eigensystem(const T WL[5], const T WR[5], int d, double gamma) {
+  T UL[5], UR[5];
+  conservative_of(WL, gamma, UL);
+  conservative_of(WR, gamma, UR);
+  const T sL = sqrt(WL[0]), sR = sqrt(WR[0]);
+  T u[3];
+  for (int m = 0; m < 3; ++m) u[m] = (sL * WL[1 + m] + sR * WR[1 + m]) / (sL + sR);
+  const T H = (sL * (UL[4] + WL[4]) / WL[0] + sR * (UR[4] + WR[4]) / WR[0]) / (sL + sR);
+  const T q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T c = sqrt((gamma - 1.0) * (H - 0.5 * q2));
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  Eigensystem<T> es;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) es.R[i][j] = es.L[i][j] = T(0.0);
+  const T un = u[d];
+  es.lambda[0] = un - c;
+  es.lambda[1] = un;
+  es.lambda[2] = un;
+  es.lambda[3] = un;
+  es.lambda[4] = un + c;
+  // right eigenvectors (columns)
+  es.R[0][0] = T(1.0);
+  es.R[0][1] = T(1.0);
+  es.R[0][4] = T(1.0);
+  for (int m = 0; m < 3; ++m) {
+    es.R[1 + m][0] = u[m];
+    es.R[1 + m][1] = u[m];
+    es.R[1 + m][4] = u[m];
+  }
+  es.R[1 + d][0] = un - c;
+  es.R[1 + d][4] = un + c;
+  es.R[4][0] = H - un * c;
+  es.R[4][1] = 0.5 * q2;
+  es.R[4][4] = H + un * c;
+  es.R[1 + t1][2] = T(1.0);
+  es.R[4][2] = u[t1];
+  es.R[1 + t2][3] = T(1.0);
+  es.R[4][3] = u[t2];
+  // left eigenvectors (rows)
+  const T b1 = (gamma - 1.0) / (c * c);
+  const T b2 = 0.5 * b1 * q2;
+  es.L[0][0] = 0.5 * (b2 + un / c);
+  es.L[4][0] = 0.5 * (b2 - un / c);
+  es.L[1][0] = 1.0 - b2;
+  for (int m = 0; m < 3; ++m) {
+    es.L[0][1 + m] = -0.5 * b1 * u[m];
+    es.L[4][1 + m] = -0.5 * b1 * u[m];
+    es.L[1][1 + m] = b1 * u[m];
+  }
+  es.L[0][1 + d] = es.L[0][1 + d] - 0.5 / c;
+  es.L[4][1 + d] = es.L[4][1 + d] + 0.5 / c;
+  es.L[0][4] = 0.5 * b1;
+  es.L[4][4] = 0.5 * b1;
+  es.L[1][4] = -b1;
+  es.L[2][0] = -u[t1];
+  es.L[2][1 + t1] = T(1.0);
+  es.L[3][0] = -u[t2];
+  es.L[3][1 + t2] = T(1.0);
+  return es;
+}
+
+// Flux-splitting face flux (Section 3.3, steps 3-7) with Roe flux splitting
+// (Lambda_bar = |Lambda| of the Roe eigensystem): for the stencil cells
+// j = i-2 .. i+3 of the face x_{i+1/2},
+//   V_j = L U_j, G_j = L F_j, G^+-_j = (G_j +- |Lambda| V_j) / 2;
+// G^+ at the face by the left-biased WENO5 of cells i-2..i+2, G^- by the
+// mirrored stencil i+3..i-1; F = R (G^+ + G^-).
+template <class T>
+void flux_splitting_face_flux(const Field<T>& W, const Config& c, int d, const Cell& cell, T F[5]) {
+  T Ws[6][5];
+  for (int j = 0; j < 6; ++j)
+    for (int m = 0; m < 5; ++m) Ws[j][m] = at(W, m, cell.shift(d, j - 2));
+  const Eigensystem<T> es = roe_eigensystem(Ws[2], Ws[3], d, c.gamma);
+  T Gp[6][5], Gm[6][5];
+  for (int j = 0; j < 6; ++j) {
+    T U[5], Fj[5];
+    conservative_of(Ws[j], c.gamma, U);
+    physical_flux(Ws[j], U, d, Fj);
+    for (int k = 0; k < 5; ++k) {
+      T v = T(0.0), g = T(0.0);
+      for (int m = 0; m < 5; ++m) {
+        v = v + es.L[k][m] * U[m];
+        g = g + es.L[k][m] * Fj[m];
+      }
+      const T a = fabs(es.lambda[k]);
+      Gp[j][k] = 0.5 * (g + a * v);
+      Gm[j][k] = 0.5 * (g - a * v);
+    }
+  }
+  T Gh[5];
+  for (int k = 0; k < 5; ++k) {
+    T gp, gm;
+    if (c.recon == RECON_WENO5_Z) {
+      gp = weno5_z(Gp[0][k], Gp[1][k], Gp[2][k], Gp[3][k], Gp[4][k], c.eps);
+      gm = weno5_z(Gm[5][k], Gm[4][k], Gm[3][k], Gm[2][k], Gm[1][k], c.eps);
+    } else {
+      gp = weno5_js(Gp[0][k], Gp[1][k], Gp[2][k], Gp[3][k], Gp[4][k], c.eps);
+      gm = weno5_js(Gm[5][k], Gm[4][k], Gm[3][k], Gm[2][k], Gm[1][k], c.eps);
+    }
+    Gh[k] = gp + gm;
+  }
+  for (int m = 0; m < 5; ++m) {
+    T f = T(0.0);
+    for (int k = 0; k < 5; ++k) f = f + es.R[m][k] * Gh[k];
+    F[m] = f;
+  }
+}
+
 // Convective flux at the face between cell c and cell c + e_d (Section 3.3,
 // High-order Godunov approach): WENO5-JS (or -Z) on each primitive component
 // in physical space ("reconstruction_var": "PRIMITIVE"), the right state by
 // the mirrored stencil, then the Riemann solver (HLLC by default).
 template <class T>
 void convective_face_flux(const Field<T>& W, const Config& c, int d, const Cell& cell, T F[5]) {
+  if (c.flux == FLUX_ROE_FS) {
+    flux_splitting_face_flux(W, c, d, cell, F);
+    return;
+  }
   T Wm[5], Wp[5];
   for (int m = 0; m < 5; ++m) {
     const T a = at(W, m, cell.shift(d, -2));

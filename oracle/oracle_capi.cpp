@@ -72,7 +72,7 @@ static bool valid(const Config* c) {
     const bool p0 = c->bc[2 * d] == BC_PERIODIC, p1 = c->bc[2 * d + 1] == BC_PERIODIC;
     if (p0 != p1) return false;  // periodic must be set on both sides
   }
-  if (c->flux < FLUX_HLLC || c->flux > FLUX_RUSANOV) return false;
+  if (c->flux < FLUX_HLLC || c->flux > FLUX_ROE_FS) return false;
   if (c->recon < RECON_WENO5_JS || c->recon > RECON_WENO5_Z) return false;
   if (c->speeds < SPEED_EINFELDT || c->speeds > SPEED_TORO) return false;
   if (c->integrator < TIME_RK3 || c->integrator > TIME_EULER) return false;
@@ -225,7 +225,10 @@ double orc_weno5_z(const double* v, double eps) { return weno5_z(v[0], v[1], v[2
 
 // Signal speed estimate `kind` (SPEED_*): out = (S_L, S_R).
 void orc_signal_speeds(const double* WL, const double* WR, int d, double gamma, int kind, double* out) {
-  signal_speeds(WL, WR, d, gamma, kind, out[0], out[1]);
+  double UL[5], UR[5];
+  conservative_of(WL, gamma, UL);
+  conservative_of(WR, gamma, UR);
+  signal_speeds(WL, WR, UL[4], UR[4], d, gamma, kind, out[0], out[1]);
 }
 
 // Toro's shock/rarefaction factor q_K for a given star pressure.
@@ -238,6 +241,53 @@ void orc_flux(const double* WL, const double* WR, int d, double gamma, int flux,
   c.flux = flux;
   c.speeds = speeds;
   riemann_flux(c, WL, WR, d, F);
+}
+
+// Roe eigensystem at a face along d: lambda[5], R[25] and L[25] row-major.
+void orc_roe_eigensystem(const double* WL, const double* WR, int d, double gamma, double* lambda, double* R,
+                         double* L) {
+  const Eigensystem<double> es = roe_eigensystem(WL, WR, d, gamma);
+  for (int i = 0; i < 5; ++i) {
+    lambda[i] = es.lambda[i];
+    for (int j = 0; j < 5; ++j) {
+      R[5 * i + j] = es.R[i][j];
+      L[5 * i + j] = es.L[i][j];
+    }
+  }
+}
+
+// Flux-splitting (ROE setup) face flux of a 1D stencil of six primitive
+// states W6[6][5] (cells i-2 .. i+3 of the face x_{i+1/2}) along d.
+void orc_fs_flux(const double* W6, int d, double gamma, double eps, int recon, double* F) {
+  Config c{};
+  c.n[0] = 6;
+  c.n[1] = c.n[2] = 1;
+  c.hi[0] = c.hi[1] = c.hi[2] = 1.0;
+  for (int k = 0; k < 6; ++k) c.bc[k] = BC_ZERO_GRADIENT;
+  c.gamma = gamma;
+  c.eps = eps;
+  c.recon = recon;
+  c.flux = FLUX_ROE_FS;
+  // the stencil along x (d = 0 layout), velocities permuted so that the
+  // normal component of axis d sits in the x slot
+  Field<double> W(c, 5);
+  for (int j = 0; j < 6; ++j)
+    for (int m = 0; m < 5; ++m) W(m, j, 0, 0) = W6[5 * j + m];
+  if (d != 0) {
+    for (int j = 0; j < 6; ++j) {
+      const double un = W6[5 * j + 1 + d], ut1 = W6[5 * j + 1 + (d + 1) % 3], ut2 = W6[5 * j + 1 + (d + 2) % 3];
+      W(1, j, 0, 0) = un;
+      W(2, j, 0, 0) = ut1;
+      W(3, j, 0, 0) = ut2;
+    }
+  }
+  double G[5];
+  flux_splitting_face_flux(W, c, 0, Cell(2, 0, 0), G);
+  F[0] = G[0];
+  F[4] = G[4];
+  F[1 + d] = G[1];
+  F[1 + (d + 1) % 3] = G[2];
+  F[1 + (d + 2) % 3] = G[3];
 }
 
 // HLL flux for given signal speeds (S_L, S_R).

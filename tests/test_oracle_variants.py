@@ -263,3 +263,92 @@ def test_rk2_is_the_average_of_two_euler_steps(orc):
     U2, _, _ = orc.run(orc.config(**dict(case.params(), integrator="rk2")), case.U, 1, dt)
     UE, _, _ = orc.run(orc.config(**dict(case.params(), integrator="euler")), case.U, 2, dt)
     np.testing.assert_allclose(U2, 0.5 * (case.U + UE), rtol=0, atol=1e-14 * np.abs(case.U).max())
+
+
+# ---------------------------------------------------------------------------
+# The ROE setup (Section 3.3 flux-splitting formulation, Section 5): Roe
+# average, eigen-decomposition, WENO5 on the split characteristic fluxes.
+
+def _conserved_from_roe_state(rho, u, H, gamma=GAMMA):
+    """A state with velocity u and total enthalpy H (p from H = c^2/(gamma-1) + |u|^2/2)."""
+    p = (gamma - 1) / gamma * rho * (H - 0.5 * u @ u)
+    return np.array([rho, *u, p])
+
+
+def _jacobian_fd(W, d, gamma=GAMMA, h=1e-6):
+    """Flux Jacobian dF/dU of the Euler equations along d by central differences."""
+    U0 = conserved(W, gamma)
+
+    def prim(U):
+        rho = U[0]
+        vel = U[1:4] / rho
+        p = (gamma - 1) * (U[4] - 0.5 * rho * vel @ vel)
+        return np.array([rho, *vel, p])
+
+    A = np.zeros((5, 5))
+    for k in range(5):
+        e = np.zeros(5)
+        e[k] = h * max(1.0, abs(U0[k]))
+        A[:, k] = (euler_flux(prim(U0 + e), d, gamma) - euler_flux(prim(U0 - e), d, gamma)) / (2 * e[k])
+    return A
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_roe_eigensystem(orc, d):
+    """L = R^-1; R diag(lambda) L is the flux Jacobian at the Roe state
+    (finite differences of the Euler flux); and the defining property of the
+    Roe average: A~ (U_R - U_L) = F(U_R) - F(U_L) exactly."""
+    rng = np.random.default_rng(7 + d)
+    for WL, WR in zip(random_states(rng, 10), random_states(rng, 10)):
+        lam, R, L = orc.roe_eigensystem(WL, WR, d, GAMMA)
+        np.testing.assert_allclose(L @ R, np.eye(5), atol=1e-13)
+        A = R @ np.diag(lam) @ L
+        sL, sR = np.sqrt(WL[0]), np.sqrt(WR[0])
+        u = (sL * np.array(WL[1:4]) + sR * np.array(WR[1:4])) / (sL + sR)
+        H = lambda W: (conserved(W)[4] + W[4]) / W[0]  # noqa: E731
+        Ht = (sL * H(WL) + sR * H(WR)) / (sL + sR)
+        Wt = _conserved_from_roe_state(sL * sR, u, Ht)
+        np.testing.assert_allclose(A, _jacobian_fd(Wt, d), rtol=1e-7, atol=1e-7 * np.abs(A).max())
+        dF = euler_flux(WR, d) - euler_flux(WL, d)
+        np.testing.assert_allclose(A @ (conserved(WR) - conserved(WL)), dF, rtol=1e-12,
+                                   atol=1e-12 * np.abs(dF).max())
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_flux_splitting_consistent(orc, d):
+    """A uniform stencil gives the physical flux: WENO of a constant is the
+    constant, G+ + G- = G and R L F = F."""
+    rng = np.random.default_rng(9)
+    for W in random_states(rng, 10):
+        np.testing.assert_allclose(orc.fs_flux(np.tile(W, (6, 1)), d), euler_flux(W, d), rtol=1e-13, atol=1e-13)
+
+
+def test_roe_setup_fifth_order(orc):
+    """Section 5.1.1 convergence case with the ROE setup: WENO5 on the
+    characteristic fluxes converges at fifth order (dt = 1e-4 to t = 0.2)."""
+    errs = []
+    steps = 2000
+    for n in (20, 40, 80):
+        case = inputs.sine_advection(n)
+        c = orc.config(**dict(case.params(), flux="roe"))
+        U, t, _ = orc.run(c, case.U, steps, 1e-4)
+        errs.append(np.mean(np.abs(U[0, 0, 0] - inputs.sine_exact_average(n, t))))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 4.6), orders
+
+
+@pytest.mark.parametrize("recon", ["weno5-js", "weno5-z"])
+def test_roe_setup_shock_tubes(orc, recon):
+    """Section 5.1.2 with the ROE setup: Sod and Lax converge to the exact
+    Riemann solution."""
+    for WL, WR, T, bound in ((inputs.SOD_LEFT, inputs.SOD_RIGHT, 0.2, 3.2e-3),
+                             (inputs.LAX_LEFT, inputs.LAX_RIGHT, inputs.LAX_END_TIME, 1.25e-2)):
+        errs = []
+        for n in (100, 200, 400):
+            case = inputs.riemann_1d(n, WL, WR)
+            c = orc.config(**dict(case.params(), flux="roe", recon=recon))
+            U, t, _ = orc.run(c, case.U, 100000, 0.0, T)
+            ex = orc.exact_sample(WL, WR, inputs.centres(n, 0.0, 1.0), t)
+            errs.append(np.mean(np.abs(U[0, 0, 0] - ex[:, 0])))
+        assert errs[0] > errs[1] > errs[2], errs
+        assert errs[1] < bound, errs
