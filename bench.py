@@ -43,18 +43,55 @@ WORKLOADS = {
     "tgv256_f64": ("taylor_green", {"n": 256}, "f64"),
     "tgv128_f64": ("taylor_green", {"n": 128}, "f64"),
     "hit384": ("solenoidal_turbulence", {"n": 384}, "f32"),
+    # the paper's ROE setup (flux splitting with the Roe eigensystem, Table 3)
+    "tgv256_roe": ("taylor_green", {"n": 256}, "f32"),
+    "tgv128_roe": ("taylor_green", {"n": 128}, "f32"),
+    "tgv128_roe_f64": ("taylor_green", {"n": 128}, "f64"),
 }
+# scheme options of a workload (the others run the default HLLC setup)
+WORKLOAD_SCHEME = {"tgv256_roe": {"flux": "roe"}, "tgv128_roe": {"flux": "roe"}, "tgv128_roe_f64": {"flux": "roe"}}
+
+
+def physics_name(case):
+    conv = ("ROE setup: Roe flux splitting, WENO5-JS on characteristic fluxes" if case.flux == "roe"
+            else "WENO5-JS, HLLC/Einfeldt")
+    return f"Navier-Stokes ({conv}, C4 viscous + heat)" if case.viscous else f"Euler ({conv})"
+
+
+def paper_context(case, dtype):
+    """The paper's Table 3 (RTX A6000, JAX): mean wall-clock time per cell and
+    step of the same setup and precision; context only (another machine)."""
+    table = {("hllc", "f32"): {"64^3": 24.39, "128^3": 25.09, "256^3": 28.36, "384^3": 28.11},
+             ("hllc", "f64"): {"64^3": 93.94, "128^3": 92.55, "256^3": 92.76},
+             ("roe", "f32"): {"64^3": 302.20, "128^3": 304.55, "256^3": 301.78},
+             ("roe", "f64"): {"64^3": 746.78, "128^3": 759.36, "256^3": 760.09}}
+    setup = "roe" if case.flux == "roe" else "hllc"
+    return {"hardware": "RTX A6000", "setup": setup.upper(), f"ns_per_cell_step_{dtype}": table[(setup, dtype)],
+            "source": "Table 3"}
+
+
+def with_scheme(case, workload):
+    for k, v in WORKLOAD_SCHEME.get(workload, {}).items():
+        setattr(case, k, v)
+    return case
 
 # Algorithmic floating-point operations per cell and per stage launch, as the
 # scheme is defined (one evaluation per face), counted by the oracle's
 # operation-counting scalar (oracle.count_flops: rhs_per_cell + rk_combine).
 FLOPS_PER_CELL_STAGE = {
-    (3, True): 3041.0 + 20.0,   # 3D, viscous + heat
-    (3, False): 2504.0 + 20.0,  # 3D, inviscid
-    (2, True): 1912.0 + 20.0,
-    (2, False): 1674.0 + 20.0,
-    (1, True): 903.0 + 20.0,
-    (1, False): 844.0 + 20.0,
+    (3, True, "hllc"): 3041.0 + 20.0,   # 3D, viscous + heat
+    (3, False, "hllc"): 2504.0 + 20.0,  # 3D, inviscid
+    (2, True, "hllc"): 1912.0 + 20.0,
+    (2, False, "hllc"): 1674.0 + 20.0,
+    (1, True, "hllc"): 903.0 + 20.0,
+    (1, False, "hllc"): 844.0 + 20.0,
+    # ROE setup (flux splitting in characteristic space)
+    (3, True, "roe"): 5798.0 + 20.0,
+    (3, False, "roe"): 5261.0 + 20.0,
+    (2, True, "roe"): 3750.0 + 20.0,
+    (2, False, "roe"): 3512.0 + 20.0,
+    (1, True, "roe"): 1822.0 + 20.0,
+    (1, False, "roe"): 1763.0 + 20.0,
 }
 # Algorithmic HBM values per cell for the three stages of one RK3 step:
 # stage 1 reads Un, writes U1 (10); stages 2 and 3 read U_s and Un and write (15 + 15).
@@ -85,7 +122,7 @@ def make_case(workload):
     if gen == "solenoidal_turbulence":
         import torch
         kw = dict(kw, device="cuda" if torch.cuda.is_available() else None)
-    return getattr(inputs, gen)(**kw), dtype
+    return with_scheme(getattr(inputs, gen)(**kw), workload), dtype
 
 
 def measured_peaks():
@@ -98,7 +135,8 @@ def measured_peaks():
 
 # the files that define the forward stage kernel and its compile flags
 STAGE_SOURCES = ("csrc/stage.cuh", "csrc/stage_inst.cuh", "csrc/stage_f32.cu", "csrc/stage_f64.cu",
-                 "csrc/stage_f32_gen.cu", "csrc/stage_f64_gen.cu", "csrc/jf_math.cuh", "csrc/variants.h",
+                 "csrc/stage_f32_gen.cu", "csrc/stage_f64_gen.cu", "csrc/stage_f32_roe.cu",
+                 "csrc/stage_f64_roe.cu", "csrc/jf_math.cuh", "csrc/variants.h",
                  "_build.py")
 
 
@@ -225,7 +263,7 @@ def cpu_baseline(workload, budget_s=15.0, threads=None):
     from paper_2203_13760_gb300 import inputs
     gen, kw, _ = WORKLOADS[workload]
     n = 64
-    case = getattr(inputs, gen)(**dict(kw, n=n))
+    case = with_scheme(getattr(inputs, gen)(**dict(kw, n=n)), workload)
     c = oracle.config(**case.params())
     cores = oracle.set_threads(threads or os.cpu_count() or 1)
     U = case.U.astype(np.float64)
@@ -253,7 +291,7 @@ def run_reference(args):
     from paper_2203_13760_gb300 import inputs
     gen, kw, dtype = WORKLOADS[args.workload]
     n = 48
-    case = getattr(inputs, gen)(**dict(kw, n=n))
+    case = with_scheme(getattr(inputs, gen)(**dict(kw, n=n)), args.workload)
     c = oracle.config(**case.params())
     cores = oracle.set_threads(os.cpu_count() or 1)
     U = case.U.astype(np.float64)
@@ -344,7 +382,7 @@ def run_jf(args):
     sms = props.multi_processor_count
     stage_avg_s = statistics.mean(stage_ms) * 1e-3
     dim = 3 if case.n[2] > 1 else (2 if case.n[1] > 1 else 1)
-    flops = FLOPS_PER_CELL_STAGE.get((dim, bool(case.viscous)), None)
+    flops = FLOPS_PER_CELL_STAGE.get((dim, bool(case.viscous), "roe" if case.flux == "roe" else "hllc"), None)
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     if dtype == "f32":
         peak_tflops = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
@@ -393,8 +431,7 @@ def run_jf(args):
             "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "cells": N, "grid": list(case.n), "flow": case.name,
-                       "physics": "Navier-Stokes (WENO5-JS, HLLC/Einfeldt, C4 viscous + heat)" if case.viscous
-                       else "Euler (WENO5-JS, HLLC/Einfeldt)", "integrator": "TVD-RK3, CFL 0.5 on device",
+                       "physics": physics_name(case), "integrator": "TVD-RK3, CFL 0.5 on device",
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state %.0f MB)" % (5 * N * esize / 1e6),
                        "variant": variant},
@@ -404,8 +441,7 @@ def run_jf(args):
             "gpu_launches": 4 * K,
             "clocks": clk,
             "breakdown_ms": {"cfl": statistics.mean(cfl_ms), "stage": statistics.mean(stage_ms)},
-            "paper_context": {"hardware": "RTX A6000", "ns_per_cell_step_fp32": {"256^3": 28.36, "384^3": 28.11},
-                              "source": "Table 3"},
+            "paper_context": paper_context(case, dtype),
         }
         if extras:
             line["extras"] = extras
@@ -535,6 +571,7 @@ VARIANT_SCHEMES = {
     "hllc_toro": {"speeds": "toro"},
     "hllc_weno5z": {"recon": "weno5-z"},
     "hllc_rk2": {"integrator": "rk2"},
+    "roe (flux splitting)": {"flux": "roe"},
 }
 
 

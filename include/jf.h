@@ -59,7 +59,8 @@ typedef enum { JF_BC_PERIODIC = 0, JF_BC_ZERO_GRADIENT = 1 } jf_bc;
 enum { JF_F32 = 0, JF_F64 = 1 };
 /* Scheme options (Table 2 of the paper; 0 is the Appendix A configuration). */
 enum { JF_EINFELDT = 0, JF_DAVIS = 1, JF_TORO = 2 };           /* signal speed estimates */
-enum { JF_FLUX_HLLC = 0, JF_FLUX_HLL = 1, JF_FLUX_RUSANOV = 2 }; /* Riemann solvers */
+enum { JF_FLUX_HLLC = 0, JF_FLUX_HLL = 1, JF_FLUX_RUSANOV = 2, /* Riemann solvers */
+       JF_FLUX_ROE = 3 };                                         /* flux splitting (ROE setup) */
 enum { JF_WENO5_JS = 0, JF_WENO5_Z = 1 };                        /* reconstructions */
 enum { JF_RK3 = 0, JF_RK2 = 1, JF_EULER = 2 };                   /* time integrators */
 
@@ -93,7 +94,11 @@ typedef struct {
  *                 1988), JF_TORO (Toro 1994: PVRS star pressure)
  *   flux          JF_FLUX_HLLC (Toro 1994), JF_FLUX_HLL (Harten, Lax, van Leer
  *                 1983), JF_FLUX_RUSANOV (local Lax-Friedrichs); the signal
- *                 speeds apply to HLLC and HLL
+ *                 speeds apply to HLLC and HLL.  JF_FLUX_ROE selects the
+ *                 flux-splitting formulation of Section 3.3 with the Roe
+ *                 eigensystem and Roe splitting (the paper's "ROE" setup):
+ *                 `recon` then reconstructs the split characteristic
+ *                 fluxes, and safe_recon has no effect
  *   recon         JF_WENO5_JS (Jiang & Shu 1996), JF_WENO5_Z (Borges et al.
  *                 2008, power 1)
  *   integrator    JF_RK3 / JF_RK2 (TVD Runge-Kutta of Gottlieb & Shu 1998,

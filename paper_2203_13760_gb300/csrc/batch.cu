@@ -34,12 +34,12 @@ __global__ void __launch_bounds__(256) batch_copy_kernel(const SimDesc<T>* __res
 namespace {
 
 template <typename T>
-std::vector<int> batch_variant_list(int dim, bool visc, bool general) {
+std::vector<int> batch_variant_list(int dim, bool visc, int kind) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
   std::vector<int> out;
   for (int i = 0; i < count; ++i)
-    if (tab[i].dim == dim && tab[i].visc == visc && tab[i].general == general && tab[i].launch_batch)
+    if (tab[i].dim == dim && tab[i].visc == visc && tab[i].scheme == kind && tab[i].launch_batch)
       out.push_back(i);
   return out;
 }
@@ -48,7 +48,7 @@ std::vector<int> batch_variant_list(int dim, bool visc, bool general) {
 template <typename T>
 jf_status setup_variant(jf_ctx* h, int v) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = batch_variant_list<T>(h->dim, visc, general_scheme(h->scheme));
+  auto list = batch_variant_list<T>(h->dim, visc, scheme_kind(h->scheme));
   if (list.empty()) { set_error(h, "batch: no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
   if (v < 0) v = 0;
   if (v >= (int)list.size()) { set_error(h, "batch: variant index out of range"); return JF_ERR_ARG; }
@@ -227,12 +227,12 @@ int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   std::vector<int> list;
   int bx = 0, by = 0;
   if (h->scheme.dtype == JF_F32) {
-    list = batch_variant_list<float>(h->dim, visc, general_scheme(h->scheme));
+    list = batch_variant_list<float>(h->dim, visc, scheme_kind(h->scheme));
     int c = 0;
     const StageVariant<float>* tab = stage_variants<float>(&c);
     if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
   } else {
-    list = batch_variant_list<double>(h->dim, visc, general_scheme(h->scheme));
+    list = batch_variant_list<double>(h->dim, visc, scheme_kind(h->scheme));
     int c = 0;
     const StageVariant<double>* tab = stage_variants<double>(&c);
     if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }

@@ -67,8 +67,8 @@ jf_status check_physics(jf_ctx* h, const jf_gas& gas, const jf_scheme& s) {
     set_error(h, "scheme: signal_speed must be JF_EINFELDT, JF_DAVIS or JF_TORO");
     return JF_ERR_ARG;
   }
-  if (s.flux < JF_FLUX_HLLC || s.flux > JF_FLUX_RUSANOV) {
-    set_error(h, "scheme: flux must be JF_FLUX_HLLC, JF_FLUX_HLL or JF_FLUX_RUSANOV");
+  if (s.flux < JF_FLUX_HLLC || s.flux > JF_FLUX_ROE) {
+    set_error(h, "scheme: flux must be JF_FLUX_HLLC, JF_FLUX_HLL, JF_FLUX_RUSANOV or JF_FLUX_ROE");
     return JF_ERR_ARG;
   }
   if (s.recon != JF_WENO5_JS && s.recon != JF_WENO5_Z) {
@@ -137,17 +137,19 @@ int reduce_blocks(long long N, int sms) {
 // Variant selection.  A variant = (compiled tile shape, z chunk).
 static const int kZChunks[] = {32, 16, 64, 8};
 
-bool general_scheme(const jf_scheme& s) {
-  return s.flux != JF_FLUX_HLLC || s.signal_speed != JF_EINFELDT || s.recon != JF_WENO5_JS;
+int scheme_kind(const jf_scheme& s) {
+  if (s.flux == JF_FLUX_ROE) return SCH_ROE;
+  const bool general = s.flux != JF_FLUX_HLLC || s.signal_speed != JF_EINFELDT || s.recon != JF_WENO5_JS;
+  return general ? SCH_GENERAL : SCH_DEFAULT;
 }
 
 template <typename T>
-std::vector<std::pair<int, int>> variant_list(int dim, bool visc, bool general) {
+std::vector<std::pair<int, int>> variant_list(int dim, bool visc, int kind) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
   std::vector<std::pair<int, int>> out;
   for (int i = 0; i < count; ++i) {
-    if (tab[i].dim != dim || tab[i].visc != visc || tab[i].general != general) continue;
+    if (tab[i].dim != dim || tab[i].visc != visc || tab[i].scheme != kind) continue;
     if (dim == 3)
       for (int z : kZChunks) out.emplace_back(i, z);
     else
@@ -159,7 +161,7 @@ std::vector<std::pair<int, int>> variant_list(int dim, bool visc, bool general) 
 template <typename T>
 jf_status select_variant(jf_ctx* h, int v, bool prepare) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = variant_list<T>(h->dim, visc, general_scheme(h->scheme));
+  auto list = variant_list<T>(h->dim, visc, scheme_kind(h->scheme));
   if (list.empty()) { set_error(h, "no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
   if (v < 0) v = 0;
   if (v >= (int)list.size()) { set_error(h, "variant index out of range"); return JF_ERR_ARG; }
@@ -178,13 +180,14 @@ jf_status select_variant(jf_ctx* h, int v, bool prepare) {
 template <typename T>
 int describe_variant(jf_ctx* h, int v, char* buf, int len) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = variant_list<T>(h->dim, visc, general_scheme(h->scheme));
+  auto list = variant_list<T>(h->dim, visc, scheme_kind(h->scheme));
   if (v < 0 || v >= (int)list.size()) return (int)list.size();
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
   const StageVariant<T>& s = tab[list[v].first];
   if (buf && len > 0)
-    std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=%d smem=%zu", s.bx, s.by, s.dim == 3 ? list[v].second : 1, s.smem);
+    std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=%d smem=%zu ctas/sm=%d", s.bx, s.by,
+                  s.dim == 3 ? list[v].second : 1, s.smem, s.minb);
   return (int)list.size();
 }
 

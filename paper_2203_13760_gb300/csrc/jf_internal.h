@@ -81,8 +81,9 @@ jf_status check_physics(jf_ctx* h, const jf_gas& gas, const jf_scheme& s);
 double spacing(const jf_grid& g, int d);
 double conductivity(const jf_gas& gas, const jf_scheme& s);
 bool dissipative(const jf_gas& gas, const jf_scheme& s);
-// a Table 2 variant that needs the run-time-scheme kernels
-bool general_scheme(const jf_scheme& s);
+// kernel family of a scheme: SCH_DEFAULT, SCH_GENERAL (run-time Table 2
+// Godunov variants) or SCH_ROE (flux splitting)
+int scheme_kind(const jf_scheme& s);
 CflArgs make_cfl(const jf_grid& g, const jf_gas& gas, const jf_scheme& s);
 int reduce_blocks(long long N, int sms);
 bool aligned16(const void* p);

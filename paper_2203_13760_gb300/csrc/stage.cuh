@@ -180,20 +180,115 @@ template <> struct Roles<2> {
   __device__ static void map(int n, int t1, int t2, int& x, int& y, int& e) { x = t1; y = t2; e = n; }
 };
 
+// Scheme codes of the stage kernels (template parameter SCH).
+enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2 };
+
+// Flux-splitting face flux of the ROE setup (Section 3.3, Flux-Splitting
+// approach; Section 5): Roe average of the two cells beside the face, the
+// eigenvectors of the flux Jacobian there, the six stencil cells' conservative
+// states U_j and fluxes F_j projected on the characteristic fields
+// (V_j = L U_j, G_j = L F_j), Roe splitting G+-_j = (G_j +- |lambda| V_j) / 2,
+// WENO5 of G+ (left-biased, cells -2..2) and G- (mirrored, cells 3..-1) per
+// field, and the sum transformed back, F = R (G+ + G-).  L and R are applied
+// in closed form (b1 = (gamma - 1) / c^2, b2 = b1 |u|^2 / 2,
+// s(X) = b2 X_0 - b1 u.X_m + b1 X_4, d(X) = (u_n X_0 - X_n) / c):
+//   L X = [(s + d) / 2, X_0 - s, X_t1 - u_t1 X_0, X_t2 - u_t2 X_0, (s - d) / 2],
+//   R G: mass = G0 + G1 + G4 =: S, momentum u S + c n (G4 - G0) + t1 G2 + t2 G3,
+//        energy H (G0 + G4) + u_n c (G4 - G0) + |u|^2 / 2 G1 + u_t1 G2 + u_t2 G3.
+template <typename T, int D, typename Val>
+__device__ __forceinline__ void fs_flux(const Val& val, const Gas<T>& g, int recon, T F[5]) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  // Roe average
+  const T rL = val(0, 0), rR = val(0, 1);
+  const T sL = tsqrt(rL), sR = tsqrt(rR), is = trcp(sL + sR);
+  T u[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) u[m] = (sL * val(1 + m, 0) + sR * val(1 + m, 1)) * is;
+  const T kH = g.gamma * g.inv_gm1;  // H = gamma/(gamma-1) p/rho + |u|^2/2
+  const T qL = val(1, 0) * val(1, 0) + val(2, 0) * val(2, 0) + val(3, 0) * val(3, 0);
+  const T qR = val(1, 1) * val(1, 1) + val(2, 1) * val(2, 1) + val(3, 1) * val(3, 1);
+  const T HL = kH * val(4, 0) * trcp(rL) + T(0.5) * qL;
+  const T HR = kH * val(4, 1) * trcp(rR) + T(0.5) * qR;
+  const T H = (sL * HL + sR * HR) * is;
+  const T q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T c2 = g.gm1 * (H - T(0.5) * q2);
+  const T c = tsqrt(c2), ic = trcp(c);
+  const T b1 = g.gm1 * trcp(c2), b2 = T(0.5) * b1 * q2;
+  const T un = u[D];
+  const T a0 = T(0.5) * fabs(un - c), a1 = T(0.5) * fabs(un), a4 = T(0.5) * fabs(un + c);
+  // projected, split fluxes: Pp[k][j] = G+_j (j = 0..4 for cells -2..2),
+  // Pm[k][j] = G-_{5-j} (j = 0..4 for cells 3..-1), field k
+  T Pp[5][5], Pm[5][5];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int n = j - 2;
+    const T r = val(0, n), v0 = val(1, n), v1 = val(2, n), v2 = val(3, n), p = val(4, n);
+    const T vn = D == 0 ? v0 : (D == 1 ? v1 : v2);
+    const T E = p * g.inv_gm1 + T(0.5) * r * (v0 * v0 + v1 * v1 + v2 * v2);
+    const T U[5] = {r, r * v0, r * v1, r * v2, E};
+    const T mass = r * vn;
+    T Fj[5] = {mass, mass * v0, mass * v1, mass * v2, vn * (E + p)};
+    Fj[1 + D] += p;
+    T V[5], G[5];
+    auto project = [&](const T X[5], T Y[5]) {
+      const T s = b2 * X[0] - b1 * (u[0] * X[1] + u[1] * X[2] + u[2] * X[3]) + b1 * X[4];
+      const T d = (un * X[0] - X[1 + D]) * ic;
+      Y[0] = T(0.5) * (s + d);
+      Y[1] = X[0] - s;
+      Y[2] = X[1 + T1] - u[T1] * X[0];
+      Y[3] = X[1 + T2] - u[T2] * X[0];
+      Y[4] = T(0.5) * (s - d);
+    };
+    project(U, V);
+    project(Fj, G);
+    const T a[5] = {a0, a1, a1, a1, a4};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const T half_g = T(0.5) * G[k];
+      if (j <= 4) Pp[k][j] = half_g + a[k] * V[k];
+      if (j >= 1) Pm[k][5 - j] = half_g - a[k] * V[k];
+    }
+  }
+  T Gh[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if constexpr (sizeof(T) == 4) {
+      const float2 r = weno5_pair(make_float2(Pp[k][0], Pm[k][0]), make_float2(Pp[k][1], Pm[k][1]),
+                                  make_float2(Pp[k][2], Pm[k][2]), make_float2(Pp[k][3], Pm[k][3]),
+                                  make_float2(Pp[k][4], Pm[k][4]), g.eps, recon);
+      Gh[k] = r.x + r.y;
+    } else {
+      Gh[k] = weno5(Pp[k][0], Pp[k][1], Pp[k][2], Pp[k][3], Pp[k][4], g.eps, recon) +
+              weno5(Pm[k][0], Pm[k][1], Pm[k][2], Pm[k][3], Pm[k][4], g.eps, recon);
+    }
+  }
+  const T S = Gh[0] + Gh[1] + Gh[4], Dw = Gh[4] - Gh[0];
+  F[0] = S;
+  F[1 + D] = u[D] * S + c * Dw;
+  F[1 + T1] = u[T1] * S + Gh[2];
+  F[1 + T2] = u[T2] * S + Gh[3];
+  F[4] = H * (Gh[0] + Gh[4]) + un * c * Dw + T(0.5) * q2 * Gh[1] + u[T1] * Gh[2] + u[T2] * Gh[3];
+}
+
 // Net flux NF = F^d - F through the face between the cell at shared-memory
 // position (x0, y0, plane 0) and its neighbour along D.
-// GEN = false: the default scheme (WENO5-JS, HLLC, Einfeldt speeds) compiled
-// alone; GEN = true: the Table 2 variants chosen at run time from g.
-template <typename T, int D, int BX, int BY, int DIM, bool VISC, bool GEN>
+// SCH_DEFAULT: the default scheme (WENO5-JS, HLLC, Einfeldt speeds) compiled
+// alone; SCH_GENERAL: the Table 2 Godunov variants chosen at run time from g;
+// SCH_ROE: the flux-splitting ROE setup (reconstruction chosen from g).
+template <typename T, int D, int BX, int BY, int DIM, bool VISC, int SCH>
 __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
                                           const Gas<T>& g, const T inv_h[3], T NF[5]) {
   using Ro = Roles<D>;
-  const int recon = GEN ? g.recon : 0;
+  const int recon = SCH == SCH_DEFAULT ? 0 : g.recon;
   auto val = [&](int c, int n, int t1, int t2) -> T {
     int x, y, e;
     Ro::map(n, t1, t2, x, y, e);
     return R.at(c, x0 + x, y0 + y, e);
   };
+  T F[5];
+  if constexpr (SCH == SCH_ROE) {
+    fs_flux<T, D>([&](int c, int n) { return val(c, n, 0, 0); }, g, recon, F);
+  } else {
   // WENO5-JS left / right states of each primitive component (Section 3.3)
   T Wm[5], Wp[5];
 #pragma unroll
@@ -220,9 +315,9 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
       for (int c = 0; c < 5; ++c) Wp[c] = val(c, 1, 0, 0);
     }
   }
-  T F[5];
-  if constexpr (GEN) riemann_flux<T, D>(Wm, Wp, g, F);
+  if constexpr (SCH == SCH_GENERAL) riemann_flux<T, D>(Wm, Wp, g, F);
   else hllc<T, D>(Wm, Wp, g, F, 0);
+  }
 #pragma unroll
   for (int c = 0; c < 5; ++c) NF[c] = -F[c];
   if constexpr (VISC) {
@@ -343,7 +438,7 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
 // for its cells.  Shared memory: the ring and the face buffers.  All threads
 // of the CTA call it; it starts and ends without pending shared-memory reads
 // that a following call could disturb (the first barrier inside orders them).
-template <typename T, int DIM, bool VISC, int BX, int BY, bool GEN>
+template <typename T, int DIM, bool VISC, int BX, int BY, int SCH>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& g, int bx, int by, int bz,
                                            T* smem) {
   using G = Geo<BX, BY, DIM, VISC>;
@@ -402,7 +497,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     // lower face of plane z0 = upper face of plane z0 - 1 (slot 2); plane
     // offset -3 is never read
     set_view(5);
-    if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, GEN>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+    if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
     __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
     load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, z0 + 3);
     if (z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC>(A, next, gx0, gy0, z0 + 4);
@@ -428,20 +523,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
 
     if (xf_x >= 0) {
       T NF[5];
-      face_flux<T, 0, BX, BY, DIM, VISC, GEN>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
+      face_flux<T, 0, BX, BY, DIM, VISC, SCH>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
       const int t = xf_y * (BX + 1) + xf_x;
 #pragma unroll
       for (int c = 0; c < 5; ++c) Fx[c * G::NFX + t] = NF[c];
     }
     if (DIM >= 2) {
       T NF[5];
-      face_flux<T, 1, BX, BY, DIM, VISC, GEN>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
+      face_flux<T, 1, BX, BY, DIM, VISC, SCH>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
       const int t = yf_y * BX + yf_x;
 #pragma unroll
       for (int c = 0; c < 5; ++c) Fy[c * G::NFY + t] = NF[c];
     }
     T NFz_hi[5];
-    if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, GEN>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+    if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
     __syncthreads();
 
     if (own) {
@@ -509,7 +604,7 @@ struct WorkItem {
 //    U = 1/2 U + 1/2 (U1 + dt L(U1)).
 // Both forms reach the tile computation through the same call below, so a
 // simulation advanced in a batch is bitwise the one advanced alone.
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, bool GEN>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
     stage_kernel(const StageArgs<T> A0, const SimDesc<T>* __restrict__ sims, const WorkItem* __restrict__ work,
                  int nwork, int stage, const Gas<T> g) {
@@ -550,7 +645,7 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
     } else if (item != (int)blockIdx.x) {
       break;
     }
-    stage_tile<T, DIM, VISC, BX, BY, GEN>(A, g, bx, by, bz, reinterpret_cast<T*>(smem_raw));
+    stage_tile<T, DIM, VISC, BX, BY, SCH>(A, g, bx, by, bz, reinterpret_cast<T*>(smem_raw));
   }
 }
 

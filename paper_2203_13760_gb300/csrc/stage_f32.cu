@@ -9,30 +9,33 @@
 namespace jf {
 
 // The default-scheme kernels (WENO5-JS, HLLC, Einfeldt) of every tile shape,
-// then the run-time-scheme kernels of stage_f32_gen.cu (one tile shape each).
+// then the run-time-scheme kernels of stage_f32_gen.cu (one tile shape each)
+// and the flux-splitting kernels of stage_f32_roe.cu.
 template <>
 const StageVariant<float>* stage_variants<float>(int* count) {
   static const std::vector<StageVariant<float>> table = [] {
     std::vector<StageVariant<float>> v = {
       // 3D (the first entry per configuration is the default)
-      make_variant<float, 3, true, 32, 8, 2, false>(),
-      make_variant<float, 3, true, 32, 6, 3, false>(),
-      make_variant<float, 3, true, 32, 4, 3, false>(),
-      make_variant<float, 3, false, 32, 8, 2, false>(),
-      make_variant<float, 3, false, 32, 6, 3, false>(),
-      make_variant<float, 3, false, 32, 4, 3, false>(),
+      make_variant<float, 3, true, 32, 8, 2, SCH_DEFAULT>(),
+      make_variant<float, 3, true, 32, 6, 3, SCH_DEFAULT>(),
+      make_variant<float, 3, true, 32, 4, 3, SCH_DEFAULT>(),
+      make_variant<float, 3, false, 32, 8, 2, SCH_DEFAULT>(),
+      make_variant<float, 3, false, 32, 6, 3, SCH_DEFAULT>(),
+      make_variant<float, 3, false, 32, 4, 3, SCH_DEFAULT>(),
       // 2D
-      make_variant<float, 2, true, 32, 8, 2, false>(),
-      make_variant<float, 2, true, 32, 4, 4, false>(),
-      make_variant<float, 2, false, 32, 8, 2, false>(),
-      make_variant<float, 2, false, 32, 4, 4, false>(),
+      make_variant<float, 2, true, 32, 8, 2, SCH_DEFAULT>(),
+      make_variant<float, 2, true, 32, 4, 4, SCH_DEFAULT>(),
+      make_variant<float, 2, false, 32, 8, 2, SCH_DEFAULT>(),
+      make_variant<float, 2, false, 32, 4, 4, SCH_DEFAULT>(),
       // 1D
-      make_variant<float, 1, true, 128, 1, 2, false>(),
-      make_variant<float, 1, false, 128, 1, 2, false>(),
+      make_variant<float, 1, true, 128, 1, 2, SCH_DEFAULT>(),
+      make_variant<float, 1, false, 128, 1, 2, SCH_DEFAULT>(),
     };
     int ng = 0;
     const StageVariant<float>* gen = general_variants_f32(&ng);
     v.insert(v.end(), gen, gen + ng);
+    const StageVariant<float>* roe = roe_variants_f32(&ng);
+    v.insert(v.end(), roe, roe + ng);
     return v;
   }();
   *count = (int)table.size();

@@ -6,28 +6,31 @@
 namespace jf {
 
 // The default-scheme kernels (WENO5-JS, HLLC, Einfeldt) of every tile shape,
-// then the run-time-scheme kernels of stage_f64_gen.cu (one tile shape each).
+// then the run-time-scheme kernels of stage_f64_gen.cu (one tile shape each)
+// and the flux-splitting kernels of stage_f64_roe.cu.
 template <>
 const StageVariant<double>* stage_variants<double>(int* count) {
   static const std::vector<StageVariant<double>> table = [] {
     std::vector<StageVariant<double>> v = {
       // 3D (the first entry per configuration is the default)
-      make_variant<double, 3, true, 32, 4, 1, false>(),
-      make_variant<double, 3, true, 32, 2, 2, false>(),
-      make_variant<double, 3, false, 32, 4, 1, false>(),
-      make_variant<double, 3, false, 32, 2, 2, false>(),
+      make_variant<double, 3, true, 32, 4, 1, SCH_DEFAULT>(),
+      make_variant<double, 3, true, 32, 2, 2, SCH_DEFAULT>(),
+      make_variant<double, 3, false, 32, 4, 1, SCH_DEFAULT>(),
+      make_variant<double, 3, false, 32, 2, 2, SCH_DEFAULT>(),
       // 2D
-      make_variant<double, 2, true, 32, 8, 1, false>(),
-      make_variant<double, 2, true, 32, 4, 2, false>(),
-      make_variant<double, 2, false, 32, 8, 1, false>(),
-      make_variant<double, 2, false, 32, 4, 2, false>(),
+      make_variant<double, 2, true, 32, 8, 1, SCH_DEFAULT>(),
+      make_variant<double, 2, true, 32, 4, 2, SCH_DEFAULT>(),
+      make_variant<double, 2, false, 32, 8, 1, SCH_DEFAULT>(),
+      make_variant<double, 2, false, 32, 4, 2, SCH_DEFAULT>(),
       // 1D
-      make_variant<double, 1, true, 128, 1, 1, false>(),
-      make_variant<double, 1, false, 128, 1, 1, false>(),
+      make_variant<double, 1, true, 128, 1, 1, SCH_DEFAULT>(),
+      make_variant<double, 1, false, 128, 1, 1, SCH_DEFAULT>(),
     };
     int ng = 0;
     const StageVariant<double>* gen = general_variants_f64(&ng);
     v.insert(v.end(), gen, gen + ng);
+    const StageVariant<double>* roe = roe_variants_f64(&ng);
+    v.insert(v.end(), roe, roe + ng);
     return v;
   }();
   *count = (int)table.size();

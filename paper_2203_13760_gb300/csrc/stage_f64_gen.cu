@@ -1,18 +1,18 @@
 // FP64 stage kernels with the scheme chosen at run time (Table 2 variants:
-// HLL / Rusanov fluxes, Davis / Toro signal speeds, WENO5-Z), one tile shape
-// per dimensionality and physics.
+// HLL / Rusanov fluxes, Davis / Toro signal speeds, WENO5-Z), one tile shape per dimensionality
+// and physics.
 #include "stage_inst.cuh"
 
 namespace jf {
 
 const StageVariant<double>* general_variants_f64(int* count) {
   static const StageVariant<double> table[] = {
-      make_variant<double, 3, true, 32, 4, 1, true>(),
-      make_variant<double, 3, false, 32, 4, 1, true>(),
-      make_variant<double, 2, true, 32, 8, 1, true>(),
-      make_variant<double, 2, false, 32, 8, 1, true>(),
-      make_variant<double, 1, true, 128, 1, 1, true>(),
-      make_variant<double, 1, false, 128, 1, 1, true>(),
+      make_variant<double, 3, true, 32, 4, 1, SCH_GENERAL>(),
+      make_variant<double, 3, false, 32, 4, 1, SCH_GENERAL>(),
+      make_variant<double, 2, true, 32, 8, 1, SCH_GENERAL>(),
+      make_variant<double, 2, false, 32, 8, 1, SCH_GENERAL>(),
+      make_variant<double, 1, true, 128, 1, 1, SCH_GENERAL>(),
+      make_variant<double, 1, false, 128, 1, 1, SCH_GENERAL>(),
   };
   *count = (int)(sizeof(table) / sizeof(table[0]));
   return table;

@@ -5,51 +5,51 @@
 namespace jf {
 
 // MINB: CTAs per SM the register allocation must allow (__launch_bounds__).
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, bool GEN>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t prepare_stage() {
   constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
-  return cudaFuncSetAttribute(stage_kernel<T, DIM, VISC, BX, BY, MINB, GEN>,
+  return cudaFuncSetAttribute(stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, bool GEN>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t launch_stage(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s) {
   constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
   const dim3 grid((A.nx + BX - 1) / BX, DIM >= 2 ? (A.ny + BY - 1) / BY : 1,
                   DIM == 3 ? (A.nz + A.zchunk - 1) / A.zchunk : 1);
-  stage_kernel<T, DIM, VISC, BX, BY, MINB, GEN><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, nullptr, nullptr, 0, 0,
+  stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, nullptr, nullptr, 0, 0,
                                                                                           g);
   return cudaGetLastError();
 }
 
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, bool GEN>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t prepare_batch(int* blocks_per_sm) {
   constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
-  auto k = stage_kernel<T, DIM, VISC, BX, BY, MINB, GEN>;
+  auto k = stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, Geo<BX, BY, DIM, VISC>::NT, smem);
 }
 
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, bool GEN>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t launch_batch(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
                          int* flag, int grid, cudaStream_t s) {
   constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
   StageArgs<T> A{};
   A.flag = flag;
-  stage_kernel<T, DIM, VISC, BX, BY, MINB, GEN><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, sims, work, nwork,
+  stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, sims, work, nwork,
                                                                                           stage, g);
   return cudaGetLastError();
 }
 
-template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, bool GEN>
+template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 StageVariant<T> make_variant() {
   StageVariant<T> v{DIM, VISC, BX, BY, stage_smem_bytes<T, DIM, VISC, BX, BY>(),
-                    &prepare_stage<T, DIM, VISC, BX, BY, MINB, GEN>, &launch_stage<T, DIM, VISC, BX, BY, MINB, GEN>,
-                    nullptr, nullptr, Geo<BX, BY, DIM, VISC>::NT, GEN};
+                    &prepare_stage<T, DIM, VISC, BX, BY, MINB, SCH>, &launch_stage<T, DIM, VISC, BX, BY, MINB, SCH>,
+                    nullptr, nullptr, Geo<BX, BY, DIM, VISC>::NT, SCH, MINB};
   if constexpr (DIM <= 2) {  // batches are built for 1D and 2D grids
-    v.prepare_batch = &prepare_batch<T, DIM, VISC, BX, BY, MINB, GEN>;
-    v.launch_batch = &launch_batch<T, DIM, VISC, BX, BY, MINB, GEN>;
+    v.prepare_batch = &prepare_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
+    v.launch_batch = &launch_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
   }
   return v;
 }

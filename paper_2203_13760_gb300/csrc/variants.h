@@ -25,16 +25,20 @@ struct StageVariant {
   cudaError_t (*launch_batch)(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
                               int* flag, int grid, cudaStream_t s);
   int threads;
-  bool general;  // compiled with the run-time scheme choice (Table 2 variants)
+  int scheme;    // SCH_DEFAULT, SCH_GENERAL (run-time Table 2 choice) or SCH_ROE
+  int minb;      // CTAs per SM the register allocation was bounded for
 };
 
 // All compiled variants for precision T (defined in stage_f32.cu / stage_f64.cu).
 template <typename T>
 const StageVariant<T>* stage_variants(int* count);
 
-// The run-time-scheme kernels (general = true), in their own translation
-// units (stage_f32_gen.cu / stage_f64_gen.cu) so that they compile in parallel.
+// The run-time-scheme kernels (SCH_GENERAL) and the flux-splitting kernels
+// (SCH_ROE), in their own translation units (stage_*_gen.cu, stage_*_roe.cu)
+// so that they compile in parallel with the default ones.
 const StageVariant<float>* general_variants_f32(int* count);
 const StageVariant<double>* general_variants_f64(int* count);
+const StageVariant<float>* roe_variants_f32(int* count);
+const StageVariant<double>* roe_variants_f64(int* count);
 
 }  // namespace jf

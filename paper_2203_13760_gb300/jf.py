@@ -47,7 +47,7 @@ class Scheme(ctypes.Structure):
 
 
 # scheme options of include/jf.h (0: the default configuration)
-FLUX = {"hllc": 0, "hll": 1, "rusanov": 2}
+FLUX = {"hllc": 0, "hll": 1, "rusanov": 2, "roe": 3}
 RECON = {"weno5-js": 0, "weno5-z": 1}
 SPEEDS = {"einfeldt": 0, "davis": 1, "toro": 2}
 INTEGRATOR = {"rk3": 0, "rk2": 1, "euler": 2}

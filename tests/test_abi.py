@@ -58,8 +58,8 @@ def test_bad_arguments_rejected_on_host(libjf):
     visc = libjf.make_scheme("f32", viscous=True)  # viscous with mu = 0
     assert L.jf_init(ctypes.byref(grid), ctypes.byref(gas), ctypes.byref(visc), ctypes.byref(h)) == libjf.JF_ERR_ARG
     assert L.jf_init(None, None, None, None) == libjf.JF_ERR_ARG
-    # scheme options out of range (Table 2 variants are 0..2 / 0..1)
-    for field, value in (("flux", 3), ("recon", 2), ("signal_speed", 3), ("integrator", -1)):
+    # scheme options out of range (flux 0..3, recon 0..1, speeds and integrators 0..2)
+    for field, value in (("flux", 4), ("recon", 2), ("signal_speed", 3), ("integrator", -1)):
         bad = libjf.make_scheme("f32")
         setattr(bad, field, value)
         assert L.jf_init(ctypes.byref(grid), ctypes.byref(gas), ctypes.byref(bad), ctypes.byref(h)) == libjf.JF_ERR_ARG

@@ -1,5 +1,6 @@
 """Scheme variants of Table 2 on the GPU (HLL, Rusanov, Davis and Toro
-signal speeds, WENO5-Z, TVD-RK2, Euler) against the oracle, through the C ABI.
+signal speeds, WENO5-Z, TVD-RK2, Euler) and the flux-splitting ROE setup
+against the oracle, through the C ABI.
 
 Same norms and bars as test_gpu_parity.py: FP64 <= 1e-12 (right-hand side
 relative to the flux scale, states per conserved group), FP32 <= 1e-5 after
@@ -29,6 +30,8 @@ SCHEMES = {
     "hllc_toro_z": dict(speeds="toro", recon="weno5-z"),
     "hllc_z_rk2": dict(recon="weno5-z", integrator="rk2"),
     "hll_euler": dict(flux="hll", integrator="euler"),
+    "roe": dict(flux="roe"),
+    "roe_z_rk2": dict(flux="roe", recon="weno5-z", integrator="rk2"),
 }
 
 CASES = {
@@ -65,7 +68,7 @@ def test_variant_rhs_and_steps_fp64(orc, scheme, name):
     assert rel_err(U.cpu().numpy(), want) <= 1e-12
 
 
-@pytest.mark.parametrize("scheme", ["hll_davis_z", "rusanov", "hllc_toro_z", "hllc_z_rk2", "hll_euler"])
+@pytest.mark.parametrize("scheme", ["hll_davis_z", "rusanov", "hllc_toro_z", "hllc_z_rk2", "hll_euler", "roe"])
 def test_variant_ten_steps_fp32(orc, scheme):
     case = with_scheme(inputs.random_smooth((19, 13, 11), seed=6, viscous=True, mu=0.01), **SCHEMES[scheme])
     c = orc.config(**case.params())
@@ -82,7 +85,7 @@ def test_variant_ten_steps_fp32(orc, scheme):
 
 
 @pytest.mark.parametrize("problem", ["sod", "lax"])
-@pytest.mark.parametrize("scheme", ["hll_einfeldt", "hll_toro", "rusanov", "hllc_davis", "hllc_toro_z"])
+@pytest.mark.parametrize("scheme", ["hll_einfeldt", "hll_toro", "rusanov", "hllc_davis", "hllc_toro_z", "roe"])
 def test_shock_tubes_gpu(orc, problem, scheme):
     """Section 5.1.2 at the paper's N = 100: the FP64 GPU run to the end time
     equals the oracle's run, and both follow the exact Riemann solution."""
@@ -113,7 +116,7 @@ def test_shock_tubes_gpu(orc, problem, scheme):
     assert np.mean(np.abs(got[0, 0, 0] - ex[:, 0])) < (6.5e-3 if problem == "sod" else 2.2e-2)
 
 
-@pytest.mark.parametrize("scheme", ["hll_euler", "hllc_z_rk2", "hll_toro"])
+@pytest.mark.parametrize("scheme", ["hll_euler", "hllc_z_rk2", "hll_toro", "roe"])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_batch_variant_equals_single_grid(scheme, dtype):
     """The batch form of each integrator and solver (stage codes and the
@@ -136,6 +139,23 @@ def test_batch_variant_equals_single_grid(scheme, dtype):
         s.sync()
         assert torch.equal(U, Us[i]), f"simulation {i} differs"
         assert dts[i].item() == used.item()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_roe_launch_variants_agree(dtype):
+    """Every compiled tile shape of the ROE kernels computes the same bits."""
+    case = with_scheme(inputs.random_smooth((19, 13, 11), seed=6, viscous=True, mu=0.01), flux="roe")
+    s = jf.Solver.from_case(case, dtype=dtype)
+    U0 = to_dev(case.U, dtype)
+    ref = None
+    for v in range(len(s.variants())):
+        s.set_variant(v)
+        out = s.rhs(U0)
+        s.sync()
+        if ref is None:
+            ref = out
+        else:
+            assert torch.equal(out, ref), s.variants()[v]
 
 
 def test_adjoint_rejects_variant_schemes():
