@@ -11,15 +11,25 @@ namespace jf {
 // The default-scheme kernels (WENO5-JS, HLLC, Einfeldt) of every tile shape,
 // then the run-time-scheme kernels of stage_f32_gen.cu (one tile shape each)
 // and the flux-splitting kernels of stage_f32_roe.cu.
+// 3D default tile: 32 x 7 cells, 8 warps (seven face/cell rows and the warp
+// of the extra faces), two CTAs per SM.  Registers are allocated to warps in
+// groups of four, so two 9-warp CTAs (32 x 8) count as 20 warps and cap a
+// thread at 96 registers (the kernel then spills); two 8-warp CTAs allow
+// 128.  Measured at TGV 256^3: 32 x 7 1.64 ms, 32 x 8 1.75 ms, 32 x 15 (one
+// CTA per SM) 1.77 ms.
 template <>
 const StageVariant<float>* stage_variants<float>(int* count) {
   static const std::vector<StageVariant<float>> table = [] {
     std::vector<StageVariant<float>> v = {
       // 3D (the first entry per configuration is the default)
+      make_variant<float, 3, true, 32, 7, 2, SCH_DEFAULT>(),
       make_variant<float, 3, true, 32, 8, 2, SCH_DEFAULT>(),
+      make_variant<float, 3, true, 32, 15, 1, SCH_DEFAULT>(),
       make_variant<float, 3, true, 32, 6, 3, SCH_DEFAULT>(),
       make_variant<float, 3, true, 32, 4, 3, SCH_DEFAULT>(),
+      make_variant<float, 3, false, 32, 7, 2, SCH_DEFAULT>(),
       make_variant<float, 3, false, 32, 8, 2, SCH_DEFAULT>(),
+      make_variant<float, 3, false, 32, 15, 1, SCH_DEFAULT>(),
       make_variant<float, 3, false, 32, 6, 3, SCH_DEFAULT>(),
       make_variant<float, 3, false, 32, 4, 3, SCH_DEFAULT>(),
       // 2D

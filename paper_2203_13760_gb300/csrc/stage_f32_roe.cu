@@ -2,9 +2,10 @@
 // Flux-Splitting approach; Section 5), in several tile shapes: the larger face
 // computation needs more registers than the Godunov kernels, and which
 // register / occupancy trade-off wins is measured (jf_set_variant, autotune).
-// The first 3D entry is the default: at TGV 256^3 the 32 x 8 tile with two
-// CTAs per SM (96 registers, its spills served by L1) ran fastest, ahead of
-// 32 x 8 at one CTA per SM (168 registers, no spills).
+// The first 3D entry is the default.  Measured at TGV 256^3 (viscous, stage
+// ms): 32 x 7 at two CTAs per SM (8 warps, 128 registers) 2.43; 32 x 15 at
+// one (16 warps, 128 registers) 2.41; 32 x 8 at two (9 warps: 96 registers,
+// spilling) 2.87; 32 x 8 at one (168 registers) 2.88.
 // Compiled with the same approximate division and square root as stage_f32.cu.
 #include "stage_inst.cuh"
 
@@ -12,10 +13,14 @@ namespace jf {
 
 const StageVariant<float>* roe_variants_f32(int* count) {
   static const StageVariant<float> table[] = {
+      make_variant<float, 3, true, 32, 7, 2, SCH_ROE>(),
+      make_variant<float, 3, true, 32, 15, 1, SCH_ROE>(),
       make_variant<float, 3, true, 32, 8, 2, SCH_ROE>(),
       make_variant<float, 3, true, 32, 8, 1, SCH_ROE>(),
       make_variant<float, 3, true, 32, 4, 2, SCH_ROE>(),
       make_variant<float, 3, true, 32, 4, 3, SCH_ROE>(),
+      make_variant<float, 3, false, 32, 7, 2, SCH_ROE>(),
+      make_variant<float, 3, false, 32, 15, 1, SCH_ROE>(),
       make_variant<float, 3, false, 32, 8, 2, SCH_ROE>(),
       make_variant<float, 3, false, 32, 8, 1, SCH_ROE>(),
       make_variant<float, 3, false, 32, 4, 2, SCH_ROE>(),

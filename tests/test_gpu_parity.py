@@ -180,18 +180,35 @@ def test_deterministic():
     assert torch.equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
-def test_variants_agree(variant):
-    """Every launch variant (tile shape / z chunk) gives the same bits."""
-    case = inputs.random_smooth((40, 24, 20), seed=12, viscous=True, mu=0.01)
-    s = solver_for(case, "f32")
-    U = to_dev(case.U, "f32")
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("viscous", [True, False])
+def test_variants_agree(orc, dtype, viscous):
+    """Every launch variant (tile shape / z chunk / CTAs per SM), on a grid
+    that is ragged for every tile shape: the z chunks of one tile shape give
+    the same bits; different tile shapes are separate instantiations of the
+    same expressions, whose multiply-adds the compiler may contract
+    differently, so they agree to rounding (FP64 <= 1e-13, FP32 <= 2e-6 of
+    the flux scale) and every one meets the oracle bar."""
+    case = inputs.random_smooth((40, 29, 23), seed=12, viscous=viscous, mu=0.01)
+    c = orc.config(**case.params())
+    want = orc.rhs(c, case.U)
+    rate = case.cfl / orc.compute_dt(c, case.U)
+    U64 = case.U if dtype == "f64" else case.U.astype(np.float32).astype(np.float64)
+    s = solver_for(case, dtype)
+    U = to_dev(U64, dtype)
+    names = s.variants()
     ref = s.rhs(U).clone()
-    nv = len(s.variants())
-    s.set_variant(variant % nv)
-    got = s.rhs(U)
-    s.sync()
-    assert torch.equal(ref, got)
+    ref_np = ref.double().cpu().numpy()
+    tol = 1e-13 if dtype == "f64" else 2e-6
+    for v in range(1, len(names)):
+        s.set_variant(v)
+        got = s.rhs(U)
+        s.sync()
+        if names[v].split(" zchunk")[0] == names[0].split(" zchunk")[0]:
+            assert torch.equal(ref, got), names[v]
+        assert rate_err(got.double().cpu().numpy(), ref_np, U64, rate) <= tol, names[v]
+        if dtype == "f64":
+            assert rate_err(got.cpu().numpy(), want, case.U, rate) <= 1e-12, names[v]
 
 
 def test_sod_gpu_against_exact(orc):
