@@ -506,10 +506,23 @@ def run_batched(steps=100, nsim=64):
     t_plain = e0.elapsed_time(e1) * 1e-3
     # the batch advanced 2 x steps, the graph path 2 x steps: same states
     same = all(torch.equal(U, V) for U, V in zip(Us, Vs))
+    # feed_forward: the trajectories of fixed-dt steps (every state kept)
+    dts = [0.5 * x for x in b.step(Us, 1).tolist()]
+    ff_steps = 20
+    b.feed_forward(Us, ff_steps, dts)
+    torch.cuda.synchronize()
+    e0.record()
+    trajs = b.feed_forward(Us, ff_steps, dts)
+    e1.record()
+    torch.cuda.synchronize()
+    t_ff = e0.elapsed_time(e1) * 1e-3
+    del trajs
     return {"workload": f"{nsim} four-quadrant Riemann problems, sides {{64,128,256,512}}, FP32, CFL 0.5",
             "cells": cells, "steps": steps, "unit": "cell-updates/s",
             "batched": cells * steps / t_batch, "plain_graph_per_sim": cells * steps / t_graph,
             "plain_per_step_calls": cells * steps / t_plain,
+            "feed_forward_trajectory": cells * ff_steps / t_ff,
+            "feed_forward_note": f"{ff_steps} fixed-dt steps with every state stored (jf_batch_feed_forward)",
             "speedup_vs_graph_per_sim": t_graph / t_batch, "speedup_vs_per_step_calls": t_plain / t_batch,
             "bitwise_equal_to_plain": bool(same), "gpu_launches_batched": 4 * steps}
 

@@ -201,6 +201,21 @@ jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, con
  * at the first call for a given (U_ptrs, nsteps) and replayed afterwards. */
 jf_status jf_batch_step(jf_handle batch, void* const* U_ptrs, int nsteps, double* dt_dev, void* stream);
 
+/* feed_forward of Section 4.5: the solution trajectories of a batch for
+ * nsteps steps of a FIXED step per simulation.  U0_ptrs: HOST array of nsim
+ * device pointers to the initial states (read only).  traj_ptrs: HOST array of
+ * nsim device pointers, simulation s owning (nsteps + 1) * 5 * N_s elements
+ * of the batch's dtype laid out [t][5][nz][ny][nx]: slot 0 receives U0, slot
+ * t + 1 one step of slot t (the paper's (N_b, N_T + 1, 5, ...) trajectory,
+ * per simulation since sizes may differ).  dt_dev: device array of nsim FP64
+ * steps.  The integrator of the scheme is used; the arithmetic is that of
+ * jf_batch_step and jf_rk3_step, so slot t equals t fixed-dt steps of the
+ * single-grid path bit for bit.  Asynchronous on `stream` except for the
+ * upload of the per-call pointer tables (a stream-ordered allocation, freed
+ * on the stream). */
+jf_status jf_batch_feed_forward(jf_handle batch, void* const* U0_ptrs, void* const* traj_ptrs, int nsteps,
+                                const double* dt_dev, void* stream);
+
 /* Choose the launch variant of a handle (autotuner hook): `variant` indexes
  * the tile/schedule table of jf_variant_info; -1 restores the default.
  * Returns JF_ERR_ARG for an index outside the table. */

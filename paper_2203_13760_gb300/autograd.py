@@ -12,6 +12,13 @@ a fixed step).
 ``density_l2(solver, U, target)``
                               sum_cells (rho - target)^2 dV (jf_loss_density_l2)
                               with its gradient.
+``feed_forward(batch, U0s, n, dt)``
+                              Section 4.5: the trajectories of a batch of
+                              (uneven) simulations, differentiable w.r.t. the
+                              initial states (reverse sweep on the stored
+                              trajectory with jf_rk3_step_vjp).
+``trajectory_mse(trajs, refs)``
+                              Section 7.2: 1/N_T sum_i MSE(U^i, U^i_ref).
 
 dt is a float64 CUDA scalar tensor and is not differentiated (the paper's
 feed_forward uses a fixed step).  Every computation runs in libjf's kernels.
@@ -95,3 +102,51 @@ class _DensityL2(torch.autograd.Function):
 
 def density_l2(solver, U, target):
     return _DensityL2.apply(U, solver, target)
+
+
+class _FeedForward(torch.autograd.Function):
+    """Trajectories of a batch (jf_batch_feed_forward) with the reverse sweep
+    of each simulation: for U^{t+1} = S(U^t), dL/dU^t = g_t + J_t^T dL/dU^{t+1},
+    J_t^T applied by jf_rk3_step_vjp of a single-grid solver of the same grid
+    and scheme, on the stored trajectory (no recomputation of states)."""
+
+    @staticmethod
+    def forward(ctx, batch, nsteps, dt, *U0s):
+        trajs = batch.feed_forward([U.detach().contiguous() for U in U0s], nsteps, dt)
+        ctx.batch, ctx.nsteps = batch, nsteps
+        ctx.dts = [float(dt)] * batch.nsim if not hasattr(dt, "__len__") else [float(x) for x in dt]
+        ctx.save_for_backward(*trajs)
+        return tuple(trajs)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        trajs = ctx.saved_tensors
+        out = []
+        for i, (traj, g) in enumerate(zip(trajs, grads)):
+            solver = ctx.batch.solver(i)
+            dt = solver.scalar(ctx.dts[i])
+            g = torch.zeros_like(traj) if g is None else g.contiguous()
+            lam = g[ctx.nsteps].clone()
+            for t in reversed(range(ctx.nsteps)):
+                lam = solver.rk3_step_vjp(traj[t], dt, lam)
+                lam += g[t]
+            out.append(lam)
+        return (None, None, None, *out)
+
+
+def feed_forward(batch, U0s, nsteps, dt):
+    """Section 4.5 feed_forward, differentiable: per simulation of ``batch``
+    (a jf.Batch; sizes may differ) the trajectory (nsteps + 1, 5, nz, ny, nx)
+    of fixed-dt steps from U0s[i]; gradients flow back to every U0s[i]."""
+    return list(_FeedForward.apply(batch, int(nsteps), dt, *U0s))
+
+
+def trajectory_mse(trajs, refs):
+    """Section 7.2 trajectory loss L = 1/N_T sum_{i=1..N_T} MSE(U^i, U^i_ref)
+    (the initial state excluded), averaged over the simulations of a batch.
+    trajs / refs: lists of (N_T + 1, 5, ...) tensors."""
+    total = 0.0
+    for traj, ref in zip(trajs, refs):
+        nt = traj.shape[0] - 1
+        total = total + sum(torch.mean((traj[i] - ref[i]) ** 2) for i in range(1, nt + 1)) / nt
+    return total / len(trajs)

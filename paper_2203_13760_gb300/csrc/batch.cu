@@ -31,6 +31,19 @@ __global__ void __launch_bounds__(256) batch_copy_kernel(const SimDesc<T>* __res
     d.U[i] = d.U1[i];
 }
 
+// Trajectories (jf_batch_feed_forward): dst[s] = src[s] for every
+// simulation (blockIdx.y) of one row of the pointer tables.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_copy_pairs_kernel(const T* const* __restrict__ src,
+                                                               T* const* __restrict__ dst,
+                                                               const long long* __restrict__ count) {
+  const T* a = src[blockIdx.y];
+  T* b = dst[blockIdx.y];
+  const long long n = count[blockIdx.y];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
 namespace {
 
 template <typename T>
@@ -191,6 +204,85 @@ jf_status enqueue_steps(jf_ctx* h, int nsteps, double* dt_out, cudaStream_t s) {
   return JF_OK;
 }
 
+// feed_forward (Section 4.5): trajectory slot 0 = U0, slot t + 1 = one step of
+// slot t with the fixed per-simulation dt, for t < nsteps.  Per step: copy
+// slot t to slot t + 1, then the integrator's stages in place on slot t + 1
+// (descriptor row t points the simulations' U there).  Direct launches: the
+// trajectory pointers are new at every call.
+template <typename T>
+jf_status feed_forward_batch(jf_ctx* h, void* const* U0_ptrs, void* const* traj_ptrs, int nsteps,
+                             const double* dt_dev, cudaStream_t s) {
+  const int ns = h->nsim;
+  const size_t rows = (size_t)nsteps + 1;
+  const SimDesc<T>* base = reinterpret_cast<const SimDesc<T>*>(h->host_desc.data());
+  std::vector<SimDesc<T>> desc((size_t)nsteps * ns);
+  std::vector<const T*> src(rows * ns);
+  std::vector<T*> dst(rows * ns);
+  std::vector<long long> count(ns);
+  for (int i = 0; i < ns; ++i) {
+    const long long n5 = 5 * base[i].N;
+    count[i] = n5;
+    T* traj = static_cast<T*>(traj_ptrs[i]);
+    src[i] = static_cast<const T*>(U0_ptrs[i]);
+    dst[i] = traj;
+    for (int t = 0; t < nsteps; ++t) {
+      src[(size_t)(t + 1) * ns + i] = traj + (size_t)t * n5;
+      dst[(size_t)(t + 1) * ns + i] = traj + (size_t)(t + 1) * n5;
+      SimDesc<T> d = base[i];
+      d.U = traj + (size_t)(t + 1) * n5;
+      d.dt = dt_dev + i;
+      desc[(size_t)t * ns + i] = d;
+    }
+  }
+  // one allocation for the tables; freed after the stream has used them
+  const size_t bytes_desc = desc.size() * sizeof(SimDesc<T>), bytes_ptr = rows * ns * sizeof(void*);
+  const size_t bytes = bytes_desc + 2 * bytes_ptr + ns * sizeof(long long);
+  std::vector<unsigned char> host(bytes);
+  std::memcpy(host.data(), desc.data(), bytes_desc);
+  std::memcpy(host.data() + bytes_desc, src.data(), bytes_ptr);
+  std::memcpy(host.data() + bytes_desc + bytes_ptr, dst.data(), bytes_ptr);
+  std::memcpy(host.data() + bytes_desc + 2 * bytes_ptr, count.data(), ns * sizeof(long long));
+  unsigned char* dev = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dev), bytes, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "feed_forward: tables");
+  e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffer is local
+  if (e != cudaSuccess) { cudaFreeAsync(dev, s); return cuda_fail(h, e, "feed_forward: tables"); }
+  const SimDesc<T>* d_desc = reinterpret_cast<const SimDesc<T>*>(dev);
+  const T* const* d_src = reinterpret_cast<const T* const*>(dev + bytes_desc);
+  T* const* d_dst = reinterpret_cast<T* const*>(dev + bytes_desc + bytes_ptr);
+  const long long* d_count = reinterpret_cast<const long long*>(dev + bytes_desc + 2 * bytes_ptr);
+  int count_v = 0;
+  const StageVariant<T>* tab = stage_variants<T>(&count_v);
+  const StageVariant<T>& sv = tab[h->table_index];
+  const Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  const WorkItem* work = static_cast<const WorkItem*>(h->d_work);
+  const int integ = h->scheme.integrator;
+  const int codes[3] = {1, integ == JF_RK2 ? 4 : 2, 3};
+  const int nst = integ == JF_RK3 ? 3 : (integ == JF_RK2 ? 2 : 1);
+  const dim3 cgrid((unsigned)h->sms, (unsigned)ns);
+  jf_status st = JF_OK;
+  // row 0 of the copy tables: U0 -> slot 0; row t + 1: slot t -> slot t + 1
+  batch_copy_pairs_kernel<T><<<cgrid, 256, 0, s>>>(d_src, d_dst, d_count);
+  if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(h, e, "feed_forward: copy launch");
+  for (int t = 0; t < nsteps && st == JF_OK; ++t) {
+    batch_copy_pairs_kernel<T><<<cgrid, 256, 0, s>>>(d_src + (size_t)(t + 1) * ns, d_dst + (size_t)(t + 1) * ns,
+                                                     d_count);
+    if ((e = cudaGetLastError()) != cudaSuccess) { st = cuda_fail(h, e, "feed_forward: copy launch"); break; }
+    const SimDesc<T>* sims = d_desc + (size_t)t * ns;  // U = slot t + 1
+    for (int q = 0; q < nst; ++q) {
+      e = sv.launch_batch(sims, work, h->nwork, codes[q], g, h->flag, h->batch_blocks, s);
+      if (e != cudaSuccess) { st = cuda_fail(h, e, "feed_forward: stage launch"); break; }
+    }
+    if (st == JF_OK && integ == JF_EULER) {
+      batch_copy_kernel<T><<<cgrid, 256, 0, s>>>(sims);
+      if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(h, e, "feed_forward: copy launch");
+    }
+  }
+  cudaFreeAsync(dev, s);
+  return st;
+}
+
 template <typename T>
 jf_status step_batch(jf_ctx* h, void* const* U_ptrs, int nsteps, double* dt_out, cudaStream_t s) {
   jf_status st = bind_fields<T>(h, U_ptrs, s);
@@ -287,6 +379,23 @@ jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, con
   }
   *out = h;
   return JF_OK;
+}
+
+jf_status jf_batch_feed_forward(jf_handle h, void* const* U0_ptrs, void* const* traj_ptrs, int nsteps,
+                                const double* dt_dev, void* stream) {
+  if (!h || h->kind != 1) { set_error(h, "jf_batch_feed_forward: not a batch handle"); return JF_ERR_ARG; }
+  if (!U0_ptrs || !traj_ptrs || !dt_dev || nsteps < 0) {
+    set_error(h, "jf_batch_feed_forward: null argument or nsteps < 0");
+    return JF_ERR_ARG;
+  }
+  for (int s = 0; s < h->nsim; ++s)
+    if (!U0_ptrs[s] || !traj_ptrs[s] || !aligned16(U0_ptrs[s]) || !aligned16(traj_ptrs[s])) {
+      set_error(h, "jf_batch_feed_forward: every state and trajectory must be a 16-byte aligned device array");
+      return JF_ERR_ARG;
+    }
+  return h->scheme.dtype == JF_F32
+             ? feed_forward_batch<float>(h, U0_ptrs, traj_ptrs, nsteps, dt_dev, (cudaStream_t)stream)
+             : feed_forward_batch<double>(h, U0_ptrs, traj_ptrs, nsteps, dt_dev, (cudaStream_t)stream);
 }
 
 jf_status jf_batch_step(jf_handle h, void* const* U_ptrs, int nsteps, double* dt_dev, void* stream) {

@@ -68,6 +68,7 @@ SIGNATURES = {
     "jf_batch_create": (_I, [ctypes.POINTER(Grid), _I, ctypes.POINTER(GasParams), ctypes.POINTER(Scheme),
                              ctypes.POINTER(_VP)]),
     "jf_batch_step": (_I, [_VP, ctypes.POINTER(_VP), _I, _VP, _VP]),
+    "jf_batch_feed_forward": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP, _VP]),
     "jf_set_variant": (_I, [_VP, _I]),
     "jf_variant_info": (_I, [_VP, _I, ctypes.c_char_p, _I]),
     "jf_status_sync": (_I, [_VP]),
@@ -264,14 +265,47 @@ class Batch:
                                      ctypes.byref(h)))
         self.h = h
 
-    def step(self, Us, nsteps, dt_out=None):
-        import torch
+    def solver(self, i):
+        """A single-grid Solver with simulation i's grid and this batch's gas and
+        scheme (cached; used by the batch's adjoint)."""
+        cache = self.__dict__.setdefault("_solvers", {})
+        if i not in cache:
+            g, s, gas = self.grids[i], self.scheme, self.gas
+            names = {v: k for k, v in FLUX.items()}, {v: k for k, v in RECON.items()}, \
+                {v: k for k, v in SPEEDS.items()}, {v: k for k, v in INTEGRATOR.items()}
+            cache[i] = Solver((g.nx, g.ny, g.nz), tuple(g.lo), tuple(g.hi), tuple(g.bc), gas.gamma, gas.R, gas.mu,
+                              gas.Pr, "f32" if s.dtype == JF_F32 else "f64", s.weno_eps, s.cfl, bool(s.viscous),
+                              bool(s.heat), bool(s.safe_recon), names[0][s.flux], names[1][s.recon],
+                              names[2][s.signal_speed], names[3][s.integrator])
+        return cache[i]
+
+    def _check_fields(self, Us):
         if len(Us) != self.nsim:
             raise ValueError("one field per simulation")
         for i, (U, g) in enumerate(zip(Us, self.grids)):
             if (not U.is_cuda or U.dtype != self.dtype or not U.is_contiguous()
                     or tuple(U.shape) != (5, g.nz, g.ny, g.nx)):
                 raise ValueError(f"field {i} has the wrong shape / dtype / device")
+
+    def feed_forward(self, U0s, nsteps, dt):
+        """Section 4.5 feed_forward: per simulation the trajectory tensor
+        (nsteps + 1, 5, nz, ny, nx), slot 0 = U0, slot t = t steps of the fixed
+        step dt (a float, or one value per simulation)."""
+        import torch
+        self._check_fields(U0s)
+        dts = [float(dt)] * self.nsim if not hasattr(dt, "__len__") else [float(x) for x in dt]
+        if len(dts) != self.nsim:
+            raise ValueError("one dt per simulation")
+        dt_dev = torch.tensor(dts, dtype=torch.float64, device="cuda")
+        trajs = [torch.empty((int(nsteps) + 1,) + tuple(U.shape), dtype=self.dtype, device="cuda") for U in U0s]
+        u0 = (ctypes.c_void_p * self.nsim)(*[U.data_ptr() for U in U0s])
+        tp = (ctypes.c_void_p * self.nsim)(*[T.data_ptr() for T in trajs])
+        _check(lib().jf_batch_feed_forward(self.h, u0, tp, int(nsteps), _ptr(dt_dev), _stream()), self.h)
+        return trajs
+
+    def step(self, Us, nsteps, dt_out=None):
+        import torch
+        self._check_fields(Us)
         ptrs = (ctypes.c_void_p * self.nsim)(*[U.data_ptr() for U in Us])
         dt_out = torch.zeros(self.nsim, dtype=torch.float64, device="cuda") if dt_out is None else dt_out
         _check(lib().jf_batch_step(self.h, ptrs, int(nsteps), _ptr(dt_out), _stream()), self.h)
@@ -293,6 +327,8 @@ class Batch:
         _check(lib().jf_status_sync(self.h), self.h)
 
     def close(self):
+        for s in self.__dict__.pop("_solvers", {}).values():
+            s.close()
         if getattr(self, "h", None):
             lib().jf_destroy(self.h)
             self.h = None
