@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     const int gz = DIM == 3 ? map_index(g0[2] + lz - G::HZ, A.n[2], A.periodic[2]) : 0;
     const long long q = ((long long)gz * A.n[1] + gy) * A.n[0] + gx;
     const T r = A.Us[q];
-    const T inv = T(1) / r;
+    const T inv = trcp(r);
     const T u = A.Us[q + A.N] * inv, v = A.Us[q + 2 * A.N] * inv, w = A.Us[q + 3 * A.N] * inv;
     const T p = g.gm1 * (A.Us[q + 4 * A.N] - T(0.5) * r * (u * u + v * v + w * w));
     bad |= !(r > T(0)) || !(p > T(0));
@@ -367,11 +367,27 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     const int B1 = act1 ? B[F.t1] : 1, B2 = act2 ? B[F.t2] : 1;
     // convective faces: left cells -3 .. B_d+1 along d (a face reaches cells
     // -2 .. +3 along d), the box's own cells across
+    // face index -> (s along d, a along t1, b along t2) with the x coordinate
+    // fastest across the lanes of a warp (consecutive shared-memory words, no
+    // bank conflicts on the loads and the atomic accumulation): x is s for
+    // d = 0, b (t2) for d = 1 and a (t1) for d = 2
     {
       const int en = B[d] + 5, cnt = en * B1 * B2;
       for (int f = tid; f < cnt; f += G::NT) {
-        const int s = f % en - 3, r = f / en;
-        const int a = r % B1, b = r / B1;
+        int s, a, b;
+        if (d == 0) {
+          s = f % en - 3;
+          a = (f / en) % B1;
+          b = f / (en * B1);
+        } else if (d == 1) {
+          b = f % B2;
+          s = (f / B2) % en - 3;
+          a = f / (B2 * en);
+        } else {
+          a = f % B1;
+          b = (f / B1) % B2;
+          s = f / (B1 * B2) - 3;
+        }
         const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
         T nu[5];
         if (face_nu(F, p, nu)) conv_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g);
@@ -383,8 +399,20 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
       const int en = B[d] + 3, e1 = act1 ? B1 + 4 : 1, e2 = act2 ? B2 + 4 : 1, cnt = en * e1 * e2;
       const int o1 = act1 ? 2 : 0, o2 = act2 ? 2 : 0;
       for (int f = tid; f < cnt; f += G::NT) {
-        const int s = f % en - 2, r = f / en;
-        const int a = r % e1 - o1, b = r / e1 - o2;
+        int s, a, b;  // x fastest, as above
+        if (d == 0) {
+          s = f % en - 2;
+          a = (f / en) % e1 - o1;
+          b = f / (en * e1) - o2;
+        } else if (d == 1) {
+          b = f % e2 - o2;
+          s = (f / e2) % en - 2;
+          a = f / (e2 * en) - o1;
+        } else {
+          a = f % e1 - o1;
+          b = (f / e1) % e2 - o2;
+          s = f / (e1 * e2) - 2;
+        }
         const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
         T nu[5];
         if (face_nu(F, p, nu)) visc_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g, inv_h);
@@ -402,13 +430,13 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     const int cell = (tz * BY + ty) * BX + tx;
     T br = acc[cell], bu = acc[G::NCELL + cell], bv = acc[2 * G::NCELL + cell], bw = acc[3 * G::NCELL + cell];
     T bp = acc[4 * G::NCELL + cell];
+    const T inv = trcp(r);
     if (VISC) {
       const T bT = acc[5 * G::NCELL + cell];
       const T Tc = V.w(5, tx, ty, tz);
-      br -= bT * Tc / r;  // T = p / (rho R)
-      bp += bT * Tc / p;
+      br -= bT * Tc * inv;  // T = p / (rho R)
+      bp += bT * Tc * trcp(p);
     }
-    const T inv = T(1) / r;
     T bU[5];
     bU[0] = br - (bu * u + bv * v + bw * w) * inv + bp * g.gm1 * T(0.5) * (u * u + v * v + w * w);
     bU[1] = bu * inv - bp * g.gm1 * u;

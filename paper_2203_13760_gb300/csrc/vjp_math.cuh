@@ -26,15 +26,17 @@ JF_HD void weno5_vjp(T v0, T v1, T v2, T v3, T v4, T eps, T yb, T vb[5]) {
   const T t0 = eps + c13 * d0 * d0 + T(0.25) * e0 * e0;
   const T t1 = eps + c13 * d1 * d1 + T(0.25) * e1 * e1;
   const T t2 = eps + c13 * d2 * d2 + T(0.25) * e2 * e2;
-  const T a0 = T(0.1) / (t0 * t0), a1 = T(0.6) / (t1 * t1), a2 = T(0.3) / (t2 * t2);
-  const T inv = T(1) / (a0 + a1 + a2);
+  // every division through a reciprocal (trcp: approximate in FP32 device code)
+  const T r0 = trcp(t0), r1 = trcp(t1), r2 = trcp(t2);
+  const T a0 = T(0.1) * r0 * r0, a1 = T(0.6) * r1 * r1, a2 = T(0.3) * r2 * r2;
+  const T inv = trcp(a0 + a1 + a2);
   const T y = (a0 * q0 + a1 * q1 + a2 * q2) * inv;
   const T s = yb * inv;
   const T qb0 = s * a0, qb1 = s * a1, qb2 = s * a2;
   // d alpha_k / d t_k = -2 alpha_k / t_k;  beta_k enters t_k with slope 1
-  const T tb0 = -T(2) * s * (q0 - y) * a0 / t0;
-  const T tb1 = -T(2) * s * (q1 - y) * a1 / t1;
-  const T tb2 = -T(2) * s * (q2 - y) * a2 / t2;
+  const T tb0 = -T(2) * s * (q0 - y) * a0 * r0;
+  const T tb1 = -T(2) * s * (q1 - y) * a1 * r1;
+  const T tb2 = -T(2) * s * (q2 - y) * a2 * r2;
   const T db0 = T(2) * c13 * d0 * tb0, eb0 = T(0.5) * e0 * tb0;
   const T db1 = T(2) * c13 * d1 * tb1, eb1 = T(0.5) * e1 * tb1;
   const T db2 = T(2) * c13 * d2 * tb2, eb2 = T(0.5) * e2 * tb2;
@@ -57,11 +59,12 @@ JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5]
   const T q2R = WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3];
   const T EL = pL * g.inv_gm1 + T(0.5) * rL * q2L;
   const T ER = pR * g.inv_gm1 + T(0.5) * rR * q2R;
-  const T cL = tsqrt(g.gamma * pL / rL);
-  const T cR = tsqrt(g.gamma * pR / rR);
+  const T irL = trcp(rL), irR = trcp(rR);
+  const T cL = tsqrt(g.gamma * pL * irL);
+  const T cR = tsqrt(g.gamma * pR * irR);
   const T sL = tsqrt(rL), sR = tsqrt(rR);
-  const T is = T(1) / (sL + sR);
-  const T HL = (EL + pL) / rL, HR = (ER + pR) / rR;
+  const T is = trcp(sL + sR);
+  const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   T ut[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) ut[m] = (sL * WL[1 + m] + sR * WR[1 + m]) * is;
@@ -75,8 +78,8 @@ JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5]
   const bool selR = aR < bR;  // S_R = max(aR, bR) takes bR
   const T SR = selR ? bR : aR;
   const T mL = rL * (SL - unL), mR = rR * (SR - unR);
-  const T den = mL - mR;
-  const T Ss = (pR - pL + mL * unL - mR * unR) / den;
+  const T den = mL - mR, iden = trcp(den);
+  const T Ss = (pR - pL + mL * unL - mR * unR) * iden;
   const bool left = (SL >= T(0)) || (Ss >= T(0));
   const bool star = left ? !(SL >= T(0)) : (SR > T(0));
 
@@ -91,8 +94,10 @@ JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5]
   T wb[3] = {0, 0, 0};
   if (star) {
     // F = F_K + S (U*_K - U_K)
-    const T fac = m / (S - Ss);
-    const T X = E / r + (Ss - un) * (Ss + p / m);
+    const T ir = left ? irL : irR, im = trcp(m);
+    const T dS = S - Ss, idS = trcp(dS);
+    const T fac = m * idS;
+    const T X = E * ir + (Ss - un) * (Ss + p * im);
     T Us[5] = {fac, fac * w[0], fac * w[1], fac * w[2], fac * X};
     Us[1 + D] = fac * Ss;
     const T Uk[5] = {r, r * w[0], r * w[1], r * w[2], E};
@@ -120,19 +125,18 @@ JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5]
     }
     const T Xb = S * Fb[4] * fac;
     // X = E / r + (S* - un)(S* + p / m)
-    const T A = Ss - un, B = Ss + p / m;
-    Eb += Xb / r;
-    rb -= Xb * E / (r * r);
+    const T A = Ss - un, B = Ss + p * im;
+    Eb += Xb * ir;
+    rb -= Xb * E * ir * ir;
     const T Ab = Xb * B, Bb = Xb * A;
     Ssb += Ab + Bb;
     wb[D] -= Ab;
-    pb += Bb / m;
-    mb -= Bb * p / (m * m);
+    pb += Bb * im;
+    mb -= Bb * p * im * im;
     // fac = m / (S - S*)
-    const T dS = S - Ss;
-    mb += facb / dS;
-    Sb -= facb * fac / dS;
-    Ssb += facb * fac / dS;
+    mb += facb * idS;
+    Sb -= facb * fac * idS;
+    Ssb += facb * fac * idS;
   }
   // physical flux F_K = [r un, r un w, un (E + p)] + p e_normal (cotangent Fb)
   {
@@ -161,7 +165,7 @@ JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5]
   }
   if (star) {
     // S* = (pR - pL + mL unL - mR unR) / (mL - mR)
-    const T numb = Ssb / den, denb = -Ssb * Ss / den;
+    const T numb = Ssb * iden, denb = -Ssb * Ss * iden;
     pRb += numb;
     pLb -= numb;
     mLb += numb * unL + denb;
@@ -180,7 +184,7 @@ JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5]
     if (selL) { untb += SLb; ctb -= SLb; } else { wLb[D] += SLb; cLb -= SLb; }
     if (selR) { untb += SRb; ctb += SRb; } else { wRb[D] += SRb; cRb += SRb; }
     // c~ = sqrt(Z), Z = (gamma - 1)(H~ - |u~|^2 / 2)
-    const T Zb = ctb * T(0.5) / ct;
+    const T Zb = ctb * T(0.5) * trcp(ct);
     const T Htb = Zb * g.gm1;
     T utb[3];
 #pragma unroll
@@ -202,21 +206,21 @@ JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5]
     sLb += ssb;
     sRb += ssb;
     // H_K = (E_K + p_K) / r_K
-    ELb += HLb / rL;
-    pLb += HLb / rL;
-    rLb -= HLb * HL / rL;
-    ERb += HRb / rR;
-    pRb += HRb / rR;
-    rRb -= HRb * HR / rR;
-    // s_K = sqrt(r_K)
-    rLb += sLb * T(0.5) / sL;
-    rRb += sRb * T(0.5) / sR;
+    ELb += HLb * irL;
+    pLb += HLb * irL;
+    rLb -= HLb * HL * irL;
+    ERb += HRb * irR;
+    pRb += HRb * irR;
+    rRb -= HRb * HR * irR;
+    // s_K = sqrt(r_K): d s / d r = 1 / (2 s) = s / (2 r)
+    rLb += sLb * T(0.5) * sL * irL;
+    rRb += sRb * T(0.5) * sR * irR;
     // c_K = sqrt(gamma p_K / r_K)
-    const T zLb = cLb * T(0.5) / cL, zRb = cRb * T(0.5) / cR;
-    pLb += zLb * g.gamma / rL;
-    rLb -= zLb * g.gamma * pL / (rL * rL);
-    pRb += zRb * g.gamma / rR;
-    rRb -= zRb * g.gamma * pR / (rR * rR);
+    const T zLb = cLb * T(0.5) * trcp(cL), zRb = cRb * T(0.5) * trcp(cR);
+    pLb += zLb * g.gamma * irL;
+    rLb -= zLb * g.gamma * pL * irL * irL;
+    pRb += zRb * g.gamma * irR;
+    rRb -= zRb * g.gamma * pR * irR * irR;
   }
   // E_K = p_K / (gamma - 1) + r_K |w_K|^2 / 2
   pLb += ELb * g.inv_gm1;

@@ -83,11 +83,14 @@ def _tgv_off_symmetry(n):
     return case
 
 
+# FP32: the reverse pass chains O(100) dependent FP32 operations per output
+# value (approximate reciprocals included, <= 2 ulp each), so the identity
+# holds to a few hundred FP32 epsilons (6e-8) of the sum of |terms|: 3e-5.
 @pytest.mark.parametrize("dtype,tol,make", [
     ("f64", 1e-12, lambda: inputs.kelvin_helmholtz(32, seed=3)),
-    ("f32", 1e-5, lambda: inputs.kelvin_helmholtz(32, seed=3)),
+    ("f32", 3e-5, lambda: inputs.kelvin_helmholtz(32, seed=3)),
     ("f64", 1e-12, lambda: _tgv_off_symmetry(12)),
-    ("f32", 1e-5, lambda: _tgv_off_symmetry(16)),
+    ("f32", 3e-5, lambda: _tgv_off_symmetry(16)),
 ])
 def test_dot_product_identity(orc, dtype, tol, make):
     case = make()
