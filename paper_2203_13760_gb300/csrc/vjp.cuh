@@ -32,6 +32,8 @@
 // every axis.
 #pragma once
 #include "stage.cuh"
+#include <type_traits>
+
 #include "vjp_math.cuh"
 
 namespace jf {
@@ -77,6 +79,21 @@ struct Frame {
   int d, t1, t2;
   __device__ __forceinline__ int pick(int axis, int n, int a, int b) const {
     return axis == d ? n : (axis == t1 ? a : b);
+  }
+};
+
+// Face-task counts of a box per direction (zero for inactive directions).
+template <int DIM, int BX, int BY, int BZ>
+struct VCount {
+  static constexpr int B(int a) { return a == 0 ? BX : (a == 1 ? BY : BZ); }
+  static constexpr int conv(int d) {
+    return d < DIM ? (B(d) + 5) * ((d + 1) % 3 < DIM ? B((d + 1) % 3) : 1) * ((d + 2) % 3 < DIM ? B((d + 2) % 3) : 1)
+                   : 0;
+  }
+  static constexpr int visc(int d) {
+    return d < DIM ? (B(d) + 3) * ((d + 1) % 3 < DIM ? B((d + 1) % 3) + 4 : 1) *
+                         ((d + 2) % 3 < DIM ? B((d + 2) % 3) + 4 : 1)
+                   : 0;
   }
 };
 
@@ -295,7 +312,6 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   T* Wb = reinterpret_cast<T*>(smem_raw);
   T* Mb = Wb + G::NCW * G::CS;
   T* acc = Mb + 5 * G::MCS;
-  const int B[3] = {BX, BY, BZ};
   const int g0[3] = {(int)blockIdx.x * BX, (int)blockIdx.y * BY, (int)blockIdx.z * BZ};
   const int tid = threadIdx.x;
 
@@ -360,63 +376,91 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     return any;
   };
 
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    const Frame F{d, (d + 1) % 3, (d + 2) % 3};
-    const bool act1 = F.t1 < DIM, act2 = F.t2 < DIM;
-    const int B1 = act1 ? B[F.t1] : 1, B2 = act2 ? B[F.t2] : 1;
-    // convective faces: left cells -3 .. B_d+1 along d (a face reaches cells
-    // -2 .. +3 along d), the box's own cells across
-    // face index -> (s along d, a along t1, b along t2) with the x coordinate
-    // fastest across the lanes of a warp (consecutive shared-memory words, no
-    // bank conflicts on the loads and the atomic accumulation): x is s for
-    // d = 0, b (t2) for d = 1 and a (t1) for d = 2
-    {
-      const int en = B[d] + 5, cnt = en * B1 * B2;
-      for (int f = tid; f < cnt; f += G::NT) {
-        int s, a, b;
-        if (d == 0) {
-          s = f % en - 3;
-          a = (f / en) % B1;
-          b = f / (en * B1);
-        } else if (d == 1) {
-          b = f % B2;
-          s = (f / B2) % en - 3;
-          a = f / (B2 * en);
-        } else {
-          a = f % B1;
-          b = (f / B1) % B2;
-          s = f / (B1 * B2) - 3;
-        }
-        const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
-        T nu[5];
-        if (face_nu(F, p, nu)) conv_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g);
-      }
+  // The face reverse passes of the box as one flat list of tasks, so that
+  // every thread takes the same number of faces (up to one) whatever the
+  // per-direction counts: convective faces of each active direction (left
+  // cells -3 .. B_d+1 along d: a face reaches cells -2 .. +3 along d; the
+  // box's own cells across), then, if viscous, the dissipative faces (left
+  // cells -2 .. B_d along d, -2 .. B+1 across on the active tangential axes).
+  // Face index -> (s along d, a along t1, b along t2) with the x coordinate
+  // fastest across the lanes of a warp (consecutive shared-memory words, no
+  // bank conflicts on the loads and the atomic accumulation): x is s for
+  // d = 0, b (t2) for d = 1 and a (t1) for d = 2.
+  auto conv_task = [&](auto dtag, int f) {
+    constexpr int d = decltype(dtag)::value;
+    constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const Frame F{d, t1, t2};
+    constexpr int en = VCount<DIM, BX, BY, BZ>::B(d) + 5;
+    constexpr int B1 = t1 < DIM ? VCount<DIM, BX, BY, BZ>::B(t1) : 1;
+    constexpr int B2 = t2 < DIM ? VCount<DIM, BX, BY, BZ>::B(t2) : 1;
+    int s, a, b;
+    if (d == 0) {
+      s = f % en - 3;
+      a = (f / en) % B1;
+      b = f / (en * B1);
+    } else if (d == 1) {
+      b = f % B2;
+      s = (f / B2) % en - 3;
+      a = f / (B2 * en);
+    } else {
+      a = f % B1;
+      b = (f / B1) % B2;
+      s = f / (B1 * B2) - 3;
     }
-    if (VISC) {
-      // dissipative faces: left cells -2 .. B_d along d (cells -1 .. +2) and
-      // -2 .. B+1 across on the active tangential axes (reach +-2)
-      const int en = B[d] + 3, e1 = act1 ? B1 + 4 : 1, e2 = act2 ? B2 + 4 : 1, cnt = en * e1 * e2;
-      const int o1 = act1 ? 2 : 0, o2 = act2 ? 2 : 0;
-      for (int f = tid; f < cnt; f += G::NT) {
-        int s, a, b;  // x fastest, as above
-        if (d == 0) {
-          s = f % en - 2;
-          a = (f / en) % e1 - o1;
-          b = f / (en * e1) - o2;
-        } else if (d == 1) {
-          b = f % e2 - o2;
-          s = (f / e2) % en - 2;
-          a = f / (e2 * en) - o1;
-        } else {
-          a = f % e1 - o1;
-          b = (f / e1) % e2 - o2;
-          s = f / (e1 * e2) - 2;
-        }
-        const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
-        T nu[5];
-        if (face_nu(F, p, nu)) visc_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g, inv_h);
+    const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
+    T nu[5];
+    if (face_nu(F, p, nu)) conv_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g);
+  };
+  auto visc_task = [&](auto dtag, int f) {
+    constexpr int d = decltype(dtag)::value;
+    constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const Frame F{d, t1, t2};
+    constexpr int en = VCount<DIM, BX, BY, BZ>::B(d) + 3;
+    constexpr int e1 = t1 < DIM ? VCount<DIM, BX, BY, BZ>::B(t1) + 4 : 1;
+    constexpr int e2 = t2 < DIM ? VCount<DIM, BX, BY, BZ>::B(t2) + 4 : 1;
+    constexpr int o1 = t1 < DIM ? 2 : 0, o2 = t2 < DIM ? 2 : 0;
+    int s, a, b;
+    if (d == 0) {
+      s = f % en - 2;
+      a = (f / en) % e1 - o1;
+      b = f / (en * e1) - o2;
+    } else if (d == 1) {
+      b = f % e2 - o2;
+      s = (f / e2) % en - 2;
+      a = f / (e2 * en) - o1;
+    } else {
+      a = f % e1 - o1;
+      b = (f / e1) % e2 - o2;
+      s = f / (e1 * e2) - 2;
+    }
+    const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
+    T nu[5];
+    if (face_nu(F, p, nu)) visc_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g, inv_h);
+  };
+  using C = VCount<DIM, BX, BY, BZ>;
+  constexpr int c0 = C::conv(0), c1 = C::conv(1), c2 = C::conv(2);
+  constexpr int v0 = VISC ? C::visc(0) : 0, v1 = VISC ? C::visc(1) : 0, v2 = VISC ? C::visc(2) : 0;
+  constexpr int total = c0 + c1 + c2 + v0 + v1 + v2;
+  for (int f = tid; f < total; f += G::NT) {
+    int r = f;
+    if (r < c0) { conv_task(std::integral_constant<int, 0>{}, r); continue; }
+    r -= c0;
+    if constexpr (DIM >= 2) {
+      if (r < c1) { conv_task(std::integral_constant<int, 1>{}, r); continue; }
+      r -= c1;
+    }
+    if constexpr (DIM == 3) {
+      if (r < c2) { conv_task(std::integral_constant<int, 2>{}, r); continue; }
+      r -= c2;
+    }
+    if constexpr (VISC) {
+      if (r < v0) { visc_task(std::integral_constant<int, 0>{}, r); continue; }
+      r -= v0;
+      if constexpr (DIM >= 2) {
+        if (r < v1) { visc_task(std::integral_constant<int, 1>{}, r); continue; }
+        r -= v1;
       }
+      if constexpr (DIM == 3) visc_task(std::integral_constant<int, 2>{}, r);
     }
   }
   __syncthreads();
