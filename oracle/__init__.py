@@ -36,6 +36,14 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   fs_flux (ROE setup)    Jacobian by finite differences; Roe's property
                          A~ (U_R - U_L) = F_R - F_L; consistency; fifth order
                          on smooth advection; Sod and Lax convergence)
+  wall boundary          pinned (equals the mirror-doubled periodic domain to
+                         rounding; closed box conserves mass and energy)
+  weno3                  pinned (linear exactness, non-oscillation at a jump,
+                         third-order convergence)
+  flux_nn / nn_alpha /   pinned (constant alpha gives Lax-Friedrichs = HLL
+  jvp_params_run         with -+alpha; a network built to compute
+                         exp(a . x + b) matches the closed form with the
+                         paper's inputs; parameter JVP = central differences)
   count_flops            descriptive only (an operation count, not a result)
 """
 from __future__ import annotations
@@ -91,19 +99,22 @@ class Config(ctypes.Structure):
         ("recon", ctypes.c_int),
         ("speeds", ctypes.c_int),
         ("integrator", ctypes.c_int),
+        ("nn", ctypes.POINTER(ctypes.c_double)),
+        ("nn_dot", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
 # scheme options (Table 2); 0 is the Appendix A configuration
-FLUX = {"hllc": 0, "hll": 1, "rusanov": 2, "roe": 3}
-RECON = {"weno5-js": 0, "weno5-z": 1}
+FLUX = {"hllc": 0, "hll": 1, "rusanov": 2, "roe": 3, "rusanov-nn": 4}
+RECON = {"weno5-js": 0, "weno5-z": 1, "weno3-js": 2}
+NN_PARAMS = 32 * 4 + 32 + 2 * (32 * 32 + 32) + 32 + 1
 SPEEDS = {"einfeldt": 0, "davis": 1, "toro": 2}
 INTEGRATOR = {"rk3": 0, "rk2": 1, "euler": 2}
 
 
 def config(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gamma=1.4, R=1.0,
            mu=0.0, Pr=0.72, eps=1e-6, cfl=0.5, convective=True, viscous=False, heat=False,
-           safe=False, flux="hllc", recon="weno5-js", speeds="einfeldt", integrator="rk3") -> Config:
+           safe=False, flux="hllc", recon="weno5-js", speeds="einfeldt", integrator="rk3", nn=None) -> Config:
     n = tuple(int(x) for x in n) + (1,) * (3 - len(n))
     c = Config()
     c.n[:] = n
@@ -114,6 +125,12 @@ def config(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gam
     c.convective, c.viscous, c.heat, c.safe = int(convective), int(viscous), int(heat), int(safe)
     c.flux, c.recon = FLUX[flux], RECON[recon]
     c.speeds, c.integrator = SPEEDS[speeds], INTEGRATOR[integrator]
+    if nn is not None:
+        arr = np.ascontiguousarray(nn, dtype=np.float64)
+        if arr.size != NN_PARAMS:
+            raise ValueError(f"the Rusanov-NN network has {NN_PARAMS} parameters")
+        c._nn_keep = arr  # the structure holds a raw pointer into it
+        c.nn = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return c
 
 
@@ -151,6 +168,14 @@ def lib():
             L.orc_flux.restype = None
             L.orc_hll_speeds.argtypes = [dp, dp, ctypes.c_int, d, d, d, dp]
             L.orc_hll_speeds.restype = None
+            L.orc_jvp_params_run.argtypes = [cp, dp, dp, ctypes.c_int, d, dp]
+            L.orc_jvp_params_run.restype = ctypes.c_int
+            L.orc_flux_nn.argtypes = [dp, dp, ctypes.c_int, d, dp, dp]
+            L.orc_flux_nn.restype = None
+            L.orc_nn_alpha.argtypes = [dp, dp]
+            L.orc_nn_alpha.restype = d
+            L.orc_weno3.argtypes = [dp, d]
+            L.orc_weno3.restype = d
             L.orc_roe_eigensystem.argtypes = [dp, dp, ctypes.c_int, d, dp, dp, dp]
             L.orc_roe_eigensystem.restype = None
             L.orc_fs_flux.argtypes = [dp, ctypes.c_int, d, d, ctypes.c_int, dp]
@@ -284,6 +309,37 @@ def hll_with_speeds(WL, WR, SL: float, SR: float, d: int = 0, gamma: float = 1.4
     F = np.empty(5)
     lib().orc_hll_speeds(_ptr(WL), _ptr(WR), int(d), float(gamma), float(SL), float(SR), _ptr(F))
     return F
+
+
+def jvp_params_run(c: Config, U, nsteps: int, dt: float, theta_dot):
+    """(U_n, dU_n/dtheta . theta_dot) for nsteps fixed-dt steps of the
+    Rusanov-NN configuration, by dual-number parameters."""
+    U = _state(c, U)
+    V = np.zeros_like(U)
+    td = np.ascontiguousarray(theta_dot, dtype=np.float64)
+    if lib().orc_jvp_params_run(ctypes.byref(c), _ptr(U), _ptr(V), int(nsteps), float(dt), _ptr(td)) != 0:
+        raise ValueError("orc_jvp_params_run failed")
+    return U, V
+
+
+def flux_nn(WL, WR, theta, d: int = 0, gamma: float = 1.4) -> np.ndarray:
+    WL = np.ascontiguousarray(WL, dtype=np.float64)
+    WR = np.ascontiguousarray(WR, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    F = np.empty(5)
+    lib().orc_flux_nn(_ptr(WL), _ptr(WR), int(d), float(gamma), _ptr(th), _ptr(F))
+    return F
+
+
+def nn_alpha(theta, x) -> float:
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().orc_nn_alpha(_ptr(th), _ptr(xv)))
+
+
+def weno3(v, eps: float = 1e-6) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return float(lib().orc_weno3(_ptr(v), float(eps)))
 
 
 def roe_eigensystem(WL, WR, d: int = 0, gamma: float = 1.4):

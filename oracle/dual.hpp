@@ -58,12 +58,17 @@ inline Dual sqrt(const Dual& a) {
   return Dual(s, a.d / (2.0 * s));
 }
 inline Dual log(const Dual& a) { return Dual(std::log(a.v), a.d / a.v); }
+inline Dual exp(const Dual& a) {
+  const double e = std::exp(a.v);
+  return Dual(e, e * a.d);
+}
 inline Dual fabs(const Dual& a) { return a.v < 0.0 ? -a : a; }
 
 // double overloads, so that unqualified calls inside namespace orc resolve to
 // the exact double function rather than converting to Dual
 inline double sqrt(double x) { return std::sqrt(x); }
 inline double log(double x) { return std::log(x); }
+inline double exp(double x) { return std::exp(x); }
 inline double fabs(double x) { return std::fabs(x); }
 
 inline double value_of(double x) { return x; }

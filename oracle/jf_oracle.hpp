@@ -33,6 +33,8 @@
 //                      HLLC (Toro 1994) and the chosen signal speeds
 //   hll_flux           HLL (Harten, Lax, van Leer 1983), Table 2
 //   rusanov_flux       local Lax-Friedrichs / Rusanov, Table 2
+//   rusanov_nn_flux    Section 7.4 Rusanov-NN: dissipation from an MLP
+//   weno3_js           Table 2 WENO3-JS (the ground-truth scheme of Section 7.4)
 //   roe_eigensystem,   Section 3.3 "Flux-Splitting approach" with the Roe
 //   flux_splitting_    average and Roe flux splitting: the paper's ROE setup
 //   face_flux          (Section 5: WENO5 in characteristic space)
@@ -50,16 +52,22 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <type_traits>
 #include <vector>
 
 #include "dual.hpp"
 
 namespace orc {
 
-enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1 };
+enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_WALL = 2 };
 // scheme options of Table 2 (0 = the Appendix A configuration)
-enum { FLUX_HLLC = 0, FLUX_HLL = 1, FLUX_RUSANOV = 2, FLUX_ROE_FS = 3 };
-enum { RECON_WENO5_JS = 0, RECON_WENO5_Z = 1 };
+enum { FLUX_HLLC = 0, FLUX_HLL = 1, FLUX_RUSANOV = 2, FLUX_ROE_FS = 3, FLUX_RUSANOV_NN = 4 };
+enum { RECON_WENO5_JS = 0, RECON_WENO5_Z = 1, RECON_WENO3_JS = 2 };
+// the Rusanov-NN dissipation network (Section 7.4): 4 inputs, three hidden
+// layers of 32 ReLU units, one exponential output; parameters in the order
+// W1 [32][4], b1 [32], W2 [32][32], b2 [32], W3 [32][32], b3 [32], W4 [32], b4
+constexpr int NN_HIDDEN = 32;
+constexpr int NN_PARAMS = 32 * 4 + 32 + 2 * (32 * 32 + 32) + 32 + 1;
 enum { SPEED_EINFELDT = 0, SPEED_DAVIS = 1, SPEED_TORO = 2 };
 enum { TIME_RK3 = 0, TIME_RK2 = 1, TIME_EULER = 2 };
 constexpr int NG = 3;  // ghost cells per side on an active axis (WENO5 reaches 3)
@@ -82,6 +90,8 @@ struct Config {
   int recon;          // RECON_*: reconstruction
   int speeds;         // SPEED_*: signal speed estimate (HLLC, HLL)
   int integrator;     // TIME_*: time integration
+  const double* nn;   // FLUX_RUSANOV_NN: the NN_PARAMS network parameters
+  const double* nn_dot;  // optional tangent of the parameters (dual-number runs)
 };
 
 inline bool active(const Config& c, int d) { return c.n[d] > 1; }
@@ -122,7 +132,7 @@ struct Cell {
 template <class T>
 inline const T& at(const Field<T>& f, int m, const Cell& c) { return f(m, c.i[0], c.i[1], c.i[2]); }
 
-// Boundary conditions (Section 3.7, Table 2): periodic, or zero gradient
+// Boundary conditions (Section 3.7, Table 2): periodic, wall (symmetry) or zero gradient
 // (the ghost cell copies the nearest interior cell; "transmissive",
 // "neumann" with zero flux in Appendix A).  Axes are filled one after the
 // other; each later axis copies whole ghost-extended lines of the earlier
@@ -151,10 +161,15 @@ void fill_ghosts(Field<T>& f, const Config& c) {
               Cell glo = base, ghi = base, slo = base, shi = base;
               glo.i[d] = -q;
               ghi.i[d] = n - 1 + q;
-              slo.i[d] = (c.bc[2 * d] == BC_PERIODIC) ? n - q : 0;
-              shi.i[d] = (c.bc[2 * d + 1] == BC_PERIODIC) ? q - 1 : n - 1;
-              f(m, glo.i[0], glo.i[1], glo.i[2]) = f(m, slo.i[0], slo.i[1], slo.i[2]);
-              f(m, ghi.i[0], ghi.i[1], ghi.i[2]) = f(m, shi.i[0], shi.i[1], shi.i[2]);
+              // periodic: wrap; zero gradient: the nearest cell; wall: the
+              // mirror cell with the normal momentum negated (slip wall)
+              const int blo = c.bc[2 * d], bhi = c.bc[2 * d + 1];
+              slo.i[d] = blo == BC_PERIODIC ? n - q : (blo == BC_WALL ? q - 1 : 0);
+              shi.i[d] = bhi == BC_PERIODIC ? q - 1 : (bhi == BC_WALL ? n - q : n - 1);
+              const double sgn_lo = (blo == BC_WALL && m == 1 + d) ? -1.0 : 1.0;
+              const double sgn_hi = (bhi == BC_WALL && m == 1 + d) ? -1.0 : 1.0;
+              f(m, glo.i[0], glo.i[1], glo.i[2]) = sgn_lo * f(m, slo.i[0], slo.i[1], slo.i[2]);
+              f(m, ghi.i[0], ghi.i[1], ghi.i[2]) = sgn_hi * f(m, shi.i[0], shi.i[1], shi.i[2]);
             }
           }
   }
@@ -185,6 +200,8 @@ void primitives(const Field<T>& U, Field<T>& W, const Config& c) {
 }
 
 template <class T> inline T sq(const T& x) { return x * x; }
+// rho^gamma = exp(gamma ln rho) (rho > 0)
+template <class T> inline T pow_gamma(const T& r, double gamma) { return exp(gamma * log(r)); }
 template <class T> inline T tmin(const T& a, const T& b) { return (b < a) ? b : a; }
 template <class T> inline T tmax(const T& a, const T& b) { return (a < b) ? b : a; }
 
@@ -229,6 +246,22 @@ T weno5_z(const T& vm2, const T& vm1, const T& v0, const T& vp1, const T& vp2, d
   const T s = a0 + a1 + a2;
   const T w0 = a0 / s, w1 = a1 / s, w2 = a2 / s;
   return w0 * q0 + w1 * q1 + w2 * q2;
+}
+
+// WENO3-JS (Jiang & Shu 1996; Table 2 "WENO3-JS"): value at x_{i+1/2} biased
+// to the left from v[i-1], v[i], v[i+1]: candidates q0 = (-v[i-1] + 3 v[i]) / 2,
+// q1 = (v[i] + v[i+1]) / 2, smoothness beta0 = (v[i] - v[i-1])^2,
+// beta1 = (v[i+1] - v[i])^2, alpha_k = d_k / (eps + beta_k)^2 with
+// d = (1/3, 2/3), omega_k = alpha_k / sum(alpha).
+template <class T>
+T weno3_js(const T& vm1, const T& v0, const T& vp1, double eps) {
+  const T q0 = (-vm1 + 3.0 * v0) / 2.0;
+  const T q1 = (v0 + vp1) / 2.0;
+  const T b0 = sq(v0 - vm1), b1 = sq(vp1 - v0);
+  const T a0 = (1.0 / 3.0) / sq(eps + b0);
+  const T a1 = (2.0 / 3.0) / sq(eps + b1);
+  const T s = a0 + a1;
+  return (a0 / s) * q0 + (a1 / s) * q1;
 }
 
 // Conservative state and physical flux along axis d (Section 2: F, G, H).
@@ -384,11 +417,77 @@ void rusanov_flux(const T WL[5], const T WR[5], int d, double gamma, T F[5]) {
   for (int m = 0; m < 5; ++m) F[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * a * (UR[m] - UL[m]);
 }
 
+// Rusanov-NN (Section 7.4, Eq. (Rusanov)): the Rusanov flux with the
+// dissipation alpha given by a multi-layer perceptron of the face states,
+//   F = (F_L + F_R) / 2 - alpha (U_R - U_L) / 2,
+//   alpha = exp(W4 h3 + b4), h_l = ReLU(W_l h_{l-1} + b_l), h0 = x,
+//   x = (|u_R - u_L|, (u_L + u_R) / 2, (c_L + c_R) / 2, |s_R - s_L|),
+// with u the face-normal velocity and s = ln(p / rho^gamma) / (gamma - 1) the
+// entropy (R = 1).  P is the parameter type (double, or Dual for derivatives
+// with respect to the parameters).
+template <class T, class P>
+T nn_alpha(const P* theta, const T x[4]) {
+  const P* W1 = theta;
+  const P* b1 = W1 + NN_HIDDEN * 4;
+  const P* W2 = b1 + NN_HIDDEN;
+  const P* b2 = W2 + NN_HIDDEN * NN_HIDDEN;
+  const P* W3 = b2 + NN_HIDDEN;
+  const P* b3 = W3 + NN_HIDDEN * NN_HIDDEN;
+  const P* W4 = b3 + NN_HIDDEN;
+  const P* b4 = W4 + NN_HIDDEN;
+  T h1[NN_HIDDEN], h2[NN_HIDDEN], h3[NN_HIDDEN];
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T z = T(0.0) + b1[i];
+    for (int j = 0; j < 4; ++j) z = z + W1[4 * i + j] * x[j];
+    h1[i] = tmax(T(0.0), z);
+  }
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T z = T(0.0) + b2[i];
+    for (int j = 0; j < NN_HIDDEN; ++j) z = z + W2[NN_HIDDEN * i + j] * h1[j];
+    h2[i] = tmax(T(0.0), z);
+  }
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T z = T(0.0) + b3[i];
+    for (int j = 0; j < NN_HIDDEN; ++j) z = z + W3[NN_HIDDEN * i + j] * h2[j];
+    h3[i] = tmax(T(0.0), z);
+  }
+  T z = T(0.0) + b4[0];
+  for (int j = 0; j < NN_HIDDEN; ++j) z = z + W4[j] * h3[j];
+  return exp(z);
+}
+template <class T>
+void rusanov_nn_flux(const Config& c, const T WL[5], const T WR[5], int d, T F[5]) {
+  T UL[5], UR[5], FL[5], FR[5];
+  conservative_of(WL, c.gamma, UL);
+  conservative_of(WR, c.gamma, UR);
+  physical_flux(WL, UL, d, FL);
+  physical_flux(WR, UR, d, FR);
+  const T cL = sqrt(c.gamma * WL[4] / WL[0]);
+  const T cR = sqrt(c.gamma * WR[4] / WR[0]);
+  const T sL = log(WL[4] / pow_gamma(WL[0], c.gamma)) / (c.gamma - 1.0);
+  const T sR = log(WR[4] / pow_gamma(WR[0], c.gamma)) / (c.gamma - 1.0);
+  const T x[4] = {fabs(WR[1 + d] - WL[1 + d]), 0.5 * (WL[1 + d] + WR[1 + d]), 0.5 * (cL + cR), fabs(sR - sL)};
+  T alpha;
+  if constexpr (std::is_same<T, Dual>::value) {
+    if (c.nn_dot) {
+      Dual th[NN_PARAMS];
+      for (int i = 0; i < NN_PARAMS; ++i) th[i] = Dual(c.nn[i], c.nn_dot[i]);
+      alpha = nn_alpha(th, x);
+    } else {
+      alpha = nn_alpha(c.nn, x);
+    }
+  } else {
+    alpha = nn_alpha(c.nn, x);
+  }
+  for (int m = 0; m < 5; ++m) F[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * alpha * (UR[m] - UL[m]);
+}
+
 // The Riemann solver of the configuration.
 template <class T>
 void riemann_flux(const Config& c, const T WL[5], const T WR[5], int d, T F[5]) {
   if (c.flux == FLUX_HLL) hll_flux(WL, WR, d, c.gamma, F, c.speeds);
   else if (c.flux == FLUX_RUSANOV) rusanov_flux(WL, WR, d, c.gamma, F);
+  else if (c.flux == FLUX_RUSANOV_NN) rusanov_nn_flux(c, WL, WR, d, F);
   else hllc_flux(WL, WR, d, c.gamma, F, c.speeds);
 }
 
@@ -511,6 +610,9 @@ void flux_splitting_face_flux(const Field<T>& W, const Config& c, int d, const C
     if (c.recon == RECON_WENO5_Z) {
       gp = weno5_z(Gp[0][k], Gp[1][k], Gp[2][k], Gp[3][k], Gp[4][k], c.eps);
       gm = weno5_z(Gm[5][k], Gm[4][k], Gm[3][k], Gm[2][k], Gm[1][k], c.eps);
+    } else if (c.recon == RECON_WENO3_JS) {
+      gp = weno3_js(Gp[1][k], Gp[2][k], Gp[3][k], c.eps);
+      gm = weno3_js(Gm[4][k], Gm[3][k], Gm[2][k], c.eps);
     } else {
       gp = weno5_js(Gp[0][k], Gp[1][k], Gp[2][k], Gp[3][k], Gp[4][k], c.eps);
       gm = weno5_js(Gm[5][k], Gm[4][k], Gm[3][k], Gm[2][k], Gm[1][k], c.eps);
@@ -545,6 +647,9 @@ void convective_face_flux(const Field<T>& W, const Config& c, int d, const Cell&
     if (c.recon == RECON_WENO5_Z) {
       Wm[m] = weno5_z(a, b, e0, f1, g2, c.eps);
       Wp[m] = weno5_z(h3, g2, f1, e0, b, c.eps);
+    } else if (c.recon == RECON_WENO3_JS) {
+      Wm[m] = weno3_js(b, e0, f1, c.eps);
+      Wp[m] = weno3_js(g2, f1, e0, c.eps);
     } else {
       Wm[m] = weno5_js(a, b, e0, f1, g2, c.eps);
       Wp[m] = weno5_js(h3, g2, f1, e0, b, c.eps);

@@ -44,6 +44,8 @@ inline Counted sqrt(const Counted& a) { ++Counted::ops(); return Counted(std::sq
 inline bool operator<=(const Counted& a, const Counted& b) { return a.v <= b.v; }
 inline bool operator<=(const Counted& a, double b) { return a.v <= b; }
 inline Counted fabs(const Counted& a) { return Counted(std::fabs(a.v)); }  // sign only: not counted
+inline Counted exp(const Counted& a) { ++Counted::ops(); return Counted(std::exp(a.v)); }
+inline Counted log(const Counted& a) { ++Counted::ops(); return Counted(std::log(a.v)); }
 
 template <class T>
 static void store_state(const Config& c, const Field<T>& f, double* U, double* V) {
@@ -72,8 +74,11 @@ static bool valid(const Config* c) {
     const bool p0 = c->bc[2 * d] == BC_PERIODIC, p1 = c->bc[2 * d + 1] == BC_PERIODIC;
     if (p0 != p1) return false;  // periodic must be set on both sides
   }
-  if (c->flux < FLUX_HLLC || c->flux > FLUX_ROE_FS) return false;
-  if (c->recon < RECON_WENO5_JS || c->recon > RECON_WENO5_Z) return false;
+  if (c->flux < FLUX_HLLC || c->flux > FLUX_RUSANOV_NN) return false;
+  if (c->flux == FLUX_RUSANOV_NN && !c->nn) return false;
+  if (c->recon < RECON_WENO5_JS || c->recon > RECON_WENO3_JS) return false;
+  for (int k = 0; k < 6; ++k)
+    if (c->bc[k] < BC_PERIODIC || c->bc[k] > BC_WALL) return false;
   if (c->speeds < SPEED_EINFELDT || c->speeds > SPEED_TORO) return false;
   if (c->integrator < TIME_RK3 || c->integrator > TIME_EULER) return false;
   return true;
@@ -150,6 +155,30 @@ int orc_jvp_run(const Config* c, double* U, double* V, int nsteps, double dt) {
   store_state(*c, f, U, V);
   return 0;
 }
+
+// Forward-mode derivative with respect to the Rusanov-NN parameters: nsteps
+// fixed-dt steps from U (tangent zero) with the parameters carrying the
+// tangent theta_dot; on return U holds the state and V its derivative along
+// theta_dot.
+int orc_jvp_params_run(const Config* c, double* U, double* V, int nsteps, double dt, const double* theta_dot) {
+  if (!valid(c) || !(dt > 0.0) || c->flux != FLUX_RUSANOV_NN || !theta_dot) return -1;
+  Config cc = *c;
+  cc.nn_dot = theta_dot;
+  const size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
+  std::vector<Dual> ud(5 * N);
+  for (size_t q = 0; q < 5 * N; ++q) ud[q] = Dual(U[q], 0.0);
+  Field<Dual> f(cc, 5);
+  load_state(cc, ud.data(), f);
+  for (int s = 0; s < nsteps; ++s) time_step(cc, f, dt);
+  store_state(cc, f, U, V);
+  return 0;
+}
+
+// Rusanov-NN dissipation alpha for given network inputs x[4].
+double orc_nn_alpha(const double* theta, const double* x) { return nn_alpha(theta, x); }
+
+// Single WENO3-JS reconstruction v^-_{i+1/2} from v[i-1..i+1].
+double orc_weno3(const double* v, double eps) { return weno3_js(v[0], v[1], v[2], eps); }
 
 // Sampled cells of a full-size run, computed one by one: for each sample
 // cell, a cube of half-width 9 * nsteps + 3 cells around it is copied from U
@@ -288,6 +317,15 @@ void orc_fs_flux(const double* W6, int d, double gamma, double eps, int recon, d
   F[1 + d] = G[1];
   F[1 + (d + 1) % 3] = G[2];
   F[1 + (d + 2) % 3] = G[3];
+}
+
+// Single Rusanov-NN flux along axis d with network parameters theta.
+void orc_flux_nn(const double* WL, const double* WR, int d, double gamma, const double* theta, double* F) {
+  Config c{};
+  c.gamma = gamma;
+  c.flux = FLUX_RUSANOV_NN;
+  c.nn = theta;
+  riemann_flux(c, WL, WR, d, F);
 }
 
 // HLL flux for given signal speeds (S_L, S_R).
