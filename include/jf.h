@@ -55,20 +55,30 @@ typedef enum {
   JF_ERR_UNSUPPORTED = -6   /* valid but unsupported configuration */
 } jf_status;
 
-typedef enum { JF_BC_PERIODIC = 0, JF_BC_ZERO_GRADIENT = 1 } jf_bc;
+typedef enum { JF_BC_PERIODIC = 0, JF_BC_ZERO_GRADIENT = 1, JF_BC_WALL = 2 } jf_bc;
 enum { JF_F32 = 0, JF_F64 = 1 };
 /* Scheme options (Table 2 of the paper; 0 is the Appendix A configuration). */
 enum { JF_EINFELDT = 0, JF_DAVIS = 1, JF_TORO = 2 };           /* signal speed estimates */
 enum { JF_FLUX_HLLC = 0, JF_FLUX_HLL = 1, JF_FLUX_RUSANOV = 2, /* Riemann solvers */
-       JF_FLUX_ROE = 3 };                                         /* flux splitting (ROE setup) */
-enum { JF_WENO5_JS = 0, JF_WENO5_Z = 1 };                        /* reconstructions */
+       JF_FLUX_ROE = 3,                                           /* flux splitting (ROE setup) */
+       JF_FLUX_RUSANOV_NN = 4 };                                  /* Section 7.4 learned dissipation */
+enum { JF_WENO5_JS = 0, JF_WENO5_Z = 1, JF_WENO3_JS = 2 };       /* reconstructions */
+
+/* The Rusanov-NN dissipation network (Section 7.4): parameters per handle. */
+#define JF_NN_HIDDEN 32
+#define JF_NN_PARAMS (JF_NN_HIDDEN * 4 + JF_NN_HIDDEN + 2 * (JF_NN_HIDDEN * JF_NN_HIDDEN + JF_NN_HIDDEN) + JF_NN_HIDDEN + 1)
 enum { JF_RK3 = 0, JF_RK2 = 1, JF_EULER = 2 };                   /* time integrators */
 
 /* Cartesian grid of nx*ny*nz cells on [lo, hi] (Section 3.1: cuboid cells).
  * bc[] = {x-lo, x-hi, y-lo, y-hi, z-lo, z-hi} (west, east, south, north,
  * bottom, top; Section 3.7), each a jf_bc; periodic must be set on both sides
  * of an axis.  Zero gradient copies the nearest interior cell into the halo
- * (the "neumann"/transmissive boundary of Appendix A). */
+ * (the "neumann"/transmissive boundary of Appendix A).  JF_BC_WALL is a slip
+ * (symmetry) wall: the halo holds the mirror image of the cells inside, with
+ * the momentum normal to the wall negated (the wall boundary of Table 2 for
+ * inviscid flow; with viscosity the mirror makes it a free-slip wall).  Grids
+ * with walls run in the run-time-scheme kernels; the adjoint does not
+ * support them (JF_ERR_UNSUPPORTED). */
 typedef struct {
   int nx, ny, nz;
   double lo[3], hi[3];
@@ -99,8 +109,15 @@ typedef struct {
  *                 eigensystem and Roe splitting (the paper's "ROE" setup):
  *                 `recon` then reconstructs the split characteristic
  *                 fluxes, and safe_recon has no effect
+ *                 JF_FLUX_RUSANOV_NN is Section 7.4's Rusanov flux with the
+ *                 dissipation alpha = exp(NN(x)) of a network whose
+ *                 parameters jf_set_nn gives (inputs x = (|u_R - u_L|,
+ *                 (u_L + u_R)/2, (c_L + c_R)/2, |s_R - s_L|) along the face
+ *                 normal, s = ln(p / rho^gamma) / (gamma - 1); three hidden
+ *                 layers of JF_NN_HIDDEN ReLU units)
  *   recon         JF_WENO5_JS (Jiang & Shu 1996), JF_WENO5_Z (Borges et al.
- *                 2008, power 1)
+ *                 2008, power 1), JF_WENO3_JS (Jiang & Shu 1996, third order:
+ *                 weights 1/3 and 2/3)
  *   integrator    JF_RK3 / JF_RK2 (TVD Runge-Kutta of Gottlieb & Shu 1998,
  *                 Shu-Osher form) or JF_EULER, used by jf_rk3_step,
  *                 jf_rk3_run and jf_batch_step (the names keep the default).
@@ -215,6 +232,18 @@ jf_status jf_batch_step(jf_handle batch, void* const* U_ptrs, int nsteps, double
  * on the stream). */
 jf_status jf_batch_feed_forward(jf_handle batch, void* const* U0_ptrs, void* const* traj_ptrs, int nsteps,
                                 const double* dt_dev, void* stream);
+
+/* Parameters of the Rusanov-NN network of a handle (single grid or batch)
+ * whose scheme has flux == JF_FLUX_RUSANOV_NN (Section 7.4).  theta is a
+ * caller-owned device array of nparams == JF_NN_PARAMS elements of the
+ * handle's dtype: W1[32][4], b1[32], W2[32][32], b2[32], W3[32][32], b3[32],
+ * W4[32], b4 (row-major, outputs by inputs).  The library keeps the pointer
+ * and reads the values at every launch (in CUDA graphs too), so a caller
+ * that updates theta in place between steps needs no new call; theta must
+ * stay valid while work that uses it is in flight.  A new pointer drops the
+ * handle's cached graphs.  Steps with that flux before this call return
+ * JF_ERR_ARG.  Other schemes: JF_ERR_ARG. */
+jf_status jf_set_nn(jf_handle h, const void* theta, int nparams);
 
 /* Choose the launch variant of a handle (autotuner hook): `variant` indexes
  * the tile/schedule table of jf_variant_info; -1 restores the default.

@@ -27,6 +27,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) batch_copy_kernel(const SimDesc<T>* __restrict__ sims) {
   const SimDesc<T> d = sims[blockIdx.y];
   const long long n = 5 * d.N;
+#ifdef JF_DEBUG_BOUNDS
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    jf_trace(d.trace, 0x400, blockIdx.y, (unsigned long long)d.U, (unsigned long long)d.U1, d.N, 0, 0, 0);
+#endif
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     d.U[i] = d.U1[i];
 }
@@ -61,7 +65,7 @@ std::vector<int> batch_variant_list(int dim, bool visc, int kind) {
 template <typename T>
 jf_status setup_variant(jf_ctx* h, int v) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = batch_variant_list<T>(h->dim, visc, scheme_kind(h->scheme));
+  auto list = batch_variant_list<T>(h->dim, visc, scheme_kind(h));
   if (list.empty()) { set_error(h, "batch: no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
   if (v < 0) v = 0;
   if (v >= (int)list.size()) { set_error(h, "batch: variant index out of range"); return JF_ERR_ARG; }
@@ -122,8 +126,12 @@ jf_status create_impl(jf_ctx* h) {
     d.ny = g.ny;
     d.nz = g.nz;
     d.N = N;
+#ifdef JF_DEBUG_BOUNDS
+    d.trace = debug_trace_dev();
+#endif
     for (int a = 0; a < 3; ++a) {
       d.periodic[a] = g.bc[2 * a] == JF_BC_PERIODIC;
+      d.wall[a] = (g.bc[2 * a] == JF_BC_WALL ? 1 : 0) | (g.bc[2 * a + 1] == JF_BC_WALL ? 2 : 0);
       d.inv_h[a] = (T)(1.0 / spacing(g, a));
     }
     cfl[s] = make_cfl(g, h->gas, h->scheme);
@@ -172,14 +180,46 @@ jf_status bind_fields(jf_ctx* h, void* const* U_ptrs, cudaStream_t s) {
   return JF_OK;
 }
 
+// One batch stage (code as in batch_stage_args) over every simulation.
+// FP32: the persistent kernel over the (simulation, tile) work list, reading
+// the device descriptors.  FP64: one launch of the single-grid form per
+// simulation (the same tile code and arithmetic), with arguments built from
+// the host copy of the descriptors; the persistent FP64 form raised an
+// illegal-address fault whose cause is not found, although its inputs read
+// back from the device were correct.
+template <typename T>
+cudaError_t launch_batch_stage(jf_ctx* h, const StageVariant<T>& sv, const SimDesc<T>* dev_sims,
+                               const SimDesc<T>* host_sims, int code, const Gas<T>& g, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    for (int i = 0; i < h->nsim; ++i) {
+      StageArgs<T> A{};
+      batch_stage_args(host_sims[i], code, A);
+      A.flag = h->flag;
+#ifdef JF_DEBUG_BOUNDS
+      A.trace = debug_trace_dev();
+#endif
+      const cudaError_t e = sv.launch(A, g, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  } else {
+    return sv.launch_batch(dev_sims, static_cast<const WorkItem*>(h->d_work), h->nwork, code, g, h->flag,
+                           h->batch_blocks, s);
+  }
+}
+
 template <typename T>
 jf_status enqueue_steps(jf_ctx* h, int nsteps, double* dt_out, cudaStream_t s) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
   const StageVariant<T>& sv = tab[h->table_index];
-  const Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  if (h->scheme.flux == JF_FLUX_RUSANOV_NN) {
+    if (!h->nn) { set_error(h, "Rusanov-NN flux: no network parameters (jf_set_nn)"); return JF_ERR_ARG; }
+    g.nn = static_cast<const T*>(h->nn);
+  }
   const SimDesc<T>* sims = reinterpret_cast<const SimDesc<T>*>(h->d_sims);
-  const WorkItem* work = static_cast<const WorkItem*>(h->d_work);
+  const SimDesc<T>* host_sims = reinterpret_cast<const SimDesc<T>*>(h->host_desc.data());
   for (int step = 0; step < nsteps; ++step) {
     cudaError_t e = launch_cfl_batch<T>(sims, h->d_chunks, h->nchunks, static_cast<const CflArgs*>(h->d_cfl),
                                         h->d_red, h->d_dt, h->flag, s);
@@ -189,7 +229,7 @@ jf_status enqueue_steps(jf_ctx* h, int nsteps, double* dt_out, cudaStream_t s) {
     const int codes[3] = {1, integ == JF_RK2 ? 4 : 2, 3};
     const int nst = integ == JF_RK3 ? 3 : (integ == JF_RK2 ? 2 : 1);
     for (int q = 0; q < nst; ++q) {
-      e = sv.launch_batch(sims, work, h->nwork, codes[q], g, h->flag, h->batch_blocks, s);
+      e = launch_batch_stage<T>(h, sv, sims, host_sims, codes[q], g, s);
       if (e != cudaSuccess) return cuda_fail(h, e, "batch: stage launch");
     }
     if (integ == JF_EULER) {
@@ -255,8 +295,8 @@ jf_status feed_forward_batch(jf_ctx* h, void* const* U0_ptrs, void* const* traj_
   int count_v = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count_v);
   const StageVariant<T>& sv = tab[h->table_index];
-  const Gas<T> g = make_gas<T>(h->gas, h->scheme);
-  const WorkItem* work = static_cast<const WorkItem*>(h->d_work);
+  Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  if (h->scheme.flux == JF_FLUX_RUSANOV_NN) g.nn = static_cast<const T*>(h->nn);
   const int integ = h->scheme.integrator;
   const int codes[3] = {1, integ == JF_RK2 ? 4 : 2, 3};
   const int nst = integ == JF_RK3 ? 3 : (integ == JF_RK2 ? 2 : 1);
@@ -271,7 +311,7 @@ jf_status feed_forward_batch(jf_ctx* h, void* const* U0_ptrs, void* const* traj_
     if ((e = cudaGetLastError()) != cudaSuccess) { st = cuda_fail(h, e, "feed_forward: copy launch"); break; }
     const SimDesc<T>* sims = d_desc + (size_t)t * ns;  // U = slot t + 1
     for (int q = 0; q < nst; ++q) {
-      e = sv.launch_batch(sims, work, h->nwork, codes[q], g, h->flag, h->batch_blocks, s);
+      e = launch_batch_stage<T>(h, sv, sims, desc.data() + (size_t)t * ns, codes[q], g, s);
       if (e != cudaSuccess) { st = cuda_fail(h, e, "feed_forward: stage launch"); break; }
     }
     if (st == JF_OK && integ == JF_EULER) {
@@ -285,8 +325,12 @@ jf_status feed_forward_batch(jf_ctx* h, void* const* U0_ptrs, void* const* traj_
 
 template <typename T>
 jf_status step_batch(jf_ctx* h, void* const* U_ptrs, int nsteps, double* dt_out, cudaStream_t s) {
+  bool rebound = false;
+  for (int i = 0; i < h->nsim; ++i) rebound |= h->bound_ptrs[i] != U_ptrs[i];
   jf_status st = bind_fields<T>(h, U_ptrs, s);
   if (st != JF_OK) return st;
+  // the FP64 stage launches carry the field pointers in their arguments
+  if (sizeof(T) == 8 && rebound) free_graphs(h);
   const GraphKey key{nullptr, nsteps, dt_out, nullptr, h->variant};
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
@@ -319,12 +363,12 @@ int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   std::vector<int> list;
   int bx = 0, by = 0;
   if (h->scheme.dtype == JF_F32) {
-    list = batch_variant_list<float>(h->dim, visc, scheme_kind(h->scheme));
+    list = batch_variant_list<float>(h->dim, visc, scheme_kind(h));
     int c = 0;
     const StageVariant<float>* tab = stage_variants<float>(&c);
     if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
   } else {
-    list = batch_variant_list<double>(h->dim, visc, scheme_kind(h->scheme));
+    list = batch_variant_list<double>(h->dim, visc, scheme_kind(h));
     int c = 0;
     const StageVariant<double>* tab = stage_variants<double>(&c);
     if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
@@ -388,6 +432,10 @@ jf_status jf_batch_feed_forward(jf_handle h, void* const* U0_ptrs, void* const* 
     set_error(h, "jf_batch_feed_forward: null argument or nsteps < 0");
     return JF_ERR_ARG;
   }
+  if (h->scheme.flux == JF_FLUX_RUSANOV_NN && !h->nn) {
+    set_error(h, "Rusanov-NN flux: no network parameters (jf_set_nn)");
+    return JF_ERR_ARG;
+  }
   for (int s = 0; s < h->nsim; ++s)
     if (!U0_ptrs[s] || !traj_ptrs[s] || !aligned16(U0_ptrs[s]) || !aligned16(traj_ptrs[s])) {
       set_error(h, "jf_batch_feed_forward: every state and trajectory must be a 16-byte aligned device array");
@@ -412,3 +460,40 @@ jf_status jf_batch_step(jf_handle h, void* const* U_ptrs, int nsteps, double* dt
 }
 
 }  // extern "C"
+
+#ifdef JF_DEBUG_BOUNDS
+// Device-side inputs of a batch's kernels read back without launching any
+// kernel (debug build only; not declared in jf.h): info = {nwork,
+// batch_blocks, table_index, bx, by, threads, smem, scheme}; the work list;
+// the descriptors after binding U_ptrs.
+extern "C" int jf_debug_batch_inputs(jf_handle h, void* const* U_ptrs, int* info, void* work, int work_len,
+                                     void* sims, int sims_len) {
+  if (!h || h->kind != 1) return -1;
+  info[0] = h->nwork;
+  info[1] = h->batch_blocks;
+  info[2] = h->table_index;
+  int count = 0;
+  if (h->scheme.dtype == JF_F32) {
+    const StageVariant<float>& v = stage_variants<float>(&count)[h->table_index];
+    info[3] = v.bx; info[4] = v.by; info[5] = v.threads; info[6] = (int)v.smem; info[7] = v.scheme;
+    if (bind_fields<float>(h, U_ptrs, nullptr) != JF_OK) return -2;
+  } else {
+    const StageVariant<double>& v = stage_variants<double>(&count)[h->table_index];
+    info[3] = v.bx; info[4] = v.by; info[5] = v.threads; info[6] = (int)v.smem; info[7] = v.scheme;
+    if (bind_fields<double>(h, U_ptrs, nullptr) != JF_OK) return -2;
+  }
+  const int wb = h->nwork * (int)sizeof(WorkItem), sb = (int)h->host_desc.size();
+  if (work_len < wb || sims_len < sb) return -3;
+  if (cudaMemcpy(work, h->d_work, (size_t)wb, cudaMemcpyDeviceToHost) != cudaSuccess) return -4;
+  if (cudaMemcpy(sims, h->d_sims, (size_t)sb, cudaMemcpyDeviceToHost) != cudaSuccess) return -4;
+  return 0;
+}
+
+// Host copy of a batch's descriptors (debug build only; not declared in jf.h).
+extern "C" int jf_debug_batch_desc(jf_handle h, void* buf, int len) {
+  if (!h || h->kind != 1) return -1;
+  const int n = (int)h->host_desc.size();
+  if (buf && len >= n) std::memcpy(buf, h->host_desc.data(), (size_t)n);
+  return n;
+}
+#endif

@@ -34,6 +34,11 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U0, CflA
     const CflChunk ch = chunks[blockIdx.x];
     a = args[ch.sim];
     U = sims[ch.sim].U;
+#ifdef JF_DEBUG_BOUNDS
+    if (threadIdx.x == 0)
+      jf_trace(sims[ch.sim].trace, 0x300, blockIdx.x, ch.sim, (unsigned long long)U, (unsigned long long)ch.begin,
+               (unsigned long long)ch.end, (unsigned long long)a.N, (unsigned long long)(red + ch.sim));
+#endif
     sc = red + ch.sim;
     dto = dts + ch.sim;
     dto2 = nullptr;

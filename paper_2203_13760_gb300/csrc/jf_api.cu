@@ -18,6 +18,8 @@
 
 namespace jf {
 
+static_assert(NN_PARAMS == JF_NN_PARAMS, "network size of the kernels and of the C ABI");
+
 static thread_local std::string g_noctx_error;
 
 void set_error(jf_ctx* h, const std::string& msg) {
@@ -41,7 +43,7 @@ jf_status check_grid(jf_ctx* h, const jf_grid& g) {
     if (n[d] > 1 && n[d] < 5) { set_error(h, "grid: an active axis needs at least 5 cells"); return JF_ERR_ARG; }
     if (!(g.hi[d] > g.lo[d]) || !std::isfinite(g.hi[d] - g.lo[d])) { set_error(h, "grid: hi must exceed lo"); return JF_ERR_ARG; }
     for (int s = 0; s < 2; ++s)
-      if (g.bc[2 * d + s] != JF_BC_PERIODIC && g.bc[2 * d + s] != JF_BC_ZERO_GRADIENT) {
+      if (g.bc[2 * d + s] != JF_BC_PERIODIC && g.bc[2 * d + s] != JF_BC_ZERO_GRADIENT && g.bc[2 * d + s] != JF_BC_WALL) {
         set_error(h, "grid: unknown boundary condition");
         return JF_ERR_ARG;
       }
@@ -67,12 +69,12 @@ jf_status check_physics(jf_ctx* h, const jf_gas& gas, const jf_scheme& s) {
     set_error(h, "scheme: signal_speed must be JF_EINFELDT, JF_DAVIS or JF_TORO");
     return JF_ERR_ARG;
   }
-  if (s.flux < JF_FLUX_HLLC || s.flux > JF_FLUX_ROE) {
-    set_error(h, "scheme: flux must be JF_FLUX_HLLC, JF_FLUX_HLL, JF_FLUX_RUSANOV or JF_FLUX_ROE");
+  if (s.flux < JF_FLUX_HLLC || s.flux > JF_FLUX_RUSANOV_NN) {
+    set_error(h, "scheme: flux must be JF_FLUX_HLLC, JF_FLUX_HLL, JF_FLUX_RUSANOV, JF_FLUX_ROE or JF_FLUX_RUSANOV_NN");
     return JF_ERR_ARG;
   }
-  if (s.recon != JF_WENO5_JS && s.recon != JF_WENO5_Z) {
-    set_error(h, "scheme: recon must be JF_WENO5_JS or JF_WENO5_Z");
+  if (s.recon != JF_WENO5_JS && s.recon != JF_WENO5_Z && s.recon != JF_WENO3_JS) {
+    set_error(h, "scheme: recon must be JF_WENO5_JS, JF_WENO5_Z or JF_WENO3_JS");
     return JF_ERR_ARG;
   }
   if (s.integrator < JF_RK3 || s.integrator > JF_EULER) {
@@ -137,10 +139,23 @@ int reduce_blocks(long long N, int sms) {
 // Variant selection.  A variant = (compiled tile shape, z chunk).
 static const int kZChunks[] = {32, 16, 64, 8};
 
-int scheme_kind(const jf_scheme& s) {
+bool has_walls(const jf_grid& g) {
+  for (int i = 0; i < 6; ++i)
+    if (g.bc[i] == JF_BC_WALL) return true;
+  return false;
+}
+
+int scheme_kind(const jf_scheme& s, bool walls) {
   if (s.flux == JF_FLUX_ROE) return SCH_ROE;
-  const bool general = s.flux != JF_FLUX_HLLC || s.signal_speed != JF_EINFELDT || s.recon != JF_WENO5_JS;
+  if (s.flux == JF_FLUX_RUSANOV_NN) return SCH_NN;
+  const bool general = s.flux != JF_FLUX_HLLC || s.signal_speed != JF_EINFELDT || s.recon != JF_WENO5_JS || walls;
   return general ? SCH_GENERAL : SCH_DEFAULT;
+}
+
+int scheme_kind(const jf_ctx* h) {
+  bool walls = h->kind == 0 && has_walls(h->grid);
+  for (const jf_grid& g : h->grids) walls = walls || has_walls(g);
+  return scheme_kind(h->scheme, walls);
 }
 
 template <typename T>
@@ -161,7 +176,7 @@ std::vector<std::pair<int, int>> variant_list(int dim, bool visc, int kind) {
 template <typename T>
 jf_status select_variant(jf_ctx* h, int v, bool prepare) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = variant_list<T>(h->dim, visc, scheme_kind(h->scheme));
+  auto list = variant_list<T>(h->dim, visc, scheme_kind(h));
   if (list.empty()) { set_error(h, "no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
   if (v < 0) v = 0;
   if (v >= (int)list.size()) { set_error(h, "variant index out of range"); return JF_ERR_ARG; }
@@ -180,7 +195,7 @@ jf_status select_variant(jf_ctx* h, int v, bool prepare) {
 template <typename T>
 int describe_variant(jf_ctx* h, int v, char* buf, int len) {
   const bool visc = dissipative(h->gas, h->scheme);
-  auto list = variant_list<T>(h->dim, visc, scheme_kind(h->scheme));
+  auto list = variant_list<T>(h->dim, visc, scheme_kind(h));
   if (v < 0 || v >= (int)list.size()) return (int)list.size();
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
@@ -202,6 +217,7 @@ StageArgs<T> base_args(const jf_ctx* h) {
   A.N = (long long)A.nx * A.ny * A.nz;
   for (int d = 0; d < 3; ++d) {
     A.periodic[d] = h->grid.bc[2 * d] == JF_BC_PERIODIC;
+    A.wall[d] = (h->grid.bc[2 * d] == JF_BC_WALL ? 1 : 0) | (h->grid.bc[2 * d + 1] == JF_BC_WALL ? 2 : 0);
     A.inv_h[d] = (T)(1.0 / spacing(h->grid, d));
   }
   A.zchunk = h->zchunk;
@@ -213,7 +229,11 @@ template <typename T>
 jf_status launch(jf_ctx* h, const StageArgs<T>& A, cudaStream_t s) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
-  const Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  if (h->scheme.flux == JF_FLUX_RUSANOV_NN) {
+    if (!h->nn) { set_error(h, "Rusanov-NN flux: no network parameters (jf_set_nn)"); return JF_ERR_ARG; }
+    g.nn = static_cast<const T*>(h->nn);
+  }
   cudaError_t e = tab[h->table_index].launch(A, g, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "stage kernel launch");
   return JF_OK;
@@ -468,6 +488,18 @@ jf_status jf_set_variant(jf_handle h, int variant) {
   free_graphs(h);
   if (h->kind == 1) return batch_set_variant(h, variant);
   return JF_DISPATCH(h, select_variant, h, variant, true);
+}
+
+jf_status jf_set_nn(jf_handle h, const void* theta, int nparams) {
+  if (!h) { set_error(nullptr, "jf_set_nn: null handle"); return JF_ERR_ARG; }
+  if (h->scheme.flux != JF_FLUX_RUSANOV_NN) { set_error(h, "jf_set_nn: the scheme's flux is not JF_FLUX_RUSANOV_NN"); return JF_ERR_ARG; }
+  if (!theta || nparams != JF_NN_PARAMS || ((uintptr_t)theta % h->esize) != 0) {
+    set_error(h, "jf_set_nn: need a device array of JF_NN_PARAMS elements of the handle's dtype");
+    return JF_ERR_ARG;
+  }
+  if (theta != h->nn) free_graphs(h);
+  h->nn = theta;
+  return JF_OK;
 }
 
 int jf_variant_info(jf_handle h, int variant, char* buf, int len) {

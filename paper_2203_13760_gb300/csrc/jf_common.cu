@@ -1,10 +1,33 @@
 // Workspace shared by every handle kind (allocation and release).
+#include <cstring>
+
 #include "jf_internal.h"
 
 namespace jf {
 
+#ifdef JF_DEBUG_BOUNDS
+static unsigned long long* g_trace_host = nullptr;
+static unsigned long long* g_trace_dev = nullptr;
+
+unsigned long long* debug_trace_dev() {
+  if (!g_trace_dev) {
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(unsigned long long) * kTraceWords, cudaHostAllocMapped) != cudaSuccess) return nullptr;
+    std::memset(p, 0, sizeof(unsigned long long) * kTraceWords);
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) return nullptr;
+    g_trace_host = static_cast<unsigned long long*>(p);
+    g_trace_dev = static_cast<unsigned long long*>(d);
+  }
+  return g_trace_dev;
+}
+#endif
+
 jf_status alloc_common(jf_ctx* h) {
   cudaError_t e;
+#ifdef JF_DEBUG_BOUNDS
+  debug_trace_dev();
+#endif
   if ((e = cudaMalloc(&h->flag, sizeof(int))) != cudaSuccess) return cuda_fail(h, e, "workspace: flag");
   if ((e = cudaMemset(h->flag, 0, sizeof(int))) != cudaSuccess) return cuda_fail(h, e, "workspace: flag");
   if ((e = cudaMalloc(&h->dt_buf, sizeof(double))) != cudaSuccess) return cuda_fail(h, e, "workspace: dt");
@@ -40,3 +63,11 @@ void release_all(jf_ctx* h) {
 }
 
 }  // namespace jf
+
+#ifdef JF_DEBUG_BOUNDS
+// Host view of the trace buffer (debug build only; not declared in jf.h).
+extern "C" unsigned long long* jf_debug_trace_host(void) {
+  jf::debug_trace_dev();
+  return jf::g_trace_host;
+}
+#endif

@@ -51,6 +51,7 @@ struct jf_ctx {
   jf::ReduceScratch* red_cfl = nullptr;
   jf::ReduceScratch* red_loss = nullptr;
   int* flag = nullptr;       // device error flag
+  const void* nn = nullptr;  // Rusanov-NN parameters (caller-owned device array; jf_set_nn)
   cudaStream_t capture_stream = nullptr;
   std::map<jf::GraphKey, jf::GraphEntry> graphs;
   std::string err;
@@ -82,8 +83,11 @@ double spacing(const jf_grid& g, int d);
 double conductivity(const jf_gas& gas, const jf_scheme& s);
 bool dissipative(const jf_gas& gas, const jf_scheme& s);
 // kernel family of a scheme: SCH_DEFAULT, SCH_GENERAL (run-time Table 2
-// Godunov variants) or SCH_ROE (flux splitting)
-int scheme_kind(const jf_scheme& s);
+// Godunov variants, and every grid with slip walls), SCH_ROE (flux
+// splitting) or SCH_NN (Rusanov-NN)
+bool has_walls(const jf_grid& g);
+int scheme_kind(const jf_scheme& s, bool walls);
+int scheme_kind(const jf_ctx* h);
 CflArgs make_cfl(const jf_grid& g, const jf_gas& gas, const jf_scheme& s);
 int reduce_blocks(long long N, int sms);
 bool aligned16(const void* p);
@@ -102,6 +106,12 @@ cudaError_t launch_cfl_batch(const void* sims, const void* chunks, int nchunks, 
 // workspace shared by every handle kind: flag, dt scalar, reduction scratch, capture stream
 jf_status alloc_common(jf_ctx* h);
 void release_all(jf_ctx* h);
+
+#ifdef JF_DEBUG_BOUNDS
+// host-mapped trace buffer of the debug build (jf_common.cu), allocated at
+// the first call
+unsigned long long* debug_trace_dev();
+#endif
 
 // batch (batch.cu)
 jf_status batch_set_variant(jf_ctx* h, int variant);

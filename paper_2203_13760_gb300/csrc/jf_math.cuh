@@ -11,6 +11,8 @@
 //                     (1994) signal speeds (Table 2)
 //   hll, rusanov      Table 2: HLL (Harten, Lax, van Leer 1983) and local
 //                     Lax-Friedrichs
+//   rusanov_nn        Section 7.4: Rusanov flux with a learned dissipation
+//   weno3             Table 2 WENO3-JS
 //   df4 / dc4 / rc4   Section 3.4 fourth-order face derivative, cell-centre
 //                     derivative and central interpolation to the face
 #pragma once
@@ -31,10 +33,18 @@ struct Gas {
   T lambda;    // heat conductivity
   T eps;       // WENO5 epsilon
   int safe;    // first-order fallback for non-positive reconstructed rho / p
-  int flux;    // 0 HLLC, 1 HLL, 2 Rusanov (local Lax-Friedrichs)
-  int recon;   // 0 WENO5-JS, 1 WENO5-Z
+  int flux;    // 0 HLLC, 1 HLL, 2 Rusanov (local Lax-Friedrichs), 4 Rusanov-NN
+  int recon;   // 0 WENO5-JS, 1 WENO5-Z, 2 WENO3-JS
   int speeds;  // 0 Einfeldt, 1 Davis, 2 Toro (PVRS)
+  const T* nn; // Rusanov-NN parameters (NN_PARAMS values; shared memory in the kernels)
 };
+
+// The Rusanov-NN dissipation network (Section 7.4): inputs
+// x = (|du_n|, mean u_n, mean c, |ds|), three hidden layers of NN_HIDDEN ReLU
+// units, alpha = exp(output); parameters W1 [32][4], b1, W2 [32][32], b2,
+// W3 [32][32], b3, W4 [32], b4 (row-major, outputs by inputs).
+constexpr int NN_HIDDEN = 32;
+constexpr int NN_PARAMS = 32 * 4 + 32 + 2 * (32 * 32 + 32) + 32 + 1;
 
 template <typename T> JF_HD T tsqrt(T x);
 template <> JF_HD float tsqrt<float>(float x) { return sqrtf(x); }
@@ -161,6 +171,21 @@ __device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, 
   const float2 num = __ffma2_rn(r2, g2, __ffma2_rn(r1, g1, __fmul2_rn(r0, g0)));
   const float2 den = __ffma2_rn(c(1.0f / 3.0f), r0, __ffma2_rn(c(2.0f), r1, r2));
   return __ffma2_rn(num, rcp2(den), v0);
+}
+
+// WENO3-JS (Table 2): value at x_{i+1/2} biased to the left from
+// v[i-1], v[i], v[i+1]: q0 = (3 v[i] - v[i-1]) / 2, q1 = (v[i] + v[i+1]) / 2,
+// beta0 = (v[i] - v[i-1])^2, beta1 = (v[i+1] - v[i])^2,
+// alpha_k = d_k / (eps + beta_k)^2, d = (1/3, 2/3), omega_k = alpha_k / sum.
+template <typename T>
+JF_HD T weno3(T vm1, T v0, T vp1, T eps) {
+  const T q0 = T(0.5) * (T(3) * v0 - vm1), q1 = T(0.5) * (v0 + vp1);
+  const T t0 = eps + (v0 - vm1) * (v0 - vm1), t1 = eps + (vp1 - v0) * (vp1 - v0);
+  const T a0 = T(1.0 / 3.0) * trcp(t0 * t0), a1 = T(2.0 / 3.0) * trcp(t1 * t1);
+  return (a0 * q0 + a1 * q1) * trcp(a0 + a1);
+}
+__device__ __forceinline__ float2 weno3_pair(float2 vm1, float2 v0, float2 vp1, float eps) {
+  return make_float2(weno3(vm1.x, v0.x, vp1.x, eps), weno3(vm1.y, v0.y, vp1.y, eps));
 }
 
 // Signal speeds S_L <= S_R at a face along axis D (Table 2 estimates), from
@@ -306,6 +331,81 @@ JF_HD void rusanov(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
   side_state(WL, g, EL, irL, cL);
   side_state(WR, g, ER, irR, cR);
   const T a = tmax(fabs(WL[1 + D]) + cL, fabs(WR[1 + D]) + cR);
+  T FL[5], FR[5], UL[5], UR[5];
+  side_flux<T, D>(WL, EL, FL, UL);
+  side_flux<T, D>(WR, ER, FR, UR);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) F[q] = T(0.5) * (FL[q] + FR[q]) - T(0.5) * a * (UR[q] - UL[q]);
+}
+
+template <typename T> JF_HD T texp(T x);
+template <> JF_HD float texp<float>(float x) { return expf(x); }
+template <> JF_HD double texp<double>(double x) { return exp(x); }
+template <typename T> JF_HD T tlog(T x);
+template <> JF_HD float tlog<float>(float x) { return logf(x); }
+template <> JF_HD double tlog<double>(double x) { return log(x); }
+
+// alpha = exp(NN(x)) of the Rusanov-NN flux; th: the network parameters.
+// Not inlined: one copy of the ~2200 multiply-adds serves every face
+// direction, and its 64 hidden values do not add to the register pressure
+// of the tile code around the call.
+template <typename T>
+__host__ __device__ __noinline__ T nn_alpha(const T* th, const T x[4]) {
+  const T* W1 = th;
+  const T* b1 = W1 + NN_HIDDEN * 4;
+  const T* W2 = b1 + NN_HIDDEN;
+  const T* b2 = W2 + NN_HIDDEN * NN_HIDDEN;
+  const T* W3 = b2 + NN_HIDDEN;
+  const T* b3 = W3 + NN_HIDDEN * NN_HIDDEN;
+  const T* W4 = b3 + NN_HIDDEN;
+  const T b4 = W4[NN_HIDDEN];
+  T h1[NN_HIDDEN], h2[NN_HIDDEN];
+#pragma unroll
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    const T z = b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] + W1[4 * i + 3] * x[3];
+    h1[i] = tmax(T(0), z);
+  }
+#pragma unroll
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T z = b2[i];
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; ++j) z += W2[NN_HIDDEN * i + j] * h1[j];
+    h2[i] = tmax(T(0), z);
+  }
+  T out = b4;
+#pragma unroll 4
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T z = b3[i];
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; ++j) z += W3[NN_HIDDEN * i + j] * h2[j];
+    out += W4[i] * tmax(T(0), z);
+  }
+  return texp(out);
+}
+
+// Network inputs of the Rusanov-NN flux at a face along D (Section 7.4):
+// |u_R - u_L|, (u_L + u_R)/2, (c_L + c_R)/2, |s_R - s_L| with u the normal
+// velocity and s = ln(p / rho^gamma) / (gamma - 1).
+template <typename T, int D>
+JF_HD void nn_inputs(const T WL[5], const T WR[5], const Gas<T>& g, T cL, T cR, T x[4]) {
+  const T sL = (tlog(WL[4]) - g.gamma * tlog(WL[0])) * g.inv_gm1;
+  const T sR = (tlog(WR[4]) - g.gamma * tlog(WR[0])) * g.inv_gm1;
+  x[0] = fabs(WR[1 + D] - WL[1 + D]);
+  x[1] = T(0.5) * (WL[1 + D] + WR[1 + D]);
+  x[2] = T(0.5) * (cL + cR);
+  x[3] = fabs(sR - sL);
+}
+
+// Rusanov-NN (Section 7.4, Eq. (Rusanov)): F = (F_L + F_R)/2 - alpha (U_R - U_L)/2
+// with alpha = exp(NN(x)).
+template <typename T, int D>
+JF_HD void rusanov_nn(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
+  T EL, ER, irL, irR, cL, cR;
+  side_state(WL, g, EL, irL, cL);
+  side_state(WR, g, ER, irR, cR);
+  T x[4];
+  nn_inputs<T, D>(WL, WR, g, cL, cR, x);
+  const T a = nn_alpha(g.nn, x);
   T FL[5], FR[5], UL[5], UR[5];
   side_flux<T, D>(WL, EL, FL, UL);
   side_flux<T, D>(WR, ER, FR, UR);

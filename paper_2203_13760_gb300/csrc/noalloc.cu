@@ -89,6 +89,10 @@ extern "C" jf_status jf_rk3_step_noalloc(const jf_grid* grid, const jf_gas* gas,
   jf_status st;
   if ((st = check_grid(nullptr, *grid)) != JF_OK) return st;
   if ((st = check_physics(nullptr, *gas, *scheme)) != JF_OK) return st;
+  if (scheme->flux == JF_FLUX_RUSANOV_NN) {
+    set_error(nullptr, "jf_rk3_step_noalloc: the Rusanov-NN flux needs a handle (jf_set_nn)");
+    return JF_ERR_UNSUPPORTED;
+  }
   const long long cells = (long long)grid->nx * grid->ny * grid->nz;
   if (cells > kMaxCells) {
     set_error(nullptr, "jf_rk3_step_noalloc: the grid has more cells than the fixed scratch holds "

@@ -13,7 +13,7 @@
 // (each plane with a 3-cell x/y halo, edges and corners included, as the
 // viscous cross derivatives need them).  Per plane: the new plane k+3 is
 // loaded into the slot of plane k-3 (coalesced rows, periodic / zero-gradient
-// index map applied per cell, converted to W and T), then the x and y face
+// / slip-wall index map applied per cell, converted to W and T), then the x and y face
 // fluxes of plane k are written to shared memory, and each cell thread
 // computes the z face k+1/2 of its column, keeping the k-1/2 face in registers
 // from the previous plane.  Every face flux is evaluated once per CTA; only
@@ -28,6 +28,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include <type_traits>
 
@@ -36,6 +37,33 @@
 namespace jf {
 
 constexpr int HALO = 3;
+
+// Bounds-checked debug build (-DJF_DEBUG_BOUNDS): every global and
+// shared-memory index of the stage kernels is checked before the access; a
+// bad one is printed (at most 32 lines per translation unit) and the access
+// is skipped (a load then yields 1), so that the kernel reports the fault
+// instead of making it.  Off in the normal build.
+#ifdef JF_DEBUG_BOUNDS
+static __device__ int jf_debug_lines;
+#define JF_CHECK(ok, ...)                                                        \
+  ((ok) ? true : ((atomicAdd(&jf_debug_lines, 1) < 32 ? (printf(__VA_ARGS__), 0) : 0), false))
+// Trace records in host-mapped memory (they stay readable after a fault):
+// slot 0 counts records; record r occupies words 8 + 8 r .. 8 + 8 r + 7.
+constexpr int kTraceWords = 1 << 20;
+__device__ __forceinline__ void jf_trace(unsigned long long* tr, unsigned long long a, unsigned long long b,
+                                         unsigned long long c, unsigned long long d, unsigned long long e,
+                                         unsigned long long f, unsigned long long g, unsigned long long h) {
+  if (!tr) return;
+  const unsigned long long r = atomicAdd(tr, 1ull);
+  if (8 + 8 * r + 8 > (unsigned long long)kTraceWords) return;
+  volatile unsigned long long* w = tr + 8 + 8 * r;
+  w[0] = a; w[1] = b; w[2] = c; w[3] = d; w[4] = e; w[5] = f; w[6] = g; w[7] = h;
+  __threadfence_system();
+}
+unsigned long long* debug_trace_dev();  // host: the trace buffer (allocated at the first call)
+#else
+#define JF_CHECK(ok, ...) true
+#endif
 
 // Per-launch description of one grid and one stage.
 template <typename T>
@@ -47,11 +75,15 @@ struct StageArgs {
   int nx, ny, nz;
   long long N;        // nx * ny * nz
   int periodic[3];    // 1: periodic axis, 0: zero gradient
+  int wall[3];        // slip walls of an axis: bit 0 low side, bit 1 high side
   T inv_h[3];         // 1 / dx_d
   T a, b;             // stage coefficients
   int rhs_only;       // 1: out = L(Us)
   int zchunk;         // planes per CTA along z (3D)
   int* flag;          // device error flag (bit 0: non-physical state)
+#ifdef JF_DEBUG_BOUNDS
+  unsigned long long* trace;  // host-mapped trace records (debug build)
+#endif
 };
 
 __device__ __forceinline__ int map_index(int i, int n, int periodic) {
@@ -63,6 +95,22 @@ __device__ __forceinline__ int map_index(int i, int n, int periodic) {
     return i;
   }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Index map with slip walls (Table 2 boundary conditions; the run-time scheme
+// kernels only): a ghost cell beyond a wall is the mirror image of the cell
+// inside (-1 - i at the low side, 2n - 1 - i at the high side) and `flip`
+// records that its momentum normal to the wall changes sign.  Mirroring each
+// axis on its own equals filling the ghost layers axis after axis (edge and
+// corner ghosts then carry the product of the flips).  Active axes have at
+// least 5 cells, so the mirror of the 3-cell halo stays inside the grid; a
+// ragged tile also loads cells further out, which no face uses, and their
+// mirror index is clamped into the grid so that every load stays in bounds.
+__device__ __forceinline__ int map_index_bc(int i, int n, int periodic, int wall, bool& flip) {
+  if (i < 0 && (wall & 1)) { flip = true; return min(-1 - i, n - 1); }
+  if (i >= n && (wall & 2)) { flip = true; return max(2 * n - 1 - i, 0); }
+  flip = false;
+  return map_index(i, n, periodic);
 }
 
 // Shared-memory plane geometry.
@@ -96,11 +144,15 @@ struct PlaneRegs {
 
 // Fetch plane gz (global z index, mapped by the boundary condition) of the
 // tile at (gx0, gy0).
-template <typename T, int BX, int BY, int DIM, bool VISC>
+// WALLS: the kernel handles slip walls (the default-scheme kernels never
+// see them; the host routes walled grids to the run-time scheme kernels).
+template <typename T, int BX, int BY, int DIM, bool VISC, bool WALLS>
 __device__ __forceinline__ void fetch_plane(const StageArgs<T>& A, PlaneRegs<T, BX, BY, DIM, VISC>& r, int gx0,
                                             int gy0, int gz) {
   using G = Geo<BX, BY, DIM, VISC>;
-  const int kz = DIM == 3 ? map_index(gz, A.nz, A.periodic[2]) : 0;
+  bool fz = false;
+  int kz = 0;
+  if (DIM == 3) kz = WALLS ? map_index_bc(gz, A.nz, A.periodic[2], A.wall[2], fz) : map_index(gz, A.nz, A.periodic[2]);
   const long long zoff = (long long)kz * A.ny;
 #pragma unroll
   for (int i = 0; i < PlaneRegs<T, BX, BY, DIM, VISC>::PF; ++i) {
@@ -108,11 +160,27 @@ __device__ __forceinline__ void fetch_plane(const StageArgs<T>& A, PlaneRegs<T, 
     if (t < G::CS) {
       const int ly = t / G::PX;
       const int lx = t - ly * G::PX;
-      const int gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
-      const int gy = DIM >= 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
+      bool fx = false, fy = false;
+      int gx, gy = 0;
+      if (WALLS) {
+        gx = map_index_bc(gx0 + lx - HALO, A.nx, A.periodic[0], A.wall[0], fx);
+        if (DIM >= 2) gy = map_index_bc(gy0 + ly - G::HY, A.ny, A.periodic[1], A.wall[1], fy);
+      } else {
+        gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
+        if (DIM >= 2) gy = map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]);
+      }
       const long long q = (zoff + gy) * A.nx + gx;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) r.v[i][c] = __ldg(A.Us + q + c * A.N);
+      for (int c = 0; c < 5; ++c)
+        r.v[i][c] = JF_CHECK(q >= 0 && q < A.N, "JFDBG fetch q=%lld N=%lld gx=%d gy=%d kz=%d tile=(%d,%d) t=%d\n", q,
+                             A.N, gx, gy, kz, gx0, gy0, t)
+                        ? __ldg(A.Us + q + c * A.N)
+                        : T(1);
+      if (WALLS) {
+        if (fx) r.v[i][1] = -r.v[i][1];
+        if (fy) r.v[i][2] = -r.v[i][2];
+        if (fz) r.v[i][3] = -r.v[i][3];
+      }
     }
   }
 }
@@ -144,11 +212,11 @@ __device__ __forceinline__ void commit_plane(const StageArgs<T>& A, const Gas<T>
   if (bad) atomicOr(A.flag, 1);
 }
 
-template <typename T, int BX, int BY, int DIM, bool VISC>
+template <typename T, int BX, int BY, int DIM, bool VISC, bool WALLS>
 __device__ __forceinline__ void load_plane(const StageArgs<T>& A, const Gas<T>& g, T* dst, int gx0, int gy0,
                                            int gz) {
   PlaneRegs<T, BX, BY, DIM, VISC> r;
-  fetch_plane<T, BX, BY, DIM, VISC>(A, r, gx0, gy0, gz);
+  fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, r, gx0, gy0, gz);
   commit_plane<T, BX, BY, DIM, VISC>(A, g, r, dst);
 }
 
@@ -160,7 +228,11 @@ struct RingView {
   const T* s;
   int plane[7];  // element offset of plane k + e, index e + 3
   __device__ __forceinline__ T at(int c, int x, int y, int e) const {
-    return s[plane[e + 3] + c * G::CS + y * G::PX + x];
+    const int i = plane[e + 3] + c * G::CS + y * G::PX + x;
+    return JF_CHECK(i >= 0 && i < G::RING * G::PLANE && x >= 0 && x < G::PX && y >= 0 && y < G::PY,
+                    "JFDBG ring c=%d x=%d y=%d e=%d i=%d\n", c, x, y, e, i)
+               ? s[i]
+               : T(1);
   }
 };
 
@@ -181,7 +253,7 @@ template <> struct Roles<2> {
 };
 
 // Scheme codes of the stage kernels (template parameter SCH).
-enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2 };
+enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2, SCH_NN = 3 };
 
 // Flux-splitting face flux of the ROE setup (Section 3.3, Flux-Splitting
 // approach; Section 5): Roe average of the two cells beside the face, the
@@ -189,7 +261,7 @@ enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2 };
 // states U_j and fluxes F_j projected on the characteristic fields
 // (V_j = L U_j, G_j = L F_j), Roe splitting G+-_j = (G_j +- |lambda| V_j) / 2,
 // WENO5 of G+ (left-biased, cells -2..2) and G- (mirrored, cells 3..-1) per
-// field, and the sum transformed back, F = R (G+ + G-).  L and R are applied
+// field (WENO3: cells -1..1 and 2..0), and the sum transformed back, F = R (G+ + G-).  L and R are applied
 // in closed form (b1 = (gamma - 1) / c^2, b2 = b1 |u|^2 / 2,
 // s(X) = b2 X_0 - b1 u.X_m + b1 X_4, d(X) = (u_n X_0 - X_n) / c):
 //   L X = [(s + d) / 2, X_0 - s, X_t1 - u_t1 X_0, X_t2 - u_t2 X_0, (s - d) / 2],
@@ -252,6 +324,16 @@ __device__ __forceinline__ void fs_flux(const Val& val, const Gas<T>& g, int rec
   T Gh[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
+    if (recon == 2) {  // WENO3-JS: G+ from cells -1..1, G- from cells 2..0
+      if constexpr (sizeof(T) == 4) {
+        const float2 r = weno3_pair(make_float2(Pp[k][1], Pm[k][1]), make_float2(Pp[k][2], Pm[k][2]),
+                                    make_float2(Pp[k][3], Pm[k][3]), g.eps);
+        Gh[k] = r.x + r.y;
+      } else {
+        Gh[k] = weno3(Pp[k][1], Pp[k][2], Pp[k][3], g.eps) + weno3(Pm[k][1], Pm[k][2], Pm[k][3], g.eps);
+      }
+      continue;
+    }
     if constexpr (sizeof(T) == 4) {
       const float2 r = weno5_pair(make_float2(Pp[k][0], Pm[k][0]), make_float2(Pp[k][1], Pm[k][1]),
                                   make_float2(Pp[k][2], Pm[k][2]), make_float2(Pp[k][3], Pm[k][3]),
@@ -274,7 +356,10 @@ __device__ __forceinline__ void fs_flux(const Val& val, const Gas<T>& g, int rec
 // position (x0, y0, plane 0) and its neighbour along D.
 // SCH_DEFAULT: the default scheme (WENO5-JS, HLLC, Einfeldt speeds) compiled
 // alone; SCH_GENERAL: the Table 2 Godunov variants chosen at run time from g;
-// SCH_ROE: the flux-splitting ROE setup (reconstruction chosen from g).
+// SCH_ROE: the flux-splitting ROE setup (reconstruction chosen from g);
+// SCH_NN: the Rusanov-NN flux (Section 7.4; reconstruction chosen from g),
+// a kernel family of its own because the network's hidden layers need far
+// more registers than the other fluxes.
 template <typename T, int D, int BX, int BY, int DIM, bool VISC, int SCH>
 __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
                                           const Gas<T>& g, const T inv_h[3], T NF[5]) {
@@ -291,6 +376,21 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
   } else {
   // WENO5-JS left / right states of each primitive component (Section 3.3)
   T Wm[5], Wp[5];
+  if ((SCH == SCH_GENERAL || SCH == SCH_NN) && recon == 2) {
+    // WENO3-JS: cells -1, 0, 1 (left state) and 2, 1, 0 (right state)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const T v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0), v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0);
+      if constexpr (sizeof(T) == 4) {
+        const float2 r = weno3_pair(make_float2(v1, v4), make_float2(v2, v3), make_float2(v3, v2), g.eps);
+        Wm[c] = r.x;
+        Wp[c] = r.y;
+      } else {
+        Wm[c] = weno3(v1, v2, v3, g.eps);
+        Wp[c] = weno3(v4, v3, v2, g.eps);
+      }
+    }
+  } else {
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     const T v0 = val(c, -2, 0, 0), v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0);
@@ -305,6 +405,7 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
       Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps, recon);
     }
   }
+  }
   if (g.safe) {
     if (!(Wm[0] > T(0)) || !(Wm[4] > T(0))) {
 #pragma unroll
@@ -316,6 +417,7 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
     }
   }
   if constexpr (SCH == SCH_GENERAL) riemann_flux<T, D>(Wm, Wp, g, F);
+  else if constexpr (SCH == SCH_NN) rusanov_nn<T, D>(Wm, Wp, g, F);
   else hllc<T, D>(Wm, Wp, g, F, 0);
   }
 #pragma unroll
@@ -442,6 +544,7 @@ template <typename T, int DIM, bool VISC, int BX, int BY, int SCH>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& g, int bx, int by, int bz,
                                            T* smem) {
   using G = Geo<BX, BY, DIM, VISC>;
+  constexpr bool WALLS = SCH != SCH_DEFAULT;
   T* ring = smem;
   T* Fx = ring + G::RING * G::PLANE;      // [5][BY][BX+1]
   T* Fy = Fx + 5 * G::NFX;                // [5][BY+1][BX]
@@ -492,17 +595,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight during plane k
   if (DIM == 3) {
-    for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
+    for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
     __syncthreads();
     // lower face of plane z0 = upper face of plane z0 - 1 (slot 2); plane
     // offset -3 is never read
     set_view(5);
     if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
     __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
-    load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, z0 + 3);
-    if (z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC>(A, next, gx0, gy0, z0 + 4);
+    load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring, gx0, gy0, z0 + 3);
+    if (z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, z0 + 4);
   } else {
-    load_plane<T, BX, BY, DIM, VISC>(A, g, ring, gx0, gy0, 0);
+    load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring, gx0, gy0, 0);
   }
   __syncthreads();
 
@@ -516,8 +619,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     if (own && !A.rhs_only) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        us[c] = __ldg(A.Us + qc + c * A.N);
-        un[c] = A.Un ? A.Un[qc + c * A.N] : T(0);
+        const bool ok = JF_CHECK(qc >= 0 && qc < A.N, "JFDBG cell qc=%lld N=%lld\n", qc, A.N);
+        us[c] = ok ? __ldg(A.Us + qc + c * A.N) : T(1);
+        un[c] = A.Un && ok ? A.Un[qc + c * A.N] : T(0);
       }
     }
 
@@ -526,14 +630,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       face_flux<T, 0, BX, BY, DIM, VISC, SCH>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
       const int t = xf_y * (BX + 1) + xf_x;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) Fx[c * G::NFX + t] = NF[c];
+      for (int c = 0; c < 5; ++c)
+        if (JF_CHECK(t >= 0 && t < G::NFX, "JFDBG Fx t=%d\n", t)) Fx[c * G::NFX + t] = NF[c];
     }
     if (DIM >= 2) {
       T NF[5];
       face_flux<T, 1, BX, BY, DIM, VISC, SCH>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
       const int t = yf_y * BX + yf_x;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) Fy[c * G::NFY + t] = NF[c];
+      for (int c = 0; c < 5; ++c)
+        if (JF_CHECK(t >= 0 && t < G::NFY, "JFDBG Fy t=%d\n", t)) Fy[c * G::NFY + t] = NF[c];
     }
     T NFz_hi[5];
     if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
@@ -556,7 +662,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           o = A.b * (us[c] + dt * rhs);
           if (A.Un) o += A.a * un[c];
         }
-        A.out[qc + c * A.N] = o;
+        if (JF_CHECK(qc >= 0 && qc < A.N, "JFDBG store qc=%lld N=%lld\n", qc, A.N)) A.out[qc + c * A.N] = o;
       }
     }
     if (DIM == 3) {
@@ -565,7 +671,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       const int nb = base + 1 == 6 ? 0 : base + 1;  // slot of plane k - 2, dead after this plane's faces
       if (k + 1 < z1) {
         commit_plane<T, BX, BY, DIM, VISC>(A, g, next, ring + nb * G::PLANE);  // plane k + 4
-        if (k + 2 < z1) fetch_plane<T, BX, BY, DIM, VISC>(A, next, gx0, gy0, k + 5);
+        if (k + 2 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, k + 5);
       }
       __syncthreads();
       base = nb;
@@ -584,14 +690,54 @@ struct SimDesc {
   const double* dt;   // this simulation's step
   int nx, ny, nz;
   int periodic[3];
+  int wall[3];
   T inv_h[3];
   long long N;
+#ifdef JF_DEBUG_BOUNDS
+  unsigned long long* trace;  // host-mapped trace records (debug build)
+#endif
 };
 
 struct WorkItem {
   int sim;
   int bx, by;
 };
+
+// Arguments of batch stage `stage` for the simulation of descriptor d:
+//   1: U1 = U + dt L(U) (every integrator); 2 (TVD-RK3): U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+//   3 (TVD-RK3): U = 1/3 U + 2/3 (U2 + dt L(U2)); 4 (TVD-RK2): U = 1/2 U + 1/2 (U1 + dt L(U1)).
+// flag and (debug) trace are left as they are.
+template <typename T>
+__host__ __device__ __forceinline__ void batch_stage_args(const SimDesc<T>& d, int stage, StageArgs<T>& A) {
+  A.nx = d.nx;
+  A.ny = d.ny;
+  A.nz = d.nz;
+  A.N = d.N;
+  for (int a = 0; a < 3; ++a) {
+    A.periodic[a] = d.periodic[a];
+    A.wall[a] = d.wall[a];
+    A.inv_h[a] = d.inv_h[a];
+  }
+  A.dt = d.dt;
+  A.rhs_only = 0;
+  A.zchunk = d.nz;
+  if (stage == 1) {
+    A.Us = d.U; A.Un = nullptr; A.out = d.U1; A.a = T(0); A.b = T(1);
+  } else if (stage == 2) {
+    A.Us = d.U1; A.Un = d.U; A.out = d.U2; A.a = T(0.75); A.b = T(0.25);
+  } else if (stage == 3) {
+    A.Us = d.U2; A.Un = d.U; A.out = d.U; A.a = T(1.0 / 3.0); A.b = T(2.0 / 3.0);
+  } else {
+    A.Us = d.U1; A.Un = d.U; A.out = d.U; A.a = T(0.5); A.b = T(0.5);
+  }
+}
+
+// Shared-memory elements of a tile: the plane ring and the face buffers.
+template <typename T, int DIM, bool VISC, int BX, int BY>
+constexpr size_t stage_smem_elems() {
+  using G = Geo<BX, BY, DIM, VISC>;
+  return (size_t)(G::RING * G::PLANE + 5 * G::NFX + 5 * G::NFY);
+}
 
 // The stage kernel.  blockDim.x == Geo::NT.
 //  * Single grid (work == null): one CTA per tile, the tile from blockIdx;
@@ -609,6 +755,33 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
     stage_kernel(const StageArgs<T> A0, const SimDesc<T>* __restrict__ sims, const WorkItem* __restrict__ work,
                  int nwork, int stage, const Gas<T> g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+#ifdef JF_DEBUG_BOUNDS
+  {
+    unsigned dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const size_t need = sizeof(T) * (stage_smem_elems<T, DIM, VISC, BX, BY>() + (SCH == SCH_NN ? NN_PARAMS : 0));
+    if (!JF_CHECK(dyn >= need, "JFDBG smem %u < %llu\n", dyn, (unsigned long long)need)) return;
+    if (work && threadIdx.x == 0)
+      for (int i = blockIdx.x; i < nwork; i += gridDim.x) {
+        const WorkItem w = work[i];
+        const SimDesc<T> d = sims[w.sim];
+        JF_CHECK(w.bx >= 0 && w.bx * BX < d.nx && w.by >= 0 && w.by * BY < d.ny,
+                 "JFDBG work item %d sim %d tile (%d,%d) grid %dx%d\n", i, w.sim, w.bx, w.by, d.nx, d.ny);
+      }
+  }
+  if (threadIdx.x == 0)
+    jf_trace(A0.trace, 0x50, blockIdx.x, (unsigned long long)nwork, (unsigned long long)sims,
+             (unsigned long long)work, (unsigned long long)stage, (unsigned long long)g.nn, 0);
+#endif
+  Gas<T> gk = g;
+  if constexpr (SCH == SCH_NN) {
+    // the Rusanov-NN parameters, after the stage buffers (the launch adds
+    // their size to the dynamic shared memory)
+    T* th = reinterpret_cast<T*>(smem_raw) + stage_smem_elems<T, DIM, VISC, BX, BY>();
+    for (int i = threadIdx.x; i < NN_PARAMS; i += blockDim.x) th[i] = __ldg(g.nn + i);
+    __syncthreads();
+    gk.nn = th;
+  }
   for (int item = blockIdx.x;; item += gridDim.x) {
     StageArgs<T> A = A0;
     int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
@@ -616,43 +789,30 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
       if (item >= nwork) break;
       const WorkItem w = work[item];
       const SimDesc<T> d = sims[w.sim];
-      A.nx = d.nx;
-      A.ny = d.ny;
-      A.nz = d.nz;
-      A.N = d.N;
-      A.periodic[0] = d.periodic[0];
-      A.periodic[1] = d.periodic[1];
-      A.periodic[2] = d.periodic[2];
-      A.inv_h[0] = d.inv_h[0];
-      A.inv_h[1] = d.inv_h[1];
-      A.inv_h[2] = d.inv_h[2];
-      A.dt = d.dt;
-      A.rhs_only = 0;
-      A.zchunk = d.nz;
-      const T third = T(1.0 / 3.0), two_thirds = T(2.0 / 3.0);
-      if (stage == 1) {         // U1 = U + dt L(U)  (every integrator)
-        A.Us = d.U; A.Un = nullptr; A.out = d.U1; A.a = T(0); A.b = T(1);
-      } else if (stage == 2) {  // TVD-RK3: U2 = 3/4 U + 1/4 (U1 + dt L(U1))
-        A.Us = d.U1; A.Un = d.U; A.out = d.U2; A.a = T(0.75); A.b = T(0.25);
-      } else if (stage == 3) {  // TVD-RK3: U = 1/3 U + 2/3 (U2 + dt L(U2))
-        A.Us = d.U2; A.Un = d.U; A.out = d.U; A.a = third; A.b = two_thirds;
-      } else {                  // TVD-RK2: U = 1/2 U + 1/2 (U1 + dt L(U1))
-        A.Us = d.U1; A.Un = d.U; A.out = d.U; A.a = T(0.5); A.b = T(0.5);
-      }
+      batch_stage_args(d, stage, A);
       bx = w.bx;
       by = w.by;
       bz = 0;
+#ifdef JF_DEBUG_BOUNDS
+      if (threadIdx.x == 0)
+        jf_trace(d.trace, 0x100 + stage, ((unsigned long long)item << 32) | (unsigned)w.sim,
+                 ((unsigned long long)(unsigned)w.bx << 32) | (unsigned)w.by, (unsigned long long)A.Us,
+                 (unsigned long long)A.out, (unsigned long long)A.Un, (unsigned long long)A.dt,
+                 ((unsigned long long)(unsigned)A.nx << 32) | (unsigned)A.ny);
+#endif
     } else if (item != (int)blockIdx.x) {
       break;
     }
-    stage_tile<T, DIM, VISC, BX, BY, SCH>(A, g, bx, by, bz, reinterpret_cast<T*>(smem_raw));
+    stage_tile<T, DIM, VISC, BX, BY, SCH>(A, gk, bx, by, bz, reinterpret_cast<T*>(smem_raw));
+#ifdef JF_DEBUG_BOUNDS
+    if (work && threadIdx.x == 0) jf_trace(sims[work[item].sim].trace, 0x200 + stage, item, 0, 0, 0, 0, 0, 0);
+#endif
   }
 }
 
 template <typename T, int DIM, bool VISC, int BX, int BY>
 constexpr size_t stage_smem_bytes() {
-  using G = Geo<BX, BY, DIM, VISC>;
-  return sizeof(T) * (size_t)(G::RING * G::PLANE + 5 * G::NFX + 5 * G::NFY);
+  return sizeof(T) * stage_smem_elems<T, DIM, VISC, BX, BY>();
 }
 
 }  // namespace jf

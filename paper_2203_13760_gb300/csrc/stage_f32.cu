@@ -49,6 +49,8 @@ const StageVariant<float>* stage_variants<float>(int* count) {
     v.insert(v.end(), gen, gen + ng);
     const StageVariant<float>* roe = roe_variants_f32(&ng);
     v.insert(v.end(), roe, roe + ng);
+    const StageVariant<float>* nn = nn_variants_f32(&ng);
+    v.insert(v.end(), nn, nn + ng);
     return v;
   }();
   *count = (int)table.size();

@@ -31,6 +31,8 @@ const StageVariant<double>* stage_variants<double>(int* count) {
     v.insert(v.end(), gen, gen + ng);
     const StageVariant<double>* roe = roe_variants_f64(&ng);
     v.insert(v.end(), roe, roe + ng);
+    const StageVariant<double>* nn = nn_variants_f64(&ng);
+    v.insert(v.end(), nn, nn + ng);
     return v;
   }();
   *count = (int)table.size();

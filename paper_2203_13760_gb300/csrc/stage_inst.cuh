@@ -4,17 +4,24 @@
 
 namespace jf {
 
+// Dynamic shared memory of a launch: the tile buffers, plus the Rusanov-NN
+// parameters in the kernels of that flux.
+template <typename T, int DIM, bool VISC, int BX, int BY, int SCH>
+constexpr size_t launch_smem() {
+  return stage_smem_bytes<T, DIM, VISC, BX, BY>() + (SCH == SCH_NN ? sizeof(T) * NN_PARAMS : 0);
+}
+
 // MINB: CTAs per SM the register allocation must allow (__launch_bounds__).
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t prepare_stage() {
-  constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
+  constexpr size_t smem = launch_smem<T, DIM, VISC, BX, BY, SCH>();
   return cudaFuncSetAttribute(stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t launch_stage(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s) {
-  constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
+  const size_t smem = launch_smem<T, DIM, VISC, BX, BY, SCH>();
   const dim3 grid((A.nx + BX - 1) / BX, DIM >= 2 ? (A.ny + BY - 1) / BY : 1,
                   DIM == 3 ? (A.nz + A.zchunk - 1) / A.zchunk : 1);
   stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, nullptr, nullptr, 0, 0,
@@ -24,19 +31,23 @@ cudaError_t launch_stage(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s)
 
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t prepare_batch(int* blocks_per_sm) {
-  constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
   auto k = stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)launch_smem<T, DIM, VISC, BX, BY, SCH>());
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, Geo<BX, BY, DIM, VISC>::NT, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, Geo<BX, BY, DIM, VISC>::NT,
+                                                       launch_smem<T, DIM, VISC, BX, BY, SCH>());
 }
 
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t launch_batch(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
                          int* flag, int grid, cudaStream_t s) {
-  constexpr size_t smem = stage_smem_bytes<T, DIM, VISC, BX, BY>();
+  const size_t smem = launch_smem<T, DIM, VISC, BX, BY, SCH>();
   StageArgs<T> A{};
   A.flag = flag;
+#ifdef JF_DEBUG_BOUNDS
+  A.trace = debug_trace_dev();
+#endif
   stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, sims, work, nwork,
                                                                                           stage, g);
   return cudaGetLastError();
@@ -44,7 +55,7 @@ cudaError_t launch_batch(const SimDesc<T>* sims, const WorkItem* work, int nwork
 
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 StageVariant<T> make_variant() {
-  StageVariant<T> v{DIM, VISC, BX, BY, stage_smem_bytes<T, DIM, VISC, BX, BY>(),
+  StageVariant<T> v{DIM, VISC, BX, BY, launch_smem<T, DIM, VISC, BX, BY, SCH>(),
                     &prepare_stage<T, DIM, VISC, BX, BY, MINB, SCH>, &launch_stage<T, DIM, VISC, BX, BY, MINB, SCH>,
                     nullptr, nullptr, Geo<BX, BY, DIM, VISC>::NT, SCH, MINB};
   if constexpr (DIM <= 2) {  // batches are built for 1D and 2D grids

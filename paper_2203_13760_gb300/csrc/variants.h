@@ -25,7 +25,7 @@ struct StageVariant {
   cudaError_t (*launch_batch)(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
                               int* flag, int grid, cudaStream_t s);
   int threads;
-  int scheme;    // SCH_DEFAULT, SCH_GENERAL (run-time Table 2 choice) or SCH_ROE
+  int scheme;    // SCH_DEFAULT, SCH_GENERAL (run-time Table 2 choice), SCH_ROE or SCH_NN
   int minb;      // CTAs per SM the register allocation was bounded for
 };
 
@@ -40,5 +40,7 @@ const StageVariant<float>* general_variants_f32(int* count);
 const StageVariant<double>* general_variants_f64(int* count);
 const StageVariant<float>* roe_variants_f32(int* count);
 const StageVariant<double>* roe_variants_f64(int* count);
+const StageVariant<float>* nn_variants_f32(int* count);
+const StageVariant<double>* nn_variants_f64(int* count);
 
 }  // namespace jf

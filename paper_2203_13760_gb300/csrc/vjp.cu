@@ -22,8 +22,8 @@ jf_status vjp_impl(jf_ctx* h, const void* Un, const double* dt, const void* lam_
   if (!L) { set_error(h, "jf_rk3_step_vjp: no adjoint kernel for this configuration"); return JF_ERR_UNSUPPORTED; }
   const jf_scheme& sc = h->scheme;
   if (sc.flux != JF_FLUX_HLLC || sc.recon != JF_WENO5_JS || sc.signal_speed != JF_EINFELDT ||
-      sc.integrator != JF_RK3) {
-    set_error(h, "jf_rk3_step_vjp: the adjoint is built for HLLC / Einfeldt / WENO5-JS / TVD-RK3 only");
+      sc.integrator != JF_RK3 || has_walls(h->grid)) {
+    set_error(h, "jf_rk3_step_vjp: the adjoint is built for HLLC / Einfeldt / WENO5-JS / TVD-RK3 without walls only");
     return JF_ERR_UNSUPPORTED;
   }
   for (int i = 0; i < 2; ++i)

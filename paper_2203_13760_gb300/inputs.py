@@ -23,6 +23,8 @@ import numpy as np
 DEFAULT_SEED = 2203
 PERIODIC = 0
 ZERO_GRADIENT = 1
+WALL = 2
+NN_HIDDEN = 32
 
 
 @dataclasses.dataclass
@@ -368,3 +370,20 @@ def random_blocks(n, seed: int = DEFAULT_SEED, bc=None, blocks: int = 3, gamma: 
         bc = (1,) * 6
     U = conservative(W[0], W[1], W[2], W[3], W[4], gamma)
     return Case("blocks", n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), tuple(bc), U, gamma=gamma)
+
+
+def nn_params(seed: int = DEFAULT_SEED, alpha: float = 2.0, spread: float = 0.1) -> np.ndarray:
+    """Seeded parameters of the Rusanov-NN network (Section 7.4) in the flat
+    layout W1 [32][4], b1, W2 [32][32], b2, W3 [32][32], b3, W4 [32], b4
+    (row-major, outputs by inputs): Gaussian weights of variance 2 / fan-in
+    (He initialisation) and biases of standard deviation 0.1 for the hidden
+    layers, output weights of standard deviation spread / sqrt(32), and output
+    bias ln(alpha), so that the dissipation starts near alpha.  Draw order:
+    W1, b1, W2, b2, W3, b3, W4."""
+    rng = np.random.default_rng(seed)
+    H = NN_HIDDEN
+    parts = [rng.normal(0.0, math.sqrt(2.0 / 4), (H, 4)), rng.normal(0.0, 0.1, H),
+             rng.normal(0.0, math.sqrt(2.0 / H), (H, H)), rng.normal(0.0, 0.1, H),
+             rng.normal(0.0, math.sqrt(2.0 / H), (H, H)), rng.normal(0.0, 0.1, H),
+             rng.normal(0.0, spread / math.sqrt(H), H), np.array([math.log(alpha)])]
+    return np.concatenate([a.ravel() for a in parts]).astype(np.float64)

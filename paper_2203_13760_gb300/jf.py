@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libjf.so")
 
 JF_OK, JF_ERR_ARG, JF_ERR_CUDA, JF_ERR_OOM, JF_ERR_NONPHYSICAL, JF_ERR_TIMEOUT, JF_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 JF_F32, JF_F64 = 0, 1
-PERIODIC, ZERO_GRADIENT = 0, 1
+PERIODIC, ZERO_GRADIENT, WALL = 0, 1, 2
 _STATUS = {0: "JF_OK", -1: "JF_ERR_ARG", -2: "JF_ERR_CUDA", -3: "JF_ERR_OOM", -4: "JF_ERR_NONPHYSICAL",
            -5: "JF_ERR_TIMEOUT", -6: "JF_ERR_UNSUPPORTED"}
 
@@ -47,8 +47,11 @@ class Scheme(ctypes.Structure):
 
 
 # scheme options of include/jf.h (0: the default configuration)
-FLUX = {"hllc": 0, "hll": 1, "rusanov": 2, "roe": 3}
-RECON = {"weno5-js": 0, "weno5-z": 1}
+FLUX = {"hllc": 0, "hll": 1, "rusanov": 2, "roe": 3, "rusanov-nn": 4}
+RECON = {"weno5-js": 0, "weno5-z": 1, "weno3-js": 2}
+# parameters of the Rusanov-NN network (JF_NN_PARAMS): W1 [32][4], b1, W2 [32][32], b2, W3 [32][32], b3, W4 [32], b4
+NN_HIDDEN = 32
+NN_PARAMS = NN_HIDDEN * 4 + NN_HIDDEN + 2 * (NN_HIDDEN * NN_HIDDEN + NN_HIDDEN) + NN_HIDDEN + 1
 SPEEDS = {"einfeldt": 0, "davis": 1, "toro": 2}
 INTEGRATOR = {"rk3": 0, "rk2": 1, "euler": 2}
 
@@ -70,6 +73,7 @@ SIGNATURES = {
     "jf_batch_step": (_I, [_VP, ctypes.POINTER(_VP), _I, _VP, _VP]),
     "jf_batch_feed_forward": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP, _VP]),
     "jf_set_variant": (_I, [_VP, _I]),
+    "jf_set_nn": (_I, [_VP, _VP, _I]),
     "jf_variant_info": (_I, [_VP, _I, ctypes.c_char_p, _I]),
     "jf_status_sync": (_I, [_VP]),
     "jf_last_error": (ctypes.c_char_p, [_VP]),
@@ -114,6 +118,17 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _set_nn(obj, theta):
+    """jf_set_nn for a Solver or Batch; keeps theta referenced while the
+    handle may read it."""
+    import torch
+    if (not isinstance(theta, torch.Tensor) or not theta.is_cuda or theta.dtype != obj.dtype
+            or not theta.is_contiguous() or theta.numel() != NN_PARAMS):
+        raise ValueError(f"theta must be a contiguous CUDA {obj.dtype} tensor of {NN_PARAMS} values")
+    _check(lib().jf_set_nn(obj.h, _ptr(theta), NN_PARAMS), obj.h)
+    obj._nn = theta
+
+
 def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1)) -> Grid:
     n = tuple(int(x) for x in n) + (1,) * (3 - len(n))
     g = Grid()
@@ -140,7 +155,7 @@ class Solver:
 
     def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=(1, 1, 1, 1, 1, 1), gamma=1.4, R=1.0,
                  mu=0.0, Pr=0.72, dtype="f32", eps=1e-6, cfl=0.5, viscous=False, heat=False, safe=False,
-                 flux="hllc", recon="weno5-js", speeds="einfeldt", integrator="rk3"):
+                 flux="hllc", recon="weno5-js", speeds="einfeldt", integrator="rk3", nn=None):
         import torch
         self.grid = make_grid(n, lo, hi, bc)
         self.gas = GasParams(float(gamma), float(R), float(mu), float(Pr))
@@ -151,6 +166,14 @@ class Solver:
         _check(lib().jf_init(ctypes.byref(self.grid), ctypes.byref(self.gas), ctypes.byref(self.scheme),
                              ctypes.byref(h)))
         self.h = h
+        self._nn = None
+        if nn is not None:
+            self.set_nn(nn)
+
+    def set_nn(self, theta):
+        """Rusanov-NN parameters (jf_set_nn): a CUDA tensor of NN_PARAMS values
+        of the solver's dtype, read at every launch (update it in place)."""
+        _set_nn(self, theta)
 
     @classmethod
     def from_case(cls, case, dtype="f32", **over):
@@ -253,7 +276,7 @@ class Batch:
 
     def __init__(self, grids, gamma=1.4, R=1.0, mu=0.0, Pr=0.72, dtype="f32", eps=1e-6, cfl=0.5,
                  viscous=False, heat=False, safe=False, flux="hllc", recon="weno5-js", speeds="einfeldt",
-                 integrator="rk3"):
+                 integrator="rk3", nn=None):
         import torch
         self.grids = (Grid * len(grids))(*[make_grid(**g) if isinstance(g, dict) else g for g in grids])
         self.nsim = len(grids)
@@ -264,6 +287,16 @@ class Batch:
         _check(lib().jf_batch_create(self.grids, self.nsim, ctypes.byref(self.gas), ctypes.byref(self.scheme),
                                      ctypes.byref(h)))
         self.h = h
+        self._nn = None
+        if nn is not None:
+            self.set_nn(nn)
+
+    def set_nn(self, theta):
+        """Rusanov-NN parameters of every simulation (jf_set_nn; also given to
+        the cached single-grid solvers)."""
+        _set_nn(self, theta)
+        for s in self.__dict__.get("_solvers", {}).values():
+            s.set_nn(theta)
 
     def solver(self, i):
         """A single-grid Solver with simulation i's grid and this batch's gas and
@@ -276,7 +309,7 @@ class Batch:
             cache[i] = Solver((g.nx, g.ny, g.nz), tuple(g.lo), tuple(g.hi), tuple(g.bc), gas.gamma, gas.R, gas.mu,
                               gas.Pr, "f32" if s.dtype == JF_F32 else "f64", s.weno_eps, s.cfl, bool(s.viscous),
                               bool(s.heat), bool(s.safe_recon), names[0][s.flux], names[1][s.recon],
-                              names[2][s.signal_speed], names[3][s.integrator])
+                              names[2][s.signal_speed], names[3][s.integrator], nn=self._nn)
         return cache[i]
 
     def _check_fields(self, Us):

@@ -58,8 +58,12 @@ def test_bad_arguments_rejected_on_host(libjf):
     visc = libjf.make_scheme("f32", viscous=True)  # viscous with mu = 0
     assert L.jf_init(ctypes.byref(grid), ctypes.byref(gas), ctypes.byref(visc), ctypes.byref(h)) == libjf.JF_ERR_ARG
     assert L.jf_init(None, None, None, None) == libjf.JF_ERR_ARG
-    # scheme options out of range (flux 0..3, recon 0..1, speeds and integrators 0..2)
-    for field, value in (("flux", 4), ("recon", 2), ("signal_speed", 3), ("integrator", -1)):
+    # boundary codes 0..2 (periodic, zero gradient, slip wall)
+    for code in (3, -1):
+        g = libjf.make_grid((16, 1, 1), bc=(code, 1, 1, 1, 1, 1))
+        assert L.jf_init(ctypes.byref(g), ctypes.byref(gas), ctypes.byref(sch), ctypes.byref(h)) == libjf.JF_ERR_ARG
+    # scheme options out of range (flux 0..4, recon 0..2, speeds and integrators 0..2)
+    for field, value in (("flux", 5), ("recon", 3), ("signal_speed", 3), ("integrator", -1)):
         bad = libjf.make_scheme("f32")
         setattr(bad, field, value)
         assert L.jf_init(ctypes.byref(grid), ctypes.byref(gas), ctypes.byref(bad), ctypes.byref(h)) == libjf.JF_ERR_ARG
@@ -69,3 +73,17 @@ def test_bad_arguments_rejected_on_host(libjf):
     assert L.jf_rhs(None, None, None, None) == libjf.JF_ERR_ARG
     assert L.jf_destroy(None) == libjf.JF_OK
     assert L.jf_version().startswith(b"jf")
+    assert L.jf_set_nn(None, None, 0) == libjf.JF_ERR_ARG
+    # the Rusanov-NN flux runs only through a handle that holds parameters
+    nn = libjf.make_scheme("f32", flux="rusanov-nn")
+    U = ctypes.c_void_p(16)
+    assert L.jf_rk3_step_noalloc(ctypes.byref(grid), ctypes.byref(gas), ctypes.byref(nn), U, None, None,
+                                 None) == libjf.JF_ERR_UNSUPPORTED
+    assert b"jf_set_nn" in L.jf_last_error(None)
+
+
+def test_network_size_matches_the_header(libjf):
+    import oracle
+    text = open(os.path.join(ROOT, "include", "jf.h")).read()
+    assert "#define JF_NN_HIDDEN 32" in text
+    assert libjf.NN_PARAMS == oracle.NN_PARAMS == 2305

@@ -184,11 +184,14 @@ def test_deterministic():
 @pytest.mark.parametrize("viscous", [True, False])
 def test_variants_agree(orc, dtype, viscous):
     """Every launch variant (tile shape / z chunk / CTAs per SM), on a grid
-    that is ragged for every tile shape: the z chunks of one tile shape give
-    the same bits; different tile shapes are separate instantiations of the
-    same expressions, whose multiply-adds the compiler may contract
-    differently, so they agree to rounding (FP64 <= 1e-13, FP32 <= 2e-6 of
-    the flux scale) and every one meets the oracle bar."""
+    that is ragged for every tile shape, agrees with the default to rounding
+    (FP64 <= 1e-13, FP32 <= 2e-6 of the flux scale) and every one meets the
+    oracle bar.  Different tile shapes are separate instantiations of the
+    same expressions, and within one tile shape the lower z face of a chunk's
+    first plane is computed by the chunk prologue, a second inlined copy of
+    the face code: the compiler may contract the multiply-adds of the copies
+    differently, so neither is bitwise.  A repeated launch of one variant is
+    bitwise (test_deterministic)."""
     case = inputs.random_smooth((40, 29, 23), seed=12, viscous=viscous, mu=0.01)
     c = orc.config(**case.params())
     want = orc.rhs(c, case.U)
@@ -204,8 +207,6 @@ def test_variants_agree(orc, dtype, viscous):
         s.set_variant(v)
         got = s.rhs(U)
         s.sync()
-        if names[v].split(" zchunk")[0] == names[0].split(" zchunk")[0]:
-            assert torch.equal(ref, got), names[v]
         assert rate_err(got.double().cpu().numpy(), ref_np, U64, rate) <= tol, names[v]
         if dtype == "f64":
             assert rate_err(got.cpu().numpy(), want, case.U, rate) <= 1e-12, names[v]
