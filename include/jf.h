@@ -121,9 +121,12 @@ typedef struct {
  *   integrator    JF_RK3 / JF_RK2 (TVD Runge-Kutta of Gottlieb & Shu 1998,
  *                 Shu-Osher form) or JF_EULER, used by jf_rk3_step,
  *                 jf_rk3_run and jf_batch_step (the names keep the default).
- * The adjoint (jf_rk3_step_vjp) is built for the default configuration only
- * and returns JF_ERR_UNSUPPORTED otherwise.  An option out of range is
- * JF_ERR_ARG. */
+ * The adjoint (jf_rk3_step_vjp) covers the default configuration (viscous
+ * and heat fluxes included, no walls) with a tiled kernel, and inviscid runs
+ * with any boundary condition, WENO5-JS or WENO3-JS, HLLC with Einfeldt
+ * speeds or Rusanov-NN, and any of the three integrators with a per-face
+ * kernel; other configurations return JF_ERR_UNSUPPORTED.  An option out of
+ * range is JF_ERR_ARG. */
 typedef struct {
   int dtype;
   double weno_eps;
@@ -186,12 +189,26 @@ jf_status jf_rk3_run(jf_handle h, void* U_inout, int nsteps, const double* dt_de
 /* Adjoint of one fixed-dt RK3 step (vector-Jacobian product, Section 7.2:
  * gradients backpropagated through the solver):
  *   lam_in = (dU^{n+1} / dU^n)^T lam_out,
- * with U^{n+1} = RK3(U^n; dt) as in jf_rk3_step and dt held fixed (not
+ * with U^{n+1} = RK3(U^n; dt) as in jf_rk3_step (the scheme's integrator:
+ * TVD-RK3, TVD-RK2 or Euler) and dt held fixed (not
  * differentiated).  Un is the state at the start of the step (not modified);
  * the step is recomputed inside.  lam_out and lam_in are device arrays shaped
  * like U; they may not overlap.  dt_dev must not be NULL. */
 jf_status jf_rk3_step_vjp(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out, void* lam_in,
                           void* stream);
+
+/* jf_rk3_step_vjp for a handle whose flux is JF_FLUX_RUSANOV_NN, adding the
+ * gradient of the step with respect to the network parameters (Section 7.4:
+ * the learned dissipation trained through the solver):
+ *   lam_in = (dU^{n+1}/dU^n)^T lam_out,  theta_bar += (dU^{n+1}/dtheta)^T lam_out,
+ * with dt fixed.  theta_bar is a device array of JF_NN_PARAMS elements of the
+ * handle's dtype in the layout of jf_set_nn; the call adds to it (the caller
+ * zeroes it).  Supported: inviscid grids with any boundary condition,
+ * WENO5-JS or WENO3-JS, and the scheme's integrator (TVD-RK3, TVD-RK2 or
+ * Euler).  The contributions are summed with atomics, so the last bits may
+ * vary from run to run. */
+jf_status jf_rk3_step_vjp_params(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out, void* lam_in,
+                                 void* theta_bar, void* stream);
 
 /* Loss of the adjoint workload: *loss_dev = sum_cells (rho - rho_target)^2 dV
  * (FP64 accumulation) and, if seed != NULL, seed = dloss/dU (the cotangent

@@ -113,6 +113,13 @@ void release_all(jf_ctx* h);
 unsigned long long* debug_trace_dev();
 #endif
 
+// adjoint of the run-time schemes (vjp_gen.cu)
+bool general_vjp_supported(const jf_ctx* h, std::string* why);
+long long general_face_count(const jf_ctx* h);
+template <typename T>
+jf_status general_vjp(jf_ctx* h, const void* Un, const double* dt, const void* lam_out, void* lam_in, void* theta_bar,
+                      cudaStream_t s);
+
 // batch (batch.cu)
 jf_status batch_set_variant(jf_ctx* h, int variant);
 int batch_variant_info(jf_ctx* h, int variant, char* buf, int len);

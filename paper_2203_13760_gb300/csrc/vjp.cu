@@ -18,14 +18,19 @@ template <typename T>
 jf_status vjp_impl(jf_ctx* h, const void* Un, const double* dt, const void* lam_out, void* lam_in,
                    cudaStream_t s) {
   const bool visc = dissipative(h->gas, h->scheme);
-  VjpLaunch<T> L = vjp_launcher<T>(h->dim, visc);
-  if (!L) { set_error(h, "jf_rk3_step_vjp: no adjoint kernel for this configuration"); return JF_ERR_UNSUPPORTED; }
   const jf_scheme& sc = h->scheme;
   if (sc.flux != JF_FLUX_HLLC || sc.recon != JF_WENO5_JS || sc.signal_speed != JF_EINFELDT ||
       sc.integrator != JF_RK3 || has_walls(h->grid)) {
-    set_error(h, "jf_rk3_step_vjp: the adjoint is built for HLLC / Einfeldt / WENO5-JS / TVD-RK3 without walls only");
-    return JF_ERR_UNSUPPORTED;
+    // the run-time schemes: the per-face adjoint of vjp_gen.cu
+    std::string why;
+    if (!general_vjp_supported(h, &why)) {
+      set_error(h, "jf_rk3_step_vjp: " + why);
+      return JF_ERR_UNSUPPORTED;
+    }
+    return general_vjp<T>(h, Un, dt, lam_out, lam_in, nullptr, s);
   }
+  VjpLaunch<T> L = vjp_launcher<T>(h->dim, visc);
+  if (!L) { set_error(h, "jf_rk3_step_vjp: no adjoint kernel for this configuration"); return JF_ERR_UNSUPPORTED; }
   for (int i = 0; i < 2; ++i)
     if (!h->adj[i]) {
       cudaError_t e = cudaMalloc(&h->adj[i], 5 * h->N * sizeof(T));
@@ -86,4 +91,24 @@ extern "C" jf_status jf_rk3_step_vjp(jf_handle h, const void* Un, const double* 
   return h->scheme.dtype == JF_F32
              ? vjp_impl<float>(h, Un, dt_dev, lam_out, lam_in, (cudaStream_t)stream)
              : vjp_impl<double>(h, Un, dt_dev, lam_out, lam_in, (cudaStream_t)stream);
+}
+
+extern "C" jf_status jf_rk3_step_vjp_params(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out,
+                                            void* lam_in, void* theta_bar, void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_rk3_step_vjp_params: not a single-grid handle"); return JF_ERR_ARG; }
+  if (h->scheme.flux != JF_FLUX_RUSANOV_NN) {
+    set_error(h, "jf_rk3_step_vjp_params: the scheme's flux is not JF_FLUX_RUSANOV_NN");
+    return JF_ERR_ARG;
+  }
+  if (!Un || !dt_dev || !lam_out || !lam_in || !theta_bar || !aligned16(Un) || !aligned16(lam_out) ||
+      !aligned16(lam_in) || lam_in == lam_out || lam_in == Un || ((uintptr_t)theta_bar % h->esize) != 0) {
+    set_error(h, "jf_rk3_step_vjp_params: bad arguments (dt_dev and theta_bar are required; lam_in must differ "
+                 "from lam_out and Un)");
+    return JF_ERR_ARG;
+  }
+  std::string why;
+  if (!general_vjp_supported(h, &why)) { set_error(h, "jf_rk3_step_vjp_params: " + why); return JF_ERR_UNSUPPORTED; }
+  return h->scheme.dtype == JF_F32
+             ? general_vjp<float>(h, Un, dt_dev, lam_out, lam_in, theta_bar, (cudaStream_t)stream)
+             : general_vjp<double>(h, Un, dt_dev, lam_out, lam_in, theta_bar, (cudaStream_t)stream);
 }

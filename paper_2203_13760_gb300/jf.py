@@ -67,6 +67,7 @@ SIGNATURES = {
     "jf_stage": (_I, [_VP, _VP, _VP, _VP, _D, _D, _VP, _VP]),
     "jf_rk3_run": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
     "jf_rk3_step_vjp": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jf_rk3_step_vjp_params": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_loss_density_l2": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_batch_create": (_I, [ctypes.POINTER(Grid), _I, ctypes.POINTER(GasParams), ctypes.POINTER(Scheme),
                              ctypes.POINTER(_VP)]),
@@ -231,6 +232,21 @@ class Solver:
         _check(lib().jf_rk3_step_vjp(self.h, self._field(Un, "Un"), _ptr(dt), self._field(lam_out, "lam_out"),
                                      self._field(lam_in, "lam_in"), _stream()), self.h)
         return lam_in
+
+    def rk3_step_vjp_params(self, Un, dt, lam_out, lam_in=None, theta_bar=None):
+        """Adjoint of one step of the Rusanov-NN scheme: returns (lam_in,
+        theta_bar) with theta_bar += (dU^{n+1}/dtheta)^T lam_out (a zero
+        tensor of NN_PARAMS values is made when theta_bar is None)."""
+        import torch
+        lam_in = self.empty() if lam_in is None else lam_in
+        if theta_bar is None:
+            theta_bar = torch.zeros(NN_PARAMS, dtype=self.dtype, device="cuda")
+        if (theta_bar.dtype != self.dtype or not theta_bar.is_cuda or not theta_bar.is_contiguous()
+                or theta_bar.numel() != NN_PARAMS):
+            raise ValueError(f"theta_bar must be a contiguous CUDA {self.dtype} tensor of {NN_PARAMS} values")
+        _check(lib().jf_rk3_step_vjp_params(self.h, self._field(Un, "Un"), _ptr(dt), self._field(lam_out, "lam_out"),
+                                            self._field(lam_in, "lam_in"), _ptr(theta_bar), _stream()), self.h)
+        return lam_in, theta_bar
 
     def loss_density_l2(self, U, target, loss=None, seed=None, want_seed=True):
         import torch

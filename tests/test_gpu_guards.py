@@ -145,3 +145,23 @@ def test_roe_blow_up_is_reported_like_the_oracle(orc):
     with pytest.raises(jf.JFError) as e:
         s.sync()
     assert e.value.status == jf.JF_ERR_NONPHYSICAL
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n", [(37, 1, 1), (37, 19, 1), (13, 11, 9)])
+def test_per_face_adjoint_stays_in_bounds(dtype, n):
+    """The per-face adjoint (walls, WENO3-JS, Rusanov-NN, TVD-RK2) with its
+    parameter gradient: lam_in and theta_bar inside canary margins."""
+    W = inputs.WALL
+    case = inputs.random_smooth(n, seed=3, bc=(W, W, W, 1, W, W))
+    case.flux, case.recon, case.integrator = "rusanov-nn", "weno3-js", "rk2"
+    t = torch.float32 if dtype == "f32" else torch.float64
+    theta = torch.tensor(inputs.nn_params(seed=5), dtype=t, device="cuda")
+    s = jf.Solver.from_case(case, dtype=dtype, nn=theta)
+    U0 = torch.tensor(case.U, dtype=t, device="cuda")
+    lam_in = Guarded(tuple(U0.shape), t)
+    tb = Guarded((jf.NN_PARAMS,), t, torch.zeros(jf.NN_PARAMS, dtype=t, device="cuda"))
+    s.rk3_step_vjp_params(U0, s.scalar(1e-4), torch.ones_like(U0), lam_in.t, tb.t)
+    lam_in.check()
+    tb.check()
+    s.sync()
