@@ -210,6 +210,23 @@ jf_status jf_rk3_step_vjp(jf_handle h, const void* Un, const double* dt_dev, con
 jf_status jf_rk3_step_vjp_params(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out, void* lam_in,
                                  void* theta_bar, void* stream);
 
+/* Adjoint of one fixed-dt step of every simulation of a batch in the same
+ * launches (the per-face adjoint of jf_rk3_step_vjp's run-time schemes;
+ * inviscid, WENO5-JS or WENO3-JS, HLLC with Einfeldt speeds or Rusanov-NN,
+ * the scheme's integrator):
+ *   lam_in[s] = (dU_s^{n+1}/dU_s^n)^T lam_out[s] + add[s],
+ *   theta_bar += sum_s (dU_s^{n+1}/dtheta)^T lam_out[s]   (Rusanov-NN, if theta_bar != NULL).
+ * Un_ptrs, lam_out_ptrs, lam_in_ptrs: HOST arrays of nsim device pointers
+ * (the states at the start of the step, not modified; lam_in may not alias
+ * lam_out or Un); add_ptrs: NULL or a HOST array of nsim device pointers
+ * (NULL entries add nothing), the cotangent of a loss at U^n in a trajectory
+ * sweep; dt_dev: nsim FP64 device values.  The step states are recomputed
+ * inside; the adjoint buffers are allocated at the first call.  theta_bar as
+ * in jf_rk3_step_vjp_params.  Paper: Section 7.4 (training over batches of
+ * trajectory windows). */
+jf_status jf_batch_step_vjp(jf_handle batch, void* const* Un_ptrs, const double* dt_dev, void* const* lam_out_ptrs,
+                            void* const* lam_in_ptrs, void* const* add_ptrs, void* theta_bar, void* stream);
+
 /* Loss of the adjoint workload: *loss_dev = sum_cells (rho - rho_target)^2 dV
  * (FP64 accumulation) and, if seed != NULL, seed = dloss/dU (the cotangent
  * that starts the backward pass: 2 (rho - rho_target) dV in the density

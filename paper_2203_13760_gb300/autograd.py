@@ -12,11 +12,13 @@ a fixed step).
 ``density_l2(solver, U, target)``
                               sum_cells (rho - target)^2 dV (jf_loss_density_l2)
                               with its gradient.
-``feed_forward(batch, U0s, n, dt)``
+``feed_forward(batch, U0s, n, dt, theta=None)``
                               Section 4.5: the trajectories of a batch of
                               (uneven) simulations, differentiable w.r.t. the
                               initial states (reverse sweep on the stored
-                              trajectory with jf_rk3_step_vjp).
+                              trajectory with jf_rk3_step_vjp) and, for the
+                              Rusanov-NN flux of Section 7.4, w.r.t. the
+                              network parameters theta (jf_rk3_step_vjp_params).
 ``trajectory_mse(trajs, refs)``
                               Section 7.2: 1/N_T sum_i MSE(U^i, U^i_ref).
 
@@ -108,12 +110,17 @@ class _FeedForward(torch.autograd.Function):
     """Trajectories of a batch (jf_batch_feed_forward) with the reverse sweep
     of each simulation: for U^{t+1} = S(U^t), dL/dU^t = g_t + J_t^T dL/dU^{t+1},
     J_t^T applied by jf_rk3_step_vjp of a single-grid solver of the same grid
-    and scheme, on the stored trajectory (no recomputation of states)."""
+    and scheme, on the stored trajectory (no recomputation of states).  With
+    the network parameters theta (the Rusanov-NN flux), the same sweep runs
+    jf_rk3_step_vjp_params, which also sums dL/dtheta over the steps and
+    simulations."""
 
     @staticmethod
-    def forward(ctx, batch, nsteps, dt, *U0s):
+    def forward(ctx, batch, nsteps, dt, theta, *U0s):
+        if theta is not None and (batch._nn is None or batch._nn.data_ptr() != theta.data_ptr()):
+            raise ValueError("theta must be the tensor the batch holds (Batch.set_nn)")
         trajs = batch.feed_forward([U.detach().contiguous() for U in U0s], nsteps, dt)
-        ctx.batch, ctx.nsteps = batch, nsteps
+        ctx.batch, ctx.nsteps, ctx.with_theta = batch, nsteps, theta is not None
         ctx.dts = [float(dt)] * batch.nsim if not hasattr(dt, "__len__") else [float(x) for x in dt]
         ctx.save_for_backward(*trajs)
         return tuple(trajs)
@@ -121,6 +128,17 @@ class _FeedForward(torch.autograd.Function):
     @staticmethod
     def backward(ctx, *grads):
         trajs = ctx.saved_tensors
+        theta_bar = torch.zeros_like(ctx.batch._nn) if ctx.with_theta else None
+        if ctx.batch.supports_step_vjp():
+            # every simulation of the batch in the same launches, one call per step
+            g = [torch.zeros_like(tr) if gi is None else gi.contiguous() for tr, gi in zip(trajs, grads)]
+            dt = torch.tensor(ctx.dts, dtype=torch.float64, device=trajs[0].device)
+            lam = [gi[ctx.nsteps].clone() for gi in g]
+            nxt = [torch.empty_like(x) for x in lam]
+            for t in reversed(range(ctx.nsteps)):
+                ctx.batch.step_vjp([tr[t] for tr in trajs], dt, lam, nxt, [gi[t] for gi in g], theta_bar)
+                lam, nxt = nxt, lam
+            return (None, None, None, theta_bar, *lam)
         out = []
         for i, (traj, g) in enumerate(zip(trajs, grads)):
             solver = ctx.batch.solver(i)
@@ -128,17 +146,22 @@ class _FeedForward(torch.autograd.Function):
             g = torch.zeros_like(traj) if g is None else g.contiguous()
             lam = g[ctx.nsteps].clone()
             for t in reversed(range(ctx.nsteps)):
-                lam = solver.rk3_step_vjp(traj[t], dt, lam)
+                if theta_bar is not None:
+                    lam, _ = solver.rk3_step_vjp_params(traj[t], dt, lam, theta_bar=theta_bar)
+                else:
+                    lam = solver.rk3_step_vjp(traj[t], dt, lam)
                 lam += g[t]
             out.append(lam)
-        return (None, None, None, *out)
+        return (None, None, None, theta_bar, *out)
 
 
-def feed_forward(batch, U0s, nsteps, dt):
+def feed_forward(batch, U0s, nsteps, dt, theta=None):
     """Section 4.5 feed_forward, differentiable: per simulation of ``batch``
     (a jf.Batch; sizes may differ) the trajectory (nsteps + 1, 5, nz, ny, nx)
-    of fixed-dt steps from U0s[i]; gradients flow back to every U0s[i]."""
-    return list(_FeedForward.apply(batch, int(nsteps), dt, *U0s))
+    of fixed-dt steps from U0s[i]; gradients flow back to every U0s[i] and,
+    when given, to the Rusanov-NN parameters theta (the tensor the batch holds
+    through Batch.set_nn, updated in place by an optimizer)."""
+    return list(_FeedForward.apply(batch, int(nsteps), dt, theta, *U0s))
 
 
 def trajectory_mse(trajs, refs):

@@ -119,6 +119,9 @@ long long general_face_count(const jf_ctx* h);
 template <typename T>
 jf_status general_vjp(jf_ctx* h, const void* Un, const double* dt, const void* lam_out, void* lam_in, void* theta_bar,
                       cudaStream_t s);
+template <typename T>
+jf_status batch_general_vjp(jf_ctx* h, void* const* Un, const double* dt, void* const* lam_out, void* const* lam_in,
+                            void* const* add, void* theta_bar, cudaStream_t s);
 
 // batch (batch.cu)
 jf_status batch_set_variant(jf_ctx* h, int variant);

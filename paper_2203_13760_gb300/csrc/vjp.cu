@@ -112,3 +112,34 @@ extern "C" jf_status jf_rk3_step_vjp_params(jf_handle h, const void* Un, const d
              ? general_vjp<float>(h, Un, dt_dev, lam_out, lam_in, theta_bar, (cudaStream_t)stream)
              : general_vjp<double>(h, Un, dt_dev, lam_out, lam_in, theta_bar, (cudaStream_t)stream);
 }
+
+extern "C" jf_status jf_batch_step_vjp(jf_handle h, void* const* Un_ptrs, const double* dt_dev,
+                                       void* const* lam_out_ptrs, void* const* lam_in_ptrs, void* const* add_ptrs,
+                                       void* theta_bar, void* stream) {
+  if (!h || h->kind != 1) { set_error(h, "jf_batch_step_vjp: not a batch handle"); return JF_ERR_ARG; }
+  if (!Un_ptrs || !dt_dev || !lam_out_ptrs || !lam_in_ptrs) {
+    set_error(h, "jf_batch_step_vjp: null argument");
+    return JF_ERR_ARG;
+  }
+  for (int s = 0; s < h->nsim; ++s) {
+    const void* a = add_ptrs ? add_ptrs[s] : nullptr;
+    if (!Un_ptrs[s] || !lam_out_ptrs[s] || !lam_in_ptrs[s] || !aligned16(Un_ptrs[s]) || !aligned16(lam_out_ptrs[s]) ||
+        !aligned16(lam_in_ptrs[s]) || (a && !aligned16(a)) || lam_in_ptrs[s] == lam_out_ptrs[s] ||
+        lam_in_ptrs[s] == Un_ptrs[s]) {
+      set_error(h, "jf_batch_step_vjp: every Un / lam_out / lam_in must be a 16-byte aligned device array, and "
+                   "lam_in must differ from lam_out and Un");
+      return JF_ERR_ARG;
+    }
+  }
+  if (theta_bar && (h->scheme.flux != JF_FLUX_RUSANOV_NN || ((uintptr_t)theta_bar % h->esize) != 0)) {
+    set_error(h, "jf_batch_step_vjp: theta_bar needs the JF_FLUX_RUSANOV_NN flux (and element alignment)");
+    return JF_ERR_ARG;
+  }
+  std::string why;
+  if (!general_vjp_supported(h, &why)) { set_error(h, "jf_batch_step_vjp: " + why); return JF_ERR_UNSUPPORTED; }
+  return h->scheme.dtype == JF_F32
+             ? batch_general_vjp<float>(h, Un_ptrs, dt_dev, lam_out_ptrs, lam_in_ptrs, add_ptrs, theta_bar,
+                                        (cudaStream_t)stream)
+             : batch_general_vjp<double>(h, Un_ptrs, dt_dev, lam_out_ptrs, lam_in_ptrs, add_ptrs, theta_bar,
+                                         (cudaStream_t)stream);
+}

@@ -1,13 +1,17 @@
 // Adjoint of one fixed-dt step for the run-time schemes (vjp_gen.cuh): slip
 // walls, WENO5-JS / WENO3-JS, HLLC (Einfeldt speeds) or the Rusanov-NN flux,
-// TVD-RK3, TVD-RK2 or Euler, inviscid.  With V(U, m) = m + dt J(U)^T m:
+// TVD-RK3, TVD-RK2 or Euler, inviscid; for one grid (jf_rk3_step_vjp,
+// jf_rk3_step_vjp_params) or every simulation of a batch in the same launches
+// (jf_batch_step_vjp).  With V(U, m) = m + dt J(U)^T m and l = lam_out:
 //   TVD-RK3 (as vjp.cu): l2 = V(U2, 2/3 l); l1 = V(U1, 1/4 l2); ln = 1/3 l + 3/4 l2 + V(Un, l1);
 //   TVD-RK2 (U1 = Un + dt L(Un); U^{n+1} = 1/2 Un + 1/2 (U1 + dt L(U1))):
 //            l1 = V(U1, 1/2 l); ln = 1/2 l + V(Un, l1);
-//   Euler:   ln = V(Un, l).
-// With the Rusanov-NN flux every V also adds its parameter gradient
+//   Euler:   ln = V(Un, l);
+// plus an optional addend of ln (the loss cotangent at U^n in a trajectory
+// sweep).  With the Rusanov-NN flux every V also adds its parameter gradient
 // sum_f abar_f d alpha_f / d theta to theta_bar (when given).
 #include <cstring>
+#include <vector>
 
 #include "jf_internal.h"
 #include "vjp_gen.cuh"
@@ -16,8 +20,32 @@ namespace jf {
 
 namespace {
 
+// Geometry of one grid for the per-face adjoint (pointers and factors unset).
+template <typename T>
+GVjpArgs<T> grid_args(const jf_grid& grid, int dim) {
+  GVjpArgs<T> A;
+  std::memset(&A, 0, sizeof A);
+  const int n[3] = {grid.nx, grid.ny, grid.nz};
+  for (int a = 0; a < 3; ++a) {
+    A.n[a] = n[a];
+    A.periodic[a] = grid.bc[2 * a] == JF_BC_PERIODIC;
+    A.wall[a] = (grid.bc[2 * a] == JF_BC_WALL ? 1 : 0) | (grid.bc[2 * a + 1] == JF_BC_WALL ? 2 : 0);
+    A.inv_h[a] = (T)(1.0 / spacing(grid, a));
+  }
+  A.N = (long long)n[0] * n[1] * n[2];
+  for (int a = 0; a < dim; ++a) {
+    long long c = 1;
+    for (int e = 0; e < 3; ++e) c *= e == a ? (long long)n[e] + (A.periodic[a] ? 0 : 1) : n[e];
+    A.nface[a] = c;
+  }
+  return A;
+}
+
+template <typename T>
+long long faces_of(const GVjpArgs<T>& A) { return A.nface[0] + A.nface[1] + A.nface[2]; }
+
 template <typename T, int DIM, int RECON, int FLUX>
-cudaError_t launch_face(const GVjpArgs<T>& A, const Gas<T>& g, long long nf, cudaStream_t s) {
+cudaError_t launch_face(const GVjpBatch<T>& B, const Gas<T>& g, long long nf, cudaStream_t s) {
   constexpr size_t smem = gvjp_face_smem_bytes<T, FLUX>();
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(gvjp_face_kernel<T, DIM, RECON, FLUX>,
@@ -25,70 +53,142 @@ cudaError_t launch_face(const GVjpArgs<T>& A, const Gas<T>& g, long long nf, cud
     if (e != cudaSuccess) return e;
   }
   const long long blocks = (nf + kGvjpThreads - 1) / kGvjpThreads;
-  gvjp_face_kernel<T, DIM, RECON, FLUX><<<(unsigned)blocks, kGvjpThreads, smem, s>>>(A, g);
+  gvjp_face_kernel<T, DIM, RECON, FLUX><<<(unsigned)blocks, kGvjpThreads, smem, s>>>(B, g);
   return cudaGetLastError();
 }
 
 template <typename T, int DIM>
-cudaError_t launch_face_dim(const GVjpArgs<T>& A, const Gas<T>& g, long long nf, int recon, bool nn, cudaStream_t s) {
+cudaError_t launch_face_dim(const GVjpBatch<T>& B, const Gas<T>& g, long long nf, int recon, bool nn,
+                            cudaStream_t s) {
   if (recon == JF_WENO3_JS)
-    return nn ? launch_face<T, DIM, 2, 4>(A, g, nf, s) : launch_face<T, DIM, 2, 0>(A, g, nf, s);
-  return nn ? launch_face<T, DIM, 0, 4>(A, g, nf, s) : launch_face<T, DIM, 0, 0>(A, g, nf, s);
+    return nn ? launch_face<T, DIM, 2, 4>(B, g, nf, s) : launch_face<T, DIM, 2, 0>(B, g, nf, s);
+  return nn ? launch_face<T, DIM, 0, 4>(B, g, nf, s) : launch_face<T, DIM, 0, 0>(B, g, nf, s);
 }
 
-// One V launch: out = a1 x1 + a2 x2 + m + dt J(Us)^T m, m = s_in lam (and the
-// parameter gradient of the network into theta_bar when given).
+// One V over the grids `sims` (their pointers and factors set): the point,
+// face and (Rusanov-NN with theta_bar) parameter-gradient launches, in chunks
+// of GVjpBatch::kMax grids.  The grids' records are consecutive from the
+// first grid's rec.
 template <typename T>
-jf_status gvjp_stage(jf_ctx* h, const Gas<T>& g, const T* Us, const T* lam, T s_in, const T* x1, T a1, const T* x2,
-                     T a2, T* out, const double* dt, T* rec, T* theta_bar, cudaStream_t s) {
-  GVjpArgs<T> A;
-  std::memset(&A, 0, sizeof A);
-  A.Us = Us; A.lam = lam; A.x1 = x1; A.x2 = x2; A.out = out; A.dt = dt;
-  A.s_in = s_in; A.a1 = a1; A.a2 = a2;
-  const int nn3[3] = {h->grid.nx, h->grid.ny, h->grid.nz};
-  long long nf = 0;
-  for (int a = 0; a < 3; ++a) {
-    A.n[a] = nn3[a];
-    A.periodic[a] = h->grid.bc[2 * a] == JF_BC_PERIODIC;
-    A.wall[a] = (h->grid.bc[2 * a] == JF_BC_WALL ? 1 : 0) | (h->grid.bc[2 * a + 1] == JF_BC_WALL ? 2 : 0);
-    A.inv_h[a] = (T)(1.0 / spacing(h->grid, a));
-  }
-  A.N = (long long)h->N;
-  for (int a = 0; a < h->dim; ++a) {
-    long long c = 1;
-    for (int e = 0; e < 3; ++e) c *= e == a ? (long long)nn3[e] + (A.periodic[a] ? 0 : 1) : nn3[e];
-    A.nface[a] = c;
-    nf += c;
-  }
+jf_status gvjp_stage(jf_ctx* h, const Gas<T>& g, std::vector<GVjpArgs<T>>& sims, T* theta_bar, cudaStream_t s) {
   const bool nn = h->scheme.flux == JF_FLUX_RUSANOV_NN;
-  A.rec = nn ? rec : nullptr;
-  gvjp_point_kernel<T><<<reduce_blocks(5 * A.N, h->sms), 256, 0, s>>>(A);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: point launch");
   const int recon = h->scheme.recon;
-  e = h->dim == 1 ? launch_face_dim<T, 1>(A, g, nf, recon, nn, s)
-                  : (h->dim == 2 ? launch_face_dim<T, 2>(A, g, nf, recon, nn, s)
-                                 : launch_face_dim<T, 3>(A, g, nf, recon, nn, s));
-  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: face launch");
-  if (nn && theta_bar) {
-    nn_param_grad_kernel<T><<<(unsigned)((nf + 31) / 32), 32, nn_grad_smem_bytes<T>(), s>>>(g.nn, rec, nf, theta_bar);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "adjoint: parameter-gradient launch");
+  for (size_t c0 = 0; c0 < sims.size(); c0 += GVjpBatch<T>::kMax) {
+    GVjpBatch<T> B;
+    std::memset(&B, 0, sizeof B);
+    B.nsim = (int)std::min<size_t>(GVjpBatch<T>::kMax, sims.size() - c0);
+    for (int k = 0; k < B.nsim; ++k) {
+      B.sim[k] = sims[c0 + k];
+      if (!nn) B.sim[k].rec = nullptr;
+      B.face_base[k + 1] = B.face_base[k] + faces_of(B.sim[k]);
+      B.cell_base[k + 1] = B.cell_base[k] + B.sim[k].N;
+    }
+    const long long nf = B.face_base[B.nsim];
+    gvjp_point_kernel<T><<<reduce_blocks(B.cell_base[B.nsim], h->sms), 256, 0, s>>>(B);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: point launch");
+    e = h->dim == 1 ? launch_face_dim<T, 1>(B, g, nf, recon, nn, s)
+                    : (h->dim == 2 ? launch_face_dim<T, 2>(B, g, nf, recon, nn, s)
+                                   : launch_face_dim<T, 3>(B, g, nf, recon, nn, s));
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: face launch");
+    if (nn && theta_bar) {
+      nn_param_grad_kernel<T><<<(unsigned)((nf + 31) / 32), 32, nn_grad_smem_bytes<T>(), s>>>(g.nn, B.sim[0].rec,
+                                                                                                nf, theta_bar);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "adjoint: parameter-gradient launch");
+    }
   }
   return JF_OK;
 }
 
+// Per-grid state of one adjoint step: the step's inputs and its buffers.
+template <typename T>
+struct StepPtrs {
+  const T* Un;
+  const T* lam;    // lam_out
+  T* lam_in;
+  const T* add;    // added to lam_in (may be null)
+  const double* dt;
+  T* U1;
+  T* U2;
+  T* l1;
+  T* l2;
+  T* rec;
+};
+
+// The integrator's chain over the grids (geometry in `geo`, one entry per grid).
+template <typename T>
+jf_status gvjp_chain(jf_ctx* h, const Gas<T>& g, const std::vector<GVjpArgs<T>>& geo,
+                     const std::vector<StepPtrs<T>>& P, T* theta_bar, cudaStream_t s) {
+  const int integ = h->scheme.integrator;
+  std::vector<GVjpArgs<T>> V(geo);
+  auto set = [&](size_t k, const T* Us, const T* lam, T s_in, const T* x1, T a1, const T* x2, T a2, const T* x3,
+                 T a3, T* out) {
+    GVjpArgs<T>& A = V[k];
+    A.Us = Us; A.lam = lam; A.s_in = s_in; A.x1 = x1; A.a1 = a1; A.x2 = x2; A.a2 = a2; A.x3 = x3; A.a3 = a3;
+    A.out = out; A.dt = P[k].dt; A.rec = P[k].rec;
+  };
+  jf_status st;
+  if (integ == JF_RK3) {
+    for (size_t k = 0; k < V.size(); ++k)
+      set(k, P[k].U2, P[k].lam, T(2.0 / 3.0), nullptr, T(0), nullptr, T(0), nullptr, T(0), P[k].l2);
+    if ((st = gvjp_stage<T>(h, g, V, theta_bar, s)) != JF_OK) return st;
+    for (size_t k = 0; k < V.size(); ++k)
+      set(k, P[k].U1, P[k].l2, T(0.25), nullptr, T(0), nullptr, T(0), nullptr, T(0), P[k].l1);
+    if ((st = gvjp_stage<T>(h, g, V, theta_bar, s)) != JF_OK) return st;
+    for (size_t k = 0; k < V.size(); ++k)
+      set(k, P[k].Un, P[k].l1, T(1), P[k].lam, T(1.0 / 3.0), P[k].l2, T(0.75), P[k].add, T(1), P[k].lam_in);
+    return gvjp_stage<T>(h, g, V, theta_bar, s);
+  }
+  if (integ == JF_RK2) {
+    for (size_t k = 0; k < V.size(); ++k)
+      set(k, P[k].U1, P[k].lam, T(0.5), nullptr, T(0), nullptr, T(0), nullptr, T(0), P[k].l1);
+    if ((st = gvjp_stage<T>(h, g, V, theta_bar, s)) != JF_OK) return st;
+    for (size_t k = 0; k < V.size(); ++k)
+      set(k, P[k].Un, P[k].l1, T(1), P[k].lam, T(0.5), P[k].add, T(1), nullptr, T(0), P[k].lam_in);
+    return gvjp_stage<T>(h, g, V, theta_bar, s);
+  }
+  for (size_t k = 0; k < V.size(); ++k)
+    set(k, P[k].Un, P[k].lam, T(1), P[k].add, T(1), nullptr, T(0), nullptr, T(0), P[k].lam_in);
+  return gvjp_stage<T>(h, g, V, theta_bar, s);
+}
+
+// Forward recompute of one grid's stage states with the stage kernels of the
+// step (single-grid form of the handle's table entry).
+template <typename T>
+jf_status recompute(jf_ctx* h, const StageVariant<T>& sv, const Gas<T>& g, StageArgs<T> A, const StepPtrs<T>& p,
+                    cudaStream_t s) {
+  const int integ = h->scheme.integrator;
+  if (integ == JF_EULER) return JF_OK;
+  A.dt = p.dt;
+  A.Us = p.Un; A.Un = nullptr; A.out = p.U1; A.a = T(0); A.b = T(1);
+  cudaError_t e = sv.launch(A, g, s);
+  if (e == cudaSuccess && integ == JF_RK3) {
+    A.Us = p.U1; A.Un = p.Un; A.out = p.U2; A.a = T(0.75); A.b = T(0.25);
+    e = sv.launch(A, g, s);
+  }
+  return e == cudaSuccess ? JF_OK : cuda_fail(h, e, "adjoint: forward recompute");
+}
+
+template <typename T>
+jf_status network(jf_ctx* h, Gas<T>& g) {
+  if (h->scheme.flux != JF_FLUX_RUSANOV_NN) return JF_OK;
+  if (!h->nn) { set_error(h, "Rusanov-NN flux: no network parameters (jf_set_nn)"); return JF_ERR_ARG; }
+  g.nn = static_cast<const T*>(h->nn);
+  return JF_OK;
+}
+
+template <typename T>
+jf_status prepare_param_grad(jf_ctx* h, const void* theta_bar) {
+  static_assert(nn_grad_smem_bytes<T>() <= 227 * 1024, "parameter-gradient tile exceeds shared memory");
+  if (!theta_bar) return JF_OK;
+  const cudaError_t e = cudaFuncSetAttribute(nn_param_grad_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)nn_grad_smem_bytes<T>());
+  return e == cudaSuccess ? JF_OK : cuda_fail(h, e, "adjoint: kernel set-up");
+}
+
 }  // namespace
 
-long long general_face_count(const jf_ctx* h) {
-  const int n[3] = {h->grid.nx, h->grid.ny, h->grid.nz};
-  long long nf = 0;
-  for (int a = 0; a < h->dim; ++a) {
-    long long c = 1;
-    for (int e = 0; e < 3; ++e) c *= e == a ? (long long)n[e] + (h->grid.bc[2 * a] == JF_BC_PERIODIC ? 0 : 1) : n[e];
-    nf += c;
-  }
-  return nf;
-}
+long long general_face_count(const jf_ctx* h) { return faces_of(grid_args<double>(h->grid, h->dim)); }
 
 bool general_vjp_supported(const jf_ctx* h, std::string* why) {
   const jf_scheme& s = h->scheme;
@@ -103,61 +203,75 @@ bool general_vjp_supported(const jf_ctx* h, std::string* why) {
 template <typename T>
 jf_status general_vjp(jf_ctx* h, const void* Un, const double* dt, const void* lam_out, void* lam_in, void* theta_bar,
                       cudaStream_t s) {
-  const long long nf = general_face_count(h);
-  static_assert(nn_grad_smem_bytes<T>() <= 227 * 1024, "parameter-gradient tile exceeds shared memory");
-  if (theta_bar) {
-    cudaError_t e = cudaFuncSetAttribute(nn_param_grad_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)nn_grad_smem_bytes<T>());
-    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: kernel set-up");
-  }
+  const GVjpArgs<T> geo = grid_args<T>(h->grid, h->dim);
   for (int i = 0; i < 3; ++i) {
-    const size_t bytes = i < 2 ? 5 * h->N * sizeof(T) : (size_t)nf * 5 * sizeof(T);
+    const size_t bytes = i < 2 ? 5 * h->N * sizeof(T) : (size_t)faces_of(geo) * 5 * sizeof(T);
     if (!h->adj[i]) {
       cudaError_t e = cudaMalloc(&h->adj[i], bytes);
       if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: buffers");
     }
   }
-  Gas<T> g = make_gas<T>(h->gas, h->scheme);
-  if (h->scheme.flux == JF_FLUX_RUSANOV_NN) {
-    if (!h->nn) { set_error(h, "Rusanov-NN flux: no network parameters (jf_set_nn)"); return JF_ERR_ARG; }
-    g.nn = static_cast<const T*>(h->nn);
-  }
-  const T* U0 = static_cast<const T*>(Un);
-  const T* L = static_cast<const T*>(lam_out);
-  T* Lin = static_cast<T*>(lam_in);
-  T* U1 = static_cast<T*>(h->stage[0]);
-  T* U2 = static_cast<T*>(h->stage[1]);
-  T* l2 = static_cast<T*>(h->adj[0]);
-  T* l1 = static_cast<T*>(h->adj[1]);
-  T* rec = static_cast<T*>(h->adj[2]);
-  T* tb = static_cast<T*>(theta_bar);
-  // forward recompute of the stage states (same kernels as the step)
-  StageArgs<T> A = base_args<T>(h);
-  A.dt = dt;
   jf_status st;
-  const int integ = h->scheme.integrator;
-  if (integ != JF_EULER) {
-    A.Us = U0; A.Un = nullptr; A.out = U1; A.a = T(0); A.b = T(1);
-    if ((st = launch<T>(h, A, s)) != JF_OK) return st;
+  if ((st = prepare_param_grad<T>(h, theta_bar)) != JF_OK) return st;
+  Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  if ((st = network<T>(h, g)) != JF_OK) return st;
+  StepPtrs<T> p{static_cast<const T*>(Un), static_cast<const T*>(lam_out), static_cast<T*>(lam_in), nullptr, dt,
+                static_cast<T*>(h->stage[0]), static_cast<T*>(h->stage[1]), static_cast<T*>(h->adj[1]),
+                static_cast<T*>(h->adj[0]), static_cast<T*>(h->adj[2])};
+  int count = 0;
+  const StageVariant<T>& sv = stage_variants<T>(&count)[h->table_index];
+  if ((st = recompute<T>(h, sv, g, base_args<T>(h), p, s)) != JF_OK) return st;
+  return gvjp_chain<T>(h, g, std::vector<GVjpArgs<T>>{geo}, std::vector<StepPtrs<T>>{p},
+                       static_cast<T*>(theta_bar), s);
+}
+
+template <typename T>
+jf_status batch_general_vjp(jf_ctx* h, void* const* Un, const double* dt, void* const* lam_out, void* const* lam_in,
+                            void* const* add, void* theta_bar, cudaStream_t s) {
+  const int ns = h->nsim;
+  std::vector<GVjpArgs<T>> geo(ns);
+  size_t pool = 0;
+  for (int k = 0; k < ns; ++k) {
+    geo[k] = grid_args<T>(h->grids[k], h->dim);
+    pool += (size_t)(10 * geo[k].N + 5 * faces_of(geo[k]));
   }
-  if (integ == JF_RK3) {
-    A.Us = U1; A.Un = U0; A.out = U2; A.a = T(0.75); A.b = T(0.25);
-    if ((st = launch<T>(h, A, s)) != JF_OK) return st;
-    if ((st = gvjp_stage<T>(h, g, U2, L, T(2.0 / 3.0), nullptr, T(0), nullptr, T(0), l2, dt, rec, tb, s)) != JF_OK)
-      return st;
-    if ((st = gvjp_stage<T>(h, g, U1, l2, T(0.25), nullptr, T(0), nullptr, T(0), l1, dt, rec, tb, s)) != JF_OK)
-      return st;
-    return gvjp_stage<T>(h, g, U0, l1, T(1), L, T(1.0 / 3.0), l2, T(0.75), Lin, dt, rec, tb, s);
+  if (!h->adj[0]) {  // l1, l2 of every grid, then every grid's face records
+    cudaError_t e = cudaMalloc(&h->adj[0], pool * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch adjoint: buffers");
   }
-  if (integ == JF_RK2) {
-    if ((st = gvjp_stage<T>(h, g, U1, L, T(0.5), nullptr, T(0), nullptr, T(0), l1, dt, rec, tb, s)) != JF_OK)
-      return st;
-    return gvjp_stage<T>(h, g, U0, l1, T(1), L, T(0.5), nullptr, T(0), Lin, dt, rec, tb, s);
+  jf_status st;
+  if ((st = prepare_param_grad<T>(h, theta_bar)) != JF_OK) return st;
+  Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  if ((st = network<T>(h, g)) != JF_OK) return st;
+  int count = 0;
+  const StageVariant<T>& sv = stage_variants<T>(&count)[h->table_index];
+  const SimDesc<T>* desc = reinterpret_cast<const SimDesc<T>*>(h->host_desc.data());
+  std::vector<StepPtrs<T>> P(ns);
+  T* lbuf = static_cast<T*>(h->adj[0]);
+  size_t off = 0;
+  for (int k = 0; k < ns; ++k) off += 10 * (size_t)geo[k].N;
+  T* rbuf = lbuf + off;  // records of all grids, consecutive
+  off = 0;
+  size_t roff = 0;
+  for (int k = 0; k < ns; ++k) {
+    P[k] = StepPtrs<T>{static_cast<const T*>(Un[k]), static_cast<const T*>(lam_out[k]), static_cast<T*>(lam_in[k]),
+                       add ? static_cast<const T*>(add[k]) : nullptr, dt + k, desc[k].U1, desc[k].U2,
+                       lbuf + off, lbuf + off + 5 * geo[k].N, rbuf + roff};
+    off += 10 * (size_t)geo[k].N;
+    roff += 5 * (size_t)faces_of(geo[k]);
+    StageArgs<T> A{};
+    batch_stage_args(desc[k], 1, A);
+    A.flag = h->flag;
+    if ((st = recompute<T>(h, sv, g, A, P[k], s)) != JF_OK) return st;
   }
-  return gvjp_stage<T>(h, g, U0, L, T(1), nullptr, T(0), nullptr, T(0), Lin, dt, rec, tb, s);
+  return gvjp_chain<T>(h, g, geo, P, static_cast<T*>(theta_bar), s);
 }
 
 template jf_status general_vjp<float>(jf_ctx*, const void*, const double*, const void*, void*, void*, cudaStream_t);
 template jf_status general_vjp<double>(jf_ctx*, const void*, const double*, const void*, void*, void*, cudaStream_t);
+template jf_status batch_general_vjp<float>(jf_ctx*, void* const*, const double*, void* const*, void* const*,
+                                            void* const*, void*, cudaStream_t);
+template jf_status batch_general_vjp<double>(jf_ctx*, void* const*, const double*, void* const*, void* const*,
+                                             void* const*, void*, cudaStream_t);
 
 }  // namespace jf

@@ -3,11 +3,11 @@
 // and the Rusanov-NN flux of Section 7.4 (with its parameter gradient), for
 // inviscid 1D, 2D and 3D grids.
 //
-// One stage computes, as the tiled adjoint does,
-//   out = a1 x1 + a2 x2 + m + dt J(Us)^T m,   m = s_in lam,
+// One stage computes, as the tiled adjoint does (with one more addend),
+//   out = a1 x1 + a2 x2 + a3 x3 + m + dt J(Us)^T m,   m = s_in lam,
 // with J the Jacobian of the right-hand side L of Eq. (FVD) at Us.
 //
-// Layout of the work.  A point-wise launch writes a1 x1 + a2 x2 + m; then one
+// Layout of the work.  A point-wise launch writes the addends and m; then one
 // thread per face (every face of every active direction) recomputes the
 // face's stencil (6 cells along the normal, mapped through the boundary
 // condition), its reconstruction and flux, and runs the reverse pass:
@@ -36,9 +36,10 @@ struct GVjpArgs {
   const T* lam;       // cotangent of the stage output
   const T* x1;        // point-wise addends (may be null)
   const T* x2;
+  const T* x3;
   T* out;
   const double* dt;
-  T s_in, a1, a2;
+  T s_in, a1, a2, a3;
   int n[3];
   long long N;
   int periodic[3];
@@ -48,16 +49,46 @@ struct GVjpArgs {
   T* rec;             // Rusanov-NN: 5 values per face (x0..x3, abar), else null
 };
 
-// out = a1 x1 + a2 x2 + s_in lam
+// Up to kMax grids per launch (a batch, or one grid), passed by value in the
+// kernel parameters: the grids' arguments and the prefix sums of their faces
+// and cells, so that one launch covers every face (cell) of every grid.
 template <typename T>
-__global__ void __launch_bounds__(256) gvjp_point_kernel(const GVjpArgs<T> A) {
-  const long long total = 5 * A.N;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    T o = A.s_in * A.lam[q];
-    if (A.x1) o += A.a1 * A.x1[q];
-    if (A.x2) o += A.a2 * A.x2[q];
-    A.out[q] = o;
+struct GVjpBatch {
+  static constexpr int kMax = 32;
+  int nsim;
+  long long face_base[kMax + 1];
+  long long cell_base[kMax + 1];
+  GVjpArgs<T> sim[kMax];
+};
+
+// The grid an index of [0, base[nsim]) belongs to (base ascending).
+__device__ __forceinline__ int find_sim(const long long* base, int nsim, long long i) {
+  int lo = 0, hi = nsim - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// out = a1 x1 + a2 x2 + a3 x3 + s_in lam, every cell of every grid
+template <typename T>
+__global__ void __launch_bounds__(256) gvjp_point_kernel(const GVjpBatch<T> B) {
+  const long long total = B.cell_base[B.nsim];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = find_sim(B.cell_base, B.nsim, i);
+    const GVjpArgs<T>& A = B.sim[s];
+    const long long c = i - B.cell_base[s];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const long long q = c + k * A.N;
+      T o = A.s_in * A.lam[q];
+      if (A.x1) o += A.a1 * A.x1[q];
+      if (A.x2) o += A.a2 * A.x2[q];
+      if (A.x3) o += A.a3 * A.x3[q];
+      A.out[q] = o;
+    }
   }
 }
 
@@ -379,8 +410,8 @@ __device__ __forceinline__ void gvjp_face(const GVjpArgs<T>& A, const Gas<T>& g,
   }
 }
 
-// One thread per face: faces of direction 0 first, then 1, then 2; within a
-// direction x fastest.  A periodic axis has n faces (face 0 is also face n),
+// One thread per face of every grid of the launch: within a grid, faces of
+// direction 0 first, then 1, then 2; within a direction x fastest.  A periodic axis has n faces (face 0 is also face n),
 // any other n + 1.  Rusanov-NN: dynamic shared memory of
 // gvjp_face_smem_bytes holds each thread's two hidden-layer rows.
 constexpr int kGvjpThreads = 128;
@@ -390,11 +421,15 @@ constexpr size_t gvjp_face_smem_bytes() {
 }
 
 template <typename T, int DIM, int RECON, int FLUX>
-__global__ void __launch_bounds__(kGvjpThreads) gvjp_face_kernel(const GVjpArgs<T> A, const Gas<T> g) {
+__global__ void __launch_bounds__(kGvjpThreads) gvjp_face_kernel(const GVjpBatch<T> B, const Gas<T> g) {
   extern __shared__ __align__(16) unsigned char gvjp_smem[];
   T* h1 = reinterpret_cast<T*>(gvjp_smem) + threadIdx.x * (NN_HIDDEN + 1);
   T* h2 = h1 + kGvjpThreads * (NN_HIDDEN + 1);
-  long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gf = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gf >= B.face_base[B.nsim]) return;
+  const int sidx = find_sim(B.face_base, B.nsim, gf);
+  const GVjpArgs<T>& A = B.sim[sidx];
+  const long long f = gf - B.face_base[sidx];  // face of this grid (its record index)
   long long r = f;
   int d = 0;
   for (; d < DIM; ++d) {

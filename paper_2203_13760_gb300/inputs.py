@@ -372,6 +372,22 @@ def random_blocks(n, seed: int = DEFAULT_SEED, bc=None, blocks: int = 3, gamma: 
     return Case("blocks", n, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), tuple(bc), U, gamma=gamma)
 
 
+def implosion(n: int = 128, gamma: float = 1.4) -> Case:
+    """Section 7.4's implosion on [0, 1]^2: (rho, u, v, p) = (0.14, 0, 0,
+    0.125) where x + y <= 0.15 and (1, 0, 0, 1) elsewhere, evaluated at cell
+    centres; slip walls on all four sides (the shock reflects off the walls
+    of the lower-left corner); the ground-truth scheme of the section:
+    WENO3-JS, HLLC, TVD-RK2 with the fixed step 2.5e-4."""
+    x = centres(n, 0.0, 1.0)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    inner = X + Y <= 0.15
+    rho = np.where(inner, 0.14, 1.0)
+    p = np.where(inner, 0.125, 1.0)
+    U = conservative(rho, 0.0, 0.0, 0.0, p, gamma).reshape(5, 1, n, n)
+    return Case("implosion", (n, n, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (WALL, WALL, WALL, WALL, 1, 1), U,
+                gamma=gamma, recon="weno3-js", integrator="rk2", dt=2.5e-4)
+
+
 def nn_params(seed: int = DEFAULT_SEED, alpha: float = 2.0, spread: float = 0.1) -> np.ndarray:
     """Seeded parameters of the Rusanov-NN network (Section 7.4) in the flat
     layout W1 [32][4], b1, W2 [32][32], b2, W3 [32][32], b3, W4 [32], b4

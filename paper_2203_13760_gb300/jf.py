@@ -68,6 +68,8 @@ SIGNATURES = {
     "jf_rk3_run": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
     "jf_rk3_step_vjp": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_rk3_step_vjp_params": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "jf_batch_step_vjp": (_I, [_VP, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                               ctypes.POINTER(_VP), _VP, _VP]),
     "jf_loss_density_l2": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_batch_create": (_I, [ctypes.POINTER(Grid), _I, ctypes.POINTER(GasParams), ctypes.POINTER(Scheme),
                              ctypes.POINTER(_VP)]),
@@ -307,6 +309,14 @@ class Batch:
         if nn is not None:
             self.set_nn(nn)
 
+    def supports_step_vjp(self):
+        """Whether jf_batch_step_vjp covers this batch's scheme (inviscid,
+        WENO5-JS / WENO3-JS, HLLC with Einfeldt speeds or Rusanov-NN)."""
+        s = self.scheme
+        visc = bool(s.viscous or s.heat) and self.gas.mu > 0
+        flux_ok = s.flux == FLUX["rusanov-nn"] or (s.flux == FLUX["hllc"] and s.signal_speed == SPEEDS["einfeldt"])
+        return (not visc) and s.recon in (RECON["weno5-js"], RECON["weno3-js"]) and flux_ok
+
     def set_nn(self, theta):
         """Rusanov-NN parameters of every simulation (jf_set_nn; also given to
         the cached single-grid solvers)."""
@@ -351,6 +361,25 @@ class Batch:
         tp = (ctypes.c_void_p * self.nsim)(*[T.data_ptr() for T in trajs])
         _check(lib().jf_batch_feed_forward(self.h, u0, tp, int(nsteps), _ptr(dt_dev), _stream()), self.h)
         return trajs
+
+    def step_vjp(self, Uns, dt, lams, lam_ins=None, adds=None, theta_bar=None):
+        """Adjoint of one fixed-dt step of every simulation (jf_batch_step_vjp):
+        lam_ins[i] = J_i^T lams[i] + adds[i]; theta_bar (Rusanov-NN) is added to.
+        dt: a float64 CUDA tensor of one step per simulation."""
+        import torch
+        self._check_fields(Uns)
+        self._check_fields(lams)
+        lam_ins = [torch.empty_like(L) for L in lams] if lam_ins is None else lam_ins
+        self._check_fields(lam_ins)
+        if adds is not None:
+            self._check_fields(adds)
+        arr = lambda ts: (ctypes.c_void_p * self.nsim)(*[x.data_ptr() for x in ts])  # noqa: E731
+        if (dt.dtype != torch.float64 or not dt.is_cuda or dt.numel() != self.nsim):
+            raise ValueError("dt must be a float64 CUDA tensor of one step per simulation")
+        _check(lib().jf_batch_step_vjp(self.h, arr(Uns), _ptr(dt), arr(lams), arr(lam_ins),
+                                       arr(adds) if adds is not None else None,
+                                       _ptr(theta_bar) if theta_bar is not None else None, _stream()), self.h)
+        return lam_ins
 
     def step(self, Us, nsteps, dt_out=None):
         import torch

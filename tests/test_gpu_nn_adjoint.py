@@ -126,3 +126,40 @@ def test_unsupported_adjoints_are_refused():
     with pytest.raises(jf.JFError) as e:  # parameter gradient of a flux without parameters
         s.rk3_step_vjp_params(U, s.scalar(1e-3), torch.ones_like(U))
     assert e.value.status == jf.JF_ERR_ARG
+
+
+@pytest.mark.parametrize("scheme", ["nn_weno3_rk2", "hllc_weno5_rk3", "nn_weno3_euler"])
+def test_batch_adjoint_equals_single_grids(scheme):
+    """jf_batch_step_vjp over an uneven batch (with walls) equals each grid's
+    single-grid adjoint plus the addend, and its theta_bar the sum of the
+    single-grid parameter gradients (FP64, to rounding: atomic order)."""
+    cases = [with_scheme(c, **SCHEMES[scheme]) for c in inputs.four_quadrant_batch(nsim=3, sides=(32, 48), seed=7)]
+    for c in cases:
+        c.bc = (W, W, W, 1, 1, 1)
+    nn = cases[0].flux == "rusanov-nn"
+    theta = torch.tensor(THETA, dtype=torch.float64, device="cuda") if nn else None
+    p = cases[0].params()
+    b = jf.Batch([jf.make_grid(c.n, c.lo, c.hi, c.bc) for c in cases], dtype="f64", nn=theta,
+                 **{k: p[k] for k in ("gamma", "R", "mu", "Pr", "eps", "cfl", "viscous", "heat", "flux", "recon",
+                                      "speeds", "integrator")})
+    assert b.supports_step_vjp()
+    rng = np.random.default_rng(4)
+    Us = [torch.tensor(c.U, dtype=torch.float64, device="cuda") for c in cases]
+    lams = [torch.tensor(rng.standard_normal(c.U.shape), device="cuda") for c in cases]
+    adds = [torch.tensor(rng.standard_normal(c.U.shape), device="cuda") for c in cases]
+    dts = [2e-4, 3e-4, 2.5e-4]
+    tb = torch.zeros(jf.NN_PARAMS, dtype=torch.float64, device="cuda") if nn else None
+    got = b.step_vjp(Us, torch.tensor(dts, dtype=torch.float64, device="cuda"), lams, None, adds, tb)
+    b.sync()
+    tb_ref = torch.zeros_like(tb) if nn else None
+    for i, c in enumerate(cases):
+        s = b.solver(i)
+        if nn:
+            want, _ = s.rk3_step_vjp_params(Us[i], s.scalar(dts[i]), lams[i], theta_bar=tb_ref)
+        else:
+            want = s.rk3_step_vjp(Us[i], s.scalar(dts[i]), lams[i])
+        s.sync()
+        want = want + adds[i]
+        assert (got[i] - want).abs().max().item() <= 1e-12 * want.abs().max().item(), i
+    if nn:
+        assert (tb - tb_ref).abs().max().item() <= 1e-12 * tb_ref.abs().max().item()
