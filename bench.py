@@ -109,7 +109,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=-1)
-    p.add_argument("--only", choices=["batched", "adjoint", "variants"], default=None,
+    p.add_argument("--only", choices=["batched", "adjoint", "variants", "learned_flux"], default=None,
                    help="run only the batched or the adjoint measurement and print it")
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--adjoint-steps", type=int, default=400)
@@ -618,6 +618,51 @@ def run_variants(n=256, steps=10):
     return out
 
 
+def run_learned_flux(steps=20, warmup=3):
+    """Section 7.4 training at the paper's settings (32^2 Rusanov-NN model,
+    WENO3-JS / TVD-RK2, batches of 20 windows of 15 steps): time per Adam step
+    (forward trajectories with jf_batch_feed_forward, loss, the reverse sweep
+    with jf_batch_step_vjp including the parameter gradient), the forward
+    alone, and the reference's generation time (128^2 run, 2501 samples)."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2203_13760_gb300 import autograd, inputs
+    from paper_2203_13760_gb300 import learned_flux as lf
+    t0 = time.perf_counter()
+    cg = lf.ground_truth(nsamples=2501)
+    torch.cuda.synchronize()
+    t_ref = time.perf_counter() - t0
+    tr = lf.Trainer(cg, inputs.nn_params(seed=0), batch=20, unroll=15, lr=5e-4, n_train=1000, dtype="f32")
+    rng = np.random.default_rng(0)
+    batches = [rng.choice(tr.starts, 20, replace=False) for _ in range(warmup + steps)]
+    for b in batches[:warmup]:
+        tr.step(b)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for b in batches[warmup:]:
+        tr.step(b)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / steps
+    e0.record()
+    with torch.no_grad():
+        for b in batches[warmup:]:
+            autograd.feed_forward(tr.batch, [tr.cg[s] for s in b], tr.unroll, tr.dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / steps
+    cells = 20 * 15 * cg.shape[-1] * cg.shape[-2]
+    return {"workload": "Section 7.4: 32^2 Rusanov-NN, WENO3-JS/TVD-RK2, batch 20 x 15 steps, FP32",
+            "ms_per_adam_step": ms_step, "ms_forward_trajectories": ms_fwd,
+            "ms_backward_and_loss": ms_step - ms_fwd,
+            "forward_cell_updates_per_s": cells / (ms_fwd * 1e-3),
+            "reference_seconds": t_ref}
+
+
 def run_extras(args):
     """Batched and adjoint forms against the plain per-simulation launch, and
     the scheme variants on the bench flow."""
@@ -634,6 +679,10 @@ def run_extras(args):
         out["variants"] = run_variants()
     except Exception as e:
         out["variants"] = {"error": repr(e)}
+    try:
+        out["learned_flux"] = run_learned_flux()
+    except Exception as e:
+        out["learned_flux"] = {"error": repr(e)}
     return out
 
 
@@ -651,6 +700,8 @@ def main():
             out = run_batched()
         elif args.only == "variants":
             out = run_variants()
+        elif args.only == "learned_flux":
+            out = run_learned_flux()
         else:
             out = run_adjoint(args.adjoint_n, args.adjoint_steps)
         print(json.dumps({args.only: out}), flush=True)

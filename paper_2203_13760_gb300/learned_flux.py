@@ -69,6 +69,10 @@ def trajectory_loss(trajs, refs, gamma: float = GAMMA):
     """Mean over the windows of 1/N_T sum_{i=1..N_T} MSE(W_i, W_i^ref): each
     window is an (N_T + 1, 5, ...) trajectory, slot 0 the shared initial state;
     MSE averages over the four primitive variables and the cells."""
+    if all(t.shape == trajs[0].shape for t in trajs) and all(r.shape == trajs[0].shape for r in refs):
+        # equal windows: one stacked computation (the mean of equal-size means)
+        d = primitives(torch.stack(trajs)[:, 1:], gamma) - primitives(torch.stack(refs)[:, 1:], gamma)
+        return (d * d).mean()
     total = 0.0
     for traj, ref in zip(trajs, refs):
         d = primitives(traj[1:], gamma) - primitives(ref[1:], gamma)
