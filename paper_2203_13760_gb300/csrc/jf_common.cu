@@ -50,6 +50,12 @@ void release_all(jf_ctx* h) {
   if (h->dt_buf) cudaFree(h->dt_buf);
   if (h->red_cfl) cudaFree(h->red_cfl);
   if (h->d_sims) cudaFree(h->d_sims);
+  if (h->vjp_desc_done) cudaEventSynchronize(h->vjp_desc_done);
+  if (h->vjp_desc_host) cudaFreeHost(h->vjp_desc_host);
+  if (h->vjp_desc_dev) cudaFree(h->vjp_desc_dev);
+  if (h->vjp_desc_done) cudaEventDestroy(h->vjp_desc_done);
+  h->vjp_desc_host = h->vjp_desc_dev = nullptr;
+  h->vjp_desc_done = nullptr;
   if (h->d_work) cudaFree(h->d_work);
   if (h->d_dt) cudaFree(h->d_dt);
   if (h->d_red) cudaFree(h->d_red);

@@ -61,6 +61,11 @@ struct jf_ctx {
   std::vector<void*> sim_stage;        // 2 per simulation
   void* d_sims = nullptr;              // device array of SimDesc<T> (stage.cuh)
   std::vector<unsigned char> host_desc;  // host copy of the descriptors
+  // batch adjoint: descriptors of the recompute (pinned staging, device copy,
+  // event guarding the staging buffer's reuse)
+  void* vjp_desc_host = nullptr;
+  void* vjp_desc_dev = nullptr;
+  cudaEvent_t vjp_desc_done = nullptr;
   void* d_cfl = nullptr;               // per-simulation CflArgs
   void* d_chunks = nullptr;            // CFL chunk list
   int nchunks = 0;

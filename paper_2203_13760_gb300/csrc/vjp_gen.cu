@@ -92,8 +92,10 @@ jf_status gvjp_stage(jf_ctx* h, const Gas<T>& g, std::vector<GVjpArgs<T>>& sims,
                                    : launch_face_dim<T, 3>(B, g, nf, recon, nn, s));
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: face launch");
     if (nn && theta_bar) {
-      nn_param_grad_kernel<T><<<(unsigned)((nf + 31) / 32), 32, nn_grad_smem_bytes<T>(), s>>>(g.nn, B.sim[0].rec,
-                                                                                                nf, theta_bar);
+      const long long chunks = (nf + 31) / 32;
+      const long long blocks = std::min<long long>((chunks + kNnWarps - 1) / kNnWarps, (long long)h->sms);
+      nn_param_grad_kernel<T><<<(unsigned)blocks, 32 * kNnWarps, nn_grad_smem_bytes<T>(), s>>>(
+          g.nn, B.sim[0].rec, nf, theta_bar);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "adjoint: parameter-gradient launch");
     }
   }
@@ -225,6 +227,54 @@ jf_status general_vjp(jf_ctx* h, const void* Un, const double* dt, const void* l
                        static_cast<T*>(theta_bar), s);
 }
 
+// Forward recompute of every grid's stage states in one launch per stage
+// (FP32: the persistent batch kernel over the handle's work list, with a
+// descriptor row whose U is each grid's Un and whose dt is its step, staged
+// through pinned memory; FP64: the single-grid form per grid, as the batch's
+// forward runs).
+template <typename T>
+jf_status recompute_batch(jf_ctx* h, const StageVariant<T>& sv, const Gas<T>& g, const std::vector<StepPtrs<T>>& P,
+                          cudaStream_t s) {
+  const SimDesc<T>* desc = reinterpret_cast<const SimDesc<T>*>(h->host_desc.data());
+  const int ns = h->nsim, integ = h->scheme.integrator;
+  if (integ == JF_EULER) return JF_OK;
+  if constexpr (sizeof(T) == 8) {
+    for (int k = 0; k < ns; ++k) {
+      StageArgs<T> A{};
+      batch_stage_args(desc[k], 1, A);
+      A.flag = h->flag;
+      jf_status st = recompute<T>(h, sv, g, A, P[k], s);
+      if (st != JF_OK) return st;
+    }
+    return JF_OK;
+  } else {
+    const size_t bytes = (size_t)ns * sizeof(SimDesc<T>);
+    cudaError_t e = cudaSuccess;
+    if (!h->vjp_desc_host) {
+      if ((e = cudaMallocHost(&h->vjp_desc_host, bytes)) != cudaSuccess) return cuda_fail(h, e, "batch adjoint: staging");
+      if ((e = cudaMalloc(&h->vjp_desc_dev, bytes)) != cudaSuccess) return cuda_fail(h, e, "batch adjoint: descriptors");
+      if ((e = cudaEventCreateWithFlags(&h->vjp_desc_done, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(h, e, "batch adjoint: event");
+    } else if ((e = cudaEventSynchronize(h->vjp_desc_done)) != cudaSuccess) {
+      return cuda_fail(h, e, "batch adjoint: staging reuse");
+    }
+    SimDesc<T>* row = static_cast<SimDesc<T>*>(h->vjp_desc_host);
+    for (int k = 0; k < ns; ++k) {
+      row[k] = desc[k];
+      row[k].U = const_cast<T*>(P[k].Un);
+      row[k].dt = P[k].dt;
+    }
+    e = cudaMemcpyAsync(h->vjp_desc_dev, row, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->vjp_desc_done, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch adjoint: descriptor upload");
+    const SimDesc<T>* dev = static_cast<const SimDesc<T>*>(h->vjp_desc_dev);
+    e = sv.launch_batch(dev, static_cast<const WorkItem*>(h->d_work), h->nwork, 1, g, h->flag, h->batch_blocks, s);
+    if (e == cudaSuccess && integ == JF_RK3)
+      e = sv.launch_batch(dev, static_cast<const WorkItem*>(h->d_work), h->nwork, 2, g, h->flag, h->batch_blocks, s);
+    return e == cudaSuccess ? JF_OK : cuda_fail(h, e, "batch adjoint: forward recompute");
+  }
+}
+
 template <typename T>
 jf_status batch_general_vjp(jf_ctx* h, void* const* Un, const double* dt, void* const* lam_out, void* const* lam_in,
                             void* const* add, void* theta_bar, cudaStream_t s) {
@@ -259,11 +309,8 @@ jf_status batch_general_vjp(jf_ctx* h, void* const* Un, const double* dt, void* 
                        lbuf + off, lbuf + off + 5 * geo[k].N, rbuf + roff};
     off += 10 * (size_t)geo[k].N;
     roff += 5 * (size_t)faces_of(geo[k]);
-    StageArgs<T> A{};
-    batch_stage_args(desc[k], 1, A);
-    A.flag = h->flag;
-    if ((st = recompute<T>(h, sv, g, A, P[k], s)) != JF_OK) return st;
   }
+  if ((st = recompute_batch<T>(h, sv, g, P, s)) != JF_OK) return st;
   return gvjp_chain<T>(h, g, geo, P, static_cast<T*>(theta_bar), s);
 }
 

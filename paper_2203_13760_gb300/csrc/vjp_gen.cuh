@@ -450,121 +450,168 @@ __global__ void __launch_bounds__(kGvjpThreads) gvjp_face_kernel(const GVjpBatch
 }
 
 // Parameter gradient of the Rusanov-NN dissipation: grad += sum over the
-// face records (x_f, abar_f) of abar_f d alpha(x_f) / d theta.  One warp per
-// 32 records (one record per lane): each lane evaluates the network of its
-// record and the cotangents of every layer (seed d alpha / d o = alpha, scaled
-// by abar), kept in shared memory rows of 33 (conflict-free); then lane L
-// forms row L of every weight gradient as a sum over the 32 records
-// (dW[L][k] = sum_f G[f][L] H[f][k]) and adds it to grad.
+// face records (x_f, abar_f) of abar_f d alpha(x_f) / d theta.
+//
+// Persistent blocks of kNnWarps warps; the block stages theta in shared
+// memory, and each warp takes chunks of 32 records (one per lane).  Per
+// chunk, each lane evaluates the network of its record and the cotangents of
+// every layer (seed d alpha / d o = alpha, scaled by abar) into shared rows of
+// 33 (conflict-free), reusing rows once they are consumed; then lane L adds
+// row L of every weight gradient summed over the 32 records
+// (dW[L][k] = sum_f G[f][L] H[f][k]) to accumulators kept in registers across
+// chunks.  At the end the block sums its warps' accumulators in shared memory
+// and adds them to grad with one atomic per parameter.
 constexpr int kNnRow = NN_HIDDEN + 1;
+constexpr int kNnWarps = 4;
+constexpr int kNnWarpElems = 4 * 32 * kNnRow + 32 * 5;  // four row sets, inputs, output cotangents
 template <typename T>
 constexpr size_t nn_grad_smem_bytes() {
-  return sizeof(T) * (size_t)(6 * 32 * kNnRow + 32 * 5);
+  return sizeof(T) * (size_t)(NN_PARAMS + kNnWarps * kNnWarpElems);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32) nn_param_grad_kernel(const T* __restrict__ th, const T* __restrict__ rec,
-                                                           long long nrec, T* grad) {
+__global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* __restrict__ theta,
+                                                                      const T* __restrict__ rec, long long nrec,
+                                                                      T* grad) {
   extern __shared__ __align__(16) unsigned char nn_smem[];
-  T* H1 = reinterpret_cast<T*>(nn_smem);  // [32][kNnRow] activations of layer 1
-  T* H2 = H1 + 32 * kNnRow;
-  T* H3 = H2 + 32 * kNnRow;
-  T* G1 = H3 + 32 * kNnRow;               // cotangents of the pre-activations
-  T* G2 = G1 + 32 * kNnRow;
-  T* G3 = G2 + 32 * kNnRow;
-  T* X = G3 + 32 * kNnRow;                // [32][4] inputs
-  T* OB = X + 32 * 4;                     // [32] cotangent of the output o
-  const T* W1 = th;
+  T* TH = reinterpret_cast<T*>(nn_smem);
+  for (int i = threadIdx.x; i < NN_PARAMS; i += blockDim.x) TH[i] = theta[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* base = TH + NN_PARAMS + warp * kNnWarpElems;
+  T* R1 = base;                 // H1
+  T* R2 = R1 + 32 * kNnRow;     // H2
+  T* R3 = R2 + 32 * kNnRow;     // H3, then G2
+  T* R4 = R3 + 32 * kNnRow;     // G3, then G1
+  T* X = R4 + 32 * kNnRow;      // [32][4]
+  T* OB = X + 32 * 4;           // [32]
+  const T* W1 = TH;
   const T* b1 = W1 + NN_HIDDEN * 4;
   const T* W2 = b1 + NN_HIDDEN;
   const T* b2 = W2 + NN_HIDDEN * NN_HIDDEN;
   const T* W3 = b2 + NN_HIDDEN;
   const T* b3 = W3 + NN_HIDDEN * NN_HIDDEN;
   const T* W4 = b3 + NN_HIDDEN;
-  const int lane = threadIdx.x;
-  const long long f = (long long)blockIdx.x * 32 + lane;
-  T x[4] = {T(0), T(0), T(0), T(0)}, abar = T(0);
-  if (f < nrec) {
+  __syncthreads();
+  // row `lane` of every gradient, accumulated over this warp's chunks
+  T a3[NN_HIDDEN], a2[NN_HIDDEN], a1[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int m = 0; m < 4; ++m) x[m] = rec[f * 5 + m];
-    abar = rec[f * 5 + 4];
-  }
-  T* h1 = H1 + lane * kNnRow;
-  T* h2 = H2 + lane * kNnRow;
-  T* h3 = H3 + lane * kNnRow;
-  T* g1 = G1 + lane * kNnRow;
-  T* g2 = G2 + lane * kNnRow;
-  T* g3 = G3 + lane * kNnRow;
+  for (int k = 0; k < NN_HIDDEN; ++k) a3[k] = a2[k] = T(0);
+  T ab1 = T(0), ab2 = T(0), ab3 = T(0), a4 = T(0), ab4 = T(0);
+  const long long nchunk = (nrec + 31) / 32;
+  T* h1 = R1 + lane * kNnRow;
+  T* h2 = R2 + lane * kNnRow;
+  T* r3 = R3 + lane * kNnRow;
+  T* r4 = R4 + lane * kNnRow;
+  for (long long ch = (long long)blockIdx.x * kNnWarps + warp; ch < nchunk; ch += (long long)gridDim.x * kNnWarps) {
+    const long long f = ch * 32 + lane;
+    T x[4] = {T(0), T(0), T(0), T(0)}, abar = T(0);
+    if (f < nrec) {
 #pragma unroll
-  for (int m = 0; m < 4; ++m) X[lane * 4 + m] = x[m];
-  // forward
-  for (int i = 0; i < NN_HIDDEN; ++i)
-    h1[i] = tmax(T(0), b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] + W1[4 * i + 3] * x[3]);
-  for (int i = 0; i < NN_HIDDEN; ++i) {
-    T z = b2[i];
-    for (int j = 0; j < NN_HIDDEN; ++j) z += W2[NN_HIDDEN * i + j] * h1[j];
-    h2[i] = tmax(T(0), z);
-  }
-  T o = W4[NN_HIDDEN];
-  for (int i = 0; i < NN_HIDDEN; ++i) {
-    T z = b3[i];
-    for (int j = 0; j < NN_HIDDEN; ++j) z += W3[NN_HIDDEN * i + j] * h2[j];
-    h3[i] = tmax(T(0), z);
-    o += W4[i] * h3[i];
-  }
-  const T ob = f < nrec ? abar * texp(o) : T(0);
-  OB[lane] = ob;
-  // reverse
-  for (int i = 0; i < NN_HIDDEN; ++i) g3[i] = h3[i] > T(0) ? ob * W4[i] : T(0);
-  for (int j = 0; j < NN_HIDDEN; ++j) {
-    T s = T(0);
-    for (int i = 0; i < NN_HIDDEN; ++i) s += W3[NN_HIDDEN * i + j] * g3[i];
-    g2[j] = h2[j] > T(0) ? s : T(0);
-  }
-  for (int k = 0; k < NN_HIDDEN; ++k) {
-    T s = T(0);
-    for (int j = 0; j < NN_HIDDEN; ++j) s += W2[NN_HIDDEN * j + k] * g2[j];
-    g1[k] = h1[k] > T(0) ? s : T(0);
-  }
-  __syncwarp();
-  // row `lane` of every gradient, summed over the warp's records
-  T* gW1 = grad;
-  T* gb1 = gW1 + NN_HIDDEN * 4;
-  T* gW2 = gb1 + NN_HIDDEN;
-  T* gb2 = gW2 + NN_HIDDEN * NN_HIDDEN;
-  T* gW3 = gb2 + NN_HIDDEN;
-  T* gb3 = gW3 + NN_HIDDEN * NN_HIDDEN;
-  T* gW4 = gb3 + NN_HIDDEN;
-  const int L = lane;
-  T sb1 = T(0), sb2 = T(0), sb3 = T(0), s4 = T(0), sx[4] = {T(0), T(0), T(0), T(0)};
-  for (int r = 0; r < 32; ++r) {
-    const T a1 = G1[r * kNnRow + L], a2 = G2[r * kNnRow + L], a3 = G3[r * kNnRow + L];
-    sb1 += a1;
-    sb2 += a2;
-    sb3 += a3;
-    s4 += OB[r] * H3[r * kNnRow + L];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) sx[m] += a1 * X[r * 4 + m];
-  }
-  atomicAdd(gb1 + L, sb1);
-  atomicAdd(gb2 + L, sb2);
-  atomicAdd(gb3 + L, sb3);
-  atomicAdd(gW4 + L, s4);
-#pragma unroll
-  for (int m = 0; m < 4; ++m) atomicAdd(gW1 + 4 * L + m, sx[m]);
-  if (L == 0) {
-    T s = T(0);
-    for (int r = 0; r < 32; ++r) s += OB[r];
-    atomicAdd(gW4 + NN_HIDDEN, s);
-  }
-  for (int k = 0; k < NN_HIDDEN; ++k) {
-    T s2 = T(0), s3 = T(0);
-    for (int r = 0; r < 32; ++r) {
-      s2 += G2[r * kNnRow + L] * H1[r * kNnRow + k];
-      s3 += G3[r * kNnRow + L] * H2[r * kNnRow + k];
+      for (int m = 0; m < 4; ++m) x[m] = rec[f * 5 + m];
+      abar = rec[f * 5 + 4];
     }
-    atomicAdd(gW2 + NN_HIDDEN * L + k, s2);
-    atomicAdd(gW3 + NN_HIDDEN * L + k, s3);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) X[lane * 4 + m] = x[m];
+    // forward: h1, h2, h3 (r3)
+#pragma unroll 4
+    for (int i = 0; i < NN_HIDDEN; ++i)
+      h1[i] = tmax(T(0), b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] +
+                             W1[4 * i + 3] * x[3]);
+#pragma unroll 1
+    for (int i = 0; i < NN_HIDDEN; ++i) {
+      T z = b2[i];
+#pragma unroll 8
+      for (int j = 0; j < NN_HIDDEN; ++j) z += W2[NN_HIDDEN * i + j] * h1[j];
+      h2[i] = tmax(T(0), z);
+    }
+    T o = W4[NN_HIDDEN];
+#pragma unroll 1
+    for (int i = 0; i < NN_HIDDEN; ++i) {
+      T z = b3[i];
+#pragma unroll 8
+      for (int j = 0; j < NN_HIDDEN; ++j) z += W3[NN_HIDDEN * i + j] * h2[j];
+      r3[i] = tmax(T(0), z);
+      o += W4[i] * r3[i];
+    }
+    const T ob = f < nrec ? abar * texp(o) : T(0);  // d alpha / d o = alpha
+    OB[lane] = ob;
+#pragma unroll 4
+    for (int i = 0; i < NN_HIDDEN; ++i) r4[i] = r3[i] > T(0) ? ob * W4[i] : T(0);  // G3
+    __syncwarp();
+    // layers 4 and 3 (H3 in R3, G3 in R4, H2 in R2)
+#pragma unroll 1
+    for (int r = 0; r < 32; ++r) {
+      const T g3 = R4[r * kNnRow + lane];
+      ab3 += g3;
+      a4 += OB[r] * R3[r * kNnRow + lane];
+      if (lane == 0) ab4 += OB[r];
+#pragma unroll
+      for (int k = 0; k < NN_HIDDEN; ++k) a3[k] += g3 * R2[r * kNnRow + k];
+    }
+    __syncwarp();
+    // G2 into R3: g2[j] = [h2_j > 0] sum_i W3[i][j] g3[i]
+#pragma unroll 1
+    for (int j = 0; j < NN_HIDDEN; ++j) {
+      T sum = T(0);
+#pragma unroll 8
+      for (int i = 0; i < NN_HIDDEN; ++i) sum += W3[NN_HIDDEN * i + j] * r4[i];
+      r3[j] = h2[j] > T(0) ? sum : T(0);
+    }
+    __syncwarp();
+    // layer 2 (G2 in R3, H1 in R1)
+#pragma unroll 1
+    for (int r = 0; r < 32; ++r) {
+      const T g2 = R3[r * kNnRow + lane];
+      ab2 += g2;
+#pragma unroll
+      for (int k = 0; k < NN_HIDDEN; ++k) a2[k] += g2 * R1[r * kNnRow + k];
+    }
+    __syncwarp();
+    // G1 into R4: g1[k] = [h1_k > 0] sum_j W2[j][k] g2[j]
+#pragma unroll 1
+    for (int k = 0; k < NN_HIDDEN; ++k) {
+      T sum = T(0);
+#pragma unroll 8
+      for (int j = 0; j < NN_HIDDEN; ++j) sum += W2[NN_HIDDEN * j + k] * r3[j];
+      r4[k] = h1[k] > T(0) ? sum : T(0);
+    }
+    __syncwarp();
+    // layer 1 (G1 in R4, inputs in X)
+#pragma unroll 1
+    for (int r = 0; r < 32; ++r) {
+      const T g1 = R4[r * kNnRow + lane];
+      ab1 += g1;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) a1[m] += g1 * X[r * 4 + m];
+    }
+    __syncwarp();
+  }
+  // block sum of the warps' rows (the row sets are free now), then one
+  // atomic per parameter
+  __syncthreads();
+  T* S = TH + NN_PARAMS;  // [kNnWarps][NN_PARAMS]
+  T* Sw = S + warp * NN_PARAMS;
+  const int L = lane;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Sw[4 * L + m] = a1[m];
+  Sw[NN_HIDDEN * 4 + L] = ab1;
+  T* sW2 = Sw + NN_HIDDEN * 4 + NN_HIDDEN;
+#pragma unroll
+  for (int k = 0; k < NN_HIDDEN; ++k) sW2[NN_HIDDEN * L + k] = a2[k];
+  sW2[NN_HIDDEN * NN_HIDDEN + L] = ab2;
+  T* sW3 = sW2 + NN_HIDDEN * NN_HIDDEN + NN_HIDDEN;
+#pragma unroll
+  for (int k = 0; k < NN_HIDDEN; ++k) sW3[NN_HIDDEN * L + k] = a3[k];
+  sW3[NN_HIDDEN * NN_HIDDEN + L] = ab3;
+  T* sW4 = sW3 + NN_HIDDEN * NN_HIDDEN + NN_HIDDEN;
+  sW4[L] = a4;
+  if (L == 0) sW4[NN_HIDDEN] = ab4;
+  __syncthreads();
+  for (int i = threadIdx.x; i < NN_PARAMS; i += blockDim.x) {
+    T sum = T(0);
+#pragma unroll
+    for (int w = 0; w < kNnWarps; ++w) sum += S[w * NN_PARAMS + i];
+    if (sum != T(0)) atomicAdd(grad + i, sum);
   }
 }
 

@@ -165,3 +165,27 @@ def test_per_face_adjoint_stays_in_bounds(dtype, n):
     lam_in.check()
     tb.check()
     s.sync()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_adjoint_stays_in_bounds(dtype):
+    """jf_batch_step_vjp over an uneven walled batch with the Rusanov-NN flux:
+    every lam_in and theta_bar inside canary margins."""
+    W = inputs.WALL
+    cases = inputs.four_quadrant_batch(nsim=3, sides=(32, 48, 40), seed=11)
+    for c in cases:
+        c.bc = (W, W, W, 1, 1, 1)
+    t = torch.float32 if dtype == "f32" else torch.float64
+    theta = torch.tensor(inputs.nn_params(seed=5), dtype=t, device="cuda")
+    b = jf.Batch([jf.make_grid(c.n, c.lo, c.hi, c.bc) for c in cases], dtype=dtype, flux="rusanov-nn",
+                 recon="weno3-js", integrator="rk2", nn=theta)
+    Us = [torch.tensor(c.U, dtype=t, device="cuda") for c in cases]
+    lams = [torch.ones_like(U) for U in Us]
+    outs = [Guarded(tuple(U.shape), t) for U in Us]
+    tb = Guarded((jf.NN_PARAMS,), t, torch.zeros(jf.NN_PARAMS, dtype=t, device="cuda"))
+    dt = torch.full((3,), 1e-4, dtype=torch.float64, device="cuda")
+    b.step_vjp(Us, dt, lams, [g.t for g in outs], lams, tb.t)
+    for g in outs:
+        g.check()
+    tb.check()
+    b.sync()
