@@ -109,7 +109,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=-1)
-    p.add_argument("--only", choices=["batched", "adjoint", "variants", "learned_flux"], default=None,
+    p.add_argument("--only", choices=["batched", "adjoint", "variants", "learned_flux", "table3"], default=None,
                    help="run only the batched or the adjoint measurement and print it")
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--adjoint-steps", type=int, default=400)
@@ -663,6 +663,58 @@ def run_learned_flux(steps=20, warmup=3):
             "reference_seconds": t_ref}
 
 
+# Table 3 of the paper: ns per cell per RK3 step on the TGV (RTX A6000, JAX; context)
+PAPER_TABLE3 = {("hllc", "f32"): {32: 64.41, 64: 24.39, 128: 25.09, 256: 28.36, 384: 28.11},
+                ("hllc", "f64"): {32: 98.20, 64: 93.94, 128: 92.55, 256: 92.76},
+                ("roe", "f32"): {32: 241.71, 64: 302.20, 128: 304.55, 256: 301.78},
+                ("roe", "f64"): {32: 703.40, 64: 746.78, 128: 759.36, 256: 760.09}}
+
+
+def run_table3(target_s=0.4):
+    """The paper's Table 3 workloads on this GPU: TGV n^3 with the HLLC setup
+    (WENO5-JS + HLLC) and the ROE setup (flux splitting), FP32 and FP64, CFL
+    RK3 steps through jf_rk3_step (Navier-Stokes, the bench physics); ns per
+    cell per step next to the paper's."""
+    import torch
+
+    from paper_2203_13760_gb300 import inputs, jf
+    rows = []
+    for (scheme, dtype), paper in PAPER_TABLE3.items():
+        sizes = sorted(set(paper) | ({384} if dtype == "f32" else set()))
+        for n in sizes:
+            case = inputs.taylor_green(n)
+            kw = {"flux": "roe"} if scheme == "roe" else {}
+            s = jf.Solver.from_case(case, dtype=dtype, **kw)
+            t = torch.float32 if dtype == "f32" else torch.float64
+            U = torch.tensor(case.U, dtype=t, device="cuda")
+            used = s.scalar()
+            for _ in range(3):
+                s.rk3_step(U, None, used)
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record()
+            s.rk3_step(U, None, used)
+            e1.record()
+            torch.cuda.synchronize()
+            one = e0.elapsed_time(e1) * 1e-3
+            k = max(3, min(200, int(target_s / max(one, 1e-6))))
+            e0.record()
+            for _ in range(k):
+                s.rk3_step(U, None, used)
+            e1.record()
+            torch.cuda.synchronize()
+            s.sync()
+            ns = e0.elapsed_time(e1) * 1e6 / (k * case.cells)
+            rows.append({"setup": scheme.upper(), "dtype": dtype, "n": n, "steps": k, "ns_per_cell_step": ns,
+                         "paper_ns_per_cell_step": paper.get(n),
+                         "paper_over_this": (paper[n] / ns) if n in paper else None})
+            s.close()
+            del U
+            torch.cuda.empty_cache()
+    return {"workload": "TGV n^3, Navier-Stokes, CFL RK3 steps (paper Table 3 sizes; RTX A6000 numbers as context)",
+            "rows": rows}
+
+
 def run_extras(args):
     """Batched and adjoint forms against the plain per-simulation launch, and
     the scheme variants on the bench flow."""
@@ -702,6 +754,8 @@ def main():
             out = run_variants()
         elif args.only == "learned_flux":
             out = run_learned_flux()
+        elif args.only == "table3":
+            out = run_table3()
         else:
             out = run_adjoint(args.adjoint_n, args.adjoint_steps)
         print(json.dumps({args.only: out}), flush=True)

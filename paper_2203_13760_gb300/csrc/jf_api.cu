@@ -136,8 +136,22 @@ int reduce_blocks(long long N, int sms) {
 }
 
 // ------------------------------------------------------------------------
-// Variant selection.  A variant = (compiled tile shape, z chunk).
-static const int kZChunks[] = {32, 16, 64, 8};
+// Variant selection.  A variant = (compiled tile shape, z chunk).  z chunk 0
+// (the first, default, one per tile) is chosen from the grid at launch: the
+// planes per CTA that give about one wave of resident CTAs (SMs x the CTAs
+// per SM the tile is bounded for), at most 32.  Large grids then take 32
+// planes (halo planes re-read once per 32), small ones fewer, so that a
+// 32^3 grid does not run on a handful of SMs.
+static const int kZChunks[] = {0, 32, 16, 64, 8};
+
+int auto_zchunk(const jf_ctx* h, int bx, int by, int ctas_per_sm) {
+  const long long tiles = (long long)((h->grid.nx + bx - 1) / bx) * ((h->grid.ny + by - 1) / by);
+  const long long target = (long long)h->sms * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+  long long z = (h->grid.nz * tiles + target - 1) / target;
+  if (z < 1) z = 1;
+  if (z > 32) z = 32;
+  return (int)z;
+}
 
 bool has_walls(const jf_grid& g) {
   for (int i = 0; i < 6; ++i)
@@ -200,9 +214,14 @@ int describe_variant(jf_ctx* h, int v, char* buf, int len) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
   const StageVariant<T>& s = tab[list[v].first];
-  if (buf && len > 0)
-    std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=%d smem=%zu ctas/sm=%d", s.bx, s.by,
-                  s.dim == 3 ? list[v].second : 1, s.smem, s.minb);
+  if (buf && len > 0) {
+    const int z = s.dim == 3 ? list[v].second : 1;
+    if (z == 0)
+      std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=auto(%d) smem=%zu ctas/sm=%d", s.bx, s.by,
+                    auto_zchunk(h, s.bx, s.by, s.minb), s.smem, s.minb);
+    else
+      std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=%d smem=%zu ctas/sm=%d", s.bx, s.by, z, s.smem, s.minb);
+  }
   return (int)list.size();
 }
 
@@ -221,6 +240,11 @@ StageArgs<T> base_args(const jf_ctx* h) {
     A.inv_h[d] = (T)(1.0 / spacing(h->grid, d));
   }
   A.zchunk = h->zchunk;
+  if (A.zchunk <= 0) {
+    int count = 0;
+    const StageVariant<T>& v = stage_variants<T>(&count)[h->table_index];
+    A.zchunk = auto_zchunk(h, v.bx, v.by, v.minb);
+  }
   A.flag = h->flag;
   return A;
 }
