@@ -179,6 +179,21 @@ jf_status jf_rk3_step(jf_handle h, void* U_inout, const double* dt_dev, double* 
 jf_status jf_stage(jf_handle h, const void* Us, const void* Un, void* out, double a, double b, const double* dt_dev,
                    void* stream);
 
+/* n independent RK3 steps of host-resident states (the end-to-end form: a
+ * serving loop of states that live in host memory): for k = 0 .. n-1, copy
+ * U_in_host[k] to the device, advance it one step as jf_rk3_step does (dt_dev
+ * as there; NULL = its own CFL step) and copy the result to U_out_host[k].
+ * U_in_host / U_out_host: HOST arrays of n host pointers, each to a whole
+ * state [5][nz][ny][nx] of the handle's dtype; pinned (page-locked) memory
+ * lets the copies overlap the steps: the upload of state k + 1 and the
+ * download of state k - 1 run on two internal streams while state k steps
+ * on `stream`, in two device buffers of the handle (allocated, with the
+ * streams, at the first call).  `stream` waits for the last download, so a
+ * synchronisation of it makes every U_out_host[k] readable.  In and out
+ * pointers may be equal (state k is read before it is written). */
+jf_status jf_rk3_step_host(jf_handle h, const void* const* U_in_host, void* const* U_out_host, int n,
+                           const double* dt_dev, void* stream);
+
 /* nsteps RK3 steps in place, enqueued as one CUDA graph (captured at the
  * first call for a given (U, nsteps, dt mode) and replayed afterwards).
  * dt_dev as for jf_rk3_step (a fixed step is read at every step).

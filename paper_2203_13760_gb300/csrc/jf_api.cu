@@ -462,6 +462,58 @@ jf_status jf_rk3_step(jf_handle h, void* U, const double* dt_dev, double* dt_use
   return JF_DISPATCH(h, step_impl, h, U, dt_dev, dt_used_dev, (cudaStream_t)stream);
 }
 
+// Independent steps of host-resident states, pipelined: state k's upload
+// (stream pipe_in), its step (the caller's stream) and its download (stream
+// pipe_out) on two device buffers, so that the copies of states k + 1 and
+// k - 1 overlap the step of state k.  Events: ev[b] upload of buffer b done,
+// ev[2 + b] step on buffer b done, ev[4 + b] download of buffer b done (the
+// buffer is free again), ev[6] the caller's stream at entry.
+jf_status jf_rk3_step_host(jf_handle h, const void* const* U_in_host, void* const* U_out_host, int n,
+                           const double* dt_dev, void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_rk3_step_host: not a single-grid handle"); return JF_ERR_ARG; }
+  if (n < 0 || (n > 0 && (!U_in_host || !U_out_host))) { set_error(h, "jf_rk3_step_host: bad arguments"); return JF_ERR_ARG; }
+  for (int k = 0; k < n; ++k)
+    if (!U_in_host[k] || !U_out_host[k]) { set_error(h, "jf_rk3_step_host: null state pointer"); return JF_ERR_ARG; }
+  if (n == 0) return JF_OK;
+  const size_t bytes = 5 * h->N * h->esize;
+  cudaError_t e = cudaSuccess;
+  if (!h->pipe_buf[0]) {
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&h->pipe_buf[b], bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->pipe_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->pipe_out, cudaStreamNonBlocking);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&h->pipe_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_host: pipeline set-up");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t* ev = h->pipe_ev;
+  // everything starts after the work already queued on the caller's stream
+  e = cudaEventRecord(ev[6], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_in, ev[6], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_out, ev[6], 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_host: stream ordering");
+  for (int k = 0; k < n; ++k) {
+    const int b = k & 1;
+    void* buf = h->pipe_buf[b];
+    // upload once the buffer's previous download has finished
+    if (k >= 2) e = cudaStreamWaitEvent(h->pipe_in, ev[4 + b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf, U_in_host[k], bytes, cudaMemcpyHostToDevice, h->pipe_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[b], h->pipe_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[b], 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_host: upload");
+    jf_status st = JF_DISPATCH(h, step_impl, h, buf, dt_dev, nullptr, s);
+    if (st != JF_OK) return st;
+    e = cudaEventRecord(ev[2 + b], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_out, ev[2 + b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U_out_host[k], buf, bytes, cudaMemcpyDeviceToHost, h->pipe_out);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 + b], h->pipe_out);
+    if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_host: download");
+  }
+  // the caller's stream resumes after the last download
+  e = cudaStreamWaitEvent(s, ev[4 + ((n - 1) & 1)], 0);
+  if (e == cudaSuccess && n >= 2) e = cudaStreamWaitEvent(s, ev[4 + ((n - 2) & 1)], 0);
+  return e == cudaSuccess ? JF_OK : cuda_fail(h, e, "jf_rk3_step_host: join");
+}
+
 jf_status jf_stage(jf_handle h, const void* Us, const void* Un, void* out, double a, double b, const double* dt_dev,
                    void* stream) {
   if (!h || h->kind != 0) { set_error(h, "jf_stage: not a single-grid handle"); return JF_ERR_ARG; }

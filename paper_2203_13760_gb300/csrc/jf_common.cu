@@ -64,6 +64,11 @@ void release_all(jf_ctx* h) {
   h->d_cfl = nullptr;
   h->d_chunks = nullptr;
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  for (void*& p : h->pipe_buf) { if (p) cudaFree(p); p = nullptr; }
+  if (h->pipe_in) cudaStreamDestroy(h->pipe_in);
+  if (h->pipe_out) cudaStreamDestroy(h->pipe_out);
+  h->pipe_in = h->pipe_out = nullptr;
+  for (cudaEvent_t& ev : h->pipe_ev) { if (ev) cudaEventDestroy(ev); ev = nullptr; }
   h->flag = nullptr; h->dt_buf = nullptr; h->red_cfl = h->red_loss = nullptr;
   h->d_sims = nullptr; h->d_work = nullptr; h->d_dt = nullptr; h->d_red = nullptr; h->capture_stream = nullptr;
 }

@@ -53,6 +53,11 @@ struct jf_ctx {
   int* flag = nullptr;       // device error flag
   const void* nn = nullptr;  // Rusanov-NN parameters (caller-owned device array; jf_set_nn)
   cudaStream_t capture_stream = nullptr;
+  // host-state pipeline (jf_rk3_step_host): two device buffers, the copy
+  // streams and the events that order them (created at the first call)
+  void* pipe_buf[2] = {nullptr, nullptr};
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   std::map<jf::GraphKey, jf::GraphEntry> graphs;
   std::string err;
   // batch

@@ -66,6 +66,7 @@ SIGNATURES = {
     "jf_rk3_step": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "jf_stage": (_I, [_VP, _VP, _VP, _VP, _D, _D, _VP, _VP]),
     "jf_rk3_run": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    "jf_rk3_step_host": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP, _VP]),
     "jf_rk3_step_vjp": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_rk3_step_vjp_params": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_batch_step_vjp": (_I, [_VP, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -216,6 +217,21 @@ class Solver:
         """One RK3 step in place; dt: None (CFL) or a float64 CUDA tensor."""
         _check(lib().jf_rk3_step(self.h, self._field(U, "U"), _ptr(dt), _ptr(dt_used), _stream()), self.h)
         return U
+
+    def step_host(self, U_in, U_out, dt=None):
+        """Independent RK3 steps of host states (jf_rk3_step_host): U_in /
+        U_out are lists of CPU tensors shaped like a state (pinned for
+        overlap); U_out[k] receives one step of U_in[k]."""
+        if len(U_in) != len(U_out):
+            raise ValueError("one output per input state")
+        for t_ in list(U_in) + list(U_out):
+            if (t_.is_cuda or t_.dtype != self.dtype or tuple(t_.shape) != self.shape or not t_.is_contiguous()):
+                raise ValueError(f"host states must be contiguous CPU {self.dtype} tensors of shape {self.shape}")
+        n = len(U_in)
+        ins = (ctypes.c_void_p * max(n, 1))(*[t_.data_ptr() for t_ in U_in])
+        outs = (ctypes.c_void_p * max(n, 1))(*[t_.data_ptr() for t_ in U_out])
+        _check(lib().jf_rk3_step_host(self.h, ins, outs, n, _ptr(dt), _stream()), self.h)
+        return U_out
 
     def stage(self, Us, Un, out, a, b, dt):
         """out = a Un + b (Us + dt L(Us)); dt a float64 CUDA scalar tensor."""

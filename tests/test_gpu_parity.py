@@ -253,3 +253,26 @@ def test_compute_dt_fp64(orc):
     s = solver_for(case, "f64")
     dt = s.compute_dt(to_dev(case.U, "f64")).item()
     assert dt == pytest.approx(orc.compute_dt(c, case.U), rel=1e-14)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_step_host_equals_device_steps(dtype):
+    """jf_rk3_step_host: each host state advanced one CFL step equals
+    jf_rk3_step on the device, bit for bit; in and out may alias; five
+    states cycle through the two device buffers."""
+    cases = [inputs.random_smooth((20, 12, 10), seed=k, viscous=True, mu=0.01) for k in range(5)]
+    s = solver_for(cases[0], dtype)
+    t = torch.float32 if dtype == "f32" else torch.float64
+    ins = [torch.tensor(c.U, dtype=t).pin_memory() for c in cases]
+    outs = [torch.empty_like(x).pin_memory() for x in ins]
+    outs[3] = ins[3]  # aliased in/out
+    want = []
+    for c in cases:
+        U = to_dev(c.U, dtype)
+        s.rk3_step(U)
+        want.append(U.cpu())
+    s.step_host(ins, outs)
+    torch.cuda.current_stream().synchronize()
+    s.sync()
+    for k in range(5):
+        assert torch.equal(outs[k], want[k]), k
