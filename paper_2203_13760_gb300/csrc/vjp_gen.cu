@@ -93,7 +93,7 @@ jf_status gvjp_stage(jf_ctx* h, const Gas<T>& g, std::vector<GVjpArgs<T>>& sims,
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: face launch");
     if (nn && theta_bar) {
       const long long chunks = (nf + 31) / 32;
-      const long long blocks = std::min<long long>((chunks + kNnWarps - 1) / kNnWarps, (long long)h->sms);
+      const long long blocks = std::min<long long>((chunks + kNnWarps - 1) / kNnWarps, 2LL * h->sms);
       nn_param_grad_kernel<T><<<(unsigned)blocks, 32 * kNnWarps, nn_grad_smem_bytes<T>(), s>>>(
           g.nn, B.sim[0].rec, nf, theta_bar);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "adjoint: parameter-gradient launch");

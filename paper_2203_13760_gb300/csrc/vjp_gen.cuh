@@ -145,13 +145,13 @@ __device__ __forceinline__ T nn_alpha_grad(const T* th, const T x[4], T dx[4], T
   const T* W4 = b3 + NN_HIDDEN;
   const T b4 = W4[NN_HIDDEN];
   unsigned m1 = 0, m2 = 0, m3 = 0;  // ReLU masks (bit i: unit i active)
-#pragma unroll 1
+#pragma unroll 4
   for (int i = 0; i < NN_HIDDEN; ++i) {
     const T z = b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] + W1[4 * i + 3] * x[3];
     h1[i] = tmax(T(0), z);
     m1 |= (z > T(0) ? 1u : 0u) << i;
   }
-#pragma unroll 1
+#pragma unroll 4
   for (int i = 0; i < NN_HIDDEN; ++i) {
     T z = b2[i];
 #pragma unroll 8
@@ -160,7 +160,7 @@ __device__ __forceinline__ T nn_alpha_grad(const T* th, const T x[4], T dx[4], T
     m2 |= (z > T(0) ? 1u : 0u) << i;
   }
   T o = b4;
-#pragma unroll 1
+#pragma unroll 4
   for (int i = 0; i < NN_HIDDEN; ++i) {
     T z = b3[i];
 #pragma unroll 8
@@ -171,7 +171,7 @@ __device__ __forceinline__ T nn_alpha_grad(const T* th, const T x[4], T dx[4], T
   const T alpha = texp(o);
   // reverse with seed d alpha / d o = alpha: h2 <- cotangent of layer 2's
   // outputs, h1 <- cotangent of layer 1's outputs
-#pragma unroll 1
+#pragma unroll 4
   for (int j = 0; j < NN_HIDDEN; ++j) {
     T s = T(0);
 #pragma unroll 8
@@ -179,7 +179,7 @@ __device__ __forceinline__ T nn_alpha_grad(const T* th, const T x[4], T dx[4], T
       if ((m3 >> i) & 1u) s += W3[NN_HIDDEN * i + j] * W4[i];
     h2[j] = (m2 >> j) & 1u ? alpha * s : T(0);
   }
-#pragma unroll 1
+#pragma unroll 4
   for (int k = 0; k < NN_HIDDEN; ++k) {
     T s = T(0);
 #pragma unroll 8
@@ -187,7 +187,7 @@ __device__ __forceinline__ T nn_alpha_grad(const T* th, const T x[4], T dx[4], T
     h1[k] = (m1 >> k) & 1u ? s : T(0);
   }
   dx[0] = dx[1] = dx[2] = dx[3] = T(0);
-#pragma unroll 1
+#pragma unroll 4
   for (int k = 0; k < NN_HIDDEN; ++k) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) dx[m] += W1[4 * k + m] * h1[k];
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* _
     for (int i = 0; i < NN_HIDDEN; ++i)
       h1[i] = tmax(T(0), b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] +
                              W1[4 * i + 3] * x[3]);
-#pragma unroll 1
+#pragma unroll 4
     for (int i = 0; i < NN_HIDDEN; ++i) {
       T z = b2[i];
 #pragma unroll 8
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* _
       h2[i] = tmax(T(0), z);
     }
     T o = W4[NN_HIDDEN];
-#pragma unroll 1
+#pragma unroll 4
     for (int i = 0; i < NN_HIDDEN; ++i) {
       T z = b3[i];
 #pragma unroll 8
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* _
     }
     __syncwarp();
     // G2 into R3: g2[j] = [h2_j > 0] sum_i W3[i][j] g3[i]
-#pragma unroll 1
+#pragma unroll 4
     for (int j = 0; j < NN_HIDDEN; ++j) {
       T sum = T(0);
 #pragma unroll 8
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* _
     }
     __syncwarp();
     // G1 into R4: g1[k] = [h1_k > 0] sum_j W2[j][k] g2[j]
-#pragma unroll 1
+#pragma unroll 4
     for (int k = 0; k < NN_HIDDEN; ++k) {
       T sum = T(0);
 #pragma unroll 8
