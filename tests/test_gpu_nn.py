@@ -212,7 +212,7 @@ def test_batch_with_walls_equals_single_grid(scheme, dtype):
         assert torch.equal(trajs[i][3], V)
 
 
-def test_nn_flux_needs_parameters_and_adjoint_rejects_walls():
+def test_nn_flux_needs_parameters_and_adjoint_covers_inviscid_walls():
     case = with_scheme(inputs.random_smooth((16, 12, 1), seed=1), flux="rusanov-nn")
     s = jf.Solver.from_case(case, dtype="f64")
     U = to_dev(case.U, "f64")
@@ -225,9 +225,15 @@ def test_nn_flux_needs_parameters_and_adjoint_rejects_walls():
     with pytest.raises(jf.JFError) as e:
         hl.set_nn(torch.zeros(jf.NN_PARAMS, dtype=torch.float64, device="cuda"))
     assert e.value.status == jf.JF_ERR_ARG
+    # walls: the per-face adjoint covers inviscid runs; viscous walls are refused
     walled = inputs.random_smooth((16, 12, 1), seed=1, bc=(W, W, 1, 1, 1, 1))
     sw = jf.Solver.from_case(walled, dtype="f64")
+    lam = sw.rk3_step_vjp(U, sw.scalar(1e-3), torch.ones_like(U))
+    sw.sync()
+    assert torch.isfinite(lam).all().item()
+    visc = inputs.random_smooth((16, 12, 1), seed=1, bc=(W, W, 1, 1, 1, 1), viscous=True, mu=0.01)
+    sv = jf.Solver.from_case(visc, dtype="f64")
     with pytest.raises(jf.JFError) as e:
-        sw.rk3_step_vjp(U, sw.scalar(1e-3), torch.ones_like(U))
+        sv.rk3_step_vjp(U, sv.scalar(1e-3), torch.ones_like(U))
     assert e.value.status == jf.JF_ERR_UNSUPPORTED
 
