@@ -11,7 +11,11 @@ const StageVariant<float>* nn_variants_f32(int* count) {
   static const StageVariant<float> table[] = {
       make_variant<float, 3, true, 32, 7, 1, SCH_NN>(),
       make_variant<float, 3, false, 32, 7, 1, SCH_NN>(),
+      // 2D: 32 x 3 tiles (4 warps, two CTAs per SM: up to 256 registers) fill
+      // the SMs on small grids such as the 32^2 grids of a training batch
+      make_variant<float, 2, true, 32, 3, 2, SCH_NN>(),
       make_variant<float, 2, true, 32, 8, 1, SCH_NN>(),
+      make_variant<float, 2, false, 32, 3, 2, SCH_NN>(),
       make_variant<float, 2, false, 32, 8, 1, SCH_NN>(),
       make_variant<float, 2, false, 32, 7, 1, SCH_NN>(),
       make_variant<float, 1, true, 128, 1, 1, SCH_NN>(),
