@@ -160,10 +160,13 @@ bool has_walls(const jf_grid& g) {
 }
 
 int scheme_kind(const jf_scheme& s, bool walls) {
-  if (s.flux == JF_FLUX_ROE) return SCH_ROE;
+  // walls and WENO3-JS need the extended kernel forms
+  const bool ext = walls || s.recon == JF_WENO3_JS;
+  if (s.flux == JF_FLUX_ROE) return ext ? SCH_ROE_EXT : SCH_ROE;
   if (s.flux == JF_FLUX_RUSANOV_NN) return SCH_NN;
   const bool general = s.flux != JF_FLUX_HLLC || s.signal_speed != JF_EINFELDT || s.recon != JF_WENO5_JS || walls;
-  return general ? SCH_GENERAL : SCH_DEFAULT;
+  if (!general) return SCH_DEFAULT;
+  return ext ? SCH_GENERAL_EXT : SCH_GENERAL;
 }
 
 int scheme_kind(const jf_ctx* h) {

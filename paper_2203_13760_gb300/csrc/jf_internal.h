@@ -93,8 +93,9 @@ double spacing(const jf_grid& g, int d);
 double conductivity(const jf_gas& gas, const jf_scheme& s);
 bool dissipative(const jf_gas& gas, const jf_scheme& s);
 // kernel family of a scheme: SCH_DEFAULT, SCH_GENERAL (run-time Table 2
-// Godunov variants, and every grid with slip walls), SCH_ROE (flux
-// splitting) or SCH_NN (Rusanov-NN)
+// Godunov variants), SCH_ROE (flux splitting), their _EXT forms (slip walls
+// or WENO3-JS; a walled grid with the default scheme runs SCH_GENERAL_EXT),
+// or SCH_NN (Rusanov-NN)
 bool has_walls(const jf_grid& g);
 int scheme_kind(const jf_scheme& s, bool walls);
 int scheme_kind(const jf_ctx* h);

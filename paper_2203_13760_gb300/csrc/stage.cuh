@@ -253,7 +253,13 @@ template <> struct Roles<2> {
 };
 
 // Scheme codes of the stage kernels (template parameter SCH).
-enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2, SCH_NN = 3 };
+// The _EXT families also handle slip walls and WENO3-JS; their plain
+// counterparts leave that code out (it costs the run-time-scheme and ROE
+// kernels 15-20 % even on grids without walls: more registers, more spills).
+enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2, SCH_NN = 3, SCH_GENERAL_EXT = 4, SCH_ROE_EXT = 5 };
+constexpr bool sch_general(int s) { return s == SCH_GENERAL || s == SCH_GENERAL_EXT; }
+constexpr bool sch_roe(int s) { return s == SCH_ROE || s == SCH_ROE_EXT; }
+constexpr bool sch_ext(int s) { return s == SCH_GENERAL_EXT || s == SCH_ROE_EXT || s == SCH_NN; }
 
 // Flux-splitting face flux of the ROE setup (Section 3.3, Flux-Splitting
 // approach; Section 5): Roe average of the two cells beside the face, the
@@ -267,7 +273,7 @@ enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2, SCH_NN = 3 };
 //   L X = [(s + d) / 2, X_0 - s, X_t1 - u_t1 X_0, X_t2 - u_t2 X_0, (s - d) / 2],
 //   R G: mass = G0 + G1 + G4 =: S, momentum u S + c n (G4 - G0) + t1 G2 + t2 G3,
 //        energy H (G0 + G4) + u_n c (G4 - G0) + |u|^2 / 2 G1 + u_t1 G2 + u_t2 G3.
-template <typename T, int D, typename Val>
+template <typename T, int D, bool EXT, typename Val>
 __device__ __forceinline__ void fs_flux(const Val& val, const Gas<T>& g, int recon, T F[5]) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   // Roe average
@@ -324,7 +330,7 @@ __device__ __forceinline__ void fs_flux(const Val& val, const Gas<T>& g, int rec
   T Gh[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    if (recon == 2) {  // WENO3-JS: G+ from cells -1..1, G- from cells 2..0
+    if (EXT && recon == 2) {  // WENO3-JS: G+ from cells -1..1, G- from cells 2..0
       if constexpr (sizeof(T) == 4) {
         const float2 r = weno3_pair(make_float2(Pp[k][1], Pm[k][1]), make_float2(Pp[k][2], Pm[k][2]),
                                     make_float2(Pp[k][3], Pm[k][3]), g.eps);
@@ -355,8 +361,9 @@ __device__ __forceinline__ void fs_flux(const Val& val, const Gas<T>& g, int rec
 // Net flux NF = F^d - F through the face between the cell at shared-memory
 // position (x0, y0, plane 0) and its neighbour along D.
 // SCH_DEFAULT: the default scheme (WENO5-JS, HLLC, Einfeldt speeds) compiled
-// alone; SCH_GENERAL: the Table 2 Godunov variants chosen at run time from g;
-// SCH_ROE: the flux-splitting ROE setup (reconstruction chosen from g);
+// alone; SCH_GENERAL(_EXT): the Table 2 Godunov variants chosen at run time
+// from g; SCH_ROE(_EXT): the flux-splitting ROE setup (reconstruction chosen
+// from g); the _EXT forms add WENO3-JS (and walls, in the plane fetch);
 // SCH_NN: the Rusanov-NN flux (Section 7.4; reconstruction chosen from g),
 // a kernel family of its own because the network's hidden layers need far
 // more registers than the other fluxes.
@@ -371,12 +378,12 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
     return R.at(c, x0 + x, y0 + y, e);
   };
   T F[5];
-  if constexpr (SCH == SCH_ROE) {
-    fs_flux<T, D>([&](int c, int n) { return val(c, n, 0, 0); }, g, recon, F);
+  if constexpr (sch_roe(SCH)) {
+    fs_flux<T, D, sch_ext(SCH)>([&](int c, int n) { return val(c, n, 0, 0); }, g, recon, F);
   } else {
   // WENO5-JS left / right states of each primitive component (Section 3.3)
   T Wm[5], Wp[5];
-  if ((SCH == SCH_GENERAL || SCH == SCH_NN) && recon == 2) {
+  if (sch_ext(SCH) && recon == 2) {
     // WENO3-JS: cells -1, 0, 1 (left state) and 2, 1, 0 (right state)
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -416,7 +423,7 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
       for (int c = 0; c < 5; ++c) Wp[c] = val(c, 1, 0, 0);
     }
   }
-  if constexpr (SCH == SCH_GENERAL) riemann_flux<T, D>(Wm, Wp, g, F);
+  if constexpr (sch_general(SCH)) riemann_flux<T, D>(Wm, Wp, g, F);
   else if constexpr (SCH == SCH_NN) rusanov_nn<T, D>(Wm, Wp, g, F);
   else hllc<T, D>(Wm, Wp, g, F, 0);
   }
@@ -544,7 +551,7 @@ template <typename T, int DIM, bool VISC, int BX, int BY, int SCH>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& g, int bx, int by, int bz,
                                            T* smem) {
   using G = Geo<BX, BY, DIM, VISC>;
-  constexpr bool WALLS = SCH != SCH_DEFAULT;
+  constexpr bool WALLS = sch_ext(SCH);
   T* ring = smem;
   T* Fx = ring + G::RING * G::PLANE;      // [5][BY][BX+1]
   T* Fy = Fx + 5 * G::NFX;                // [5][BY+1][BX]

@@ -51,6 +51,8 @@ const StageVariant<float>* stage_variants<float>(int* count) {
     v.insert(v.end(), roe, roe + ng);
     const StageVariant<float>* nn = nn_variants_f32(&ng);
     v.insert(v.end(), nn, nn + ng);
+    const StageVariant<float>* ext = ext_variants_f32(&ng);
+    v.insert(v.end(), ext, ext + ng);
     return v;
   }();
   *count = (int)table.size();

@@ -33,6 +33,8 @@ const StageVariant<double>* stage_variants<double>(int* count) {
     v.insert(v.end(), roe, roe + ng);
     const StageVariant<double>* nn = nn_variants_f64(&ng);
     v.insert(v.end(), nn, nn + ng);
+    const StageVariant<double>* ext = ext_variants_f64(&ng);
+    v.insert(v.end(), ext, ext + ng);
     return v;
   }();
   *count = (int)table.size();

@@ -25,7 +25,7 @@ struct StageVariant {
   cudaError_t (*launch_batch)(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
                               int* flag, int grid, cudaStream_t s);
   int threads;
-  int scheme;    // SCH_DEFAULT, SCH_GENERAL (run-time Table 2 choice), SCH_ROE or SCH_NN
+  int scheme;    // SCH_DEFAULT, SCH_GENERAL (run-time Table 2 choice), SCH_ROE, SCH_NN or an _EXT form
   int minb;      // CTAs per SM the register allocation was bounded for
 };
 
@@ -33,14 +33,18 @@ struct StageVariant {
 template <typename T>
 const StageVariant<T>* stage_variants(int* count);
 
-// The run-time-scheme kernels (SCH_GENERAL) and the flux-splitting kernels
-// (SCH_ROE), in their own translation units (stage_*_gen.cu, stage_*_roe.cu)
-// so that they compile in parallel with the default ones.
+// The run-time-scheme kernels (SCH_GENERAL), the flux-splitting kernels
+// (SCH_ROE), the Rusanov-NN kernels (SCH_NN) and the extended forms of the
+// first two (walls, WENO3-JS), in their own translation units
+// (stage_*_gen.cu, stage_*_roe.cu, stage_*_nn.cu, stage_*_ext.cu) so that they
+// compile in parallel with the default ones.
 const StageVariant<float>* general_variants_f32(int* count);
 const StageVariant<double>* general_variants_f64(int* count);
 const StageVariant<float>* roe_variants_f32(int* count);
 const StageVariant<double>* roe_variants_f64(int* count);
 const StageVariant<float>* nn_variants_f32(int* count);
 const StageVariant<double>* nn_variants_f64(int* count);
+const StageVariant<float>* ext_variants_f32(int* count);
+const StageVariant<double>* ext_variants_f64(int* count);
 
 }  // namespace jf
