@@ -63,6 +63,14 @@ struct VGeo {
   static constexpr int MPX = BX + 2 * MX, MPY = BY + 2 * MY, MPZ = BZ + 2 * MZ, MCS = MPX * MPY * MPZ;
   static constexpr int NCELL = BX * BY * BZ;
   static constexpr int NT = NCELL;
+  // 1D / 2D: cotangents accumulate over the box and a 5-cell halo (every cell
+  // a face's stencil reaches), with no ownership test per addition; boxes
+  // near a non-periodic boundary fold ghost cells onto the cells they copy
+  // afterwards.  3D: the halo would not fit in shared memory, so additions
+  // test ownership and only box cells are held.
+  static constexpr bool EXT = DIM <= 2;
+  static constexpr int AX = EXT ? 5 : 0, AY = EXT && DIM >= 2 ? 5 : 0;
+  static constexpr int APX = BX + 2 * AX, APY = BY + 2 * AY, ACS = EXT ? APX * APY : NCELL;
   static_assert(DIM >= 2 || BY == 1, "1D boxes are one row");
   static_assert(DIM == 3 || BZ == 1, "1D/2D boxes are one plane");
 };
@@ -70,7 +78,7 @@ struct VGeo {
 template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
 constexpr size_t vjp_smem_bytes() {
   using G = VGeo<BX, BY, BZ, DIM, VISC>;
-  return sizeof(T) * (size_t)(G::NCW * G::CS + 5 * G::MCS + 6 * G::NCELL);
+  return sizeof(T) * (size_t)(G::NCW * G::CS + 5 * G::MCS + 6 * G::ACS);
 }
 
 // Position along the axes of a face frame: offset n along the normal d, a
@@ -103,7 +111,7 @@ struct VTile {
   using G = VGeo<BX, BY, BZ, DIM, VISC>;
   const T* W;   // [NCW][PZ][PY][PX], box cell (0, 0, 0) at (HX, HY, HZ)
   const T* M;   // [5][MPZ][MPY][MPX]
-  T* acc;       // [6][BZ][BY][BX]
+  T* acc;       // [6][APY][APX] (1D / 2D, box cell (0, 0) at (AX, AY)) or [6][BZ][BY][BX] (3D)
   int g0[3], n[3], per[3];
 
   // coordinates along inactive axes are always 0: fold them at compile time
@@ -125,6 +133,11 @@ struct VTile {
     return (t >= 0 && t < B) ? t : -1;
   }
   __device__ __forceinline__ void add(int c, int x, int y, int z, T v) const {
+    if constexpr (G::EXT) {
+      const int yy = DIM >= 2 ? y : 0;
+      atomicAdd(acc + c * G::ACS + (yy + G::AY) * G::APX + x + G::AX, v);
+      return;
+    }
     const int tx = owner(x, g0[0], n[0], per[0], BX);
     const int ty = DIM >= 2 ? owner(y, g0[1], n[1], per[1], BY) : 0;
     const int tz = DIM == 3 ? owner(z, g0[2], n[2], per[2], BZ) : 0;
@@ -349,7 +362,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
 #pragma unroll
     for (int c = 0; c < 5; ++c) Mb[c * G::MCS + t] = ghost ? T(0) : A.s_in * A.lam[q + c * A.N];
   }
-  for (int t = tid; t < 6 * G::NCELL; t += G::NT) acc[t] = T(0);
+  for (int t = tid; t < 6 * G::ACS; t += G::NT) acc[t] = T(0);
   __syncthreads();
 
   VTile<T, DIM, VISC, BX, BY, BZ> V;
@@ -465,18 +478,45 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   }
   __syncthreads();
 
+  if constexpr (G::EXT) {
+    // ghost cells of a non-periodic axis pass their cotangents to the cell
+    // they copy (if it is in this box); everything else outside the box (and
+    // beyond the grid on a periodic axis) belongs to another box, which
+    // evaluates the same faces.  Only boxes within reach of such a boundary
+    // (or ragged against it) have ghosts to fold; the test is uniform per CTA.
+    bool fold = false;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int B = a == 0 ? BX : BY, h = a == 0 ? G::AX : G::AY;
+      fold |= !A.periodic[a] && (g0[a] - h < 0 || g0[a] + B + h > A.n[a]);
+    }
+    if (fold) {
+      for (int t = tid; t < G::ACS; t += G::NT) {
+        const int lx = t % G::APX - G::AX, ly = t / G::APX - G::AY;
+        const int ox = V.owner(lx, g0[0], A.n[0], A.periodic[0], BX);
+        const int oy = DIM >= 2 ? V.owner(ly, g0[1], A.n[1], A.periodic[1], BY) : 0;
+        if (ox >= 0 && oy >= 0 && (ox != lx || oy != ly)) {
+          const int to = (oy + G::AY) * G::APX + ox + G::AX;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) atomicAdd(acc + c * G::ACS + to, acc[c * G::ACS + t]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+
   // cells: cotangent of W (+T) -> cotangent of U, then the stage combination
   const int tx = tid % BX, ty = (tid / BX) % BY, tz = tid / (BX * BY);
   const int gx = g0[0] + tx, gy = g0[1] + ty, gz = g0[2] + tz;
   if (gx < A.n[0] && gy < A.n[1] && gz < A.n[2]) {
     const T r = V.w(0, tx, ty, tz), u = V.w(1, tx, ty, tz), v = V.w(2, tx, ty, tz), w = V.w(3, tx, ty, tz);
     const T p = V.w(4, tx, ty, tz);
-    const int cell = (tz * BY + ty) * BX + tx;
-    T br = acc[cell], bu = acc[G::NCELL + cell], bv = acc[2 * G::NCELL + cell], bw = acc[3 * G::NCELL + cell];
-    T bp = acc[4 * G::NCELL + cell];
+    const int cell = G::EXT ? (ty + G::AY) * G::APX + tx + G::AX : (tz * BY + ty) * BX + tx;
+    T br = acc[cell], bu = acc[G::ACS + cell], bv = acc[2 * G::ACS + cell], bw = acc[3 * G::ACS + cell];
+    T bp = acc[4 * G::ACS + cell];
     const T inv = trcp(r);
     if (VISC) {
-      const T bT = acc[5 * G::NCELL + cell];
+      const T bT = acc[5 * G::ACS + cell];
       const T Tc = V.w(5, tx, ty, tz);
       br -= bT * Tc * inv;  // T = p / (rho R)
       bp += bT * Tc * trcp(p);
