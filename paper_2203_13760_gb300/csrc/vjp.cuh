@@ -71,6 +71,12 @@ struct VGeo {
   static constexpr bool EXT = DIM <= 2;
   static constexpr int AX = EXT ? 5 : 0, AY = EXT && DIM >= 2 ? 5 : 0;
   static constexpr int APX = BX + 2 * AX, APY = BY + 2 * AY, ACS = EXT ? APX * APY : NCELL;
+  // 2D viscous: the tangential C4 stencil (DC4 along the tangent at the cells
+  // -1..2 along the normal, then RC4 to the face) is separable, so a face
+  // adds its cotangents of the four cell-centre derivatives (slots
+  // d * 2 + k: k = 0 for du_n/de, 1 for du_e/de) and one gather pass applies
+  // the transposed DC4 afterwards: 8 instead of 32 additions per face.
+  static constexpr int NCB = EXT && DIM == 2 && VISC ? 4 : 0;
   static_assert(DIM >= 2 || BY == 1, "1D boxes are one row");
   static_assert(DIM == 3 || BZ == 1, "1D/2D boxes are one plane");
 };
@@ -78,7 +84,7 @@ struct VGeo {
 template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
 constexpr size_t vjp_smem_bytes() {
   using G = VGeo<BX, BY, BZ, DIM, VISC>;
-  return sizeof(T) * (size_t)(G::NCW * G::CS + 5 * G::MCS + 6 * G::ACS);
+  return sizeof(T) * (size_t)(G::NCW * G::CS + 5 * G::MCS + (6 + G::NCB) * G::ACS);
 }
 
 // Position along the axes of a face frame: offset n along the normal d, a
@@ -112,6 +118,7 @@ struct VTile {
   const T* W;   // [NCW][PZ][PY][PX], box cell (0, 0, 0) at (HX, HY, HZ)
   const T* M;   // [5][MPZ][MPY][MPX]
   T* acc;       // [6][APY][APX] (1D / 2D, box cell (0, 0) at (AX, AY)) or [6][BZ][BY][BX] (3D)
+  T* cb;        // [NCB][APY][APX]: cotangents of cell-centre tangential derivatives (2D viscous)
   int g0[3], n[3], per[3];
 
   // coordinates along inactive axes are always 0: fold them at compile time
@@ -142,6 +149,9 @@ struct VTile {
     const int ty = DIM >= 2 ? owner(y, g0[1], n[1], per[1], BY) : 0;
     const int tz = DIM == 3 ? owner(z, g0[2], n[2], per[2], BZ) : 0;
     if (tx >= 0 && ty >= 0 && tz >= 0) atomicAdd(acc + ((c * BZ + tz) * BY + ty) * BX + tx, v);
+  }
+  __device__ __forceinline__ void add_cb(int slot, int x, int y, T v) const {
+    atomicAdd(cb + slot * G::ACS + (y + G::AY) * G::APX + x + G::AX, v);
   }
 };
 
@@ -305,13 +315,20 @@ __device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY, 
     for (int k = 0; k < 2; ++k) {
       const int c = k == 0 ? comp[0] : comp[1 + j];
       const T gb = (k == 0 ? g.mu * taub[1 + j] : divb) * he[j];
+      if constexpr (VGeo<BX, BY, BZ, DIM, VISC>::NCB > 0) {
+        // centre-derivative cotangents; the gather pass spreads them along the tangent
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 4; ++q)
+          V.add_cb(F.d * 2 + k, p[0] + F.pick(0, q - 1, 0, 0), p[1] + F.pick(1, q - 1, 0, 0), gb * rc[q]);
+      } else {
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const T val = gb * rc[q] * dcw[o];
-          if (j == 0) put(c, q - 1, dco[o], 0, val); else put(c, q - 1, 0, dco[o], val);
-        }
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const T val = gb * rc[q] * dcw[o];
+            if (j == 0) put(c, q - 1, dco[o], 0, val); else put(c, q - 1, 0, dco[o], val);
+          }
+      }
     }
   }
 }
@@ -325,6 +342,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   T* Wb = reinterpret_cast<T*>(smem_raw);
   T* Mb = Wb + G::NCW * G::CS;
   T* acc = Mb + 5 * G::MCS;
+  T* cbuf = acc + 6 * G::ACS;
   const int g0[3] = {(int)blockIdx.x * BX, (int)blockIdx.y * BY, (int)blockIdx.z * BZ};
   const int tid = threadIdx.x;
 
@@ -362,13 +380,14 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
 #pragma unroll
     for (int c = 0; c < 5; ++c) Mb[c * G::MCS + t] = ghost ? T(0) : A.s_in * A.lam[q + c * A.N];
   }
-  for (int t = tid; t < 6 * G::ACS; t += G::NT) acc[t] = T(0);
+  for (int t = tid; t < (6 + G::NCB) * G::ACS; t += G::NT) acc[t] = T(0);
   __syncthreads();
 
   VTile<T, DIM, VISC, BX, BY, BZ> V;
   V.W = Wb;
   V.M = Mb;
   V.acc = acc;
+  V.cb = cbuf;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     V.g0[a] = g0[a];
@@ -477,6 +496,31 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     }
   }
   __syncthreads();
+
+  if constexpr (G::NCB > 0) {
+    // transposed DC4 along the tangent: cell Y receives
+    // sum_o dcw[o] cb(Y - dco[o] e) (dco = -2, -1, 1, 2; dcw = (1, -8, 8, -1) / 12).
+    // Slots: x faces (tangent y) 0: du/dy -> u, 1: dv/dy -> v;
+    // y faces (tangent x) 2: dv/dx -> v, 3: du/dx -> u.
+    for (int t = tid; t < G::ACS; t += G::NT) {
+      const int lx = t % G::APX, ly = t / G::APX;
+      // (cells beyond the accumulation region hold no cotangent)
+      auto spread = [&](int slot, int step, int pos, int len) {
+        const T* s = cbuf + slot * G::ACS + t;
+        T v = T(0);
+        if (pos + 2 < len) v += (T(1) / T(12)) * s[2 * step];
+        if (pos + 1 < len) v += (-T(8) / T(12)) * s[step];
+        if (pos >= 1) v += (T(8) / T(12)) * s[-step];
+        if (pos >= 2) v += (-T(1) / T(12)) * s[-2 * step];
+        return v;
+      };
+      const T du = spread(0, G::APX, ly, G::APY) + spread(3, 1, lx, G::APX);
+      const T dv = spread(1, G::APX, ly, G::APY) + spread(2, 1, lx, G::APX);
+      acc[G::ACS + t] += du;
+      acc[2 * G::ACS + t] += dv;
+    }
+    __syncthreads();
+  }
 
   if constexpr (G::EXT) {
     // ghost cells of a non-periodic axis pass their cotangents to the cell
