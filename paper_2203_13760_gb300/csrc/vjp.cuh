@@ -174,12 +174,21 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY, 
   };
   const int cn = 1 + F.d, c1 = 1 + F.t1, c2 = 1 + F.t2;  // physical components of the frame velocities
   auto phys = [&](int c) { return c == 1 ? cn : (c == 2 ? c1 : (c == 3 ? c2 : c)); };
+  constexpr bool PACKED = std::is_same<T, float>::value;  // FP32: both sides in FP32x2 lanes
   T Wm[5], Wp[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     const int pc = phys(c);
-    Wm[c] = weno5(at(pc, -2), at(pc, -1), at(pc, 0), at(pc, 1), at(pc, 2), g.eps);
-    Wp[c] = weno5(at(pc, 3), at(pc, 2), at(pc, 1), at(pc, 0), at(pc, -1), g.eps);
+    if constexpr (PACKED) {
+      const float2 r = weno5_pair(make_float2(at(pc, -2), at(pc, 3)), make_float2(at(pc, -1), at(pc, 2)),
+                                  make_float2(at(pc, 0), at(pc, 1)), make_float2(at(pc, 1), at(pc, 0)),
+                                  make_float2(at(pc, 2), at(pc, -1)), g.eps);
+      Wm[c] = r.x;
+      Wp[c] = r.y;
+    } else {
+      Wm[c] = weno5(at(pc, -2), at(pc, -1), at(pc, 0), at(pc, 1), at(pc, 2), g.eps);
+      Wp[c] = weno5(at(pc, 3), at(pc, 2), at(pc, 1), at(pc, 0), at(pc, -1), g.eps);
+    }
   }
   bool fm = false, fp = false;
   if (g.safe) {
@@ -206,6 +215,19 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY, 
 #pragma unroll
     for (int q = 0; q < 6; ++q) v[q] = at(pc, q - 2);
     T vb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    if constexpr (PACKED) {
+      float2 t2[5];
+      weno5_vjp_pair(make_float2(v[0], v[5]), make_float2(v[1], v[4]), make_float2(v[2], v[3]),
+                     make_float2(v[3], v[2]), make_float2(v[4], v[1]), g.eps,
+                     make_float2(fm ? 0.0f : bm, fp ? 0.0f : bp), t2);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        vb[q] += t2[q].x;
+        vb[5 - q] += t2[q].y;
+      }
+      if (fm) vb[2] += bm;
+      if (fp) vb[3] += bp;
+    } else {
     if (fm) {
       vb[2] += bm;
     } else {
@@ -221,6 +243,7 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY, 
       weno5_vjp(v[5], v[4], v[3], v[2], v[1], g.eps, bp, t);
 #pragma unroll
       for (int q = 0; q < 5; ++q) vb[5 - q] += t[q];
+    }
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q)

@@ -48,6 +48,62 @@ JF_HD void weno5_vjp(T v0, T v1, T v2, T v3, T v4, T eps, T yb, T vb[5]) {
   vb[4] += db2 + eb2 - sixth * qb2;
 }
 
+#ifdef __CUDACC__
+// weno5_vjp for two stencils at once in packed FP32x2 arithmetic (lane x:
+// v0..v4 = v[i-2..i+2] -> v^-, lane y: the mirrored stencil -> v^+, as in
+// weno5_pair): vb[k] = yb * dy/dv_k per lane (assigned, not added).  The
+// same formulas as weno5_vjp, grouped into fused multiply-adds.
+__device__ __forceinline__ void weno5_vjp_pair(float2 v0, float2 v1, float2 v2, float2 v3, float2 v4, float eps,
+                                               float2 yb, float2 vb[5]) {
+  auto c = [](float x) { return make_float2(x, x); };
+  auto rcp2 = [](float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); };
+  const float2 q0 = __ffma2_rn(c(11.0f / 6.0f), v2, __ffma2_rn(c(-7.0f / 6.0f), v1, __fmul2_rn(c(2.0f / 6.0f), v0)));
+  const float2 q1 = __ffma2_rn(c(2.0f / 6.0f), v3, __ffma2_rn(c(5.0f / 6.0f), v2, __fmul2_rn(c(-1.0f / 6.0f), v1)));
+  const float2 q2 = __ffma2_rn(c(-1.0f / 6.0f), v4, __ffma2_rn(c(5.0f / 6.0f), v3, __fmul2_rn(c(2.0f / 6.0f), v2)));
+  const float2 d0 = __ffma2_rn(c(-2.0f), v1, __fadd2_rn(v0, v2));
+  const float2 e0 = __ffma2_rn(c(3.0f), v2, __ffma2_rn(c(-4.0f), v1, v0));
+  const float2 d1 = __ffma2_rn(c(-2.0f), v2, __fadd2_rn(v1, v3));
+  const float2 e1 = __ffma2_rn(c(-1.0f), v3, v1);
+  const float2 d2 = __ffma2_rn(c(-2.0f), v3, __fadd2_rn(v2, v4));
+  const float2 e2 = __ffma2_rn(c(3.0f), v2, __ffma2_rn(c(-4.0f), v3, v4));
+  const float2 k13 = c(13.0f / 12.0f), kq = c(0.25f), ke = c(eps);
+  const float2 t0 = __ffma2_rn(__fmul2_rn(k13, d0), d0, __ffma2_rn(__fmul2_rn(kq, e0), e0, ke));
+  const float2 t1 = __ffma2_rn(__fmul2_rn(k13, d1), d1, __ffma2_rn(__fmul2_rn(kq, e1), e1, ke));
+  const float2 t2 = __ffma2_rn(__fmul2_rn(k13, d2), d2, __ffma2_rn(__fmul2_rn(kq, e2), e2, ke));
+  const float2 r0 = rcp2(t0), r1 = rcp2(t1), r2 = rcp2(t2);
+  const float2 a0 = __fmul2_rn(__fmul2_rn(c(0.1f), r0), r0);
+  const float2 a1 = __fmul2_rn(__fmul2_rn(c(0.6f), r1), r1);
+  const float2 a2 = __fmul2_rn(__fmul2_rn(c(0.3f), r2), r2);
+  const float2 inv = rcp2(__fadd2_rn(__fadd2_rn(a0, a1), a2));
+  const float2 y = __fmul2_rn(__ffma2_rn(a2, q2, __ffma2_rn(a1, q1, __fmul2_rn(a0, q0))), inv);
+  const float2 s = __fmul2_rn(yb, inv);
+  const float2 qb0 = __fmul2_rn(s, a0), qb1 = __fmul2_rn(s, a1), qb2 = __fmul2_rn(s, a2);
+  // d alpha_k / d t_k = -2 alpha_k / t_k: tb_k = -2 qb_k (q_k - y) r_k
+  const float2 m1 = c(-1.0f), m2 = c(-2.0f);
+  const float2 tb0 = __fmul2_rn(__fmul2_rn(m2, qb0), __fmul2_rn(__ffma2_rn(m1, y, q0), r0));
+  const float2 tb1 = __fmul2_rn(__fmul2_rn(m2, qb1), __fmul2_rn(__ffma2_rn(m1, y, q1), r1));
+  const float2 tb2 = __fmul2_rn(__fmul2_rn(m2, qb2), __fmul2_rn(__ffma2_rn(m1, y, q2), r2));
+  const float2 k26 = c(13.0f / 6.0f), kh = c(0.5f);
+  const float2 db0 = __fmul2_rn(__fmul2_rn(k26, d0), tb0), eb0 = __fmul2_rn(__fmul2_rn(kh, e0), tb0);
+  const float2 db1 = __fmul2_rn(__fmul2_rn(k26, d1), tb1), eb1 = __fmul2_rn(__fmul2_rn(kh, e1), tb1);
+  const float2 db2 = __fmul2_rn(__fmul2_rn(k26, d2), tb2), eb2 = __fmul2_rn(__fmul2_rn(kh, e2), tb2);
+  vb[0] = __ffma2_rn(c(2.0f / 6.0f), qb0, __fadd2_rn(db0, eb0));
+  vb[1] = __ffma2_rn(c(-1.0f / 6.0f), qb1,
+                     __ffma2_rn(c(-7.0f / 6.0f), qb0,
+                                __fadd2_rn(__fadd2_rn(db1, eb1), __ffma2_rn(c(-4.0f), eb0, __fmul2_rn(m2, db0)))));
+  vb[2] = __ffma2_rn(c(2.0f / 6.0f), qb2,
+                     __ffma2_rn(c(5.0f / 6.0f), qb1,
+                                __ffma2_rn(c(11.0f / 6.0f), qb0,
+                                           __ffma2_rn(c(3.0f), eb2,
+                                                      __fadd2_rn(__ffma2_rn(m2, db1, db2),
+                                                                 __ffma2_rn(c(3.0f), eb0, db0))))));
+  vb[3] = __ffma2_rn(c(5.0f / 6.0f), qb2,
+                     __ffma2_rn(c(2.0f / 6.0f), qb1,
+                                __ffma2_rn(c(-4.0f), eb2, __ffma2_rn(m2, db2, __ffma2_rn(m1, eb1, db1)))));
+  vb[4] = __ffma2_rn(c(-1.0f / 6.0f), qb2, __fadd2_rn(db2, eb2));
+}
+#endif
+
 // hllc<T, D>: given Fb = dLoss/dF, set WLb, WRb = dLoss/dWL, dLoss/dWR.
 template <typename T, int D>
 JF_HD void hllc_vjp(const T WL[5], const T WR[5], const Gas<T>& g, const T Fb[5], T WLb[5],
