@@ -212,6 +212,25 @@ jf_status jf_rk3_run(jf_handle h, void* U_inout, int nsteps, const double* dt_de
 jf_status jf_rk3_step_vjp(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out, void* lam_in,
                           void* stream);
 
+/* One fixed-dt TVD-RK3 step of U_inout in place (the same launches and
+ * result as jf_rk3_step with dt_dev), keeping the stage states: U1_out and
+ * U2_out (device arrays shaped like U, caller-owned, distinct from U_inout and
+ * from each other) receive U1 = Un + dt L(Un) and
+ * U2 = 3/4 Un + 1/4 (U1 + dt L(U1)) (Section 3.1, TVD-RK3).  They let the
+ * adjoint of the step skip its recomputation (jf_rk3_step_vjp_stages).
+ * JF_ERR_UNSUPPORTED unless the scheme's integrator is TVD-RK3. */
+jf_status jf_rk3_step_keep(jf_handle h, void* U_inout, const double* dt_dev, void* U1_out, void* U2_out,
+                           void* stream);
+
+/* jf_rk3_step_vjp from the stage states of the step (Un, U1, U2 as kept by
+ * jf_rk3_step_keep; not modified) instead of recomputing them: the three
+ * stage-VJP launches only.  lam_in must differ from every other array.
+ * JF_ERR_UNSUPPORTED unless the scheme is the default one (HLLC, Einfeldt
+ * speeds, WENO5-JS, TVD-RK3) on a grid without walls; the other schemes use
+ * jf_rk3_step_vjp. */
+jf_status jf_rk3_step_vjp_stages(jf_handle h, const void* Un, const void* U1, const void* U2, const double* dt_dev,
+                                 const void* lam_out, void* lam_in, void* stream);
+
 /* jf_rk3_step_vjp for a handle whose flux is JF_FLUX_RUSANOV_NN, adding the
  * gradient of the step with respect to the network parameters (Section 7.4:
  * the learned dissipation trained through the solver):

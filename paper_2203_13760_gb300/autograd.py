@@ -8,7 +8,9 @@ a fixed step).
                               n fixed-dt steps whose backward pass recomputes
                               each segment of ``ckpt_every`` steps from a stored
                               checkpoint (memory: n / ckpt_every + ckpt_every
-                              states instead of n).
+                              states instead of n; with the default scheme the
+                              replay keeps each step's two stage states for
+                              jf_rk3_step_vjp_stages, 3 ckpt_every states).
 ``density_l2(solver, U, target)``
                               sum_cells (rho - target)^2 dV (jf_loss_density_l2)
                               with its gradient.
@@ -70,16 +72,36 @@ class _Rollout(torch.autograd.Function):
         s, n, c = ctx.solver, ctx.nsteps, ctx.ckpt_every
         lam = grad.contiguous().clone()
         lam_next = torch.empty_like(lam)
+        # the default scheme keeps the stage states of the segment's replay, so
+        # the step adjoints do not recompute them (memory: 3 states per step)
+        keep = s.supports_stage_vjp()
         for seg in reversed(range(len(ctx.ckpts))):
             start = seg * c
             length = min(c, n - start)
             states = [ctx.ckpts[seg]]
-            for _ in range(length - 1):
-                nxt = states[-1].clone()
-                s.rk3_step(nxt, dt)
-                states.append(nxt)
+            stages = []
+            for k in range(length):
+                if keep:
+                    U1, U2 = s.empty(), s.empty()
+                    if k < length - 1:
+                        nxt = states[-1].clone()
+                        s.rk3_step_keep(nxt, dt, U1, U2)
+                        states.append(nxt)
+                    else:  # the last step's result is not needed, only its stages
+                        s.stage(states[k], None, U1, 0.0, 1.0, dt)
+                        s.stage(U1, states[k], U2, 0.75, 0.25, dt)
+                    stages.append((U1, U2))
+                elif k < length - 1:
+                    nxt = states[-1].clone()
+                    s.rk3_step(nxt, dt)
+                    states.append(nxt)
             for k in reversed(range(length)):
-                s.rk3_step_vjp(states[k], dt, lam, lam_next)
+                if keep:
+                    U1, U2 = stages[k]
+                    s.rk3_step_vjp_stages(states[k], U1, U2, dt, lam, lam_next)
+                    stages[k] = None
+                else:
+                    s.rk3_step_vjp(states[k], dt, lam, lam_next)
                 lam, lam_next = lam_next, lam
         ctx.ckpts = None
         return lam, None, None, None, None

@@ -7,49 +7,35 @@
 //   l2 = V(U2, 2/3 l3);  l1 = V(U1, 1/4 l2);
 //   ln = 1/3 l3 + 3/4 l2 + V(Un, l1).
 // U1 and U2 are recomputed with the forward stage kernel (dt fixed, not
-// differentiated); l2 and l1 live in two adjoint buffers allocated at the
-// first call of a handle.
+// differentiated), or taken from the caller (jf_rk3_step_vjp_stages, after
+// jf_rk3_step_keep kept them); l2 and l1 live in two adjoint buffers
+// allocated at the first call of a handle.
 #include "jf_internal.h"
 #include "vjp_inst.cuh"
 
 namespace jf {
 
-template <typename T>
-jf_status vjp_impl(jf_ctx* h, const void* Un, const double* dt, const void* lam_out, void* lam_in,
-                   cudaStream_t s) {
-  const bool visc = dissipative(h->gas, h->scheme);
+// the configurations of the fused stage-VJP kernel: the default scheme
+// (HLLC, Einfeldt speeds, WENO5-JS, TVD-RK3) without walls
+static bool fused_vjp(const jf_ctx* h) {
   const jf_scheme& sc = h->scheme;
-  if (sc.flux != JF_FLUX_HLLC || sc.recon != JF_WENO5_JS || sc.signal_speed != JF_EINFELDT ||
-      sc.integrator != JF_RK3 || has_walls(h->grid)) {
-    // the run-time schemes: the per-face adjoint of vjp_gen.cu
-    std::string why;
-    if (!general_vjp_supported(h, &why)) {
-      set_error(h, "jf_rk3_step_vjp: " + why);
-      return JF_ERR_UNSUPPORTED;
-    }
-    return general_vjp<T>(h, Un, dt, lam_out, lam_in, nullptr, s);
-  }
-  VjpLaunch<T> L = vjp_launcher<T>(h->dim, visc);
+  return sc.flux == JF_FLUX_HLLC && sc.recon == JF_WENO5_JS && sc.signal_speed == JF_EINFELDT &&
+         sc.integrator == JF_RK3 && !has_walls(h->grid);
+}
+
+// The three stage-VJP launches of one step, from the stage states U0, U1, U2.
+template <typename T>
+jf_status vjp_backward(jf_ctx* h, const T* U0, const T* U1, const T* U2, const double* dt, const void* lam_out,
+                       void* lam_in, cudaStream_t s) {
+  VjpLaunch<T> L = vjp_launcher<T>(h->dim, dissipative(h->gas, h->scheme));
   if (!L) { set_error(h, "jf_rk3_step_vjp: no adjoint kernel for this configuration"); return JF_ERR_UNSUPPORTED; }
   for (int i = 0; i < 2; ++i)
     if (!h->adj[i]) {
       cudaError_t e = cudaMalloc(&h->adj[i], 5 * h->N * sizeof(T));
       if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_vjp: adjoint buffers");
     }
-  const T* U0 = static_cast<const T*>(Un);
-  T* U1 = static_cast<T*>(h->stage[0]);
-  T* U2 = static_cast<T*>(h->stage[1]);
   T* l2 = static_cast<T*>(h->adj[0]);
   T* l1 = static_cast<T*>(h->adj[1]);
-  // forward recompute of the stage states
-  StageArgs<T> A = base_args<T>(h);
-  A.dt = dt;
-  A.Us = U0; A.Un = nullptr; A.out = U1; A.a = T(0); A.b = T(1);
-  jf_status st = launch<T>(h, A, s);
-  if (st != JF_OK) return st;
-  A.Us = U1; A.Un = U0; A.out = U2; A.a = T(0.75); A.b = T(0.25);
-  if ((st = launch<T>(h, A, s)) != JF_OK) return st;
-  // backward
   VjpArgs<T> V;
   V.n[0] = h->grid.nx;
   V.n[1] = h->grid.ny;
@@ -76,6 +62,54 @@ jf_status vjp_impl(jf_ctx* h, const void* Un, const double* dt, const void* lam_
   return JF_OK;
 }
 
+// One fixed-dt TVD-RK3 step of U in place with the stage states written to
+// U1o and U2o (the launches of step_impl with other output buffers).
+template <typename T>
+jf_status step_keep(jf_ctx* h, void* U, const double* dt, void* U1o, void* U2o, cudaStream_t s) {
+  T* Un = static_cast<T*>(U);
+  T* U1 = static_cast<T*>(U1o);
+  T* U2 = static_cast<T*>(U2o);
+  StageArgs<T> A = base_args<T>(h);
+  A.dt = dt;
+  jf_status st;
+  A.Us = Un; A.Un = nullptr; A.out = U1; A.a = T(0); A.b = T(1);
+  if ((st = launch<T>(h, A, s)) != JF_OK) return st;
+  A.Us = U1; A.Un = Un; A.out = U2; A.a = T(0.75); A.b = T(0.25);
+  if ((st = launch<T>(h, A, s)) != JF_OK) return st;
+  A.Us = U2; A.Un = Un; A.out = Un; A.a = T(1.0 / 3.0); A.b = T(2.0 / 3.0);
+  return launch<T>(h, A, s);
+}
+
+template <typename T>
+jf_status vjp_impl(jf_ctx* h, const void* Un, const double* dt, const void* lam_out, void* lam_in,
+                   cudaStream_t s) {
+  if (!fused_vjp(h)) {
+    // the run-time schemes: the per-face adjoint of vjp_gen.cu
+    std::string why;
+    if (!general_vjp_supported(h, &why)) {
+      set_error(h, "jf_rk3_step_vjp: " + why);
+      return JF_ERR_UNSUPPORTED;
+    }
+    return general_vjp<T>(h, Un, dt, lam_out, lam_in, nullptr, s);
+  }
+  if (!vjp_launcher<T>(h->dim, dissipative(h->gas, h->scheme))) {
+    set_error(h, "jf_rk3_step_vjp: no adjoint kernel for this configuration");
+    return JF_ERR_UNSUPPORTED;
+  }
+  const T* U0 = static_cast<const T*>(Un);
+  T* U1 = static_cast<T*>(h->stage[0]);
+  T* U2 = static_cast<T*>(h->stage[1]);
+  // forward recompute of the stage states
+  StageArgs<T> A = base_args<T>(h);
+  A.dt = dt;
+  A.Us = U0; A.Un = nullptr; A.out = U1; A.a = T(0); A.b = T(1);
+  jf_status st = launch<T>(h, A, s);
+  if (st != JF_OK) return st;
+  A.Us = U1; A.Un = U0; A.out = U2; A.a = T(0.75); A.b = T(0.25);
+  if ((st = launch<T>(h, A, s)) != JF_OK) return st;
+  return vjp_backward<T>(h, U0, U1, U2, dt, lam_out, lam_in, s);
+}
+
 }  // namespace jf
 
 using namespace jf;
@@ -91,6 +125,42 @@ extern "C" jf_status jf_rk3_step_vjp(jf_handle h, const void* Un, const double* 
   return h->scheme.dtype == JF_F32
              ? vjp_impl<float>(h, Un, dt_dev, lam_out, lam_in, (cudaStream_t)stream)
              : vjp_impl<double>(h, Un, dt_dev, lam_out, lam_in, (cudaStream_t)stream);
+}
+
+extern "C" jf_status jf_rk3_step_keep(jf_handle h, void* U_inout, const double* dt_dev, void* U1_out, void* U2_out,
+                                      void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_rk3_step_keep: not a single-grid handle"); return JF_ERR_ARG; }
+  if (h->scheme.integrator != JF_RK3) {
+    set_error(h, "jf_rk3_step_keep: the scheme's integrator is not TVD-RK3");
+    return JF_ERR_UNSUPPORTED;
+  }
+  if (!U_inout || !dt_dev || !U1_out || !U2_out || !aligned16(U_inout) || !aligned16(U1_out) || !aligned16(U2_out) ||
+      U1_out == U_inout || U2_out == U_inout || U1_out == U2_out) {
+    set_error(h, "jf_rk3_step_keep: bad arguments (dt_dev is required; U, U1_out and U2_out must be distinct)");
+    return JF_ERR_ARG;
+  }
+  return h->scheme.dtype == JF_F32 ? step_keep<float>(h, U_inout, dt_dev, U1_out, U2_out, (cudaStream_t)stream)
+                                   : step_keep<double>(h, U_inout, dt_dev, U1_out, U2_out, (cudaStream_t)stream);
+}
+
+extern "C" jf_status jf_rk3_step_vjp_stages(jf_handle h, const void* Un, const void* U1, const void* U2,
+                                            const double* dt_dev, const void* lam_out, void* lam_in, void* stream) {
+  if (!h || h->kind != 0) { set_error(h, "jf_rk3_step_vjp_stages: not a single-grid handle"); return JF_ERR_ARG; }
+  if (!fused_vjp(h)) {
+    set_error(h, "jf_rk3_step_vjp_stages: only the default scheme (HLLC, Einfeldt, WENO5-JS, TVD-RK3) without walls");
+    return JF_ERR_UNSUPPORTED;
+  }
+  if (!Un || !U1 || !U2 || !dt_dev || !lam_out || !lam_in || !aligned16(Un) || !aligned16(U1) || !aligned16(U2) ||
+      !aligned16(lam_out) || !aligned16(lam_in) || lam_in == lam_out || lam_in == Un || lam_in == U1 ||
+      lam_in == U2) {
+    set_error(h, "jf_rk3_step_vjp_stages: bad arguments (dt_dev is required; lam_in must differ from the other arrays)");
+    return JF_ERR_ARG;
+  }
+  return h->scheme.dtype == JF_F32
+             ? vjp_backward<float>(h, static_cast<const float*>(Un), static_cast<const float*>(U1),
+                                   static_cast<const float*>(U2), dt_dev, lam_out, lam_in, (cudaStream_t)stream)
+             : vjp_backward<double>(h, static_cast<const double*>(Un), static_cast<const double*>(U1),
+                                    static_cast<const double*>(U2), dt_dev, lam_out, lam_in, (cudaStream_t)stream);
 }
 
 extern "C" jf_status jf_rk3_step_vjp_params(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out,

@@ -68,6 +68,8 @@ SIGNATURES = {
     "jf_rk3_run": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
     "jf_rk3_step_host": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP, _VP]),
     "jf_rk3_step_vjp": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jf_rk3_step_keep": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jf_rk3_step_vjp_stages": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_rk3_step_vjp_params": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_batch_step_vjp": (_I, [_VP, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                ctypes.POINTER(_VP), _VP, _VP]),
@@ -249,6 +251,29 @@ class Solver:
         lam_in = self.empty() if lam_in is None else lam_in
         _check(lib().jf_rk3_step_vjp(self.h, self._field(Un, "Un"), _ptr(dt), self._field(lam_out, "lam_out"),
                                      self._field(lam_in, "lam_in"), _stream()), self.h)
+        return lam_in
+
+    def supports_stage_vjp(self):
+        """True when rk3_step_vjp_stages serves this solver: the default
+        scheme (HLLC, Einfeldt speeds, WENO5-JS, TVD-RK3) without walls."""
+        s = self.scheme
+        return (s.flux == FLUX["hllc"] and s.recon == RECON["weno5-js"] and s.signal_speed == SPEEDS["einfeldt"]
+                and s.integrator == INTEGRATOR["rk3"] and WALL not in list(self.grid.bc))
+
+    def rk3_step_keep(self, U, dt, U1, U2):
+        """One fixed-dt RK3 step of U in place (as rk3_step), writing the stage
+        states U1 and U2 into the given tensors (jf_rk3_step_keep)."""
+        _check(lib().jf_rk3_step_keep(self.h, self._field(U, "U"), _ptr(dt), self._field(U1, "U1"),
+                                      self._field(U2, "U2"), _stream()), self.h)
+        return U
+
+    def rk3_step_vjp_stages(self, Un, U1, U2, dt, lam_out, lam_in=None):
+        """rk3_step_vjp from the kept stage states of the step
+        (jf_rk3_step_vjp_stages: no recomputation)."""
+        lam_in = self.empty() if lam_in is None else lam_in
+        _check(lib().jf_rk3_step_vjp_stages(self.h, self._field(Un, "Un"), self._field(U1, "U1"),
+                                            self._field(U2, "U2"), _ptr(dt), self._field(lam_out, "lam_out"),
+                                            self._field(lam_in, "lam_in"), _stream()), self.h)
         return lam_in
 
     def rk3_step_vjp_params(self, Un, dt, lam_out, lam_in=None, theta_bar=None):

@@ -7,6 +7,8 @@
   after 5 steps of dt = 1e-2 w.r.t. the shock Mach number, against the
   oracle's forward-mode gradient and central differences (second order).
 * Checkpointed trajectory gradient (autograd) against finite differences.
+* Kept stage states: jf_rk3_step_keep equals jf_rk3_step and the stage calls
+  bit for bit, and jf_rk3_step_vjp_stages equals jf_rk3_step_vjp.
 """
 import math
 
@@ -209,3 +211,46 @@ def test_checkpointed_rollout_gradient():
     fd = (L(U0 + eps * v) - L(U0 - eps * v)) / (2 * eps)
     ad = float((g_ckpt * v).sum())
     assert abs(fd - ad) <= 1e-5 * abs(ad)
+
+
+@pytest.mark.parametrize("dtype,rtol", [("f64", 1e-13), ("f32", 2e-5)])
+@pytest.mark.parametrize("make", [lambda: inputs.kelvin_helmholtz(48, seed=5),
+                                  lambda: inputs.random_smooth((12, 10, 9), seed=6, viscous=True, mu=0.02),
+                                  lambda: inputs.random_blocks((40, 1, 1), seed=7)])
+def test_kept_stage_states(make, dtype, rtol):
+    case = make()
+    s = jf.Solver.from_case(case, dtype=dtype)
+    assert s.supports_stage_vjp()
+    t = s.dtype
+    Un = torch.tensor(case.U, dtype=t, device="cuda")
+    dt = s.scalar(0.5 * s.compute_dt(Un).item())
+    Ua, Ub = Un.clone(), Un.clone()
+    U1, U2 = s.empty(), s.empty()
+    s.rk3_step_keep(Ua, dt, U1, U2)
+    s.rk3_step(Ub, dt)
+    assert torch.equal(Ua, Ub)
+    assert torch.equal(U1, s.stage(Un, None, s.empty(), 0.0, 1.0, dt))
+    assert torch.equal(U2, s.stage(U1, Un, s.empty(), 0.75, 0.25, dt))
+    g = torch.Generator(device="cpu").manual_seed(11)
+    lam = torch.randn(s.shape, generator=g, dtype=torch.float64).to(device="cuda", dtype=t)
+    a = s.rk3_step_vjp(Un, dt, lam)
+    b = s.rk3_step_vjp_stages(Un, U1, U2, dt, lam)
+    s.sync()
+    scale = float(a.abs().max())
+    assert float((a - b).abs().max()) <= rtol * scale
+
+
+def test_kept_stage_states_refused_elsewhere():
+    case = inputs.kelvin_helmholtz(32, seed=5)
+    s = jf.Solver.from_case(case, dtype="f64", flux="hll")
+    assert not s.supports_stage_vjp()
+    Un = torch.tensor(case.U, dtype=torch.float64, device="cuda")
+    dt = s.scalar(1e-3)
+    U1, U2 = s.empty(), s.empty()
+    with pytest.raises(jf.JFError) as e:
+        s.rk3_step_vjp_stages(Un, U1, U2, dt, Un.clone())
+    assert e.value.status == jf.JF_ERR_UNSUPPORTED
+    r = jf.Solver.from_case(case, dtype="f64", integrator="rk2")
+    with pytest.raises(jf.JFError) as e:
+        r.rk3_step_keep(Un.clone(), dt, U1, U2)
+    assert e.value.status == jf.JF_ERR_UNSUPPORTED
