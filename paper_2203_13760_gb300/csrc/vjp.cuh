@@ -111,6 +111,27 @@ struct VCount {
   }
 };
 
+// 2D task order: a face family covers R rows (y) by C columns (x) of faces.
+// Task f goes to row r and column c (0-based) so that a warp takes 16
+// consecutive rows of two adjacent columns: every shared array of a box has a
+// row pitch of 2 (mod 4) words (26 or 22), so the 16 rows of one column fall
+// on 16 distinct even banks (plus the column) and the next column on the odd
+// ones, and the warp's loads and atomics are free of bank conflicts.  Rows
+// beyond the first 16 follow as a second block in row-fastest order.
+template <int R, int C>
+__device__ __forceinline__ void task_rc(int f, int& r, int& c) {
+  constexpr int RA = R >= 16 ? 16 : 0;
+  constexpr int RB = R - RA > 0 ? R - RA : 1;  // rows of the second block (none when R == 16)
+  if (f < RA * C) {
+    r = f % 16;
+    c = f / 16;
+  } else {
+    const int g = f - RA * C;
+    r = RA + g % RB;
+    c = g / RB;
+  }
+}
+
 // Shared-memory views and the boundary-aware accumulator of one box.
 template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
 struct VTile {
@@ -437,10 +458,10 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   // cells -3 .. B_d+1 along d: a face reaches cells -2 .. +3 along d; the
   // box's own cells across), then, if viscous, the dissipative faces (left
   // cells -2 .. B_d along d, -2 .. B+1 across on the active tangential axes).
-  // Face index -> (s along d, a along t1, b along t2) with the x coordinate
-  // fastest across the lanes of a warp (consecutive shared-memory words, no
-  // bank conflicts on the loads and the atomic accumulation): x is s for
-  // d = 0, b (t2) for d = 1 and a (t1) for d = 2.
+  // Face index -> (s along d, a along t1, b along t2): in 2D by task_rc (16
+  // rows of two adjacent columns per warp); in 1D and 3D with the x
+  // coordinate fastest across the lanes of a warp (x is s for d = 0, b (t2)
+  // for d = 1 and a (t1) for d = 2).
   auto conv_task = [&](auto dtag, int f) {
     constexpr int d = decltype(dtag)::value;
     constexpr int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
@@ -449,7 +470,19 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     constexpr int B1 = t1 < DIM ? VCount<DIM, BX, BY, BZ>::B(t1) : 1;
     constexpr int B2 = t2 < DIM ? VCount<DIM, BX, BY, BZ>::B(t2) : 1;
     int s, a, b;
-    if (d == 0) {
+    if (DIM == 2 && d == 0) {  // rows: a (y), columns: s (x)
+      int r, c;
+      task_rc<B1, en>(f, r, c);
+      s = c - 3;
+      a = r;
+      b = 0;
+    } else if (DIM == 2 && d == 1) {  // rows: s (y), columns: b (x)
+      int r, c;
+      task_rc<en, B2>(f, r, c);
+      s = r - 3;
+      a = 0;
+      b = c;
+    } else if (d == 0) {
       s = f % en - 3;
       a = (f / en) % B1;
       b = f / (en * B1);
@@ -475,7 +508,19 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     constexpr int e2 = t2 < DIM ? VCount<DIM, BX, BY, BZ>::B(t2) + 4 : 1;
     constexpr int o1 = t1 < DIM ? 2 : 0, o2 = t2 < DIM ? 2 : 0;
     int s, a, b;
-    if (d == 0) {
+    if (DIM == 2 && d == 0) {  // rows: a (y), columns: s (x)
+      int r, c;
+      task_rc<e1, en>(f, r, c);
+      s = c - 2;
+      a = r - o1;
+      b = 0;
+    } else if (DIM == 2 && d == 1) {  // rows: s (y), columns: b (x)
+      int r, c;
+      task_rc<en, e2>(f, r, c);
+      s = r - 2;
+      a = 0;
+      b = c - o2;
+    } else if (d == 0) {
       s = f % en - 2;
       a = (f / en) % e1 - o1;
       b = f / (en * e1) - o2;
