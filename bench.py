@@ -395,6 +395,13 @@ def run_jf(args):
                 "kernel": "stage_kernel", "launch_ms": 1e3 * stage_avg_s,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x {clock_mhz:.0f} MHz"
                 if dtype == "f32" else "nominal FP64 rate"}
+    # the FMA rate measured on this GPU (jf_fma_peak), beside the derived peak
+    try:
+        fma_tflops = jf.fma_peak(dtype) / 1e12
+    except Exception:  # report the main line even if the microbenchmark fails
+        fma_tflops = None
+    roofline["measured_fma_peak"] = fma_tflops
+    roofline["frac_of_measured_fma"] = (achieved_tflops / fma_tflops) if achieved_tflops and fma_tflops else None
     stage_bytes = (VALUES_PER_CELL_STEP / 3.0) * esize * N
     hbm_gbs = stage_bytes / stage_avg_s / 1e9
     hbm = {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_gbs / peaks["hbm_gbs"],

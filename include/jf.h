@@ -356,6 +356,15 @@ const char* jf_last_error(jf_handle h);
 jf_status jf_rk3_step_noalloc(const jf_grid* grid, const jf_gas* gas, const jf_scheme* scheme, void* U_inout,
                               const double* dt_dev, double* dt_used_dev, void* stream);
 
+/* Measurement helper (not part of the method): the fused-multiply-add rate
+ * of the device in FLOP/s (2 per FMA) for dtype JF_F32 or JF_F64, from one
+ * launch of a kernel of independent FMA chains at full occupancy (iters
+ * loop trips of 128 FMAs per thread), timed with CUDA events on `stream`
+ * after one shorter warm-up launch.  This is the ALU roofline of the stage
+ * kernels.  Blocks the host until the timed launch ends; errors go to
+ * jf_last_error(NULL). */
+jf_status jf_fma_peak(int dtype, int iters, double* flops_per_s, void* stream);
+
 /* Library version string. */
 const char* jf_version(void);
 

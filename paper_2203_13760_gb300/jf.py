@@ -84,6 +84,7 @@ SIGNATURES = {
     "jf_status_sync": (_I, [_VP]),
     "jf_last_error": (ctypes.c_char_p, [_VP]),
     "jf_version": (ctypes.c_char_p, []),
+    "jf_fma_peak": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double), _VP]),
     "jf_rk3_step_noalloc": (_I, [ctypes.POINTER(Grid), ctypes.POINTER(GasParams), ctypes.POINTER(Scheme), _VP, _VP,
                                  _VP, _VP]),
 }
@@ -122,6 +123,18 @@ def _stream():
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def fma_peak(dtype="f32", iters=None):
+    """Measured fused-multiply-add rate of the current device in FLOP/s
+    (jf_fma_peak): the ALU roofline of the stage kernels.  iters defaults to
+    a launch of roughly 30 ms (30000 loop trips in FP32, 500 in FP64)."""
+    code = JF_F32 if dtype in ("f32", "float32") else JF_F64
+    if iters is None:
+        iters = 30000 if code == JF_F32 else 500
+    out = ctypes.c_double(0.0)
+    _check(lib().jf_fma_peak(code, int(iters), ctypes.byref(out), _stream()))
+    return out.value
 
 
 def _set_nn(obj, theta):
