@@ -97,9 +97,10 @@ __device__ __forceinline__ int map_index(int i, int n, int periodic) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-// Index map with slip walls (Table 2 boundary conditions; the run-time scheme
-// kernels only): a ghost cell beyond a wall is the mirror image of the cell
-// inside (-1 - i at the low side, 2n - 1 - i at the high side) and `flip`
+// Index map with slip walls (Table 2 boundary conditions; the extended and
+// Rusanov-NN kernel families only): a ghost cell beyond a wall is the mirror
+// image of the cell inside (-1 - i at the low side, 2n - 1 - i at the high
+// side) and `flip`
 // records that its momentum normal to the wall changes sign.  Mirroring each
 // axis on its own equals filling the ghost layers axis after axis (edge and
 // corner ghosts then carry the product of the flips).  Active axes have at
@@ -144,8 +145,8 @@ struct PlaneRegs {
 
 // Fetch plane gz (global z index, mapped by the boundary condition) of the
 // tile at (gx0, gy0).
-// WALLS: the kernel handles slip walls (the default-scheme kernels never
-// see them; the host routes walled grids to the run-time scheme kernels).
+// WALLS: the kernel handles slip walls (only the extended and Rusanov-NN
+// kernel families; the host routes every walled grid to one of them).
 template <typename T, int BX, int BY, int DIM, bool VISC, bool WALLS>
 __device__ __forceinline__ void fetch_plane(const StageArgs<T>& A, PlaneRegs<T, BX, BY, DIM, VISC>& r, int gx0,
                                             int gy0, int gz) {
