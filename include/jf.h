@@ -261,6 +261,21 @@ jf_status jf_rk3_step_vjp_params(jf_handle h, const void* Un, const double* dt_d
 jf_status jf_batch_step_vjp(jf_handle batch, void* const* Un_ptrs, const double* dt_dev, void* const* lam_out_ptrs,
                             void* const* lam_in_ptrs, void* const* add_ptrs, void* theta_bar, void* stream);
 
+/* Deferred parameter gradient of a Rusanov-NN batch over a backward sweep
+ * (Section 7.4: the gradient of a training loss sums over every face of
+ * every stage of every step).  After jf_batch_param_grad_begin, each
+ * jf_batch_step_vjp call with a non-NULL theta_bar (its value is not read)
+ * keeps its face records (network inputs and cotangents) in a store owned by
+ * the handle instead of adding to theta_bar, for at most max_steps calls
+ * (JF_ERR_ARG beyond).  jf_batch_param_grad_end then adds the sum over all
+ * kept records to theta_bar (a device array of JF_NN_PARAMS elements of the
+ * batch's dtype) in one launch and leaves the deferred mode.  The result
+ * equals the per-call gradients up to the order of the floating-point sums.
+ * begin allocates the store (5 values per face per stage per step) when it
+ * is smaller than needed; the other calls do not allocate. */
+jf_status jf_batch_param_grad_begin(jf_handle batch, int max_steps);
+jf_status jf_batch_param_grad_end(jf_handle batch, void* theta_bar, void* stream);
+
 /* Loss of the adjoint workload: *loss_dev = sum_cells (rho - rho_target)^2 dV
  * (FP64 accumulation) and, if seed != NULL, seed = dloss/dU (the cotangent
  * that starts the backward pass: 2 (rho - rho_target) dV in the density

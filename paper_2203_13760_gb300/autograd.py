@@ -157,9 +157,13 @@ class _FeedForward(torch.autograd.Function):
             dt = torch.tensor(ctx.dts, dtype=torch.float64, device=trajs[0].device)
             lam = [gi[ctx.nsteps].clone() for gi in g]
             nxt = [torch.empty_like(x) for x in lam]
+            if theta_bar is not None:  # one parameter-gradient launch for the whole sweep
+                ctx.batch.param_grad_begin(ctx.nsteps)
             for t in reversed(range(ctx.nsteps)):
                 ctx.batch.step_vjp([tr[t] for tr in trajs], dt, lam, nxt, [gi[t] for gi in g], theta_bar)
                 lam, nxt = nxt, lam
+            if theta_bar is not None:
+                ctx.batch.param_grad_end(theta_bar)
             return (None, None, None, theta_bar, *lam)
         out = []
         for i, (traj, g) in enumerate(zip(trajs, grads)):

@@ -56,6 +56,10 @@ void release_all(jf_ctx* h) {
   if (h->vjp_desc_done) cudaEventDestroy(h->vjp_desc_done);
   h->vjp_desc_host = h->vjp_desc_dev = nullptr;
   h->vjp_desc_done = nullptr;
+  if (h->rec_store) cudaFree(h->rec_store);
+  h->rec_store = nullptr;
+  h->rec_cap = h->rec_limit = h->rec_used = 0;
+  h->rec_defer = false;
   if (h->d_work) cudaFree(h->d_work);
   if (h->d_dt) cudaFree(h->d_dt);
   if (h->d_red) cudaFree(h->d_red);

@@ -71,6 +71,13 @@ struct jf_ctx {
   void* vjp_desc_host = nullptr;
   void* vjp_desc_dev = nullptr;
   cudaEvent_t vjp_desc_done = nullptr;
+  // deferred Rusanov-NN parameter gradient (jf_batch_param_grad_begin / end):
+  // face records of the adjoint steps in between, summed in one launch
+  void* rec_store = nullptr;
+  size_t rec_cap = 0;    // elements allocated
+  size_t rec_limit = 0;  // elements of the open sweep (max_steps of the begin call)
+  size_t rec_used = 0;   // elements
+  bool rec_defer = false;
   void* d_cfl = nullptr;               // per-simulation CflArgs
   void* d_chunks = nullptr;            // CFL chunk list
   int nchunks = 0;
@@ -133,6 +140,11 @@ jf_status general_vjp(jf_ctx* h, const void* Un, const double* dt, const void* l
 template <typename T>
 jf_status batch_general_vjp(jf_ctx* h, void* const* Un, const double* dt, void* const* lam_out, void* const* lam_in,
                             void* const* add, void* theta_bar, cudaStream_t s);
+// deferred parameter gradient of a batch (jf_batch_param_grad_begin / end)
+template <typename T>
+jf_status batch_param_grad_begin(jf_ctx* h, int max_steps);
+template <typename T>
+jf_status batch_param_grad_end(jf_ctx* h, void* theta_bar, cudaStream_t s);
 
 // batch (batch.cu)
 jf_status batch_set_variant(jf_ctx* h, int variant);

@@ -213,3 +213,23 @@ extern "C" jf_status jf_batch_step_vjp(jf_handle h, void* const* Un_ptrs, const 
              : batch_general_vjp<double>(h, Un_ptrs, dt_dev, lam_out_ptrs, lam_in_ptrs, add_ptrs, theta_bar,
                                          (cudaStream_t)stream);
 }
+
+extern "C" jf_status jf_batch_param_grad_begin(jf_handle h, int max_steps) {
+  if (!h || h->kind != 1) { set_error(h, "jf_batch_param_grad_begin: not a batch handle"); return JF_ERR_ARG; }
+  if (h->scheme.flux != JF_FLUX_RUSANOV_NN || max_steps < 1) {
+    set_error(h, "jf_batch_param_grad_begin: needs the JF_FLUX_RUSANOV_NN flux and max_steps >= 1");
+    return JF_ERR_ARG;
+  }
+  return h->scheme.dtype == JF_F32 ? batch_param_grad_begin<float>(h, max_steps)
+                                   : batch_param_grad_begin<double>(h, max_steps);
+}
+
+extern "C" jf_status jf_batch_param_grad_end(jf_handle h, void* theta_bar, void* stream) {
+  if (!h || h->kind != 1) { set_error(h, "jf_batch_param_grad_end: not a batch handle"); return JF_ERR_ARG; }
+  if (!h->rec_defer || !theta_bar || ((uintptr_t)theta_bar % h->esize) != 0) {
+    set_error(h, "jf_batch_param_grad_end: needs a preceding jf_batch_param_grad_begin and an aligned theta_bar");
+    return JF_ERR_ARG;
+  }
+  return h->scheme.dtype == JF_F32 ? batch_param_grad_end<float>(h, theta_bar, (cudaStream_t)stream)
+                                   : batch_param_grad_end<double>(h, theta_bar, (cudaStream_t)stream);
+}

@@ -117,17 +117,27 @@ struct StepPtrs {
   T* rec;
 };
 
+// Stages of one step of the integrator.
+int step_stages(const jf_ctx* h) {
+  return h->scheme.integrator == JF_RK3 ? 3 : (h->scheme.integrator == JF_RK2 ? 2 : 1);
+}
+
 // The integrator's chain over the grids (geometry in `geo`, one entry per grid).
+// The face records of stage j (in the chain's order) start rec_stride * j
+// elements after P[k].rec (0: every stage reuses the same records).
 template <typename T>
 jf_status gvjp_chain(jf_ctx* h, const Gas<T>& g, const std::vector<GVjpArgs<T>>& geo,
-                     const std::vector<StepPtrs<T>>& P, T* theta_bar, cudaStream_t s) {
+                     const std::vector<StepPtrs<T>>& P, T* theta_bar, size_t rec_stride, cudaStream_t s) {
   const int integ = h->scheme.integrator;
   std::vector<GVjpArgs<T>> V(geo);
+  size_t stage = 0;  // stages set up so far, counted per grid 0
   auto set = [&](size_t k, const T* Us, const T* lam, T s_in, const T* x1, T a1, const T* x2, T a2, const T* x3,
                  T a3, T* out) {
     GVjpArgs<T>& A = V[k];
     A.Us = Us; A.lam = lam; A.s_in = s_in; A.x1 = x1; A.a1 = a1; A.x2 = x2; A.a2 = a2; A.x3 = x3; A.a3 = a3;
-    A.out = out; A.dt = P[k].dt; A.rec = P[k].rec;
+    A.out = out; A.dt = P[k].dt;
+    if (k == 0) ++stage;
+    A.rec = P[k].rec ? P[k].rec + rec_stride * (stage - 1) : nullptr;
   };
   jf_status st;
   if (integ == JF_RK3) {
@@ -224,7 +234,7 @@ jf_status general_vjp(jf_ctx* h, const void* Un, const double* dt, const void* l
   const StageVariant<T>& sv = stage_variants<T>(&count)[h->table_index];
   if ((st = recompute<T>(h, sv, g, base_args<T>(h), p, s)) != JF_OK) return st;
   return gvjp_chain<T>(h, g, std::vector<GVjpArgs<T>>{geo}, std::vector<StepPtrs<T>>{p},
-                       static_cast<T*>(theta_bar), s);
+                       static_cast<T*>(theta_bar), 0, s);
 }
 
 // Forward recompute of every grid's stage states in one launch per stage
@@ -301,6 +311,18 @@ jf_status batch_general_vjp(jf_ctx* h, void* const* Un, const double* dt, void* 
   size_t off = 0;
   for (int k = 0; k < ns; ++k) off += 10 * (size_t)geo[k].N;
   T* rbuf = lbuf + off;  // records of all grids, consecutive
+  size_t faces = 0;
+  for (int k = 0; k < ns; ++k) faces += (size_t)faces_of(geo[k]);
+  const bool defer = h->rec_defer && theta_bar && h->scheme.flux == JF_FLUX_RUSANOV_NN;
+  const size_t rec_step = (size_t)step_stages(h) * 5 * faces;  // record elements of one step
+  if (defer) {
+    if (h->rec_used + rec_step > h->rec_limit) {
+      set_error(h, "jf_batch_step_vjp: the record store of jf_batch_param_grad_begin is full (more steps than "
+                   "max_steps)");
+      return JF_ERR_ARG;
+    }
+    rbuf = static_cast<T*>(h->rec_store) + h->rec_used;
+  }
   off = 0;
   size_t roff = 0;
   for (int k = 0; k < ns; ++k) {
@@ -311,7 +333,49 @@ jf_status batch_general_vjp(jf_ctx* h, void* const* Un, const double* dt, void* 
     roff += 5 * (size_t)faces_of(geo[k]);
   }
   if ((st = recompute_batch<T>(h, sv, g, P, s)) != JF_OK) return st;
-  return gvjp_chain<T>(h, g, geo, P, static_cast<T*>(theta_bar), s);
+  if (!defer) return gvjp_chain<T>(h, g, geo, P, static_cast<T*>(theta_bar), 0, s);
+  // deferred parameter gradient: the records stay in the store for
+  // jf_batch_param_grad_end, one region per stage
+  if ((st = gvjp_chain<T>(h, g, geo, P, nullptr, rec_step / step_stages(h), s)) != JF_OK) return st;
+  h->rec_used += rec_step;
+  return JF_OK;
+}
+
+template <typename T>
+jf_status batch_param_grad_begin(jf_ctx* h, int max_steps) {
+  size_t faces = 0;
+  for (int k = 0; k < h->nsim; ++k) faces += (size_t)faces_of(grid_args<T>(h->grids[k], h->dim));
+  const size_t need = (size_t)max_steps * step_stages(h) * 5 * faces;
+  if (need > h->rec_cap) {
+    if (h->rec_store) cudaFree(h->rec_store);
+    h->rec_store = nullptr;
+    h->rec_cap = 0;
+    const cudaError_t e = cudaMalloc(&h->rec_store, need * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e, "jf_batch_param_grad_begin: record store");
+    h->rec_cap = need;
+  }
+  h->rec_limit = need;
+  h->rec_used = 0;
+  h->rec_defer = true;
+  return JF_OK;
+}
+
+template <typename T>
+jf_status batch_param_grad_end(jf_ctx* h, void* theta_bar, cudaStream_t s) {
+  const long long n = (long long)(h->rec_used / 5);
+  h->rec_defer = false;
+  h->rec_used = 0;
+  if (n == 0) return JF_OK;
+  jf_status st;
+  if ((st = prepare_param_grad<T>(h, theta_bar)) != JF_OK) return st;
+  Gas<T> g = make_gas<T>(h->gas, h->scheme);
+  if ((st = network<T>(h, g)) != JF_OK) return st;
+  const long long chunks = (n + 31) / 32;
+  const long long blocks = std::min<long long>((chunks + kNnWarps - 1) / kNnWarps, 2LL * h->sms);
+  nn_param_grad_kernel<T><<<(unsigned)blocks, 32 * kNnWarps, nn_grad_smem_bytes<T>(), s>>>(
+      g.nn, static_cast<const T*>(h->rec_store), n, static_cast<T*>(theta_bar));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? JF_OK : cuda_fail(h, e, "jf_batch_param_grad_end: launch");
 }
 
 template jf_status general_vjp<float>(jf_ctx*, const void*, const double*, const void*, void*, void*, cudaStream_t);
@@ -320,5 +384,9 @@ template jf_status batch_general_vjp<float>(jf_ctx*, void* const*, const double*
                                             void* const*, void*, cudaStream_t);
 template jf_status batch_general_vjp<double>(jf_ctx*, void* const*, const double*, void* const*, void* const*,
                                              void* const*, void*, cudaStream_t);
+template jf_status batch_param_grad_begin<float>(jf_ctx*, int);
+template jf_status batch_param_grad_begin<double>(jf_ctx*, int);
+template jf_status batch_param_grad_end<float>(jf_ctx*, void*, cudaStream_t);
+template jf_status batch_param_grad_end<double>(jf_ctx*, void*, cudaStream_t);
 
 }  // namespace jf

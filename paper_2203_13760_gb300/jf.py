@@ -73,6 +73,8 @@ SIGNATURES = {
     "jf_rk3_step_vjp_params": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_batch_step_vjp": (_I, [_VP, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                ctypes.POINTER(_VP), _VP, _VP]),
+    "jf_batch_param_grad_begin": (_I, [_VP, _I]),
+    "jf_batch_param_grad_end": (_I, [_VP, _VP, _VP]),
     "jf_loss_density_l2": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jf_batch_create": (_I, [ctypes.POINTER(Grid), _I, ctypes.POINTER(GasParams), ctypes.POINTER(Scheme),
                              ctypes.POINTER(_VP)]),
@@ -434,6 +436,21 @@ class Batch:
                                        arr(adds) if adds is not None else None,
                                        _ptr(theta_bar) if theta_bar is not None else None, _stream()), self.h)
         return lam_ins
+
+    def param_grad_begin(self, max_steps):
+        """Keep the face records of the next (at most max_steps) step_vjp calls
+        with theta_bar instead of adding to theta_bar
+        (jf_batch_param_grad_begin)."""
+        _check(lib().jf_batch_param_grad_begin(self.h, int(max_steps)), self.h)
+
+    def param_grad_end(self, theta_bar):
+        """Add the parameter gradient of every kept record to theta_bar in one
+        launch (jf_batch_param_grad_end)."""
+        if (theta_bar.dtype != self.dtype or not theta_bar.is_cuda or not theta_bar.is_contiguous()
+                or theta_bar.numel() != NN_PARAMS):
+            raise ValueError(f"theta_bar must be a contiguous CUDA {self.dtype} tensor of {NN_PARAMS} values")
+        _check(lib().jf_batch_param_grad_end(self.h, _ptr(theta_bar), _stream()), self.h)
+        return theta_bar
 
     def step(self, Us, nsteps, dt_out=None):
         import torch

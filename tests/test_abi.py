@@ -79,6 +79,8 @@ def test_bad_arguments_rejected_on_host(libjf):
     assert L.jf_fma_peak(7, 10, ctypes.byref(out), None) == libjf.JF_ERR_ARG
     assert L.jf_fma_peak(libjf.JF_F32, 0, ctypes.byref(out), None) == libjf.JF_ERR_ARG
     assert L.jf_fma_peak(libjf.JF_F32, 10, None, None) == libjf.JF_ERR_ARG
+    assert L.jf_batch_param_grad_begin(None, 1) == libjf.JF_ERR_ARG
+    assert L.jf_batch_param_grad_end(None, None, None) == libjf.JF_ERR_ARG
     assert L.jf_rk3_step_vjp_stages(None, None, None, None, None, None, None, None) == libjf.JF_ERR_ARG
     # the Rusanov-NN flux runs only through a handle that holds parameters
     nn = libjf.make_scheme("f32", flux="rusanov-nn")

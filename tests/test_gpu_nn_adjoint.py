@@ -163,3 +163,45 @@ def test_batch_adjoint_equals_single_grids(scheme):
         assert (got[i] - want).abs().max().item() <= 1e-12 * want.abs().max().item(), i
     if nn:
         assert (tb - tb_ref).abs().max().item() <= 1e-12 * tb_ref.abs().max().item()
+
+
+@pytest.mark.parametrize("scheme", ["nn_weno3_rk2", "nn_weno3_euler"])
+def test_deferred_parameter_gradient(scheme):
+    """jf_batch_param_grad_begin / end: the parameter gradient of several
+    batch adjoint steps summed in one launch equals the sum of the per-call
+    gradients (FP64, to rounding), the state cotangents are unchanged, and
+    the record store refuses more steps than it was opened for."""
+    cases = [with_scheme(c, **SCHEMES[scheme]) for c in inputs.four_quadrant_batch(nsim=3, sides=(32, 48), seed=9)]
+    for c in cases:
+        c.bc = (W, W, W, 1, 1, 1)
+    theta = torch.tensor(THETA, dtype=torch.float64, device="cuda")
+    p = cases[0].params()
+    b = jf.Batch([jf.make_grid(c.n, c.lo, c.hi, c.bc) for c in cases], dtype="f64", nn=theta,
+                 **{k: p[k] for k in ("gamma", "R", "mu", "Pr", "eps", "cfl", "viscous", "heat", "flux", "recon",
+                                      "speeds", "integrator")})
+    rng = np.random.default_rng(5)
+    Us = [torch.tensor(c.U, dtype=torch.float64, device="cuda") for c in cases]
+    dt = torch.tensor([2e-4, 3e-4, 2.5e-4], dtype=torch.float64, device="cuda")
+    lams = [[torch.tensor(rng.standard_normal(c.U.shape), device="cuda") for c in cases] for _ in range(3)]
+    tb_each = torch.zeros(jf.NN_PARAMS, dtype=torch.float64, device="cuda")
+    outs_each = [b.step_vjp(Us, dt, lams[k], None, None, tb_each) for k in range(3)]
+    tb_once = torch.zeros_like(tb_each)
+    b.param_grad_begin(3)
+    outs_once = [b.step_vjp(Us, dt, lams[k], None, None, tb_once) for k in range(3)]
+    assert float(tb_once.abs().max()) == 0.0  # nothing added before the end call
+    b.param_grad_end(tb_once)
+    b.sync()
+    for a, c in zip(outs_each, outs_once):
+        for x, y in zip(a, c):
+            assert (x - y).abs().max().item() <= 1e-12 * x.abs().max().item()
+    assert (tb_once - tb_each).abs().max().item() <= 1e-12 * tb_each.abs().max().item()
+    # the store holds max_steps steps; the end call needs a begin
+    b.param_grad_begin(1)
+    b.step_vjp(Us, dt, lams[0], None, None, tb_once)
+    with pytest.raises(jf.JFError) as e:
+        b.step_vjp(Us, dt, lams[1], None, None, tb_once)
+    assert e.value.status == jf.JF_ERR_ARG
+    b.param_grad_end(tb_once)
+    with pytest.raises(jf.JFError) as e:
+        b.param_grad_end(tb_once)
+    assert e.value.status == jf.JF_ERR_ARG
