@@ -131,9 +131,57 @@ JF_HD void side_flux_vjp(const T W[5], const Gas<T>& g, const T Fb[5], const T U
   Wb[4] += pb;
 }
 
-// alpha = exp(NN(x)) (as nn_alpha) and dx = d alpha / dx.  h1 and h2 are
-// this thread's rows of shared memory (NN_HIDDEN values each): the hidden
-// activations, then the cotangents.
+// Four consecutive parameters or row values from shared memory (16-byte
+// aligned: every weight row of the layout, and every hidden row, starts at
+// a multiple of 4 elements of a 16-byte aligned base).
+__device__ __forceinline__ void ld4(const float* p, float o[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double o[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+// row[0 .. NN_HIDDEN) -> registers
+template <typename T>
+__device__ __forceinline__ void ld_row(const T* row, T v[NN_HIDDEN]) {
+#pragma unroll
+  for (int j = 0; j < NN_HIDDEN; j += 4) ld4(row + j, v + j);
+}
+// sum_j w[j] v[j] with the weight row w read four at a time
+template <typename T>
+__device__ __forceinline__ T dot_row(const T* w, const T v[NN_HIDDEN], T acc) {
+#pragma unroll
+  for (int j = 0; j < NN_HIDDEN; j += 4) {
+    T q[4];
+    ld4(w + j, q);
+    acc += q[0] * v[j] + q[1] * v[j + 1] + q[2] * v[j + 2] + q[3] * v[j + 3];
+  }
+  return acc;
+}
+// acc[j] += s w[j] over a weight row w
+template <typename T>
+__device__ __forceinline__ void axpy_row(const T* w, T s, T acc[NN_HIDDEN]) {
+#pragma unroll
+  for (int j = 0; j < NN_HIDDEN; j += 4) {
+    T q[4];
+    ld4(w + j, q);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[j + m] += s * q[m];
+  }
+}
+
+// Row pitch of the per-thread hidden rows (a multiple of 4 for the vector
+// loads; 36 puts the 16-byte accesses of 8 consecutive threads on distinct
+// banks).
+constexpr int kHRow = NN_HIDDEN + 4;
+
+// alpha = exp(NN(x)) (as nn_alpha) and dx = d alpha / dx.  th: the
+// parameters in shared memory; h1, h2: this thread's two hidden rows (kHRow
+// pitch, shared memory).  Each layer's input is held in registers while its
+// outputs are formed one weight row at a time; the reverse passes run over
+// weight rows too (output cotangent times row added into register
+// accumulators), so every parameter is read as part of a 16-byte row load.
 template <typename T>
 __device__ __forceinline__ T nn_alpha_grad(const T* th, const T x[4], T dx[4], T* h1, T* h2) {
   const T* W1 = th;
@@ -145,52 +193,60 @@ __device__ __forceinline__ T nn_alpha_grad(const T* th, const T x[4], T dx[4], T
   const T* W4 = b3 + NN_HIDDEN;
   const T b4 = W4[NN_HIDDEN];
   unsigned m1 = 0, m2 = 0, m3 = 0;  // ReLU masks (bit i: unit i active)
+  // layer 1 -> h1
 #pragma unroll 4
   for (int i = 0; i < NN_HIDDEN; ++i) {
-    const T z = b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] + W1[4 * i + 3] * x[3];
+    T w[4];
+    ld4(W1 + 4 * i, w);
+    const T z = b1[i] + w[0] * x[0] + w[1] * x[1] + w[2] * x[2] + w[3] * x[3];
     h1[i] = tmax(T(0), z);
     m1 |= (z > T(0) ? 1u : 0u) << i;
   }
-#pragma unroll 4
+  T v[NN_HIDDEN];
+  // layer 2 -> h2
+  ld_row(h1, v);
+#pragma unroll 2
   for (int i = 0; i < NN_HIDDEN; ++i) {
-    T z = b2[i];
-#pragma unroll 8
-    for (int j = 0; j < NN_HIDDEN; ++j) z += W2[NN_HIDDEN * i + j] * h1[j];
+    const T z = dot_row(W2 + NN_HIDDEN * i, v, b2[i]);
     h2[i] = tmax(T(0), z);
     m2 |= (z > T(0) ? 1u : 0u) << i;
   }
+  // layer 3 and the output
+  ld_row(h2, v);
   T o = b4;
-#pragma unroll 4
+#pragma unroll 2
   for (int i = 0; i < NN_HIDDEN; ++i) {
-    T z = b3[i];
-#pragma unroll 8
-    for (int j = 0; j < NN_HIDDEN; ++j) z += W3[NN_HIDDEN * i + j] * h2[j];
+    const T z = dot_row(W3 + NN_HIDDEN * i, v, b3[i]);
     o += W4[i] * tmax(T(0), z);
     m3 |= (z > T(0) ? 1u : 0u) << i;
   }
   const T alpha = texp(o);
-  // reverse with seed d alpha / d o = alpha: h2 <- cotangent of layer 2's
-  // outputs, h1 <- cotangent of layer 1's outputs
-#pragma unroll 4
+  // reverse, seed d alpha / d o = alpha: cotangent of layer 2's outputs
+  // (v, then masked into h2) = sum over active layer-3 units i of
+  // alpha W4[i] W3[i][:]
+#pragma unroll
+  for (int j = 0; j < NN_HIDDEN; ++j) v[j] = T(0);
+#pragma unroll 2
+  for (int i = 0; i < NN_HIDDEN; ++i)
+    if ((m3 >> i) & 1u) axpy_row(W3 + NN_HIDDEN * i, alpha * W4[i], v);
+#pragma unroll
+  for (int j = 0; j < NN_HIDDEN; ++j) h2[j] = (m2 >> j) & 1u ? v[j] : T(0);
+  // cotangent of layer 1's outputs = sum_j h2[j] W2[j][:], masked
+#pragma unroll
+  for (int k = 0; k < NN_HIDDEN; ++k) v[k] = T(0);
+#pragma unroll 2
   for (int j = 0; j < NN_HIDDEN; ++j) {
-    T s = T(0);
-#pragma unroll 8
-    for (int i = 0; i < NN_HIDDEN; ++i)
-      if ((m3 >> i) & 1u) s += W3[NN_HIDDEN * i + j] * W4[i];
-    h2[j] = (m2 >> j) & 1u ? alpha * s : T(0);
-  }
-#pragma unroll 4
-  for (int k = 0; k < NN_HIDDEN; ++k) {
-    T s = T(0);
-#pragma unroll 8
-    for (int j = 0; j < NN_HIDDEN; ++j) s += W2[NN_HIDDEN * j + k] * h2[j];
-    h1[k] = (m1 >> k) & 1u ? s : T(0);
+    const T s = h2[j];
+    if (s != T(0)) axpy_row(W2 + NN_HIDDEN * j, s, v);
   }
   dx[0] = dx[1] = dx[2] = dx[3] = T(0);
-#pragma unroll 4
-  for (int k = 0; k < NN_HIDDEN; ++k) {
 #pragma unroll
-    for (int m = 0; m < 4; ++m) dx[m] += W1[4 * k + m] * h1[k];
+  for (int k = 0; k < NN_HIDDEN; ++k) {
+    const T s = (m1 >> k) & 1u ? v[k] : T(0);
+    T w[4];
+    ld4(W1 + 4 * k, w);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) dx[m] += w[m] * s;
   }
   return alpha;
 }
@@ -413,18 +469,27 @@ __device__ __forceinline__ void gvjp_face(const GVjpArgs<T>& A, const Gas<T>& g,
 // One thread per face of every grid of the launch: within a grid, faces of
 // direction 0 first, then 1, then 2; within a direction x fastest.  A periodic axis has n faces (face 0 is also face n),
 // any other n + 1.  Rusanov-NN: dynamic shared memory of
-// gvjp_face_smem_bytes holds each thread's two hidden-layer rows.
+// gvjp_face_smem_bytes holds the network parameters (padded to a multiple
+// of 4) and each thread's two hidden-layer rows.
 constexpr int kGvjpThreads = 128;
+constexpr int kNnParamsPad = (NN_PARAMS + 3) / 4 * 4;
 template <typename T, int FLUX>
 constexpr size_t gvjp_face_smem_bytes() {
-  return FLUX == 4 ? sizeof(T) * (size_t)kGvjpThreads * 2 * (NN_HIDDEN + 1) : 0;
+  return FLUX == 4 ? sizeof(T) * ((size_t)kNnParamsPad + (size_t)kGvjpThreads * 2 * kHRow) : 0;
 }
 
 template <typename T, int DIM, int RECON, int FLUX>
 __global__ void __launch_bounds__(kGvjpThreads) gvjp_face_kernel(const GVjpBatch<T> B, const Gas<T> g) {
   extern __shared__ __align__(16) unsigned char gvjp_smem[];
-  T* h1 = reinterpret_cast<T*>(gvjp_smem) + threadIdx.x * (NN_HIDDEN + 1);
-  T* h2 = h1 + kGvjpThreads * (NN_HIDDEN + 1);
+  T* th = reinterpret_cast<T*>(gvjp_smem);  // the network parameters (Rusanov-NN)
+  T* h1 = th + kNnParamsPad + threadIdx.x * kHRow;
+  T* h2 = h1 + kGvjpThreads * kHRow;
+  Gas<T> gs = g;
+  if constexpr (FLUX == 4) {
+    for (int i = threadIdx.x; i < NN_PARAMS; i += blockDim.x) th[i] = g.nn[i];
+    __syncthreads();
+    gs.nn = th;
+  }
   const long long gf = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gf >= B.face_base[B.nsim]) return;
   const int sidx = find_sim(B.face_base, B.nsim, gf);
@@ -444,9 +509,9 @@ __global__ void __launch_bounds__(kGvjpThreads) gvjp_face_kernel(const GVjpBatch
   r /= ext[0];
   c[1] = (int)(r % ext[1]);
   c[2] = (int)(r / ext[1]);
-  if (d == 0) gvjp_face<T, DIM, RECON, FLUX, 0>(A, g, c, f, h1, h2);
-  if constexpr (DIM >= 2) if (d == 1) gvjp_face<T, DIM, RECON, FLUX, 1>(A, g, c, f, h1, h2);
-  if constexpr (DIM == 3) if (d == 2) gvjp_face<T, DIM, RECON, FLUX, 2>(A, g, c, f, h1, h2);
+  if (d == 0) gvjp_face<T, DIM, RECON, FLUX, 0>(A, gs, c, f, h1, h2);
+  if constexpr (DIM >= 2) if (d == 1) gvjp_face<T, DIM, RECON, FLUX, 1>(A, gs, c, f, h1, h2);
+  if constexpr (DIM == 3) if (d == 2) gvjp_face<T, DIM, RECON, FLUX, 2>(A, gs, c, f, h1, h2);
 }
 
 // Parameter gradient of the Rusanov-NN dissipation: grad += sum over the
