@@ -349,6 +349,21 @@ template <> JF_HD double tlog<double>(double x) { return log(x); }
 // Not inlined: one copy of the ~2200 multiply-adds serves every face
 // direction, and its 64 hidden values do not add to the register pressure
 // of the tile code around the call.
+#ifdef __CUDACC__
+// Four consecutive network parameters (or hidden-row values) from a 16-byte
+// aligned address: every weight row of the parameter layout starts at a
+// multiple of 4 elements, and the kernels place the parameters at a 16-byte
+// aligned offset of their shared memory.
+__device__ __forceinline__ void ld4(const float* p, float o[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double o[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+#endif
+
 template <typename T>
 __host__ __device__ __noinline__ T nn_alpha(const T* th, const T x[4]) {
   const T* W1 = th;
@@ -360,6 +375,38 @@ __host__ __device__ __noinline__ T nn_alpha(const T* th, const T x[4]) {
   const T* W4 = b3 + NN_HIDDEN;
   const T b4 = W4[NN_HIDDEN];
   T h1[NN_HIDDEN], h2[NN_HIDDEN];
+#ifdef __CUDA_ARCH__
+  // device: th is 16-byte aligned shared memory; weight rows read four at a time
+#pragma unroll
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T w[4];
+    ld4(W1 + 4 * i, w);
+    h1[i] = tmax(T(0), b1[i] + w[0] * x[0] + w[1] * x[1] + w[2] * x[2] + w[3] * x[3]);
+  }
+#pragma unroll
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T z = b2[i];
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; j += 4) {
+      T w[4];
+      ld4(W2 + NN_HIDDEN * i + j, w);
+      z += w[0] * h1[j] + w[1] * h1[j + 1] + w[2] * h1[j + 2] + w[3] * h1[j + 3];
+    }
+    h2[i] = tmax(T(0), z);
+  }
+  T out = b4;
+#pragma unroll 4
+  for (int i = 0; i < NN_HIDDEN; ++i) {
+    T z = b3[i];
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; j += 4) {
+      T w[4];
+      ld4(W3 + NN_HIDDEN * i + j, w);
+      z += w[0] * h2[j] + w[1] * h2[j + 1] + w[2] * h2[j + 2] + w[3] * h2[j + 3];
+    }
+    out += W4[i] * tmax(T(0), z);
+  }
+#else
 #pragma unroll
   for (int i = 0; i < NN_HIDDEN; ++i) {
     const T z = b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] + W1[4 * i + 3] * x[3];
@@ -380,6 +427,7 @@ __host__ __device__ __noinline__ T nn_alpha(const T* th, const T x[4]) {
     for (int j = 0; j < NN_HIDDEN; ++j) z += W3[NN_HIDDEN * i + j] * h2[j];
     out += W4[i] * tmax(T(0), z);
   }
+#endif
   return texp(out);
 }
 

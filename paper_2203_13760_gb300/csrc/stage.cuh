@@ -747,6 +747,15 @@ constexpr size_t stage_smem_elems() {
   return (size_t)(G::RING * G::PLANE + 5 * G::NFX + 5 * G::NFY);
 }
 
+// Element offset of the Rusanov-NN parameters in the dynamic shared memory:
+// after the tile buffers, rounded up to 16 bytes (nn_alpha reads its weight
+// rows with 16-byte loads).
+template <typename T, int DIM, bool VISC, int BX, int BY>
+constexpr size_t nn_smem_offset() {
+  constexpr size_t q = 16 / sizeof(T);
+  return (stage_smem_elems<T, DIM, VISC, BX, BY>() + q - 1) / q * q;
+}
+
 // The stage kernel.  blockDim.x == Geo::NT.
 //  * Single grid (work == null): one CTA per tile, the tile from blockIdx;
 //    grid = (ceil(nx/BX), ceil(ny/BY), ceil(nz/zchunk)) (3D), (.., .., 1) otherwise.
@@ -767,7 +776,8 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
   {
     unsigned dyn;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-    const size_t need = sizeof(T) * (stage_smem_elems<T, DIM, VISC, BX, BY>() + (SCH == SCH_NN ? NN_PARAMS : 0));
+    const size_t need = sizeof(T) * (SCH == SCH_NN ? nn_smem_offset<T, DIM, VISC, BX, BY>() + NN_PARAMS
+                                                   : stage_smem_elems<T, DIM, VISC, BX, BY>());
     if (!JF_CHECK(dyn >= need, "JFDBG smem %u < %llu\n", dyn, (unsigned long long)need)) return;
     if (work && threadIdx.x == 0)
       for (int i = blockIdx.x; i < nwork; i += gridDim.x) {
@@ -783,9 +793,9 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
 #endif
   Gas<T> gk = g;
   if constexpr (SCH == SCH_NN) {
-    // the Rusanov-NN parameters, after the stage buffers (the launch adds
-    // their size to the dynamic shared memory)
-    T* th = reinterpret_cast<T*>(smem_raw) + stage_smem_elems<T, DIM, VISC, BX, BY>();
+    // the Rusanov-NN parameters, after the stage buffers at a 16-byte
+    // aligned offset (the launch adds them to the dynamic shared memory)
+    T* th = reinterpret_cast<T*>(smem_raw) + nn_smem_offset<T, DIM, VISC, BX, BY>();
     for (int i = threadIdx.x; i < NN_PARAMS; i += blockDim.x) th[i] = __ldg(g.nn + i);
     __syncthreads();
     gk.nn = th;

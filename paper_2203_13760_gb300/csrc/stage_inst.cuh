@@ -5,10 +5,11 @@
 namespace jf {
 
 // Dynamic shared memory of a launch: the tile buffers, plus the Rusanov-NN
-// parameters in the kernels of that flux.
+// parameters (at a 16-byte aligned offset) in the kernels of that flux.
 template <typename T, int DIM, bool VISC, int BX, int BY, int SCH>
 constexpr size_t launch_smem() {
-  return stage_smem_bytes<T, DIM, VISC, BX, BY>() + (SCH == SCH_NN ? sizeof(T) * NN_PARAMS : 0);
+  return SCH == SCH_NN ? sizeof(T) * (nn_smem_offset<T, DIM, VISC, BX, BY>() + NN_PARAMS)
+                       : stage_smem_bytes<T, DIM, VISC, BX, BY>();
 }
 
 // MINB: CTAs per SM the register allocation must allow (__launch_bounds__).

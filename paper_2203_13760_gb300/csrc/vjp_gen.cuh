@@ -131,17 +131,6 @@ JF_HD void side_flux_vjp(const T W[5], const Gas<T>& g, const T Fb[5], const T U
   Wb[4] += pb;
 }
 
-// Four consecutive parameters or row values from shared memory (16-byte
-// aligned: every weight row of the layout, and every hidden row, starts at
-// a multiple of 4 elements of a 16-byte aligned base).
-__device__ __forceinline__ void ld4(const float* p, float o[4]) {
-  const float4 q = *reinterpret_cast<const float4*>(p);
-  o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double o[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
 // row[0 .. NN_HIDDEN) -> registers
 template <typename T>
 __device__ __forceinline__ void ld_row(const T* row, T v[NN_HIDDEN]) {
