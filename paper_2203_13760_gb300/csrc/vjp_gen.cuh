@@ -566,26 +566,27 @@ __global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* _
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) X[lane * 4 + m] = x[m];
-    // forward: h1, h2, h3 (r3)
-#pragma unroll 4
-    for (int i = 0; i < NN_HIDDEN; ++i)
-      h1[i] = tmax(T(0), b1[i] + W1[4 * i] * x[0] + W1[4 * i + 1] * x[1] + W1[4 * i + 2] * x[2] +
-                             W1[4 * i + 3] * x[3]);
+    // forward: h1, h2, h3 (r3); each layer's input in registers (v), the
+    // weight rows read four at a time from the shared copy of theta
+    T v[NN_HIDDEN];
 #pragma unroll 4
     for (int i = 0; i < NN_HIDDEN; ++i) {
-      T z = b2[i];
-#pragma unroll 8
-      for (int j = 0; j < NN_HIDDEN; ++j) z += W2[NN_HIDDEN * i + j] * h1[j];
-      h2[i] = tmax(T(0), z);
+      T w[4];
+      ld4(W1 + 4 * i, w);
+      h1[i] = tmax(T(0), b1[i] + w[0] * x[0] + w[1] * x[1] + w[2] * x[2] + w[3] * x[3]);
     }
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; ++j) v[j] = h1[j];
+#pragma unroll 2
+    for (int i = 0; i < NN_HIDDEN; ++i) h2[i] = tmax(T(0), dot_row(W2 + NN_HIDDEN * i, v, b2[i]));
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; ++j) v[j] = h2[j];
     T o = W4[NN_HIDDEN];
-#pragma unroll 4
+#pragma unroll 2
     for (int i = 0; i < NN_HIDDEN; ++i) {
-      T z = b3[i];
-#pragma unroll 8
-      for (int j = 0; j < NN_HIDDEN; ++j) z += W3[NN_HIDDEN * i + j] * h2[j];
-      r3[i] = tmax(T(0), z);
-      o += W4[i] * r3[i];
+      const T h3 = tmax(T(0), dot_row(W3 + NN_HIDDEN * i, v, b3[i]));
+      r3[i] = h3;
+      o += W4[i] * h3;
     }
     const T ob = f < nrec ? abar * texp(o) : T(0);  // d alpha / d o = alpha
     OB[lane] = ob;
@@ -603,14 +604,13 @@ __global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* _
       for (int k = 0; k < NN_HIDDEN; ++k) a3[k] += g3 * R2[r * kNnRow + k];
     }
     __syncwarp();
-    // G2 into R3: g2[j] = [h2_j > 0] sum_i W3[i][j] g3[i]
-#pragma unroll 4
-    for (int j = 0; j < NN_HIDDEN; ++j) {
-      T sum = T(0);
-#pragma unroll 8
-      for (int i = 0; i < NN_HIDDEN; ++i) sum += W3[NN_HIDDEN * i + j] * r4[i];
-      r3[j] = h2[j] > T(0) ? sum : T(0);
-    }
+    // G2 into R3: g2[j] = [h2_j > 0] sum_i W3[i][j] g3[i] (row updates of v)
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; ++j) v[j] = T(0);
+#pragma unroll 2
+    for (int i = 0; i < NN_HIDDEN; ++i) axpy_row(W3 + NN_HIDDEN * i, r4[i], v);
+#pragma unroll
+    for (int j = 0; j < NN_HIDDEN; ++j) r3[j] = h2[j] > T(0) ? v[j] : T(0);
     __syncwarp();
     // layer 2 (G2 in R3, H1 in R1)
 #pragma unroll 1
@@ -621,14 +621,13 @@ __global__ void __launch_bounds__(32 * kNnWarps) nn_param_grad_kernel(const T* _
       for (int k = 0; k < NN_HIDDEN; ++k) a2[k] += g2 * R1[r * kNnRow + k];
     }
     __syncwarp();
-    // G1 into R4: g1[k] = [h1_k > 0] sum_j W2[j][k] g2[j]
-#pragma unroll 4
-    for (int k = 0; k < NN_HIDDEN; ++k) {
-      T sum = T(0);
-#pragma unroll 8
-      for (int j = 0; j < NN_HIDDEN; ++j) sum += W2[NN_HIDDEN * j + k] * r3[j];
-      r4[k] = h1[k] > T(0) ? sum : T(0);
-    }
+    // G1 into R4: g1[k] = [h1_k > 0] sum_j W2[j][k] g2[j] (row updates of v)
+#pragma unroll
+    for (int k = 0; k < NN_HIDDEN; ++k) v[k] = T(0);
+#pragma unroll 2
+    for (int j = 0; j < NN_HIDDEN; ++j) axpy_row(W2 + NN_HIDDEN * j, r3[j], v);
+#pragma unroll
+    for (int k = 0; k < NN_HIDDEN; ++k) r4[k] = h1[k] > T(0) ? v[k] : T(0);
     __syncwarp();
     // layer 1 (G1 in R4, inputs in X)
 #pragma unroll 1
