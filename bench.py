@@ -420,17 +420,23 @@ def run_jf(args):
     s.step_host([host_in[k % 2] for k in range(Ke)], host_out)
     torch.cuda.synchronize()
     barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step_host([host_in[k % 2] for k in range(Ke)], host_out)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    # three timed passes of Ke steps; the median pass is reported (the copies
+    # share the host's memory with whatever else runs on the machine)
+    passes = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step_host([host_in[k % 2] for k in range(Ke)], host_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        passes.append(e0.elapsed_time(e1))
     s.sync()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_ms = max_over_ranks(statistics.median(passes), world)
     e2e = {"value": world * N * Ke / (e2e_ms * 1e-3), "unit": "cell-updates/s",
            "h2d_bytes_per_step": int(host_in[0].numel() * esize),
            "d2h_bytes_per_step": int(host_out[0].numel() * esize),
-           "call": "jf_rk3_step_host (uploads, steps and downloads overlapped across states)"}
+           "steps_per_pass": Ke, "pass_ms": passes,
+           "call": "jf_rk3_step_host (uploads, steps and downloads overlapped across states); median of 3 passes"}
 
     extras = {}
     if not args.no_extras and rank == 0:

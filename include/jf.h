@@ -159,7 +159,9 @@ jf_status jf_rhs(jf_handle h, const void* U, void* dUdt, void* stream);
 /* *dt_dev = CFL time step of U (Section 3.2; formula of this library):
  *   dt = CFL min(dt_c, dt_v), dt_c = min_d dx_d / max_cells max_d (|u_d| + c),
  *   dt_v = 3/14 min_d dx_d^2 / max_cells max(mu / rho, lambda / (rho c_v))
- *   (dt_v only when viscous or heat is on), computed in FP64. */
+ *   (dt_v only when viscous or heat is on), computed in FP64.  U is a
+ * 16-byte aligned device array of the handle's dtype (JF_ERR_ARG otherwise);
+ * dt_dev receives one FP64 value. */
 jf_status jf_compute_dt(jf_handle h, const void* U, double* dt_dev, void* stream);
 
 /* One TVD-RK3 step in place (Section 3.2, Algorithm 2):

@@ -60,7 +60,28 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U0, CflA
   T conv = T(0), diff = T(0);
   const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
   bool bad = false;
-  for (long long q = q0; q < end; q += stride) cell_rates(U, q, a.N, a.nactive, gamma, gm1, kdiff, conv, diff, bad);
+  constexpr int V = 16 / (int)sizeof(T);  // cells per 16-byte vector
+  if (!chunks && a.N % V == 0) {
+    // single grid: every component read in 16-byte vectors (U is 16-byte
+    // aligned and a component spans a whole number of vectors); the maxima
+    // are exact, so dt equals the scalar form's
+    using VT = typename Vec16<T>::type;
+    const VT* Uv = reinterpret_cast<const VT*>(U);
+    const long long Nv = a.N / V;
+    for (long long qv = q0; qv < Nv; qv += stride) {
+      T r[V], ru[V], rv[V], rw[V], E[V];
+      unpack(Uv[qv], r);
+      unpack(Uv[qv + Nv], ru);
+      unpack(Uv[qv + 2 * Nv], rv);
+      unpack(Uv[qv + 3 * Nv], rw);
+      unpack(Uv[qv + 4 * Nv], E);
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        cell_rates_of(r[k], ru[k], rv[k], rw[k], E[k], a.nactive, gamma, gm1, kdiff, conv, diff, bad);
+    }
+  } else {
+    for (long long q = q0; q < end; q += stride) cell_rates(U, q, a.N, a.nactive, gamma, gm1, kdiff, conv, diff, bad);
+  }
   if (bad) atomicOr(flag, 1);
   finish_cfl((double)conv, (double)diff, sc, nblocks, a.hmin, a.cfl, dto, dto2);
 }

@@ -456,6 +456,7 @@ jf_status jf_rhs(jf_handle h, const void* U, void* dUdt, void* stream) {
 jf_status jf_compute_dt(jf_handle h, const void* U, double* dt_dev, void* stream) {
   if (!h || h->kind != 0) { set_error(h, "jf_compute_dt: not a single-grid handle"); return JF_ERR_ARG; }
   if (!U || !dt_dev) { set_error(h, "jf_compute_dt: null pointer"); return JF_ERR_ARG; }
+  if (!aligned16(U)) { set_error(h, "jf_compute_dt: U must be a 16-byte aligned device array"); return JF_ERR_ARG; }
   return JF_DISPATCH(h, cfl_impl, h, U, dt_dev, nullptr, (cudaStream_t)stream);
 }
 

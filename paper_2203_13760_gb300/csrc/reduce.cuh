@@ -49,14 +49,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 // maxima are later formed in FP64, and a rate converted to FP64 is exact, so
 // the result is the exact maximum of the per-cell values.
 template <typename T>
-__device__ __forceinline__ void cell_rates(const T* __restrict__ U, long long q, long long N, int nactive, T gamma,
-                                           T gm1, T kdiff, T& conv, T& diff, bool& bad) {
-  const T r = U[q];
+__device__ __forceinline__ void cell_rates_of(T r, T ru, T rv, T rw, T E, int nactive, T gamma, T gm1, T kdiff,
+                                              T& conv, T& diff, bool& bad) {
   const T inv = T(1) / r;
-  const T u = U[q + N] * inv;
-  const T v = U[q + 2 * N] * inv;
-  const T w = U[q + 3 * N] * inv;
-  const T p = gm1 * (U[q + 4 * N] - T(0.5) * r * (u * u + v * v + w * w));
+  const T u = ru * inv;
+  const T v = rv * inv;
+  const T w = rw * inv;
+  const T p = gm1 * (E - T(0.5) * r * (u * u + v * v + w * w));
   bad |= !(r > T(0)) || !(p > T(0));
   const T c = tsqrt(gamma * p * inv);
   T m = fabs(u);
@@ -65,6 +64,19 @@ __device__ __forceinline__ void cell_rates(const T* __restrict__ U, long long q,
   conv = fmax(conv, m + c);
   diff = fmax(diff, kdiff * inv);
 }
+template <typename T>
+__device__ __forceinline__ void cell_rates(const T* __restrict__ U, long long q, long long N, int nactive, T gamma,
+                                           T gm1, T kdiff, T& conv, T& diff, bool& bad) {
+  cell_rates_of(U[q], U[q + N], U[q + 2 * N], U[q + 3 * N], U[q + 4 * N], nactive, gamma, gm1, kdiff, conv, diff,
+                bad);
+}
+
+// 16-byte vectors of cells (4 in FP32, 2 in FP64) for the CFL pass
+__device__ __forceinline__ void unpack(const float4& a, float o[4]) { o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; }
+__device__ __forceinline__ void unpack(const double2& a, double o[2]) { o[0] = a.x; o[1] = a.y; }
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
 
 // Block-wide FP64 maxima of (conv, diff) folded into sc; the CTA that takes
 // the last of `nblocks` tickets forms dt = CFL min(hmin / C, 3/14 hmin^2 / D)
