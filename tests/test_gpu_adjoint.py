@@ -93,6 +93,14 @@ def _tgv_off_symmetry(n):
     ("f32", 3e-5, lambda: inputs.kelvin_helmholtz(32, seed=3)),
     ("f64", 1e-12, lambda: _tgv_off_symmetry(12)),
     ("f32", 3e-5, lambda: _tgv_off_symmetry(16)),
+    # several ragged 2D boxes against zero-gradient and mixed boundaries: the
+    # ghost-cell fold of the halo accumulator, edges and corners included
+    ("f64", 1e-12, lambda: inputs.random_blocks((37, 21, 1), seed=13, bc=(1,) * 6)),
+    ("f32", 3e-5, lambda: inputs.random_blocks((37, 21, 1), seed=13, bc=(1,) * 6)),
+    ("f64", 1e-12, lambda: inputs.random_smooth((35, 19, 1), seed=14, bc=(0, 0, 1, 1, 1, 1), viscous=True,
+                                                mu=0.02)),
+    ("f64", 1e-12, lambda: inputs.random_smooth((18, 34, 1), seed=15, bc=(1, 1, 0, 0, 1, 1), viscous=True,
+                                                mu=0.02)),
 ])
 def test_dot_product_identity(orc, dtype, tol, make):
     case = make()
