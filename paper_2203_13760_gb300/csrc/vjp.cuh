@@ -19,12 +19,18 @@
 // a 5-cell halo around the box on every active axis (WENO5 of a face 3 cells
 // outside reads 2 more) and m with a 3-cell halo, evaluates the reverse pass
 // of every face whose stencil touches a cell of the box, and accumulates the
-// resulting cotangents of box cells in shared memory (shared-memory atomics:
-// the summation order, and so the last bits, may vary from run to run).
+// resulting cotangents in shared memory (shared-memory atomics: the
+// summation order, and so the last bits, may vary from run to run).
 // Ghost cells follow the boundary condition: with zero gradient a ghost has
 // no right-hand side (m = 0) and its cotangent goes to the interior cell it
 // copies; with periodic wrap every ghost face is a real face that the owning
 // box also evaluates, so only cotangents of the box's own cells are kept.
+// In 1D and 2D the accumulator covers the box and a 5-cell halo, so an
+// addition needs no ownership test; boxes near a non-periodic boundary fold
+// their ghost cells afterwards.  In 2D the viscous tangential stencil is
+// applied in two separable steps (cell-centre derivative cotangents, then a
+// gather pass) and the face tasks are ordered for conflict-free banks.  3D
+// boxes test ownership per addition (the halo accumulator would not fit).
 //
 // Faces are handled in their own frame (normal axis d, tangential axes t1,
 // t2): HLLC of the rotated state (normal velocity first) and the viscous
