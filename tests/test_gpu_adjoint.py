@@ -101,6 +101,11 @@ def _tgv_off_symmetry(n):
                                                 mu=0.02)),
     ("f64", 1e-12, lambda: inputs.random_smooth((18, 34, 1), seed=15, bc=(1, 1, 0, 0, 1, 1), viscous=True,
                                                 mu=0.02)),
+    # several 3D boxes: periodic 16^3 (every box has all its neighbours), and
+    # zero-gradient 24^3 (the middle box away from the boundary, the others
+    # folding ghost cotangents)
+    ("f64", 1e-12, lambda: _tgv_off_symmetry(16)),
+    ("f64", 1e-12, lambda: inputs.random_smooth((24, 24, 24), seed=16, bc=(1,) * 6, viscous=True, mu=0.02)),
 ])
 def test_dot_product_identity(orc, dtype, tol, make):
     case = make()
