@@ -25,9 +25,16 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   hll / rusanov flux     pinned (consistency, Rankine-Hugoniot across the HLL
                          fan, Rusanov = HLL with symmetric speeds, upwinding,
                          contact diffusion ordering)
-  signal_speeds          pinned (equal states give u -+ c; Toro's factor with
-                         the exact p* gives the exact shock speed; PVRS error
-                         of second order in the jump)
+  signal_speeds          pinned (equal states give u -+ c; Einfeldt's speed
+                         equals the exact shock speed of an isolated
+                         Rankine-Hugoniot shock, which only sqrt(rho)-weighted
+                         Roe averages give; Toro's factor with the exact p*
+                         gives the exact shock speed; PVRS error of second
+                         order in the jump)
+  safe reconstruction    pinned (the right-hand side with the flag equals the
+                         one assembled face by face with each non-positive
+                         WENO5 side replaced by its cell value; inert where
+                         every face state is positive)
   time_step (rk2/euler)  pinned (temporal orders 1, 2, 3; RK2 = mean of U and
                          two Euler steps)
   shock tubes            Sod and Lax against the exact solution for every

@@ -151,6 +151,13 @@ class _FeedForward(torch.autograd.Function):
     def backward(ctx, *grads):
         trajs = ctx.saved_tensors
         theta_bar = torch.zeros_like(ctx.batch._nn) if ctx.with_theta else None
+
+        # the C ABI wants 16-byte aligned states, which a trajectory slot of a
+        # state whose size is not a multiple of 16 bytes is not: such slots are
+        # passed as aligned copies
+        def aligned(x):
+            return x if x.data_ptr() % 16 == 0 else x.clone()
+
         if ctx.batch.supports_step_vjp():
             # every simulation of the batch in the same launches, one call per step
             g = [torch.zeros_like(tr) if gi is None else gi.contiguous() for tr, gi in zip(trajs, grads)]
@@ -160,7 +167,8 @@ class _FeedForward(torch.autograd.Function):
             if theta_bar is not None:  # one parameter-gradient launch for the whole sweep
                 ctx.batch.param_grad_begin(ctx.nsteps)
             for t in reversed(range(ctx.nsteps)):
-                ctx.batch.step_vjp([tr[t] for tr in trajs], dt, lam, nxt, [gi[t] for gi in g], theta_bar)
+                ctx.batch.step_vjp([aligned(tr[t]) for tr in trajs], dt, lam, nxt, [aligned(gi[t]) for gi in g],
+                                   theta_bar)
                 lam, nxt = nxt, lam
             if theta_bar is not None:
                 ctx.batch.param_grad_end(theta_bar)
@@ -173,9 +181,9 @@ class _FeedForward(torch.autograd.Function):
             lam = g[ctx.nsteps].clone()
             for t in reversed(range(ctx.nsteps)):
                 if theta_bar is not None:
-                    lam, _ = solver.rk3_step_vjp_params(traj[t], dt, lam, theta_bar=theta_bar)
+                    lam, _ = solver.rk3_step_vjp_params(aligned(traj[t]), dt, lam, theta_bar=theta_bar)
                 else:
-                    lam = solver.rk3_step_vjp(traj[t], dt, lam)
+                    lam = solver.rk3_step_vjp(aligned(traj[t]), dt, lam)
                 lam += g[t]
             out.append(lam)
         return (None, None, None, theta_bar, *out)
