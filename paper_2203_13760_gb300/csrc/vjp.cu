@@ -34,8 +34,13 @@ jf_status vjp_backward(jf_ctx* h, const T* U0, const T* U1, const T* U2, const d
       cudaError_t e = cudaMalloc(&h->adj[i], 5 * h->N * sizeof(T));
       if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_vjp: adjoint buffers");
     }
+  if (h->dim == 3 && !h->adj[3]) {  // the z-marching kernel's accumulator of W (+T) cotangents
+    cudaError_t e = cudaMalloc(&h->adj[3], 6 * h->N * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_vjp: adjoint accumulator");
+  }
   T* l2 = static_cast<T*>(h->adj[0]);
   T* l1 = static_cast<T*>(h->adj[1]);
+  T* scratch = static_cast<T*>(h->adj[3]);
   VjpArgs<T> V;
   V.n[0] = h->grid.nx;
   V.n[1] = h->grid.ny;
@@ -56,7 +61,7 @@ jf_status vjp_backward(jf_ctx* h, const T* U0, const T* U1, const T* U2, const d
   };
   for (const Call& c : calls) {
     V.Us = c.Us; V.lam = c.lam; V.s_in = c.s_in; V.x1 = c.x1; V.a1 = c.a1; V.x2 = c.x2; V.a2 = c.a2; V.out = c.out;
-    cudaError_t e = L(V, g, s);
+    cudaError_t e = L(V, g, scratch, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "jf_rk3_step_vjp: kernel launch");
   }
   return JF_OK;

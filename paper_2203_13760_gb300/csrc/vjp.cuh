@@ -1,5 +1,7 @@
 // Adjoint (vector-Jacobian product) of one Shu-Osher stage (Sections 3.1-3.4,
-// Section 7.2), for 1D, 2D and 3D grids.
+// Section 7.2): the per-face reverse passes, and the box kernel that runs
+// them on 1D and 2D grids (3D grids: the z-marching kernel of vjp3.cuh,
+// which calls the same reverse passes).
 //
 // One launch computes, for every interior cell,
 //   out = a1 x1 + a2 x2 + m + dt J(Us)^T m,   m = s_in lam,
@@ -15,7 +17,7 @@
 // its stencil cells; the cell then applies the transposed Jacobian of
 // W(U) (and of T = p / (rho R)).
 //
-// Tiling.  A CTA owns a BX x BY x BZ box of cells.  It stages the primitives of
+// Tiling.  A CTA owns a BX (x BY) box of cells.  It stages the primitives of
 // a 5-cell halo around the box on every active axis (WENO5 of a face 3 cells
 // outside reads 2 more) and m with a 3-cell halo, evaluates the reverse pass
 // of every face whose stencil touches a cell of the box, and accumulates the
@@ -25,12 +27,11 @@
 // no right-hand side (m = 0) and its cotangent goes to the interior cell it
 // copies; with periodic wrap every ghost face is a real face that the owning
 // box also evaluates, so only cotangents of the box's own cells are kept.
-// In 1D and 2D the accumulator covers the box and a 5-cell halo, so an
-// addition needs no ownership test; boxes near a non-periodic boundary fold
-// their ghost cells afterwards.  In 2D the viscous tangential stencil is
-// applied in two separable steps (cell-centre derivative cotangents, then a
-// gather pass) and the face tasks are ordered for conflict-free banks.  3D
-// boxes test ownership per addition (the halo accumulator would not fit).
+// The accumulator covers the box and a 5-cell halo, so an addition needs no
+// ownership test; boxes near a non-periodic boundary fold their ghost cells
+// afterwards.  In 2D the viscous tangential stencil is applied in two
+// separable steps (cell-centre derivative cotangents, then a gather pass) and
+// the face tasks are ordered for conflict-free banks.
 //
 // Faces are handled in their own frame (normal axis d, tangential axes t1,
 // t2): HLLC of the rotated state (normal velocity first) and the viscous
@@ -62,29 +63,27 @@ struct VjpArgs {
 
 template <int BX, int BY, int BZ, int DIM, bool VISC>
 struct VGeo {
-  static constexpr int HX = 5, HY = DIM >= 2 ? 5 : 0, HZ = DIM == 3 ? 5 : 0;  // W halo
+  static constexpr int HX = 5, HY = DIM >= 2 ? 5 : 0, HZ = 0;  // W halo
   static constexpr int PX = BX + 2 * HX, PY = BY + 2 * HY, PZ = BZ + 2 * HZ, CS = PX * PY * PZ;
   static constexpr int NCW = VISC ? 6 : 5;
-  static constexpr int MX = 3, MY = DIM >= 2 ? 3 : 0, MZ = DIM == 3 ? 3 : 0;  // m halo
+  static constexpr int MX = 3, MY = DIM >= 2 ? 3 : 0, MZ = 0;  // m halo
   static constexpr int MPX = BX + 2 * MX, MPY = BY + 2 * MY, MPZ = BZ + 2 * MZ, MCS = MPX * MPY * MPZ;
   static constexpr int NCELL = BX * BY * BZ;
   static constexpr int NT = NCELL;
-  // 1D / 2D: cotangents accumulate over the box and a 5-cell halo (every cell
-  // a face's stencil reaches), with no ownership test per addition; boxes
-  // near a non-periodic boundary fold ghost cells onto the cells they copy
-  // afterwards.  3D: the halo would not fit in shared memory, so additions
-  // test ownership and only box cells are held.
-  static constexpr bool EXT = DIM <= 2;
-  static constexpr int AX = EXT ? 5 : 0, AY = EXT && DIM >= 2 ? 5 : 0;
-  static constexpr int APX = BX + 2 * AX, APY = BY + 2 * AY, ACS = EXT ? APX * APY : NCELL;
+  // cotangents accumulate over the box and a 5-cell halo (every cell a face's
+  // stencil reaches), with no ownership test per addition; boxes near a
+  // non-periodic boundary fold ghost cells onto the cells they copy afterwards
+  static constexpr int AX = 5, AY = DIM >= 2 ? 5 : 0;
+  static constexpr int APX = BX + 2 * AX, APY = BY + 2 * AY, ACS = APX * APY;
   // 2D viscous: the tangential C4 stencil (DC4 along the tangent at the cells
   // -1..2 along the normal, then RC4 to the face) is separable, so a face
   // adds its cotangents of the four cell-centre derivatives (slots
   // d * 2 + k: k = 0 for du_n/de, 1 for du_e/de) and one gather pass applies
   // the transposed DC4 afterwards: 8 instead of 32 additions per face.
-  static constexpr int NCB = EXT && DIM == 2 && VISC ? 4 : 0;
+  static constexpr int NCB = DIM == 2 && VISC ? 4 : 0;
+  static_assert(DIM <= 2, "3D grids take the z-marching kernel (vjp3.cuh)");
   static_assert(DIM >= 2 || BY == 1, "1D boxes are one row");
-  static_assert(DIM == 3 || BZ == 1, "1D/2D boxes are one plane");
+  static_assert(BZ == 1, "boxes are one plane");
 };
 
 template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
@@ -142,20 +141,21 @@ __device__ __forceinline__ void task_rc(int f, int& r, int& c) {
 template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
 struct VTile {
   using G = VGeo<BX, BY, BZ, DIM, VISC>;
-  const T* W;   // [NCW][PZ][PY][PX], box cell (0, 0, 0) at (HX, HY, HZ)
-  const T* M;   // [5][MPZ][MPY][MPX]
-  T* acc;       // [6][APY][APX] (1D / 2D, box cell (0, 0) at (AX, AY)) or [6][BZ][BY][BX] (3D)
+  static constexpr int NCB = G::NCB;
+  const T* W;   // [NCW][PY][PX], box cell (0, 0) at (HX, HY)
+  const T* M;   // [5][MPY][MPX]
+  T* acc;       // [6][APY][APX], box cell (0, 0) at (AX, AY)
   T* cb;        // [NCB][APY][APX]: cotangents of cell-centre tangential derivatives (2D viscous)
   int g0[3], n[3], per[3];
 
   // coordinates along inactive axes are always 0: fold them at compile time
-  __device__ __forceinline__ T w(int c, int x, int y, int z) const {
-    const int yy = DIM >= 2 ? y : 0, zz = DIM == 3 ? z : 0;
-    return W[c * G::CS + ((zz + G::HZ) * G::PY + (yy + G::HY)) * G::PX + x + G::HX];
+  __device__ __forceinline__ T w(int c, int x, int y, int) const {
+    const int yy = DIM >= 2 ? y : 0;
+    return W[c * G::CS + (yy + G::HY) * G::PX + x + G::HX];
   }
-  __device__ __forceinline__ T m(int c, int x, int y, int z) const {
-    const int yy = DIM >= 2 ? y : 0, zz = DIM == 3 ? z : 0;
-    return M[c * G::MCS + ((zz + G::MZ) * G::MPY + (yy + G::MY)) * G::MPX + x + G::MX];
+  __device__ __forceinline__ T m(int c, int x, int y, int) const {
+    const int yy = DIM >= 2 ? y : 0;
+    return M[c * G::MCS + (yy + G::MY) * G::MPX + x + G::MX];
   }
   // box coordinate that keeps a cotangent landing on box-relative coordinate
   // x along an axis, or -1 if it is not this box's to keep
@@ -166,16 +166,9 @@ struct VTile {
     const int t = c - x0;
     return (t >= 0 && t < B) ? t : -1;
   }
-  __device__ __forceinline__ void add(int c, int x, int y, int z, T v) const {
-    if constexpr (G::EXT) {
-      const int yy = DIM >= 2 ? y : 0;
-      atomicAdd(acc + c * G::ACS + (yy + G::AY) * G::APX + x + G::AX, v);
-      return;
-    }
-    const int tx = owner(x, g0[0], n[0], per[0], BX);
-    const int ty = DIM >= 2 ? owner(y, g0[1], n[1], per[1], BY) : 0;
-    const int tz = DIM == 3 ? owner(z, g0[2], n[2], per[2], BZ) : 0;
-    if (tx >= 0 && ty >= 0 && tz >= 0) atomicAdd(acc + ((c * BZ + tz) * BY + ty) * BX + tx, v);
+  __device__ __forceinline__ void add(int c, int x, int y, int, T v) const {
+    const int yy = DIM >= 2 ? y : 0;
+    atomicAdd(acc + c * G::ACS + (yy + G::AY) * G::APX + x + G::AX, v);
   }
   __device__ __forceinline__ void add_cb(int slot, int x, int y, T v) const {
     atomicAdd(cb + slot * G::ACS + (y + G::AY) * G::APX + x + G::AX, v);
@@ -193,9 +186,11 @@ __device__ __forceinline__ T sel5(const T v[5], int i) {
 
 // Reverse pass of the convective flux of the face between box cell p and its
 // neighbour along F.d; nu = dLoss/dNF (NF = -F + ...).
-template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
-__device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY, BZ>& V, const Frame& F,
-                                              const int p[3], const T nu[5], const Gas<T>& g) {
+// Tile: any accessor with w(c, x, y, z) (primitive c of a cell, tile-relative
+// coordinates) and add(c, x, y, z, v) (cotangent accumulation).
+template <typename T, int DIM, bool VISC, typename Tile>
+__device__ __forceinline__ void conv_face_vjp(const Tile& V, const Frame& F, const int p[3], const T nu[5],
+                                              const Gas<T>& g) {
   auto at = [&](int c, int s) -> T {
     return V.w(c, p[0] + F.pick(0, s, 0, 0), p[1] + F.pick(1, s, 0, 0), p[2] + F.pick(2, s, 0, 0));
   };
@@ -287,9 +282,9 @@ __device__ __forceinline__ void conv_face_vjp(const VTile<T, DIM, VISC, BX, BY, 
 //   div = du_n/dn + sum_j du_ej/de_j;
 //   tau_n = mu (2 du_n/dn - 2/3 div), tau_ej = mu (du_n/de_j + du_ej/dn);
 //   F^d = [0, tau, u_f . tau + lambda dT/dn] (tau_n in component 1 + d).
-template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
-__device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY, BZ>& V, const Frame& F,
-                                              const int p[3], const T nu[5], const Gas<T>& g, const T inv_h[3]) {
+template <typename T, int DIM, bool VISC, typename Tile>
+__device__ __forceinline__ void visc_face_vjp(const Tile& V, const Frame& F, const int p[3], const T nu[5],
+                                              const Gas<T>& g, const T inv_h[3]) {
   auto at = [&](int c, int s, int a, int b) -> T {
     return V.w(c, p[0] + F.pick(0, s, a, b), p[1] + F.pick(1, s, a, b), p[2] + F.pick(2, s, a, b));
   };
@@ -365,7 +360,7 @@ __device__ __forceinline__ void visc_face_vjp(const VTile<T, DIM, VISC, BX, BY, 
     for (int k = 0; k < 2; ++k) {
       const int c = k == 0 ? comp[0] : comp[1 + j];
       const T gb = (k == 0 ? g.mu * taub[1 + j] : divb) * he[j];
-      if constexpr (VGeo<BX, BY, BZ, DIM, VISC>::NCB > 0) {
+      if constexpr (Tile::NCB > 0) {
         // centre-derivative cotangents; the gather pass spreads them along the tangent
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -393,17 +388,16 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   T* Mb = Wb + G::NCW * G::CS;
   T* acc = Mb + 5 * G::MCS;
   T* cbuf = acc + 6 * G::ACS;
-  const int g0[3] = {(int)blockIdx.x * BX, (int)blockIdx.y * BY, (int)blockIdx.z * BZ};
+  const int g0[3] = {(int)blockIdx.x * BX, (int)blockIdx.y * BY, 0};
   const int tid = threadIdx.x;
 
   // stage W (halo 5) and m = s_in lam (halo 3; zero on zero-gradient ghosts)
   bool bad = false;
   for (int t = tid; t < G::CS; t += G::NT) {
-    const int lx = t % G::PX, ly = (t / G::PX) % G::PY, lz = t / (G::PX * G::PY);
+    const int lx = t % G::PX, ly = t / G::PX;
     const int gx = map_index(g0[0] + lx - G::HX, A.n[0], A.periodic[0]);
     const int gy = DIM >= 2 ? map_index(g0[1] + ly - G::HY, A.n[1], A.periodic[1]) : 0;
-    const int gz = DIM == 3 ? map_index(g0[2] + lz - G::HZ, A.n[2], A.periodic[2]) : 0;
-    const long long q = ((long long)gz * A.n[1] + gy) * A.n[0] + gx;
+    const long long q = (long long)gy * A.n[0] + gx;
     const T r = A.Us[q];
     const T inv = trcp(r);
     const T u = A.Us[q + A.N] * inv, v = A.Us[q + 2 * A.N] * inv, w = A.Us[q + 3 * A.N] * inv;
@@ -418,15 +412,14 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   }
   if (bad) atomicOr(A.flag, 1);
   for (int t = tid; t < G::MCS; t += G::NT) {
-    const int lx = t % G::MPX, ly = (t / G::MPX) % G::MPY, lz = t / (G::MPX * G::MPY);
-    const int r[3] = {g0[0] + lx - G::MX, DIM >= 2 ? g0[1] + ly - G::MY : 0, DIM == 3 ? g0[2] + lz - G::MZ : 0};
+    const int lx = t % G::MPX, ly = t / G::MPX;
+    const int r[2] = {g0[0] + lx - G::MX, DIM >= 2 ? g0[1] + ly - G::MY : 0};
     bool ghost = false;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) ghost |= !A.periodic[a] && (r[a] < 0 || r[a] >= A.n[a]);
     const int gx = map_index(r[0], A.n[0], A.periodic[0]);
     const int gy = DIM >= 2 ? map_index(r[1], A.n[1], A.periodic[1]) : 0;
-    const int gz = DIM == 3 ? map_index(r[2], A.n[2], A.periodic[2]) : 0;
-    const long long q = ((long long)gz * A.n[1] + gy) * A.n[0] + gx;
+    const long long q = (long long)gy * A.n[0] + gx;
 #pragma unroll
     for (int c = 0; c < 5; ++c) Mb[c * G::MCS + t] = ghost ? T(0) : A.s_in * A.lam[q + c * A.N];
   }
@@ -465,7 +458,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   // box's own cells across), then, if viscous, the dissipative faces (left
   // cells -2 .. B_d along d, -2 .. B+1 across on the active tangential axes).
   // Face index -> (s along d, a along t1, b along t2): in 2D by task_rc (16
-  // rows of two adjacent columns per warp); in 1D and 3D with the x
+  // rows of two adjacent columns per warp); in 1D with the x
   // coordinate fastest across the lanes of a warp (x is s for d = 0, b (t2)
   // for d = 1 and a (t1) for d = 2).
   auto conv_task = [&](auto dtag, int f) {
@@ -503,7 +496,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     }
     const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
     T nu[5];
-    if (face_nu(F, p, nu)) conv_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g);
+    if (face_nu(F, p, nu)) conv_face_vjp<T, DIM, VISC>(V, F, p, nu, g);
   };
   auto visc_task = [&](auto dtag, int f) {
     constexpr int d = decltype(dtag)::value;
@@ -541,7 +534,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     }
     const int p[3] = {F.pick(0, s, a, b), F.pick(1, s, a, b), F.pick(2, s, a, b)};
     T nu[5];
-    if (face_nu(F, p, nu)) visc_face_vjp<T, DIM, VISC, BX, BY, BZ>(V, F, p, nu, g, inv_h);
+    if (face_nu(F, p, nu)) visc_face_vjp<T, DIM, VISC>(V, F, p, nu, g, inv_h);
   };
   using C = VCount<DIM, BX, BY, BZ>;
   constexpr int c0 = C::conv(0), c1 = C::conv(1), c2 = C::conv(2);
@@ -555,10 +548,6 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
       if (r < c1) { conv_task(std::integral_constant<int, 1>{}, r); continue; }
       r -= c1;
     }
-    if constexpr (DIM == 3) {
-      if (r < c2) { conv_task(std::integral_constant<int, 2>{}, r); continue; }
-      r -= c2;
-    }
     if constexpr (VISC) {
       if (r < v0) { visc_task(std::integral_constant<int, 0>{}, r); continue; }
       r -= v0;
@@ -566,7 +555,6 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
         if (r < v1) { visc_task(std::integral_constant<int, 1>{}, r); continue; }
         r -= v1;
       }
-      if constexpr (DIM == 3) visc_task(std::integral_constant<int, 2>{}, r);
     }
   }
   __syncthreads();
@@ -596,7 +584,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     __syncthreads();
   }
 
-  if constexpr (G::EXT) {
+  {
     // ghost cells of a non-periodic axis pass their cotangents to the cell
     // they copy (if it is in this box); everything else outside the box (and
     // beyond the grid on a periodic axis) belongs to another box, which
@@ -624,12 +612,12 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
   }
 
   // cells: cotangent of W (+T) -> cotangent of U, then the stage combination
-  const int tx = tid % BX, ty = (tid / BX) % BY, tz = tid / (BX * BY);
-  const int gx = g0[0] + tx, gy = g0[1] + ty, gz = g0[2] + tz;
-  if (gx < A.n[0] && gy < A.n[1] && gz < A.n[2]) {
+  const int tx = tid % BX, ty = tid / BX, tz = 0;
+  const int gx = g0[0] + tx, gy = g0[1] + ty;
+  if (gx < A.n[0] && gy < A.n[1]) {
     const T r = V.w(0, tx, ty, tz), u = V.w(1, tx, ty, tz), v = V.w(2, tx, ty, tz), w = V.w(3, tx, ty, tz);
     const T p = V.w(4, tx, ty, tz);
-    const int cell = G::EXT ? (ty + G::AY) * G::APX + tx + G::AX : (tz * BY + ty) * BX + tx;
+    const int cell = (ty + G::AY) * G::APX + tx + G::AX;
     T br = acc[cell], bu = acc[G::ACS + cell], bv = acc[2 * G::ACS + cell], bw = acc[3 * G::ACS + cell];
     T bp = acc[4 * G::ACS + cell];
     const T inv = trcp(r);
@@ -646,7 +634,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, MINB) vjp_stage_kernel(const Vjp
     bU[3] = bw * inv - bp * g.gm1 * w;
     bU[4] = bp * g.gm1;
     const T dt = T(*A.dt);
-    const long long q = ((long long)gz * A.n[1] + gy) * A.n[0] + gx;
+    const long long q = (long long)gy * A.n[0] + gx;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       T o = V.m(c, tx, ty, tz) + dt * bU[c];

@@ -1,0 +1,284 @@
+// Adjoint of one Shu-Osher stage on 3D grids, marching along z (Sections
+// 3.1-3.4, Section 7.2).  Same product as vjp_stage_kernel,
+//   out = a1 x1 + a2 x2 + m + dt J(Us)^T m,   m = s_in lam,
+// organised like the forward stage kernel instead of in boxes:
+//
+//  * A CTA owns a BX x BY column of cells and a chunk of planes along z.  It
+//    evaluates every face it owns exactly once: the lower face of each of its
+//    cells along x, y and z, and on a non-periodic axis also the upper
+//    boundary face of the grid's last cell.  Every face of the grid is owned
+//    by exactly one CTA, so no face is evaluated twice (the box kernel
+//    evaluated the faces of a 5-cell halo around every box).
+//  * The primitive variables (+T) of the planes k-3 .. k+2 live in a
+//    six-slot shared-memory ring with a 3-cell x/y halo, and m = s_in lam of
+//    the planes k-1, k in a two-slot ring with a 1-cell halo (zero on
+//    zero-gradient ghosts: ghosts have no right-hand side).
+//  * At face plane k the CTA runs the reverse passes of the x and y faces of
+//    plane k and of the z face between planes k-1 and k (convective and, if
+//    viscous, dissipative: the same per-face code as the box kernel).  Their
+//    cotangents of W (+T) land on cells of the planes k-3 .. k+2 (tile plus a
+//    3-cell halo) and are accumulated in a second six-slot shared-memory
+//    ring with shared-memory atomics.
+//  * Plane k-3 then receives nothing more from this CTA: its accumulator slot
+//    is added to a global accumulator G[NCW][N] with global atomics, each
+//    halo or ghost cell mapped to the cell it stands for (periodic wrap,
+//    zero-gradient clamp: a ghost copies the boundary cell, so its cotangent
+//    belongs to that cell), and the slot takes plane k+3.
+//  * A per-cell pass (vjp3_finish_kernel) applies the transposed Jacobian of
+//    W(U) and T = p / (rho R) to G and forms the stage combination.
+//
+// Summation order of the atomics, and so the last bits, may vary between
+// runs, as in the box kernel.
+#pragma once
+#include "vjp.cuh"
+
+namespace jf {
+
+template <int BX, int BY, bool VISC>
+struct V3Geo {
+  static constexpr int H = 3;                        // halo of the W and accumulator planes
+  static constexpr int PX = BX + 2 * H, PY = BY + 2 * H, CS = PX * PY;
+  static constexpr int NCW = VISC ? 6 : 5;           // rho, u, v, w, p (, T)
+  static constexpr int PLANE = NCW * CS;
+  static constexpr int RING = 6;                     // planes k-3 .. k+2
+  static constexpr int MPX = BX + 2, MPY = BY + 2, MCS = MPX * MPY;  // m planes, 1-cell halo
+};
+
+template <typename T, bool VISC, int BX, int BY>
+constexpr size_t vjp3_smem_bytes() {
+  using G = V3Geo<BX, BY, VISC>;
+  return sizeof(T) * (size_t)(2 * G::RING * G::PLANE + 2 * 5 * G::MCS);
+}
+
+// Accessor of the rings at face plane k: coordinates relative to the tile
+// origin along x, y and to plane k along z (z in -3 .. 2 for W and the
+// accumulator, -1 .. 0 for m).
+template <typename T, bool VISC, int BX, int BY>
+struct V3Tile {
+  using G = V3Geo<BX, BY, VISC>;
+  static constexpr int NCB = 0;  // tangential cotangents scattered directly
+  const T* W;
+  T* acc;
+  const T* M;
+  int wp[6];  // element offset of the W / accumulator slot of plane k + z, index z + 3
+  int mp[2];  // element offset of the m slot of plane k + z, index z + 1
+  __device__ __forceinline__ T w(int c, int x, int y, int z) const {
+    return W[wp[z + 3] + c * G::CS + (y + G::H) * G::PX + x + G::H];
+  }
+  __device__ __forceinline__ void add(int c, int x, int y, int z, T v) const {
+    atomicAdd(acc + wp[z + 3] + c * G::CS + (y + G::H) * G::PX + x + G::H, v);
+  }
+  __device__ __forceinline__ T m(int c, int x, int y, int z) const {
+    return M[mp[z + 1] + c * G::MCS + (y + 1) * G::MPX + x + 1];
+  }
+};
+
+// Primitives (+T) of plane gz (unmapped) into W slot dst.
+template <typename T, bool VISC, int BX, int BY, int NT>
+__device__ __forceinline__ void vjp3_load_w(const VjpArgs<T>& A, const Gas<T>& g, T* dst, int x0, int y0, int gz,
+                                            bool& bad) {
+  using G = V3Geo<BX, BY, VISC>;
+  const int kz = map_index(gz, A.n[2], A.periodic[2]);
+  for (int t = threadIdx.x; t < G::CS; t += NT) {
+    const int ly = t / G::PX, lx = t - ly * G::PX;
+    const int gx = map_index(x0 + lx - G::H, A.n[0], A.periodic[0]);
+    const int gy = map_index(y0 + ly - G::H, A.n[1], A.periodic[1]);
+    const long long q = ((long long)kz * A.n[1] + gy) * A.n[0] + gx;
+    const T r = A.Us[q];
+    const T inv = trcp(r);
+    const T u = A.Us[q + A.N] * inv, v = A.Us[q + 2 * A.N] * inv, w = A.Us[q + 3 * A.N] * inv;
+    const T p = g.gm1 * (A.Us[q + 4 * A.N] - T(0.5) * r * (u * u + v * v + w * w));
+    bad |= !(r > T(0)) || !(p > T(0));
+    dst[t] = r;
+    dst[G::CS + t] = u;
+    dst[2 * G::CS + t] = v;
+    dst[3 * G::CS + t] = w;
+    dst[4 * G::CS + t] = p;
+    if (VISC) dst[5 * G::CS + t] = p * inv * g.inv_R;
+  }
+}
+
+// m = s_in lam of plane gz (unmapped) into m slot dst; zero on zero-gradient ghosts.
+template <typename T, bool VISC, int BX, int BY, int NT>
+__device__ __forceinline__ void vjp3_load_m(const VjpArgs<T>& A, T* dst, int x0, int y0, int gz) {
+  using G = V3Geo<BX, BY, VISC>;
+  const bool gzout = !A.periodic[2] && (gz < 0 || gz >= A.n[2]);
+  const int kz = map_index(gz, A.n[2], A.periodic[2]);
+  for (int t = threadIdx.x; t < G::MCS; t += NT) {
+    const int ly = t / G::MPX, lx = t - ly * G::MPX;
+    const int rx = x0 + lx - 1, ry = y0 + ly - 1;
+    const bool ghost = gzout || (!A.periodic[0] && (rx < 0 || rx >= A.n[0])) ||
+                       (!A.periodic[1] && (ry < 0 || ry >= A.n[1]));
+    const int gx = map_index(rx, A.n[0], A.periodic[0]);
+    const int gy = map_index(ry, A.n[1], A.periodic[1]);
+    const long long q = ((long long)kz * A.n[1] + gy) * A.n[0] + gx;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) dst[c * G::MCS + t] = ghost ? T(0) : A.s_in * A.lam[q + c * A.N];
+  }
+}
+
+// Accumulator slot src (plane gz, unmapped) added to Gacc and cleared.
+template <typename T, bool VISC, int BX, int BY, int NT>
+__device__ __forceinline__ void vjp3_flush(const VjpArgs<T>& A, T* src, T* __restrict__ Gacc, int x0, int y0,
+                                           int gz) {
+  using G = V3Geo<BX, BY, VISC>;
+  const int kz = map_index(gz, A.n[2], A.periodic[2]);
+  for (int t = threadIdx.x; t < G::PLANE; t += NT) {
+    const T v = src[t];
+    if (v != T(0)) {
+      const int c = t / G::CS, r = t - c * G::CS;
+      const int ly = r / G::PX, lx = r - ly * G::PX;
+      const int gx = map_index(x0 + lx - G::H, A.n[0], A.periodic[0]);
+      const int gy = map_index(y0 + ly - G::H, A.n[1], A.periodic[1]);
+      atomicAdd(Gacc + (long long)c * A.N + ((long long)kz * A.n[1] + gy) * A.n[0] + gx, v);
+      src[t] = T(0);
+    }
+  }
+}
+
+// The face reverse passes.  blockDim.x == NT; grid = (ceil(nx/BX),
+// ceil(ny/BY), ceil(nz/zchunk)).  Gacc [NCW][N] must be zero on entry.
+template <typename T, bool VISC, int BX, int BY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    vjp3_kernel(const VjpArgs<T> A, const Gas<T> g, T* __restrict__ Gacc, int zchunk) {
+  using G = V3Geo<BX, BY, VISC>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Wr = reinterpret_cast<T*>(smem_raw);  // [RING][NCW][PY][PX]
+  T* Ar = Wr + G::RING * G::PLANE;         // [RING][NCW][PY][PX]
+  T* Mr = Ar + G::RING * G::PLANE;         // [2][5][MPY][MPX]
+  const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, nz);
+  const int ex = min(BX, nx - x0), ey = min(BY, ny - y0);
+  // owned faces per row / column: the lower faces of the tile's cells, plus
+  // the upper boundary face of the grid's last cell on a non-periodic axis
+  const int fx = ex + ((!A.periodic[0] && x0 + BX >= nx) ? 1 : 0);
+  const int fy = ey + ((!A.periodic[1] && y0 + BY >= ny) ? 1 : 0);
+  const int kend = z1 + ((!A.periodic[2] && z1 == nz) ? 1 : 0);  // face plane nz: the top boundary z face
+  const T inv_h[3] = {A.inv_h[0], A.inv_h[1], A.inv_h[2]};
+
+  bool bad = false;
+  for (int q = 0; q < G::RING; ++q)
+    vjp3_load_w<T, VISC, BX, BY, NT>(A, g, Wr + q * G::PLANE, x0, y0, z0 - 3 + q, bad);
+  for (int t = threadIdx.x; t < G::RING * G::PLANE; t += NT) Ar[t] = T(0);
+  vjp3_load_m<T, VISC, BX, BY, NT>(A, Mr, x0, y0, z0 - 1);
+  vjp3_load_m<T, VISC, BX, BY, NT>(A, Mr + 5 * G::MCS, x0, y0, z0);
+  if (bad) atomicOr(A.flag, 1);
+  __syncthreads();
+
+  V3Tile<T, VISC, BX, BY> V;
+  V.W = Wr;
+  V.acc = Ar;
+  V.M = Mr;
+  for (int k = z0; k < kend; ++k) {
+    const int b = (k - z0) % G::RING;  // slot of plane k - 3
+#pragma unroll
+    for (int z = -3; z <= 2; ++z) {
+      int s = b + z + 3;
+      s = s >= G::RING ? s - G::RING : s;
+      V.wp[z + 3] = s * G::PLANE;
+    }
+    V.mp[0] = ((k - z0) & 1) * 5 * G::MCS;
+    V.mp[1] = ((k - z0 + 1) & 1) * 5 * G::MCS;
+
+    auto face_nu = [&](auto dtag, const int p[3], T nu[5]) -> bool {
+      constexpr int d = decltype(dtag)::value;
+      const T h = inv_h[d];
+      bool any = false;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        nu[c] = (V.m(c, p[0], p[1], p[2]) - V.m(c, p[0] + (d == 0), p[1] + (d == 1), p[2] + (d == 2))) * h;
+        any |= nu[c] != T(0);
+      }
+      return any;
+    };
+    auto run_face = [&](auto dtag, const int p[3], bool visc) {
+      constexpr int d = decltype(dtag)::value;
+      const Frame F{d, (d + 1) % 3, (d + 2) % 3};
+      T nu[5];
+      if (!face_nu(dtag, p, nu)) return;
+      if (VISC && visc)
+        visc_face_vjp<T, 3, VISC>(V, F, p, nu, g, inv_h);
+      else
+        conv_face_vjp<T, 3, VISC>(V, F, p, nu, g);
+    };
+
+    const bool xy = k < z1;  // plane nz (top boundary) has only its z face
+    const int nfx = xy ? ey * fx : 0, nfy = xy ? fy * ex : 0, nfz = ex * ey;
+    const int nconv = nfx + nfy + nfz;
+    const int total = VISC ? 2 * nconv : nconv;
+    for (int t = threadIdx.x; t < total; t += NT) {
+      int r = t;
+      const bool visc = VISC && r >= nconv;
+      if (visc) r -= nconv;
+      if (r < nfx) {  // x face: lower face of cell (x0 + f, y0 + j, k)
+        const int j = r / fx, f = r - j * fx;
+        const int p[3] = {f - 1, j, 0};
+        run_face(std::integral_constant<int, 0>{}, p, visc);
+      } else if ((r -= nfx) < nfy) {  // y face: lower face of cell (x0 + i, y0 + f, k)
+        const int f = r / ex, i = r - f * ex;
+        const int p[3] = {i, f - 1, 0};
+        run_face(std::integral_constant<int, 1>{}, p, visc);
+      } else {  // z face between planes k - 1 and k
+        r -= nfy;
+        const int j = r / ex, i = r - j * ex;
+        const int p[3] = {i, j, -1};
+        run_face(std::integral_constant<int, 2>{}, p, visc);
+      }
+    }
+    __syncthreads();
+    // plane k - 3 is complete: add it to the global accumulator, then its
+    // slots take plane k + 3 (W, cleared accumulator) and the m slot of plane
+    // k - 1 takes plane k + 1
+    vjp3_flush<T, VISC, BX, BY, NT>(A, Ar + b * G::PLANE, Gacc, x0, y0, k - 3);
+    if (k + 1 < kend) {
+      vjp3_load_w<T, VISC, BX, BY, NT>(A, g, Wr + b * G::PLANE, x0, y0, k + 3, bad);
+      vjp3_load_m<T, VISC, BX, BY, NT>(A, Mr + ((k - z0) & 1) * 5 * G::MCS, x0, y0, k + 1);
+    }
+    __syncthreads();
+  }
+  // the planes still held: kend - 3 .. kend + 1
+  for (int pl = kend - 3; pl <= kend + 1; ++pl) {
+    int s = (pl - z0 + 3) % G::RING;
+    vjp3_flush<T, VISC, BX, BY, NT>(A, Ar + s * G::PLANE, Gacc, x0, y0, pl);
+  }
+  if (bad) atomicOr(A.flag, 1);
+}
+
+// Per cell: cotangent of W (+T) in Gacc -> cotangent of U (transposed
+// Jacobian of W(U), and of T = p / (rho R)), then
+// out = m + dt J^T m + a1 x1 + a2 x2.
+template <typename T, bool VISC>
+__global__ void __launch_bounds__(256) vjp3_finish_kernel(const VjpArgs<T> A, const Gas<T> g,
+                                                          const T* __restrict__ Gacc) {
+  const long long N = A.N;
+  const T dt = T(*A.dt);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+    const T r = A.Us[q];
+    const T inv = trcp(r);
+    const T u = A.Us[q + N] * inv, v = A.Us[q + 2 * N] * inv, w = A.Us[q + 3 * N] * inv;
+    const T p = g.gm1 * (A.Us[q + 4 * N] - T(0.5) * r * (u * u + v * v + w * w));
+    T br = Gacc[q], bu = Gacc[q + N], bv = Gacc[q + 2 * N], bw = Gacc[q + 3 * N], bp = Gacc[q + 4 * N];
+    if (VISC) {
+      const T bT = Gacc[q + 5 * N];
+      const T Tc = p * inv * g.inv_R;
+      br -= bT * Tc * inv;  // T = p / (rho R)
+      bp += bT * Tc * trcp(p);
+    }
+    T bU[5];
+    bU[0] = br - (bu * u + bv * v + bw * w) * inv + bp * g.gm1 * T(0.5) * (u * u + v * v + w * w);
+    bU[1] = bu * inv - bp * g.gm1 * u;
+    bU[2] = bv * inv - bp * g.gm1 * v;
+    bU[3] = bw * inv - bp * g.gm1 * w;
+    bU[4] = bp * g.gm1;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      T o = A.s_in * A.lam[q + c * N] + dt * bU[c];
+      if (A.x1) o += A.a1 * A.x1[q + c * N];
+      if (A.x2) o += A.a2 * A.x2[q + c * N];
+      A.out[q + c * N] = o;
+    }
+  }
+}
+
+}  // namespace jf
