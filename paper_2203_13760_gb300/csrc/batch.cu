@@ -165,6 +165,11 @@ jf_status create_impl(jf_ctx* h) {
 }
 
 // Point the descriptors at the caller's fields (only when they changed).
+// Every graph launch and upload records desc_done on its stream; waiting for
+// it before the upload makes sure that no work queued earlier, on any stream,
+// still reads the old descriptors and that the staging copy is free.  The
+// upload itself is queued on s from pinned memory, so the launches that
+// follow on s see the new descriptors.
 template <typename T>
 jf_status bind_fields(jf_ctx* h, void* const* U_ptrs, cudaStream_t s) {
   bool same = true;
@@ -172,9 +177,16 @@ jf_status bind_fields(jf_ctx* h, void* const* U_ptrs, cudaStream_t s) {
   if (same) return JF_OK;
   SimDesc<T>* desc = reinterpret_cast<SimDesc<T>*>(h->host_desc.data());
   for (int i = 0; i < h->nsim; ++i) desc[i].U = static_cast<T*>(U_ptrs[i]);
-  // work already queued may still read the old descriptors
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_sims, desc, h->nsim * sizeof(SimDesc<T>), cudaMemcpyHostToDevice);
+  const size_t bytes = h->nsim * sizeof(SimDesc<T>);
+  cudaError_t e = cudaSuccess;
+  if (!h->desc_pinned) e = cudaMallocHost(&h->desc_pinned, bytes);
+  if (e == cudaSuccess && !h->desc_done) e = cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventSynchronize(h->desc_done);
+  if (e == cudaSuccess) {
+    std::memcpy(h->desc_pinned, desc, bytes);
+    e = cudaMemcpyAsync(h->d_sims, h->desc_pinned, bytes, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->desc_done, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch: descriptor update");
   for (int i = 0; i < h->nsim; ++i) h->bound_ptrs[i] = U_ptrs[i];
   return JF_OK;
@@ -348,6 +360,7 @@ jf_status step_batch(jf_ctx* h, void* const* U_ptrs, int nsteps, double* dt_out,
     it = h->graphs.emplace(key, GraphEntry{graph, exec}).first;
   }
   cudaError_t e = cudaGraphLaunch(it->second.exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->desc_done, s);  // the graph reads the descriptors
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
   return JF_OK;
 }

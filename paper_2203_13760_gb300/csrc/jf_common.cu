@@ -50,6 +50,11 @@ void release_all(jf_ctx* h) {
   if (h->dt_buf) cudaFree(h->dt_buf);
   if (h->red_cfl) cudaFree(h->red_cfl);
   if (h->d_sims) cudaFree(h->d_sims);
+  if (h->desc_done) cudaEventSynchronize(h->desc_done);
+  if (h->desc_pinned) cudaFreeHost(h->desc_pinned);
+  if (h->desc_done) cudaEventDestroy(h->desc_done);
+  h->desc_pinned = nullptr;
+  h->desc_done = nullptr;
   if (h->vjp_desc_done) cudaEventSynchronize(h->vjp_desc_done);
   if (h->vjp_desc_host) cudaFreeHost(h->vjp_desc_host);
   if (h->vjp_desc_dev) cudaFree(h->vjp_desc_dev);

@@ -66,6 +66,10 @@ struct jf_ctx {
   std::vector<void*> sim_stage;        // 2 per simulation
   void* d_sims = nullptr;              // device array of SimDesc<T> (stage.cuh)
   std::vector<unsigned char> host_desc;  // host copy of the descriptors
+  // descriptor uploads: pinned staging copy, and an event recorded after every
+  // graph launch and upload (work that reads the descriptors, on any stream)
+  void* desc_pinned = nullptr;
+  cudaEvent_t desc_done = nullptr;
   // batch adjoint: descriptors of the recompute (pinned staging, device copy,
   // event guarding the staging buffer's reuse)
   void* vjp_desc_host = nullptr;

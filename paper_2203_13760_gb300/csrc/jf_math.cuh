@@ -173,6 +173,86 @@ __device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, 
   return __ffma2_rn(num, rcp2(den), v0);
 }
 
+// WENO5-JS per cell: both face values one cell j contributes, from the same
+// five values v[j-2..j+2]:
+//   right = v^-_{j+1/2} (left-biased, the weno5 formula above),
+//   left  = v^+_{j-1/2} (right-biased: the same formula on the mirrored
+//           stencil v[j+2..j-2]).
+// The mirrored stencil has the smoothness indicators in reverse order
+// (beta'_k = beta_{2-k}: the three 3-cell sub-stencils are the same), so
+// both values share the indicators and their reciprocals; only the linear
+// weights and candidates differ.  With the differences D1..D4 of weno5_pair
+// the mirrored ones are D1' = -D4, D2' = -D3, D3' = -D2, D4' = -D1.
+// Equal to two weno5 calls up to rounding.
+template <typename T>
+JF_HD void weno5_cell(T vm2, T vm1, T v0, T vp1, T vp2, T eps, T& right, T& left) {
+  const T D1 = vm2 - vm1, D2 = v0 - vm1, D3 = vp1 - v0, D4 = vp1 - vp2;
+  const T c13 = T(13) / T(12);
+  const T d0 = D2 + D1, e0 = T(3) * D2 + D1;
+  const T d1 = D3 - D2, e1 = D2 + D3;
+  const T d2 = D3 + D4, e2 = T(3) * D3 + D4;
+  const T t0 = eps + (c13 * d0 * d0 + T(0.25) * e0 * e0);
+  const T t1 = eps + (c13 * d1 * d1 + T(0.25) * e1 * e1);
+  const T t2 = eps + (c13 * d2 * d2 + T(0.25) * e2 * e2);
+  // candidate offsets q_k - v0 (times 6) of both reconstructions
+  const T g0 = T(5) * D2 + T(2) * D1, g1 = D2 + T(2) * D3, g2 = T(4) * D3 + D4;
+  const T h0 = -(T(5) * D3 + T(2) * D4), h1 = -(D3 + T(2) * D2), h2 = -(T(4) * D2 + D1);
+  if constexpr (sizeof(T) == 8) {
+    // alpha_k scaled by the common product (t0 t1 t2)^2 (one division per
+    // value; the factors are >= eps, far inside the FP64 range):
+    // right: (0.1 s1 s2, 0.6 s0 s2, 0.3 s0 s1); left (mirrored t):
+    // (0.1 s0 s1, 0.6 s0 s2, 0.3 s1 s2), s_k = t_k^2
+    const T s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
+    const T p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
+    const T a0 = T(0.1) * p12, a1 = T(0.6) * p02, a2 = T(0.3) * p01;
+    const T b0 = T(0.1) * p01, b2 = T(0.3) * p12;
+    right = v0 + (a0 * g0 + a1 * g1 + a2 * g2) / (T(6) * (a0 + a1 + a2));
+    left = v0 + (b0 * h0 + a1 * h1 + b2 * h2) / (T(6) * (b0 + a1 + b2));
+  } else {
+    const T r0 = trcp(t0 * t0), r1 = trcp(t1 * t1), r2 = trcp(t2 * t2);
+    const T a0 = T(0.1) * r0, a1 = T(0.6) * r1, a2 = T(0.3) * r2;
+    const T b0 = T(0.1) * r2, b2 = T(0.3) * r0;
+    right = v0 + (a0 * g0 + a1 * g1 + a2 * g2) * trcp(T(6) * (a0 + a1 + a2));
+    left = v0 + (b0 * h0 + a1 * h1 + b2 * h2) * trcp(T(6) * (b0 + a1 + b2));
+  }
+}
+
+// weno5_cell for two components of one cell in the lanes of packed FP32x2
+// operations (the arithmetic of weno5_pair: indicators scaled by 12/13,
+// linear weights scaled by 10/3).
+__device__ __forceinline__ void weno5_cell_pair(float2 vm2, float2 vm1, float2 v0, float2 vp1, float2 vp2, float eps,
+                                                float2& right, float2& left) {
+  auto c = [](float x) { return make_float2(x, x); };
+  const float2 m1 = c(-1.0f);
+  const float2 D1 = __ffma2_rn(m1, vm1, vm2);
+  const float2 D2 = __ffma2_rn(m1, vm1, v0);
+  const float2 D3 = __ffma2_rn(m1, v0, vp1);
+  const float2 D4 = __ffma2_rn(m1, vp2, vp1);
+  const float2 d0 = __fadd2_rn(D2, D1), e0 = __ffma2_rn(c(3.0f), D2, D1);
+  const float2 d1 = __ffma2_rn(m1, D2, D3), e1 = __fadd2_rn(D2, D3);
+  const float2 d2 = __fadd2_rn(D3, D4), e2 = __ffma2_rn(c(3.0f), D3, D4);
+  const float2 k3 = c(3.0f / 13.0f), ke = c(12.0f / 13.0f * eps);
+  const float2 t0 = __ffma2_rn(d0, d0, __ffma2_rn(__fmul2_rn(k3, e0), e0, ke));
+  const float2 t1 = __ffma2_rn(d1, d1, __ffma2_rn(__fmul2_rn(k3, e1), e1, ke));
+  const float2 t2 = __ffma2_rn(d2, d2, __ffma2_rn(__fmul2_rn(k3, e2), e2, ke));
+  auto rcp2 = [](float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); };
+  const float2 r0 = rcp2(__fmul2_rn(t0, t0)), r1 = rcp2(__fmul2_rn(t1, t1)), r2 = rcp2(__fmul2_rn(t2, t2));
+  // right: v0 + (r0 g0 + r1 g1 + r2 g2) / (r0/3 + 2 r1 + r2)
+  const float2 g0 = __ffma2_rn(c(5.0f / 18.0f), D2, __fmul2_rn(c(1.0f / 9.0f), D1));
+  const float2 g1 = __ffma2_rn(c(2.0f / 3.0f), D3, __fmul2_rn(c(1.0f / 3.0f), D2));
+  const float2 g2 = __ffma2_rn(c(2.0f / 3.0f), D3, __fmul2_rn(c(1.0f / 6.0f), D4));
+  const float2 num = __ffma2_rn(r2, g2, __ffma2_rn(r1, g1, __fmul2_rn(r0, g0)));
+  const float2 den = __ffma2_rn(c(1.0f / 3.0f), r0, __ffma2_rn(c(2.0f), r1, r2));
+  right = __ffma2_rn(num, rcp2(den), v0);
+  // left: the mirrored stencil (r and D reversed and negated)
+  const float2 h0 = __ffma2_rn(c(-5.0f / 18.0f), D3, __fmul2_rn(c(-1.0f / 9.0f), D4));
+  const float2 h1 = __ffma2_rn(c(-2.0f / 3.0f), D2, __fmul2_rn(c(-1.0f / 3.0f), D3));
+  const float2 h2 = __ffma2_rn(c(-2.0f / 3.0f), D2, __fmul2_rn(c(-1.0f / 6.0f), D1));
+  const float2 numl = __ffma2_rn(r0, h2, __ffma2_rn(r1, h1, __fmul2_rn(r2, h0)));
+  const float2 denl = __ffma2_rn(c(1.0f / 3.0f), r2, __ffma2_rn(c(2.0f), r1, r0));
+  left = __ffma2_rn(numl, rcp2(denl), v0);
+}
+
 // WENO3-JS (Table 2): value at x_{i+1/2} biased to the left from
 // v[i-1], v[i], v[i+1]: q0 = (3 v[i] - v[i-1]) / 2, q1 = (v[i] + v[i+1]) / 2,
 // beta0 = (v[i] - v[i-1])^2, beta1 = (v[i+1] - v[i])^2,

@@ -359,61 +359,18 @@ __device__ __forceinline__ void fs_flux(const Val& val, const Gas<T>& g, int rec
   F[4] = H * (Gh[0] + Gh[4]) + un * c * Dw + T(0.5) * q2 * Gh[1] + u[T1] * Gh[2] + u[T2] * Gh[3];
 }
 
-// Net flux NF = F^d - F through the face between the cell at shared-memory
-// position (x0, y0, plane 0) and its neighbour along D.
-// SCH_DEFAULT: the default scheme (WENO5-JS, HLLC, Einfeldt speeds) compiled
-// alone; SCH_GENERAL(_EXT): the Table 2 Godunov variants chosen at run time
-// from g; SCH_ROE(_EXT): the flux-splitting ROE setup (reconstruction chosen
-// from g); the _EXT forms add WENO3-JS (and walls, in the plane fetch);
-// SCH_NN: the Rusanov-NN flux (Section 7.4; reconstruction chosen from g),
-// a kernel family of its own because the network's hidden layers need far
-// more registers than the other fluxes.
+// Convective flux F of a Godunov-type face from its reconstructed states Wm
+// (left) and Wp (right): the safe-reconstruction fallback, then the Riemann
+// solver of the kernel family.
 template <typename T, int D, int BX, int BY, int DIM, bool VISC, int SCH>
-__device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
-                                          const Gas<T>& g, const T inv_h[3], T NF[5]) {
+__device__ __forceinline__ void face_riemann(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
+                                             const Gas<T>& g, T Wm[5], T Wp[5], T F[5]) {
   using Ro = Roles<D>;
-  const int recon = SCH == SCH_DEFAULT ? 0 : g.recon;
   auto val = [&](int c, int n, int t1, int t2) -> T {
     int x, y, e;
     Ro::map(n, t1, t2, x, y, e);
     return R.at(c, x0 + x, y0 + y, e);
   };
-  T F[5];
-  if constexpr (sch_roe(SCH)) {
-    fs_flux<T, D, sch_ext(SCH)>([&](int c, int n) { return val(c, n, 0, 0); }, g, recon, F);
-  } else {
-  // WENO5-JS left / right states of each primitive component (Section 3.3)
-  T Wm[5], Wp[5];
-  if (sch_ext(SCH) && recon == 2) {
-    // WENO3-JS: cells -1, 0, 1 (left state) and 2, 1, 0 (right state)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const T v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0), v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0);
-      if constexpr (sizeof(T) == 4) {
-        const float2 r = weno3_pair(make_float2(v1, v4), make_float2(v2, v3), make_float2(v3, v2), g.eps);
-        Wm[c] = r.x;
-        Wp[c] = r.y;
-      } else {
-        Wm[c] = weno3(v1, v2, v3, g.eps);
-        Wp[c] = weno3(v4, v3, v2, g.eps);
-      }
-    }
-  } else {
-#pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    const T v0 = val(c, -2, 0, 0), v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0);
-    const T v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0), v5 = val(c, 3, 0, 0);
-    if constexpr (sizeof(T) == 4) {
-      const float2 r = weno5_pair(make_float2(v0, v5), make_float2(v1, v4), make_float2(v2, v3), make_float2(v3, v2),
-                                  make_float2(v4, v1), g.eps, recon);
-      Wm[c] = r.x;
-      Wp[c] = r.y;
-    } else {
-      Wm[c] = weno5(v0, v1, v2, v3, v4, g.eps, recon);
-      Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps, recon);
-    }
-  }
-  }
   if (g.safe) {
     if (!(Wm[0] > T(0)) || !(Wm[4] > T(0))) {
 #pragma unroll
@@ -427,10 +384,20 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
   if constexpr (sch_general(SCH)) riemann_flux<T, D>(Wm, Wp, g, F);
   else if constexpr (SCH == SCH_NN) rusanov_nn<T, D>(Wm, Wp, g, F);
   else hllc<T, D>(Wm, Wp, g, F, 0);
-  }
-#pragma unroll
-  for (int c = 0; c < 5; ++c) NF[c] = -F[c];
-  if constexpr (VISC) {
+}
+
+// Dissipative part of the net flux (Sections 2 and 3.4) through the face
+// between the cell at shared-memory position (x0, y0, plane 0) and its
+// neighbour along D, added to NF.
+template <typename T, int D, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void face_visc_add(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
+                                              const Gas<T>& g, const T inv_h[3], T NF[5]) {
+  using Ro = Roles<D>;
+  auto val = [&](int c, int n, int t1, int t2) -> T {
+    int x, y, e;
+    Ro::map(n, t1, t2, x, y, e);
+    return R.at(c, x0 + x, y0 + y, e);
+  };
   // Dissipative flux (Sections 2 and 3.4).  G[a][b] = du_a/dx_b at the face.
   T G[3][3];
 #pragma unroll
@@ -539,6 +506,96 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
   NF[2] += tau[1];
   NF[3] += tau[2];
   NF[4] += uf[0] * tau[0] + uf[1] * tau[1] + uf[2] * tau[2] + g.lambda * dTdn;
+}
+
+// Net flux NF = F^d - F through the face between the cell at shared-memory
+// position (x0, y0, plane 0) and its neighbour along D.
+// SCH_DEFAULT: the default scheme (WENO5-JS, HLLC, Einfeldt speeds) compiled
+// alone; SCH_GENERAL(_EXT): the Table 2 Godunov variants chosen at run time
+// from g; SCH_ROE(_EXT): the flux-splitting ROE setup (reconstruction chosen
+// from g); the _EXT forms add WENO3-JS (and walls, in the plane fetch);
+// SCH_NN: the Rusanov-NN flux (Section 7.4; reconstruction chosen from g),
+// a kernel family of its own because the network's hidden layers need far
+// more registers than the other fluxes.
+template <typename T, int D, int BX, int BY, int DIM, bool VISC, int SCH>
+__device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
+                                          const Gas<T>& g, const T inv_h[3], T NF[5]) {
+  using Ro = Roles<D>;
+  const int recon = SCH == SCH_DEFAULT ? 0 : g.recon;
+  auto val = [&](int c, int n, int t1, int t2) -> T {
+    int x, y, e;
+    Ro::map(n, t1, t2, x, y, e);
+    return R.at(c, x0 + x, y0 + y, e);
+  };
+  T F[5];
+  if constexpr (sch_roe(SCH)) {
+    fs_flux<T, D, sch_ext(SCH)>([&](int c, int n) { return val(c, n, 0, 0); }, g, recon, F);
+  } else {
+  // WENO5-JS left / right states of each primitive component (Section 3.3)
+  T Wm[5], Wp[5];
+  if (sch_ext(SCH) && recon == 2) {
+    // WENO3-JS: cells -1, 0, 1 (left state) and 2, 1, 0 (right state)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const T v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0), v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0);
+      if constexpr (sizeof(T) == 4) {
+        const float2 r = weno3_pair(make_float2(v1, v4), make_float2(v2, v3), make_float2(v3, v2), g.eps);
+        Wm[c] = r.x;
+        Wp[c] = r.y;
+      } else {
+        Wm[c] = weno3(v1, v2, v3, g.eps);
+        Wp[c] = weno3(v4, v3, v2, g.eps);
+      }
+    }
+  } else {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const T v0 = val(c, -2, 0, 0), v1 = val(c, -1, 0, 0), v2 = val(c, 0, 0, 0);
+    const T v3 = val(c, 1, 0, 0), v4 = val(c, 2, 0, 0), v5 = val(c, 3, 0, 0);
+    if constexpr (sizeof(T) == 4) {
+      const float2 r = weno5_pair(make_float2(v0, v5), make_float2(v1, v4), make_float2(v2, v3), make_float2(v3, v2),
+                                  make_float2(v4, v1), g.eps, recon);
+      Wm[c] = r.x;
+      Wp[c] = r.y;
+    } else {
+      Wm[c] = weno5(v0, v1, v2, v3, v4, g.eps, recon);
+      Wp[c] = weno5(v5, v4, v3, v2, v1, g.eps, recon);
+    }
+  }
+  }
+  face_riemann<T, D, BX, BY, DIM, VISC, SCH>(R, x0, y0, g, Wm, Wp, F);
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) NF[c] = -F[c];
+  if constexpr (VISC) face_visc_add<T, D, BX, BY, DIM, VISC>(R, x0, y0, g, inv_h, NF);
+}
+
+// WENO5-JS face values of one cell along D (default scheme, weno5_cell): the
+// cell sits `shift` cells along D from ring position (x0, y0, plane 0);
+// right[c] = v^-_{+1/2}, its value at the face to its right (the left state
+// of that face), left[c] = v^+_{-1/2} (the right state of the face to its
+// left).  FP32: (rho, p) and (u, v) in packed lanes, w alone.
+template <typename T, int D, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void cell_recon(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0, int shift, T eps,
+                                           T right[5], T left[5]) {
+  using Ro = Roles<D>;
+  auto val = [&](int c, int n) -> T {
+    int x, y, e;
+    Ro::map(n + shift, 0, 0, x, y, e);
+    return R.at(c, x0 + x, y0 + y, e);
+  };
+  if constexpr (sizeof(T) == 4) {
+    auto pr = [&](int a, int b, int n) { return make_float2(val(a, n), val(b, n)); };
+    float2 r, l;
+    weno5_cell_pair(pr(0, 4, -2), pr(0, 4, -1), pr(0, 4, 0), pr(0, 4, 1), pr(0, 4, 2), eps, r, l);
+    right[0] = r.x; right[4] = r.y; left[0] = l.x; left[4] = l.y;
+    weno5_cell_pair(pr(1, 2, -2), pr(1, 2, -1), pr(1, 2, 0), pr(1, 2, 1), pr(1, 2, 2), eps, r, l);
+    right[1] = r.x; right[2] = r.y; left[1] = l.x; left[2] = l.y;
+    weno5_cell<float>(val(3, -2), val(3, -1), val(3, 0), val(3, 1), val(3, 2), eps, right[3], left[3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      weno5_cell<T>(val(c, -2), val(c, -1), val(c, 0), val(c, 1), val(c, 2), eps, right[c], left[c]);
   }
 }
 
@@ -600,6 +657,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     }
   };
 
+  // default scheme: WENO5 runs once per cell and direction (weno5_cell), the
+  // face values of a plane kept in shared memory (x, y) or, along z, in
+  // registers (zL: the value of the current cell at its upper face)
+  constexpr bool PC = SCH == SCH_DEFAULT;
+  constexpr int SX = BY * (BX + 2), SY = (BY + 2) * BX;
+  T* EX = Fy + 5 * G::NFY;  // [2][5][BY][BX+2] (PC only)
+  T* EY = EX + 2 * 5 * SX;  // [2][5][BY+2][BX] (PC, DIM >= 2)
+  T zL[5];
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight during plane k
   if (DIM == 3) {
@@ -608,7 +673,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     // lower face of plane z0 = upper face of plane z0 - 1 (slot 2); plane
     // offset -3 is never read
     set_view(5);
-    if (cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+    if (cell_thread) {
+      if constexpr (PC) {
+        // face z0 - 1/2 from the values of cells z0 - 1 and z0; zL: cell z0 at z0 + 1/2
+        T r[5], l[5], lz[5];
+        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 0, g.eps, r, l);
+        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, zL, lz);
+        T F[5];
+        face_riemann<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, r, lz, F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) NFz_lo[c] = -F[c];
+        if constexpr (VISC) face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+      } else {
+        face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+      }
+    }
     __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
     load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring, gx0, gy0, z0 + 3);
     if (z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, z0 + 4);
@@ -633,6 +712,97 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       }
     }
 
+    T NFz_hi[5];
+    if constexpr (PC) {
+      // phase 1: face values of the cells along x (rows 0 .. BY-1, cells
+      // -1 .. BX) and y (rows -1 .. BY), and the z face of each column
+      auto put_x = [&](int row, int j) {
+        T r[5], l[5];
+        cell_recon<T, 0, BX, BY, DIM, VISC>(R, HALO + j, G::HY + row, 0, g.eps, r, l);
+        const int i = row * (BX + 2) + j + 1;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          if (JF_CHECK(i >= 0 && i < SX, "JFDBG EX i=%d\n", i)) {
+            EX[c * SX + i] = r[c];
+            EX[(5 + c) * SX + i] = l[c];
+          }
+        }
+      };
+      auto put_y = [&](int row, int x) {
+        T r[5], l[5];
+        cell_recon<T, 1, BX, BY, DIM, VISC>(R, HALO + x, G::HY + row, 0, g.eps, r, l);
+        const int i = (row + 1) * BX + x;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          if (JF_CHECK(i >= 0 && i < SY, "JFDBG EY i=%d\n", i)) {
+            EY[c * SY + i] = r[c];
+            EY[(5 + c) * SY + i] = l[c];
+          }
+        }
+      };
+      if (DIM == 1) {
+        if (threadIdx.x < BX + 2) put_x(0, (int)threadIdx.x - 1);
+      } else {
+        // warps 0 .. BY-1: x row `warp` (cells -1 .. 30), y row warp - 1;
+        // warp BY: cells 31, 32 of every x row and the y rows BY - 1, BY
+        if (warp < BY) put_x(warp, lane - 1);
+        else if (lane < 2 * BY) put_x(lane >> 1, BX - 1 + (lane & 1));
+        if (warp < BY) {
+          put_y(warp - 1, lane);
+        } else {
+          put_y(BY - 1, lane);
+          put_y(BY, lane);
+        }
+      }
+      if (DIM == 3 && cell_thread) {
+        // face k + 1/2: zL (cell k) and the lower value of cell k + 1
+        T r[5], l[5], F[5];
+        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, r, l);
+        face_riemann<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, zL, l, F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          NFz_hi[c] = -F[c];
+          zL[c] = r[c];
+        }
+        if constexpr (VISC) face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+      }
+      __syncthreads();
+      // phase 2: the x and y faces from the stored values
+      if (xf_x >= 0) {
+        T Wm[5], Wp[5], F[5], NF[5];
+        const int i = xf_y * (BX + 2) + xf_x;  // left cell xf_x - 1
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          Wm[c] = EX[c * SX + i];
+          Wp[c] = EX[(5 + c) * SX + i + 1];
+        }
+        face_riemann<T, 0, BX, BY, DIM, VISC, SCH>(R, HALO + xf_x - 1, G::HY + xf_y, g, Wm, Wp, F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) NF[c] = -F[c];
+        if constexpr (VISC) face_visc_add<T, 0, BX, BY, DIM, VISC>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
+        const int t = xf_y * (BX + 1) + xf_x;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          if (JF_CHECK(t >= 0 && t < G::NFX, "JFDBG Fx t=%d\n", t)) Fx[c * G::NFX + t] = NF[c];
+      }
+      if (DIM >= 2) {
+        T Wm[5], Wp[5], F[5], NF[5];
+        const int i = yf_y * BX + yf_x;  // lower cell row yf_y - 1
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          Wm[c] = EY[c * SY + i];
+          Wp[c] = EY[(5 + c) * SY + i + BX];
+        }
+        face_riemann<T, 1, BX, BY, DIM, VISC, SCH>(R, HALO + yf_x, G::HY + yf_y - 1, g, Wm, Wp, F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) NF[c] = -F[c];
+        if constexpr (VISC) face_visc_add<T, 1, BX, BY, DIM, VISC>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
+        const int t = yf_y * BX + yf_x;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+          if (JF_CHECK(t >= 0 && t < G::NFY, "JFDBG Fy t=%d\n", t)) Fy[c * G::NFY + t] = NF[c];
+      }
+    } else {
     if (xf_x >= 0) {
       T NF[5];
       face_flux<T, 0, BX, BY, DIM, VISC, SCH>(R, HALO + xf_x - 1, G::HY + xf_y, g, inv_h, NF);
@@ -649,8 +819,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       for (int c = 0; c < 5; ++c)
         if (JF_CHECK(t >= 0 && t < G::NFY, "JFDBG Fy t=%d\n", t)) Fy[c * G::NFY + t] = NF[c];
     }
-    T NFz_hi[5];
     if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+    }
     __syncthreads();
 
     if (own) {
@@ -747,6 +917,14 @@ constexpr size_t stage_smem_elems() {
   return (size_t)(G::RING * G::PLANE + 5 * G::NFX + 5 * G::NFY);
 }
 
+// Default scheme: the per-cell WENO5 face values of a plane, after the face
+// buffers: x [2][5][BY][BX+2] (cells -1 .. BX of each row), y [2][5][BY+2][BX]
+// (rows -1 .. BY); index 0 the value at the cell's right face, 1 at its left.
+template <int DIM, int BX, int BY>
+constexpr size_t recon_smem_elems() {
+  return (size_t)2 * 5 * (BY * (BX + 2) + (DIM >= 2 ? (BY + 2) * BX : 0));
+}
+
 // Element offset of the Rusanov-NN parameters in the dynamic shared memory:
 // after the tile buffers, rounded up to 16 bytes (nn_alpha reads its weight
 // rows with 16-byte loads).
@@ -777,7 +955,8 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
     unsigned dyn;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
     const size_t need = sizeof(T) * (SCH == SCH_NN ? nn_smem_offset<T, DIM, VISC, BX, BY>() + NN_PARAMS
-                                                   : stage_smem_elems<T, DIM, VISC, BX, BY>());
+                                                   : stage_smem_elems<T, DIM, VISC, BX, BY>() +
+                                                         (SCH == SCH_DEFAULT ? recon_smem_elems<DIM, BX, BY>() : 0));
     if (!JF_CHECK(dyn >= need, "JFDBG smem %u < %llu\n", dyn, (unsigned long long)need)) return;
     if (work && threadIdx.x == 0)
       for (int i = blockIdx.x; i < nwork; i += gridDim.x) {

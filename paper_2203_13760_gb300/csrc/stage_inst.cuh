@@ -5,11 +5,13 @@
 namespace jf {
 
 // Dynamic shared memory of a launch: the tile buffers, plus the Rusanov-NN
-// parameters (at a 16-byte aligned offset) in the kernels of that flux.
+// parameters (at a 16-byte aligned offset) in the kernels of that flux, or the
+// per-cell WENO5 face values in the default-scheme kernels.
 template <typename T, int DIM, bool VISC, int BX, int BY, int SCH>
 constexpr size_t launch_smem() {
   return SCH == SCH_NN ? sizeof(T) * (nn_smem_offset<T, DIM, VISC, BX, BY>() + NN_PARAMS)
-                       : stage_smem_bytes<T, DIM, VISC, BX, BY>();
+                       : stage_smem_bytes<T, DIM, VISC, BX, BY>() +
+                             (SCH == SCH_DEFAULT ? sizeof(T) * recon_smem_elems<DIM, BX, BY>() : 0);
 }
 
 // MINB: CTAs per SM the register allocation must allow (__launch_bounds__).
