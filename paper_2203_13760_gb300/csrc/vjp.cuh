@@ -142,6 +142,8 @@ template <typename T, int DIM, bool VISC, int BX, int BY, int BZ>
 struct VTile {
   using G = VGeo<BX, BY, BZ, DIM, VISC>;
   static constexpr int NCB = G::NCB;
+  static constexpr bool SEP3 = false;
+  __device__ __forceinline__ void add_sep(int, int, int, int, int, int, T) const {}
   const T* W;   // [NCW][PY][PX], box cell (0, 0) at (HX, HY)
   const T* M;   // [5][MPY][MPX]
   T* acc;       // [6][APY][APX], box cell (0, 0) at (AX, AY)
@@ -360,7 +362,15 @@ __device__ __forceinline__ void visc_face_vjp(const Tile& V, const Frame& F, con
     for (int k = 0; k < 2; ++k) {
       const int c = k == 0 ? comp[0] : comp[1 + j];
       const T gb = (k == 0 ? g.mu * taub[1 + j] : divb) * he[j];
-      if constexpr (Tile::NCB > 0) {
+      if constexpr (Tile::SEP3) {
+        // 3D: centre-derivative cotangents by (tangent axis, component); the
+        // tile spreads them along the tangent once per plane
+        const int e = j == 0 ? F.t1 : F.t2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          V.add_sep(F.d, e, c, p[0] + F.pick(0, q - 1, 0, 0), p[1] + F.pick(1, q - 1, 0, 0),
+                    p[2] + F.pick(2, q - 1, 0, 0), gb * rc[q]);
+      } else if constexpr (Tile::NCB > 0) {
         // centre-derivative cotangents; the gather pass spreads them along the tangent
 #pragma unroll
         for (int q = 0; q < 4; ++q)

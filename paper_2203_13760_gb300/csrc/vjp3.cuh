@@ -42,12 +42,18 @@ struct V3Geo {
   static constexpr int PLANE = NCW * CS;
   static constexpr int RING = 6;                     // planes k-3 .. k+2
   static constexpr int MPX = BX + 2, MPY = BY + 2, MCS = MPX * MPY;  // m planes, 1-cell halo
+  // viscous: cotangents of the cell-centre tangential derivatives (the DC4
+  // stencil is separable from the face's RC4): the x and y faces of the face
+  // plane in 7 slots (spread along y: u, v; along x: u, v; along z: u, v, w),
+  // the z faces in a ring of 4 planes (k-2 .. k+1) of 4 slots (spread along
+  // x: w, u; along y: w, v)
+  static constexpr int NXY = VISC ? 7 : 0, NZ = VISC ? 4 : 0, ZRING = 4;
 };
 
 template <typename T, bool VISC, int BX, int BY>
 constexpr size_t vjp3_smem_bytes() {
   using G = V3Geo<BX, BY, VISC>;
-  return sizeof(T) * (size_t)(2 * G::RING * G::PLANE + 2 * 5 * G::MCS);
+  return sizeof(T) * (size_t)(2 * G::RING * G::PLANE + 2 * 5 * G::MCS + (G::NXY + G::ZRING * G::NZ) * G::CS);
 }
 
 // Accessor of the rings at face plane k: coordinates relative to the tile
@@ -56,12 +62,16 @@ constexpr size_t vjp3_smem_bytes() {
 template <typename T, bool VISC, int BX, int BY>
 struct V3Tile {
   using G = V3Geo<BX, BY, VISC>;
-  static constexpr int NCB = 0;  // tangential cotangents scattered directly
+  static constexpr int NCB = 0;
+  static constexpr bool SEP3 = VISC;  // tangential cotangents through add_sep
   const T* W;
   T* acc;
   const T* M;
+  T* cbxy;    // [7][PY][PX]
+  T* cbz;     // [4 planes][4][PY][PX]
   int wp[6];  // element offset of the W / accumulator slot of plane k + z, index z + 3
   int mp[2];  // element offset of the m slot of plane k + z, index z + 1
+  int zp[4];  // element offset of the z-face cotangent slot of plane k + z, index z + 2
   __device__ __forceinline__ T w(int c, int x, int y, int z) const {
     return W[wp[z + 3] + c * G::CS + (y + G::H) * G::PX + x + G::H];
   }
@@ -71,7 +81,35 @@ struct V3Tile {
   __device__ __forceinline__ T m(int c, int x, int y, int z) const {
     return M[mp[z + 1] + c * G::MCS + (y + 1) * G::MPX + x + 1];
   }
+  // cotangent of the centre derivative of component c along axis e at a
+  // cell of a face normal to d (x, y faces: plane k; z faces: planes k-2 .. k+1)
+  __device__ __forceinline__ void add_sep(int d, int e, int c, int x, int y, int z, T v) const {
+    const int cell = (y + G::H) * G::PX + x + G::H;
+    if (d == 2) {
+      const int slot = e == 0 ? (c == 3 ? 0 : 1) : (c == 3 ? 2 : 3);
+      atomicAdd(cbz + zp[z + 2] + slot * G::CS + cell, v);
+    } else {
+      const int slot = e == 1 ? (c == 1 ? 0 : 1) : (e == 0 ? (c == 1 ? 2 : 3) : (c == 1 ? 4 : (c == 2 ? 5 : 6)));
+      atomicAdd(cbxy + slot * G::CS + cell, v);
+    }
+  }
 };
+
+// Transposed DC4 along x or y at plane cell t of a cotangent slot src: the
+// sum over o of dcw[o] src(t - dco[o] e) (dco = -2, -1, 1, 2; dcw = (1, -8, 8,
+// -1) / 12); cells beyond the plane region hold no cotangent.
+template <typename T, int BX, int BY, bool VISC>
+__device__ __forceinline__ T vjp3_pull(const T* src, int t, int axis) {
+  using G = V3Geo<BX, BY, VISC>;
+  const int ly = t / G::PX, lx = t - ly * G::PX;
+  const int pos = axis == 0 ? lx : ly, len = axis == 0 ? G::PX : G::PY, step = axis == 0 ? 1 : G::PX;
+  T v = T(0);
+  if (pos + 2 < len) v += (T(1) / T(12)) * src[t + 2 * step];
+  if (pos + 1 < len) v += (-T(8) / T(12)) * src[t + step];
+  if (pos >= 1) v += (T(8) / T(12)) * src[t - step];
+  if (pos >= 2) v += (-T(1) / T(12)) * src[t - 2 * step];
+  return v;
+}
 
 // Primitives (+T) of plane gz (unmapped) into W slot dst.
 template <typename T, bool VISC, int BX, int BY, int NT>
@@ -146,6 +184,8 @@ __global__ void __launch_bounds__(NT, MINB)
   T* Wr = reinterpret_cast<T*>(smem_raw);  // [RING][NCW][PY][PX]
   T* Ar = Wr + G::RING * G::PLANE;         // [RING][NCW][PY][PX]
   T* Mr = Ar + G::RING * G::PLANE;         // [2][5][MPY][MPX]
+  T* Cxy = Mr + 2 * 5 * G::MCS;            // viscous: [7][PY][PX]
+  T* Cz = Cxy + G::NXY * G::CS;            // viscous: [4 planes][4][PY][PX]
   const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, nz);
@@ -161,6 +201,7 @@ __global__ void __launch_bounds__(NT, MINB)
   for (int q = 0; q < G::RING; ++q)
     vjp3_load_w<T, VISC, BX, BY, NT>(A, g, Wr + q * G::PLANE, x0, y0, z0 - 3 + q, bad);
   for (int t = threadIdx.x; t < G::RING * G::PLANE; t += NT) Ar[t] = T(0);
+  for (int t = threadIdx.x; t < (G::NXY + G::ZRING * G::NZ) * G::CS; t += NT) Cxy[t] = T(0);
   vjp3_load_m<T, VISC, BX, BY, NT>(A, Mr, x0, y0, z0 - 1);
   vjp3_load_m<T, VISC, BX, BY, NT>(A, Mr + 5 * G::MCS, x0, y0, z0);
   if (bad) atomicOr(A.flag, 1);
@@ -170,6 +211,24 @@ __global__ void __launch_bounds__(NT, MINB)
   V.W = Wr;
   V.acc = Ar;
   V.M = Mr;
+  V.cbxy = Cxy;
+  V.cbz = Cz;
+  // the z-face cotangents of plane p sit in ring slot (p - z0 + 2) mod 4
+  auto zslot = [&](int p) { return ((p - z0 + 2) & 3) * G::NZ * G::CS; };
+  // transposed DC4 along x and y of the z-face cotangents of plane p into
+  // its accumulator slot (thread per plane cell; no other thread writes the
+  // cell meanwhile)
+  auto gather_z = [&](int p) {
+    if constexpr (VISC) {
+      const T* src = Cz + zslot(p);
+      T* dst = Ar + ((p - z0 + 3) % G::RING) * G::PLANE;
+      for (int t = threadIdx.x; t < G::CS; t += NT) {
+        dst[3 * G::CS + t] += vjp3_pull<T, BX, BY, VISC>(src, t, 0) + vjp3_pull<T, BX, BY, VISC>(src + 2 * G::CS, t, 1);
+        dst[G::CS + t] += vjp3_pull<T, BX, BY, VISC>(src + G::CS, t, 0);
+        dst[2 * G::CS + t] += vjp3_pull<T, BX, BY, VISC>(src + 3 * G::CS, t, 1);
+      }
+    }
+  };
   for (int k = z0; k < kend; ++k) {
     const int b = (k - z0) % G::RING;  // slot of plane k - 3
 #pragma unroll
@@ -180,6 +239,8 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     V.mp[0] = ((k - z0) & 1) * 5 * G::MCS;
     V.mp[1] = ((k - z0 + 1) & 1) * 5 * G::MCS;
+#pragma unroll
+    for (int z = -2; z <= 1; ++z) V.zp[z + 2] = zslot(k + z);
 
     auto face_nu = [&](auto dtag, const int p[3], T nu[5]) -> bool {
       constexpr int d = decltype(dtag)::value;
@@ -227,6 +288,33 @@ __global__ void __launch_bounds__(NT, MINB)
       }
     }
     __syncthreads();
+    if constexpr (VISC) {
+      // the x and y faces' centre-derivative cotangents of plane k: transposed
+      // DC4 along y and x into plane k, along z into planes k -+ 1, 2; the
+      // z faces' of plane k - 2 are complete (their faces lie at planes up to
+      // k - 1 / k): along x and y into plane k - 2
+      constexpr int dco[4] = {-2, -1, 1, 2};
+      constexpr T dcw[4] = {T(1) / T(12), -T(8) / T(12), T(8) / T(12), -T(1) / T(12)};
+      T* a0 = Ar + V.wp[3];
+      for (int t = threadIdx.x; t < G::CS; t += NT) {
+        a0[G::CS + t] += vjp3_pull<T, BX, BY, VISC>(Cxy, t, 1) + vjp3_pull<T, BX, BY, VISC>(Cxy + 2 * G::CS, t, 0);
+        a0[2 * G::CS + t] +=
+            vjp3_pull<T, BX, BY, VISC>(Cxy + G::CS, t, 1) + vjp3_pull<T, BX, BY, VISC>(Cxy + 3 * G::CS, t, 0);
+        const T zu = Cxy[4 * G::CS + t], zv = Cxy[5 * G::CS + t], zw = Cxy[6 * G::CS + t];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          T* ao = Ar + V.wp[dco[o] + 3];
+          ao[G::CS + t] += dcw[o] * zu;
+          ao[2 * G::CS + t] += dcw[o] * zv;
+          ao[3 * G::CS + t] += dcw[o] * zw;
+        }
+      }
+      gather_z(k - 2);
+      __syncthreads();
+      for (int t = threadIdx.x; t < G::NXY * G::CS; t += NT) Cxy[t] = T(0);
+      T* cz = Cz + zslot(k - 2);  // becomes plane k + 2
+      for (int t = threadIdx.x; t < G::NZ * G::CS; t += NT) cz[t] = T(0);
+    }
     // plane k - 3 is complete: add it to the global accumulator, then its
     // slots take plane k + 3 (W, cleared accumulator) and the m slot of plane
     // k - 1 takes plane k + 1
@@ -237,7 +325,12 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
   }
-  // the planes still held: kend - 3 .. kend + 1
+  // the z-face cotangents still held (planes kend - 2 .. kend), then the
+  // planes still held: kend - 3 .. kend + 1
+  if constexpr (VISC) {
+    for (int pl = kend - 2; pl <= kend; ++pl) gather_z(pl);
+    __syncthreads();
+  }
   for (int pl = kend - 3; pl <= kend + 1; ++pl) {
     int s = (pl - z0 + 3) % G::RING;
     vjp3_flush<T, VISC, BX, BY, NT>(A, Ar + s * G::PLANE, Gacc, x0, y0, pl);

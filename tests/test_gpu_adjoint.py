@@ -106,6 +106,14 @@ def _tgv_off_symmetry(n):
     # folding ghost cotangents)
     ("f64", 1e-12, lambda: _tgv_off_symmetry(16)),
     ("f64", 1e-12, lambda: inputs.random_smooth((24, 24, 24), seed=16, bc=(1,) * 6, viscous=True, mu=0.02)),
+    # the z-marching 3D kernel: ragged columns (45 = 32 + 13 along x in FP32,
+    # 2 x 16 + 13 in FP64), the upper boundary faces of zero-gradient axes,
+    # a periodic axis between them, several z chunks
+    ("f64", 1e-12, lambda: inputs.random_smooth((45, 19, 13), seed=17, bc=(1, 1, 0, 0, 1, 1), viscous=True,
+                                                mu=0.02)),
+    ("f32", 3e-5, lambda: inputs.random_smooth((45, 19, 13), seed=17, bc=(1, 1, 0, 0, 1, 1), viscous=True,
+                                               mu=0.02)),
+    ("f64", 1e-12, lambda: inputs.random_blocks((45, 19, 13), seed=18, bc=(0, 0, 1, 1, 1, 1))),
 ])
 def test_dot_product_identity(orc, dtype, tol, make):
     case = make()
