@@ -210,7 +210,9 @@ jf_status jf_rk3_run(jf_handle h, void* U_inout, int nsteps, const double* dt_de
  * TVD-RK3, TVD-RK2 or Euler) and dt held fixed (not
  * differentiated).  Un is the state at the start of the step (not modified);
  * the step is recomputed inside.  lam_out and lam_in are device arrays shaped
- * like U; they may not overlap.  dt_dev must not be NULL. */
+ * like U; they may not overlap.  dt_dev must not be NULL.  The first call of
+ * a handle allocates its adjoint workspace: two states, and on 3D grids an
+ * accumulator of 6 values per cell. */
 jf_status jf_rk3_step_vjp(jf_handle h, const void* Un, const double* dt_dev, const void* lam_out, void* lam_in,
                           void* stream);
 
