@@ -288,6 +288,21 @@ jf_status jf_batch_param_grad_end(jf_handle batch, void* theta_bar, void* stream
 jf_status jf_loss_density_l2(jf_handle h, const void* U, const void* target, double* loss_dev, void* seed,
                              void* stream);
 
+/* Training loss of Section 7.4 (the mean squared error of the primitive
+ * state vectors of a predicted and a reference trajectory):
+ *   *loss_dev = 1/(nstates ncomp ncells) sum (W(U) - W(Uref))^2,
+ * over nstates states of ncells cells each, stored one after another as
+ * [nstates][5][ncells] in U and Uref (device arrays of the handle's dtype,
+ * 16-byte aligned), and over the primitive components (rho, u, v, p) for
+ * ncomp = 4 (two-dimensional states) or (rho, u, v, w, p) for ncomp = 5;
+ * FP64 accumulation.  If grad != NULL (same layout as U) it receives
+ * dloss/dU through the transposed Jacobian of W(U).  h (a single-grid or
+ * batch handle) supplies gamma and the reduction scratch; its grid is not
+ * used.  Errors: JF_ERR_ARG for a null pointer, ncomp outside {4, 5} or a
+ * non-positive count. */
+jf_status jf_loss_primitive_mse(jf_handle h, const void* U, const void* Uref, long long nstates, long long ncells,
+                                int ncomp, double* loss_dev, void* grad, void* stream);
+
 /* Batch of nsim independent simulations with their own grid sizes (Section
  * 4.5, feed_forward over a batch of initial buffers; here sizes may differ).
  * All share gas and scheme.  Each grid must be 2D or 1D (nz == 1);

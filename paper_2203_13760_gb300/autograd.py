@@ -23,6 +23,10 @@ a fixed step).
                               network parameters theta (jf_rk3_step_vjp_params).
 ``trajectory_mse(trajs, refs)``
                               Section 7.2: 1/N_T sum_i MSE(U^i, U^i_ref).
+``primitive_mse(owner, U, Uref, ncomp=4)``
+                              Section 7.4: MSE of the primitive state
+                              vectors (jf_loss_primitive_mse) with its
+                              gradient.
 
 dt is a float64 CUDA scalar tensor and is not differentiated (the paper's
 feed_forward uses a fixed step).  Every computation runs in libjf's kernels.
@@ -196,6 +200,29 @@ def feed_forward(batch, U0s, nsteps, dt, theta=None):
     when given, to the Rusanov-NN parameters theta (the tensor the batch holds
     through Batch.set_nn, updated in place by an optimizer)."""
     return list(_FeedForward.apply(batch, int(nsteps), dt, theta, *U0s))
+
+
+class _PrimitiveMSE(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, Uref, owner, ncomp):
+        from . import jf
+        loss, grad = jf.loss_primitive_mse(owner, U.detach(), Uref.detach(), ncomp, want_grad=U.requires_grad)
+        ctx.save_for_backward(grad if grad is not None else loss)
+        ctx.has_grad = grad is not None
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return (grad * g if ctx.has_grad else None), None, None, None
+
+
+def primitive_mse(owner, U, Uref, ncomp=4):
+    """Section 7.4 loss, the mean squared difference of the primitive state
+    vectors of U and Uref (jf_loss_primitive_mse; ncomp 4: rho, u, v, p), with
+    its gradient w.r.t. U; owner is the jf.Solver or jf.Batch whose gamma
+    applies.  Uref is not differentiated."""
+    return _PrimitiveMSE.apply(U, Uref, owner, int(ncomp))
 
 
 def trajectory_mse(trajs, refs):

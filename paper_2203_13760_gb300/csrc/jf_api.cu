@@ -556,6 +556,31 @@ jf_status jf_rk3_run(jf_handle h, void* U, int nsteps, const double* dt_dev, dou
   return JF_OK;
 }
 
+jf_status jf_loss_primitive_mse(jf_handle h, const void* U, const void* Uref, long long nstates, long long ncells,
+                                int ncomp, double* loss_dev, void* grad, void* stream) {
+  if (!h) { set_error(nullptr, "jf_loss_primitive_mse: null handle"); return JF_ERR_ARG; }
+  if (!U || !Uref || !loss_dev || nstates < 1 || ncells < 1 || (ncomp != 4 && ncomp != 5) || !aligned16(U) ||
+      !aligned16(Uref) || (grad && !aligned16(grad))) {
+    set_error(h, "jf_loss_primitive_mse: null or misaligned array, ncomp outside {4, 5} or a non-positive count");
+    return JF_ERR_ARG;
+  }
+  const long long total = nstates * ncells;
+  const unsigned blocks = (unsigned)reduce_blocks(total, h->sms);
+  const double gm1 = h->gas.gamma - 1.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->scheme.dtype == JF_F32)
+    primitive_mse_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(U), static_cast<const float*>(Uref),
+                                                        nstates, ncells, ncomp, gm1, h->red_loss, loss_dev,
+                                                        static_cast<float*>(grad));
+  else
+    primitive_mse_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(U),
+                                                         static_cast<const double*>(Uref), nstates, ncells, ncomp,
+                                                         gm1, h->red_loss, loss_dev, static_cast<double*>(grad));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "jf_loss_primitive_mse: kernel launch");
+  return JF_OK;
+}
+
 jf_status jf_loss_density_l2(jf_handle h, const void* U, const void* target, double* loss_dev, void* seed,
                              void* stream) {
   if (!h || h->kind != 0) { set_error(h, "jf_loss_density_l2: not a single-grid handle"); return JF_ERR_ARG; }

@@ -160,4 +160,75 @@ __global__ void __launch_bounds__(256) loss_density_kernel(const T* __restrict__
   }
 }
 
+// Section 7.4 training loss: the mean square difference of the primitive
+// state vectors of nstates states U and Uref (each [5][ncells], stored one
+// after another), over the states, the cells and ncomp components: (rho, u,
+// v, p) for ncomp = 4 (two-dimensional states), (rho, u, v, w, p) for 5.
+//   loss = 1/(nstates ncomp ncells) sum (W(U) - W(Uref))^2,
+//   grad = d loss / dU: the cotangent g = 2 (W(U) - W(Uref)) / count of the
+//   primitives through the transposed Jacobian of W(U) (u_i = m_i / rho,
+//   p = (gamma - 1)(E - |m|^2 / (2 rho))).
+// FP64 accumulation; the last CTA (ticket) writes the loss and resets sc.
+template <typename T>
+__global__ void __launch_bounds__(256) primitive_mse_kernel(const T* __restrict__ U, const T* __restrict__ Uref,
+                                                            long long nstates, long long ncells, int ncomp,
+                                                            double gm1, ReduceScratch* sc, double* loss, T* grad) {
+  const long long total = nstates * ncells;
+  const double inv_count = 1.0 / ((double)total * ncomp);
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+    const long long st = q / ncells, i = q - st * ncells;
+    const long long b = st * 5 * ncells + i;
+    double W[5], D[5];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const T* X = side == 0 ? U : Uref;
+      const double r = (double)X[b], ir = 1.0 / r;
+      const double u = (double)X[b + ncells] * ir, v = (double)X[b + 2 * ncells] * ir;
+      const double w = (double)X[b + 3 * ncells] * ir;
+      const double p = gm1 * ((double)X[b + 4 * ncells] - 0.5 * r * (u * u + v * v + w * w));
+      const double P[5] = {r, u, v, w, p};
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        if (side == 0) W[c] = P[c];
+        else D[c] = W[c] - P[c];
+      }
+    }
+    if (ncomp == 4) D[3] = 0.0;
+    s += D[0] * D[0] + D[1] * D[1] + D[2] * D[2] + D[3] * D[3] + D[4] * D[4];
+    if (grad) {
+      const double k = 2.0 * inv_count, ir = 1.0 / W[0];
+      const double gr = k * D[0], gu = k * D[1], gv = k * D[2], gw = k * D[3], gp = k * D[4];
+      grad[b] = (T)(gr - (gu * W[1] + gv * W[2] + gw * W[3]) * ir +
+                    gp * gm1 * 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]));
+      grad[b + ncells] = (T)(gu * ir - gp * gm1 * W[1]);
+      grad[b + 2 * ncells] = (T)(gv * ir - gp * gm1 * W[2]);
+      grad[b + 3 * ncells] = (T)(gw * ir - gp * gm1 * W[3]);
+      grad[b + 4 * ncells] = (T)(gp * gm1);
+    }
+  }
+  __shared__ double s_sum[8];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s_sum[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? s_sum[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) {
+      atomicAdd(&sc->sum, s);
+      __threadfence();
+      const unsigned int t = atomicAdd(&sc->ticket, 1u);
+      if (t == gridDim.x - 1) {
+        __threadfence();
+        *loss = atomicAdd(&sc->sum, 0.0) * inv_count;
+        sc->sum = 0.0;
+        sc->ticket = 0u;
+        __threadfence();
+      }
+    }
+  }
+}
+
 }  // namespace jf

@@ -76,6 +76,7 @@ SIGNATURES = {
     "jf_batch_param_grad_begin": (_I, [_VP, _I]),
     "jf_batch_param_grad_end": (_I, [_VP, _VP, _VP]),
     "jf_loss_density_l2": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jf_loss_primitive_mse": (_I, [_VP, _VP, _VP, ctypes.c_longlong, ctypes.c_longlong, _I, _VP, _VP, _VP]),
     "jf_batch_create": (_I, [ctypes.POINTER(Grid), _I, ctypes.POINTER(GasParams), ctypes.POINTER(Scheme),
                              ctypes.POINTER(_VP)]),
     "jf_batch_step": (_I, [_VP, ctypes.POINTER(_VP), _I, _VP, _VP]),
@@ -343,6 +344,28 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def loss_primitive_mse(owner, U, Uref, ncomp=4, loss=None, grad=None, want_grad=True):
+    """Section 7.4 training loss (jf_loss_primitive_mse): the mean squared
+    difference of the primitive variables of U and Uref, contiguous CUDA
+    tensors of states (..., 5, nz, ny, nx) in the dtype of `owner` (a Solver
+    or a Batch, which supplies gamma and the reduction scratch).  ncomp = 4:
+    (rho, u, v, p); 5: (rho, u, v, w, p).  Returns (loss, dloss/dU or None)."""
+    import torch
+    if (not U.is_cuda or U.dtype != owner.dtype or U.shape != Uref.shape or U.dtype != Uref.dtype
+            or U.shape[-4] != 5):
+        raise ValueError("U and Uref must be CUDA tensors of states (..., 5, nz, ny, nx) in the owner's dtype")
+    U = U.contiguous()
+    Uref = Uref.contiguous()
+    ncells = int(U.shape[-1] * U.shape[-2] * U.shape[-3])
+    nstates = int(U.numel() // (5 * ncells))
+    loss = torch.empty(1, dtype=torch.float64, device="cuda") if loss is None else loss
+    if want_grad and grad is None:
+        grad = torch.empty_like(U)
+    _check(lib().jf_loss_primitive_mse(owner.h, _ptr(U), _ptr(Uref), nstates, ncells, int(ncomp), _ptr(loss),
+                                       _ptr(grad) if want_grad else None, _stream()), owner.h)
+    return loss, (grad if want_grad else None)
 
 
 class Batch:

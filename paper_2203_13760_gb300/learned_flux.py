@@ -10,12 +10,15 @@ starting at the samples of the first ``n_train`` time steps, batches of
 simulations, the loss L = 1/N_T sum_{i=1..N_T} MSE(W_i^NN, W_i^CG) over the
 primitive variables (rho, u, v, p), Adam.  Every solver step and every
 gradient through it runs in libjf's kernels (jf_batch_feed_forward,
-jf_rk3_step_vjp_params); PyTorch holds the parameters, forms the loss of the
-primitive variables and takes the Adam step.
+jf_rk3_step_vjp_params), and so does the loss of the primitive variables
+with its gradient (jf_loss_primitive_mse); PyTorch holds the parameters and
+takes the Adam step.
 
 ``ground_truth(...)``        coarse-grained reference trajectory
 ``primitives(U)``            (rho, u, v, p) of conservative states
-``trajectory_loss(...)``     the loss above for a batch of windows
+``trajectory_loss(...)``     the loss above for a batch of windows (PyTorch
+                             reference of its definition)
+``trajectory_loss_jf(...)``  the same loss by libjf, as the trainer uses it
 ``Trainer``                  batches, forward / backward through the solver, Adam
 ``rollout_errors(...)``      relative L1 errors of rho and p along a run of the model
 """
@@ -80,6 +83,18 @@ def trajectory_loss(trajs, refs, gamma: float = GAMMA):
     return total / len(trajs)
 
 
+def trajectory_loss_jf(owner, trajs, refs):
+    """trajectory_loss evaluated by libjf (jf_loss_primitive_mse, with its
+    gradient), for CUDA trajectories; owner: the jf.Batch (or jf.Solver)
+    whose gas applies."""
+    if all(t.shape == trajs[0].shape for t in trajs) and all(r.shape == trajs[0].shape for r in refs):
+        return autograd.primitive_mse(owner, torch.stack(trajs)[:, 1:], torch.stack(refs)[:, 1:], 4)
+    total = 0.0
+    for traj, ref in zip(trajs, refs):
+        total = total + autograd.primitive_mse(owner, traj[1:], ref[1:], 4)
+    return total / len(trajs)
+
+
 def model_batch(n: int, nsim: int, dtype: str, theta=None, flux: str = "rusanov-nn"):
     """A jf.Batch of nsim coarse implosion grids with the model's scheme."""
     grids = [jf.make_grid((n, n, 1), bc=WALLS) for _ in range(nsim)]
@@ -109,7 +124,7 @@ class Trainer:
         U0s = [self.cg[s] for s in starts]
         trajs = autograd.feed_forward(self.batch, U0s, self.unroll, self.dt, theta=self.theta)
         refs = [self.cg[s:s + self.unroll + 1] for s in starts]
-        loss = trajectory_loss(trajs, refs)
+        loss = trajectory_loss_jf(self.batch, trajs, refs)
         if self.theta.grad is not None:
             self.theta.grad = None
         loss.backward()

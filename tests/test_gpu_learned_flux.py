@@ -1,7 +1,8 @@
 """Section 7.4 end to end on the GPU: the implosion reference, the gradient
 of the trajectory loss with respect to the network parameters (through
 jf_batch_feed_forward and jf_rk3_step_vjp_params) against central
-differences, and training that lowers the loss."""
+differences, training that lowers the loss, and the loss kernel
+(jf_loss_primitive_mse) against its definition."""
 import numpy as np
 import pytest
 
@@ -13,6 +14,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+from paper_2203_13760_gb300 import autograd as jfa  # noqa: E402
+from paper_2203_13760_gb300 import jf  # noqa: E402
 from paper_2203_13760_gb300 import learned_flux as lf  # noqa: E402
 
 
@@ -70,3 +73,39 @@ def test_rollout_errors_are_finite(small_reference):
     assert e_rho.shape == (10,) and np.all(np.isfinite(e_rho)) and np.all(np.isfinite(e_p))
     e2, _ = lf.rollout_errors(small_reference, 10, theta=inputs.nn_params(seed=7), dtype="f64")
     assert np.all(np.isfinite(e2))
+
+
+@pytest.mark.parametrize("dtype,ncomp,tol", [("f64", 4, 1e-13), ("f64", 5, 1e-13), ("f32", 4, 1e-6)])
+def test_primitive_mse_kernel_matches_definition(dtype, ncomp, tol):
+    """jf_loss_primitive_mse against the Section 7.4 loss written out in
+    PyTorch (FP64): the loss and its gradient w.r.t. the predicted states
+    (autograd of the written-out definition), on a stack of ragged states."""
+    t = torch.float32 if dtype == "f32" else torch.float64
+    cases = [inputs.random_blocks((13, 11, 1), seed=s) for s in range(6)]
+    refs = [inputs.random_smooth((13, 11, 1), seed=10 + s) for s in range(6)]
+    U = torch.tensor(np.stack([c.U for c in cases]), dtype=t, device="cuda").reshape(2, 3, 5, 1, 11, 13)
+    R = torch.tensor(np.stack([c.U for c in refs]), dtype=t, device="cuda").reshape(2, 3, 5, 1, 11, 13)
+    grids = [jf.make_grid((13, 11, 1))]
+    b = jf.Batch(grids, dtype=dtype)
+    loss, grad = jf.loss_primitive_mse(b, U, R, ncomp)
+    b.sync()
+
+    def prim(X):
+        rho = X[..., 0, :, :, :]
+        u, v, w = (X[..., k, :, :, :] / rho for k in (1, 2, 3))
+        p = 0.4 * (X[..., 4, :, :, :] - 0.5 * rho * (u * u + v * v + w * w))
+        comps = [rho, u, v, p] if ncomp == 4 else [rho, u, v, w, p]
+        return torch.stack(comps, dim=-4)
+
+    Ud = U.double().clone().requires_grad_(True)
+    want = ((prim(Ud) - prim(R.double())) ** 2).mean()
+    want.backward()
+    assert abs(loss.item() - want.item()) <= tol * abs(want.item())
+    gscale = Ud.grad.abs().max().item()
+    assert torch.allclose(grad.double(), Ud.grad, rtol=0, atol=tol * 10 * gscale)
+    # through autograd, with the loss of a window stack
+    X = U.clone().requires_grad_(True)
+    autograd_loss = jfa.primitive_mse(b, X, R, ncomp)
+    autograd_loss.backward()
+    assert torch.equal(X.grad, grad)
+    b.close()
