@@ -361,21 +361,25 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speed
   const T ir = left ? irL : irR;
   const T w0 = left ? WL[1] : WR[1], w1 = left ? WL[2] : WR[2], w2 = left ? WL[3] : WR[3];
   const T S = left ? SL : SR, m = left ? mL : mR;
-  // physical flux of the chosen side
+  // physical flux F_K of the chosen side, plus S_K (U*_K - U_K) on a star
+  // side.  Mass: r u_n + S (fac - r); a tangential momentum component is
+  // (r u_n + S (fac - r)) u_t on either branch (its U* - U is (fac - r) u_t),
+  // so it is the mass flux times u_t; normal momentum: r u_n^2 + p +
+  // S (fac S* - r u_n); energy: u_n (E + p) + S (fac e* - E).
   const T mass = r * un;
-  T Fk[5] = {mass, mass * w0, mass * w1, mass * w2, un * (E + p)};
-  Fk[1 + D] += p;
+  T F0 = mass, Fn = mass * un + p, F4 = un * (E + p);
   if (star) {
     const T fac = m * trcp(S - Ss);
-    T Us[5] = {fac, fac * w0, fac * w1, fac * w2, fac * (E * ir + (Ss - un) * (Ss + p * trcp(m)))};
-    Us[1 + D] = fac * Ss;
-    const T Uk[5] = {r, r * w0, r * w1, r * w2, E};
-#pragma unroll
-    for (int q = 0; q < 5; ++q) F[q] = Fk[q] + S * (Us[q] - Uk[q]);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) F[q] = Fk[q];
+    F0 = mass + S * (fac - r);
+    Fn = Fn + S * (fac * Ss - mass);
+    F4 = F4 + S * (fac * (E * ir + (Ss - un) * (Ss + p * trcp(m))) - E);
   }
+  F[0] = F0;
+  F[1] = F0 * w0;
+  F[2] = F0 * w1;
+  F[3] = F0 * w2;
+  F[1 + D] = Fn;
+  F[4] = F4;
 }
 
 // HLL flux (Harten, Lax, van Leer 1983): F_L if 0 <= S_L, F_R if S_R <= 0,

@@ -386,12 +386,26 @@ __device__ __forceinline__ void face_riemann(const RingView<T, BX, BY, DIM, VISC
   else hllc<T, D>(Wm, Wp, g, F, 0);
 }
 
+// Cell-centre C4 tangential derivative sums of the z faces of one column
+// (FP32, z-marching kernels): h[t][j] for tangent t (0: x, 1: y) at the
+// planes k, k + 1, k + 2 of the face k + 1/2 (j = 0, 1, 2), the packed pair
+// (w, u_t) as in face_visc_add.  The face k + 3/2 reuses them and computes
+// only plane k + 3.
+struct ZTangents {
+  float2 h[2][3];
+};
+
 // Dissipative part of the net flux (Sections 2 and 3.4) through the face
 // between the cell at shared-memory position (x0, y0, plane 0) and its
 // neighbour along D, added to NF.
-template <typename T, int D, int BX, int BY, int DIM, bool VISC>
+// ZC (FP32, D == 2 only): 0 computes every tangential stencil; 1 computes
+// them and keeps those of planes 0..2 in *zc; 2 takes planes -1..1 from *zc,
+// computes plane 2 and shifts *zc to planes 0..2.
+template <typename T, int D, int BX, int BY, int DIM, bool VISC, int ZC = 0>
 __device__ __forceinline__ void face_visc_add(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0,
-                                              const Gas<T>& g, const T inv_h[3], T NF[5]) {
+                                              const Gas<T>& g, const T inv_h[3], T NF[5],
+                                              ZTangents* zc = nullptr) {
+  static_assert(ZC == 0 || (D == 2 && sizeof(T) == 4), "carried tangential stencils: FP32 z faces only");
   using Ro = Roles<D>;
   auto val = [&](int c, int n, int t1, int t2) -> T {
     int x, y, e;
@@ -446,9 +460,17 @@ __device__ __forceinline__ void face_visc_add(const RingView<T, BX, BY, DIM, VIS
       float2 h[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
+        if (ZC == 2 && q < 3) {
+          h[q] = zc->h[R - 1][q];
+          continue;
+        }
         auto at = [&](int j) { return R == 1 ? pair(1 + D, 1 + e, q - 1, j, 0) : pair(1 + D, 1 + e, q - 1, 0, j); };
         const float2 vm2 = at(-2), vm1 = at(-1), vp1 = at(1), vp2 = at(2);
         h[q] = __ffma2_rn(c2(8.0f), __ffma2_rn(m1, vm1, vp1), __ffma2_rn(m1, vp2, vm2));
+      }
+      if (ZC != 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) zc->h[R - 1][q] = h[q + 1];
       }
       const float he = inv_h[e];
       const float2 Ge = __ffma2_rn(c2(9.0f / 192.0f * he), __fadd2_rn(h[1], h[2]),
@@ -666,6 +688,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   T* EY = EX + 2 * 5 * SX;  // [2][5][BY+2][BX] (PC, DIM >= 2)
   T zL[5];
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
+  ZTangents ztan;  // FP32 z faces: the tangential stencils of the planes k .. k + 2
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight during plane k
   if (DIM == 3) {
     for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
@@ -683,7 +706,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         face_riemann<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, r, lz, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) NFz_lo[c] = -F[c];
-        if constexpr (VISC) face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+        if constexpr (VISC && sizeof(T) == 4)
+          face_visc_add<T, 2, BX, BY, DIM, VISC, 1>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo, &ztan);
+        else if constexpr (VISC)
+          face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
       } else {
         face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
       }
@@ -699,18 +725,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   int base = 0;  // slot of plane k - 3 (and of plane k + 3)
   for (int k = z0; k < z1; ++k) {
     set_view(base);
-    // this cell's U_s and U^n for the stage combination, loaded now so that
-    // their latency overlaps with the face computations
+    // this cell's U_s and U^n for the stage combination, loaded ahead of
+    // face computations so that their latency overlaps with them (default
+    // scheme: after the reconstruction phase, which keeps the registers
+    // free while it runs)
     const long long qc = ((long long)(DIM == 3 ? k : 0) * A.ny + gy) * A.nx + gx;
     T us[5], un[5];
-    if (own && !A.rhs_only) {
+    auto load_cell = [&]() {
+      if (own && !A.rhs_only) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        const bool ok = JF_CHECK(qc >= 0 && qc < A.N, "JFDBG cell qc=%lld N=%lld\n", qc, A.N);
-        us[c] = ok ? __ldg(A.Us + qc + c * A.N) : T(1);
-        un[c] = A.Un && ok ? A.Un[qc + c * A.N] : T(0);
+        for (int c = 0; c < 5; ++c) {
+          const bool ok = JF_CHECK(qc >= 0 && qc < A.N, "JFDBG cell qc=%lld N=%lld\n", qc, A.N);
+          us[c] = ok ? __ldg(A.Us + qc + c * A.N) : T(1);
+          un[c] = A.Un && ok ? A.Un[qc + c * A.N] : T(0);
+        }
       }
-    }
+    };
+    if constexpr (SCH != SCH_DEFAULT) load_cell();
 
     T NFz_hi[5];
     if constexpr (PC) {
@@ -764,9 +795,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           NFz_hi[c] = -F[c];
           zL[c] = r[c];
         }
-        if constexpr (VISC) face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+        if constexpr (VISC && sizeof(T) == 4)
+          face_visc_add<T, 2, BX, BY, DIM, VISC, 2>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi, &ztan);
+        else if constexpr (VISC)
+          face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
       }
       __syncthreads();
+      load_cell();
       // phase 2: the x and y faces from the stored values
       if (xf_x >= 0) {
         T Wm[5], Wp[5], F[5], NF[5];
