@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <queue>
 #include <vector>
 
 #include "../../include/jf.h"
@@ -137,19 +138,59 @@ int reduce_blocks(long long N, int sms) {
 
 // ------------------------------------------------------------------------
 // Variant selection.  A variant = (compiled tile shape, z chunk).  z chunk 0
-// (the first, default, one per tile) is chosen from the grid at launch: the
-// planes per CTA that give about one wave of resident CTAs (SMs x the CTAs
-// per SM the tile is bounded for), at most 32.  Large grids then take 32
-// planes (halo planes re-read once per 32), small ones fewer, so that a
-// 32^3 grid does not run on a handful of SMs.
+// (the first, default, one per tile) is chosen from the grid: grids whose
+// CTAs fit in one wave of resident CTAs (SMs x the CTAs per SM the tile is
+// bounded for) at 32 planes take the planes per CTA that give one wave, so
+// that a 32^3 grid does not run on a handful of SMs; larger grids take the
+// chunk length in 20..40 whose CTAs, dealt in launch order to the resident
+// slots, finish first (schedule_length), which keeps the partly filled last
+// wave short.
 static const int kZChunks[] = {0, 32, 16, 64, 8};
 
+// Length, in planes, of the greedy schedule of a 3D launch's CTAs: `tiles`
+// CTAs per z chunk of z planes (the last chunk shorter), chunk after chunk
+// as the hardware issues them, each costing its planes plus kPrologue planes
+// for its prologue (six plane loads and a face, measured at about half a
+// plane), over `slots` resident CTA slots.
+static double schedule_length(long long tiles, int nz, int z, long long slots) {
+  constexpr double kPrologue = 0.5;
+  std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+  for (long long i = 0; i < slots; ++i) free_at.push(0.0);
+  double end = 0.0;
+  for (int z0 = 0; z0 < nz; z0 += z) {
+    const double cost = (nz - z0 < z ? nz - z0 : z) + kPrologue;
+    for (long long t = 0; t < tiles; ++t) {
+      const double done = free_at.top() + cost;
+      free_at.pop();
+      free_at.push(done);
+      end = done > end ? done : end;
+    }
+  }
+  return end;
+}
+
 int auto_zchunk(const jf_ctx* h, int bx, int by, int ctas_per_sm) {
+  const long long key = ((long long)bx * 4096 + by) * 64 + ctas_per_sm;
+  auto it = h->zauto.find(key);
+  if (it != h->zauto.end()) return it->second;
   const long long tiles = (long long)((h->grid.nx + bx - 1) / bx) * ((h->grid.ny + by - 1) / by);
-  const long long target = (long long)h->sms * (ctas_per_sm > 0 ? ctas_per_sm : 1);
-  long long z = (h->grid.nz * tiles + target - 1) / target;
+  const long long slots = (long long)h->sms * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+  const long long nz = h->grid.nz;
+  long long z = (nz * tiles + slots - 1) / slots;
   if (z < 1) z = 1;
-  if (z > 32) z = 32;
+  if (z > 32) {
+    z = 32;
+    // larger grids: the shortest schedule over 20..40 planes (longest chunk
+    // on ties); very large launches keep 32 to bound the host's work
+    if (tiles * ((nz + 19) / 20) <= 400000) {
+      double best = 0.0;
+      for (int c = 40; c >= 20; --c) {
+        const double len = schedule_length(tiles, (int)nz, c, slots);
+        if (c == 40 || len < best - 1e-9) { best = len; z = c; }
+      }
+    }
+  }
+  h->zauto[key] = (int)z;
   return (int)z;
 }
 

@@ -45,6 +45,7 @@ struct jf_ctx {
   int variant = 0;           // index into the variant list of this configuration
   int table_index = 0;       // compiled-kernel table entry
   int zchunk = 32;           // planes per CTA (3D)
+  mutable std::map<long long, int> zauto;  // chosen automatic z chunk per (tile, CTAs per SM)
   void* stage[2] = {nullptr, nullptr};  // U1, U2
   void* adj[4] = {nullptr, nullptr, nullptr, nullptr};  // adjoint buffers (lazy)
   double* dt_buf = nullptr;  // device scalar

@@ -294,13 +294,15 @@ JF_HD void signal_speeds(const T WL[5], const T WR[5], const Gas<T>& g, int spee
     SL = unL - cL * qL;
     SR = unR + cR * qR;
   } else {
-    const T sL = tsqrt(rL), sR = tsqrt(rR);
-    const T inv_s = trcp(sL + sR);
+    // Roe weights sqrt(rho_K) / (sqrt(rho_L) + sqrt(rho_R)) from the ratio
+    // q = sqrt(rho_R / rho_L): w_L = 1 / (1 + q), w_R = q w_L
+    const T q = tsqrt(rR * irL);
+    const T wL = trcp(T(1) + q), wR = q * wL;
     const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
-    const T u0 = (sL * WL[1] + sR * WR[1]) * inv_s;
-    const T u1 = (sL * WL[2] + sR * WR[2]) * inv_s;
-    const T u2 = (sL * WL[3] + sR * WR[3]) * inv_s;
-    const T Ht = (sL * HL + sR * HR) * inv_s;
+    const T u0 = wL * WL[1] + wR * WR[1];
+    const T u1 = wL * WL[2] + wR * WR[2];
+    const T u2 = wL * WL[3] + wR * WR[3];
+    const T Ht = wL * HL + wR * HR;
     const T ct = tsqrt(g.gm1 * (Ht - T(0.5) * (u0 * u0 + u1 * u1 + u2 * u2)));
     const T un_t = D == 0 ? u0 : (D == 1 ? u1 : u2);
     SL = tmin(unL - cL, un_t - ct);
