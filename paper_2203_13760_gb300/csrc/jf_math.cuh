@@ -206,8 +206,13 @@ JF_HD void weno5_cell(T vm2, T vm1, T v0, T vp1, T vp2, T eps, T& right, T& left
     const T p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
     const T a0 = T(0.1) * p12, a1 = T(0.6) * p02, a2 = T(0.3) * p01;
     const T b0 = T(0.1) * p01, b2 = T(0.3) * p12;
-    right = v0 + (a0 * g0 + a1 * g1 + a2 * g2) / (T(6) * (a0 + a1 + a2));
-    left = v0 + (b0 * h0 + a1 * h1 + b2 * h2) / (T(6) * (b0 + a1 + b2));
+    // one division for both values: 1/D_r = D_l / (D_r D_l) and the converse
+    // (D >= 6e-25 as every s_k >= eps^2; the product stays far inside the
+    // FP64 range)
+    const T Dr = T(6) * (a0 + a1 + a2), Dl = T(6) * (b0 + a1 + b2);
+    const T inv = T(1) / (Dr * Dl);
+    right = v0 + (a0 * g0 + a1 * g1 + a2 * g2) * (Dl * inv);
+    left = v0 + (b0 * h0 + a1 * h1 + b2 * h2) * (Dr * inv);
   } else {
     const T r0 = trcp(t0 * t0), r1 = trcp(t1 * t1), r2 = trcp(t2 * t2);
     const T a0 = T(0.1) * r0, a1 = T(0.6) * r1, a2 = T(0.3) * r2;
@@ -318,6 +323,25 @@ JF_HD void side_state(const T W[5], const Gas<T>& g, T& E, T& ir, T& c) {
   c = tsqrt(g.gamma * W[4] * ir);
 }
 
+// Both sides' E, 1/rho and c; FP64 forms the two reciprocals from one
+// division, 1/rho_L = rho_R / (rho_L rho_R) and the converse.
+template <typename T>
+JF_HD void side_states(const T WL[5], const T WR[5], const Gas<T>& g, T& EL, T& ER, T& irL, T& irR, T& cL,
+                       T& cR) {
+  if constexpr (sizeof(T) == 8) {
+    const T inv = T(1) / (WL[0] * WR[0]);
+    irL = WR[0] * inv;
+    irR = WL[0] * inv;
+    EL = WL[4] * g.inv_gm1 + T(0.5) * WL[0] * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
+    ER = WR[4] * g.inv_gm1 + T(0.5) * WR[0] * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]);
+    cL = tsqrt(g.gamma * WL[4] * irL);
+    cR = tsqrt(g.gamma * WR[4] * irR);
+  } else {
+    side_state(WL, g, EL, irL, cL);
+    side_state(WR, g, ER, irR, cR);
+  }
+}
+
 // Physical flux along D and conservative state of one side.
 template <typename T, int D>
 JF_HD void side_flux(const T W[5], T E, T F[5], T U[5]) {
@@ -350,8 +374,7 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speed
   const T unL = WL[1 + D], unR = WR[1 + D];
   // every division goes through a reciprocal (1/rho of each side shared)
   T EL, ER, irL, irR, cL, cR;
-  side_state(WL, g, EL, irL, cL);
-  side_state(WR, g, ER, irR, cR);
+  side_states(WL, WR, g, EL, ER, irL, irR, cL, cR);
   T SL, SR;
   signal_speeds<T, D>(WL, WR, g, speeds, EL, ER, irL, irR, cL, cR, SL, SR);
   const T mL = rL * (SL - unL), mR = rR * (SR - unR);
@@ -389,8 +412,7 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speed
 template <typename T, int D>
 JF_HD void hll(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speeds = 0) {
   T EL, ER, irL, irR, cL, cR;
-  side_state(WL, g, EL, irL, cL);
-  side_state(WR, g, ER, irR, cR);
+  side_states(WL, WR, g, EL, ER, irL, irR, cL, cR);
   T SL, SR;
   signal_speeds<T, D>(WL, WR, g, speeds, EL, ER, irL, irR, cL, cR, SL, SR);
   T FL[5], FR[5], UL[5], UR[5];
@@ -414,8 +436,7 @@ JF_HD void hll(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speeds
 template <typename T, int D>
 JF_HD void rusanov(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
   T EL, ER, irL, irR, cL, cR;
-  side_state(WL, g, EL, irL, cL);
-  side_state(WR, g, ER, irR, cR);
+  side_states(WL, WR, g, EL, ER, irL, irR, cL, cR);
   const T a = tmax(fabs(WL[1 + D]) + cL, fabs(WR[1 + D]) + cR);
   T FL[5], FR[5], UL[5], UR[5];
   side_flux<T, D>(WL, EL, FL, UL);
@@ -535,8 +556,7 @@ JF_HD void nn_inputs(const T WL[5], const T WR[5], const Gas<T>& g, T cL, T cR, 
 template <typename T, int D>
 JF_HD void rusanov_nn(const T WL[5], const T WR[5], const Gas<T>& g, T F[5]) {
   T EL, ER, irL, irR, cL, cR;
-  side_state(WL, g, EL, irL, cL);
-  side_state(WR, g, ER, irR, cR);
+  side_states(WL, WR, g, EL, ER, irL, irR, cL, cR);
   T x[4];
   nn_inputs<T, D>(WL, WR, g, cL, cR, x);
   const T a = nn_alpha(g.nn, x);
