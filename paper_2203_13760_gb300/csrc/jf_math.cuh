@@ -394,10 +394,21 @@ JF_HD void hllc(const T WL[5], const T WR[5], const Gas<T>& g, T F[5], int speed
   const T mass = r * un;
   T F0 = mass, Fn = mass * un + p, F4 = un * (E + p);
   if (star) {
-    const T fac = m * trcp(S - Ss);
+    // fac = m / (S - S*) and p / m; FP64 takes both from one division,
+    // x = 1 / (m (S - S*)) (m and S - S* are non-zero on a star side:
+    // S_L < u_L - c_L, S_L < 0 <= S*, and the mirror image)
+    T fac, p_m;
+    if constexpr (sizeof(T) == 8) {
+      const T d = S - Ss, x = T(1) / (m * d);
+      fac = m * m * x;
+      p_m = p * d * x;
+    } else {
+      fac = m * trcp(S - Ss);
+      p_m = p * trcp(m);
+    }
     F0 = mass + S * (fac - r);
     Fn = Fn + S * (fac * Ss - mass);
-    F4 = F4 + S * (fac * (E * ir + (Ss - un) * (Ss + p * trcp(m))) - E);
+    F4 = F4 + S * (fac * (E * ir + (Ss - un) * (Ss + p_m)) - E);
   }
   F[0] = F0;
   F[1] = F0 * w0;
