@@ -691,6 +691,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   ZTangents ztan;  // FP32 z faces: the tangential stencils of the planes k .. k + 2
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight during plane k
   if (DIM == 3) {
+#pragma unroll 1
     for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
     __syncthreads();
     // lower face of plane z0 = upper face of plane z0 - 1 (slot 2); plane
@@ -775,15 +776,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         if (threadIdx.x < BX + 2) put_x(0, (int)threadIdx.x - 1);
       } else {
         // warps 0 .. BY-1: x row `warp` (cells -1 .. 30), y row warp - 1;
-        // warp BY: cells 31, 32 of every x row and the y rows BY - 1, BY
-        if (warp < BY) put_x(warp, lane - 1);
-        else if (lane < 2 * BY) put_x(lane >> 1, BX - 1 + (lane & 1));
-        if (warp < BY) {
-          put_y(warp - 1, lane);
-        } else {
-          put_y(BY - 1, lane);
-          put_y(BY, lane);
-        }
+        // warp BY: cells 31, 32 of every x row and the y rows BY - 1, BY.
+        // One call site each (the loop is not unrolled), so that the code of
+        // the plane loop stays small for the instruction cache.
+        const int xrow = warp < BY ? warp : (lane < 2 * BY ? lane >> 1 : -1);
+        const int xcol = warp < BY ? lane - 1 : BX - 1 + (lane & 1);
+        if (xrow >= 0) put_x(xrow, xcol);
+        const int yrow0 = warp < BY ? warp - 1 : BY - 1, nyrows = warp < BY ? 1 : 2;
+#pragma unroll 1
+        for (int q = 0; q < nyrows; ++q) put_y(yrow0 + q, lane);
       }
       if (DIM == 3 && cell_thread) {
         // face k + 1/2: zL (cell k) and the lower value of cell k + 1
