@@ -357,6 +357,21 @@ jf_status jf_set_variant(jf_handle h, int variant);
  * of variants (>= 1), or a negative jf_status. */
 int jf_variant_info(jf_handle h, int variant, char* buf, int len);
 
+/* Planes per CTA of the default launch variant of a 3D grid (host logic, no
+ * GPU needed; the "auto" z chunk that jf_variant_info reports).  Inputs: the
+ * grid's cells nx, ny, nz; the tile bx x by of the kernel; ctas_per_sm, the
+ * CTAs of that tile resident on one SM; sms, the GPU's SM count.  With
+ * tiles = ceil(nx/bx) ceil(ny/by) CTAs per plane and slots = sms x
+ * ctas_per_sm: if one wave of 32-plane CTAs covers the grid, the chunk is
+ * ceil(nz tiles / slots) (>= 1); otherwise it is the length z in 20..40
+ * (the longest on ties) whose launch finishes first in a greedy schedule of
+ * the CTAs in launch order (tiles CTAs per chunk, chunk after chunk, the
+ * last chunk nz - (ceil(nz/z) - 1) z planes, each CTA costing its planes
+ * plus half a plane of prologue) over `slots` identical slots; launches of
+ * more than 400000 CTAs at z = 20 keep 32.  Returns the chunk (>= 1), or 0
+ * if an argument is not positive. */
+int jf_auto_zchunk(int nx, int ny, int nz, int bx, int by, int ctas_per_sm, int sms);
+
 /* Wait for the handle's stream work (cudaDeviceSynchronize), then read and
  * clear the device error flag.  Returns JF_ERR_NONPHYSICAL if a kernel met a
  * non-physical state since the last call, JF_ERR_CUDA on a CUDA error,

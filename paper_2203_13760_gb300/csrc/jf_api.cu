@@ -169,13 +169,10 @@ static double schedule_length(long long tiles, int nz, int z, long long slots) {
   return end;
 }
 
-int auto_zchunk(const jf_ctx* h, int bx, int by, int ctas_per_sm) {
-  const long long key = ((long long)bx * 4096 + by) * 64 + ctas_per_sm;
-  auto it = h->zauto.find(key);
-  if (it != h->zauto.end()) return it->second;
-  const long long tiles = (long long)((h->grid.nx + bx - 1) / bx) * ((h->grid.ny + by - 1) / by);
-  const long long slots = (long long)h->sms * (ctas_per_sm > 0 ? ctas_per_sm : 1);
-  const long long nz = h->grid.nz;
+// The rule of jf_auto_zchunk (include/jf.h).
+int zchunk_rule(long long nx, long long ny, long long nz, int bx, int by, int ctas_per_sm, int sms) {
+  const long long tiles = ((nx + bx - 1) / bx) * ((ny + by - 1) / by);
+  const long long slots = (long long)sms * ctas_per_sm;
   long long z = (nz * tiles + slots - 1) / slots;
   if (z < 1) z = 1;
   if (z > 32) {
@@ -190,8 +187,16 @@ int auto_zchunk(const jf_ctx* h, int bx, int by, int ctas_per_sm) {
       }
     }
   }
-  h->zauto[key] = (int)z;
   return (int)z;
+}
+
+int auto_zchunk(const jf_ctx* h, int bx, int by, int ctas_per_sm) {
+  const long long key = ((long long)bx * 4096 + by) * 64 + ctas_per_sm;
+  auto it = h->zauto.find(key);
+  if (it != h->zauto.end()) return it->second;
+  const int z = zchunk_rule(h->grid.nx, h->grid.ny, h->grid.nz, bx, by, ctas_per_sm > 0 ? ctas_per_sm : 1, h->sms);
+  h->zauto[key] = z;
+  return z;
 }
 
 bool has_walls(const jf_grid& g) {
@@ -652,6 +657,11 @@ int jf_variant_info(jf_handle h, int variant, char* buf, int len) {
   if (!h) return JF_ERR_ARG;
   if (h->kind == 1) return batch_variant_info(h, variant, buf, len);
   return JF_DISPATCH(h, describe_variant, h, variant, buf, len);
+}
+
+int jf_auto_zchunk(int nx, int ny, int nz, int bx, int by, int ctas_per_sm, int sms) {
+  if (nx < 1 || ny < 1 || nz < 1 || bx < 1 || by < 1 || ctas_per_sm < 1 || sms < 1) return 0;
+  return zchunk_rule(nx, ny, nz, bx, by, ctas_per_sm, sms);
 }
 
 jf_status jf_status_sync(jf_handle h) {

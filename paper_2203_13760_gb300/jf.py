@@ -84,6 +84,7 @@ SIGNATURES = {
     "jf_set_variant": (_I, [_VP, _I]),
     "jf_set_nn": (_I, [_VP, _VP, _I]),
     "jf_variant_info": (_I, [_VP, _I, ctypes.c_char_p, _I]),
+    "jf_auto_zchunk": (_I, [_I, _I, _I, _I, _I, _I, _I]),
     "jf_status_sync": (_I, [_VP]),
     "jf_last_error": (ctypes.c_char_p, [_VP]),
     "jf_version": (ctypes.c_char_p, []),
@@ -126,6 +127,13 @@ def _stream():
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def auto_zchunk(n, tile=(32, 7), ctas_per_sm=2, sms=152):
+    """Default planes per CTA of a 3D grid n = (nx, ny, nz) (jf_auto_zchunk;
+    host logic, no GPU needed)."""
+    return int(lib().jf_auto_zchunk(int(n[0]), int(n[1]), int(n[2]), int(tile[0]), int(tile[1]),
+                                    int(ctas_per_sm), int(sms)))
 
 
 def fma_peak(dtype="f32", iters=None):
