@@ -689,7 +689,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   T zL[5];
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
   ZTangents ztan;  // FP32 z faces: the tangential stencils of the planes k .. k + 2
-  PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight during plane k
+  PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight while plane k is computed
   if (DIM == 3) {
 #pragma unroll 1
     for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
@@ -717,7 +717,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     }
     __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
     load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring, gx0, gy0, z0 + 3);
-    if (z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, z0 + 4);
+    // (default scheme: each plane fetches plane k + 4 after its reconstruction phase)
+    if (!PC && z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, z0 + 4);
   } else {
     load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring, gx0, gy0, 0);
   }
@@ -803,6 +804,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       }
       __syncthreads();
       load_cell();
+      // plane k + 4 in flight during the faces and the update (committed at
+      // the end of this plane); its registers are free during the
+      // reconstruction phase
+      if (DIM == 3 && k + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, k + 4);
       // phase 2: the x and y faces from the stored values
       if (xf_x >= 0) {
         T Wm[5], Wp[5], F[5], NF[5];
@@ -885,7 +890,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       const int nb = base + 1 == 6 ? 0 : base + 1;  // slot of plane k - 2, dead after this plane's faces
       if (k + 1 < z1) {
         commit_plane<T, BX, BY, DIM, VISC>(A, g, next, ring + nb * G::PLANE);  // plane k + 4
-        if (k + 2 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, k + 5);
+        if (!PC && k + 2 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, k + 5);
       }
       __syncthreads();
       base = nb;
