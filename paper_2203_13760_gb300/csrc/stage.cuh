@@ -803,7 +803,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
       }
       __syncthreads();
-      load_cell();
       // plane k + 4 in flight during the faces and the update (committed at
       // the end of this plane); its registers are free during the
       // reconstruction phase
@@ -826,6 +825,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         for (int c = 0; c < 5; ++c)
           if (JF_CHECK(t >= 0 && t < G::NFX, "JFDBG Fx t=%d\n", t)) Fx[c * G::NFX + t] = NF[c];
       }
+      load_cell();
       if (DIM >= 2) {
         T Wm[5], Wp[5], F[5], NF[5];
         const int i = yf_y * BX + yf_x;  // lower cell row yf_y - 1
