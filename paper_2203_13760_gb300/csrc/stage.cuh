@@ -680,14 +680,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   };
 
   // default scheme: WENO5 runs once per cell and direction (weno5_cell), the
-  // face values of a plane kept in shared memory (x, y) or, along z, in
-  // registers (zL: the value of the current cell at its upper face)
+  // face values of a plane kept in shared memory (x, y; along z only the
+  // current cell's value at its upper face, zl, is kept, by its column)
   constexpr bool PC = SCH == SCH_DEFAULT;
   constexpr int SX = BY * (BX + 2), SY = (BY + 2) * BX;
   T* EX = Fy + 5 * G::NFY;  // [2][5][BY][BX+2] (PC only)
   T* EY = EX + 2 * 5 * SX;  // [2][5][BY+2][BX] (PC, DIM >= 2)
-  T zL[5];
-  T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};
+  // default scheme, 3D: the net fluxes of a column's z faces in shared
+  // memory, [2][5][NCELL] (face k + 1/2 in slot k & 1), written and read by
+  // the column's own thread, so that they hold no registers across the phases
+  constexpr bool ZS = PC && DIM == 3;
+  T* ZF = EY + 2 * 5 * SY;
+  auto zf = [&](int k, int c) -> T& { return ZF[((k & 1) * 5 + c) * G::NCELL + threadIdx.x]; };
+  // and the WENO5 value of the column's cell k at k + 1/2 (the left state of
+  // the next z face), [5][NCELL]
+  auto zl = [&](int c) -> T& { return ZF[(10 + c) * G::NCELL + threadIdx.x]; };
+  T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};  // other schemes: the lower z face's net flux
   ZTangents ztan;  // FP32 z faces: the tangential stencils of the planes k .. k + 2
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight while plane k is computed
   if (DIM == 3) {
@@ -699,18 +707,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     set_view(5);
     if (cell_thread) {
       if constexpr (PC) {
-        // face z0 - 1/2 from the values of cells z0 - 1 and z0; zL: cell z0 at z0 + 1/2
-        T r[5], l[5], lz[5];
+        // face z0 - 1/2 from the values of cells z0 - 1 and z0; zl: cell z0 at z0 + 1/2
+        T r[5], l[5], rz[5], lz[5];
         cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 0, g.eps, r, l);
-        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, zL, lz);
-        T F[5];
+        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, rz, lz);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) zl(c) = rz[c];
+        T F[5], NF[5];
         face_riemann<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, r, lz, F);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) NFz_lo[c] = -F[c];
+        for (int c = 0; c < 5; ++c) NF[c] = -F[c];
         if constexpr (VISC && sizeof(T) == 4)
-          face_visc_add<T, 2, BX, BY, DIM, VISC, 1>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo, &ztan);
+          face_visc_add<T, 2, BX, BY, DIM, VISC, 1>(R, HALO + tx, G::HY + ty, g, inv_h, NF, &ztan);
         else if constexpr (VISC)
-          face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
+          face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NF);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) zf(z0 - 1, c) = NF[c];
       } else {
         face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_lo);
       }
@@ -788,19 +800,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         for (int q = 0; q < nyrows; ++q) put_y(yrow0 + q, lane);
       }
       if (DIM == 3 && cell_thread) {
-        // face k + 1/2: zL (cell k) and the lower value of cell k + 1
-        T r[5], l[5], F[5];
+        // face k + 1/2: the stored value of cell k (zl) and the lower value of cell k + 1
+        T r[5], l[5], F[5], NF[5], zl0[5];
         cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, r, l);
-        face_riemann<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, zL, l, F);
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          NFz_hi[c] = -F[c];
-          zL[c] = r[c];
+          zl0[c] = zl(c);
+          zl(c) = r[c];
         }
+        face_riemann<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, zl0, l, F);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) NF[c] = -F[c];
         if constexpr (VISC && sizeof(T) == 4)
-          face_visc_add<T, 2, BX, BY, DIM, VISC, 2>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi, &ztan);
+          face_visc_add<T, 2, BX, BY, DIM, VISC, 2>(R, HALO + tx, G::HY + ty, g, inv_h, NF, &ztan);
         else if constexpr (VISC)
-          face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+          face_visc_add<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, g, inv_h, NF);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) zf(k, c) = NF[c];
       }
       __syncthreads();
       // plane k + 4 in flight during the faces and the update (committed at
@@ -873,7 +889,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           const int fy = ty * BX + tx;
           rhs += (Fy[c * G::NFY + fy + BX] - Fy[c * G::NFY + fy]) * inv_h[1];
         }
-        if (DIM == 3) rhs += (NFz_hi[c] - NFz_lo[c]) * inv_h[2];
+        if constexpr (ZS) rhs += (zf(k, c) - zf(k + 1, c)) * inv_h[2];  // faces k + 1/2 and k - 1/2
+        else if (DIM == 3) rhs += (NFz_hi[c] - NFz_lo[c]) * inv_h[2];
         T o;
         if (A.rhs_only) {
           o = rhs;
@@ -886,7 +903,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     }
     if (DIM == 3) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) NFz_lo[c] = NFz_hi[c];
+      for (int c = 0; c < 5; ++c) NFz_lo[c] = NFz_hi[c];  // (other schemes)
       const int nb = base + 1 == 6 ? 0 : base + 1;  // slot of plane k - 2, dead after this plane's faces
       if (k + 1 < z1) {
         commit_plane<T, BX, BY, DIM, VISC>(A, g, next, ring + nb * G::PLANE);  // plane k + 4
@@ -961,9 +978,11 @@ constexpr size_t stage_smem_elems() {
 // Default scheme: the per-cell WENO5 face values of a plane, after the face
 // buffers: x [2][5][BY][BX+2] (cells -1 .. BX of each row), y [2][5][BY+2][BX]
 // (rows -1 .. BY); index 0 the value at the cell's right face, 1 at its left.
+// 3D: then the z-face net fluxes [2][5][NCELL] and the upper WENO5 values of
+// the columns' current cells [5][NCELL].
 template <int DIM, int BX, int BY>
 constexpr size_t recon_smem_elems() {
-  return (size_t)2 * 5 * (BY * (BX + 2) + (DIM >= 2 ? (BY + 2) * BX : 0));
+  return (size_t)2 * 5 * (BY * (BX + 2) + (DIM >= 2 ? (BY + 2) * BX : 0)) + (DIM == 3 ? 3 * 5 * BX * BY : 0);
 }
 
 // Element offset of the Rusanov-NN parameters in the dynamic shared memory:
