@@ -739,10 +739,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   int base = 0;  // slot of plane k - 3 (and of plane k + 3)
   for (int k = z0; k < z1; ++k) {
     set_view(base);
-    // this cell's U_s and U^n for the stage combination, loaded ahead of
+    // this cell's U_s and U^n for the stage combination, loaded ahead of the
     // face computations so that their latency overlaps with them (default
-    // scheme: after the reconstruction phase, which keeps the registers
-    // free while it runs)
+    // scheme in 3D: after the x face, which keeps their registers free during
+    // the reconstruction phase and the x face; the 3D march holds more state)
     const long long qc = ((long long)(DIM == 3 ? k : 0) * A.ny + gy) * A.nx + gx;
     T us[5], un[5];
     auto load_cell = [&]() {
@@ -755,7 +755,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         }
       }
     };
-    if constexpr (SCH != SCH_DEFAULT) load_cell();
+    // (default scheme in 3D: after the x face below)
+    if constexpr (SCH != SCH_DEFAULT || DIM < 3) load_cell();
 
     T NFz_hi[5];
     if constexpr (PC) {
@@ -841,7 +842,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         for (int c = 0; c < 5; ++c)
           if (JF_CHECK(t >= 0 && t < G::NFX, "JFDBG Fx t=%d\n", t)) Fx[c * G::NFX + t] = NF[c];
       }
-      load_cell();
+      if constexpr (DIM == 3) load_cell();
       if (DIM >= 2) {
         T Wm[5], Wp[5], F[5], NF[5];
         const int i = yf_y * BX + yf_x;  // lower cell row yf_y - 1
