@@ -596,8 +596,9 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
 // cell sits `shift` cells along D from ring position (x0, y0, plane 0);
 // right[c] = v^-_{+1/2}, its value at the face to its right (the left state
 // of that face), left[c] = v^+_{-1/2} (the right state of the face to its
-// left).  FP32: (rho, p) and (u, v) in packed lanes, w alone.
-template <typename T, int D, int BX, int BY, int DIM, bool VISC>
+// left).  FP32: (rho, p) and (u, v) in packed lanes, w alone (or, NOW, not
+// at all: the caller pairs it with another cell's w).
+template <typename T, int D, int BX, int BY, int DIM, bool VISC, bool NOW = false>
 __device__ __forceinline__ void cell_recon(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0, int shift, T eps,
                                            T right[5], T left[5]) {
   using Ro = Roles<D>;
@@ -613,7 +614,7 @@ __device__ __forceinline__ void cell_recon(const RingView<T, BX, BY, DIM, VISC>&
     right[0] = r.x; right[4] = r.y; left[0] = l.x; left[4] = l.y;
     weno5_cell_pair(pr(1, 2, -2), pr(1, 2, -1), pr(1, 2, 0), pr(1, 2, 1), pr(1, 2, 2), eps, r, l);
     right[1] = r.x; right[2] = r.y; left[1] = l.x; left[2] = l.y;
-    weno5_cell<float>(val(3, -2), val(3, -1), val(3, 0), val(3, 1), val(3, 2), eps, right[3], left[3]);
+    if constexpr (!NOW) weno5_cell<float>(val(3, -2), val(3, -1), val(3, 0), val(3, 1), val(3, 2), eps, right[3], left[3]);
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c)
@@ -788,6 +789,52 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       };
       if (DIM == 1) {
         if (threadIdx.x < BX + 2) put_x(0, (int)threadIdx.x - 1);
+      } else if constexpr (sizeof(T) == 4) {
+        // the same cells as below; the w components of a thread's x cell and
+        // (first) y cell share one packed WENO5 (threads without an x cell
+        // reconstruct an in-range one and discard it)
+        const bool hx = warp < BY || lane < 2 * BY;
+        const int xrow = warp < BY ? warp : (hx ? lane >> 1 : 0);
+        const int xcol = warp < BY ? lane - 1 : (hx ? BX - 1 + (lane & 1) : 0);
+        const int yrow0 = warp < BY ? warp - 1 : BY - 1;
+        T r[5], l[5];
+        cell_recon<T, 0, BX, BY, DIM, VISC, true>(R, HALO + xcol, G::HY + xrow, 0, g.eps, r, l);
+        const int ix = xrow * (BX + 2) + xcol + 1;
+        if (hx) {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            if (c == 3) continue;
+            if (JF_CHECK(ix >= 0 && ix < SX, "JFDBG EX i=%d\n", ix)) {
+              EX[c * SX + ix] = r[c];
+              EX[(5 + c) * SX + ix] = l[c];
+            }
+          }
+        }
+        cell_recon<T, 1, BX, BY, DIM, VISC, true>(R, HALO + lane, G::HY + yrow0, 0, g.eps, r, l);
+        const int iy = (yrow0 + 1) * BX + lane;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          if (c == 3) continue;
+          if (JF_CHECK(iy >= 0 && iy < SY, "JFDBG EY i=%d\n", iy)) {
+            EY[c * SY + iy] = r[c];
+            EY[(5 + c) * SY + iy] = l[c];
+          }
+        }
+        float2 wv[5];
+#pragma unroll
+        for (int n = 0; n < 5; ++n)
+          wv[n] = make_float2(R.at(3, HALO + xcol + n - 2, G::HY + xrow, 0), R.at(3, HALO + lane, G::HY + yrow0 + n - 2, 0));
+        float2 wr, wl;
+        weno5_cell_pair(wv[0], wv[1], wv[2], wv[3], wv[4], g.eps, wr, wl);
+        if (hx && JF_CHECK(ix >= 0 && ix < SX, "JFDBG EX i=%d\n", ix)) {
+          EX[3 * SX + ix] = wr.x;
+          EX[8 * SX + ix] = wl.x;
+        }
+        if (JF_CHECK(iy >= 0 && iy < SY, "JFDBG EY i=%d\n", iy)) {
+          EY[3 * SY + iy] = wr.y;
+          EY[8 * SY + iy] = wl.y;
+        }
+        if (warp == BY) put_y(BY, lane);  // warp BY's second y row
       } else {
         // warps 0 .. BY-1: x row `warp` (cells -1 .. 30), y row warp - 1;
         // warp BY: cells 31, 32 of every x row and the y rows BY - 1, BY.
@@ -881,7 +928,43 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     }
     __syncthreads();
 
-    if (own) {
+    if constexpr (sizeof(T) == 4 && (ZS || DIM < 3)) {
+      // FP32: the components (0, 1) and (2, 3) in the lanes of packed
+      // operations (per lane the operations of the scalar form below), 4 alone
+      if (own) {
+        const int fx = ty * (BX + 1) + tx, fy = ty * BX + tx;
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        auto c2 = [](float x) { return make_float2(x, x); };
+        auto comb = [&](int c, bool two) {  // components c and (two) c + 1
+          auto pr = [&](auto get) { return make_float2(get(c), two ? get(c + 1) : 0.0f); };
+          float2 lo = pr([&](int cc) { return Fx[cc * G::NFX + fx]; });
+          float2 hi = pr([&](int cc) { return Fx[cc * G::NFX + fx + 1]; });
+          float2 rhs = __fmul2_rn(__ffma2_rn(m1, lo, hi), c2(inv_h[0]));
+          if constexpr (DIM >= 2) {
+            lo = pr([&](int cc) { return Fy[cc * G::NFY + fy]; });
+            hi = pr([&](int cc) { return Fy[cc * G::NFY + fy + BX]; });
+            rhs = __ffma2_rn(__ffma2_rn(m1, lo, hi), c2(inv_h[1]), rhs);
+          }
+          if constexpr (ZS) {  // faces k + 1/2 and k - 1/2
+            lo = pr([&](int cc) { return zf(k + 1, cc); });
+            hi = pr([&](int cc) { return zf(k, cc); });
+            rhs = __ffma2_rn(__ffma2_rn(m1, lo, hi), c2(inv_h[2]), rhs);
+          }
+          float2 o = rhs;
+          if (!A.rhs_only) {
+            o = __fmul2_rn(c2(A.b), __ffma2_rn(c2(dt), rhs, pr([&](int cc) { return us[cc]; })));
+            if (A.Un) o = __ffma2_rn(c2(A.a), pr([&](int cc) { return un[cc]; }), o);
+          }
+          if (JF_CHECK(qc >= 0 && qc < A.N, "JFDBG store qc=%lld N=%lld\n", qc, A.N)) {
+            A.out[qc + c * A.N] = o.x;
+            if (two) A.out[qc + (c + 1) * A.N] = o.y;
+          }
+        };
+        comb(0, true);
+        comb(2, true);
+        comb(4, false);
+      }
+    } else if (own) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         const int fx = ty * (BX + 1) + tx;
