@@ -186,6 +186,49 @@ __device__ __forceinline__ void fetch_plane(const StageArgs<T>& A, PlaneRegs<T, 
   }
 }
 
+// In-plane offsets (gy nx + gx, after the index map) of the cells a thread
+// fetches: the same for every plane of a z-march without walls, so the march
+// computes them once per tile (plane_map) and fetches with them
+// (fetch_plane_mapped).
+template <typename T, int BX, int BY, int DIM, bool VISC>
+struct PlaneMap {
+  int off[PlaneRegs<T, BX, BY, DIM, VISC>::PF];
+};
+
+template <typename T, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void plane_map(const StageArgs<T>& A, PlaneMap<T, BX, BY, DIM, VISC>& m, int gx0,
+                                          int gy0) {
+  using G = Geo<BX, BY, DIM, VISC>;
+#pragma unroll
+  for (int i = 0; i < PlaneRegs<T, BX, BY, DIM, VISC>::PF; ++i) {
+    const int t = threadIdx.x + i * G::NT;
+    const int ly = t / G::PX, lx = t - ly * G::PX;
+    const int gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
+    const int gy = DIM >= 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
+    m.off[i] = t < G::CS ? gy * A.nx + gx : 0;
+  }
+}
+
+template <typename T, int BX, int BY, int DIM, bool VISC>
+__device__ __forceinline__ void fetch_plane_mapped(const StageArgs<T>& A, PlaneRegs<T, BX, BY, DIM, VISC>& r,
+                                                   const PlaneMap<T, BX, BY, DIM, VISC>& m, int gz) {
+  using G = Geo<BX, BY, DIM, VISC>;
+  const int kz = DIM == 3 ? map_index(gz, A.nz, A.periodic[2]) : 0;
+  const long long zoff = (long long)kz * A.ny * A.nx;
+#pragma unroll
+  for (int i = 0; i < PlaneRegs<T, BX, BY, DIM, VISC>::PF; ++i) {
+    const int t = threadIdx.x + i * G::NT;
+    if (t < G::CS) {
+      const long long q = zoff + m.off[i];
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        r.v[i][c] = JF_CHECK(q >= 0 && q < A.N, "JFDBG fetch q=%lld N=%lld t=%d\n", q, A.N, t)
+                        ? __ldg(A.Us + q + c * A.N)
+                        : T(1);
+    }
+  }
+}
+
 // Convert fetched conservative values to primitives (+ temperature) and
 // store them into the plane at dst.
 template <typename T, int BX, int BY, int DIM, bool VISC>
@@ -699,6 +742,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};  // other schemes: the lower z face's net flux
   ZTangents ztan;  // FP32 z faces: the tangential stencils of the planes k .. k + 2
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight while plane k is computed
+  PlaneMap<T, BX, BY, DIM, VISC> pmap;    // default scheme (no walls): the in-plane offsets of its cells
+  if constexpr (PC && DIM == 3) plane_map<T, BX, BY, DIM, VISC>(A, pmap, gx0, gy0);
   if (DIM == 3) {
 #pragma unroll 1
     for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
@@ -870,7 +915,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       // plane k + 4 in flight during the faces and the update (committed at
       // the end of this plane); its registers are free during the
       // reconstruction phase
-      if (DIM == 3 && k + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, k + 4);
+      if (DIM == 3 && k + 1 < z1) fetch_plane_mapped<T, BX, BY, DIM, VISC>(A, next, pmap, k + 4);
       // phase 2: the x and y faces from the stored values
       if (xf_x >= 0) {
         T Wm[5], Wp[5], F[5], NF[5];
