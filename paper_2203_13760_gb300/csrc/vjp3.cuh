@@ -155,21 +155,25 @@ __device__ __forceinline__ void vjp3_load_m(const VjpArgs<T>& A, T* dst, int x0,
   }
 }
 
-// Accumulator slot src (plane gz, unmapped) added to Gacc and cleared.
+// Accumulator slot src (plane gz, unmapped) added to Gacc and cleared: a
+// thread per plane cell maps the cell once and adds its components.
 template <typename T, bool VISC, int BX, int BY, int NT>
 __device__ __forceinline__ void vjp3_flush(const VjpArgs<T>& A, T* src, T* __restrict__ Gacc, int x0, int y0,
                                            int gz) {
   using G = V3Geo<BX, BY, VISC>;
   const int kz = map_index(gz, A.n[2], A.periodic[2]);
-  for (int t = threadIdx.x; t < G::PLANE; t += NT) {
-    const T v = src[t];
-    if (v != T(0)) {
-      const int c = t / G::CS, r = t - c * G::CS;
-      const int ly = r / G::PX, lx = r - ly * G::PX;
-      const int gx = map_index(x0 + lx - G::H, A.n[0], A.periodic[0]);
-      const int gy = map_index(y0 + ly - G::H, A.n[1], A.periodic[1]);
-      atomicAdd(Gacc + (long long)c * A.N + ((long long)kz * A.n[1] + gy) * A.n[0] + gx, v);
-      src[t] = T(0);
+  for (int t = threadIdx.x; t < G::CS; t += NT) {
+    const int ly = t / G::PX, lx = t - ly * G::PX;
+    const int gx = map_index(x0 + lx - G::H, A.n[0], A.periodic[0]);
+    const int gy = map_index(y0 + ly - G::H, A.n[1], A.periodic[1]);
+    const long long q = ((long long)kz * A.n[1] + gy) * A.n[0] + gx;
+#pragma unroll
+    for (int c = 0; c < G::NCW; ++c) {
+      const T v = src[c * G::CS + t];
+      if (v != T(0)) {
+        atomicAdd(Gacc + (long long)c * A.N + q, v);
+        src[c * G::CS + t] = T(0);
+      }
     }
   }
 }
