@@ -199,6 +199,13 @@ __global__ void __launch_bounds__(NT, MINB)
   const int fx = ex + ((!A.periodic[0] && x0 + BX >= nx) ? 1 : 0);
   const int fy = ey + ((!A.periodic[1] && y0 + BY >= ny) ? 1 : 0);
   const int kend = z1 + ((!A.periodic[2] && z1 == nz) ? 1 : 0);  // face plane nz: the top boundary z face
+  // task decoding divides by fx and ex (1 .. BX + 1): for d >= 2,
+  // r / d = (r m_d) >> 32 with m_d = ceil(2^32 / d) < 2^32, exact for
+  // r < 2^16 (the error r (m_d - 2^32/d) / 2^32 < 2^-16 stays below 1/d);
+  // d = 1 keeps r (m = 0 flags it)
+  const unsigned mfx = fx > 1 ? 0xffffffffu / (unsigned)fx + 1u : 0u;
+  const unsigned mex = ex > 1 ? 0xffffffffu / (unsigned)ex + 1u : 0u;
+  auto divu = [](int r, unsigned m) { return m ? (int)__umulhi((unsigned)r, m) : r; };
   const T inv_h[3] = {A.inv_h[0], A.inv_h[1], A.inv_h[2]};
 
   bool bad = false;
@@ -277,16 +284,16 @@ __global__ void __launch_bounds__(NT, MINB)
       const bool visc = VISC && r >= nconv;
       if (visc) r -= nconv;
       if (r < nfx) {  // x face: lower face of cell (x0 + f, y0 + j, k)
-        const int j = r / fx, f = r - j * fx;
+        const int j = divu(r, mfx), f = r - j * fx;
         const int p[3] = {f - 1, j, 0};
         run_face(std::integral_constant<int, 0>{}, p, visc);
       } else if ((r -= nfx) < nfy) {  // y face: lower face of cell (x0 + i, y0 + f, k)
-        const int f = r / ex, i = r - f * ex;
+        const int f = divu(r, mex), i = r - f * ex;
         const int p[3] = {i, f - 1, 0};
         run_face(std::integral_constant<int, 1>{}, p, visc);
       } else {  // z face between planes k - 1 and k
         r -= nfy;
-        const int j = r / ex, i = r - j * ex;
+        const int j = divu(r, mex), i = r - j * ex;
         const int p[3] = {i, j, -1};
         run_face(std::integral_constant<int, 2>{}, p, visc);
       }
