@@ -292,3 +292,18 @@ def test_step_host_equals_device_steps(dtype):
     s.sync()
     for k in range(5):
         assert torch.equal(outs[k], want[k]), k
+
+
+@pytest.mark.parametrize("n", [(32, 32, 32), (128, 128, 128), (256, 256, 256), (200, 96, 300)])
+def test_auto_zchunk_is_the_launch_rule(n):
+    """The default variant of a 3D handle reports the z chunk that
+    jf_auto_zchunk computes for its grid, tile and occupancy on this GPU."""
+    import re
+    s = jf.Solver(n, dtype="f32", viscous=True, heat=True, mu=0.01)
+    desc = s.variants()[0]
+    m = re.match(r"tile=(\d+)x(\d+) zchunk=auto\((\d+)\) smem=\d+ ctas/sm=(\d+)", desc)
+    assert m, desc
+    bx, by, z, cps = (int(v) for v in m.groups())
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert z == jf.auto_zchunk(n, tile=(bx, by), ctas_per_sm=cps, sms=sms)
+    s.close()
