@@ -23,7 +23,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr"]
 # FP32 kernels use approximate division / square root (see stage_f32.cu)
 _FAST = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
-PER_FILE_FLAGS = {"stage_f32.cu": _FAST, "stage_f32_gen.cu": _FAST, "stage_f32_roe.cu": _FAST, "stage_f32_nn.cu": _FAST, "stage_f32_ext.cu": _FAST, "vjp_f32.cu": _FAST}
+PER_FILE_FLAGS = {"stage_f32.cu": _FAST, "stage_f32_gen.cu": _FAST, "stage_f32_roe.cu": _FAST, "stage_f32_nn.cu": _FAST, "stage_f32_ext.cu": _FAST,
+                  "stage_f32_rows.cu": _FAST, "vjp_f32.cu": _FAST}
 
 
 def nvcc() -> str:

@@ -67,7 +67,19 @@ jf_status setup_variant(jf_ctx* h, int v) {
   const bool visc = dissipative(h->gas, h->scheme);
   auto list = batch_variant_list<T>(h->dim, visc, scheme_kind(h));
   if (list.empty()) { set_error(h, "batch: no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
-  if (v < 0) v = 0;
+  if (v < 0) {
+    v = 0;
+    if constexpr (sizeof(T) == 4) {  // FP32 2D: the row tiles where rows_preferred says so
+      int count = 0;
+      const StageVariant<T>* tab = stage_variants<T>(&count);
+      for (int i = 0; i < (int)list.size(); ++i)
+        if (tab[list[i]].ymarch) {
+          const StageVariant<T>& t0 = tab[list[0]];
+          if (rows_preferred(h->grids.data(), h->nsim, tab[list[i]].bx, t0.bx, t0.by)) v = i;
+          break;
+        }
+    }
+  }
   if (v >= (int)list.size()) { set_error(h, "batch: variant index out of range"); return JF_ERR_ARG; }
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
@@ -76,11 +88,33 @@ jf_status setup_variant(jf_ctx* h, int v) {
   cudaError_t e = sv.prepare_batch(&per_sm);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch: kernel set-up");
   if (per_sm < 1) { set_error(h, "batch: kernel does not fit on an SM"); return JF_ERR_UNSUPPORTED; }
+  const long long cap = (long long)h->sms * per_sm;
+  const int grid_blocks_max = (int)(cap < (1LL << 30) ? cap : (1LL << 30));
+  // row-march variants: the rows per item whose static round robin over the
+  // persistent CTAs ends first (an item costs its rows plus half a row for
+  // its prologue)
+  int rows = 1;
+  if (sv.ymarch) {
+    double best = 0.0;
+    for (int r : {64, 48, 32, 24, 16}) {
+      std::vector<double> load(grid_blocks_max, 0.0);
+      long long item = 0;
+      for (int s = 0; s < h->nsim; ++s) {
+        const jf_grid& g = h->grids[s];
+        const int tx = (g.nx + sv.bx - 1) / sv.bx;
+        for (int y0 = 0; y0 < g.ny; y0 += r)
+          for (int x = 0; x < tx; ++x, ++item) load[item % grid_blocks_max] += (g.ny - y0 < r ? g.ny - y0 : r) + 0.5;
+      }
+      double end = 0.0;
+      for (double l : load) end = l > end ? l : end;
+      if (r == 64 || end < best - 1e-9) { best = end; rows = r; }
+    }
+  }
   std::vector<WorkItem> work;
   for (int s = 0; s < h->nsim; ++s) {
     const jf_grid& g = h->grids[s];
     const int tx = (g.nx + sv.bx - 1) / sv.bx;
-    const int ty = h->dim >= 2 ? (g.ny + sv.by - 1) / sv.by : 1;
+    const int ty = sv.ymarch ? (g.ny + rows - 1) / rows : (h->dim >= 2 ? (g.ny + sv.by - 1) / sv.by : 1);
     for (int y = 0; y < ty; ++y)
       for (int x = 0; x < tx; ++x) work.push_back(WorkItem{s, x, y});
   }
@@ -91,8 +125,8 @@ jf_status setup_variant(jf_ctx* h, int v) {
   e = cudaMemcpy(h->d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch: work list");
   h->nwork = (int)work.size();
-  const long long cap = (long long)h->sms * per_sm;
   h->batch_blocks = (int)(h->nwork < cap ? h->nwork : cap);
+  h->batch_rows = rows;
   h->variant = v;
   h->table_index = list[v];
   return JF_OK;
@@ -206,6 +240,7 @@ cudaError_t launch_batch_stage(jf_ctx* h, const StageVariant<T>& sv, const SimDe
     for (int i = 0; i < h->nsim; ++i) {
       StageArgs<T> A{};
       batch_stage_args(host_sims[i], code, A);
+      if (sv.ymarch) A.zchunk = h->batch_rows;
       A.flag = h->flag;
 #ifdef JF_DEBUG_BOUNDS
       A.trace = debug_trace_dev();
@@ -216,7 +251,7 @@ cudaError_t launch_batch_stage(jf_ctx* h, const StageVariant<T>& sv, const SimDe
     return cudaSuccess;
   } else {
     return sv.launch_batch(dev_sims, static_cast<const WorkItem*>(h->d_work), h->nwork, code, g, h->flag,
-                           h->batch_blocks, s);
+                           h->batch_blocks, h->batch_rows, s);
   }
 }
 
@@ -375,19 +410,24 @@ int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   const bool visc = dissipative(h->gas, h->scheme);
   std::vector<int> list;
   int bx = 0, by = 0;
+  bool ymarch = false;
+  auto get = [&](const auto* tab) {
+    if (variant >= 0 && variant < (int)list.size()) {
+      bx = tab[list[variant]].bx;
+      by = tab[list[variant]].by;
+      ymarch = tab[list[variant]].ymarch;
+    }
+  };
+  int c = 0;
   if (h->scheme.dtype == JF_F32) {
     list = batch_variant_list<float>(h->dim, visc, scheme_kind(h));
-    int c = 0;
-    const StageVariant<float>* tab = stage_variants<float>(&c);
-    if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
+    get(stage_variants<float>(&c));
   } else {
     list = batch_variant_list<double>(h->dim, visc, scheme_kind(h));
-    int c = 0;
-    const StageVariant<double>* tab = stage_variants<double>(&c);
-    if (variant >= 0 && variant < (int)list.size()) { bx = tab[list[variant]].bx; by = tab[list[variant]].by; }
+    get(stage_variants<double>(&c));
   }
   if (variant >= 0 && variant < (int)list.size() && buf && len > 0)
-    std::snprintf(buf, (size_t)len, "tile=%dx%d persistent", bx, by);
+    std::snprintf(buf, (size_t)len, ymarch ? "tile=%dx%d ymarch persistent" : "tile=%dx%d persistent", bx, by);
   return (int)list.size();
 }
 

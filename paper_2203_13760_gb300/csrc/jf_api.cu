@@ -190,11 +190,14 @@ int zchunk_rule(long long nx, long long ny, long long nz, int bx, int by, int ct
   return (int)z;
 }
 
-int auto_zchunk(const jf_ctx* h, int bx, int by, int ctas_per_sm) {
-  const long long key = ((long long)bx * 4096 + by) * 64 + ctas_per_sm;
+// ymarch: a 2D grid whose row tiles march along y (chunks of rows).
+int auto_zchunk(const jf_ctx* h, int bx, int by, int ctas_per_sm, bool ymarch) {
+  const long long key = (((long long)bx * 4096 + by) * 64 + ctas_per_sm) * 2 + (ymarch ? 1 : 0);
   auto it = h->zauto.find(key);
   if (it != h->zauto.end()) return it->second;
-  const int z = zchunk_rule(h->grid.nx, h->grid.ny, h->grid.nz, bx, by, ctas_per_sm > 0 ? ctas_per_sm : 1, h->sms);
+  const int cps = ctas_per_sm > 0 ? ctas_per_sm : 1;
+  const int z = ymarch ? zchunk_rule(h->grid.nx, 1, h->grid.ny, bx, 1, cps, h->sms)
+                       : zchunk_rule(h->grid.nx, h->grid.ny, h->grid.nz, bx, by, cps, h->sms);
   h->zauto[key] = z;
   return z;
 }
@@ -228,7 +231,7 @@ std::vector<std::pair<int, int>> variant_list(int dim, bool visc, int kind) {
   std::vector<std::pair<int, int>> out;
   for (int i = 0; i < count; ++i) {
     if (tab[i].dim != dim || tab[i].visc != visc || tab[i].scheme != kind) continue;
-    if (dim == 3)
+    if (dim == 3 || tab[i].ymarch)
       for (int z : kZChunks) out.emplace_back(i, z);
     else
       out.emplace_back(i, 1);
@@ -236,12 +239,34 @@ std::vector<std::pair<int, int>> variant_list(int dim, bool visc, int kind) {
   return out;
 }
 
+bool rows_preferred(const jf_grid* grids, int n, int rows_bx, int tile_bx, int tile_by) {
+  double rows = 0.0, tiles = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double nx = grids[i].nx, ny = grids[i].ny;
+    rows += std::ceil(nx / rows_bx) * rows_bx * ny;
+    tiles += std::ceil(nx / tile_bx) * tile_bx * std::ceil(ny / tile_by) * tile_by;
+  }
+  return rows <= 1.08 * tiles;
+}
+
 template <typename T>
 jf_status select_variant(jf_ctx* h, int v, bool prepare) {
   const bool visc = dissipative(h->gas, h->scheme);
   auto list = variant_list<T>(h->dim, visc, scheme_kind(h));
   if (list.empty()) { set_error(h, "no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
-  if (v < 0) v = 0;
+  if (v < 0) {
+    v = 0;
+    if constexpr (sizeof(T) == 4) {  // FP32 2D: the row tiles (automatic chunk) where rows_preferred says so
+      int count = 0;
+      const StageVariant<T>* tab = stage_variants<T>(&count);
+      for (int i = 0; i < (int)list.size(); ++i)
+        if (tab[list[i].first].ymarch && list[i].second == 0) {
+          const StageVariant<T>& t0 = tab[list[0].first];
+          if (rows_preferred(&h->grid, 1, tab[list[i].first].bx, t0.bx, t0.by)) v = i;
+          break;
+        }
+    }
+  }
   if (v >= (int)list.size()) { set_error(h, "variant index out of range"); return JF_ERR_ARG; }
   if (prepare) {
     int count = 0;
@@ -264,12 +289,14 @@ int describe_variant(jf_ctx* h, int v, char* buf, int len) {
   const StageVariant<T>* tab = stage_variants<T>(&count);
   const StageVariant<T>& s = tab[list[v].first];
   if (buf && len > 0) {
-    const int z = s.dim == 3 ? list[v].second : 1;
+    const int z = s.dim == 3 || s.ymarch ? list[v].second : 1;
+    const char* march = s.ymarch ? " ymarch" : "";
     if (z == 0)
-      std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=auto(%d) smem=%zu ctas/sm=%d", s.bx, s.by,
-                    auto_zchunk(h, s.bx, s.by, s.minb), s.smem, s.minb);
+      std::snprintf(buf, (size_t)len, "tile=%dx%d%s zchunk=auto(%d) smem=%zu ctas/sm=%d", s.bx, s.by, march,
+                    auto_zchunk(h, s.bx, s.by, s.minb, s.ymarch), s.smem, s.minb);
     else
-      std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=%d smem=%zu ctas/sm=%d", s.bx, s.by, z, s.smem, s.minb);
+      std::snprintf(buf, (size_t)len, "tile=%dx%d%s zchunk=%d smem=%zu ctas/sm=%d", s.bx, s.by, march, z, s.smem,
+                    s.minb);
   }
   return (int)list.size();
 }
@@ -292,7 +319,7 @@ StageArgs<T> base_args(const jf_ctx* h) {
   if (A.zchunk <= 0) {
     int count = 0;
     const StageVariant<T>& v = stage_variants<T>(&count)[h->table_index];
-    A.zchunk = auto_zchunk(h, v.bx, v.by, v.minb);
+    A.zchunk = auto_zchunk(h, v.bx, v.by, v.minb, v.ymarch);
   }
   A.flag = h->flag;
   return A;

@@ -38,6 +38,22 @@ namespace jf {
 
 constexpr int HALO = 3;
 
+// Kernel dimensionality (template parameter DIM).  1, 2 and 3 are the grid's
+// active axes: the tile spans x (1D: one row of BX cells; 2D, 3D: BX x BY
+// cells) and, in 3D, marches along z.  DIM_Y2 is a 2D grid whose tile is one
+// row of BX cells marching along y: the kernel runs it as the x axis plus a
+// marched third axis (its rows as the planes of the march), with the roles of
+// y and z, and of the v and w components, exchanged where the state is loaded
+// and stored (launch_stage and the batch path remap the grid arguments).
+constexpr int DIM_Y2 = 4;
+constexpr int plane_dims(int dim) { return dim == 2 || dim == 3 ? 2 : 1; }  // axes spanned by a tile
+constexpr bool marches(int dim) { return dim == 3 || dim == DIM_Y2; }      // z-march over planes
+constexpr bool axis_on(int dim, int a) {                                   // axis a of the kernel active
+  return a == 0 || (a == 1 && plane_dims(dim) == 2) || (a == 2 && marches(dim));
+}
+// Global component of the kernel's component c (DIM_Y2: v and w exchanged).
+constexpr int gcomp(int dim, int c) { return dim == DIM_Y2 && (c == 2 || c == 3) ? 5 - c : c; }
+
 // Bounds-checked debug build (-DJF_DEBUG_BOUNDS): every global and
 // shared-memory index of the stage kernels is checked before the access; a
 // bad one is printed (at most 32 lines per translation unit) and the access
@@ -117,19 +133,19 @@ __device__ __forceinline__ int map_index_bc(int i, int n, int periodic, int wall
 // Shared-memory plane geometry.
 template <int BX, int BY, int DIM, bool VISC>
 struct Geo {
-  static constexpr int HY = DIM >= 2 ? HALO : 0;
+  static constexpr int HY = plane_dims(DIM) == 2 ? HALO : 0;
   static constexpr int PX = BX + 2 * HALO;           // row pitch
   static constexpr int PY = BY + 2 * HY;
   static constexpr int CS = PX * PY;                 // component stride
   static constexpr int NC = VISC ? 6 : 5;            // rho, u, v, w, p (, T)
   static constexpr int PLANE = NC * CS;
-  static constexpr int RING = DIM == 3 ? 6 : 1;      // planes held
+  static constexpr int RING = marches(DIM) ? 6 : 1;  // planes held
   static constexpr int NFX = (BX + 1) * BY;          // x faces per plane
-  static constexpr int NFY = DIM >= 2 ? BX * (BY + 1) : 0;
+  static constexpr int NFY = plane_dims(DIM) == 2 ? BX * (BY + 1) : 0;
   static constexpr int NCELL = BX * BY;              // cell threads
-  static constexpr int NT = DIM >= 2 ? BX * (BY + 1) : BX + 32;  // threads
-  static_assert(DIM == 1 || BX == 32, "2D/3D tiles are one warp wide");
-  static_assert(DIM != 1 || BY == 1, "1D tiles are one row");
+  static constexpr int NT = plane_dims(DIM) == 2 ? BX * (BY + 1) : BX + 32;  // threads
+  static_assert(plane_dims(DIM) == 1 || BX == 32, "2D/3D tiles are one warp wide");
+  static_assert(plane_dims(DIM) == 2 || BY == 1, "row tiles are one row");
 };
 
 // Plane loads are split into a fetch (global loads of the conservative state
@@ -153,7 +169,7 @@ __device__ __forceinline__ void fetch_plane(const StageArgs<T>& A, PlaneRegs<T, 
   using G = Geo<BX, BY, DIM, VISC>;
   bool fz = false;
   int kz = 0;
-  if (DIM == 3) kz = WALLS ? map_index_bc(gz, A.nz, A.periodic[2], A.wall[2], fz) : map_index(gz, A.nz, A.periodic[2]);
+  if (marches(DIM)) kz = WALLS ? map_index_bc(gz, A.nz, A.periodic[2], A.wall[2], fz) : map_index(gz, A.nz, A.periodic[2]);
   const long long zoff = (long long)kz * A.ny;
 #pragma unroll
   for (int i = 0; i < PlaneRegs<T, BX, BY, DIM, VISC>::PF; ++i) {
@@ -165,17 +181,17 @@ __device__ __forceinline__ void fetch_plane(const StageArgs<T>& A, PlaneRegs<T, 
       int gx, gy = 0;
       if (WALLS) {
         gx = map_index_bc(gx0 + lx - HALO, A.nx, A.periodic[0], A.wall[0], fx);
-        if (DIM >= 2) gy = map_index_bc(gy0 + ly - G::HY, A.ny, A.periodic[1], A.wall[1], fy);
+        if (plane_dims(DIM) == 2) gy = map_index_bc(gy0 + ly - G::HY, A.ny, A.periodic[1], A.wall[1], fy);
       } else {
         gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
-        if (DIM >= 2) gy = map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]);
+        if (plane_dims(DIM) == 2) gy = map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]);
       }
       const long long q = (zoff + gy) * A.nx + gx;
 #pragma unroll
       for (int c = 0; c < 5; ++c)
         r.v[i][c] = JF_CHECK(q >= 0 && q < A.N, "JFDBG fetch q=%lld N=%lld gx=%d gy=%d kz=%d tile=(%d,%d) t=%d\n", q,
                              A.N, gx, gy, kz, gx0, gy0, t)
-                        ? __ldg(A.Us + q + c * A.N)
+                        ? __ldg(A.Us + q + gcomp(DIM, c) * A.N)
                         : T(1);
       if (WALLS) {
         if (fx) r.v[i][1] = -r.v[i][1];
@@ -204,7 +220,7 @@ __device__ __forceinline__ void plane_map(const StageArgs<T>& A, PlaneMap<T, BX,
     const int t = threadIdx.x + i * G::NT;
     const int ly = t / G::PX, lx = t - ly * G::PX;
     const int gx = map_index(gx0 + lx - HALO, A.nx, A.periodic[0]);
-    const int gy = DIM >= 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
+    const int gy = plane_dims(DIM) == 2 ? map_index(gy0 + ly - G::HY, A.ny, A.periodic[1]) : 0;
     m.off[i] = t < G::CS ? gy * A.nx + gx : 0;
   }
 }
@@ -213,7 +229,7 @@ template <typename T, int BX, int BY, int DIM, bool VISC>
 __device__ __forceinline__ void fetch_plane_mapped(const StageArgs<T>& A, PlaneRegs<T, BX, BY, DIM, VISC>& r,
                                                    const PlaneMap<T, BX, BY, DIM, VISC>& m, int gz) {
   using G = Geo<BX, BY, DIM, VISC>;
-  const int kz = DIM == 3 ? map_index(gz, A.nz, A.periodic[2]) : 0;
+  const int kz = marches(DIM) ? map_index(gz, A.nz, A.periodic[2]) : 0;
   const long long zoff = (long long)kz * A.ny * A.nx;
 #pragma unroll
   for (int i = 0; i < PlaneRegs<T, BX, BY, DIM, VISC>::PF; ++i) {
@@ -223,7 +239,7 @@ __device__ __forceinline__ void fetch_plane_mapped(const StageArgs<T>& A, PlaneR
 #pragma unroll
       for (int c = 0; c < 5; ++c)
         r.v[i][c] = JF_CHECK(q >= 0 && q < A.N, "JFDBG fetch q=%lld N=%lld t=%d\n", q, A.N, t)
-                        ? __ldg(A.Us + q + c * A.N)
+                        ? __ldg(A.Us + q + gcomp(DIM, c) * A.N)
                         : T(1);
     }
   }
@@ -521,8 +537,8 @@ __device__ __forceinline__ void face_visc_add(const RingView<T, BX, BY, DIM, VIS
       G[D][e] = Ge.x;
       G[e][e] = Ge.y;
     };
-    if constexpr (Ro::T1 < DIM) tang(std::integral_constant<int, 1>{});
-    if constexpr (Ro::T2 < DIM) tang(std::integral_constant<int, 2>{});
+    if constexpr (axis_on(DIM, Ro::T1)) tang(std::integral_constant<int, 1>{});
+    if constexpr (axis_on(DIM, Ro::T2)) tang(std::integral_constant<int, 2>{});
   } else {
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -530,7 +546,7 @@ __device__ __forceinline__ void face_visc_add(const RingView<T, BX, BY, DIM, VIS
   dTdn = df4(val(5, -1, 0, 0), val(5, 0, 0, 0), val(5, 1, 0, 0), val(5, 2, 0, 0)) * hn;
   // tangential derivatives: cell-centre C4 at cells -1..2 along the normal,
   // then fourth-order interpolation to the face
-  if (Ro::T1 < DIM) {
+  if (axis_on(DIM, Ro::T1)) {
     constexpr int e = Ro::T1;
     const T he = inv_h[e];
 #pragma unroll
@@ -544,7 +560,7 @@ __device__ __forceinline__ void face_visc_add(const RingView<T, BX, BY, DIM, VIS
       G[a][e] = rc4(cen[0], cen[1], cen[2], cen[3]) * he;
     }
   }
-  if (Ro::T2 < DIM) {
+  if (axis_on(DIM, Ro::T2)) {
     constexpr int e = Ro::T2;
     const T he = inv_h[e];
 #pragma unroll
@@ -693,17 +709,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
 
   // this thread's x face (-1: none) and y face, as (column, row) in the tile
   int xf_x = -1, xf_y = 0;
-  if (DIM == 1) {
+  if (plane_dims(DIM) == 1) {
     if (threadIdx.x <= BX) { xf_x = threadIdx.x; xf_y = 0; }
   } else if (warp < BY) {
     xf_x = lane; xf_y = warp;
   } else if (lane < BY) {
     xf_x = BX; xf_y = lane;
   }
-  const int yf_x = lane, yf_y = warp;  // DIM >= 2: NT == BX * (BY + 1) y faces
+  const int yf_x = lane, yf_y = warp;  // tiles spanning y: NT == BX * (BY + 1) y faces
 
   int z0 = 0, z1 = 1;
-  if (DIM == 3) {
+  if (marches(DIM)) {
     z0 = bz * A.zchunk;
     z1 = min(z0 + A.zchunk, A.nz);
   }
@@ -719,7 +735,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       int s = b + e;
       s = s >= G::RING ? s - G::RING : s;
       s = s >= G::RING ? s - G::RING : s;
-      R.plane[e] = (DIM == 3 ? s : 0) * G::PLANE;
+      R.plane[e] = (marches(DIM) ? s : 0) * G::PLANE;
     }
   };
 
@@ -727,13 +743,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   // face values of a plane kept in shared memory (x, y; along z only the
   // current cell's value at its upper face, zl, is kept, by its column)
   constexpr bool PC = SCH == SCH_DEFAULT;
-  constexpr int SX = BY * (BX + 2), SY = (BY + 2) * BX;
+  constexpr int SX = BY * (BX + 2), SY = plane_dims(DIM) == 2 ? (BY + 2) * BX : 0;
   T* EX = Fy + 5 * G::NFY;  // [2][5][BY][BX+2] (PC only)
-  T* EY = EX + 2 * 5 * SX;  // [2][5][BY+2][BX] (PC, DIM >= 2)
+  T* EY = EX + 2 * 5 * SX;  // [2][5][BY+2][BX] (PC, tiles spanning y)
   // default scheme, 3D: the net fluxes of a column's z faces in shared
   // memory, [2][5][NCELL] (face k + 1/2 in slot k & 1), written and read by
   // the column's own thread, so that they hold no registers across the phases
-  constexpr bool ZS = PC && DIM == 3;
+  constexpr bool ZS = PC && marches(DIM);
   T* ZF = EY + 2 * 5 * SY;
   auto zf = [&](int k, int c) -> T& { return ZF[((k & 1) * 5 + c) * G::NCELL + threadIdx.x]; };
   // and the WENO5 value of the column's cell k at k + 1/2 (the left state of
@@ -743,8 +759,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   ZTangents ztan;  // FP32 z faces: the tangential stencils of the planes k .. k + 2
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight while plane k is computed
   PlaneMap<T, BX, BY, DIM, VISC> pmap;    // default scheme (no walls): the in-plane offsets of its cells
-  if constexpr (PC && DIM == 3) plane_map<T, BX, BY, DIM, VISC>(A, pmap, gx0, gy0);
-  if (DIM == 3) {
+  if constexpr (PC && marches(DIM)) plane_map<T, BX, BY, DIM, VISC>(A, pmap, gx0, gy0);
+  if (marches(DIM)) {
 #pragma unroll 1
     for (int q = 0; q < 6; ++q) load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring + q * G::PLANE, gx0, gy0, z0 - 3 + q);
     __syncthreads();
@@ -789,20 +805,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     // face computations so that their latency overlaps with them (default
     // scheme in 3D: after the x face, which keeps their registers free during
     // the reconstruction phase and the x face; the 3D march holds more state)
-    const long long qc = ((long long)(DIM == 3 ? k : 0) * A.ny + gy) * A.nx + gx;
+    const long long qc = ((long long)(marches(DIM) ? k : 0) * A.ny + gy) * A.nx + gx;
     T us[5], un[5];
     auto load_cell = [&]() {
       if (own && !A.rhs_only) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           const bool ok = JF_CHECK(qc >= 0 && qc < A.N, "JFDBG cell qc=%lld N=%lld\n", qc, A.N);
-          us[c] = ok ? __ldg(A.Us + qc + c * A.N) : T(1);
-          un[c] = A.Un && ok ? A.Un[qc + c * A.N] : T(0);
+          us[c] = ok ? __ldg(A.Us + qc + gcomp(DIM, c) * A.N) : T(1);
+          un[c] = A.Un && ok ? A.Un[qc + gcomp(DIM, c) * A.N] : T(0);
         }
       }
     };
     // (default scheme in 3D: after the x face below)
-    if constexpr (SCH != SCH_DEFAULT || DIM < 3) load_cell();
+    if constexpr (SCH != SCH_DEFAULT || DIM != 3) load_cell();
 
     T NFz_hi[5];
     if constexpr (PC) {
@@ -832,7 +848,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           }
         }
       };
-      if (DIM == 1) {
+      if (plane_dims(DIM) == 1) {
         if (threadIdx.x < BX + 2) put_x(0, (int)threadIdx.x - 1);
       } else if constexpr (sizeof(T) == 4) {
         // the same cells as below; the w components of a thread's x cell and
@@ -892,7 +908,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
 #pragma unroll 1
         for (int q = 0; q < nyrows; ++q) put_y(yrow0 + q, lane);
       }
-      if (DIM == 3 && cell_thread) {
+      if (marches(DIM) && cell_thread) {
         // face k + 1/2: the stored value of cell k (zl) and the lower value of cell k + 1
         T r[5], l[5], F[5], NF[5], zl0[5];
         cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, r, l);
@@ -915,7 +931,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       // plane k + 4 in flight during the faces and the update (committed at
       // the end of this plane); its registers are free during the
       // reconstruction phase
-      if (DIM == 3 && k + 1 < z1) fetch_plane_mapped<T, BX, BY, DIM, VISC>(A, next, pmap, k + 4);
+      if (marches(DIM) && k + 1 < z1) fetch_plane_mapped<T, BX, BY, DIM, VISC>(A, next, pmap, k + 4);
       // phase 2: the x and y faces from the stored values
       if (xf_x >= 0) {
         T Wm[5], Wp[5], F[5], NF[5];
@@ -935,7 +951,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           if (JF_CHECK(t >= 0 && t < G::NFX, "JFDBG Fx t=%d\n", t)) Fx[c * G::NFX + t] = NF[c];
       }
       if constexpr (DIM == 3) load_cell();
-      if (DIM >= 2) {
+      if (plane_dims(DIM) == 2) {
         T Wm[5], Wp[5], F[5], NF[5];
         const int i = yf_y * BX + yf_x;  // lower cell row yf_y - 1
 #pragma unroll
@@ -961,7 +977,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       for (int c = 0; c < 5; ++c)
         if (JF_CHECK(t >= 0 && t < G::NFX, "JFDBG Fx t=%d\n", t)) Fx[c * G::NFX + t] = NF[c];
     }
-    if (DIM >= 2) {
+    if (plane_dims(DIM) == 2) {
       T NF[5];
       face_flux<T, 1, BX, BY, DIM, VISC, SCH>(R, HALO + yf_x, G::HY + yf_y - 1, g, inv_h, NF);
       const int t = yf_y * BX + yf_x;
@@ -969,11 +985,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       for (int c = 0; c < 5; ++c)
         if (JF_CHECK(t >= 0 && t < G::NFY, "JFDBG Fy t=%d\n", t)) Fy[c * G::NFY + t] = NF[c];
     }
-    if (DIM == 3 && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
+    if (marches(DIM) && cell_thread) face_flux<T, 2, BX, BY, DIM, VISC, SCH>(R, HALO + tx, G::HY + ty, g, inv_h, NFz_hi);
     }
     __syncthreads();
 
-    if constexpr (sizeof(T) == 4 && (ZS || DIM < 3)) {
+    if constexpr (sizeof(T) == 4 && (ZS || !marches(DIM))) {
       // FP32: the components (0, 1) and (2, 3) in the lanes of packed
       // operations (per lane the operations of the scalar form below), 4 alone
       if (own) {
@@ -985,7 +1001,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           float2 lo = pr([&](int cc) { return Fx[cc * G::NFX + fx]; });
           float2 hi = pr([&](int cc) { return Fx[cc * G::NFX + fx + 1]; });
           float2 rhs = __fmul2_rn(__ffma2_rn(m1, lo, hi), c2(inv_h[0]));
-          if constexpr (DIM >= 2) {
+          if constexpr (plane_dims(DIM) == 2) {
             lo = pr([&](int cc) { return Fy[cc * G::NFY + fy]; });
             hi = pr([&](int cc) { return Fy[cc * G::NFY + fy + BX]; });
             rhs = __ffma2_rn(__ffma2_rn(m1, lo, hi), c2(inv_h[1]), rhs);
@@ -1001,8 +1017,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
             if (A.Un) o = __ffma2_rn(c2(A.a), pr([&](int cc) { return un[cc]; }), o);
           }
           if (JF_CHECK(qc >= 0 && qc < A.N, "JFDBG store qc=%lld N=%lld\n", qc, A.N)) {
-            A.out[qc + c * A.N] = o.x;
-            if (two) A.out[qc + (c + 1) * A.N] = o.y;
+            A.out[qc + gcomp(DIM, c) * A.N] = o.x;
+            if (two) A.out[qc + gcomp(DIM, c + 1) * A.N] = o.y;
           }
         };
         comb(0, true);
@@ -1014,12 +1030,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       for (int c = 0; c < 5; ++c) {
         const int fx = ty * (BX + 1) + tx;
         T rhs = (Fx[c * G::NFX + fx + 1] - Fx[c * G::NFX + fx]) * inv_h[0];
-        if (DIM >= 2) {
+        if (plane_dims(DIM) == 2) {
           const int fy = ty * BX + tx;
           rhs += (Fy[c * G::NFY + fy + BX] - Fy[c * G::NFY + fy]) * inv_h[1];
         }
         if constexpr (ZS) rhs += (zf(k, c) - zf(k + 1, c)) * inv_h[2];  // faces k + 1/2 and k - 1/2
-        else if (DIM == 3) rhs += (NFz_hi[c] - NFz_lo[c]) * inv_h[2];
+        else if (marches(DIM)) rhs += (NFz_hi[c] - NFz_lo[c]) * inv_h[2];
         T o;
         if (A.rhs_only) {
           o = rhs;
@@ -1027,10 +1043,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
           o = A.b * (us[c] + dt * rhs);
           if (A.Un) o += A.a * un[c];
         }
-        if (JF_CHECK(qc >= 0 && qc < A.N, "JFDBG store qc=%lld N=%lld\n", qc, A.N)) A.out[qc + c * A.N] = o;
+        if (JF_CHECK(qc >= 0 && qc < A.N, "JFDBG store qc=%lld N=%lld\n", qc, A.N)) A.out[qc + gcomp(DIM, c) * A.N] = o;
       }
     }
-    if (DIM == 3) {
+    if (marches(DIM)) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) NFz_lo[c] = NFz_hi[c];  // (other schemes)
       const int nb = base + 1 == 6 ? 0 : base + 1;  // slot of plane k - 2, dead after this plane's faces
@@ -1097,6 +1113,20 @@ __host__ __device__ __forceinline__ void batch_stage_args(const SimDesc<T>& d, i
   }
 }
 
+// DIM_Y2 launches: a 2D grid's arguments in the kernel's frame, its rows as
+// the planes of the march (ny' = 1, nz' = ny; the y boundary condition and
+// spacing move to the third axis; the kernel's y axis is inactive).
+template <typename T>
+__host__ __device__ __forceinline__ void rows_as_planes(StageArgs<T>& A) {
+  A.nz = A.ny;
+  A.ny = 1;
+  A.periodic[2] = A.periodic[1];
+  A.wall[2] = A.wall[1];
+  A.inv_h[2] = A.inv_h[1];
+  A.periodic[1] = 0;
+  A.wall[1] = 0;
+}
+
 // Shared-memory elements of a tile: the plane ring and the face buffers.
 template <typename T, int DIM, bool VISC, int BX, int BY>
 constexpr size_t stage_smem_elems() {
@@ -1111,7 +1141,8 @@ constexpr size_t stage_smem_elems() {
 // the columns' current cells [5][NCELL].
 template <int DIM, int BX, int BY>
 constexpr size_t recon_smem_elems() {
-  return (size_t)2 * 5 * (BY * (BX + 2) + (DIM >= 2 ? (BY + 2) * BX : 0)) + (DIM == 3 ? 3 * 5 * BX * BY : 0);
+  return (size_t)2 * 5 * (BY * (BX + 2) + (plane_dims(DIM) == 2 ? (BY + 2) * BX : 0)) +
+         (marches(DIM) ? 3 * 5 * BX * BY : 0);
 }
 
 // Element offset of the Rusanov-NN parameters in the dynamic shared memory:
@@ -1131,7 +1162,8 @@ constexpr size_t nn_smem_offset() {
 //    equal cost); the grid arguments come from the simulation's descriptor,
 //    stage 1: U1 = U + dt L(U); stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1));
 //    stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2)); stage 4 (TVD-RK2):
-//    U = 1/2 U + 1/2 (U1 + dt L(U1)).
+//    U = 1/2 U + 1/2 (U1 + dt L(U1)).  DIM_Y2: an item is a tile column
+//    and a chunk of A0.zchunk rows.
 // Both forms reach the tile computation through the same call below, so a
 // simulation advanced in a batch is bitwise the one advanced alone.
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
@@ -1177,8 +1209,15 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
       const SimDesc<T> d = sims[w.sim];
       batch_stage_args(d, stage, A);
       bx = w.bx;
-      by = w.by;
-      bz = 0;
+      if constexpr (DIM == DIM_Y2) {  // w.by: the chunk of rows (planes) of A0.zchunk rows
+        rows_as_planes(A);
+        A.zchunk = A0.zchunk;
+        by = 0;
+        bz = w.by;
+      } else {
+        by = w.by;
+        bz = 0;
+      }
 #ifdef JF_DEBUG_BOUNDS
       if (threadIdx.x == 0)
         jf_trace(d.trace, 0x100 + stage, ((unsigned long long)item << 32) | (unsigned)w.sim,

@@ -53,6 +53,8 @@ const StageVariant<float>* stage_variants<float>(int* count) {
     v.insert(v.end(), nn, nn + ng);
     const StageVariant<float>* ext = ext_variants_f32(&ng);
     v.insert(v.end(), ext, ext + ng);
+    const StageVariant<float>* rows = rows_variants_f32(&ng);
+    v.insert(v.end(), rows, rows + ng);
     return v;
   }();
   *count = (int)table.size();

@@ -35,6 +35,8 @@ const StageVariant<double>* stage_variants<double>(int* count) {
     v.insert(v.end(), nn, nn + ng);
     const StageVariant<double>* ext = ext_variants_f64(&ng);
     v.insert(v.end(), ext, ext + ng);
+    const StageVariant<double>* rows = rows_variants_f64(&ng);
+    v.insert(v.end(), rows, rows + ng);
     return v;
   }();
   *count = (int)table.size();

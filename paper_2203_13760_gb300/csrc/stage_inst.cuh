@@ -22,11 +22,14 @@ cudaError_t prepare_stage() {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// A.zchunk: planes per CTA of a z-march (DIM_Y2: rows of the 2D grid).
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
-cudaError_t launch_stage(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s) {
+cudaError_t launch_stage(const StageArgs<T>& A0, const Gas<T>& g, cudaStream_t s) {
   const size_t smem = launch_smem<T, DIM, VISC, BX, BY, SCH>();
-  const dim3 grid((A.nx + BX - 1) / BX, DIM >= 2 ? (A.ny + BY - 1) / BY : 1,
-                  DIM == 3 ? (A.nz + A.zchunk - 1) / A.zchunk : 1);
+  StageArgs<T> A = A0;
+  if constexpr (DIM == DIM_Y2) rows_as_planes(A);
+  const dim3 grid((A.nx + BX - 1) / BX, plane_dims(DIM) == 2 ? (A.ny + BY - 1) / BY : 1,
+                  marches(DIM) ? (A.nz + A.zchunk - 1) / A.zchunk : 1);
   stage_kernel<T, DIM, VISC, BX, BY, MINB, SCH><<<grid, Geo<BX, BY, DIM, VISC>::NT, smem, s>>>(A, nullptr, nullptr, 0, 0,
                                                                                           g);
   return cudaGetLastError();
@@ -42,12 +45,14 @@ cudaError_t prepare_batch(int* blocks_per_sm) {
                                                        launch_smem<T, DIM, VISC, BX, BY, SCH>());
 }
 
+// rows: DIM_Y2, the rows of a work item's chunk (other kernels ignore it).
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t launch_batch(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
-                         int* flag, int grid, cudaStream_t s) {
+                         int* flag, int grid, int rows, cudaStream_t s) {
   const size_t smem = launch_smem<T, DIM, VISC, BX, BY, SCH>();
   StageArgs<T> A{};
   A.flag = flag;
+  A.zchunk = rows;
 #ifdef JF_DEBUG_BOUNDS
   A.trace = debug_trace_dev();
 #endif
@@ -58,10 +63,10 @@ cudaError_t launch_batch(const SimDesc<T>* sims, const WorkItem* work, int nwork
 
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 StageVariant<T> make_variant() {
-  StageVariant<T> v{DIM, VISC, BX, BY, launch_smem<T, DIM, VISC, BX, BY, SCH>(),
+  StageVariant<T> v{DIM == DIM_Y2 ? 2 : DIM, VISC, BX, BY, launch_smem<T, DIM, VISC, BX, BY, SCH>(),
                     &prepare_stage<T, DIM, VISC, BX, BY, MINB, SCH>, &launch_stage<T, DIM, VISC, BX, BY, MINB, SCH>,
-                    nullptr, nullptr, Geo<BX, BY, DIM, VISC>::NT, SCH, MINB};
-  if constexpr (DIM <= 2) {  // batches are built for 1D and 2D grids
+                    nullptr, nullptr, Geo<BX, BY, DIM, VISC>::NT, SCH, MINB, DIM == DIM_Y2};
+  if constexpr (DIM != 3) {  // batches are built for 1D and 2D grids
     v.prepare_batch = &prepare_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
     v.launch_batch = &launch_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
   }

@@ -23,10 +23,11 @@ struct StageVariant {
   // persistent batched launch over a work list (same tile code; 2D / 1D only, else null)
   cudaError_t (*prepare_batch)(int* blocks_per_sm);
   cudaError_t (*launch_batch)(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
-                              int* flag, int grid, cudaStream_t s);
+                              int* flag, int grid, int rows, cudaStream_t s);
   int threads;
   int scheme;    // SCH_DEFAULT, SCH_GENERAL (run-time Table 2 choice), SCH_ROE, SCH_NN or an _EXT form
   int minb;      // CTAs per SM the register allocation was bounded for
+  bool ymarch;   // 2D grid, one row of BX cells per tile marching along y (kernel DIM_Y2)
 };
 
 // All compiled variants for precision T (defined in stage_f32.cu / stage_f64.cu).
@@ -46,5 +47,9 @@ const StageVariant<float>* nn_variants_f32(int* count);
 const StageVariant<double>* nn_variants_f64(int* count);
 const StageVariant<float>* ext_variants_f32(int* count);
 const StageVariant<double>* ext_variants_f64(int* count);
+// The default-scheme kernels of 2D grids in row tiles marching along y
+// (DIM_Y2; stage_*_rows.cu).
+const StageVariant<float>* rows_variants_f32(int* count);
+const StageVariant<double>* rows_variants_f64(int* count);
 
 }  // namespace jf

@@ -278,9 +278,11 @@ jf_status recompute_batch(jf_ctx* h, const StageVariant<T>& sv, const Gas<T>& g,
     if (e == cudaSuccess) e = cudaEventRecord(h->vjp_desc_done, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "batch adjoint: descriptor upload");
     const SimDesc<T>* dev = static_cast<const SimDesc<T>*>(h->vjp_desc_dev);
-    e = sv.launch_batch(dev, static_cast<const WorkItem*>(h->d_work), h->nwork, 1, g, h->flag, h->batch_blocks, s);
+    e = sv.launch_batch(dev, static_cast<const WorkItem*>(h->d_work), h->nwork, 1, g, h->flag, h->batch_blocks,
+                        h->batch_rows, s);
     if (e == cudaSuccess && integ == JF_RK3)
-      e = sv.launch_batch(dev, static_cast<const WorkItem*>(h->d_work), h->nwork, 2, g, h->flag, h->batch_blocks, s);
+      e = sv.launch_batch(dev, static_cast<const WorkItem*>(h->d_work), h->nwork, 2, g, h->flag, h->batch_blocks,
+                          h->batch_rows, s);
     return e == cudaSuccess ? JF_OK : cuda_fail(h, e, "batch adjoint: forward recompute");
   }
 }

@@ -108,18 +108,24 @@ def test_batch_1d_and_viscous():
 
 
 def test_batch_variants_agree():
+    """The 2D tile shapes compute the same bits (one expression per face,
+    compiled per tile shape); the row tiles (ymarch, their own kernel
+    instantiations) agree to FP32 rounding (test_gpu_rows.py)."""
     cases = inputs.four_quadrant_batch(nsim=3, sides=(64,), seed=4)
     b = batch_of(cases, "f32")
     ref = fields(cases, "f32")
     b.step(ref, 3)
-    nv = len(b.variants())
-    for v in range(nv):
+    names = b.variants()
+    for v in range(len(names)):
         b.set_variant(v)
         U = fields(cases, "f32")
         b.step(U, 3)
         b.sync()
         for x, y in zip(ref, U):
-            assert torch.equal(x, y)
+            if "ymarch" in names[v]:
+                assert rel_err(y.cpu().numpy(), x.cpu().numpy()) <= 1e-5, names[v]
+            else:
+                assert torch.equal(x, y), names[v]
 
 
 def test_batch_rejects_mixed_dimensions():
