@@ -61,6 +61,31 @@ std::vector<int> batch_variant_list(int dim, bool visc, int kind) {
   return out;
 }
 
+// Rows per work item of a row-tile (ymarch) batch variant of row width bx
+// over `slots` persistent CTAs: of 64, 32, 16 and 8 rows (the explicit z
+// chunks of the single-grid variants), the one whose static round robin of
+// the items (each costing its rows plus half a row for its prologue) ends
+// first; the longest on ties.
+int row_chunk(const jf_ctx* h, int bx, long long slots) {
+  const long long n = slots < (1LL << 24) ? slots : (1LL << 24);
+  int rows = 64;
+  double best = 0.0;
+  for (int r : {64, 32, 16, 8}) {
+    std::vector<double> load((size_t)n, 0.0);
+    long long item = 0;
+    for (int s = 0; s < h->nsim; ++s) {
+      const jf_grid& g = h->grids[s];
+      const int tx = (g.nx + bx - 1) / bx;
+      for (int y0 = 0; y0 < g.ny; y0 += r)
+        for (int x = 0; x < tx; ++x, ++item) load[item % n] += (g.ny - y0 < r ? g.ny - y0 : r) + 0.5;
+    }
+    double end = 0.0;
+    for (double l : load) end = l > end ? l : end;
+    if (r == 64 || end < best - 1e-9) { best = end; rows = r; }
+  }
+  return rows;
+}
+
 // (Re)build the work list for the tile shape of the selected variant.
 template <typename T>
 jf_status setup_variant(jf_ctx* h, int v) {
@@ -89,27 +114,7 @@ jf_status setup_variant(jf_ctx* h, int v) {
   if (e != cudaSuccess) return cuda_fail(h, e, "batch: kernel set-up");
   if (per_sm < 1) { set_error(h, "batch: kernel does not fit on an SM"); return JF_ERR_UNSUPPORTED; }
   const long long cap = (long long)h->sms * per_sm;
-  const int grid_blocks_max = (int)(cap < (1LL << 30) ? cap : (1LL << 30));
-  // row-march variants: the rows per item whose static round robin over the
-  // persistent CTAs ends first (an item costs its rows plus half a row for
-  // its prologue)
-  int rows = 1;
-  if (sv.ymarch) {
-    double best = 0.0;
-    for (int r : {64, 48, 32, 24, 16}) {
-      std::vector<double> load(grid_blocks_max, 0.0);
-      long long item = 0;
-      for (int s = 0; s < h->nsim; ++s) {
-        const jf_grid& g = h->grids[s];
-        const int tx = (g.nx + sv.bx - 1) / sv.bx;
-        for (int y0 = 0; y0 < g.ny; y0 += r)
-          for (int x = 0; x < tx; ++x, ++item) load[item % grid_blocks_max] += (g.ny - y0 < r ? g.ny - y0 : r) + 0.5;
-      }
-      double end = 0.0;
-      for (double l : load) end = l > end ? l : end;
-      if (r == 64 || end < best - 1e-9) { best = end; rows = r; }
-    }
-  }
+  const int rows = sv.ymarch ? row_chunk(h, sv.bx, cap) : 1;
   std::vector<WorkItem> work;
   for (int s = 0; s < h->nsim; ++s) {
     const jf_grid& g = h->grids[s];
@@ -409,13 +414,17 @@ jf_status batch_set_variant(jf_ctx* h, int variant) {
 int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   const bool visc = dissipative(h->gas, h->scheme);
   std::vector<int> list;
-  int bx = 0, by = 0;
+  int bx = 0, by = 0, rows = 0;
   bool ymarch = false;
   auto get = [&](const auto* tab) {
     if (variant >= 0 && variant < (int)list.size()) {
-      bx = tab[list[variant]].bx;
-      by = tab[list[variant]].by;
-      ymarch = tab[list[variant]].ymarch;
+      const auto& sv = tab[list[variant]];
+      bx = sv.bx;
+      by = sv.by;
+      ymarch = sv.ymarch;
+      int per_sm = 0;
+      if (ymarch && sv.prepare_batch(&per_sm) == cudaSuccess && per_sm > 0)
+        rows = row_chunk(h, bx, (long long)h->sms * per_sm);
     }
   };
   int c = 0;
@@ -426,8 +435,12 @@ int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
     list = batch_variant_list<double>(h->dim, visc, scheme_kind(h));
     get(stage_variants<double>(&c));
   }
-  if (variant >= 0 && variant < (int)list.size() && buf && len > 0)
-    std::snprintf(buf, (size_t)len, ymarch ? "tile=%dx%d ymarch persistent" : "tile=%dx%d persistent", bx, by);
+  if (variant >= 0 && variant < (int)list.size() && buf && len > 0) {
+    if (ymarch)
+      std::snprintf(buf, (size_t)len, "tile=%dx%d ymarch rows=%d persistent", bx, by, rows);
+    else
+      std::snprintf(buf, (size_t)len, "tile=%dx%d persistent", bx, by);
+  }
   return (int)list.size();
 }
 

@@ -147,15 +147,24 @@ def test_autotuner_picks_and_caches(tmp_path):
     b2 = batch_of(cases, "f32")
     assert autotune.apply(b2, path=path) == rec["variant"]
     # the tuned batch still computes the same bits as the single-grid path
+    # with the same tiles (row tiles: the same row width and chunk)
+    import re
+    tuned = b2.variants()[rec["variant"]]
+    m = re.match(r"tile=(\d+)x1 ymarch rows=(\d+) persistent", tuned)
     V = fields(cases, "f32")
     b2.step(V, 2)
     b2.sync()
     for c, U in zip(cases, V):
         s = jf.Solver.from_case(c, dtype="f32")
+        names = s.variants()
+        if m:
+            s.set_variant(names.index(next(d for d in names if d.startswith(f"tile={m[1]}x1 ymarch zchunk={m[2]} "))))
+        else:
+            s.set_variant(names.index(next(d for d in names if d.startswith(tuned.split()[0] + " "))))
         W = fields([c], "f32")[0]
         s.run(W, 2)
         s.sync()
-        assert torch.equal(U, W)
+        assert torch.equal(U, W), (tuned, s.variants())
     case = inputs.taylor_green(48)
     s = jf.Solver.from_case(case, dtype="f32")
     U = torch.tensor(case.U, dtype=torch.float32, device="cuda")
