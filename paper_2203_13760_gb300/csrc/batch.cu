@@ -50,40 +50,24 @@ __global__ void __launch_bounds__(256) batch_copy_pairs_kernel(const T* const* _
 
 namespace {
 
+// Batch variants: (table index, rows per work item) -- the tile kernels
+// once (rows 0), the row-tile (ymarch) kernels with 32, 16 and 64 rows per
+// item (the explicit z chunks of the single-grid variants; 32 measured
+// fastest on the 64 four-quadrant problems: 6.34 G cell-updates/s against
+// 6.18 with 16).
 template <typename T>
-std::vector<int> batch_variant_list(int dim, bool visc, int kind) {
+std::vector<std::pair<int, int>> batch_variant_list(int dim, bool visc, int kind) {
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
-  std::vector<int> out;
+  std::vector<std::pair<int, int>> out;
   for (int i = 0; i < count; ++i)
-    if (tab[i].dim == dim && tab[i].visc == visc && tab[i].scheme == kind && tab[i].launch_batch)
-      out.push_back(i);
-  return out;
-}
-
-// Rows per work item of a row-tile (ymarch) batch variant of row width bx
-// over `slots` persistent CTAs: of 64, 32, 16 and 8 rows (the explicit z
-// chunks of the single-grid variants), the one whose static round robin of
-// the items (each costing its rows plus half a row for its prologue) ends
-// first; the longest on ties.
-int row_chunk(const jf_ctx* h, int bx, long long slots) {
-  const long long n = slots < (1LL << 24) ? slots : (1LL << 24);
-  int rows = 64;
-  double best = 0.0;
-  for (int r : {64, 32, 16, 8}) {
-    std::vector<double> load((size_t)n, 0.0);
-    long long item = 0;
-    for (int s = 0; s < h->nsim; ++s) {
-      const jf_grid& g = h->grids[s];
-      const int tx = (g.nx + bx - 1) / bx;
-      for (int y0 = 0; y0 < g.ny; y0 += r)
-        for (int x = 0; x < tx; ++x, ++item) load[item % n] += (g.ny - y0 < r ? g.ny - y0 : r) + 0.5;
+    if (tab[i].dim == dim && tab[i].visc == visc && tab[i].scheme == kind && tab[i].launch_batch) {
+      if (tab[i].ymarch)
+        for (int r : {32, 16, 64}) out.emplace_back(i, r);
+      else
+        out.emplace_back(i, 0);
     }
-    double end = 0.0;
-    for (double l : load) end = l > end ? l : end;
-    if (r == 64 || end < best - 1e-9) { best = end; rows = r; }
-  }
-  return rows;
+  return out;
 }
 
 // (Re)build the work list for the tile shape of the selected variant.
@@ -92,29 +76,28 @@ jf_status setup_variant(jf_ctx* h, int v) {
   const bool visc = dissipative(h->gas, h->scheme);
   auto list = batch_variant_list<T>(h->dim, visc, scheme_kind(h));
   if (list.empty()) { set_error(h, "batch: no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
-  if (v < 0) {
+  if (v < 0) {  // the first variant, or the first row-tile one where rows_preferred says so
     v = 0;
-    if constexpr (sizeof(T) == 4) {  // FP32 2D: the row tiles where rows_preferred says so
-      int count = 0;
-      const StageVariant<T>* tab = stage_variants<T>(&count);
-      for (int i = 0; i < (int)list.size(); ++i)
-        if (tab[list[i]].ymarch) {
-          const StageVariant<T>& t0 = tab[list[0]];
-          if (rows_preferred(h->grids.data(), h->nsim, tab[list[i]].bx, t0.bx, t0.by)) v = i;
-          break;
-        }
-    }
+    int count = 0;
+    const StageVariant<T>* tab = stage_variants<T>(&count);
+    for (int i = 0; i < (int)list.size(); ++i)
+      if (tab[list[i].first].ymarch) {
+        const StageVariant<T>& r = tab[list[i].first];
+        const StageVariant<T>& t0 = tab[list[0].first];
+        if (rows_preferred(h->grids.data(), h->nsim, r.bx, r.minb, t0.bx, t0.by, h->sms)) v = i;
+        break;
+      }
   }
   if (v >= (int)list.size()) { set_error(h, "batch: variant index out of range"); return JF_ERR_ARG; }
   int count = 0;
   const StageVariant<T>* tab = stage_variants<T>(&count);
-  const StageVariant<T>& sv = tab[list[v]];
+  const StageVariant<T>& sv = tab[list[v].first];
   int per_sm = 0;
   cudaError_t e = sv.prepare_batch(&per_sm);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch: kernel set-up");
   if (per_sm < 1) { set_error(h, "batch: kernel does not fit on an SM"); return JF_ERR_UNSUPPORTED; }
   const long long cap = (long long)h->sms * per_sm;
-  const int rows = sv.ymarch ? row_chunk(h, sv.bx, cap) : 1;
+  const int rows = sv.ymarch ? list[v].second : 1;
   std::vector<WorkItem> work;
   for (int s = 0; s < h->nsim; ++s) {
     const jf_grid& g = h->grids[s];
@@ -133,7 +116,7 @@ jf_status setup_variant(jf_ctx* h, int v) {
   h->batch_blocks = (int)(h->nwork < cap ? h->nwork : cap);
   h->batch_rows = rows;
   h->variant = v;
-  h->table_index = list[v];
+  h->table_index = list[v].first;
   return JF_OK;
 }
 
@@ -413,18 +396,16 @@ jf_status batch_set_variant(jf_ctx* h, int variant) {
 
 int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   const bool visc = dissipative(h->gas, h->scheme);
-  std::vector<int> list;
+  std::vector<std::pair<int, int>> list;
   int bx = 0, by = 0, rows = 0;
   bool ymarch = false;
   auto get = [&](const auto* tab) {
     if (variant >= 0 && variant < (int)list.size()) {
-      const auto& sv = tab[list[variant]];
+      const auto& sv = tab[list[variant].first];
       bx = sv.bx;
       by = sv.by;
       ymarch = sv.ymarch;
-      int per_sm = 0;
-      if (ymarch && sv.prepare_batch(&per_sm) == cudaSuccess && per_sm > 0)
-        rows = row_chunk(h, bx, (long long)h->sms * per_sm);
+      rows = list[variant].second;
     }
   };
   int c = 0;

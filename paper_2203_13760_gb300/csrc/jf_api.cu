@@ -239,14 +239,16 @@ std::vector<std::pair<int, int>> variant_list(int dim, bool visc, int kind) {
   return out;
 }
 
-bool rows_preferred(const jf_grid* grids, int n, int rows_bx, int tile_bx, int tile_by) {
-  double rows = 0.0, tiles = 0.0;
+bool rows_preferred(const jf_grid* grids, int n, int rows_bx, int rows_ctas_per_sm, int tile_bx, int tile_by,
+                    int sms) {
+  double rows = 0.0, tiles = 0.0, row_tiles = 0.0;
   for (int i = 0; i < n; ++i) {
     const double nx = grids[i].nx, ny = grids[i].ny;
+    row_tiles += std::ceil(nx / rows_bx) * ny;
     rows += std::ceil(nx / rows_bx) * rows_bx * ny;
     tiles += std::ceil(nx / tile_bx) * tile_bx * std::ceil(ny / tile_by) * tile_by;
   }
-  return rows <= 1.08 * tiles;
+  return rows <= 1.08 * tiles && row_tiles >= 24.0 * sms * (rows_ctas_per_sm > 0 ? rows_ctas_per_sm : 1);
 }
 
 template <typename T>
@@ -254,18 +256,17 @@ jf_status select_variant(jf_ctx* h, int v, bool prepare) {
   const bool visc = dissipative(h->gas, h->scheme);
   auto list = variant_list<T>(h->dim, visc, scheme_kind(h));
   if (list.empty()) { set_error(h, "no compiled kernel variant for this configuration"); return JF_ERR_UNSUPPORTED; }
-  if (v < 0) {
+  if (v < 0) {  // the first variant, or the first row-tile one (automatic chunk) where rows_preferred says so
     v = 0;
-    if constexpr (sizeof(T) == 4) {  // FP32 2D: the row tiles (automatic chunk) where rows_preferred says so
-      int count = 0;
-      const StageVariant<T>* tab = stage_variants<T>(&count);
-      for (int i = 0; i < (int)list.size(); ++i)
-        if (tab[list[i].first].ymarch && list[i].second == 0) {
-          const StageVariant<T>& t0 = tab[list[0].first];
-          if (rows_preferred(&h->grid, 1, tab[list[i].first].bx, t0.bx, t0.by)) v = i;
-          break;
-        }
-    }
+    int count = 0;
+    const StageVariant<T>* tab = stage_variants<T>(&count);
+    for (int i = 0; i < (int)list.size(); ++i)
+      if (tab[list[i].first].ymarch && list[i].second == 0) {
+        const StageVariant<T>& r = tab[list[i].first];
+        const StageVariant<T>& t0 = tab[list[0].first];
+        if (rows_preferred(&h->grid, 1, r.bx, r.minb, t0.bx, t0.by, h->sms)) v = i;
+        break;
+      }
   }
   if (v >= (int)list.size()) { set_error(h, "variant index out of range"); return JF_ERR_ARG; }
   if (prepare) {

@@ -170,13 +170,15 @@ def test_rows_batch_close_to_tiles():
     b.close()
 
 
-@pytest.mark.parametrize("n,rows", [((256, 96, 1), True), ((64, 64, 1), False), ((32, 32, 1), False)])
+@pytest.mark.parametrize("n,rows", [((2048, 700, 1), True), ((1024, 1024, 1), False), ((256, 96, 1), False),
+                                    ((64, 64, 1), False)])
 def test_fp32_2d_default_tiles(n, rows):
     """FP32 2D handles default to the row tiles (automatic chunk) when the
     rows padded to whole tiles cover at most 8 % more cells than 32 x 7
-    tiles do (256 x 96: 24576 against 25088 cells), else to the 32 x 7 tiles
-    (64 x 64: 8192 against 4480): the default launch is bitwise the launch
-    of that variant."""
+    tiles do and there are at least 24 rows of row tiles per resident CTA
+    (2048 x 700 on 152 SMs x 3 CTAs: 16 x 700 = 11200 >= 10944), else to the
+    32 x 7 tiles (1024^2: 8192 row tiles; 64 x 64: 8192 padded cells against
+    4480): the default launch is bitwise the launch of that variant."""
     case = inputs.random_smooth(n, seed=21, viscous=True, mu=0.01)
     s = jf.Solver.from_case(case, dtype="f32")
     U0 = dev(case.U, "f32")
@@ -190,11 +192,15 @@ def test_fp32_2d_default_tiles(n, rows):
 
 
 def test_batch_default_is_rows_for_the_four_quadrant_batch():
-    cases = inputs.four_quadrant_batch(nsim=8, seed=3)
+    """The 64 four-quadrant problems (about 106 rows of row tiles per
+    resident CTA) default to the row tiles with 32 rows per work item."""
+    cases = inputs.four_quadrant_batch(nsim=64)
     b = _batch(cases, "f32")
     Us = [dev(c.U, "f32") for c in cases]
     b.step(Us, 2)
-    b.set_variant(row_variants(b)[0])
+    v = row_variants(b)[0]
+    assert "tile=128x1 ymarch rows=32 persistent" == b.variants()[v]
+    b.set_variant(v)
     Vs = [dev(c.U, "f32") for c in cases]
     b.step(Vs, 2)
     b.sync()
