@@ -248,7 +248,7 @@ bool rows_preferred(const jf_grid* grids, int n, int rows_bx, int rows_ctas_per_
     rows += std::ceil(nx / rows_bx) * rows_bx * ny;
     tiles += std::ceil(nx / tile_bx) * tile_bx * std::ceil(ny / tile_by) * tile_by;
   }
-  return rows <= 1.08 * tiles && row_tiles >= 24.0 * sms * (rows_ctas_per_sm > 0 ? rows_ctas_per_sm : 1);
+  return rows <= 1.08 * tiles && row_tiles >= 12.0 * sms * (rows_ctas_per_sm > 0 ? rows_ctas_per_sm : 1);
 }
 
 template <typename T>

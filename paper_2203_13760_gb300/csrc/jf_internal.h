@@ -106,11 +106,12 @@ double spacing(const jf_grid& g, int d);
 // Default tiles of 2D grids: the row tiles (rows_bx cells per row, marching
 // along y) when the rows of the n grids, padded to whole tiles, cover at most
 // 8 % more cells than the tile_bx x tile_by tiles do, and there are at least
-// 24 rows of row tiles per resident CTA (rows_ctas_per_sm on each of sms
-// SMs).  On GB300 the row tiles measured 5-10 % faster per cell on large
-// grids (Kelvin-Helmholtz 2048^2 FP32 and 1024^2 FP64, the 64 four-quadrant
-// problems) and slower on small ones, where each CTA gets a few rows and the
-// ring's prologue dominates (Kelvin-Helmholtz 256^2, 512^2).
+// 12 rows of row tiles per resident CTA (rows_ctas_per_sm on each of sms
+// SMs).  On GB300 the row tiles measured 5-11 % faster per step on large
+// grids (Kelvin-Helmholtz FP32 1024^2 with 18 rows per CTA, 1536^2, 2048^2;
+// FP64 1024^2, 2048^2; the 64 four-quadrant problems) and slower on small
+// ones, where each CTA gets a few rows and the ring's prologue dominates
+// (Kelvin-Helmholtz FP32 512^2 with 4.5 rows per CTA: 12 % slower).
 bool rows_preferred(const jf_grid* grids, int n, int rows_bx, int rows_ctas_per_sm, int tile_bx, int tile_by,
                     int sms);
 double conductivity(const jf_gas& gas, const jf_scheme& s);

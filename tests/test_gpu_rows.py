@@ -170,15 +170,16 @@ def test_rows_batch_close_to_tiles():
     b.close()
 
 
-@pytest.mark.parametrize("n,rows", [((2048, 700, 1), True), ((1024, 1024, 1), False), ((256, 96, 1), False),
-                                    ((64, 64, 1), False)])
+@pytest.mark.parametrize("n,rows", [((2048, 350, 1), True), ((1024, 1024, 1), True), ((2048, 300, 1), False),
+                                    ((512, 512, 1), False), ((64, 64, 1), False)])
 def test_fp32_2d_default_tiles(n, rows):
     """FP32 2D handles default to the row tiles (automatic chunk) when the
     rows padded to whole tiles cover at most 8 % more cells than 32 x 7
-    tiles do and there are at least 24 rows of row tiles per resident CTA
-    (2048 x 700 on 152 SMs x 3 CTAs: 16 x 700 = 11200 >= 10944), else to the
-    32 x 7 tiles (1024^2: 8192 row tiles; 64 x 64: 8192 padded cells against
-    4480): the default launch is bitwise the launch of that variant."""
+    tiles do and there are at least 12 rows of row tiles per resident CTA
+    (152 SMs x 3 CTAs: 2048 x 350 has 16 x 350 = 5600 >= 5472, 1024^2 8192),
+    else to the 32 x 7 tiles (2048 x 300: 4800 row tiles; 512^2: 2048;
+    64 x 64: 8192 padded cells against 4480): the default launch is bitwise
+    the launch of that variant."""
     case = inputs.random_smooth(n, seed=21, viscous=True, mu=0.01)
     s = jf.Solver.from_case(case, dtype="f32")
     U0 = dev(case.U, "f32")
