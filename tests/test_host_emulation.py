@@ -1,0 +1,167 @@
+"""The stage kernel's own source, compiled for the CPU (tests/host_emu: one
+std::thread per CUDA thread, a std::barrier per CTA, exact-size heap buffers
+for the shared memory and the fields) and run under AddressSanitizer and
+UBSan where the toolchain has them: every shared-memory and global access of
+the tiles stays inside its buffer, and the results match the oracle -- FP64
+to 1e-12 (right-hand side, rate norm; one stage), FP32 to 1e-5 -- for the 2D
+tiles, the row tiles of 2D grids (several row widths and chunk lengths) and
+the 3D z-march on ragged grids with periodic, zero-gradient and mixed
+boundaries.  This checks the kernels' index arithmetic on the CPU, without a
+GPU; the GPU parity tests check the compiled kernels themselves."""
+import ctypes
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if __name__ == "__main__":
+    sys.path.insert(0, ROOT)
+
+from paper_2203_13760_gb300 import inputs  # noqa: E402
+
+CSRC = os.path.join(ROOT, "paper_2203_13760_gb300", "csrc")
+HERE = os.path.join(ROOT, "tests", "host_emu")
+GROUPS = ((0,), (1, 2, 3), (4,))
+SMEM_DECL = "extern __shared__ __align__(16) unsigned char smem_raw[];"
+
+CASES = {
+    "2d_smooth_visc_mixed": lambda: inputs.random_smooth((37, 19, 1), seed=3, bc=(0, 0, 1, 1, 1, 1), viscous=True,
+                                                         mu=0.01),
+    "2d_blocks_zg": lambda: inputs.random_blocks((40, 33, 1), seed=4),
+    "2d_wide_y_periodic": lambda: inputs.random_smooth((150, 41, 1), seed=8, bc=(1, 1, 0, 0, 1, 1), viscous=True,
+                                                       mu=0.01),
+    "3d_smooth_visc_ragged": lambda: inputs.random_smooth((19, 13, 11), seed=6, viscous=True, mu=0.01),
+}
+
+# (case, precision, kernel, z chunk): kernels as in emu.cpp (0: 2D tiles,
+# 1/2/3: row tiles 128/96/224 wide, 4: 3D tiles)
+RUNS = [
+    ("2d_smooth_visc_mixed", "f64", 0, 1), ("2d_smooth_visc_mixed", "f64", 1, 5),
+    ("2d_smooth_visc_mixed", "f64", 1, 1000), ("2d_blocks_zg", "f64", 1, 7), ("2d_wide_y_periodic", "f64", 1, 16),
+    ("2d_wide_y_periodic", "f32", 2, 3), ("2d_wide_y_periodic", "f32", 3, 41), ("2d_blocks_zg", "f32", 1, 1),
+    ("3d_smooth_visc_ragged", "f64", 4, 4), ("3d_smooth_visc_ragged", "f32", 4, 11),
+]
+
+
+def _sanitizer_libs():
+    libs = []
+    for name in ("libasan.so", "libubsan.so"):
+        p = subprocess.run(["gcc", "-print-file-name=" + name], capture_output=True, text=True).stdout.strip()
+        if not os.path.isabs(p) or not os.path.exists(p):
+            return []
+        libs.append(p)
+    return libs
+
+
+@pytest.fixture(scope="module")
+def emu_lib(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("host_emu")
+    src = d / "src"
+    src.mkdir()
+    for f in ("stage.cuh", "jf_math.cuh"):
+        shutil.copy(os.path.join(CSRC, f), src / f)
+    text = (src / "stage.cuh").read_text()
+    assert text.count(SMEM_DECL) == 1
+    text = text.replace(SMEM_DECL, "unsigned char* smem_raw = emu_smem();")
+    text = text.replace("namespace jf {\n", "unsigned char* emu_smem();\nnamespace jf {\n", 1)
+    (src / "stage.cuh").write_text(text)
+    san = _sanitizer_libs()
+    lib = d / "libemu.so"
+    cmd = ["g++", "-std=c++20", "-O1", "-g", "-fno-omit-frame-pointer", "-shared", "-fPIC",
+           "-I", os.path.join(HERE, "cuda_stub"), "-I", str(src), os.path.join(HERE, "emu.cpp"), "-o", str(lib),
+           "-lpthread"]
+    if san:
+        cmd[1:1] = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined"]
+    out = subprocess.run(cmd, capture_output=True, text=True)
+    if out.returncode != 0 and "barrier" in out.stderr:
+        pytest.skip("the C++ library has no std::barrier")
+    assert out.returncode == 0, out.stderr[-3000:]
+    return str(lib), san
+
+
+def _params(case):
+    p = case.params()
+    n = [int(x) for x in p["n"]]
+    periodic = [1 if p["bc"][2 * a] == 0 else 0 for a in range(3)]
+    inv_h = [n[a] / (p["hi"][a] - p["lo"][a]) for a in range(3)]
+    mu = p["mu"] if p["viscous"] else 0.0
+    lam = p["mu"] * p["gamma"] * p["R"] / ((p["gamma"] - 1.0) * p["Pr"]) if p["heat"] else 0.0
+    return n, periodic, inv_h, [p["gamma"], p["R"], mu, lam, p["eps"]]
+
+
+def emulate(lib_path, case, dtype, kernel, zchunk, rhs_only=True, a=0.0, b=1.0, dt=0.0, Un=None):
+    L = ctypes.CDLL(lib_path)
+    n, periodic, inv_h, gas = _params(case)
+    t = np.float64 if dtype == "f64" else np.float32
+    U = np.ascontiguousarray(case.U, dtype=t)
+    N = np.ascontiguousarray(Un, dtype=t) if Un is not None else None
+    out = np.zeros_like(U)
+    ip = lambda v: (ctypes.c_int * 3)(*v)  # noqa: E731
+    dp = lambda v: (ctypes.c_double * len(v))(*v)  # noqa: E731
+    fn = L.emu_stage_f64 if dtype == "f64" else L.emu_stage_f32
+    fn.restype = ctypes.c_int
+    flag = fn(kernel, ip(n), ip(periodic), dp(inv_h), dp(gas), int(zchunk), int(rhs_only), ctypes.c_double(a),
+              ctypes.c_double(b), ctypes.c_double(dt), U.ctypes.data_as(ctypes.c_void_p),
+              N.ctypes.data_as(ctypes.c_void_p) if N is not None else None, out.ctypes.data_as(ctypes.c_void_p))
+    assert flag == 0, flag
+    return out.astype(np.float64)
+
+
+def _run_child(lib_path, san, args):
+    """Runs this file as a script in a child process (the sanitizer runtime
+    must be loaded first, with LD_PRELOAD) and returns its JSON result."""
+    env = dict(os.environ)
+    if san:
+        env["LD_PRELOAD"] = " ".join(san)
+        env["ASAN_OPTIONS"] = "detect_leaks=0:abort_on_error=1"
+    env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), lib_path, *map(str, args)], capture_output=True,
+                         text=True, env=env, timeout=600)
+    assert out.returncode == 0, (out.stdout[-2000:], out.stderr[-4000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def _child(lib_path, name, dtype, kernel, zchunk):
+    import oracle as orc
+    case = CASES[name]()
+    c = orc.config(**case.params())
+    U = case.U if dtype == "f64" else case.U.astype(np.float32).astype(np.float64)
+    want = orc.rhs(c, U)
+    rate = case.cfl / orc.compute_dt(c, U)
+    got = emulate(lib_path, case, dtype, kernel, zchunk)
+    err = 0.0
+    for g in GROUPS:
+        g = list(g)
+        w, x, u = want.reshape(5, -1)[g], got.reshape(5, -1)[g], U.reshape(5, -1)[g]
+        err = max(err, np.abs(x - w).max() / max(np.abs(w).max(), np.abs(u).max() * rate, 1e-300))
+    res = {"rhs": err}
+    if dtype == "f64":
+        # one stage of the Shu-Osher form: out = 3/4 Un + 1/4 (Us + dt L(Us))
+        Un = inputs.random_smooth(tuple(case.n), seed=77).U
+        dt = 0.3 * orc.compute_dt(c, U)
+        want_s = 0.75 * Un + 0.25 * (U + dt * want)
+        got_s = emulate(lib_path, case, dtype, kernel, zchunk, rhs_only=False, a=0.75, b=0.25, dt=dt, Un=Un)
+        res["stage"] = float(np.abs(got_s - want_s).max() / np.abs(want_s).max())
+    return res
+
+
+@pytest.mark.parametrize("run", RUNS, ids=[f"{r[0]}-{r[1]}-k{r[2]}-z{r[3]}" for r in RUNS])
+def test_emulated_kernel_vs_oracle(emu_lib, run):
+    lib_path, san = emu_lib
+    res = _run_child(lib_path, san, run)
+    tol = 1e-12 if run[1] == "f64" else 1e-5
+    assert res["rhs"] <= tol, res
+    if "stage" in res:
+        assert res["stage"] <= 1e-13, res
+
+
+if __name__ == "__main__":
+    lib, name, dtype, kernel, zchunk = sys.argv[1:6]
+    print(json.dumps(_child(lib, name, dtype, int(kernel), int(zchunk))))
