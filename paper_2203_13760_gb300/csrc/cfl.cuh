@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U0, CflA
   CflArgs a;
   ReduceScratch* sc;
   double *dto, *dto2;
-  long long q0, end, stride;
+  long long first, q0, end, stride;
   unsigned int nblocks;
   if (chunks) {
     const CflChunk ch = chunks[blockIdx.x];
@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U0, CflA
     sc = red + ch.sim;
     dto = dts + ch.sim;
     dto2 = nullptr;
+    first = ch.begin;
     q0 = ch.begin + threadIdx.x;
     end = ch.end;
     stride = blockDim.x;
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U0, CflA
     sc = sc0;
     dto = dt0;
     dto2 = dt0b;
+    first = 0;
     q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     end = a.N;
     stride = (long long)gridDim.x * blockDim.x;
@@ -61,14 +63,15 @@ __global__ void __launch_bounds__(256) cfl_kernel(const T* __restrict__ U0, CflA
   const T gamma = (T)a.gamma, gm1 = (T)(a.gamma - 1.0), kdiff = (T)a.kdiff;
   bool bad = false;
   constexpr int V = 16 / (int)sizeof(T);  // cells per 16-byte vector
-  if (!chunks && a.N % V == 0) {
-    // single grid: every component read in 16-byte vectors (U is 16-byte
-    // aligned and a component spans a whole number of vectors); the maxima
-    // are exact, so dt equals the scalar form's
+  if (a.N % V == 0 && first % V == 0 && end % V == 0) {
+    // every component read in 16-byte vectors (U is 16-byte aligned, a
+    // component spans a whole number of vectors, and so does a batch chunk);
+    // the maxima are exact, so dt equals the scalar form's
     using VT = typename Vec16<T>::type;
     const VT* Uv = reinterpret_cast<const VT*>(U);
     const long long Nv = a.N / V;
-    for (long long qv = q0; qv < Nv; qv += stride) {
+    const long long vend = end / V;
+    for (long long qv = first / V + (q0 - first); qv < vend; qv += stride) {
       T r[V], ru[V], rv[V], rw[V], E[V];
       unpack(Uv[qv], r);
       unpack(Uv[qv + Nv], ru);
