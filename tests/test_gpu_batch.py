@@ -54,6 +54,29 @@ def test_batch_equals_single_grid_path(dtype):
         assert dt[i].item() == used.item()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_ragged_cell_counts(dtype):
+    """Cell counts that are and are not multiples of the 16-byte vector
+    (37 x 19 = 703, 40 x 33 = 1320, 129 x 130, 31 x 64): the batch CFL reads
+    the first with scalar loads and the others in vectors within one launch;
+    dt and the states stay bitwise those of the single-grid path."""
+    cases = [inputs.random_blocks((37, 19, 1), seed=1), inputs.random_blocks((40, 33, 1), seed=2),
+             inputs.random_blocks((129, 130, 1), seed=3), inputs.random_blocks((31, 64, 1), seed=4)]
+    b = batch_of(cases, dtype)
+    Us = fields(cases, dtype)
+    dt = b.step(Us, 5)
+    b.sync()
+    for i, c in enumerate(cases):
+        s = jf.Solver.from_case(c, dtype=dtype)
+        U = fields([c], dtype)[0]
+        used = s.scalar()
+        for _ in range(5):
+            s.rk3_step(U, None, used)
+        s.sync()
+        assert dt[i].item() == used.item(), i
+        assert torch.equal(U, Us[i]), i
+
+
 def test_batch_fp64_matches_oracle(orc):
     cases = inputs.four_quadrant_batch(nsim=4, sides=(24, 40), seed=9)
     b = batch_of(cases, "f64")
