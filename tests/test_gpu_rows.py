@@ -170,23 +170,27 @@ def test_rows_batch_close_to_tiles():
     b.close()
 
 
-@pytest.mark.parametrize("n,rows", [((2048, 350, 1), True), ((1024, 1024, 1), True), ((2048, 300, 1), False),
-                                    ((512, 512, 1), False), ((64, 64, 1), False)])
-def test_fp32_2d_default_tiles(n, rows):
+@pytest.mark.parametrize("n,rows,dtype", [((2048, 350, 1), True, "f32"), ((1024, 1024, 1), True, "f32"),
+                                          ((2048, 300, 1), False, "f32"), ((512, 512, 1), False, "f32"),
+                                          ((64, 64, 1), False, "f32"), ((1024, 1024, 1), True, "f64"),
+                                          ((512, 512, 1), False, "f64")])
+def test_2d_default_tiles(n, rows, dtype):
     """FP32 2D handles default to the row tiles (automatic chunk) when the
     rows padded to whole tiles cover at most 8 % more cells than 32 x 7
     tiles do and there are at least 12 rows of row tiles per resident CTA
     (152 SMs x 3 CTAs: 2048 x 350 has 16 x 350 = 5600 >= 5472, 1024^2 8192),
     else to the 32 x 7 tiles (2048 x 300: 4800 row tiles; 512^2: 2048;
-    64 x 64: 8192 padded cells against 4480): the default launch is bitwise
-    the launch of that variant."""
+    64 x 64: 8192 padded cells against 4480).  FP64 (row tiles at 2 CTAs
+    per SM, 32 x 8 tiles): 1024^2 has 26.9 rows per resident CTA, 512^2 6.7.
+    The default launch is bitwise the launch of that variant."""
     case = inputs.random_smooth(n, seed=21, viscous=True, mu=0.01)
-    s = jf.Solver.from_case(case, dtype="f32")
-    U0 = dev(case.U, "f32")
+    s = jf.Solver.from_case(case, dtype=dtype)
+    U0 = dev(case.U, dtype)
     dflt = s.rhs(U0).clone()
     want = row_variants(s, "auto")[0] if rows else 0
     s.set_variant(want)
-    assert "ymarch" in s.variants()[want] if rows else "tile=32x7" in s.variants()[want]
+    tile = "tile=32x7" if dtype == "f32" else "tile=32x8"
+    assert "ymarch" in s.variants()[want] if rows else tile in s.variants()[want]
     got = s.rhs(U0)
     s.sync()
     assert torch.equal(dflt, got)
