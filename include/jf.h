@@ -305,9 +305,11 @@ jf_status jf_loss_primitive_mse(jf_handle h, const void* U, const void* Uref, lo
 
 /* Batch of nsim independent simulations with their own grid sizes (Section
  * 4.5, feed_forward over a batch of initial buffers; here sizes may differ).
- * All share gas and scheme.  Each grid must be 2D or 1D (nz == 1);
- * 1 <= nsim <= 65535.  Allocates each simulation's stage buffers and the work
- * list. */
+ * All share gas and scheme and have the same number of active axes (1D, 2D
+ * or 3D; JF_ERR_UNSUPPORTED otherwise); 1 <= nsim <= 65535.  The work list
+ * holds the simulations' tiles, and for 3D grids and the row tiles of 2D
+ * grids chunks of 32 planes (rows) along the march (jf_set_variant selects
+ * 16 or 64).  Allocates each simulation's stage buffers and the work list. */
 jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, const jf_scheme* scheme,
                           jf_handle* out);
 

@@ -50,11 +50,11 @@ __global__ void __launch_bounds__(256) batch_copy_pairs_kernel(const T* const* _
 
 namespace {
 
-// Batch variants: (table index, rows per work item) -- the tile kernels
-// once (rows 0), the row-tile (ymarch) kernels with 32, 16 and 64 rows per
-// item (the explicit z chunks of the single-grid variants; 32 measured
-// fastest on the 64 four-quadrant problems: 6.34 G cell-updates/s against
-// 6.18 with 16).
+// Batch variants: (table index, planes per work item) -- the 1D and 2D tile
+// kernels once (0), the z-march kernels (3D tiles, 2D row tiles) with 32,
+// 16 and 64 planes (rows) per item (the explicit z chunks of the
+// single-grid variants; on the 64 four-quadrant problems 32 rows measured
+// fastest: 6.34 G cell-updates/s against 6.18 with 16).
 template <typename T>
 std::vector<std::pair<int, int>> batch_variant_list(int dim, bool visc, int kind) {
   int count = 0;
@@ -62,7 +62,7 @@ std::vector<std::pair<int, int>> batch_variant_list(int dim, bool visc, int kind
   std::vector<std::pair<int, int>> out;
   for (int i = 0; i < count; ++i)
     if (tab[i].dim == dim && tab[i].visc == visc && tab[i].scheme == kind && tab[i].launch_batch) {
-      if (tab[i].ymarch)
+      if (tab[i].ymarch || tab[i].dim == 3)
         for (int r : {32, 16, 64}) out.emplace_back(i, r);
       else
         out.emplace_back(i, 0);
@@ -97,14 +97,20 @@ jf_status setup_variant(jf_ctx* h, int v) {
   if (e != cudaSuccess) return cuda_fail(h, e, "batch: kernel set-up");
   if (per_sm < 1) { set_error(h, "batch: kernel does not fit on an SM"); return JF_ERR_UNSUPPORTED; }
   const long long cap = (long long)h->sms * per_sm;
-  const int rows = sv.ymarch ? list[v].second : 1;
+  const bool march = sv.ymarch || sv.dim == 3;
+  const int rows = march ? list[v].second : 1;
   std::vector<WorkItem> work;
   for (int s = 0; s < h->nsim; ++s) {
     const jf_grid& g = h->grids[s];
+    // tile columns (x, y) and chunks of `rows` planes along the march (3D:
+    // z; row tiles: the grid's y)
     const int tx = (g.nx + sv.bx - 1) / sv.bx;
-    const int ty = sv.ymarch ? (g.ny + rows - 1) / rows : (h->dim >= 2 ? (g.ny + sv.by - 1) / sv.by : 1);
-    for (int y = 0; y < ty; ++y)
-      for (int x = 0; x < tx; ++x) work.push_back(WorkItem{s, x, y});
+    const int ty = sv.ymarch ? 1 : (h->dim >= 2 ? (g.ny + sv.by - 1) / sv.by : 1);
+    const int marched = sv.ymarch ? g.ny : g.nz;
+    const int tz = march ? (marched + rows - 1) / rows : 1;
+    for (int z = 0; z < tz; ++z)
+      for (int y = 0; y < ty; ++y)
+        for (int x = 0; x < tx; ++x) work.push_back(WorkItem{s, x, y, z});
   }
   if (h->d_work) cudaFree(h->d_work);
   h->d_work = nullptr;
@@ -228,7 +234,7 @@ cudaError_t launch_batch_stage(jf_ctx* h, const StageVariant<T>& sv, const SimDe
     for (int i = 0; i < h->nsim; ++i) {
       StageArgs<T> A{};
       batch_stage_args(host_sims[i], code, A);
-      if (sv.ymarch) A.zchunk = h->batch_rows;
+      if (sv.ymarch || sv.dim == 3) A.zchunk = h->batch_rows;
       A.flag = h->flag;
 #ifdef JF_DEBUG_BOUNDS
       A.trace = debug_trace_dev();
@@ -398,13 +404,14 @@ int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   const bool visc = dissipative(h->gas, h->scheme);
   std::vector<std::pair<int, int>> list;
   int bx = 0, by = 0, rows = 0;
-  bool ymarch = false;
+  bool ymarch = false, dim3d = false;
   auto get = [&](const auto* tab) {
     if (variant >= 0 && variant < (int)list.size()) {
       const auto& sv = tab[list[variant].first];
       bx = sv.bx;
       by = sv.by;
       ymarch = sv.ymarch;
+      dim3d = sv.dim == 3;
       rows = list[variant].second;
     }
   };
@@ -419,6 +426,8 @@ int batch_variant_info(jf_ctx* h, int variant, char* buf, int len) {
   if (variant >= 0 && variant < (int)list.size() && buf && len > 0) {
     if (ymarch)
       std::snprintf(buf, (size_t)len, "tile=%dx%d ymarch rows=%d persistent", bx, by, rows);
+    else if (dim3d)
+      std::snprintf(buf, (size_t)len, "tile=%dx%d zchunk=%d persistent", bx, by, rows);
     else
       std::snprintf(buf, (size_t)len, "tile=%dx%d persistent", bx, by);
   }
@@ -448,7 +457,6 @@ jf_status jf_batch_create(const jf_grid* grids, int nsim, const jf_gas* gas, con
       return JF_ERR_UNSUPPORTED;
     }
   }
-  if (dim == 3) { set_error(nullptr, "jf_batch_create: batches of 3D grids are not built"); return JF_ERR_UNSUPPORTED; }
   jf_ctx* h = new jf_ctx();
   h->kind = 1;
   h->gas = *gas;

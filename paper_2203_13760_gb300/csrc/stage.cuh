@@ -1081,7 +1081,8 @@ struct SimDesc {
 
 struct WorkItem {
   int sim;
-  int bx, by;
+  int bx, by;  // tile column (DIM_Y2: by = 0)
+  int bz;      // z-march kernels (3D, DIM_Y2): the chunk of A0.zchunk planes (rows); else 0
 };
 
 // Arguments of batch stage `stage` for the simulation of descriptor d:
@@ -1162,8 +1163,8 @@ constexpr size_t nn_smem_offset() {
 //    equal cost); the grid arguments come from the simulation's descriptor,
 //    stage 1: U1 = U + dt L(U); stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1));
 //    stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2)); stage 4 (TVD-RK2):
-//    U = 1/2 U + 1/2 (U1 + dt L(U1)).  DIM_Y2: an item is a tile column
-//    and a chunk of A0.zchunk rows.
+//    U = 1/2 U + 1/2 (U1 + dt L(U1)).  z-march kernels (3D, DIM_Y2): an
+//    item is a tile column and a chunk of A0.zchunk planes (rows).
 // Both forms reach the tile computation through the same call below, so a
 // simulation advanced in a batch is bitwise the one advanced alone.
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
@@ -1208,16 +1209,11 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
       const WorkItem w = work[item];
       const SimDesc<T> d = sims[w.sim];
       batch_stage_args(d, stage, A);
+      if constexpr (DIM == DIM_Y2) rows_as_planes(A);
+      if constexpr (marches(DIM)) A.zchunk = A0.zchunk;
       bx = w.bx;
-      if constexpr (DIM == DIM_Y2) {  // w.by: the chunk of rows (planes) of A0.zchunk rows
-        rows_as_planes(A);
-        A.zchunk = A0.zchunk;
-        by = 0;
-        bz = w.by;
-      } else {
-        by = w.by;
-        bz = 0;
-      }
+      by = w.by;
+      bz = w.bz;
 #ifdef JF_DEBUG_BOUNDS
       if (threadIdx.x == 0)
         jf_trace(d.trace, 0x100 + stage, ((unsigned long long)item << 32) | (unsigned)w.sim,

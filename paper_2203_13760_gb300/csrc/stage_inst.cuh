@@ -45,7 +45,8 @@ cudaError_t prepare_batch(int* blocks_per_sm) {
                                                        launch_smem<T, DIM, VISC, BX, BY, SCH>());
 }
 
-// rows: DIM_Y2, the rows of a work item's chunk (other kernels ignore it).
+// rows: z-march kernels (3D, DIM_Y2), the planes (rows) of a work item's
+// chunk (other kernels ignore it).
 template <typename T, int DIM, bool VISC, int BX, int BY, int MINB, int SCH>
 cudaError_t launch_batch(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
                          int* flag, int grid, int rows, cudaStream_t s) {
@@ -66,10 +67,8 @@ StageVariant<T> make_variant() {
   StageVariant<T> v{DIM == DIM_Y2 ? 2 : DIM, VISC, BX, BY, launch_smem<T, DIM, VISC, BX, BY, SCH>(),
                     &prepare_stage<T, DIM, VISC, BX, BY, MINB, SCH>, &launch_stage<T, DIM, VISC, BX, BY, MINB, SCH>,
                     nullptr, nullptr, Geo<BX, BY, DIM, VISC>::NT, SCH, MINB, DIM == DIM_Y2};
-  if constexpr (DIM != 3) {  // batches are built for 1D and 2D grids
-    v.prepare_batch = &prepare_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
-    v.launch_batch = &launch_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
-  }
+  v.prepare_batch = &prepare_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
+  v.launch_batch = &launch_batch<T, DIM, VISC, BX, BY, MINB, SCH>;
   return v;
 }
 

@@ -20,7 +20,7 @@ struct StageVariant {
   size_t smem;
   cudaError_t (*prepare)();  // one-time attribute set-up (dynamic shared memory)
   cudaError_t (*launch)(const StageArgs<T>& A, const Gas<T>& g, cudaStream_t s);
-  // persistent batched launch over a work list (same tile code; 2D / 1D only, else null)
+  // persistent batched launch over a work list (same tile code)
   cudaError_t (*prepare_batch)(int* blocks_per_sm);
   cudaError_t (*launch_batch)(const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage, const Gas<T>& g,
                               int* flag, int grid, int rows, cudaStream_t s);

@@ -51,6 +51,33 @@ static void run(StageArgs<T> A, const Gas<T>& g) {
       }
 }
 
+// The persistent batch form of the same kernel: `ctas` CTAs, in turn, each
+// looping over the work items item = blockIdx.x, blockIdx.x + ctas, ...
+template <typename T, int DIM, bool VISC, int BX, int BY>
+static void run_batch(const StageArgs<T>& A0, const SimDesc<T>* sims, const WorkItem* work, int nwork, int stage,
+                      const Gas<T>& g, int ctas) {
+  using G = Geo<BX, BY, DIM, VISC>;
+  const size_t smem = sizeof(T) * (stage_smem_elems<T, DIM, VISC, BX, BY>() + recon_smem_elems<DIM, BX, BY>());
+  gridDim.x = ctas;
+  gridDim.y = gridDim.z = 1;
+  blockDim.x = G::NT;
+  for (int b = 0; b < ctas; ++b) {
+    std::unique_ptr<unsigned char[]> sm(new unsigned char[smem]);
+    std::memset(sm.get(), 0xFF, smem);
+    g_smem = sm.get();
+    std::barrier<> bar(G::NT);
+    g_bar = &bar;
+    std::vector<std::thread> th;
+    for (int t = 0; t < G::NT; ++t)
+      th.emplace_back([&, t] {
+        threadIdx = uint3{(unsigned)t, 0, 0};
+        blockIdx = uint3{(unsigned)b, 0, 0};
+        stage_kernel<T, DIM, VISC, BX, BY, 1, SCH_DEFAULT>(A0, sims, work, nwork, stage, g);
+      });
+    for (auto& x : th) x.join();
+  }
+}
+
 // Kernels: 0 the 2D tiles (FP32 32 x 7, FP64 32 x 8), 1 the 128-wide row
 // tiles, 2 the 96-wide and 3 the 224-wide row tiles (FP32), 4 the 3D tiles
 // (FP32 32 x 7, FP64 32 x 4).
@@ -133,4 +160,93 @@ extern "C" int emu_stage_f32(int kernel, const int* n, const int* periodic, cons
                              int zchunk, int rhs_only, double a, double b, double dt, const float* Us,
                              const float* Un, float* out) {
   return stage<float>(kernel, n, periodic, inv_h, gas, zchunk, rhs_only, a, b, dt, Us, Un, out);
+}
+
+// Stage 1 of a batch (U1 = U + dt L(U) for every simulation) through the
+// persistent form: nsim simulations with dims n[3 s + a], periodic flags
+// p[3 s + a], spacings 1/h in inv_h[3 s + a] and steps dts[s]; work items as
+// the library builds them (tile columns, and for the z-march kernels chunks of
+// `rows` planes); `ctas` persistent CTAs.  Us[s] / U1s[s]: 5 N_s values each.
+template <typename T>
+static int batch_stage1(int kernel, int nsim, const int* n, const int* p, const double* inv_h, const double* gas,
+                        int rows, int ctas, const double* dts, const T* const* Us, T* const* U1s) {
+  std::vector<std::unique_ptr<T[]>> us, u1;
+  std::unique_ptr<double[]> dt(new double[nsim]);
+  std::unique_ptr<SimDesc<T>[]> sims(new SimDesc<T>[nsim]);
+  std::vector<WorkItem> items;
+  const bool f32 = sizeof(T) == 4;
+  const int bx = kernel == 0 || kernel == 4 ? 32 : (kernel == 1 ? 128 : (kernel == 2 ? 96 : 224));
+  const int by = kernel == 0 ? (f32 ? 7 : 8) : (kernel == 4 ? (f32 ? 7 : 4) : 1);
+  for (int s = 0; s < nsim; ++s) {
+    const long long N = (long long)n[3 * s] * n[3 * s + 1] * n[3 * s + 2];
+    us.emplace_back(new T[5 * N]);
+    u1.emplace_back(new T[5 * N]);
+    std::memcpy(us.back().get(), Us[s], sizeof(T) * 5 * N);
+    dt[s] = dts[s];
+    SimDesc<T>& d = sims[s];
+    std::memset(&d, 0, sizeof d);
+    d.U = us.back().get();
+    d.U1 = u1.back().get();
+    d.U2 = nullptr;
+    d.dt = dt.get() + s;
+    d.nx = n[3 * s];
+    d.ny = n[3 * s + 1];
+    d.nz = n[3 * s + 2];
+    d.N = N;
+    for (int a = 0; a < 3; ++a) {
+      d.periodic[a] = p[3 * s + a];
+      d.inv_h[a] = (T)inv_h[3 * s + a];
+    }
+    const bool rows_kernel = kernel >= 1 && kernel <= 3;
+    const int tx = (d.nx + bx - 1) / bx;
+    const int ty = rows_kernel ? 1 : (d.ny + by - 1) / by;
+    const int marched = rows_kernel ? d.ny : d.nz;
+    const int tz = kernel == 0 ? 1 : (marched + rows - 1) / rows;
+    for (int z = 0; z < tz; ++z)
+      for (int y = 0; y < ty; ++y)
+        for (int x = 0; x < tx; ++x) items.push_back(WorkItem{s, x, y, z});
+  }
+  std::unique_ptr<WorkItem[]> work(new WorkItem[items.size()]);
+  std::memcpy(work.get(), items.data(), sizeof(WorkItem) * items.size());
+  int flag = 0;
+  StageArgs<T> A0;
+  std::memset(&A0, 0, sizeof A0);
+  A0.flag = &flag;
+  A0.zchunk = rows;
+  Gas<T> g;
+  std::memset(&g, 0, sizeof g);
+  g.gamma = (T)gas[0];
+  g.gm1 = (T)(gas[0] - 1.0);
+  g.inv_gm1 = (T)(1.0 / (gas[0] - 1.0));
+  g.inv_R = (T)(1.0 / gas[1]);
+  g.mu = (T)gas[2];
+  g.lambda = (T)gas[3];
+  g.eps = (T)gas[4];
+  const bool visc = gas[2] > 0.0;
+  const int nw = (int)items.size();
+  switch (kernel) {
+    case 0:
+      if (visc) run_batch<T, 2, true, 32, f32 ? 7 : 8>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      else run_batch<T, 2, false, 32, f32 ? 7 : 8>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      break;
+    case 1:
+      if (visc) run_batch<T, DIM_Y2, true, 128, 1>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      else run_batch<T, DIM_Y2, false, 128, 1>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      break;
+    case 4:
+      if (visc) run_batch<T, 3, true, 32, f32 ? 7 : 4>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      else run_batch<T, 3, false, 32, f32 ? 7 : 4>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      break;
+    default:
+      return -1;
+  }
+  for (int s = 0; s < nsim; ++s)
+    std::memcpy(U1s[s], u1[s].get(), sizeof(T) * 5 * sims[s].N);
+  return flag;
+}
+
+extern "C" int emu_batch_stage1_f64(int kernel, int nsim, const int* n, const int* p, const double* inv_h,
+                                    const double* gas, int rows, int ctas, const double* dts,
+                                    const double* const* Us, double* const* U1s) {
+  return batch_stage1<double>(kernel, nsim, n, p, inv_h, gas, rows, ctas, dts, Us, U1s);
 }

@@ -6,8 +6,12 @@ the tiles stays inside its buffer, and the results match the oracle -- FP64
 to 1e-12 (right-hand side, rate norm; one stage), FP32 to 1e-5 -- for the 2D
 tiles, the row tiles of 2D grids (several row widths and chunk lengths) and
 the 3D z-march on ragged grids with periodic, zero-gradient and mixed
-boundaries.  This checks the kernels' index arithmetic on the CPU, without a
-GPU; the GPU parity tests check the compiled kernels themselves."""
+boundaries.  The persistent batch form (descriptors and work items, with
+chunks of planes for the z-march kernels) is checked the same way: every
+simulation of an emulated batch stage equals the emulated single-grid stage
+with the same chunk, bit for bit.  This checks the kernels' index arithmetic
+on the CPU, without a GPU; the GPU parity tests check the compiled kernels
+themselves."""
 import ctypes
 import json
 import os
@@ -114,6 +118,27 @@ def emulate(lib_path, case, dtype, kernel, zchunk, rhs_only=True, a=0.0, b=1.0, 
     return out.astype(np.float64)
 
 
+def emulate_batch_stage1(lib_path, cases, kernel, rows, ctas, dts):
+    """Stage 1 (U1 = U + dt L(U)) of every simulation through the persistent
+    batch form (FP64)."""
+    L = ctypes.CDLL(lib_path)
+    ps = [_params(c) for c in cases]
+    n = [x for p in ps for x in p[0]]
+    per = [x for p in ps for x in p[1]]
+    ih = [x for p in ps for x in p[2]]
+    Us = [np.ascontiguousarray(c.U, dtype=np.float64) for c in cases]
+    outs = [np.zeros_like(U) for U in Us]
+    vp = ctypes.c_void_p
+    L.emu_batch_stage1_f64.restype = ctypes.c_int
+    flag = L.emu_batch_stage1_f64(kernel, len(cases), (ctypes.c_int * len(n))(*n), (ctypes.c_int * len(per))(*per),
+                                  (ctypes.c_double * len(ih))(*ih), (ctypes.c_double * 5)(*ps[0][3]), int(rows),
+                                  int(ctas), (ctypes.c_double * len(dts))(*dts),
+                                  (vp * len(Us))(*[U.ctypes.data for U in Us]),
+                                  (vp * len(outs))(*[o.ctypes.data for o in outs]))
+    assert flag == 0, flag
+    return outs
+
+
 def _run_child(lib_path, san, args):
     """Runs this file as a script in a child process (the sanitizer runtime
     must be loaded first, with LD_PRELOAD) and returns its JSON result."""
@@ -152,10 +177,39 @@ def _child(lib_path, name, dtype, kernel, zchunk):
     return res
 
 
+BATCHES = {
+    "3d": (4, lambda: [inputs.random_smooth((19, 13, 11), seed=6, viscous=True, mu=0.01),
+                       inputs.random_smooth((40, 9, 7), seed=7, viscous=True, mu=0.01),
+                       inputs.random_smooth((8, 16, 20), seed=8, viscous=True, mu=0.01)]),
+    "2d_rows": (1, lambda: [inputs.random_blocks((150, 41, 1), seed=9), inputs.random_blocks((37, 19, 1), seed=10),
+                            inputs.random_blocks((40, 33, 1), seed=11)]),
+    "2d_tiles": (0, lambda: [inputs.random_blocks((37, 19, 1), seed=10), inputs.random_blocks((40, 33, 1), seed=11)]),
+}
+
+
+def _child_batch(lib_path, name, rows, ctas):
+    kernel, make = BATCHES[name]
+    cases = make()
+    dts = [1e-3 * (k + 1) for k in range(len(cases))]
+    outs = emulate_batch_stage1(lib_path, cases, kernel, rows, ctas, dts)
+    same = []
+    for c, o, dt in zip(cases, outs, dts):
+        want = emulate(lib_path, c, "f64", kernel, rows, rhs_only=False, a=0.0, b=1.0, dt=dt)
+        same.append(bool(np.array_equal(o, want)))
+    return {"same": same}
+
+
+@pytest.mark.parametrize("name,rows,ctas", [("3d", 4, 5), ("3d", 16, 64), ("2d_rows", 8, 7), ("2d_tiles", 1, 3)])
+def test_emulated_batch_equals_single_grid(emu_lib, name, rows, ctas):
+    lib_path, san = emu_lib
+    res = _run_child(lib_path, san, ["batch", name, rows, ctas])
+    assert all(res["same"]), res
+
+
 @pytest.mark.parametrize("run", RUNS, ids=[f"{r[0]}-{r[1]}-k{r[2]}-z{r[3]}" for r in RUNS])
 def test_emulated_kernel_vs_oracle(emu_lib, run):
     lib_path, san = emu_lib
-    res = _run_child(lib_path, san, run)
+    res = _run_child(lib_path, san, ["single", *run])
     tol = 1e-12 if run[1] == "f64" else 1e-5
     assert res["rhs"] <= tol, res
     if "stage" in res:
@@ -163,5 +217,9 @@ def test_emulated_kernel_vs_oracle(emu_lib, run):
 
 
 if __name__ == "__main__":
-    lib, name, dtype, kernel, zchunk = sys.argv[1:6]
-    print(json.dumps(_child(lib, name, dtype, int(kernel), int(zchunk))))
+    if sys.argv[2] == "batch":
+        lib, _, name, rows, ctas = sys.argv[1:6]
+        print(json.dumps(_child_batch(lib, name, int(rows), int(ctas))))
+    else:
+        lib, _, name, dtype, kernel, zchunk = sys.argv[1:7]
+        print(json.dumps(_child(lib, name, dtype, int(kernel), int(zchunk))))
