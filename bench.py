@@ -110,7 +110,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=-1)
-    p.add_argument("--only", choices=["batched", "adjoint", "variants", "learned_flux", "table3"], default=None,
+    p.add_argument("--only", choices=["batched", "batched3d", "adjoint", "variants", "learned_flux", "table3"],
+                   default=None,
                    help="run only the batched or the adjoint measurement and print it")
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--adjoint-steps", type=int, default=400)
@@ -606,6 +607,59 @@ def run_batched(steps=300, nsim=64, passes=3):
             "bitwise_equal_to_plain": bool(same), "gpu_launches_batched": 4 * steps}
 
 
+def run_batched3d(steps=40, nsim=16, passes=3, seed=5):
+    """16 Taylor-Green vortices (viscous, FP32, CFL steps) of sides drawn from
+    {32, 48, 64, 96, 128} with a seed: one persistent launch per stage over
+    the tile columns and z chunks of all simulations (the batch's default
+    variant, 32 planes per work item) under a captured graph, against the
+    same simulations advanced one by one through jf_rk3_run (one graph per
+    simulation, each with its default variant).  Median of `passes` passes."""
+    import numpy as np
+    import torch
+
+    from paper_2203_13760_gb300 import inputs, jf
+    sides = np.random.default_rng(seed).choice([32, 48, 64, 96, 128], size=nsim)
+    cases = [inputs.taylor_green(int(n)) for n in sides]
+    cells = sum(c.cells for c in cases)
+    p = cases[0].params()
+    b = jf.Batch([jf.make_grid(c.n, c.lo, c.hi, c.bc) for c in cases], gamma=p["gamma"], R=p["R"], mu=p["mu"],
+                 Pr=p["Pr"], dtype="f32", eps=p["eps"], cfl=p["cfl"], viscous=p["viscous"], heat=p["heat"])
+    U0s = [torch.tensor(c.U, dtype=torch.float32, device="cuda") for c in cases]
+
+    def timed(run, fields):
+        out = []
+        for _ in range(passes):
+            for F, U0 in zip(fields, U0s):
+                F.copy_(U0)
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record()
+            run(fields)
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(out)
+
+    Us = [u.clone() for u in U0s]
+    b.step(Us, steps)  # capture + first run
+    torch.cuda.synchronize()
+    t_batch = timed(lambda F: b.step(F, steps), Us)
+    solvers = [jf.Solver.from_case(c, dtype="f32") for c in cases]
+    Vs = [u.clone() for u in U0s]
+
+    def graphs(F):
+        for s_, V in zip(solvers, F):
+            s_.run(V, steps)
+
+    graphs(Vs)
+    torch.cuda.synchronize()
+    t_graph = timed(graphs, Vs)
+    return {"workload": f"{nsim} Taylor-Green vortices (viscous), sides {sorted(int(x) for x in sides)}, FP32, "
+                        "CFL 0.5", "cells": cells, "steps": steps, "unit": "cell-updates/s", "passes": passes,
+            "variant": b.variants()[0], "batched": cells * steps / t_batch,
+            "plain_graph_per_sim": cells * steps / t_graph, "speedup_vs_graph_per_sim": t_graph / t_batch}
+
+
 def run_adjoint(n=256, steps=400, ckpt=20, flow="kh"):
     """Kelvin-Helmholtz 256^2 (Re 1e4), FP32, fixed dt: loss = density L2
     mismatch after 400 steps; gradient w.r.t. the initial state through the
@@ -842,6 +896,8 @@ def main():
         torch.cuda.set_device(0)
         if args.only == "batched":
             out = run_batched()
+        elif args.only == "batched3d":
+            out = run_batched3d()
         elif args.only == "variants":
             out = run_variants()
         elif args.only == "learned_flux":
