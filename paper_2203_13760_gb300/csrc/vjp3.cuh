@@ -155,6 +155,89 @@ __device__ __forceinline__ void vjp3_load_m(const VjpArgs<T>& A, T* dst, int x0,
   }
 }
 
+// The next W plane and m plane of the march in registers: their global loads
+// are issued right after a face phase (vjp3_fetch), so that their latency
+// overlaps with the gather passes and the accumulator flush, and converted
+// and stored afterwards (vjp3_commit) -- the same values as vjp3_load_w and
+// vjp3_load_m.
+template <typename T, bool VISC, int BX, int BY, int NT>
+struct V3Fetch {
+  using G = V3Geo<BX, BY, VISC>;
+  static constexpr int PW = (G::CS + NT - 1) / NT, PM = (G::MCS + NT - 1) / NT;
+  T w[PW][5];
+  T m[PM][5];
+  bool ghost[PM];
+};
+
+template <typename T, bool VISC, int BX, int BY, int NT>
+__device__ __forceinline__ void vjp3_fetch(const VjpArgs<T>& A, V3Fetch<T, VISC, BX, BY, NT>& f, int x0, int y0,
+                                           int gzw, int gzm) {
+  using G = V3Geo<BX, BY, VISC>;
+  using F = V3Fetch<T, VISC, BX, BY, NT>;
+  const int kw = map_index(gzw, A.n[2], A.periodic[2]);
+#pragma unroll
+  for (int i = 0; i < F::PW; ++i) {
+    const int t = threadIdx.x + i * NT;
+    if (t < G::CS) {
+      const int ly = t / G::PX, lx = t - ly * G::PX;
+      const int gx = map_index(x0 + lx - G::H, A.n[0], A.periodic[0]);
+      const int gy = map_index(y0 + ly - G::H, A.n[1], A.periodic[1]);
+      const long long q = ((long long)kw * A.n[1] + gy) * A.n[0] + gx;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) f.w[i][c] = A.Us[q + c * A.N];
+    }
+  }
+  const bool gzout = !A.periodic[2] && (gzm < 0 || gzm >= A.n[2]);
+  const int km = map_index(gzm, A.n[2], A.periodic[2]);
+#pragma unroll
+  for (int i = 0; i < F::PM; ++i) {
+    const int t = threadIdx.x + i * NT;
+    if (t < G::MCS) {
+      const int ly = t / G::MPX, lx = t - ly * G::MPX;
+      const int rx = x0 + lx - 1, ry = y0 + ly - 1;
+      f.ghost[i] = gzout || (!A.periodic[0] && (rx < 0 || rx >= A.n[0])) ||
+                   (!A.periodic[1] && (ry < 0 || ry >= A.n[1]));
+      const int gx = map_index(rx, A.n[0], A.periodic[0]);
+      const int gy = map_index(ry, A.n[1], A.periodic[1]);
+      const long long q = ((long long)km * A.n[1] + gy) * A.n[0] + gx;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) f.m[i][c] = f.ghost[i] ? T(0) : A.lam[q + c * A.N];
+    }
+  }
+}
+
+template <typename T, bool VISC, int BX, int BY, int NT>
+__device__ __forceinline__ void vjp3_commit(const VjpArgs<T>& A, const Gas<T>& g, const V3Fetch<T, VISC, BX, BY, NT>& f,
+                                            T* dstw, T* dstm, bool& bad) {
+  using G = V3Geo<BX, BY, VISC>;
+  using F = V3Fetch<T, VISC, BX, BY, NT>;
+#pragma unroll
+  for (int i = 0; i < F::PW; ++i) {
+    const int t = threadIdx.x + i * NT;
+    if (t < G::CS) {
+      const T r = f.w[i][0];
+      const T inv = trcp(r);
+      const T u = f.w[i][1] * inv, v = f.w[i][2] * inv, w = f.w[i][3] * inv;
+      const T p = g.gm1 * (f.w[i][4] - T(0.5) * r * (u * u + v * v + w * w));
+      bad |= !(r > T(0)) || !(p > T(0));
+      dstw[t] = r;
+      dstw[G::CS + t] = u;
+      dstw[2 * G::CS + t] = v;
+      dstw[3 * G::CS + t] = w;
+      dstw[4 * G::CS + t] = p;
+      if (VISC) dstw[5 * G::CS + t] = p * inv * g.inv_R;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < F::PM; ++i) {
+    const int t = threadIdx.x + i * NT;
+    if (t < G::MCS) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) dstm[c * G::MCS + t] = f.ghost[i] ? T(0) : A.s_in * f.m[i][c];
+    }
+  }
+}
+
 // Accumulator slot src (plane gz, unmapped) added to Gacc and cleared: a
 // thread per plane cell maps the cell once and adds its components.
 template <typename T, bool VISC, int BX, int BY, int NT>
@@ -299,6 +382,11 @@ __global__ void __launch_bounds__(NT, MINB)
       }
     }
     __syncthreads();
+    // W of plane k + 3 (slot b, last read by this face phase) and m of plane
+    // k + 1 (the slot of plane k - 1) in flight during the passes below
+    V3Fetch<T, VISC, BX, BY, NT> nxt;
+    const bool more = k + 1 < kend;
+    if (more) vjp3_fetch<T, VISC, BX, BY, NT>(A, nxt, x0, y0, k + 3, k + 1);
     if constexpr (VISC) {
       // the x and y faces' centre-derivative cotangents of plane k: transposed
       // DC4 along y and x into plane k, along z into planes k -+ 1, 2; the
@@ -330,10 +418,7 @@ __global__ void __launch_bounds__(NT, MINB)
     // slots take plane k + 3 (W, cleared accumulator) and the m slot of plane
     // k - 1 takes plane k + 1
     vjp3_flush<T, VISC, BX, BY, NT>(A, Ar + b * G::PLANE, Gacc, x0, y0, k - 3);
-    if (k + 1 < kend) {
-      vjp3_load_w<T, VISC, BX, BY, NT>(A, g, Wr + b * G::PLANE, x0, y0, k + 3, bad);
-      vjp3_load_m<T, VISC, BX, BY, NT>(A, Mr + ((k - z0) & 1) * 5 * G::MCS, x0, y0, k + 1);
-    }
+    if (more) vjp3_commit<T, VISC, BX, BY, NT>(A, g, nxt, Wr + b * G::PLANE, Mr + ((k - z0) & 1) * 5 * G::MCS, bad);
     __syncthreads();
   }
   // the z-face cotangents still held (planes kend - 2 .. kend), then the
