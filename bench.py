@@ -610,14 +610,15 @@ def run_batched(steps=300, nsim=64, passes=3):
 def run_batched3d(steps=40, nsim=16, passes=3, seed=5):
     """16 Taylor-Green vortices (viscous, FP32, CFL steps) of sides drawn from
     {32, 48, 64, 96, 128} with a seed: one persistent launch per stage over
-    the tile columns and z chunks of all simulations (the batch's default
-    variant, 32 planes per work item) under a captured graph, against the
-    same simulations advanced one by one through jf_rk3_run (one graph per
-    simulation, each with its default variant).  Median of `passes` passes."""
+    the tile columns and z chunks of all simulations (the tile and planes per
+    work item the autotuner picks: cached choice, else timed now) under a
+    captured graph, against the same simulations advanced one by one through
+    jf_rk3_run (one graph per simulation, each with its default variant).
+    Median of `passes` passes."""
     import numpy as np
     import torch
 
-    from paper_2203_13760_gb300 import inputs, jf
+    from paper_2203_13760_gb300 import autotune, inputs, jf
     sides = np.random.default_rng(seed).choice([32, 48, 64, 96, 128], size=nsim)
     cases = [inputs.taylor_green(int(n)) for n in sides]
     cells = sum(c.cells for c in cases)
@@ -625,6 +626,12 @@ def run_batched3d(steps=40, nsim=16, passes=3, seed=5):
     b = jf.Batch([jf.make_grid(c.n, c.lo, c.hi, c.bc) for c in cases], gamma=p["gamma"], R=p["R"], mu=p["mu"],
                  Pr=p["Pr"], dtype="f32", eps=p["eps"], cfl=p["cfl"], viscous=p["viscous"], heat=p["heat"])
     U0s = [torch.tensor(c.U, dtype=torch.float32, device="cuda") for c in cases]
+    tuned = autotune.apply(b)
+    if tuned is None:
+        rec = autotune.tune(b, [u.clone() for u in U0s], steps=3, reps=3)
+        tuned, tune_ms = rec["variant"], rec["ms"]
+    else:
+        tune_ms = "cached"
 
     def timed(run, fields):
         out = []
@@ -656,7 +663,7 @@ def run_batched3d(steps=40, nsim=16, passes=3, seed=5):
     t_graph = timed(graphs, Vs)
     return {"workload": f"{nsim} Taylor-Green vortices (viscous), sides {sorted(int(x) for x in sides)}, FP32, "
                         "CFL 0.5", "cells": cells, "steps": steps, "unit": "cell-updates/s", "passes": passes,
-            "variant": b.variants()[0], "batched": cells * steps / t_batch,
+            "variant": b.variants()[tuned], "autotune_ms": tune_ms, "batched": cells * steps / t_batch,
             "plain_graph_per_sim": cells * steps / t_graph, "speedup_vs_graph_per_sim": t_graph / t_batch}
 
 
