@@ -15,16 +15,19 @@
 // loaded into the slot of plane k-3 (coalesced rows, periodic / zero-gradient
 // / slip-wall index map applied per cell, converted to W and T), then the x and y face
 // fluxes of plane k are written to shared memory, and each cell thread
-// computes the z face k+1/2 of its column, keeping the k-1/2 face in registers
-// from the previous plane.  Every face flux is evaluated once per CTA; only
-// the faces on the tile rim are evaluated twice (by both tiles).
+// computes the z face k+1/2 of its column, the k-1/2 face kept from the
+// previous plane in a per-column shared-memory slot.  Every face flux is
+// evaluated once per CTA; only the faces on the tile rim are evaluated twice
+// (by both tiles).
 //
 // Work balance.  The CTA has BY + 1 warps.  x faces: warp w < BY takes face
 // row w (faces 0..31), warp BY takes the 33rd face of every row; y faces: warp
 // w takes face row w (BY + 1 rows of 32); z faces and cell updates: warps
 // 0..BY-1.  Every warp thus computes about the same number of faces between
 // two barriers, and each warp reads shared memory row-wise (no bank
-// conflicts).  In 2D / 1D there is one plane and no ring.
+// conflicts).  2D and 1D tiles hold one plane and no ring; the row tiles of 2D
+// grids (DIM_Y2: one row of BX cells, BX + 32 threads) march along y with the
+// ring, their rows as its planes.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
