@@ -183,9 +183,11 @@ __device__ __forceinline__ float2 weno5_pair(float2 vm2, float2 vm1, float2 v0, 
 // both values share the indicators and their reciprocals; only the linear
 // weights and candidates differ.  With the differences D1..D4 of weno5_pair
 // the mirrored ones are D1' = -D4, D2' = -D3, D3' = -D2, D4' = -D1.
-// Equal to two weno5 calls up to rounding.
+// Equal to two weno5 calls up to rounding.  z = 1: WENO5-Z (Table 2; alpha_k
+// = d_k (1 + tau5 / (eps + beta_k)), tau5 = |beta_0 - beta_2|, the same for
+// the mirrored stencil, so the two values share the weights' factors too).
 template <typename T>
-JF_HD void weno5_cell(T vm2, T vm1, T v0, T vp1, T vp2, T eps, T& right, T& left) {
+JF_HD void weno5_cell(T vm2, T vm1, T v0, T vp1, T vp2, T eps, T& right, T& left, int z = 0) {
   const T D1 = vm2 - vm1, D2 = v0 - vm1, D3 = vp1 - v0, D4 = vp1 - vp2;
   const T c13 = T(13) / T(12);
   const T d0 = D2 + D1, e0 = T(3) * D2 + D1;
@@ -201,11 +203,27 @@ JF_HD void weno5_cell(T vm2, T vm1, T v0, T vp1, T vp2, T eps, T& right, T& left
     // alpha_k scaled by the common product (t0 t1 t2)^2 (one division per
     // value; the factors are >= eps, far inside the FP64 range):
     // right: (0.1 s1 s2, 0.6 s0 s2, 0.3 s0 s1); left (mirrored t):
-    // (0.1 s0 s1, 0.6 s0 s2, 0.3 s1 s2), s_k = t_k^2
-    const T s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
-    const T p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
-    const T a0 = T(0.1) * p12, a1 = T(0.6) * p02, a2 = T(0.3) * p01;
-    const T b0 = T(0.1) * p01, b2 = T(0.3) * p12;
+    // (0.1 s0 s1, 0.6 s0 s2, 0.3 s1 s2), s_k = t_k^2.  WENO5-Z: the factors
+    // 1 + tau5 / t_k scaled by t0 t1 t2: u_k = (t_k + tau5) t_i t_j, the left
+    // value taking them in reverse order
+    T a0, a1, a2, b0, b2;
+    if (z) {
+      const T tau = fabs(t0 - t2);
+      const T u0 = (t0 + tau) * (t1 * t2), u1 = (t1 + tau) * (t0 * t2), u2 = (t2 + tau) * (t0 * t1);
+      a0 = T(0.1) * u0;
+      a1 = T(0.6) * u1;
+      a2 = T(0.3) * u2;
+      b0 = T(0.1) * u2;
+      b2 = T(0.3) * u0;
+    } else {
+      const T s0 = t0 * t0, s1 = t1 * t1, s2 = t2 * t2;
+      const T p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
+      a0 = T(0.1) * p12;
+      a1 = T(0.6) * p02;
+      a2 = T(0.3) * p01;
+      b0 = T(0.1) * p01;
+      b2 = T(0.3) * p12;
+    }
     // one division for both values: 1/D_r = D_l / (D_r D_l) and the converse
     // (D >= 6e-25 as every s_k >= eps^2; the product stays far inside the
     // FP64 range)
@@ -214,7 +232,17 @@ JF_HD void weno5_cell(T vm2, T vm1, T v0, T vp1, T vp2, T eps, T& right, T& left
     right = v0 + (a0 * g0 + a1 * g1 + a2 * g2) * (Dl * inv);
     left = v0 + (b0 * h0 + a1 * h1 + b2 * h2) * (Dr * inv);
   } else {
-    const T r0 = trcp(t0 * t0), r1 = trcp(t1 * t1), r2 = trcp(t2 * t2);
+    T r0, r1, r2;
+    if (z) {
+      const T tau = fabs(t0 - t2);
+      r0 = (t0 + tau) * trcp(t0);
+      r1 = (t1 + tau) * trcp(t1);
+      r2 = (t2 + tau) * trcp(t2);
+    } else {
+      r0 = trcp(t0 * t0);
+      r1 = trcp(t1 * t1);
+      r2 = trcp(t2 * t2);
+    }
     const T a0 = T(0.1) * r0, a1 = T(0.6) * r1, a2 = T(0.3) * r2;
     const T b0 = T(0.1) * r2, b2 = T(0.3) * r0;
     right = v0 + (a0 * g0 + a1 * g1 + a2 * g2) * trcp(T(6) * (a0 + a1 + a2));
@@ -224,9 +252,9 @@ JF_HD void weno5_cell(T vm2, T vm1, T v0, T vp1, T vp2, T eps, T& right, T& left
 
 // weno5_cell for two components of one cell in the lanes of packed FP32x2
 // operations (the arithmetic of weno5_pair: indicators scaled by 12/13,
-// linear weights scaled by 10/3).
+// linear weights scaled by 10/3; z = 1: WENO5-Z as in weno5_cell).
 __device__ __forceinline__ void weno5_cell_pair(float2 vm2, float2 vm1, float2 v0, float2 vp1, float2 vp2, float eps,
-                                                float2& right, float2& left) {
+                                                float2& right, float2& left, int z = 0) {
   auto c = [](float x) { return make_float2(x, x); };
   const float2 m1 = c(-1.0f);
   const float2 D1 = __ffma2_rn(m1, vm1, vm2);
@@ -241,7 +269,18 @@ __device__ __forceinline__ void weno5_cell_pair(float2 vm2, float2 vm1, float2 v
   const float2 t1 = __ffma2_rn(d1, d1, __ffma2_rn(__fmul2_rn(k3, e1), e1, ke));
   const float2 t2 = __ffma2_rn(d2, d2, __ffma2_rn(__fmul2_rn(k3, e2), e2, ke));
   auto rcp2 = [](float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); };
-  const float2 r0 = rcp2(__fmul2_rn(t0, t0)), r1 = rcp2(__fmul2_rn(t1, t1)), r2 = rcp2(__fmul2_rn(t2, t2));
+  float2 r0, r1, r2;
+  if (z) {
+    const float2 d02 = __ffma2_rn(m1, t2, t0);
+    const float2 tau = make_float2(fabsf(d02.x), fabsf(d02.y));
+    r0 = __fmul2_rn(__fadd2_rn(t0, tau), rcp2(t0));
+    r1 = __fmul2_rn(__fadd2_rn(t1, tau), rcp2(t1));
+    r2 = __fmul2_rn(__fadd2_rn(t2, tau), rcp2(t2));
+  } else {
+    r0 = rcp2(__fmul2_rn(t0, t0));
+    r1 = rcp2(__fmul2_rn(t1, t1));
+    r2 = rcp2(__fmul2_rn(t2, t2));
+  }
   // right: v0 + (r0 g0 + r1 g1 + r2 g2) / (r0/3 + 2 r1 + r2)
   const float2 g0 = __ffma2_rn(c(5.0f / 18.0f), D2, __fmul2_rn(c(1.0f / 9.0f), D1));
   const float2 g1 = __ffma2_rn(c(2.0f / 3.0f), D3, __fmul2_rn(c(1.0f / 3.0f), D2));

@@ -323,6 +323,10 @@ enum { SCH_DEFAULT = 0, SCH_GENERAL = 1, SCH_ROE = 2, SCH_NN = 3, SCH_GENERAL_EX
 constexpr bool sch_general(int s) { return s == SCH_GENERAL || s == SCH_GENERAL_EXT; }
 constexpr bool sch_roe(int s) { return s == SCH_ROE || s == SCH_ROE_EXT; }
 constexpr bool sch_ext(int s) { return s == SCH_GENERAL_EXT || s == SCH_ROE_EXT || s == SCH_NN; }
+// Families whose kernels reconstruct once per cell and direction (the face
+// values of a plane in shared memory): the default scheme and the run-time
+// Godunov schemes with WENO5-JS / WENO5-Z.
+constexpr bool sch_pc(int s) { return s == SCH_DEFAULT || s == SCH_GENERAL; }
 
 // Flux-splitting face flux of the ROE setup (Section 3.3, Flux-Splitting
 // approach; Section 5): Roe average of the two cells beside the face, the
@@ -662,7 +666,7 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
 // at all: the caller pairs it with another cell's w).
 template <typename T, int D, int BX, int BY, int DIM, bool VISC, bool NOW = false>
 __device__ __forceinline__ void cell_recon(const RingView<T, BX, BY, DIM, VISC>& R, int x0, int y0, int shift, T eps,
-                                           T right[5], T left[5]) {
+                                           T right[5], T left[5], int z = 0) {
   using Ro = Roles<D>;
   auto val = [&](int c, int n) -> T {
     int x, y, e;
@@ -672,15 +676,16 @@ __device__ __forceinline__ void cell_recon(const RingView<T, BX, BY, DIM, VISC>&
   if constexpr (sizeof(T) == 4) {
     auto pr = [&](int a, int b, int n) { return make_float2(val(a, n), val(b, n)); };
     float2 r, l;
-    weno5_cell_pair(pr(0, 4, -2), pr(0, 4, -1), pr(0, 4, 0), pr(0, 4, 1), pr(0, 4, 2), eps, r, l);
+    weno5_cell_pair(pr(0, 4, -2), pr(0, 4, -1), pr(0, 4, 0), pr(0, 4, 1), pr(0, 4, 2), eps, r, l, z);
     right[0] = r.x; right[4] = r.y; left[0] = l.x; left[4] = l.y;
-    weno5_cell_pair(pr(1, 2, -2), pr(1, 2, -1), pr(1, 2, 0), pr(1, 2, 1), pr(1, 2, 2), eps, r, l);
+    weno5_cell_pair(pr(1, 2, -2), pr(1, 2, -1), pr(1, 2, 0), pr(1, 2, 1), pr(1, 2, 2), eps, r, l, z);
     right[1] = r.x; right[2] = r.y; left[1] = l.x; left[2] = l.y;
-    if constexpr (!NOW) weno5_cell<float>(val(3, -2), val(3, -1), val(3, 0), val(3, 1), val(3, 2), eps, right[3], left[3]);
+    if constexpr (!NOW)
+      weno5_cell<float>(val(3, -2), val(3, -1), val(3, 0), val(3, 1), val(3, 2), eps, right[3], left[3], z);
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c)
-      weno5_cell<T>(val(c, -2), val(c, -1), val(c, 0), val(c, 1), val(c, 2), eps, right[c], left[c]);
+      weno5_cell<T>(val(c, -2), val(c, -1), val(c, 0), val(c, 1), val(c, 2), eps, right[c], left[c], z);
   }
 }
 
@@ -742,14 +747,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     }
   };
 
-  // default scheme: WENO5 runs once per cell and direction (weno5_cell), the
+  // per-cell families (sch_pc): WENO5 runs once per cell and direction (weno5_cell), the
   // face values of a plane kept in shared memory (x, y; along z only the
   // current cell's value at its upper face, zl, is kept, by its column)
-  constexpr bool PC = SCH == SCH_DEFAULT;
+  constexpr bool PC = sch_pc(SCH);
+  const int wz = SCH == SCH_DEFAULT ? 0 : g.recon;  // per-cell WENO5: 0 JS, 1 Z
   constexpr int SX = BY * (BX + 2), SY = plane_dims(DIM) == 2 ? (BY + 2) * BX : 0;
   T* EX = Fy + 5 * G::NFY;  // [2][5][BY][BX+2] (PC only)
   T* EY = EX + 2 * 5 * SX;  // [2][5][BY+2][BX] (PC, tiles spanning y)
-  // default scheme, 3D: the net fluxes of a column's z faces in shared
+  // per-cell families, 3D: the net fluxes of a column's z faces in shared
   // memory, [2][5][NCELL] (face k + 1/2 in slot k & 1), written and read by
   // the column's own thread, so that they hold no registers across the phases
   constexpr bool ZS = PC && marches(DIM);
@@ -761,7 +767,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   T NFz_lo[5] = {T(0), T(0), T(0), T(0), T(0)};  // other schemes: the lower z face's net flux
   ZTangents ztan;  // FP32 z faces: the tangential stencils of the planes k .. k + 2
   PlaneRegs<T, BX, BY, DIM, VISC> next;  // plane k + 4, in flight while plane k is computed
-  PlaneMap<T, BX, BY, DIM, VISC> pmap;    // default scheme (no walls): the in-plane offsets of its cells
+  PlaneMap<T, BX, BY, DIM, VISC> pmap;    // per-cell families (no walls): the in-plane offsets of its cells
   if constexpr (PC && marches(DIM)) plane_map<T, BX, BY, DIM, VISC>(A, pmap, gx0, gy0);
   if (marches(DIM)) {
 #pragma unroll 1
@@ -774,8 +780,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       if constexpr (PC) {
         // face z0 - 1/2 from the values of cells z0 - 1 and z0; zl: cell z0 at z0 + 1/2
         T r[5], l[5], rz[5], lz[5];
-        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 0, g.eps, r, l);
-        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, rz, lz);
+        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 0, g.eps, r, l, wz);
+        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, rz, lz, wz);
 #pragma unroll
         for (int c = 0; c < 5; ++c) zl(c) = rz[c];
         T F[5], NF[5];
@@ -821,7 +827,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       }
     };
     // (default scheme in 3D: after the x face below)
-    if constexpr (SCH != SCH_DEFAULT || DIM != 3) load_cell();
+    if constexpr (!PC || DIM != 3) load_cell();
 
     T NFz_hi[5];
     if constexpr (PC) {
@@ -829,7 +835,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       // -1 .. BX) and y (rows -1 .. BY), and the z face of each column
       auto put_x = [&](int row, int j) {
         T r[5], l[5];
-        cell_recon<T, 0, BX, BY, DIM, VISC>(R, HALO + j, G::HY + row, 0, g.eps, r, l);
+        cell_recon<T, 0, BX, BY, DIM, VISC>(R, HALO + j, G::HY + row, 0, g.eps, r, l, wz);
         const int i = row * (BX + 2) + j + 1;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -841,7 +847,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       };
       auto put_y = [&](int row, int x) {
         T r[5], l[5];
-        cell_recon<T, 1, BX, BY, DIM, VISC>(R, HALO + x, G::HY + row, 0, g.eps, r, l);
+        cell_recon<T, 1, BX, BY, DIM, VISC>(R, HALO + x, G::HY + row, 0, g.eps, r, l, wz);
         const int i = (row + 1) * BX + x;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -862,7 +868,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         const int xcol = warp < BY ? lane - 1 : (hx ? BX - 1 + (lane & 1) : 0);
         const int yrow0 = warp < BY ? warp - 1 : BY - 1;
         T r[5], l[5];
-        cell_recon<T, 0, BX, BY, DIM, VISC, true>(R, HALO + xcol, G::HY + xrow, 0, g.eps, r, l);
+        cell_recon<T, 0, BX, BY, DIM, VISC, true>(R, HALO + xcol, G::HY + xrow, 0, g.eps, r, l, wz);
         const int ix = xrow * (BX + 2) + xcol + 1;
         if (hx) {
 #pragma unroll
@@ -874,7 +880,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
             }
           }
         }
-        cell_recon<T, 1, BX, BY, DIM, VISC, true>(R, HALO + lane, G::HY + yrow0, 0, g.eps, r, l);
+        cell_recon<T, 1, BX, BY, DIM, VISC, true>(R, HALO + lane, G::HY + yrow0, 0, g.eps, r, l, wz);
         const int iy = (yrow0 + 1) * BX + lane;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
@@ -889,7 +895,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         for (int n = 0; n < 5; ++n)
           wv[n] = make_float2(R.at(3, HALO + xcol + n - 2, G::HY + xrow, 0), R.at(3, HALO + lane, G::HY + yrow0 + n - 2, 0));
         float2 wr, wl;
-        weno5_cell_pair(wv[0], wv[1], wv[2], wv[3], wv[4], g.eps, wr, wl);
+        weno5_cell_pair(wv[0], wv[1], wv[2], wv[3], wv[4], g.eps, wr, wl, wz);
         if (hx && JF_CHECK(ix >= 0 && ix < SX, "JFDBG EX i=%d\n", ix)) {
           EX[3 * SX + ix] = wr.x;
           EX[8 * SX + ix] = wl.x;
@@ -914,7 +920,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
       if (marches(DIM) && cell_thread) {
         // face k + 1/2: the stored value of cell k (zl) and the lower value of cell k + 1
         T r[5], l[5], F[5], NF[5], zl0[5];
-        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, r, l);
+        cell_recon<T, 2, BX, BY, DIM, VISC>(R, HALO + tx, G::HY + ty, 1, g.eps, r, l, wz);
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           zl0[c] = zl(c);
@@ -1181,7 +1187,7 @@ __global__ void __launch_bounds__(Geo<BX, BY, DIM, VISC>::NT, MINB)
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
     const size_t need = sizeof(T) * (SCH == SCH_NN ? nn_smem_offset<T, DIM, VISC, BX, BY>() + NN_PARAMS
                                                    : stage_smem_elems<T, DIM, VISC, BX, BY>() +
-                                                         (SCH == SCH_DEFAULT ? recon_smem_elems<DIM, BX, BY>() : 0));
+                                                         (sch_pc(SCH) ? recon_smem_elems<DIM, BX, BY>() : 0));
     if (!JF_CHECK(dyn >= need, "JFDBG smem %u < %llu\n", dyn, (unsigned long long)need)) return;
     if (work && threadIdx.x == 0)
       for (int i = blockIdx.x; i < nwork; i += gridDim.x) {

@@ -11,7 +11,7 @@ template <typename T, int DIM, bool VISC, int BX, int BY, int SCH>
 constexpr size_t launch_smem() {
   return SCH == SCH_NN ? sizeof(T) * (nn_smem_offset<T, DIM, VISC, BX, BY>() + NN_PARAMS)
                        : stage_smem_bytes<T, DIM, VISC, BX, BY>() +
-                             (SCH == SCH_DEFAULT ? sizeof(T) * recon_smem_elems<DIM, BX, BY>() : 0);
+                             (sch_pc(SCH) ? sizeof(T) * recon_smem_elems<DIM, BX, BY>() : 0);
 }
 
 // MINB: CTAs per SM the register allocation must allow (__launch_bounds__).

@@ -23,11 +23,12 @@ unsigned char* emu_smem() { return g_smem; }
 
 using namespace jf;
 
-template <typename T, int DIM, bool VISC, int BX, int BY>
+template <typename T, int DIM, bool VISC, int BX, int BY, int SCH = SCH_DEFAULT>
 static void run(StageArgs<T> A, const Gas<T>& g) {
   using G = Geo<BX, BY, DIM, VISC>;
   if constexpr (DIM == DIM_Y2) rows_as_planes(A);
-  const size_t smem = sizeof(T) * (stage_smem_elems<T, DIM, VISC, BX, BY>() + recon_smem_elems<DIM, BX, BY>());
+  const size_t smem = sizeof(T) * (stage_smem_elems<T, DIM, VISC, BX, BY>() +
+                                    (sch_pc(SCH) ? recon_smem_elems<DIM, BX, BY>() : 0));
   gridDim.x = (A.nx + BX - 1) / BX;
   gridDim.y = plane_dims(DIM) == 2 ? (A.ny + BY - 1) / BY : 1;
   gridDim.z = marches(DIM) ? (A.nz + A.zchunk - 1) / A.zchunk : 1;
@@ -45,7 +46,7 @@ static void run(StageArgs<T> A, const Gas<T>& g) {
           th.emplace_back([&, t] {
             threadIdx = uint3{(unsigned)t, 0, 0};
             blockIdx = uint3{bx, by, bz};
-            stage_kernel<T, DIM, VISC, BX, BY, 1, SCH_DEFAULT>(A, nullptr, nullptr, 0, 0, g);
+            stage_kernel<T, DIM, VISC, BX, BY, 1, SCH>(A, nullptr, nullptr, 0, 0, g);
           });
         for (auto& x : th) x.join();
       }
@@ -80,7 +81,8 @@ static void run_batch(const StageArgs<T>& A0, const SimDesc<T>* sims, const Work
 
 // Kernels: 0 the 2D tiles (FP32 32 x 7, FP64 32 x 8), 1 the 128-wide row
 // tiles, 2 the 96-wide and 3 the 224-wide row tiles (FP32), 4 the 3D tiles
-// (FP32 32 x 7, FP64 32 x 4).
+// (FP32 32 x 7, FP64 32 x 4); 5 and 6 the run-time-scheme kernels (Table 2
+// Godunov variants) of 2D and 3D grids with those tiles.
 template <typename T>
 static int emulate(int kernel, bool visc, StageArgs<T>& A, const Gas<T>& g) {
   constexpr bool f32 = sizeof(T) == 4;
@@ -100,12 +102,21 @@ static int emulate(int kernel, bool visc, StageArgs<T>& A, const Gas<T>& g) {
     case 4:
       if (visc) run<T, 3, true, 32, f32 ? 7 : 4>(A, g); else run<T, 3, false, 32, f32 ? 7 : 4>(A, g);
       return 0;
+    case 5:
+      if (visc) run<T, 2, true, 32, f32 ? 7 : 8, SCH_GENERAL>(A, g);
+      else run<T, 2, false, 32, f32 ? 7 : 8, SCH_GENERAL>(A, g);
+      return 0;
+    case 6:
+      if (visc) run<T, 3, true, 32, f32 ? 7 : 4, SCH_GENERAL>(A, g);
+      else run<T, 3, false, 32, f32 ? 7 : 4, SCH_GENERAL>(A, g);
+      return 0;
   }
   return -1;
 }
 
 // One launch: out = L(Us) (rhs_only) or out = a Un + b (Us + dt L(Us)) (Un may
-// be null: a = 0).  gas = {gamma, R, mu, lambda, eps}.  Returns the device
+// be null: a = 0).  gas = {gamma, R, mu, lambda, eps, flux, recon, speeds}
+// (the last three as the jf_scheme codes).  Returns the device
 // flag (bit 0: non-physical state), or -1 for an unknown kernel.
 template <typename T>
 static int stage(int kernel, const int* n, const int* periodic, const double* inv_h, const double* gas, int zchunk,
@@ -145,6 +156,9 @@ static int stage(int kernel, const int* n, const int* periodic, const double* in
   g.mu = (T)gas[2];
   g.lambda = (T)gas[3];
   g.eps = (T)gas[4];
+  g.flux = (int)gas[5];
+  g.recon = (int)gas[6];
+  g.speeds = (int)gas[7];
   if (emulate<T>(kernel, gas[2] > 0.0, A, g) != 0) return -1;
   std::memcpy(out, o.get(), sizeof(T) * 5 * N);
   return flag;

@@ -4,8 +4,9 @@ for the shared memory and the fields) and run under AddressSanitizer and
 UBSan where the toolchain has them: every shared-memory and global access of
 the tiles stays inside its buffer, and the results match the oracle -- FP64
 to 1e-12 (right-hand side, rate norm; one stage), FP32 to 1e-5 -- for the 2D
-tiles, the row tiles of 2D grids (several row widths and chunk lengths) and
-the 3D z-march on ragged grids with periodic, zero-gradient and mixed
+tiles, the row tiles of 2D grids (several row widths and chunk lengths), the
+3D z-march, and the run-time-scheme kernels (HLL, Rusanov, Davis and Toro
+speeds, WENO5-Z) on ragged grids with periodic, zero-gradient and mixed
 boundaries.  The persistent batch form (descriptors and work items, with
 chunks of planes for the z-march kernels) is checked the same way: every
 simulation of an emulated batch stage equals the emulated single-grid stage
@@ -42,13 +43,33 @@ CASES = {
     "3d_smooth_visc_ragged": lambda: inputs.random_smooth((19, 13, 11), seed=6, viscous=True, mu=0.01),
 }
 
+
+def _scheme(make, **kw):
+    def f():
+        c = make()
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+    return f
+
+
+# run-time-scheme kernels (Table 2 Godunov variants, per-cell reconstruction)
+CASES.update({
+    "2d_blocks_hll_z": _scheme(CASES["2d_blocks_zg"], flux="hll", recon="weno5-z"),
+    "2d_visc_davis": _scheme(CASES["2d_smooth_visc_mixed"], speeds="davis"),
+    "3d_visc_rusanov_z": _scheme(CASES["3d_smooth_visc_ragged"], flux="rusanov", recon="weno5-z"),
+    "3d_visc_toro": _scheme(CASES["3d_smooth_visc_ragged"], speeds="toro"),
+})
+
 # (case, precision, kernel, z chunk): kernels as in emu.cpp (0: 2D tiles,
-# 1/2/3: row tiles 128/96/224 wide, 4: 3D tiles)
+# 1/2/3: row tiles 128/96/224 wide, 4: 3D tiles, 5/6: run-time-scheme 2D/3D)
 RUNS = [
     ("2d_smooth_visc_mixed", "f64", 0, 1), ("2d_smooth_visc_mixed", "f64", 1, 5),
     ("2d_smooth_visc_mixed", "f64", 1, 1000), ("2d_blocks_zg", "f64", 1, 7), ("2d_wide_y_periodic", "f64", 1, 16),
     ("2d_wide_y_periodic", "f32", 2, 3), ("2d_wide_y_periodic", "f32", 3, 41), ("2d_blocks_zg", "f32", 1, 1),
     ("3d_smooth_visc_ragged", "f64", 4, 4), ("3d_smooth_visc_ragged", "f32", 4, 11),
+    ("2d_blocks_hll_z", "f64", 5, 1), ("2d_visc_davis", "f64", 5, 1), ("2d_blocks_hll_z", "f32", 5, 1),
+    ("3d_visc_rusanov_z", "f64", 6, 4), ("3d_visc_toro", "f64", 6, 5), ("3d_visc_rusanov_z", "f32", 6, 11),
 ]
 
 
@@ -78,7 +99,7 @@ def emu_lib(tmp_path_factory):
     (src / "stage.cuh").write_text(text)
     san = _sanitizer_libs()
     lib = d / "libemu.so"
-    cmd = ["g++", "-std=c++20", "-O1", "-g", "-fno-omit-frame-pointer", "-shared", "-fPIC",
+    cmd = ["g++", "-std=c++20", "-O1", "-g1", "-fno-omit-frame-pointer", "-shared", "-fPIC",
            "-I", os.path.join(HERE, "cuda_stub"), "-I", str(src), os.path.join(HERE, "emu.cpp"), "-o", str(lib),
            "-lpthread"]
     if san:
@@ -97,7 +118,10 @@ def _params(case):
     inv_h = [n[a] / (p["hi"][a] - p["lo"][a]) for a in range(3)]
     mu = p["mu"] if p["viscous"] else 0.0
     lam = p["mu"] * p["gamma"] * p["R"] / ((p["gamma"] - 1.0) * p["Pr"]) if p["heat"] else 0.0
-    return n, periodic, inv_h, [p["gamma"], p["R"], mu, lam, p["eps"]]
+    codes = {"flux": {"hllc": 0, "hll": 1, "rusanov": 2}, "recon": {"weno5-js": 0, "weno5-z": 1},
+             "speeds": {"einfeldt": 0, "davis": 1, "toro": 2}}
+    scheme = [float(codes[k][p[k]]) for k in ("flux", "recon", "speeds")]
+    return n, periodic, inv_h, [p["gamma"], p["R"], mu, lam, p["eps"]] + scheme
 
 
 def emulate(lib_path, case, dtype, kernel, zchunk, rhs_only=True, a=0.0, b=1.0, dt=0.0, Un=None):
@@ -131,7 +155,7 @@ def emulate_batch_stage1(lib_path, cases, kernel, rows, ctas, dts):
     vp = ctypes.c_void_p
     L.emu_batch_stage1_f64.restype = ctypes.c_int
     flag = L.emu_batch_stage1_f64(kernel, len(cases), (ctypes.c_int * len(n))(*n), (ctypes.c_int * len(per))(*per),
-                                  (ctypes.c_double * len(ih))(*ih), (ctypes.c_double * 5)(*ps[0][3]), int(rows),
+                                  (ctypes.c_double * len(ih))(*ih), (ctypes.c_double * 8)(*ps[0][3]), int(rows),
                                   int(ctas), (ctypes.c_double * len(dts))(*dts),
                                   (vp * len(Us))(*[U.ctypes.data for U in Us]),
                                   (vp * len(outs))(*[o.ctypes.data for o in outs]))
@@ -139,18 +163,41 @@ def emulate_batch_stage1(lib_path, cases, kernel, rows, ctas, dts):
     return outs
 
 
-def _run_child(lib_path, san, args):
-    """Runs this file as a script in a child process (the sanitizer runtime
-    must be loaded first, with LD_PRELOAD) and returns its JSON result."""
+def _run_children(lib_path, san, jobs):
+    """Runs this file as a script in child processes (the sanitizer runtime
+    must be loaded first, with LD_PRELOAD), a few at a time, one per job (a
+    list of arguments); returns {job: (returncode, JSON result or output)}."""
     env = dict(os.environ)
     if san:
         env["LD_PRELOAD"] = " ".join(san)
         env["ASAN_OPTIONS"] = "detect_leaks=0:abort_on_error=1"
     env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), lib_path, *map(str, args)], capture_output=True,
-                         text=True, env=env, timeout=600)
-    assert out.returncode == 0, (out.stdout[-2000:], out.stderr[-4000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    width = max(1, min(4, (os.cpu_count() or 1) // 2))
+    out, running, queue = {}, [], list(jobs)
+    while queue or running:
+        while queue and len(running) < width:
+            job = queue.pop(0)
+            p = subprocess.Popen([sys.executable, os.path.abspath(__file__), lib_path, *map(str, job)],
+                                 stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+            running.append((job, p))
+        job, p = running.pop(0)
+        so, se = p.communicate(timeout=900)
+        out[tuple(job)] = (0, json.loads(so.strip().splitlines()[-1])) if p.returncode == 0 else \
+            (p.returncode, so[-2000:] + se[-4000:])
+    return out
+
+
+@pytest.fixture(scope="module")
+def results(emu_lib):
+    lib_path, san = emu_lib
+    jobs = [["single", *r] for r in RUNS] + [["batch", *b] for b in BATCH_RUNS]
+    return _run_children(lib_path, san, jobs)
+
+
+def _result(results, job):
+    rc, res = results[tuple(job)]
+    assert rc == 0, res
+    return res
 
 
 def _child(lib_path, name, dtype, kernel, zchunk):
@@ -199,17 +246,18 @@ def _child_batch(lib_path, name, rows, ctas):
     return {"same": same}
 
 
-@pytest.mark.parametrize("name,rows,ctas", [("3d", 4, 5), ("3d", 16, 64), ("2d_rows", 8, 7), ("2d_tiles", 1, 3)])
-def test_emulated_batch_equals_single_grid(emu_lib, name, rows, ctas):
-    lib_path, san = emu_lib
-    res = _run_child(lib_path, san, ["batch", name, rows, ctas])
+BATCH_RUNS = [("3d", 4, 5), ("3d", 16, 64), ("2d_rows", 8, 7), ("2d_tiles", 1, 3)]
+
+
+@pytest.mark.parametrize("name,rows,ctas", BATCH_RUNS)
+def test_emulated_batch_equals_single_grid(results, name, rows, ctas):
+    res = _result(results, ["batch", name, rows, ctas])
     assert all(res["same"]), res
 
 
 @pytest.mark.parametrize("run", RUNS, ids=[f"{r[0]}-{r[1]}-k{r[2]}-z{r[3]}" for r in RUNS])
-def test_emulated_kernel_vs_oracle(emu_lib, run):
-    lib_path, san = emu_lib
-    res = _run_child(lib_path, san, ["single", *run])
+def test_emulated_kernel_vs_oracle(results, run):
+    res = _result(results, ["single", *run])
     tol = 1e-12 if run[1] == "f64" else 1e-5
     assert res["rhs"] <= tol, res
     if "stage" in res:
