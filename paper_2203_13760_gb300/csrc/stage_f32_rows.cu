@@ -18,6 +18,9 @@ const StageVariant<float>* rows_variants_f32(int* count) {
       make_variant<float, DIM_Y2, false, 128, 1, 3, SCH_DEFAULT>(),
       make_variant<float, DIM_Y2, false, 224, 1, 2, SCH_DEFAULT>(),
       make_variant<float, DIM_Y2, false, 96, 1, 4, SCH_DEFAULT>(),
+      // the run-time Godunov schemes (Table 2 variants), 128 cells per row
+      make_variant<float, DIM_Y2, true, 128, 1, 3, SCH_GENERAL>(),
+      make_variant<float, DIM_Y2, false, 128, 1, 3, SCH_GENERAL>(),
   };
   *count = (int)(sizeof(table) / sizeof(table[0]));
   return table;

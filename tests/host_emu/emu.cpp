@@ -82,7 +82,8 @@ static void run_batch(const StageArgs<T>& A0, const SimDesc<T>* sims, const Work
 // Kernels: 0 the 2D tiles (FP32 32 x 7, FP64 32 x 8), 1 the 128-wide row
 // tiles, 2 the 96-wide and 3 the 224-wide row tiles (FP32), 4 the 3D tiles
 // (FP32 32 x 7, FP64 32 x 4); 5 and 6 the run-time-scheme kernels (Table 2
-// Godunov variants) of 2D and 3D grids with those tiles.
+// Godunov variants) of 2D and 3D grids with those tiles, 7 their 128-wide row
+// tiles.
 template <typename T>
 static int emulate(int kernel, bool visc, StageArgs<T>& A, const Gas<T>& g) {
   constexpr bool f32 = sizeof(T) == 4;
@@ -109,6 +110,10 @@ static int emulate(int kernel, bool visc, StageArgs<T>& A, const Gas<T>& g) {
     case 6:
       if (visc) run<T, 3, true, 32, f32 ? 7 : 4, SCH_GENERAL>(A, g);
       else run<T, 3, false, 32, f32 ? 7 : 4, SCH_GENERAL>(A, g);
+      return 0;
+    case 7:
+      if (visc) run<T, DIM_Y2, true, 128, 1, SCH_GENERAL>(A, g);
+      else run<T, DIM_Y2, false, 128, 1, SCH_GENERAL>(A, g);
       return 0;
   }
   return -1;

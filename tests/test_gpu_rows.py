@@ -93,6 +93,33 @@ def test_rows_fp64_vs_oracle(orc, name, chunk):
     assert rel_err(U.cpu().numpy(), want) <= 1e-12
 
 
+@pytest.mark.parametrize("scheme", [dict(flux="hll", recon="weno5-z"), dict(speeds="davis"),
+                                    dict(flux="rusanov", speeds="toro")])
+@pytest.mark.parametrize("name", ["blocks_zg_ragged", "mixed_bc_y_periodic_wide"])
+def test_rows_run_time_schemes_fp64_vs_oracle(orc, name, scheme):
+    """The row tiles of the run-time Godunov schemes (Table 2 variants):
+    right-hand side and four CFL steps against the oracle at 1e-12."""
+    case = CASES[name]()
+    for k, v in scheme.items():
+        setattr(case, k, v)
+    c = orc.config(**case.params())
+    s = jf.Solver.from_case(case, dtype="f64")
+    vs = row_variants(s, "8")
+    assert vs, s.variants()
+    s.set_variant(vs[0])
+    rate = case.cfl / orc.compute_dt(c, case.U)
+    got = s.rhs(dev(case.U, "f64")).cpu().numpy()
+    assert rate_err(got, orc.rhs(c, case.U), case.U, rate) <= 1e-12
+    U = dev(case.U, "f64")
+    dt_used = s.scalar()
+    want = case.U.copy()
+    for _ in range(4):
+        want = orc.rk3_step(c, want, orc.compute_dt(c, want))
+        s.rk3_step(U, None, dt_used)
+    s.sync()
+    assert rel_err(U.cpu().numpy(), want) <= 1e-12
+
+
 @pytest.mark.parametrize("name", ["smooth_visc_ragged", "mixed_bc_y_periodic_wide", "kh64"])
 def test_rows_fp32_ten_steps_vs_oracle(orc, name):
     """Every FP32 row width (auto chunk and 8 rows) within 1e-5 of the oracle

@@ -62,7 +62,8 @@ CASES.update({
 })
 
 # (case, precision, kernel, z chunk): kernels as in emu.cpp (0: 2D tiles,
-# 1/2/3: row tiles 128/96/224 wide, 4: 3D tiles, 5/6: run-time-scheme 2D/3D)
+# 1/2/3: row tiles 128/96/224 wide, 4: 3D tiles, 5/6/7: run-time-scheme 2D
+# tiles, 3D tiles and 2D row tiles)
 RUNS = [
     ("2d_smooth_visc_mixed", "f64", 0, 1), ("2d_smooth_visc_mixed", "f64", 1, 5),
     ("2d_smooth_visc_mixed", "f64", 1, 1000), ("2d_blocks_zg", "f64", 1, 7), ("2d_wide_y_periodic", "f64", 1, 16),
@@ -70,6 +71,7 @@ RUNS = [
     ("3d_smooth_visc_ragged", "f64", 4, 4), ("3d_smooth_visc_ragged", "f32", 4, 11),
     ("2d_blocks_hll_z", "f64", 5, 1), ("2d_visc_davis", "f64", 5, 1), ("2d_blocks_hll_z", "f32", 5, 1),
     ("3d_visc_rusanov_z", "f64", 6, 4), ("3d_visc_toro", "f64", 6, 5), ("3d_visc_rusanov_z", "f32", 6, 11),
+    ("2d_blocks_hll_z", "f64", 7, 6), ("2d_visc_davis", "f64", 7, 4), ("2d_visc_davis", "f32", 7, 1000),
 ]
 
 
