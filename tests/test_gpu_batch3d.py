@@ -2,8 +2,9 @@
 work items are tile columns and chunks of planes along z (32 by default,
 16 or 64 by jf_set_variant).  Each simulation is bitwise the single-grid
 path with the same tiles and chunk (FP32), the FP64 batch matches the oracle
-per simulation, and the trajectories of jf_batch_feed_forward equal fixed-dt
-single-grid steps."""
+per simulation, the trajectories of jf_batch_feed_forward equal fixed-dt
+single-grid steps, and the batch adjoint (jf_batch_step_vjp) of inviscid 3D
+grids equals the single-grid z-marching adjoint."""
 import re
 
 import numpy as np
@@ -132,4 +133,28 @@ def test_batch3d_feed_forward():
             s.rk3_step(U, dtt)
             s.sync()
             assert torch.equal(tr[t + 1], U), t
+    b.close()
+
+
+def test_batch3d_step_vjp_equals_single_grids():
+    """jf_batch_step_vjp over an uneven batch of inviscid 3D grids (the
+    per-face adjoint, its forward recompute through the batch's z-chunk work
+    items) equals each grid's single-grid adjoint (the z-marching adjoint
+    kernel) plus the addend, FP64 to rounding (atomic order)."""
+    cases = cases_3d(viscous=False)
+    b = batch_of(cases, "f64")
+    assert b.supports_step_vjp()
+    rng = np.random.default_rng(4)
+    Us = fields(cases, "f64")
+    lams = [torch.tensor(rng.standard_normal(c.U.shape), device="cuda") for c in cases]
+    adds = [torch.tensor(rng.standard_normal(c.U.shape), device="cuda") for c in cases]
+    dts = [2e-4, 3e-4, 2.5e-4]
+    got = b.step_vjp(Us, torch.tensor(dts, dtype=torch.float64, device="cuda"), lams, None, adds, None)
+    b.sync()
+    for i, c in enumerate(cases):
+        s = b.solver(i)
+        want = s.rk3_step_vjp(Us[i], s.scalar(dts[i]), lams[i])
+        s.sync()
+        want = want + adds[i]
+        assert (got[i] - want).abs().max().item() <= 1e-12 * want.abs().max().item(), i
     b.close()
