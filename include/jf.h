@@ -350,8 +350,11 @@ jf_status jf_batch_feed_forward(jf_handle batch, void* const* U0_ptrs, void* con
 jf_status jf_set_nn(jf_handle h, const void* theta, int nparams);
 
 /* Choose the launch variant of a handle (autotuner hook): `variant` indexes
- * the tile/schedule table of jf_variant_info; -1 restores the default.
- * Returns JF_ERR_ARG for an index outside the table. */
+ * the tile/schedule table of jf_variant_info; -1 restores the default (the
+ * first entry, except for 2D grids whose rows padded to whole 128-cell row
+ * tiles cover at most 8 % more cells than the first entry's tiles and give
+ * at least 12 rows of row tiles per resident CTA: then the row tiles, which
+ * march along y).  Returns JF_ERR_ARG for an index outside the table. */
 jf_status jf_set_variant(jf_handle h, int variant);
 
 /* Describe launch variant `variant` for the handle's dimensionality and
