@@ -658,8 +658,9 @@ __device__ __forceinline__ void face_flux(const RingView<T, BX, BY, DIM, VISC>& 
   if constexpr (VISC) face_visc_add<T, D, BX, BY, DIM, VISC>(R, x0, y0, g, inv_h, NF);
 }
 
-// WENO5-JS face values of one cell along D (default scheme, weno5_cell): the
-// cell sits `shift` cells along D from ring position (x0, y0, plane 0);
+// WENO5 face values of one cell along D (per-cell families, weno5_cell; z:
+// the WENO5-Z weights): the cell sits `shift` cells along D from ring
+// position (x0, y0, plane 0);
 // right[c] = v^-_{+1/2}, its value at the face to its right (the left state
 // of that face), left[c] = v^+_{-1/2} (the right state of the face to its
 // left).  FP32: (rho, p) and (u, v) in packed lanes, w alone (or, NOW, not
@@ -800,7 +801,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
     }
     __syncthreads();  // slot 0 (plane z0 - 3) is overwritten next
     load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring, gx0, gy0, z0 + 3);
-    // (default scheme: each plane fetches plane k + 4 after its reconstruction phase)
+    // (per-cell families: each plane fetches plane k + 4 after its reconstruction phase)
     if (!PC && z0 + 1 < z1) fetch_plane<T, BX, BY, DIM, VISC, WALLS>(A, next, gx0, gy0, z0 + 4);
   } else {
     load_plane<T, BX, BY, DIM, VISC, WALLS>(A, g, ring, gx0, gy0, 0);
@@ -811,8 +812,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
   for (int k = z0; k < z1; ++k) {
     set_view(base);
     // this cell's U_s and U^n for the stage combination, loaded ahead of the
-    // face computations so that their latency overlaps with them (default
-    // scheme in 3D: after the x face, which keeps their registers free during
+    // face computations so that their latency overlaps with them (per-cell
+    // families in 3D: after the x face, which keeps their registers free during
     // the reconstruction phase and the x face; the 3D march holds more state)
     const long long qc = ((long long)(marches(DIM) ? k : 0) * A.ny + gy) * A.nx + gx;
     T us[5], un[5];
@@ -826,7 +827,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Gas<T>& 
         }
       }
     };
-    // (default scheme in 3D: after the x face below)
+    // (per-cell families in 3D: after the x face below)
     if constexpr (!PC || DIM != 3) load_cell();
 
     T NFz_hi[5];
