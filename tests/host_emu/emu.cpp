@@ -81,7 +81,7 @@ static void run_batch(const StageArgs<T>& A0, const SimDesc<T>* sims, const Work
 
 // Kernels: 0 the 2D tiles (FP32 32 x 7, FP64 32 x 8), 1 the 128-wide row
 // tiles, 2 the 96-wide and 3 the 224-wide row tiles (FP32), 4 the 3D tiles
-// (FP32 32 x 7, FP64 32 x 4); 5 and 6 the run-time-scheme kernels (Table 2
+// (FP32 32 x 7, FP64 32 x 6); 5 and 6 the run-time-scheme kernels (Table 2
 // Godunov variants) of 2D and 3D grids with those tiles, 7 their 128-wide row
 // tiles.
 template <typename T>
@@ -101,7 +101,7 @@ static int emulate(int kernel, bool visc, StageArgs<T>& A, const Gas<T>& g) {
       if (visc) run<T, DIM_Y2, true, 224, 1>(A, g); else run<T, DIM_Y2, false, 224, 1>(A, g);
       return 0;
     case 4:
-      if (visc) run<T, 3, true, 32, f32 ? 7 : 4>(A, g); else run<T, 3, false, 32, f32 ? 7 : 4>(A, g);
+      if (visc) run<T, 3, true, 32, f32 ? 7 : 6>(A, g); else run<T, 3, false, 32, f32 ? 7 : 6>(A, g);
       return 0;
     case 5:
       if (visc) run<T, 2, true, 32, f32 ? 7 : 8, SCH_GENERAL>(A, g);
@@ -195,7 +195,7 @@ static int batch_stage1(int kernel, int nsim, const int* n, const int* p, const 
   std::vector<WorkItem> items;
   const bool f32 = sizeof(T) == 4;
   const int bx = kernel == 0 || kernel == 4 ? 32 : (kernel == 1 ? 128 : (kernel == 2 ? 96 : 224));
-  const int by = kernel == 0 ? (f32 ? 7 : 8) : (kernel == 4 ? (f32 ? 7 : 4) : 1);
+  const int by = kernel == 0 ? (f32 ? 7 : 8) : (kernel == 4 ? (f32 ? 7 : 6) : 1);
   for (int s = 0; s < nsim; ++s) {
     const long long N = (long long)n[3 * s] * n[3 * s + 1] * n[3 * s + 2];
     us.emplace_back(new T[5 * N]);
@@ -253,8 +253,8 @@ static int batch_stage1(int kernel, int nsim, const int* n, const int* p, const 
       else run_batch<T, DIM_Y2, false, 128, 1>(A0, sims.get(), work.get(), nw, 1, g, ctas);
       break;
     case 4:
-      if (visc) run_batch<T, 3, true, 32, f32 ? 7 : 4>(A0, sims.get(), work.get(), nw, 1, g, ctas);
-      else run_batch<T, 3, false, 32, f32 ? 7 : 4>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      if (visc) run_batch<T, 3, true, 32, f32 ? 7 : 6>(A0, sims.get(), work.get(), nw, 1, g, ctas);
+      else run_batch<T, 3, false, 32, f32 ? 7 : 6>(A0, sims.get(), work.get(), nw, 1, g, ctas);
       break;
     default:
       return -1;

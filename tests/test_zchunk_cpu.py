@@ -65,7 +65,9 @@ def test_bench_grid_choice():
 
 
 def test_other_tiles_and_occupancy():
-    # 32 x 4 tile at one CTA per SM (the FP64 default): tiles = 8 x 64 per plane
+    # 32 x 6 tile at one CTA per SM (the FP64 default): tiles = 8 x 43 per plane;
+    # 32 x 4 (8 x 64)
+    assert jf.auto_zchunk((256, 256, 256), tile=(32, 6), ctas_per_sm=1) == expected((256, 256, 256), (32, 6), 1)
     assert jf.auto_zchunk((256, 256, 256), tile=(32, 4), ctas_per_sm=1) == expected((256, 256, 256), (32, 4), 1)
     # a tiny grid never goes below one plane
     assert jf.auto_zchunk((8, 8, 1)) == 1
